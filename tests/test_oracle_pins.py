@@ -1,0 +1,409 @@
+"""Pins of the CPU oracle against values and constructions that do not come
+from the oracle itself: the paper's worked example and quoted dimensions,
+brute-force enumerations, Eq. (1) built from Kronecker products, closed forms
+and exact identities of the symmetry-adapted basis."""
+from __future__ import annotations
+
+import os
+from math import comb
+
+import numpy as np
+import pytest
+
+import oracle as orc
+import qs3_inputs as qi
+from tests import pins
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def olat(spec: qi.LatticeSpec) -> orc.Lattice:
+    return orc.Lattice(**spec.as_dict())
+
+
+def read_kv(name):
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, *v = line.split()
+            out[k] = [int(x) for x in v]
+    return out
+
+
+# ------------------------------------------------------------ Eq. a_of_n, Alg 1
+
+
+def test_worked_example_fbar():
+    g = read_kv("fbar_worked_example.txt")
+    N, nd = g["N"][0], g["Nd"][0]
+    assert orc.F(N, g["n"]) == g["a"][0]
+    n, trace = orc.f_bar(N, nd, g["a"][0])
+    assert n == g["n"]
+    assert trace == g["trace"]
+
+
+@pytest.mark.parametrize("N,nd", [(1, 1), (5, 0), (6, 1), (7, 3), (9, 4), (10, 5), (12, 6), (12, 12), (13, 2)])
+def test_rank_is_colex_position(N, nd):
+    subs = pins.colex_subsets(N, nd)
+    assert orc.binom(N, nd) == len(subs) == comb(N, nd)
+    for k, c in enumerate(subs):
+        n1 = [s + 1 for s in c]
+        assert orc.F(N, n1) == k + 1
+        assert orc.f_bar(N, nd, k + 1)[0] == n1
+    if nd:
+        lists = orc.unrank_all(N, nd)
+        assert [tuple(r) for r in lists] == subs
+
+
+def test_rank_large_values():
+    # C(1000,4) and C(1024,3): ranks beyond 2^32 survive the round trip
+    for N, nd in ((1000, 4), (1024, 3), (100, 8)):
+        D = orc.binom(N, nd)
+        assert D == comb(N, nd)
+        rng = np.random.default_rng(N)
+        for _ in range(200):
+            c = sorted(rng.choice(N, nd, replace=False) + 1)
+            a = orc.F(N, c)
+            expect = 1 + sum(comb(int(c[m]) - 1, m + 1) for m in range(nd))
+            assert a == expect
+            assert orc.f_bar(N, nd, a)[0] == [int(x) for x in c]
+    assert orc.binom(200, 100) == 0          # beyond 2^63: reported as overflow
+
+
+def test_spin_exchange_matches_set_moves():
+    rng = np.random.default_rng(7)
+    N, nd = 15, 4
+    for _ in range(300):
+        c = sorted(int(x) for x in rng.choice(N, nd, replace=False) + 1)
+        r, rp = sorted(int(x) for x in rng.choice(N, 2, replace=False) + 1)
+        got = orc.spin_exchange_index(N, c, r, rp)
+        inr, inrp = r in c, rp in c
+        if inr == inrp:
+            assert got == 0
+            continue
+        new = set(c) ^ {r, rp}
+        assert got == orc.F(N, sorted(new))
+        assert got == pins.colex_subsets(N, nd).index(tuple(s - 1 for s in sorted(new))) + 1
+
+
+# --------------------------------------------------------------- Eq. (1), Alg 4
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_dense_u1_equals_kronecker_hamiltonian(seed):
+    spec = qi.random_graph(7, 11, seed)
+    Hfull = pins.kron_hamiltonian(spec)
+    for nd in range(0, 8):
+        P = pins.sector_projector(7, nd)
+        Hk = (P.T @ Hfull @ P)
+        assert np.abs(Hk.imag).max() < 1e-14
+        Ho = orc.dense_u1(olat(spec), nd)
+        np.testing.assert_allclose(Ho, Hk.real, atol=1e-13, rtol=0)
+        # the full space is block diagonal in N_down (U(1) symmetry of Eq. (1))
+    mask = np.zeros_like(Hfull, dtype=bool)
+    for nd in range(8):
+        P = pins.sector_projector(7, nd).astype(bool)
+        idx = np.where(P.any(1))[0]
+        mask[np.ix_(idx, idx)] = True
+    assert np.abs(Hfull[~mask]).max() == 0
+
+
+def test_dense_u1_bit_construction_chain16():
+    spec = qi.chain(16)
+    for nd in (1, 2, 3):
+        np.testing.assert_allclose(orc.dense_u1(olat(spec), nd), pins.bit_hamiltonian_sector(spec, nd),
+                                   atol=1e-13, rtol=0)
+
+
+def test_hphi_u1_matches_dense():
+    spec = qi.disordered_open_square(5, seed=3)
+    lat = olat(spec)
+    for nd in (1, 3):
+        H = orc.dense_u1(lat, nd)
+        x = qi.gaussian_start(11, H.shape[0], True)
+        np.testing.assert_allclose(orc.hphi_u1(lat, nd, x), H @ x, atol=1e-12, rtol=0)
+        rows = np.array([0, 3, H.shape[0] - 1])
+        np.testing.assert_allclose(orc.hphi_u1_rows(lat, nd, x, rows), (H @ x)[rows], atol=1e-12, rtol=0)
+
+
+def test_one_and_two_magnon_chain_against_closed_forms():
+    N = 16
+    spec = qi.chain(N)
+    H1 = orc.dense_u1(olat(spec), 1)
+    e1 = np.sort(np.linalg.eigvalsh(H1))
+    expect = np.sort([pins.one_magnon_energy(spec, (k, 0, 0)) for k in range(N)])
+    np.testing.assert_allclose(e1, expect, atol=1e-12)
+    # two magnons: block of Eq. (1) built on bit strings (independent construction)
+    H2 = orc.dense_u1(olat(spec), 2)
+    np.testing.assert_allclose(np.linalg.eigvalsh(H2), np.linalg.eigvalsh(pins.bit_hamiltonian_sector(spec, 2)),
+                               atol=1e-12)
+
+
+# ------------------------------------------------------- Alg 5-7, dimensions
+
+
+@pytest.mark.parametrize("dims,nd", [((12, 1, 1), 3), ((12, 1, 1), 4), ((8, 1, 1), 4), ((4, 3, 1), 3),
+                                     ((4, 4, 1), 4), ((3, 3, 2), 3), ((6, 1, 1), 0), ((6, 1, 1), 6)])
+def test_sector_dims_closed_form_and_sum(dims, nd):
+    spec = qi.hypercubic(dims)
+    lat = olat(spec)
+    N = spec.n_sites
+    total = 0
+    for K in qi.all_k(dims):
+        sec = orc.mk_list(lat, nd, K)
+        assert sec.dim == pins.sector_dim_closed_form(dims, nd, K)
+        total += sec.dim
+    assert total == comb(N, nd)
+
+
+def test_paper_dimensions_by_closed_form():
+    for line in open(os.path.join(GOLDEN, "paper_dims.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        kind, Lx, Ly, Lz, nd, val = line.split()
+        L = (int(Lx), int(Ly), int(Lz))
+        N = L[0] * L[1] * L[2]
+        if kind == "U1":
+            assert orc.binom(N, int(nd)) == int(val)
+        else:
+            assert pins.sector_dim_closed_form(L, int(nd), (0, 0, 0)) == int(val)
+
+
+def test_representatives_are_orbit_minima():
+    dims = (4, 3, 1)
+    spec = qi.hypercubic(dims)
+    lat = olat(spec)
+    nd = 3
+    subs = pins.colex_subsets(12, nd)
+    index = {c: k + 1 for k, c in enumerate(subs)}
+    for K in qi.all_k(dims):
+        sec = orc.mk_list(lat, nd, K)
+        reps = set(int(a) for a in sec.sigma1)
+        for c in subs:
+            orb = {pins.translate_set(c, t, dims) for t in pins.group(dims)}
+            rep = min(index[o] for o in orb)
+            stab = sum(1 for t in pins.group(dims) if pins.translate_set(c, t, dims) == c)
+            compat = all(abs(np.exp(2j * np.pi * sum(K[a] * t[a] / dims[a] for a in range(3))) - 1) < 1e-9
+                         for t in pins.group(dims) if pins.translate_set(c, t, dims) == c)
+            a = index[c]
+            r, l = orc.representative(lat, nd, a)
+            assert r == rep
+            assert index[pins.translate_set(c, l, dims)] == rep
+            assert (a in reps) == (a == rep and compat)
+            if a in reps:
+                i = list(sec.sigma1).index(a)
+                assert sec.stab[i] == stab
+                assert abs(sec.Nak[i] - 12 * stab) < 1e-9
+        assert list(sec.sigma1) == sorted(sec.sigma1)
+
+
+# ----------------------------------------------------------- Alg 8 / 9, Eq.
+
+
+def _unfold_matrix(sec):
+    d = sec.dim
+    return np.stack([orc.unfold(sec, np.eye(d)[i]) for i in range(d)], 1)
+
+
+@pytest.mark.parametrize("dims,nd", [((12, 1, 1), 3), ((4, 3, 1), 3), ((3, 3, 2), 2)])
+def test_unfolded_states_are_translation_eigenstates(dims, nd):
+    """|a,k> of Eq. (akstate): unit norm, orthogonal, T|a,k> = e^{ik}|a,k>."""
+    spec = qi.hypercubic(dims)
+    subs = pins.colex_subsets(spec.n_sites, nd)
+    index = {c: k for k, c in enumerate(subs)}
+    for K in qi.all_k(dims)[:5]:
+        sec = orc.mk_list(olat(spec), nd, K)
+        U = _unfold_matrix(sec)
+        np.testing.assert_allclose(U.conj().T @ U, np.eye(sec.dim), atol=1e-12)
+        for a in range(3):
+            if dims[a] == 1:
+                continue
+            t = [0, 0, 0]
+            t[a] = 1
+            perm = [index[pins.translate_set(c, t, dims)] for c in subs]
+            TU = np.zeros_like(U)
+            TU[perm, :] = U
+            ph = np.exp(2j * np.pi * K[a] / dims[a])
+            np.testing.assert_allclose(TU, ph * U, atol=1e-12)
+
+
+@pytest.mark.parametrize("dims,nd,anis", [((12, 1, 1), 3, 1.0), ((4, 3, 1), 3, 0.7), ((3, 3, 2), 3, 1.3),
+                                          ((5, 3, 1), 2, 0.5)])
+def test_dense_k_hermitian_unfolds_and_spectra_union(dims, nd, anis):
+    spec = qi.hypercubic(dims, J=1.0, Jz=anis)
+    lat = olat(spec)
+    HU = orc.dense_u1(lat, nd)
+    eig_all = []
+    for K in qi.all_k(dims):
+        sec = orc.mk_list(lat, nd, K)
+        if sec.dim == 0:
+            continue
+        Hk = orc.dense_k(sec)
+        np.testing.assert_allclose(Hk, Hk.conj().T, atol=1e-13)
+        U = _unfold_matrix(sec)
+        np.testing.assert_allclose(HU @ U, U @ Hk, atol=1e-12)
+        x = qi.gaussian_start(5, sec.dim, True)
+        np.testing.assert_allclose(orc.hphi_k(sec, x), Hk @ x, atol=1e-12)
+        rows = np.arange(0, sec.dim, 3)
+        np.testing.assert_allclose(orc.hphi_k_rows(sec, x, rows), (Hk @ x)[rows], atol=1e-12)
+        eig_all.append(np.linalg.eigvalsh(Hk))
+    np.testing.assert_allclose(np.sort(np.concatenate(eig_all)), np.linalg.eigvalsh(HU), atol=1e-11)
+
+
+@pytest.mark.parametrize("dims", [(10, 1, 1), (5, 4, 1), (4, 3, 3)])
+def test_one_magnon_dispersion_k_sectors(dims):
+    spec = qi.hypercubic(dims, J=1.0, Jz=0.8)
+    for K in qi.all_k(dims):
+        sec = orc.mk_list(olat(spec), 1, K)
+        assert sec.dim == 1
+        E = orc.dense_k(sec)[0, 0].real
+        assert abs(E - pins.one_magnon_energy(spec, K)) < 1e-12
+
+
+def test_su2_descent_isotropic():
+    """Isotropic Eq. (1): spec(N_down-1, k) is contained in spec(N_down, k)."""
+    dims = (4, 3, 1)
+    spec = qi.hypercubic(dims)
+    lat = olat(spec)
+    for K in qi.all_k(dims)[:6]:
+        e3 = np.linalg.eigvalsh(orc.dense_k(orc.mk_list(lat, 3, K)))
+        e2 = np.linalg.eigvalsh(orc.dense_k(orc.mk_list(lat, 2, K)))
+        for e in e2:
+            assert np.min(np.abs(e3 - e)) < 1e-10
+
+
+# --------------------------------------------------- Alg 10, correlations, CF
+
+
+def test_lanczos_and_trl_lowest_eigenvalues_chain16():
+    spec = qi.chain(16)
+    lat = olat(spec)
+    H = orc.dense_u1(lat, 3)
+    ev = np.linalg.eigvalsh(H)
+    v0 = qi.gaussian_start(1, H.shape[0], False).astype(np.complex128)
+    E0, vec = orc.lanczos_ground(lambda x: orc.hphi_u1(lat, 3, x), v0, max_iter=200)
+    assert abs(E0 - ev[0]) < 1e-12 * abs(ev[0])
+    r = orc.hphi_u1(lat, 3, vec) - E0 * vec
+    assert np.linalg.norm(r) < 1e-10
+    e, vecs, it = orc.thick_restart_lanczos(lambda x: orc.hphi_u1(lat, 3, x), v0, 8, 32, 500, 1e-14)
+    np.testing.assert_allclose(e[:4], ev[:4], atol=1e-11)
+
+
+def test_trl_k_sector_square():
+    spec = qi.square(4, 3)
+    lat = olat(spec)
+    sec = orc.mk_list(lat, 4, (1, 0, 0))
+    ev = np.linalg.eigvalsh(orc.dense_k(sec))
+    v0 = qi.gaussian_start(2, sec.dim, True)
+    e, vecs, it = orc.thick_restart_lanczos(lambda x: orc.hphi_k(sec, x), v0, 6, 20, 500, 1e-14)
+    np.testing.assert_allclose(e[:4], ev[:4], atol=1e-10)
+
+
+def test_correlations_against_kronecker_operators():
+    spec = qi.random_graph(7, 10, 4)
+    Hfull = pins.kron_hamiltonian(spec)
+    nd = 3
+    P = pins.sector_projector(7, nd)
+    rng = np.random.default_rng(0)
+    phi = rng.normal(size=P.shape[1]) + 1j * rng.normal(size=P.shape[1])
+    phi /= np.linalg.norm(phi)
+    full = P @ phi
+    szsz, spsm, sz = orc.corr_u1(7, nd, phi)
+    s_p = np.array([[0, 1], [0, 0]])        # s^+ raises: |down> -> |up>
+    s_m = s_p.T
+    szm = np.diag([0.5, -0.5])
+    eye = np.eye(2)
+
+    def op(m):
+        out = np.array([[1.0 + 0j]])
+        for i in reversed(range(7)):
+            out = np.kron(out, m.get(i, eye))
+        return out
+    for i in range(7):
+        assert abs(sz[i] - np.vdot(full, op({i: szm}) @ full).real) < 1e-12
+        for j in range(7):
+            zz = np.vdot(full, op({i: szm}) @ op({j: szm}) @ full) if i != j else np.vdot(full, op({i: szm @ szm}) @ full)
+            assert abs(szsz[i, j] - zz.real) < 1e-12
+            pm = np.vdot(full, op({i: s_p}) @ op({j: s_m}) @ full) if i != j else np.vdot(full, op({i: s_p @ s_m}) @ full)
+            assert abs(spsm[i, j] - pm) < 1e-12
+    del Hfull
+
+
+def _smq_dense_u1(N, nd, phi_u, Q, L):
+    """S^-_q = N^{-1/2} sum_r e^{-iq.r} s^-_r applied on colex-ordered sets."""
+    src = pins.colex_subsets(N, nd)
+    dst = {c: k for k, c in enumerate(pins.colex_subsets(N, nd + 1))}
+    out = np.zeros(len(dst), np.complex128)
+    for k, c in enumerate(src):
+        for r in range(N):
+            if r in c:
+                continue
+            x, y, z = pins.coords(r, L)
+            qr = 2 * np.pi * (Q[0] * x / L[0] + Q[1] * y / L[1] + Q[2] * z / L[2])
+            out[dst[tuple(sorted(c + (r,)))]] += np.exp(-1j * qr) * phi_u[k] / np.sqrt(N)
+    return out
+
+
+@pytest.mark.parametrize("dims,nd", [((12, 1, 1), 2), ((4, 3, 1), 2), ((3, 3, 2), 1)])
+def test_smq_push_form_against_definition(dims, nd):
+    spec = qi.hypercubic(dims)
+    lat = olat(spec)
+    N = spec.n_sites
+    for K in qi.all_k(dims)[:3]:
+        src = orc.mk_list(lat, nd, K)
+        phi = qi.gaussian_start(3, src.dim, True)
+        for Q in qi.all_k(dims)[:4]:
+            K2 = tuple((K[a] + Q[a]) % dims[a] for a in range(3))
+            dst = orc.mk_list(lat, nd + 1, K2)
+            got = orc.smq(src, phi, Q, dst)
+            want = orc.fold(dst, _smq_dense_u1(N, nd, orc.unfold(src, phi), Q, dims))
+            np.testing.assert_allclose(got, want, atol=1e-12)
+
+
+def test_smq_on_vacuum_has_unit_norm():
+    dims = (4, 3, 1)
+    lat = olat(qi.hypercubic(dims))
+    vac = orc.mk_list(lat, 0, (0, 0, 0))
+    assert vac.dim == 1
+    for Q in qi.all_k(dims):
+        dst = orc.mk_list(lat, 1, Q)
+        v = orc.smq(vac, np.ones(1, np.complex128), Q, dst)
+        assert abs(np.vdot(v, v).real - 1.0) < 1e-13
+
+
+def test_continued_fraction_equals_lorentzian_sum():
+    """Eq. (cfe) with a full Lanczos run equals the spectral sum of the
+    resolvent built from a dense eigendecomposition; the weights sum to the
+    static factor |S_q phi|^2 (sum rule)."""
+    dims = (8, 1, 1)
+    spec = qi.hypercubic(dims)
+    lat = olat(spec)
+    gs_sec = None
+    best = None
+    for K in qi.all_k(dims):
+        sec = orc.mk_list(lat, 2, K)
+        e, v = np.linalg.eigh(orc.dense_k(sec))
+        if best is None or e[0] < best[0] - 1e-12:
+            best, gs_sec = (e[0], v[:, 0]), sec
+    E0, phi = best
+    Q = (3, 0, 0)
+    K2 = tuple((gs_sec.K[a] + Q[a]) % dims[a] for a in range(3))
+    dst = orc.mk_list(lat, 3, K2)
+    v = orc.smq(gs_sec, phi, Q, dst)
+    norm2 = np.vdot(v, v).real
+    Hd = orc.dense_k(dst)
+    alpha, beta, Psi, b0 = orc.lanczos(lambda x: Hd @ x, v, 200)
+    assert abs(b0 ** 2 - norm2) < 1e-13
+    omega = np.linspace(-2, 6, 801)
+    h, eta = 1.5, 0.05
+    s_cf = orc.continued_fraction(alpha, beta, norm2, omega, E0, eta, shift=h)
+    en, U = np.linalg.eigh(Hd)
+    w = np.abs(U.conj().T @ v) ** 2
+    s_ex = sum(w[n] * (eta / np.pi) / ((omega + E0 - h - en[n]) ** 2 + eta ** 2) for n in range(len(en)))
+    np.testing.assert_allclose(s_cf, s_ex, atol=1e-10 * s_ex.max())
+    T = orc.tridiag(alpha, beta[:-1])
+    eT, C = np.linalg.eigh(T)
+    assert abs(norm2 * (C[0] ** 2).sum() - norm2) < 1e-12
+    # weights at the poles equal the spectral weights
+    assert abs((norm2 * C[0] ** 2).max() - w.max()) < 1e-10
