@@ -1,0 +1,193 @@
+/*
+ * qs3.h -- C ABI of libqs3.so, a GB300 (sm_103a) implementation of the hot
+ * path of QS^3 (Ueda, Yunoki, Shimokawa, "Quantum spin solver near
+ * saturation"): the matrix-free product H Phi of the spin-1/2 XXZ model in the
+ * basis fixed by the number N_down of down spins and the wave number k, the
+ * Lanczos / thick-restart Lanczos iteration that drives it, two-point
+ * functions, S(q) and the continued-fraction S(q, omega).
+ *
+ * Conventions (all calls):
+ *  - Sites are 0-based.  With a translation group (L[0], L[1], L[2]) the
+ *    site index is r = x + Lx (y + Ly z) and T^t moves site coordinates by
+ *    +t modulo L.
+ *  - A U(1) basis state is the ascending list c_1 < ... < c_Nd of its
+ *    down-spin sites; its rank is rank0 = sum_m C(c_m, m) (m = 1..Nd), the
+ *    paper's index a of Eq. (a_of_n) minus one.  No bit strings are used.
+ *  - A k-sector is the list sigma of representatives (minimum rank over the
+ *    translation orbit, Sec. "Representative states ...") that are
+ *    compatible with K, sorted by rank, with |Stab| of each; the
+ *    normalisation factor of Eq. (akstate) is N_{a,k} = N |Stab(a)|.
+ *    The momentum is k.a_alpha = 2 pi K_alpha / L_alpha.
+ *  - A basis handle holds one or more sectors of one lattice and one N_down
+ *    (several K at once, or one U(1)-only sector).  A vector on a basis is
+ *    the concatenation of its sectors' vectors, sector s starting at the
+ *    offset given by qs3_basis_dims (prefix sums).
+ *  - Vectors are caller-owned DEVICE pointers (e.g. torch tensors) of the
+ *    stated qs3_dtype; complex types are interleaved (re, im).  The library
+ *    never frees them.  Host outputs go to caller arrays of the stated sizes.
+ *  - stream arguments are cudaStream_t passed as void* (NULL = default
+ *    stream); calls that return host data synchronise that stream.
+ *  - Every call returns QS3_OK (0) or a negative status; no exception crosses
+ *    the ABI and the library never exits the process.  qs3_last_error()
+ *    returns a thread-local text describing the last failure.
+ */
+#ifndef QS3_H
+#define QS3_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QS3_MAX_NDOWN 8        /* largest N_down handled by the kernels        */
+#define QS3_MAX_SITES 4096     /* largest N handled by the kernels             */
+
+enum {
+    QS3_OK = 0,
+    QS3_ERR_INVALID_ARG = -1,   /* bad pointer, size, bond or option            */
+    QS3_ERR_OVERFLOW = -2,      /* C(N, N_down) >= 2^63, N_down or N too large  */
+    QS3_ERR_SYMMETRY = -3,      /* bonds/field not translation invariant, K out of range */
+    QS3_ERR_OOM = -4,           /* device allocation failed                     */
+    QS3_ERR_CUDA = -5,          /* a CUDA call failed                           */
+    QS3_ERR_NOT_CONVERGED = -6, /* iteration limit reached before convergence   */
+    QS3_ERR_TIMEOUT = -7,       /* a bounded device wait gave up                */
+    QS3_ERR_STATE = -8          /* handle in the wrong state / dtype mismatch    */
+};
+
+typedef enum { QS3_F32 = 0, QS3_F64 = 1, QS3_C64 = 2, QS3_C128 = 3 } qs3_dtype;
+
+/* Lattice and couplings of Eq. (1): H = sum_b [Jxy_b (s^x s^x + s^y s^y) +
+ * Jz_b s^z s^z] - sum_i h_i s^z_i.  Bond b joins sites bi[b] != bj[b]; a
+ * repeated pair adds its couplings.  h may be NULL (no field).  L = {0,0,0}
+ * means no translation group (U(1) only); otherwise Lx*Ly*Lz must equal
+ * n_sites.  pos (3*n_sites doubles, in lattice units) gives the site
+ * positions used by e^{-i q.r}; NULL means the coordinates (x, y, z).
+ * All pointers are host pointers and are copied; the caller keeps them. */
+typedef struct {
+    int32_t n_sites, n_bonds;
+    const int32_t *bi, *bj;
+    const double *jxy, *jz;
+    const double *h;
+    int32_t L[3];
+    const double *pos;
+} qs3_lattice;
+
+typedef struct qs3_basis_s *qs3_basis_t;
+
+/* Build a basis for N_down down spins (Sec. "Representation of states with the
+ * U(1) symmetry"; Alg. 5-6 for k-sectors).  K = NULL: one U(1)-only sector of
+ * dimension C(N, N_down) (n_sectors must be 1).  Otherwise K holds 3 ints per
+ * sector (K_alpha in [0, L_alpha)); the representative lists are enumerated,
+ * filtered and sorted on the device.  Errors: INVALID_ARG, OVERFLOW,
+ * SYMMETRY (bonds or h not invariant under the translations, K out of range),
+ * OOM, CUDA.  The handle owns its device memory until qs3_basis_destroy. */
+int qs3_basis_create(const qs3_lattice *lat, int32_t n_down, int32_t n_sectors, const int32_t *K,
+                     qs3_basis_t *out);
+int qs3_basis_destroy(qs3_basis_t b);
+
+/* n_sectors and the total dimension (sum over sectors). */
+int qs3_basis_info(qs3_basis_t b, int32_t *n_sectors, uint64_t *total_dim);
+/* dims[s] for s < n_sectors (host array). */
+int qs3_basis_dims(qs3_basis_t b, uint64_t *dims);
+/* Sector s: rank0 of each representative (sorted), copied to a host array of
+ * dims[s] entries; stab (may be NULL) receives |Stab| per representative.
+ * INVALID_ARG for a U(1)-only sector (its ranks are 0..dim-1). */
+int qs3_basis_ranks(qs3_basis_t b, int32_t s, uint64_t *ranks, uint8_t *stab);
+/* Number of structural non-zeros of H on the basis: the diagonal plus every
+ * off-diagonal term of Alg. 9 that lands on a member of the sector.  Counted
+ * once on the device and cached. */
+int qs3_basis_nnz(qs3_basis_t b, uint64_t *nnz);
+
+/* psi = H phi (Alg. 9, pull form, one row per thread, no atomics).
+ * dtype: F32/F64 on a U(1)-only basis (real H); C64/C128 on any basis.
+ * phi and psi are device vectors of the basis' total dimension and must not
+ * alias.  F32/C64 use fp32 matrix elements and fp32 row accumulation. */
+int qs3_hphi(qs3_basis_t b, qs3_dtype dtype, const void *phi, void *psi, void *stream);
+
+/* Options of the eigensolvers (input_lancz / input_TRLan of the paper). */
+typedef struct {
+    int32_t n_eig;        /* NOE: eigenpairs wanted per sector (TRL), 1 for Lanczos */
+    int32_t n_keep;       /* N_K of Alg. 10 */
+    int32_t n_max;        /* N_M of Alg. 10; for qs3_lanczos the largest Krylov size */
+    int32_t max_iter;     /* I_M (restarts) for TRL; unused by qs3_lanczos */
+    int32_t min_iter;     /* minitr: Lanczos steps before the first check */
+    int32_t check_every;  /* itrint: steps between convergence checks */
+    double eps;           /* lnc_ene_conv: relative Ritz-value change for convergence */
+    int32_t precision;    /* QS3_F64: plain fp64; QS3_F32: fp32 H Phi + fp64 recurrences + fp64 refinement */
+    int32_t use_graphs;   /* capture the Lanczos steps of a cycle in a CUDA graph */
+    uint64_t seed;        /* start vector: seeded Gaussian (SplitMix64 + Box-Muller) */
+    double refine_tol;    /* fp32 mode: refine until |dE| <= refine_tol |E| (e.g. 1e-9) */
+} qs3_solve_opts;
+
+typedef struct {
+    int32_t iterations;   /* H Phi applications (Lanczos steps), all phases */
+    int32_t restarts;     /* thick restarts performed */
+    int32_t converged;    /* sectors that met the criterion */
+    int32_t refine_iterations; /* fp64 Lanczos steps spent in refinement */
+    double max_residual;  /* max over sectors/eigenpairs of ||H v - E v|| (fp64, unit v) */
+    double seconds;       /* wall time of the call */
+} qs3_solve_info;
+
+/* Conventional Lanczos with full reorthogonalisation (Alg. 10 lines 2-12)
+ * to the lowest eigenpair of every sector, batched over the sectors.
+ * evals: host, n_sectors doubles.  evecs: device fp64 vector (F64 for a
+ * U(1)-only basis, C128 otherwise) of the total dimension, or NULL.
+ * Returns NOT_CONVERGED when n_max steps did not meet eps (results are the
+ * last Ritz values). */
+int qs3_lanczos(qs3_basis_t b, const qs3_solve_opts *o, double *evals, void *evecs, qs3_solve_info *info,
+                void *stream);
+
+/* Thick-restart Lanczos (Alg. 10) for the n_eig lowest eigenpairs of every
+ * sector, batched.  evals: host, n_sectors * n_eig (sector-major).  evecs:
+ * device, n_eig fp64 vectors of the total dimension one after another, or
+ * NULL. */
+int qs3_trlanczos(qs3_basis_t b, const qs3_solve_opts *o, double *evals, void *evecs, qs3_solve_info *info,
+                  void *stream);
+
+/* Two-point functions of a state gs (device, fp64: F64 on a U(1)-only basis,
+ * C128 otherwise) living in sector s of b (Sec. "Calculating expectation
+ * values").  For k-sectors the translation-symmetrised operators are used, so
+ * results depend on bj - bi only.  For each of n_pairs pairs (i, j) (host
+ * 2*n_pairs ints): szsz[p] = <s^z_i s^z_j>, spsm[2p..2p+1] = <s^+_i s^-_j>
+ * (re, im).  sz_local (n_sites or NULL) = <s^z_i>.  For each of n_q wave
+ * vectors (host, 3 doubles each: q.a_alpha in radians): sq_zz[n] =
+ * (1/N) sum_{r,r'} e^{iq.(r-r')} <s^z_r s^z_r'> and sq_pm[n] = the same for
+ * <s^+_r s^-_r'>.  Any output may be NULL. */
+int qs3_correlations(qs3_basis_t b, int32_t s, const void *gs, int32_t n_pairs, const int32_t *pairs,
+                     double *szsz, double *spsm, double *sz_local, int32_t n_q, const double *q,
+                     double *sq_zz, double *sq_pm, void *stream);
+
+/* S^-_q applied to a state (Alg. 11, pull form): src sector s_src of basis
+ * src (N_down, K) -> sector s_dst of basis dst (N_down + 1, K + Q), with
+ * Q[3] the integer momentum of q (q.a_alpha = 2 pi Q_alpha / L_alpha).
+ * phi, psi: device C128 vectors of the respective sector dimensions.  For a
+ * U(1)-only pair of bases Q still fixes q (the lattice needs L) or, with L =
+ * {0,0,0}, q = 0. */
+int qs3_smq(qs3_basis_t src, int32_t s_src, const void *phi, qs3_basis_t dst, int32_t s_dst, const int32_t *Q,
+            void *psi, void *stream);
+
+/* Dynamical structure factor S^-(q, omega) by the continued fraction of
+ * Eq. (cfe) from n_iter Lanczos steps (fully reorthogonalised) started from
+ * S^-_q |gs>, for n_q momenta at once (batched).  gs: device C128 state of
+ * sector s_src of src with energy e0 (field-free).  dst must hold, in order,
+ * the n_q sectors (N_down + 1, K + Q_n).  Q: host, 3*n_q ints.  The field
+ * h_field enters as the Zeeman shift of the resolvent (poles at
+ * E_n - e0 + h_field).  Outputs (host, may be NULL): s_qw[n*n_omega + w],
+ * alpha[n*n_iter + x], beta[n*n_iter + x] (beta[n*n_iter] is |S^-_q gs|,
+ * beta[x] for x >= 1 the Lanczos couplings), norm2[n] = |S^-_q gs|^2. */
+int qs3_dsf(qs3_basis_t src, int32_t s_src, const void *gs, double e0, qs3_basis_t dst, int32_t n_q,
+            const int32_t *Q, int32_t n_iter, double eta, double h_field, int32_t n_omega, const double *omega,
+            double *s_qw, double *alpha, double *beta, double *norm2, void *stream);
+
+/* Text of a status code, and of the last failure on the calling thread. */
+const char *qs3_strerror(int status);
+const char *qs3_last_error(void);
+
+/* Library version string. */
+const char *qs3_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QS3_H */

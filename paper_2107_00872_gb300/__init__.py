@@ -1,0 +1,258 @@
+"""QS^3 hot path on GB300: Python binding of libqs3.so.
+
+Every operation runs in the library's CUDA kernels; this module only
+marshals arguments (torch tensors provide device memory and streams).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _abi
+from ._abi import QS3_C64, QS3_C128, QS3_F32, QS3_F64, QS3Error, check, load
+
+__all__ = ["Basis", "QS3Error", "load", "hphi", "dtype_code", "SolveOpts"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_code(t) -> int:
+    torch = _torch()
+    m = {torch.float32: QS3_F32, torch.float64: QS3_F64, torch.complex64: QS3_C64, torch.complex128: QS3_C128}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream):
+    if stream is None:
+        torch = _torch()
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, n: int | None = None, what: str = "vector"):
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{what} has {t.numel()} elements, expected {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class SolveOpts:
+    """Fields of qs3_solve_opts with the paper's defaults (input_lancz / input_TRLan)."""
+
+    def __init__(self, n_eig=1, n_keep=8, n_max=32, max_iter=10000, min_iter=20, check_every=5, eps=1e-14,
+                 precision="f64", use_graphs=True, seed=1, refine_tol=1e-9):
+        self.n_eig, self.n_keep, self.n_max, self.max_iter = n_eig, n_keep, n_max, max_iter
+        self.min_iter, self.check_every, self.eps = min_iter, check_every, eps
+        self.precision, self.use_graphs, self.seed, self.refine_tol = precision, use_graphs, seed, refine_tol
+
+    def c(self) -> _abi.qs3_solve_opts:
+        o = _abi.qs3_solve_opts()
+        o.n_eig, o.n_keep, o.n_max, o.max_iter = self.n_eig, self.n_keep, self.n_max, self.max_iter
+        o.min_iter, o.check_every, o.eps = self.min_iter, self.check_every, self.eps
+        o.precision = QS3_F32 if self.precision in ("f32", QS3_F32) else QS3_F64
+        o.use_graphs, o.seed, o.refine_tol = int(bool(self.use_graphs)), int(self.seed), float(self.refine_tol)
+        return o
+
+
+def _info_dict(info: _abi.qs3_solve_info) -> dict:
+    return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+class Basis:
+    """A set of symmetry sectors (one U(1)-only sector, or several momenta K)
+    of one lattice and one number of down spins, built on the device.
+
+    ``lattice`` is any object with n_sites, bi, bj, jxy, jz, h, L (and
+    optionally pos) attributes; sites are 0-based.
+    """
+
+    def __init__(self, lattice, n_down: int, K=None):
+        lib = load()
+        self._keep = []
+
+        def arr(a, dt):
+            if a is None:
+                return None
+            x = np.ascontiguousarray(np.asarray(a), dtype=dt)
+            self._keep.append(x)
+            return x
+
+        lat = _abi.qs3_lattice()
+        lat.n_sites = int(lattice.n_sites)
+        bi = arr(lattice.bi, np.int32)
+        lat.n_bonds = len(bi)
+        lat.bi, lat.bj = _ptr(bi), _ptr(arr(lattice.bj, np.int32))
+        lat.jxy, lat.jz = _ptr(arr(lattice.jxy, np.float64)), _ptr(arr(lattice.jz, np.float64))
+        lat.h = _ptr(arr(getattr(lattice, "h", None), np.float64))
+        L = tuple(getattr(lattice, "L", (0, 0, 0)) or (0, 0, 0))
+        lat.L[0], lat.L[1], lat.L[2] = int(L[0]), int(L[1]), int(L[2])
+        lat.pos = _ptr(arr(getattr(lattice, "pos", None), np.float64))
+        self.lattice = lattice
+        self.n_down = int(n_down)
+        if K is None:
+            self.K = None
+            nsec, kp = 1, None
+        else:
+            Ks = [tuple(int(v) for v in k) for k in (K if isinstance(K[0], (tuple, list)) else [K])]
+            self.K = Ks
+            nsec = len(Ks)
+            kp = arr(np.array(Ks, dtype=np.int32).reshape(-1), np.int32)
+        h = ctypes.c_void_p()
+        check(lib.qs3_basis_create(ctypes.byref(lat), self.n_down, nsec, _ptr(kp), ctypes.byref(h)),
+              "qs3_basis_create")
+        self._h = h
+        n = ctypes.c_int32()
+        tot = ctypes.c_uint64()
+        check(lib.qs3_basis_info(h, ctypes.byref(n), ctypes.byref(tot)), "qs3_basis_info")
+        self.n_sectors = n.value
+        self.total_dim = tot.value
+        dims = np.zeros(self.n_sectors, np.uint64)
+        check(lib.qs3_basis_dims(h, _ptr(dims)), "qs3_basis_dims")
+        self.dims = [int(v) for v in dims]
+        self.offsets = [0]
+        for d in self.dims:
+            self.offsets.append(self.offsets[-1] + d)
+        self._nnz = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def is_complex(self) -> bool:
+        return self.K is not None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().qs3_basis_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def ranks(self, s: int = 0):
+        """(rank0 array, |Stab| array) of the representatives of sector s."""
+        d = self.dims[s]
+        r = np.zeros(max(d, 1), np.uint64)
+        st = np.zeros(max(d, 1), np.uint8)
+        check(load().qs3_basis_ranks(self._h, s, _ptr(r), _ptr(st)), "qs3_basis_ranks")
+        return r[:d], st[:d]
+
+    def nnz(self) -> int:
+        if self._nnz is None:
+            v = ctypes.c_uint64()
+            check(load().qs3_basis_nnz(self._h, ctypes.byref(v)), "qs3_basis_nnz")
+            self._nnz = v.value
+        return self._nnz
+
+    # ---------------------------------------------------------- operations
+
+    def hphi(self, phi, psi=None, stream=None):
+        """psi = H phi on the device (psi allocated like phi when omitted)."""
+        if psi is None:
+            psi = _torch().empty_like(phi)
+        check(load().qs3_hphi(self._h, dtype_code(phi), _dev(phi, self.total_dim, "phi"),
+                              _dev(psi, self.total_dim, "psi"), _stream(stream)), "qs3_hphi")
+        return psi
+
+    def _solve(self, fn, opts: SolveOpts, want_vectors: bool, stream, n_eig: int):
+        torch = _torch()
+        o = opts.c()
+        evals = np.zeros(self.n_sectors * n_eig, np.float64)
+        vec = None
+        if want_vectors:
+            dt = torch.complex128 if self.is_complex else torch.float64
+            vec = torch.zeros(n_eig * self.total_dim, dtype=dt, device="cuda")
+        info = _abi.qs3_solve_info()
+        st = fn(self._h, ctypes.byref(o), _ptr(evals), None if vec is None else _dev(vec), ctypes.byref(info),
+                _stream(stream))
+        check(st, fn.__name__, allow=(-6,))
+        d = _info_dict(info)
+        d["status"] = _abi.STATUS.get(st, st)
+        return evals.reshape(self.n_sectors, n_eig), vec, d
+
+    def lanczos(self, opts: SolveOpts | None = None, vectors: bool = True, stream=None):
+        """Lowest eigenpair per sector: (evals[n_sectors, 1], fp64 vector, info)."""
+        return self._solve(load().qs3_lanczos, opts or SolveOpts(), vectors, stream, 1)
+
+    def trlanczos(self, opts: SolveOpts | None = None, vectors: bool = True, stream=None):
+        """n_eig lowest eigenpairs per sector by thick-restart Lanczos."""
+        opts = opts or SolveOpts()
+        return self._solve(load().qs3_trlanczos, opts, vectors, stream, opts.n_eig)
+
+    def correlations(self, gs, sector: int = 0, pairs=None, q=None, local=False, stream=None):
+        """Two-point functions and S(q) of the fp64 state gs of one sector."""
+        N = int(self.lattice.n_sites)
+        pr = None if pairs is None else np.ascontiguousarray(np.asarray(pairs, np.int32).reshape(-1, 2))
+        npairs = 0 if pr is None else len(pr)
+        qa = None if q is None else np.ascontiguousarray(np.asarray(q, np.float64).reshape(-1, 3))
+        nq = 0 if qa is None else len(qa)
+        szsz = np.zeros(max(npairs, 1))
+        spsm = np.zeros(2 * max(npairs, 1))
+        sz = np.zeros(N) if local else None
+        sqz = np.zeros(max(nq, 1))
+        sqp = np.zeros(max(nq, 1))
+        check(load().qs3_correlations(self._h, sector, _dev(gs, self.dims[sector], "gs"), npairs, _ptr(pr),
+                                      _ptr(szsz) if npairs else None, _ptr(spsm) if npairs else None, _ptr(sz),
+                                      nq, _ptr(qa), _ptr(sqz) if nq else None, _ptr(sqp) if nq else None,
+                                      _stream(stream)), "qs3_correlations")
+        out = {}
+        if npairs:
+            out["szsz"] = szsz[:npairs]
+            out["spsm"] = spsm[: 2 * npairs].view(np.complex128)
+        if local:
+            out["sz"] = sz
+        if nq:
+            out["sq_zz"] = sqz[:nq]
+            out["sq_pm"] = sqp[:nq]
+        return out
+
+
+def hphi(basis: Basis, phi, psi=None, stream=None):
+    return basis.hphi(phi, psi, stream)
+
+
+def smq(src: Basis, s_src: int, phi, dst: Basis, s_dst: int, Q, psi=None, stream=None):
+    """S^-_q phi (Alg. 11, pull form) from sector s_src of src into sector s_dst of dst."""
+    torch = _torch()
+    if psi is None:
+        psi = torch.zeros(dst.dims[s_dst], dtype=torch.complex128, device="cuda")
+    q = np.ascontiguousarray(np.asarray(Q, np.int32))
+    check(load().qs3_smq(src.handle, s_src, _dev(phi, src.dims[s_src], "phi"), dst.handle, s_dst, _ptr(q),
+                         _dev(psi, dst.dims[s_dst], "psi"), _stream(stream)), "qs3_smq")
+    return psi
+
+
+def dsf(src: Basis, s_src: int, gs, e0: float, dst: Basis, Qs, n_iter: int, eta: float, h_field: float,
+        omega: np.ndarray, stream=None):
+    """S^-(q, omega) by the continued fraction for each momentum of Qs
+    (dst holds the matching sectors, in order)."""
+    Q = np.ascontiguousarray(np.asarray(Qs, np.int32).reshape(-1, 3))
+    nq = len(Q)
+    om = np.ascontiguousarray(omega, np.float64)
+    s = np.zeros(nq * len(om))
+    al = np.zeros(nq * n_iter)
+    be = np.zeros(nq * n_iter)
+    n2 = np.zeros(nq)
+    check(load().qs3_dsf(src.handle, s_src, _dev(gs, src.dims[s_src], "gs"), float(e0), dst.handle, nq, _ptr(Q),
+                         int(n_iter), float(eta), float(h_field), len(om), _ptr(om), _ptr(s), _ptr(al), _ptr(be),
+                         _ptr(n2), _stream(stream)), "qs3_dsf")
+    return s.reshape(nq, len(om)), al.reshape(nq, n_iter), be.reshape(nq, n_iter), n2

@@ -1,0 +1,571 @@
+// qs3_basis.cu -- lattice ingest and symmetry-adapted basis construction on
+// the device (Sec. "Representative states and Hamiltonian matrix elements in
+// symmetry-adapted basis sets", Alg. 5-6 of the paper, re-designed).
+//
+// Instead of testing all C(N, N_down) states with all N translations
+// (Alg. 5/6), the device enumerates the C(N-1, N_down-1) states that have a
+// down spin at site 0.  Every translation orbit contains such states: the
+// translates T^{-pos(c_m)} c that move one of its spins to the origin.  A
+// state c emits its orbit's representative exactly once, when c has the
+// smallest rank among those origin-containing translates.  The stabiliser
+// of c is the set of pos(c_m) whose translate reproduces c, which gives
+// |Stab| and the compatibility test e^{ik.t} = 1 on it (N_{a,k} > 0 in
+// Alg. 5).  The representatives are sorted by rank (CUB radix sort, a
+// library primitive) and indexed by a prefix table over their two largest
+// sites.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <utility>
+
+#include "qs3_internal.cuh"
+
+namespace qs3 {
+
+// ------------------------------------------------------------ error state
+static thread_local char g_err[1024];
+
+int set_err(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+void clear_err() { g_err[0] = 0; }
+
+const char *last_err() { return g_err; }
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+}
+
+int DevBuf::alloc(size_t bytes) {
+    release();
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return set_err(e == cudaErrorMemoryAllocation ? QS3_ERR_OOM : QS3_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
+                       cudaGetErrorString(e));
+    }
+    n = bytes;
+    return QS3_OK;
+}
+
+int DevBuf::upload(const void *src, size_t bytes) {
+    QS3_TRY(alloc(bytes));
+    if (bytes) QS3_CUDA(cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice));
+    return QS3_OK;
+}
+
+// must match carve() in qs3_hphi.cu: binomial rows 0..nd+2, coordinates,
+// sqrt table (18 doubles), per-axis phase tables (complex fp64)
+size_t row_kernel_smem(const Basis &B, int /*extra_nd*/) {
+    size_t s = (size_t)(B.nd + 3) * (B.N + 1) * sizeof(uint64_t);
+    s += (size_t)B.N * sizeof(uint32_t);
+    s = (s + 15) & ~(size_t)15;
+    s += 18 * sizeof(double);
+    s = (s + 15) & ~(size_t)15;
+    s += (size_t)(B.L[0] + B.L[1] + B.L[2]) * 2 * sizeof(double);
+    return s;
+}
+
+// ------------------------------------------------------ enumeration kernel
+
+template <int ND>
+__global__ void __launch_bounds__(NTHREADS) k_enum_reps(LatView L, int Kx, int Ky, int Kz, uint64_t ncand,
+                                                        int emit, unsigned long long *counter,
+                                                        uint64_t *out_rank, uint8_t *out_stab) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *sC = (uint64_t *)smem;
+    uint32_t *sxyz = (uint32_t *)(sC + (L.nd + 3) * L.np1);
+    const int nC = (L.nd + 3) * L.np1;
+    for (int i = threadIdx.x; i < nC; i += blockDim.x) sC[i] = L.binom[i];
+    for (int i = threadIdx.x; i < L.N; i += blockDim.x) sxyz[i] = L.xyz[i];
+    __syncthreads();
+    const int Lx = L.L[0], Ly = L.L[1], Lz = L.L[2];
+    const int N = L.N;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < ncand; base += stride) {
+        const uint64_t j = base + threadIdx.x;
+        bool take = false;
+        uint64_t rep_rank = 0;
+        int st = 0;
+        if (j < ncand) {
+            int c[ND];
+            c[0] = 0;
+            if (ND >= 2) {
+                constexpr int NM1 = (ND > 1) ? ND - 1 : 1;
+                int cc[NM1];
+                unrank<NM1>(j, sC, L.np1, cc);
+#pragma unroll
+                for (int m = 0; m + 1 < ND; ++m) c[m + 1] = cc[m] + 1;
+            }
+            const uint64_t rc = rank_of(c, sC, L.np1);
+            int X[ND], Y[ND], Z[ND];
+#pragma unroll
+            for (int m = 0; m < ND; ++m) {
+                uint32_t p = sxyz[c[m]];
+                X[m] = p & 2047u;
+                Y[m] = (p >> 11) & 2047u;
+                Z[m] = p >> 22;
+            }
+            bool designated = true, compat = true;
+#pragma unroll
+            for (int m = 0; m < ND; ++m) {
+                int s[ND];
+#pragma unroll
+                for (int q = 0; q < ND; ++q) {
+                    int xx = X[q] - X[m]; xx += (xx < 0) ? Lx : 0;
+                    int yy = Y[q] - Y[m]; yy += (yy < 0) ? Ly : 0;
+                    int zz = Z[q] - Z[m]; zz += (zz < 0) ? Lz : 0;
+                    s[q] = xx + Lx * (yy + Ly * zz);
+                }
+                sort_net(s);
+                const uint64_t rm = rank_of(s, sC, L.np1);
+                designated &= (rm >= rc);
+                if (rm == rc) {
+                    ++st;
+                    // stabiliser element t = pos(c_m): compatible iff k.t is a multiple of 2 pi
+                    long long num = (long long)Kx * X[m] * (N / Lx) + (long long)Ky * Y[m] * (N / Ly) +
+                                    (long long)Kz * Z[m] * (N / Lz);
+                    compat &= (num % N) == 0;
+                }
+            }
+            take = designated && compat;
+            if (take && emit) {
+                int rep[ND];
+                int ax, by, cz;
+                rep_rank = canon(c, L, sxyz, sC, rep, ax, by, cz);
+            }
+        }
+        // warp-aggregated slot allocation
+        const unsigned mask = __ballot_sync(0xffffffffu, take);
+        const int lane = threadIdx.x & 31;
+        unsigned long long basepos = 0;
+        if (lane == 0 && mask) basepos = atomicAdd(counter, (unsigned long long)__popc(mask));
+        basepos = __shfl_sync(0xffffffffu, basepos, 0);
+        if (take && emit) {
+            const unsigned long long pos = basepos + __popc(mask & ((1u << lane) - 1u));
+            out_rank[pos] = rep_rank;
+            out_stab[pos] = (uint8_t)st;
+        }
+    }
+}
+
+template <int ND>
+__global__ void k_prefix(LatView L, const uint64_t *__restrict__ sigma, uint64_t d, uint32_t *__restrict__ P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *sC = (uint64_t *)smem;
+    const int nC = (L.nd + 3) * L.np1;
+    for (int i = threadIdx.x; i < nC; i += blockDim.x) sC[i] = L.binom[i];
+    __syncthreads();
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d; i += (uint64_t)gridDim.x * blockDim.x) {
+        int c[ND];
+        unrank(sigma[i], sC, L.np1, c);
+        P[i] = prefix_of(c, sC, L.np1);
+    }
+}
+
+// pidx[p] = first i with P[i] >= p, for p in [0, np]
+__global__ void k_pidx(const uint32_t *__restrict__ P, uint64_t d, uint32_t np, uint32_t *__restrict__ pidx) {
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= np; p += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t lo = 0, hi = d;
+        while (lo < hi) {
+            uint64_t mid = (lo + hi) >> 1;
+            if (P[mid] < p) lo = mid + 1; else hi = mid;
+        }
+        pidx[p] = (uint32_t)lo;
+    }
+}
+
+template <int ND>
+static int build_reps_nd(Basis &B, int s) {
+    const int *K = &B.K[3 * s];
+    // C(N-1, ND-1) candidates
+    std::vector<uint64_t> hb((size_t)(B.nd + 3) * (B.N + 1));
+    QS3_CUDA(cudaMemcpy(hb.data(), B.d_binom.p, hb.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    const uint64_t nc = hb[(size_t)(ND - 1) * (B.N + 1) + (B.N - 1)];
+    const size_t smem = (size_t)(B.nd + 3) * (B.N + 1) * 8 + (size_t)B.N * 4;
+    QS3_CUDA(cudaFuncSetAttribute(k_enum_reps<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DevBuf cnt;
+    QS3_TRY(cnt.alloc(sizeof(unsigned long long)));
+    QS3_CUDA(cudaMemset(cnt.p, 0, sizeof(unsigned long long)));
+    int dev = 0, nsm = 0;
+    QS3_CUDA(cudaGetDevice(&dev));
+    QS3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    uint64_t want = (nc + NTHREADS - 1) / NTHREADS;
+    int grid = (int)std::min<uint64_t>(want ? want : 1, (uint64_t)nsm * 8);
+    k_enum_reps<ND><<<grid, NTHREADS, smem>>>(B.lv, K[0], K[1], K[2], nc, 0, cnt.as<unsigned long long>(),
+                                              nullptr, nullptr);
+    QS3_CUDA(cudaGetLastError());
+    unsigned long long d = 0;
+    QS3_CUDA(cudaMemcpy(&d, cnt.p, sizeof(d), cudaMemcpyDeviceToHost));
+    if (d >= (1ull << 32)) return set_err(QS3_ERR_OVERFLOW, "sector dimension %llu exceeds 2^32", d);
+    DevBuf kin, vin, kout, vout;
+    QS3_TRY(kin.alloc(d * 8));
+    QS3_TRY(vin.alloc(d));
+    QS3_CUDA(cudaMemset(cnt.p, 0, sizeof(unsigned long long)));
+    k_enum_reps<ND><<<grid, NTHREADS, smem>>>(B.lv, K[0], K[1], K[2], nc, 1, cnt.as<unsigned long long>(),
+                                              kin.as<uint64_t>(), vin.as<uint8_t>());
+    QS3_CUDA(cudaGetLastError());
+    QS3_TRY(kout.alloc(d * 8));
+    QS3_TRY(vout.alloc(d));
+    if (d > 0) {
+        size_t tb = 0;
+        QS3_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, kin.as<unsigned long long>(),
+                                                 kout.as<unsigned long long>(), vin.as<uint8_t>(),
+                                                 vout.as<uint8_t>(), (int64_t)d));
+        DevBuf tmp;
+        QS3_TRY(tmp.alloc(tb));
+        QS3_CUDA(cub::DeviceRadixSort::SortPairs(tmp.p, tb, kin.as<unsigned long long>(),
+                                                 kout.as<unsigned long long>(), vin.as<uint8_t>(),
+                                                 vout.as<uint8_t>(), (int64_t)d));
+    }
+    // prefix index
+    const uint32_t np = (ND >= 2) ? (uint32_t)hb[2 * (size_t)(B.N + 1) + B.N] : (uint32_t)B.N;   // number of prefixes
+    DevBuf P, pidx;
+    QS3_TRY(P.alloc(d * 4));
+    QS3_TRY(pidx.alloc(((size_t)np + 1) * 4));
+    if (d > 0) {
+        const size_t sm2 = (size_t)(B.nd + 3) * (B.N + 1) * 8;
+        QS3_CUDA(cudaFuncSetAttribute(k_prefix<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+        int g2 = (int)std::min<uint64_t>((d + 255) / 256, (uint64_t)nsm * 8);
+        k_prefix<ND><<<g2, 256, sm2>>>(B.lv, kout.as<uint64_t>(), d, P.as<uint32_t>());
+        QS3_CUDA(cudaGetLastError());
+    }
+    int g3 = (int)std::min<uint64_t>((np + 256) / 256, (uint64_t)nsm * 8);
+    k_pidx<<<g3, 256>>>(P.as<uint32_t>(), d, np, pidx.as<uint32_t>());
+    QS3_CUDA(cudaGetLastError());
+    QS3_CUDA(cudaDeviceSynchronize());
+    B.dims[s] = d;
+    B.d_sigma[s] = std::move(kout);
+    B.d_stab[s] = std::move(vout);
+    B.d_pidx[s] = std::move(pidx);
+    return QS3_OK;
+}
+
+int build_sector_reps(Basis &B, int s) {
+    switch (B.nd) {
+        case 1: return build_reps_nd<1>(B, s);
+        case 2: return build_reps_nd<2>(B, s);
+        case 3: return build_reps_nd<3>(B, s);
+        case 4: return build_reps_nd<4>(B, s);
+        case 5: return build_reps_nd<5>(B, s);
+        case 6: return build_reps_nd<6>(B, s);
+        case 7: return build_reps_nd<7>(B, s);
+        case 8: return build_reps_nd<8>(B, s);
+        default: return set_err(QS3_ERR_INVALID_ARG, "n_down %d", B.nd);
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+static bool binom_table(int N, int rows, std::vector<uint64_t> &t, uint64_t *cnd, int nd) {
+    // t[m * (N+1) + c] = C(c, m), saturated at UINT64_MAX; returns false if C(N, nd) >= 2^63
+    t.assign((size_t)rows * (N + 1), 0);
+    for (int c = 0; c <= N; ++c) t[c] = 1;
+    const uint64_t SAT = ~0ull;
+    for (int m = 1; m < rows; ++m)
+        for (int c = 1; c <= N; ++c) {
+            uint64_t a = t[(size_t)(m - 1) * (N + 1) + c - 1], b = t[(size_t)m * (N + 1) + c - 1];
+            uint64_t s = (a == SAT || b == SAT || a + b < a) ? SAT : a + b;
+            t[(size_t)m * (N + 1) + c] = s;
+        }
+    *cnd = t[(size_t)nd * (N + 1) + N];
+    return *cnd < (1ull << 63);
+}
+
+static int check_translation(const Basis &B) {
+    // bonds as an unordered-pair multiset with summed couplings
+    std::map<std::pair<int, int>, std::pair<double, double>> bonds;
+    for (int b = 0; b < B.nb; ++b) {
+        int i = std::min(B.bi[b], B.bj[b]), j = std::max(B.bi[b], B.bj[b]);
+        auto &v = bonds[{i, j}];
+        v.first += B.jxy[b];
+        v.second += B.jz[b];
+    }
+    const int Lx = B.L[0], Ly = B.L[1];
+    auto shift = [&](int r, int a) {
+        int x = r % Lx, y = (r / Lx) % Ly, z = r / (Lx * Ly);
+        if (a == 0) x = (x + 1) % Lx;
+        if (a == 1) y = (y + 1) % Ly;
+        if (a == 2) z = (z + 1) % B.L[2];
+        return x + Lx * (y + Ly * z);
+    };
+    for (int a = 0; a < 3; ++a) {
+        if (B.L[a] == 1) continue;
+        for (auto &kv : bonds) {
+            int i = shift(kv.first.first, a), j = shift(kv.first.second, a);
+            auto it = bonds.find({std::min(i, j), std::max(i, j)});
+            if (it == bonds.end() || std::fabs(it->second.first - kv.second.first) > 1e-12 ||
+                std::fabs(it->second.second - kv.second.second) > 1e-12)
+                return set_err(QS3_ERR_SYMMETRY, "bond (%d,%d) is not invariant under the translation along axis %d",
+                               kv.first.first, kv.first.second, a);
+        }
+    }
+    if (B.has_h)
+        for (int i = 1; i < B.N; ++i)
+            if (B.h[i] != B.h[0]) return set_err(QS3_ERR_SYMMETRY, "site field is not uniform (site %d)", i);
+    return QS3_OK;
+}
+
+static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t *K, Basis &B) {
+    if (!lat) return set_err(QS3_ERR_INVALID_ARG, "lattice is NULL");
+    const int N = lat->n_sites, nb = lat->n_bonds;
+    if (N < 1 || N > QS3_MAX_SITES) return set_err(QS3_ERR_OVERFLOW, "n_sites %d outside [1, %d]", N, QS3_MAX_SITES);
+    if (nd < 0 || nd > QS3_MAX_NDOWN || nd > N)
+        return set_err(nd > QS3_MAX_NDOWN ? QS3_ERR_OVERFLOW : QS3_ERR_INVALID_ARG, "n_down %d", nd);
+    if (nb < 0 || (nb > 0 && (!lat->bi || !lat->bj || !lat->jxy || !lat->jz)))
+        return set_err(QS3_ERR_INVALID_ARG, "bond arrays");
+    if (nsec < 1) return set_err(QS3_ERR_INVALID_ARG, "n_sectors %d", nsec);
+    if (!K && nsec != 1) return set_err(QS3_ERR_INVALID_ARG, "a U(1)-only basis has exactly one sector");
+    B.N = N;
+    B.nd = nd;
+    B.nb = nb;
+    B.bi.assign(lat->bi, lat->bi + nb);
+    B.bj.assign(lat->bj, lat->bj + nb);
+    B.jxy.assign(lat->jxy, lat->jxy + nb);
+    B.jz.assign(lat->jz, lat->jz + nb);
+    for (int b = 0; b < nb; ++b) {
+        if (B.bi[b] < 0 || B.bi[b] >= N || B.bj[b] < 0 || B.bj[b] >= N || B.bi[b] == B.bj[b])
+            return set_err(QS3_ERR_INVALID_ARG, "bond %d joins (%d, %d)", b, B.bi[b], B.bj[b]);
+        if (!std::isfinite(B.jxy[b]) || !std::isfinite(B.jz[b]))
+            return set_err(QS3_ERR_INVALID_ARG, "bond %d has a non-finite coupling", b);
+    }
+    B.has_h = lat->h != nullptr;
+    if (B.has_h) B.h.assign(lat->h, lat->h + N);
+    for (int a = 0; a < 3; ++a) B.L[a] = lat->L[a];
+    const bool haveL = B.L[0] > 0 || B.L[1] > 0 || B.L[2] > 0;
+    if (haveL) {
+        for (int a = 0; a < 3; ++a)
+            if (B.L[a] < 1 || B.L[a] > (a == 2 ? 1023 : 2047))
+                return set_err(QS3_ERR_INVALID_ARG, "L[%d] = %d outside the coordinate range", a, B.L[a]);
+        if ((long long)B.L[0] * B.L[1] * B.L[2] != N)
+            return set_err(QS3_ERR_INVALID_ARG, "Lx*Ly*Lz = %lld != n_sites %d", (long long)B.L[0] * B.L[1] * B.L[2], N);
+    } else {
+        if (N > 2047 && K) return set_err(QS3_ERR_INVALID_ARG, "translation group needed");
+    }
+    B.has_k = K != nullptr;
+    B.S = nsec;
+    if (B.has_k) {
+        if (!haveL) return set_err(QS3_ERR_SYMMETRY, "momentum sectors need a translation group L");
+        B.K.assign(K, K + 3 * nsec);
+        for (int s = 0; s < nsec; ++s)
+            for (int a = 0; a < 3; ++a)
+                if (B.K[3 * s + a] < 0 || B.K[3 * s + a] >= B.L[a])
+                    return set_err(QS3_ERR_SYMMETRY, "K[%d][%d] = %d outside [0, %d)", s, a, B.K[3 * s + a], B.L[a]);
+        QS3_TRY(check_translation(B));
+    } else {
+        B.K.assign(3, 0);
+    }
+    if (!haveL) { B.L[0] = N; B.L[1] = 1; B.L[2] = 1; }
+    if (lat->pos) B.pos.assign(lat->pos, lat->pos + 3 * (size_t)N);
+
+    // binomial rows 0..nd+2
+    std::vector<uint64_t> tb;
+    uint64_t cnd = 0;
+    if (!binom_table(N, nd + 3, tb, &cnd, nd))
+        return set_err(QS3_ERR_OVERFLOW, "C(%d, %d) does not fit in 63 bits", N, nd);
+    QS3_TRY(B.d_binom.upload(tb.data(), tb.size() * 8));
+
+    // adjacency (CSR, both directions), diagonal constants
+    std::vector<int> deg(N + 1, 0);
+    for (int b = 0; b < nb; ++b) { deg[B.bi[b] + 1]++; deg[B.bj[b] + 1]++; }
+    for (int i = 0; i < N; ++i) deg[i + 1] += deg[i];
+    std::vector<int> nbr(2 * (size_t)nb), fill(deg.begin(), deg.end() - 1);
+    std::vector<double> ajxy(2 * (size_t)nb), ajz(2 * (size_t)nb), u(N, 0.0);
+    std::vector<float> ajxyf(2 * (size_t)nb);
+    double c0 = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        int i = B.bi[b], j = B.bj[b];
+        int p = fill[i]++, q = fill[j]++;
+        nbr[p] = j; nbr[q] = i;
+        ajxy[p] = ajxy[q] = B.jxy[b];
+        ajz[p] = ajz[q] = B.jz[b];
+        ajxyf[p] = ajxyf[q] = (float)B.jxy[b];
+        u[i] -= 0.5 * B.jz[b];
+        u[j] -= 0.5 * B.jz[b];
+        c0 += 0.25 * B.jz[b];
+    }
+    if (B.has_h)
+        for (int i = 0; i < N; ++i) { u[i] += B.h[i]; c0 -= 0.5 * B.h[i]; }
+    QS3_TRY(B.d_adj_ptr.upload(deg.data(), deg.size() * 4));
+    QS3_TRY(B.d_adj_nbr.upload(nbr.data(), nbr.size() * 4));
+    QS3_TRY(B.d_adj_jxy.upload(ajxy.data(), ajxy.size() * 8));
+    QS3_TRY(B.d_adj_jz.upload(ajz.data(), ajz.size() * 8));
+    QS3_TRY(B.d_adj_jxy_f.upload(ajxyf.data(), ajxyf.size() * 4));
+    QS3_TRY(B.d_u.upload(u.data(), u.size() * 8));
+    std::vector<uint32_t> xyz(N);
+    for (int r = 0; r < N; ++r) {
+        int x = r % B.L[0], y = (r / B.L[0]) % B.L[1], z = r / (B.L[0] * B.L[1]);
+        // coordinates are only used with a translation group (x, y < 2048, z < 1024)
+        xyz[r] = haveL ? ((uint32_t)x | ((uint32_t)y << 11) | ((uint32_t)z << 22)) : 0u;
+    }
+    QS3_TRY(B.d_xyz.upload(xyz.data(), xyz.size() * 4));
+
+    int bits = 1;
+    while ((1 << bits) < N) ++bits;
+    LatView &L = B.lv;
+    L.N = N;
+    L.nd = nd;
+    L.np1 = N + 1;
+    for (int a = 0; a < 3; ++a) L.L[a] = B.L[a];
+    L.has_k = B.has_k;
+    L.key_bits = (bits * nd <= 64) ? bits : 0;
+    L.binom = B.d_binom.as<uint64_t>();
+    L.adj_ptr = B.d_adj_ptr.as<int>();
+    L.adj_nbr = B.d_adj_nbr.as<int>();
+    L.adj_jxy = B.d_adj_jxy.as<double>();
+    L.adj_jz = B.d_adj_jz.as<double>();
+    L.adj_jxy_f = B.d_adj_jxy_f.as<float>();
+    L.u = B.d_u.as<double>();
+    L.c0 = c0;
+    L.xyz = B.d_xyz.as<uint32_t>();
+
+    // sectors
+    B.dims.assign(nsec, 0);
+    B.d_sigma.resize(nsec);
+    B.d_stab.resize(nsec);
+    B.d_pidx.resize(nsec);
+    if (!B.has_k) {
+        B.dims[0] = cnd;
+    } else if (nd == 0) {
+        for (int s = 0; s < nsec; ++s) {
+            const bool k0 = B.K[3 * s] == 0 && B.K[3 * s + 1] == 0 && B.K[3 * s + 2] == 0;
+            B.dims[s] = k0 ? 1 : 0;
+            uint64_t zero = 0;
+            uint8_t one = 1;
+            uint32_t pi[2] = {0, k0 ? 1u : 0u};
+            QS3_TRY(B.d_sigma[s].upload(&zero, 8));
+            QS3_TRY(B.d_stab[s].upload(&one, 1));
+            QS3_TRY(B.d_pidx[s].upload(pi, 8));
+        }
+    } else {
+        for (int s = 0; s < nsec; ++s) QS3_TRY(build_sector_reps(B, s));
+    }
+    B.offs.assign(nsec + 1, 0);
+    B.tile0.assign(nsec + 1, 0);
+    for (int s = 0; s < nsec; ++s) {
+        B.offs[s + 1] = B.offs[s] + B.dims[s];
+        uint64_t nt = (B.dims[s] + TILE - 1) / TILE;
+        if ((uint64_t)B.tile0[s] + nt > (1ull << 31) - 1) return set_err(QS3_ERR_OVERFLOW, "too many rows");
+        B.tile0[s + 1] = B.tile0[s] + (int)nt;
+    }
+    B.total = B.offs[nsec];
+    B.ntiles = B.tile0[nsec];
+    B.secs.resize(nsec);
+    for (int s = 0; s < nsec; ++s) {
+        SecView &v = B.secs[s];
+        v.sigma = B.has_k ? B.d_sigma[s].as<uint64_t>() : nullptr;
+        v.stab = B.has_k ? B.d_stab[s].as<uint8_t>() : nullptr;
+        v.pidx = B.has_k ? B.d_pidx[s].as<uint32_t>() : nullptr;
+        v.dim = B.dims[s];
+        v.off = B.offs[s];
+        for (int a = 0; a < 3; ++a) v.K[a] = B.K[3 * s + a];
+        v.tile0 = B.tile0[s];
+    }
+    QS3_TRY(B.d_secs.upload(B.secs.data(), B.secs.size() * sizeof(SecView)));
+    QS3_TRY(B.d_tile0.upload(B.tile0.data(), B.tile0.size() * 4));
+    B.smem_bytes = row_kernel_smem(B, 0);
+    if (B.smem_bytes > 200 * 1024)
+        return set_err(QS3_ERR_OVERFLOW, "lattice tables need %zu bytes of shared memory", B.smem_bytes);
+    return QS3_OK;
+}
+
+}  // namespace qs3
+
+using namespace qs3;
+
+extern "C" {
+
+int qs3_basis_create(const qs3_lattice *lat, int32_t n_down, int32_t n_sectors, const int32_t *K, qs3_basis_t *out) {
+    clear_err();
+    if (!out) return set_err(QS3_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    qs3_basis_s *h = new (std::nothrow) qs3_basis_s();
+    if (!h) return set_err(QS3_ERR_OOM, "host allocation");
+    int st = basis_create(lat, n_down, n_sectors, K, h->B);
+    if (st != QS3_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return QS3_OK;
+}
+
+int qs3_basis_destroy(qs3_basis_t b) {
+    clear_err();
+    delete b;
+    return QS3_OK;
+}
+
+int qs3_basis_info(qs3_basis_t b, int32_t *n_sectors, uint64_t *total_dim) {
+    clear_err();
+    if (!b) return set_err(QS3_ERR_INVALID_ARG, "basis is NULL");
+    if (n_sectors) *n_sectors = b->B.S;
+    if (total_dim) *total_dim = b->B.total;
+    return QS3_OK;
+}
+
+int qs3_basis_dims(qs3_basis_t b, uint64_t *dims) {
+    clear_err();
+    if (!b || !dims) return set_err(QS3_ERR_INVALID_ARG, "NULL argument");
+    for (int s = 0; s < b->B.S; ++s) dims[s] = b->B.dims[s];
+    return QS3_OK;
+}
+
+int qs3_basis_ranks(qs3_basis_t b, int32_t s, uint64_t *ranks, uint8_t *stab) {
+    clear_err();
+    if (!b || !ranks) return set_err(QS3_ERR_INVALID_ARG, "NULL argument");
+    Basis &B = b->B;
+    if (s < 0 || s >= B.S) return set_err(QS3_ERR_INVALID_ARG, "sector %d", s);
+    if (!B.has_k) return set_err(QS3_ERR_INVALID_ARG, "a U(1)-only sector has ranks 0..dim-1");
+    if (B.dims[s]) {
+        QS3_CUDA(cudaMemcpy(ranks, B.d_sigma[s].p, B.dims[s] * 8, cudaMemcpyDeviceToHost));
+        if (stab) QS3_CUDA(cudaMemcpy(stab, B.d_stab[s].p, B.dims[s], cudaMemcpyDeviceToHost));
+    }
+    return QS3_OK;
+}
+
+int qs3_basis_nnz(qs3_basis_t b, uint64_t *nnz) {
+    clear_err();
+    if (!b || !nnz) return set_err(QS3_ERR_INVALID_ARG, "NULL argument");
+    if (!b->B.nnz_valid) {
+        QS3_TRY(count_nnz(b->B, &b->B.nnz));
+        b->B.nnz_valid = true;
+    }
+    *nnz = b->B.nnz;
+    return QS3_OK;
+}
+
+const char *qs3_last_error(void) { return qs3::last_err(); }
+
+const char *qs3_strerror(int status) {
+    switch (status) {
+        case QS3_OK: return "ok";
+        case QS3_ERR_INVALID_ARG: return "invalid argument";
+        case QS3_ERR_OVERFLOW: return "size overflow";
+        case QS3_ERR_SYMMETRY: return "symmetry violated";
+        case QS3_ERR_OOM: return "out of device memory";
+        case QS3_ERR_CUDA: return "CUDA error";
+        case QS3_ERR_NOT_CONVERGED: return "not converged";
+        case QS3_ERR_TIMEOUT: return "device wait timed out";
+        case QS3_ERR_STATE: return "invalid state";
+        default: return "unknown status";
+    }
+}
+
+const char *qs3_version(void) { return "qs3-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

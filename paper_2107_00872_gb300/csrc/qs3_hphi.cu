@@ -1,0 +1,373 @@
+// qs3_hphi.cu -- the matrix-free product psi = H phi (Alg. 9 of the paper,
+// with the readings: norm ratio sqrt(N_a'/N_a) of Eq. (hak2), pull-form phase
+// e^{+ik.l} with T^l a' = a'_rep, hop amplitude Jxy/2 of Eq. (1)).
+//
+// GPU design: one thread per row (consecutive threads own consecutive ranks,
+// so in the colex order the gathers phi[a'] of one hop class land close
+// together), a persistent grid striding over 256-row tiles of all sectors of
+// a basis, the binomial table and the site-coordinate table staged in shared
+// memory, and no atomics.  Per row:
+//   - unrank (Alg. 1) the row's rank, or the representative's rank sigma[row];
+//   - diagonal: sum_b Jz_b/4 - (1/2) sum_{i in a} s_i + (down-down Jz) + field,
+//     with s_i = sum_j Jz_ij folded into the per-site constant u_i;
+//   - for each down spin i and each bond (i, j) with j empty: the hop target
+//     is the sorted list with i replaced by j (Alg. 3); its rank (U(1)), or
+//     its representative and stabiliser via the pruned translation search and
+//     the two-level index over sigma (k-sectors, Alg. 7-9);
+//   - accumulate in the vector's precision (fp32 or fp64), write psi once.
+#include <algorithm>
+
+#include "qs3_internal.cuh"
+
+namespace qs3 {
+
+template <typename VT> struct VTr;
+template <> struct VTr<float> { using R = float; using C = float2; static constexpr bool cplx = false; };
+template <> struct VTr<double> { using R = double; using C = double2; static constexpr bool cplx = false; };
+template <> struct VTr<float2> { using R = float; using C = float2; static constexpr bool cplx = true; };
+template <> struct VTr<double2> { using R = double; using C = double2; static constexpr bool cplx = true; };
+
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+
+// acc += coef * x for the four vector types
+__device__ __forceinline__ void acc_add(float2 &acc, float2 coef, float2 x) {
+    acc.x += coef.x * x.x - coef.y * x.y;
+    acc.y += coef.x * x.y + coef.y * x.x;
+}
+__device__ __forceinline__ void acc_add(double2 &acc, double2 coef, double2 x) {
+    acc.x += coef.x * x.x - coef.y * x.y;
+    acc.y += coef.x * x.y + coef.y * x.x;
+}
+__device__ __forceinline__ void acc_add(float2 &acc, float2 coef, float x) { acc.x += coef.x * x; acc.y += coef.y * x; }
+__device__ __forceinline__ void acc_add(double2 &acc, double2 coef, double x) { acc.x += coef.x * x; acc.y += coef.y * x; }
+__device__ __forceinline__ void store(float *p, float2 v) { *p = v.x; }
+__device__ __forceinline__ void store(double *p, double2 v) { *p = v.x; }
+__device__ __forceinline__ void store(float2 *p, float2 v) { *p = v; }
+__device__ __forceinline__ void store(double2 *p, double2 v) { *p = v; }
+
+template <typename VT> __device__ __forceinline__ const typename VTr<VT>::R *jxy_table(const LatView &L);
+template <> __device__ __forceinline__ const float *jxy_table<float>(const LatView &L) { return L.adj_jxy_f; }
+template <> __device__ __forceinline__ const float *jxy_table<float2>(const LatView &L) { return L.adj_jxy_f; }
+template <> __device__ __forceinline__ const double *jxy_table<double>(const LatView &L) { return L.adj_jxy; }
+template <> __device__ __forceinline__ const double *jxy_table<double2>(const LatView &L) { return L.adj_jxy; }
+
+struct SmemLayout {
+    uint64_t *sC;
+    uint32_t *sxyz;
+    void *sph;      // phase tables, Lx + Ly + Lz complex entries of the vector precision
+    void *snorm;    // sqrt table: [0..8] sqrt(s), [9..17] 1/sqrt(s)
+};
+
+__device__ __forceinline__ SmemLayout carve(const LatView &L, unsigned char *smem) {
+    SmemLayout s;
+    s.sC = (uint64_t *)smem;
+    s.sxyz = (uint32_t *)(s.sC + (L.nd + 3) * L.np1);
+    size_t off = (size_t)(L.nd + 3) * L.np1 * 8 + (size_t)L.N * 4;
+    off = (off + 15) & ~(size_t)15;
+    s.snorm = smem + off;
+    off += 18 * sizeof(double);
+    off = (off + 15) & ~(size_t)15;
+    s.sph = smem + off;
+    return s;
+}
+
+template <typename CT, typename R>
+__device__ __forceinline__ void fill_phases(const LatView &L, const int *K, CT *ph) {
+    // ph[alpha-offset + v] = exp(-2 pi i K_alpha v / L_alpha): the phase e^{ik.t} of
+    // the translation t = -v along alpha that moves coordinate v to the origin
+    const int tot = L.L[0] + L.L[1] + L.L[2];
+    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+        int a = (i < L.L[0]) ? 0 : (i < L.L[0] + L.L[1] ? 1 : 2);
+        int v = i - (a == 0 ? 0 : (a == 1 ? L.L[0] : L.L[0] + L.L[1]));
+        long long num = (long long)K[a] * v % L.L[a];
+        double sn, cs;
+        sincospi(-2.0 * (double)num / (double)L.L[a], &sn, &cs);
+        ph[i].x = (R)cs;
+        ph[i].y = (R)sn;
+    }
+}
+
+template <int ND, typename VT, bool KS>
+__global__ void __launch_bounds__(NTHREADS) k_hphi(LatView L, const SecView *__restrict__ secs,
+                                                   const int *__restrict__ tile0, int S, int ntiles,
+                                                   const VT *__restrict__ phi, VT *__restrict__ psi) {
+    using R = typename VTr<VT>::R;
+    using CT = typename VTr<VT>::C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemLayout sm = carve(L, smem);
+    stage_tables(L, sm.sC, KS ? sm.sxyz : nullptr);
+    R *snorm = (R *)sm.snorm;
+    if (threadIdx.x < 9) {
+        snorm[threadIdx.x] = (R)sqrt((double)threadIdx.x);
+        snorm[9 + threadIdx.x] = threadIdx.x ? (R)(1.0 / sqrt((double)threadIdx.x)) : (R)0;
+    }
+    CT *ph = (CT *)sm.sph;
+    const CT *phx = ph, *phy = ph + L.L[0], *phz = ph + L.L[0] + L.L[1];
+    const R *jxy = jxy_table<VT>(L);
+    __syncthreads();
+    int cur = -1;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int s = (S == 1) ? 0 : sector_of_tile(tile0, S, t);
+        const SecView sv = secs[s];
+        if (KS && s != cur) {
+            __syncthreads();
+            fill_phases<CT, R>(L, sv.K, ph);
+            __syncthreads();
+            cur = s;
+        }
+        const uint64_t row = (uint64_t)(t - sv.tile0) * TILE + threadIdx.x;
+        if (row >= sv.dim) continue;
+        const uint64_t rank = KS ? __ldg(sv.sigma + row) : row;
+        int c[ND];
+        unrank(rank, sm.sC, L.np1, c);
+        const VT *ph_in = phi + sv.off;
+        const VT x0 = ph_in[row];
+        R rs = 0;
+        if constexpr (KS) rs = snorm[9 + sv.stab[row]];
+        double e = L.c0, dd = 0.0;
+        CT acc;
+        acc.x = 0; acc.y = 0;
+#pragma unroll
+        for (int m = 0; m < ND; ++m) {
+            const int i = c[m];
+            e += __ldg(L.u + i);
+            const int e0 = __ldg(L.adj_ptr + i), e1 = __ldg(L.adj_ptr + i + 1);
+            for (int q = e0; q < e1; ++q) {
+                const int j = __ldg(L.adj_nbr + q);
+                bool occ = false;
+#pragma unroll
+                for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
+                if (occ) {
+                    dd += __ldg(L.adj_jz + q);
+                    continue;
+                }
+                int tt[ND];
+#pragma unroll
+                for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
+                sort_net(tt);
+                const R jh = (R)0.5 * __ldg(jxy + q);
+                if constexpr (!KS) {
+                    const uint64_t r2 = rank_of(tt, sm.sC, L.np1);
+                    CT cf;
+                    cf.x = jh; cf.y = 0;
+                    acc_add(acc, cf, ph_in[r2]);
+                } else {
+                    int rep[ND];
+                    int ax, by, cz;
+                    const uint64_t r2 = canon(tt, L, sm.sxyz, sm.sC, rep, ax, by, cz);
+                    uint32_t idx;
+                    if (!sigma_find(sv, prefix_of(rep, sm.sC, L.np1), r2, idx)) continue;
+                    CT p = cmul(cmul(phx[ax], phy[by]), phz[cz]);
+                    const R w = jh * snorm[__ldg(sv.stab + idx)] * rs;
+                    p.x *= w;
+                    p.y *= w;
+                    acc_add(acc, p, ph_in[idx]);
+                }
+            }
+        }
+        CT dg;
+        dg.x = (R)(e + 0.5 * dd);
+        dg.y = 0;
+        acc_add(acc, dg, x0);
+        store(psi + sv.off + row, acc);
+    }
+}
+
+// nnz count: the diagonal plus every hop that lands on a member of the sector
+template <int ND, bool KS>
+__global__ void __launch_bounds__(NTHREADS) k_count(LatView L, const SecView *__restrict__ secs,
+                                                    const int *__restrict__ tile0, int S, int ntiles,
+                                                    unsigned long long *out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemLayout sm = carve(L, smem);
+    stage_tables(L, sm.sC, KS ? sm.sxyz : nullptr);
+    __syncthreads();
+    unsigned long long cnt = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int s = (S == 1) ? 0 : sector_of_tile(tile0, S, t);
+        const SecView sv = secs[s];
+        const uint64_t row = (uint64_t)(t - sv.tile0) * TILE + threadIdx.x;
+        if (row >= sv.dim) continue;
+        const uint64_t rank = KS ? sv.sigma[row] : row;
+        int c[ND];
+        unrank(rank, sm.sC, L.np1, c);
+        cnt += 1;
+#pragma unroll
+        for (int m = 0; m < ND; ++m) {
+            const int i = c[m];
+            for (int q = L.adj_ptr[i]; q < L.adj_ptr[i + 1]; ++q) {
+                const int j = L.adj_nbr[q];
+                bool occ = false;
+#pragma unroll
+                for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
+                if (occ) continue;
+                if constexpr (!KS) { ++cnt; continue; } else {
+                int tt[ND];
+#pragma unroll
+                for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
+                sort_net(tt);
+                int rep[ND];
+                int ax, by, cz;
+                const uint64_t r2 = canon(tt, L, sm.sxyz, sm.sC, rep, ax, by, cz);
+                uint32_t idx;
+                if (sigma_find(sv, prefix_of(rep, sm.sC, L.np1), r2, idx)) ++cnt;
+                }
+            }
+        }
+    }
+    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
+}
+
+// N_down = 0: H is the constant c0 on the single vacuum state of each sector
+template <typename VT>
+__global__ void k_diag0(double c0, uint64_t n, const VT *__restrict__ phi, VT *__restrict__ psi) {
+    using R = typename VTr<VT>::R;
+    using CT = typename VTr<VT>::C;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        CT acc; acc.x = 0; acc.y = 0;
+        CT d; d.x = (R)c0; d.y = 0;
+        acc_add(acc, d, phi[i]);
+        store(psi + i, acc);
+    }
+}
+
+static int g_nsm = 0;
+
+static int num_sms() {
+    if (!g_nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (g_nsm <= 0) g_nsm = 1;
+    }
+    return g_nsm;
+}
+
+template <typename KF>
+static int launch_rows(KF kern, Basis &B, size_t smem, int &cached_blocks, cudaStream_t st, int *grid_out) {
+    if (cached_blocks <= 0) {
+        QS3_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int nb = 0;
+        QS3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NTHREADS, smem));
+        cached_blocks = std::max(nb, 1);
+    }
+    int grid = std::min(B.ntiles, cached_blocks * num_sms());
+    *grid_out = std::max(grid, 1);
+    return QS3_OK;
+}
+
+template <int ND, typename VT, bool KS>
+static int hphi_nd(Basis &B, const void *phi, void *psi, cudaStream_t st) {
+    static int cached = 0;
+    static size_t cached_smem = 0;
+    if (cached_smem != B.smem_bytes) { cached = 0; cached_smem = B.smem_bytes; }
+    int grid = 1;
+    QS3_TRY(launch_rows(k_hphi<ND, VT, KS>, B, B.smem_bytes, cached, st, &grid));
+    if (B.ntiles == 0) return QS3_OK;
+    k_hphi<ND, VT, KS><<<grid, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S,
+                                                              B.ntiles, (const VT *)phi, (VT *)psi);
+    QS3_CUDA(cudaGetLastError());
+    return QS3_OK;
+}
+
+template <typename VT, bool KS>
+static int hphi_vt(Basis &B, const void *phi, void *psi, cudaStream_t st) {
+    switch (B.nd) {
+        case 1: return hphi_nd<1, VT, KS>(B, phi, psi, st);
+        case 2: return hphi_nd<2, VT, KS>(B, phi, psi, st);
+        case 3: return hphi_nd<3, VT, KS>(B, phi, psi, st);
+        case 4: return hphi_nd<4, VT, KS>(B, phi, psi, st);
+        case 5: return hphi_nd<5, VT, KS>(B, phi, psi, st);
+        case 6: return hphi_nd<6, VT, KS>(B, phi, psi, st);
+        case 7: return hphi_nd<7, VT, KS>(B, phi, psi, st);
+        case 8: return hphi_nd<8, VT, KS>(B, phi, psi, st);
+        default: return set_err(QS3_ERR_INVALID_ARG, "n_down %d", B.nd);
+    }
+}
+
+int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t st) {
+    if (!phi || !psi) return set_err(QS3_ERR_INVALID_ARG, "NULL vector");
+    if (phi == psi) return set_err(QS3_ERR_INVALID_ARG, "phi and psi alias");
+    if (B.has_k && (dt == QS3_F32 || dt == QS3_F64))
+        return set_err(QS3_ERR_STATE, "k-sector bases need complex vectors (C64/C128)");
+    if (B.total == 0) return QS3_OK;
+    if (B.nd == 0) {
+        const int grid = (int)std::min<uint64_t>((B.total + 255) / 256, 1024);
+        switch (dt) {
+            case QS3_F32: k_diag0<float><<<grid, 256, 0, st>>>(B.lv.c0, B.total, (const float *)phi, (float *)psi); break;
+            case QS3_F64: k_diag0<double><<<grid, 256, 0, st>>>(B.lv.c0, B.total, (const double *)phi, (double *)psi); break;
+            case QS3_C64: k_diag0<float2><<<grid, 256, 0, st>>>(B.lv.c0, B.total, (const float2 *)phi, (float2 *)psi); break;
+            case QS3_C128: k_diag0<double2><<<grid, 256, 0, st>>>(B.lv.c0, B.total, (const double2 *)phi, (double2 *)psi); break;
+            default: return set_err(QS3_ERR_INVALID_ARG, "dtype %d", (int)dt);
+        }
+        QS3_CUDA(cudaGetLastError());
+        return QS3_OK;
+    }
+    if (B.has_k) {
+        if (dt == QS3_C64) return hphi_vt<float2, true>(B, phi, psi, st);
+        if (dt == QS3_C128) return hphi_vt<double2, true>(B, phi, psi, st);
+    } else {
+        if (dt == QS3_F32) return hphi_vt<float, false>(B, phi, psi, st);
+        if (dt == QS3_F64) return hphi_vt<double, false>(B, phi, psi, st);
+        if (dt == QS3_C64) return hphi_vt<float2, false>(B, phi, psi, st);
+        if (dt == QS3_C128) return hphi_vt<double2, false>(B, phi, psi, st);
+    }
+    return set_err(QS3_ERR_INVALID_ARG, "dtype %d", (int)dt);
+}
+
+template <int ND, bool KS>
+static int count_nd(Basis &B, unsigned long long *d_out) {
+    static int cached = 0;
+    static size_t cached_smem = 0;
+    if (cached_smem != B.smem_bytes) { cached = 0; cached_smem = B.smem_bytes; }
+    int grid = 1;
+    QS3_TRY(launch_rows(k_count<ND, KS>, B, B.smem_bytes, cached, 0, &grid));
+    k_count<ND, KS><<<grid, NTHREADS, B.smem_bytes>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S,
+                                                       B.ntiles, d_out);
+    QS3_CUDA(cudaGetLastError());
+    return QS3_OK;
+}
+
+template <bool KS>
+static int count_ks(Basis &B, unsigned long long *d_out) {
+    switch (B.nd) {
+        case 1: return count_nd<1, KS>(B, d_out);
+        case 2: return count_nd<2, KS>(B, d_out);
+        case 3: return count_nd<3, KS>(B, d_out);
+        case 4: return count_nd<4, KS>(B, d_out);
+        case 5: return count_nd<5, KS>(B, d_out);
+        case 6: return count_nd<6, KS>(B, d_out);
+        case 7: return count_nd<7, KS>(B, d_out);
+        case 8: return count_nd<8, KS>(B, d_out);
+        default: return set_err(QS3_ERR_INVALID_ARG, "n_down %d", B.nd);
+    }
+}
+
+int count_nnz(Basis &B, uint64_t *nnz) {
+    if (B.nd == 0 || B.total == 0) {
+        *nnz = B.total;
+        return QS3_OK;
+    }
+    DevBuf d;
+    QS3_TRY(d.alloc(8));
+    QS3_CUDA(cudaMemset(d.p, 0, 8));
+    QS3_TRY(B.has_k ? count_ks<true>(B, d.as<unsigned long long>()) : count_ks<false>(B, d.as<unsigned long long>()));
+    unsigned long long v = 0;
+    QS3_CUDA(cudaMemcpy(&v, d.p, 8, cudaMemcpyDeviceToHost));
+    *nnz = v;
+    return QS3_OK;
+}
+
+}  // namespace qs3
+
+extern "C" int qs3_hphi(qs3_basis_t b, qs3_dtype dtype, const void *phi, void *psi, void *stream) {
+    qs3::clear_err();
+    if (!b) return qs3::set_err(QS3_ERR_INVALID_ARG, "basis is NULL");
+    return qs3::hphi_launch(b->B, dtype, phi, psi, (cudaStream_t)stream);
+}

@@ -1,0 +1,307 @@
+// qs3_internal.cuh -- host structures and device helpers shared by the
+// libqs3 translation units (GPU path only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "qs3.h"
+
+namespace qs3 {
+
+constexpr int MAXND = QS3_MAX_NDOWN;
+constexpr int TILE = 256;          // rows per tile (one thread per row)
+constexpr int NTHREADS = 256;
+
+// ------------------------------------------------------------------ errors
+int set_err(int code, const char *fmt, ...);
+void clear_err();
+
+#define QS3_CUDA(call)                                                                             \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return ::qs3::set_err(e_ == cudaErrorMemoryAllocation ? QS3_ERR_OOM : QS3_ERR_CUDA,   \
+                                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,       \
+                                  __LINE__);                                                       \
+    } while (0)
+
+#define QS3_TRY(expr)                                                                              \
+    do {                                                                                           \
+        int s_ = (expr);                                                                           \
+        if (s_ != QS3_OK) return s_;                                                               \
+    } while (0)
+
+// owning device buffer
+struct DevBuf {
+    void *p = nullptr;
+    size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release();
+    int alloc(size_t bytes);                      // cudaMalloc, QS3_ERR_OOM on failure
+    int upload(const void *src, size_t bytes);    // alloc + H2D copy
+    template <class T> T *as() const { return (T *)p; }
+};
+
+// ------------------------------------------------------- device-side views
+
+// Lattice data needed by every kernel.  binom rows m = 0..nd+2, each of
+// np1 = N + 1 entries: binom[m * np1 + c] = C(c, m).
+struct LatView {
+    int N, nd, np1;
+    int L[3];
+    int has_k;
+    int key_bits;                 // bits per site of a packed key, 0 -> compare ranks
+    const uint64_t *binom;
+    const int *adj_ptr;           // N + 1
+    const int *adj_nbr;           // 2 n_bonds
+    const double *adj_jxy;        // 2 n_bonds
+    const double *adj_jz;         // 2 n_bonds
+    const float *adj_jxy_f;       // fp32 copy of adj_jxy
+    const double *u;              // N: -(1/2) sum_j Jz_ij + h_i
+    double c0;                    // sum_b Jz_b / 4 - (1/2) sum_i h_i
+    const uint32_t *xyz;          // N: x | y << 11 | z << 22
+};
+
+struct SecView {
+    const uint64_t *sigma;        // sorted rank0 of the representatives (NULL: U(1))
+    const uint8_t *stab;          // |Stab| of each representative
+    const uint32_t *pidx;         // prefix index over sigma (see build_pidx)
+    uint64_t dim;
+    uint64_t off;                 // offset of the sector in a concatenated vector
+    int K[3];
+    int tile0;                    // first tile of the sector
+};
+
+// ---------------------------------------------------------- host basis
+struct Basis {
+    int N = 0, nd = 0, nb = 0;
+    int L[3] = {0, 0, 0};
+    bool has_k = false;
+    int S = 0;                              // sectors
+    std::vector<int> K;                     // 3 S
+    std::vector<uint64_t> dims, offs;       // S, S + 1
+    uint64_t total = 0;
+    std::vector<int> tile0;                 // S + 1
+    int ntiles = 0;
+    // host copies of the model
+    std::vector<int> bi, bj;
+    std::vector<double> jxy, jz, h, pos;
+    bool has_h = false;
+    // device data
+    DevBuf d_binom, d_adj_ptr, d_adj_nbr, d_adj_jxy, d_adj_jz, d_adj_jxy_f, d_u, d_xyz;
+    std::vector<DevBuf> d_sigma, d_stab, d_pidx;
+    DevBuf d_secs, d_tile0;
+    LatView lv{};
+    std::vector<SecView> secs;
+    uint64_t nnz = 0;
+    bool nnz_valid = false;
+    size_t smem_bytes = 0;                  // dynamic shared memory of the row kernels
+};
+
+// sector of tile t (binary search over tile0[0..S])
+__device__ __forceinline__ int sector_of_tile(const int *tile0, int S, int t) {
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tile0[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// --------------------------------------------------- combinatorial helpers
+
+// ascending bubble network on registers (static indexing only)
+template <int ND>
+__device__ __forceinline__ void sort_net(int (&a)[ND]) {
+#pragma unroll
+    for (int i = 0; i < ND; ++i) {
+#pragma unroll
+        for (int j = 0; j < ND - 1 - i; ++j) {
+            int lo = min(a[j], a[j + 1]);
+            int hi = max(a[j], a[j + 1]);
+            a[j] = lo;
+            a[j + 1] = hi;
+        }
+    }
+}
+
+// rank0 = sum_m C(c_m, m + 1) of an ascending list (Eq. a_of_n, 0-based)
+template <int ND>
+__device__ __forceinline__ uint64_t rank_of(const int (&c)[ND], const uint64_t *__restrict__ sC, int np1) {
+    uint64_t r = 0;
+#pragma unroll
+    for (int m = 0; m < ND; ++m) r += sC[(m + 1) * np1 + c[m]];
+    return r;
+}
+
+// inverse of rank_of (Alg. 1): greedy largest-first column search
+template <int ND>
+__device__ __forceinline__ void unrank(uint64_t r, const uint64_t *__restrict__ sC, int np1, int (&c)[ND]) {
+    int hi = np1 - 2;
+#pragma unroll
+    for (int m = ND; m >= 2; --m) {
+        const uint64_t *col = sC + m * np1;
+        int lo = m - 1, h = hi;
+        while (lo < h) {
+            int mid = (lo + h + 1) >> 1;
+            if (col[mid] <= r) lo = mid; else h = mid - 1;
+        }
+        c[m - 1] = lo;
+        r -= col[lo];
+        hi = lo - 1;
+    }
+    if (ND >= 1) c[0] = (int)r;
+}
+
+// select a[i] for a runtime i without dynamic register indexing
+template <int ND>
+__device__ __forceinline__ int pick(const int (&a)[ND], int i) {
+    int v = a[0];
+#pragma unroll
+    for (int m = 1; m < ND; ++m) v = (i == m) ? a[m] : v;
+    return v;
+}
+
+template <int ND>
+__device__ __forceinline__ bool seen_before(const int (&a)[ND], int i, int v) {
+    bool s = false;
+#pragma unroll
+    for (int m = 0; m < ND - 1; ++m) s |= (m < i) && (a[m] == v);
+    return s;
+}
+
+// Minimum-rank translate of the ascending site list t (the representative of
+// its orbit, Alg. 7).  Exact candidate pruning: the representative has a
+// down spin at x = 0, one at y = 0 and one at z = 0 (otherwise a -1 shift
+// along that axis lowers every site index and hence the rank), so only the
+// translations (-x_a, -y_b, -z_c) over spins a, b, c are tried.  On return
+// rep holds the sorted representative, (ax, by, cz) the coordinates moved to
+// the origin, and the function returns its rank0.
+template <int ND>
+__device__ __forceinline__ uint64_t canon(const int (&t)[ND], const LatView &L, const uint32_t *__restrict__ sxyz,
+                                          const uint64_t *__restrict__ sC, int (&rep)[ND], int &ax, int &by,
+                                          int &cz) {
+    int X[ND], Y[ND], Z[ND];
+#pragma unroll
+    for (int m = 0; m < ND; ++m) {
+        uint32_t p = sxyz[t[m]];
+        X[m] = p & 2047u;
+        Y[m] = (p >> 11) & 2047u;
+        Z[m] = p >> 22;
+    }
+    const int Lx = L.L[0], Ly = L.L[1], Lz = L.L[2];
+    const int LxLy = Lx * Ly;
+    const int kb = L.key_bits;
+    uint64_t best = ~0ull;
+    int bc = 0, bb = 0, ba = 0;
+#pragma unroll 1
+    for (int c = 0; c < ND; ++c) {
+        const int zc = pick(Z, c);
+        if (seen_before(Z, c, zc)) continue;
+#pragma unroll 1
+        for (int b = 0; b < ND; ++b) {
+            const int yb = pick(Y, b);
+            if (seen_before(Y, b, yb)) continue;
+            int yz[ND];
+#pragma unroll
+            for (int m = 0; m < ND; ++m) {
+                int zz = Z[m] - zc;
+                zz += (zz < 0) ? Lz : 0;
+                int yy = Y[m] - yb;
+                yy += (yy < 0) ? Ly : 0;
+                yz[m] = yy * Lx + zz * LxLy;
+            }
+#pragma unroll 1
+            for (int a = 0; a < ND; ++a) {
+                const int xa = pick(X, a);
+                if (seen_before(X, a, xa)) continue;
+                int s[ND];
+#pragma unroll
+                for (int m = 0; m < ND; ++m) {
+                    int xx = X[m] - xa;
+                    xx += (xx < 0) ? Lx : 0;
+                    s[m] = yz[m] + xx;
+                }
+                sort_net(s);
+                uint64_t key;
+                if (kb) {
+                    key = 0;
+#pragma unroll
+                    for (int m = ND - 1; m >= 0; --m) key = (key << kb) | (uint64_t)s[m];
+                } else {
+                    key = rank_of(s, sC, L.np1);
+                }
+                if (key < best) { best = key; bc = c; bb = b; ba = a; }
+            }
+        }
+    }
+    ax = pick(X, ba);
+    by = pick(Y, bb);
+    cz = pick(Z, bc);
+#pragma unroll
+    for (int m = 0; m < ND; ++m) {
+        int xx = X[m] - ax; xx += (xx < 0) ? Lx : 0;
+        int yy = Y[m] - by; yy += (yy < 0) ? Ly : 0;
+        int zz = Z[m] - cz; zz += (zz < 0) ? Lz : 0;
+        rep[m] = xx + Lx * yy + LxLy * zz;
+    }
+    sort_net(rep);
+    return rank_of(rep, sC, L.np1);
+}
+
+// prefix of a sorted list used by the two-level index over sigma: the colex
+// rank of its two largest sites (its largest site when ND == 1)
+template <int ND>
+__device__ __forceinline__ uint32_t prefix_of(const int (&c)[ND], const uint64_t *__restrict__ sC, int np1) {
+    if (ND >= 2) return (uint32_t)(sC[2 * np1 + c[ND - 1]] + (uint64_t)c[ND - 2]);
+    return (uint32_t)c[0];
+}
+
+// position of rank r in sector sv (binary search inside the prefix bucket)
+__device__ __forceinline__ bool sigma_find(const SecView &sv, uint32_t P, uint64_t r, uint32_t &idx) {
+    uint32_t lo = __ldg(sv.pidx + P), hi = __ldg(sv.pidx + P + 1);
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(sv.sigma + mid) < r) lo = mid + 1; else hi = mid;
+    }
+    idx = lo;
+    return lo < __ldg(sv.pidx + P + 1) && __ldg(sv.sigma + lo) == r;
+}
+
+// stage the binomial table (rows 0..nd+2) and the coordinate table in smem
+__device__ __forceinline__ void stage_tables(const LatView &L, uint64_t *sC, uint32_t *sxyz) {
+    const int nC = (L.nd + 3) * L.np1;
+    for (int i = threadIdx.x; i < nC; i += blockDim.x) sC[i] = L.binom[i];
+    if (sxyz)
+        for (int i = threadIdx.x; i < L.N; i += blockDim.x) sxyz[i] = L.xyz[i];
+}
+
+size_t row_kernel_smem(const Basis &B, int extra_nd);
+
+// -------------------------------------------------------------- entry points
+// implemented in qs3_hphi.cu
+int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t st);
+int count_nnz(Basis &B, uint64_t *nnz);
+// implemented in qs3_basis.cu
+int build_sector_reps(Basis &B, int s);
+// implemented in qs3_obs.cu
+int smq_launch(Basis &src, int s_src, const void *phi, Basis &dst, int s_dst, const int *Q, void *psi,
+               cudaStream_t st);
+
+}  // namespace qs3
+
+struct qs3_basis_s {
+    qs3::Basis B;
+};
