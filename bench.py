@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark of the QS^3 hot path on GB300.
+
+Workload (default): the isotropic Heisenberg model on the periodic 10x10
+square lattice, J = Jz = 1, N_down = 4, all 100 momentum sectors (total
+dimension C(100,4) = 3,921,225), complex fp64.  One step is the batched
+ground-state solve of all 100 sectors: the device-built basis is reused, a
+seeded start vector is drawn on the device, and conventional Lanczos with
+full reorthogonalisation runs every sector to its lowest eigenvalue (Ritz
+value change <= 1e-14 and Ritz residual <= 1e-12 |E|), eigenvectors
+assembled in fp64.  The metric is H Phi throughput over the whole step:
+structural non-zeros applied by all H Phi launches of the step divided by
+the step time (Gnnz/s).
+
+Also reported:
+- roofline of the dominant kernel (the k-sector H Phi) from CUDA events
+  recorded inside the library on the solve's stream;
+- e2e: the same step through the C ABI from host buffers (basis built from
+  host lattice arrays, eigenvectors copied back to host) per step;
+- the batched fp32-H Phi + fp64-refinement solve against plain fp64 on the
+  same workload (seconds and eigenvalue agreement);
+- cpu_baseline: the oracle's H Phi (Alg. 9 as printed: every bond, every
+  translation) timed on the host cores on a bounded sample of rows.
+
+--impl reference times the oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import qs3_inputs as qi  # noqa: E402
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+WORKLOADS = {
+    # name: (lattice factory, n_down, momenta)
+    "square10x10_nd4_all_k": (lambda: qi.square(10), 4, lambda: qi.all_k((10, 10, 1))),
+    "chain16_nd3_u1": (lambda: qi.chain(16), 3, lambda: None),
+}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+                 "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, gpu_index: int = 0):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9 or not f[0].isdigit() or int(f[0]) != gpu_index:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = max(mx, float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_2107_00872_gb300 as qs3
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    mk, nd, ks = WORKLOADS[args.workload]
+    spec = mk()
+    Ks = ks()
+    basis = qs3.Basis(spec, nd, Ks)
+    nnz_h = basis.nnz()
+    stream = torch.cuda.current_stream()
+    opts = qs3.SolveOpts(n_max=args.n_max, min_iter=20, check_every=5, eps=1e-14, res_tol=1e-12,
+                         precision="f64", seed=1 + rank)
+
+    def step(seed):
+        opts.seed = seed
+        return basis.lanczos(opts, vectors=True, stream=stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for w in range(args.warmup):
+        step(1000 + w)
+    torch.cuda.synchronize()
+    launches0 = qs3.load().qs3_kernel_launches()
+    clk = ClockSampler()
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    evals = None
+    for k in range(args.steps):
+        evals, vec, info = step(1 + k + 17 * rank)
+        infos.append(info)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop(dev.index or 0)
+    ms_total = ev0.elapsed_time(ev1)
+    launches = qs3.load().qs3_kernel_launches() - launches0
+    nnz_steps = sum(i["hphi_nnz"] for i in infos)
+    hphi_s = sum(i["hphi_seconds"] for i in infos)
+    hphi_calls = sum(i["hphi_calls"] for i in infos)
+    t_local = ms_total / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        n = torch.tensor([float(nnz_steps)], device=dev, dtype=torch.float64)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        t_max, nnz_all = float(t.item()), float(n.item())
+    else:
+        t_max, nnz_all = t_local, float(nnz_steps)
+    value = nnz_all / t_max / 1e9
+
+    # roofline of the H Phi launches (dominant kernel of the step)
+    peaks, peak_kind = load_peaks()
+    D = basis.total_dim
+    s_phi = 16
+    per_launch_nnz = nnz_steps / max(hphi_calls, 1)
+    # algorithmic bytes of one full launch: diagonal read, one gather per term,
+    # psi write, sigma row rank, one sigma probe per term (sectors drop out of
+    # the launches as they converge, so scale by the average work per launch)
+    frac_work = per_launch_nnz / nnz_h
+    B_alg = frac_work * (D * s_phi + (nnz_h - D) * s_phi + D * s_phi + D * 8 + (nnz_h - D) * 8)
+    t_launch = hphi_s / max(hphi_calls, 1)
+    achieved = B_alg / t_launch / 1e9
+    roof = {"kernel": "k_hphi<ND=4, complex128, k-sector>", "bound": "hbm", "achieved": round(achieved, 1),
+            "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+            "frac": round(achieved / peaks.get("hbm_gbs"), 4), "traffic": None,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback",
+            "launch_ms": round(1e3 * t_launch, 4), "launch_gnnz_s": round(per_launch_nnz / t_launch / 1e9, 2),
+            "hphi_share_of_step": round(hphi_s / (t_local), 3)}
+
+    out = {
+        "metric": "H Phi Gnnz/s (batched Lanczos ground-state solve)",
+        "value": round(value, 3),
+        "unit": "Gnnz/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1e3 * t_max / args.steps, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "lattice": spec.name, "n_sites": spec.n_sites, "n_down": nd,
+                   "sectors": basis.n_sectors, "total_dim": D, "nnz_per_hphi": nnz_h,
+                   "solver": "Lanczos, full reorthogonalisation (CGS2), fp64",
+                   "l2": "working set > L2 (Krylov basis of ~100 vectors x 63 MB)",
+                   "parallelism": f"replicas x{world} (independent sectors per GPU)"},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "lowest_E": float(np.min(evals)),
+        "lanczos_steps_per_solve": [int(i["iterations"]) for i in infos],
+        "max_residual": max(i["max_residual"] for i in infos),
+    }
+    return out, basis, spec, nd, Ks
+
+
+def e2e_ours(args, spec, nd, Ks):
+    """Same step through the public API from host buffers: basis built from
+    the host lattice arrays (H2D), solve, eigenvectors and eigenvalues back to
+    host (D2H), every step."""
+    import torch
+
+    import paper_2107_00872_gb300 as qs3
+    stream = torch.cuda.current_stream()
+    h2d = sum(np.asarray(a).nbytes for a in (spec.bi, spec.bj, spec.jxy, spec.jz)) + (12 * len(Ks) if Ks else 0)
+    times = []
+    nnz = 0
+    d2h = 0
+    for k in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B = qs3.Basis(spec, nd, Ks)
+        ev, vec, info = B.lanczos(qs3.SolveOpts(n_max=args.n_max, eps=1e-14, res_tol=1e-12, seed=7 + k),
+                                  vectors=True, stream=stream)
+        host = vec.cpu().numpy()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        nnz += info["hphi_nnz"]
+        d2h = host.nbytes + ev.nbytes
+        B.close()
+    t = float(np.sum(times))
+    return {"value": round(nnz / t / 1e9, 3), "unit": "Gnnz/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "seconds_per_step": round(t / len(times), 4),
+            "includes": "basis build from host arrays + solve + eigenvector D2H"}
+
+
+def fp32_vs_fp64(args, basis):
+    """Batched fp32 H Phi + fp64 recurrences/refinement against plain fp64."""
+    import torch
+
+    import paper_2107_00872_gb300 as qs3
+    res = {}
+    ev = {}
+    for prec in ("f64", "f32"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e, _, info = basis.lanczos(qs3.SolveOpts(n_max=args.n_max, eps=1e-14, res_tol=1e-12, precision=prec,
+                                                 seed=3), vectors=False)
+        torch.cuda.synchronize()
+        res[prec] = {"seconds": round(time.perf_counter() - t0, 4), "steps": int(info["iterations"]),
+                     "refine_steps": int(info["refine_iterations"]), "status": info["status"]}
+        ev[prec] = e[:, 0]
+    res["max_rel_dE"] = float(np.max(np.abs(ev["f32"] - ev["f64"]) / np.abs(ev["f64"])))
+    return res
+
+
+# --------------------------------------------------------- oracle timing
+
+def oracle_sample(args, seconds_budget: float = 15.0, threads: int | None = None):
+    """Oracle H Phi (Alg. 9 literally) on sampled rows of one sector of the
+    workload; returns (Gnnz/s, cores, description)."""
+    import oracle as orc
+    mk, nd, ks = WORKLOADS[args.workload]
+    spec = mk()
+    Ks = ks()
+    lat = orc.Lattice(**spec.as_dict())
+    cores = orc.set_threads(threads or os.cpu_count() or 1)
+    if Ks:
+        K = Ks[1]
+        sec = orc.mk_list(lat, nd, K)
+        d = sec.dim
+        x = qi.gaussian_start(5, d, True)
+        rng = np.random.default_rng(0)
+        n = 256
+        done_rows, done_nnz, t_sum = 0, 0, 0.0
+        while t_sum < seconds_budget and done_rows < d:
+            rows = rng.integers(0, d, n)
+            t0 = time.perf_counter()
+            y, cnt = orc.hphi_k_rows(sec, x, rows, count=True)
+            t_sum += time.perf_counter() - t0
+            done_rows += n
+            done_nnz += cnt
+            n = min(n * 2, 1 << 16)
+        desc = f"{done_rows} random rows of sector K={K} (dim {d}) of {spec.name}, N_down={nd}"
+    else:
+        D = math.comb(spec.n_sites, nd)
+        x = qi.gaussian_start(5, D, False)
+        rows = np.arange(D)
+        t0 = time.perf_counter()
+        y, cnt = orc.hphi_u1_rows(lat, nd, x, rows, count=True)
+        t_sum = time.perf_counter() - t0
+        done_nnz = cnt
+        desc = f"all {D} rows of {spec.name}, N_down={nd}"
+    return done_nnz / t_sum / 1e9, cores, desc
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    t_all = []
+    rate_all = []
+    cores = 1
+    desc = ""
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        rate, cores, desc = oracle_sample(args, seconds_budget=4.0)
+        if k >= args.warmup:
+            t_all.append(time.perf_counter() - t0)
+            rate_all.append(rate)
+    value = float(np.mean(rate_all))
+    return {"impl": "reference", "metric": "H Phi Gnnz/s (batched Lanczos ground-state solve)",
+            "value": round(value, 6), "unit": "Gnnz/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * float(np.mean(t_all)), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload},
+            "cpu_baseline": {"value": round(value, 6), "unit": "Gnnz/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": round(value, 6), "unit": "Gnnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_hphi_only(args):
+    """H Phi launches alone on the workload's basis (kernel-level numbers and
+    the small-footprint case for profiling): W warm-up and K timed launches
+    of psi = H phi over all sectors, CUDA events on the launching stream."""
+    import torch
+
+    import paper_2107_00872_gb300 as qs3
+    mk, nd, ks = WORKLOADS[args.workload]
+    spec = mk()
+    Ks = ks()
+    B = qs3.Basis(spec, nd, Ks)
+    dt = {"c128": torch.complex128, "c64": torch.complex64, "f64": torch.float64, "f32": torch.float32}[args.dtype]
+    if Ks and not dt.is_complex:
+        raise SystemExit("k-sectors need complex vectors")
+    g = torch.Generator(device="cuda").manual_seed(0)
+    phi = torch.randn(B.total_dim, dtype=dt, device="cuda", generator=g)
+    psi = torch.empty_like(phi)
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        B.hphi(phi, psi, st)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        B.hphi(phi, psi, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / args.steps
+    nnz = B.nnz()
+    s = phi.element_size()
+    D = B.total_dim
+    b_alg = D * s + (nnz - D) * s + D * s + (D * 8 + (nnz - D) * 8 if Ks else 0)
+    peaks, kind = load_peaks()
+    return {"mode": "hphi", "workload": args.workload, "dtype": args.dtype, "total_dim": D, "nnz": nnz,
+            "ms_per_launch": round(1e3 * t, 4), "gnnz_s": round(nnz / t / 1e9, 3),
+            "alg_bytes_per_launch": int(b_alg), "alg_gbs": round(b_alg / t / 1e9, 1),
+            "hbm_frac": round(b_alg / t / 1e9 / peaks["hbm_gbs"], 4), "peak_source": kind}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "hphi"])
+    ap.add_argument("--dtype", default="c128", choices=["c128", "c64", "f64", "f32"], help="--mode hphi only")
+    ap.add_argument("--workload", default="square10x10_nd4_all_k", choices=sorted(WORKLOADS))
+    ap.add_argument("--n-max", dest="n_max", type=int, default=250)
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e / fp32 / cpu_baseline legs")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.mode == "hphi":
+        print(json.dumps(run_hphi_only(args)), flush=True)
+        return
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    out, basis, spec, nd, Ks = run_ours(args, rank, world)
+    if rank == 0 and not args.no_extras:
+        out["e2e"] = e2e_ours(args, spec, nd, Ks)
+        out["fp32_vs_fp64"] = fp32_vs_fp64(args, basis)
+        rate, cores, desc = oracle_sample(args)
+        out["cpu_baseline"] = {"value": round(rate, 6), "unit": "Gnnz/s", "cores": cores, "kind": "oracle",
+                               "sample": desc}
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

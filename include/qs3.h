@@ -118,6 +118,7 @@ typedef struct {
     int32_t use_graphs;   /* capture the Lanczos steps of a cycle in a CUDA graph */
     uint64_t seed;        /* start vector: seeded Gaussian (SplitMix64 + Box-Muller) */
     double refine_tol;    /* fp32 mode: refine until |dE| <= refine_tol |E| (e.g. 1e-9) */
+    double res_tol;       /* qs3_lanczos also needs the Ritz residual beta_m |c_m| <= res_tol max(|E|, 1); 0 = off */
 } qs3_solve_opts;
 
 typedef struct {
@@ -127,6 +128,10 @@ typedef struct {
     int32_t refine_iterations; /* fp64 Lanczos steps spent in refinement */
     double max_residual;  /* max over sectors/eigenpairs of ||H v - E v|| (fp64, unit v) */
     double seconds;       /* wall time of the call */
+    uint64_t hphi_nnz;    /* structural non-zeros applied by the H Phi launches (active sectors only) */
+    double hphi_seconds;  /* device time of those launches (CUDA events on the call's stream) */
+    int32_t hphi_calls;   /* H Phi launches */
+    int32_t pad_;
 } qs3_solve_info;
 
 /* Conventional Lanczos with full reorthogonalisation (Alg. 10 lines 2-12)
@@ -186,6 +191,10 @@ const char *qs3_last_error(void);
 
 /* Library version string. */
 const char *qs3_version(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (library primitives such as the CUB sort are not counted). */
+uint64_t qs3_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -61,12 +61,12 @@ def _load():
                 "orc_spin_exchange": ([I, I, P, I, I], U),
                 "orc_dense_u1": (lat + [P], I),
                 "orc_hphi_u1": (lat + [P, P], I),
-                "orc_hphi_u1_rows": (lat + [P, L, P, P], I),
+                "orc_hphi_u1_rows": (lat + [P, L, P, P, P], I),
                 "orc_mk_list": (lat + [P, P, P], L),
                 "orc_representative": (lat + [U, P], U),
                 "orc_orbit": (lat + [U, P], I),
                 "orc_hphi_k": (lat + [P, P, P, L, P, P], I),
-                "orc_hphi_k_rows": (lat + [P, P, P, L, P, L, P, P], I),
+                "orc_hphi_k_rows": (lat + [P, P, P, L, P, L, P, P, P], I),
                 "orc_dense_k": (lat + [P, P, P, L, P], I),
                 "orc_smq": (lat + [P, P, P, L, P, P, P, P, P, L, P], I),
                 "orc_corr_u1": ([I, I, P, P, P, P], I),
@@ -169,12 +169,15 @@ def hphi_u1(lat: Lattice, nd: int, phi: np.ndarray) -> np.ndarray:
     return y
 
 
-def hphi_u1_rows(lat: Lattice, nd: int, phi: np.ndarray, rows: np.ndarray) -> np.ndarray:
+def hphi_u1_rows(lat: Lattice, nd: int, phi: np.ndarray, rows: np.ndarray, count: bool = False):
+    """U(1) H phi on the given 0-based rows; with count=True also the number
+    of matrix terms applied."""
     x = np.ascontiguousarray(phi, dtype=np.complex128)
     r = np.ascontiguousarray(rows, dtype=np.int64)
     y = np.zeros(len(r), np.complex128)
-    _load().orc_hphi_u1_rows(*lat._args(nd), _p(x), len(r), _p(r), _p(y))
-    return y
+    n = np.zeros(1, np.int64)
+    _load().orc_hphi_u1_rows(*lat._args(nd), _p(x), len(r), _p(r), _p(y), _p(n))
+    return (y, int(n[0])) if count else y
 
 
 @dataclass
@@ -236,14 +239,17 @@ def hphi_k(sec: Sector, phi: np.ndarray) -> np.ndarray:
     return y
 
 
-def hphi_k_rows(sec: Sector, phi: np.ndarray, rows: np.ndarray) -> np.ndarray:
+def hphi_k_rows(sec: Sector, phi: np.ndarray, rows: np.ndarray, count: bool = False):
+    """Alg. 9 on the given 0-based rows; with count=True also the number of
+    matrix terms applied."""
     x = np.ascontiguousarray(phi, dtype=np.complex128)
     r = np.ascontiguousarray(rows, dtype=np.int64)
     y = np.zeros(len(r), np.complex128)
+    n = np.zeros(1, np.int64)
     Kc = np.ascontiguousarray(sec.K, dtype=np.int32)
     _load().orc_hphi_k_rows(*sec.lat._args(sec.nd), _p(Kc), _p(sec.sigma1), _p(sec.Nak), sec.dim, _p(x),
-                            len(r), _p(r), _p(y))
-    return y
+                            len(r), _p(r), _p(y), _p(n))
+    return (y, int(n[0])) if count else y
 
 
 def dense_k(sec: Sector) -> np.ndarray:

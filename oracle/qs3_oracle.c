@@ -397,11 +397,12 @@ int orc_dense_u1(ORC_LAT, double *H)
 }
 
 /* one row of the U(1) product psi = H phi (Alg. 4 applied on the fly) */
-static zdbl hphi_u1_row(const orc_ctx *c, uint64_t a, const zdbl *phi)
+static zdbl hphi_u1_row(const orc_ctx *c, uint64_t a, const zdbl *phi, int64_t *terms)
 {
     int n[ORC_MAXND], np[ORC_MAXND];
     f_bar(c, a, n, NULL);
     zdbl acc = diag_elem(c, n) * phi[a - 1];
+    *terms += 1;
     for (int b = 0; b < c->nb; ++b) {
         int f, fp;
         int p = binary_search_int(c->r[b], n, 1, c->nd, &f);
@@ -410,6 +411,7 @@ static zdbl hphi_u1_row(const orc_ctx *c, uint64_t a, const zdbl *phi)
             spin_exchange(c->nd, c->r[b], p, f, c->rp[b], pp, n, np);
             uint64_t ap = F(c, np);
             acc += (c->jxy[b] / 2.0) * phi[ap - 1];
+            *terms += 1;
         }
     }
     return acc;
@@ -423,21 +425,26 @@ int orc_hphi_u1(ORC_LAT, const double *phi, double *psi)
     uint64_t D = Cb(&c, N, nd);
     const zdbl *p = (const zdbl *)phi;
     zdbl *q = (zdbl *)psi;
-#pragma omp parallel for schedule(dynamic, 256)
-    for (int64_t a = 1; a <= (int64_t)D; ++a) q[a - 1] = hphi_u1_row(&c, (uint64_t)a, p);
+    int64_t terms = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : terms)
+    for (int64_t a = 1; a <= (int64_t)D; ++a) q[a - 1] = hphi_u1_row(&c, (uint64_t)a, p, &terms);
     ctx_free(&c);
     return 0;
 }
 
-/* U(1) HPhi on a list of 0-based rows only (sampled parity / CPU timing) */
-int orc_hphi_u1_rows(ORC_LAT, const double *phi, int64_t nrows, const int64_t *rows, double *psi_rows)
+/* U(1) HPhi on a list of 0-based rows only (sampled parity / CPU timing);
+ * *nterms (may be NULL) receives the number of matrix terms applied */
+int orc_hphi_u1_rows(ORC_LAT, const double *phi, int64_t nrows, const int64_t *rows, double *psi_rows,
+                     int64_t *nterms)
 {
     orc_ctx c;
     if (ctx_init(&c, ORC_LAT_ARGS)) { ctx_free(&c); return -1; }
     const zdbl *p = (const zdbl *)phi;
     zdbl *q = (zdbl *)psi_rows;
-#pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t i = 0; i < nrows; ++i) q[i] = hphi_u1_row(&c, (uint64_t)rows[i] + 1, p);
+    int64_t terms = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : terms)
+    for (int64_t i = 0; i < nrows; ++i) q[i] = hphi_u1_row(&c, (uint64_t)rows[i] + 1, p, &terms);
+    if (nterms) *nterms = terms;
     ctx_free(&c);
     return 0;
 }
@@ -492,11 +499,12 @@ int orc_orbit(ORC_LAT, uint64_t a, uint64_t *out)
 
 /* one row of Alg. 9 (readings R1, R6) */
 static zdbl hphi_k_row(const orc_ctx *c, const int *K, const uint64_t *sigma, const double *Nak,
-                       int64_t d, int64_t row /*1-based*/, const zdbl *phi)
+                       int64_t d, int64_t row /*1-based*/, const zdbl *phi, int64_t *terms)
 {
     int n[ORC_MAXND], np[ORC_MAXND];
     f_bar(c, sigma[row - 1], n, NULL);
     zdbl acc = 0.0;
+    *terms += 1;
     for (int b = 0; b < c->nb; ++b) {
         int f, fp;
         int p = binary_search_int(c->r[b], n, 1, c->nd, &f);
@@ -514,6 +522,7 @@ static zdbl hphi_k_row(const orc_ctx *c, const int *K, const uint64_t *sigma, co
             if (found) {
                 zdbl ph = cexp(I * kdot(c, K, l));
                 acc += (c->jxy[b] / 2.0) * ph * sqrt(Nak[col - 1] / Nak[row - 1]) * phi[col - 1];
+                *terms += 1;
             }
         }
     }
@@ -537,21 +546,24 @@ int orc_hphi_k(ORC_LAT, const int *K, const uint64_t *sigma, const double *Nak, 
     if (ctx_init(&c, ORC_LAT_ARGS)) { ctx_free(&c); return -1; }
     const zdbl *p = (const zdbl *)phi;
     zdbl *q = (zdbl *)psi;
-#pragma omp parallel for schedule(dynamic, 64)
-    for (int64_t row = 1; row <= d; ++row) q[row - 1] = hphi_k_row(&c, K, sigma, Nak, d, row, p);
+    int64_t terms = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : terms)
+    for (int64_t row = 1; row <= d; ++row) q[row - 1] = hphi_k_row(&c, K, sigma, Nak, d, row, p, &terms);
     ctx_free(&c);
     return 0;
 }
 
 int orc_hphi_k_rows(ORC_LAT, const int *K, const uint64_t *sigma, const double *Nak, int64_t d,
-                    const double *phi, int64_t nrows, const int64_t *rows, double *psi_rows)
+                    const double *phi, int64_t nrows, const int64_t *rows, double *psi_rows, int64_t *nterms)
 {
     orc_ctx c;
     if (ctx_init(&c, ORC_LAT_ARGS)) { ctx_free(&c); return -1; }
     const zdbl *p = (const zdbl *)phi;
     zdbl *q = (zdbl *)psi_rows;
-#pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t i = 0; i < nrows; ++i) q[i] = hphi_k_row(&c, K, sigma, Nak, d, rows[i] + 1, p);
+    int64_t terms = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : terms)
+    for (int64_t i = 0; i < nrows; ++i) q[i] = hphi_k_row(&c, K, sigma, Nak, d, rows[i] + 1, p, &terms);
+    if (nterms) *nterms = terms;
     ctx_free(&c);
     return 0;
 }

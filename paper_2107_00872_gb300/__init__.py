@@ -55,10 +55,11 @@ class SolveOpts:
     """Fields of qs3_solve_opts with the paper's defaults (input_lancz / input_TRLan)."""
 
     def __init__(self, n_eig=1, n_keep=8, n_max=32, max_iter=10000, min_iter=20, check_every=5, eps=1e-14,
-                 precision="f64", use_graphs=True, seed=1, refine_tol=1e-9):
+                 precision="f64", use_graphs=True, seed=1, refine_tol=1e-9, res_tol=1e-12):
         self.n_eig, self.n_keep, self.n_max, self.max_iter = n_eig, n_keep, n_max, max_iter
         self.min_iter, self.check_every, self.eps = min_iter, check_every, eps
         self.precision, self.use_graphs, self.seed, self.refine_tol = precision, use_graphs, seed, refine_tol
+        self.res_tol = res_tol
 
     def c(self) -> _abi.qs3_solve_opts:
         o = _abi.qs3_solve_opts()
@@ -66,6 +67,7 @@ class SolveOpts:
         o.min_iter, o.check_every, o.eps = self.min_iter, self.check_every, self.eps
         o.precision = QS3_F32 if self.precision in ("f32", QS3_F32) else QS3_F64
         o.use_graphs, o.seed, o.refine_tol = int(bool(self.use_graphs)), int(self.seed), float(self.refine_tol)
+        o.res_tol = float(self.res_tol)
         return o
 
 

@@ -25,12 +25,13 @@ class qs3_lattice(ctypes.Structure):
 class qs3_solve_opts(ctypes.Structure):
     _fields_ = [("n_eig", I32), ("n_keep", I32), ("n_max", I32), ("max_iter", I32), ("min_iter", I32),
                 ("check_every", I32), ("eps", F64), ("precision", I32), ("use_graphs", I32), ("seed", U64),
-                ("refine_tol", F64)]
+                ("refine_tol", F64), ("res_tol", F64)]
 
 
 class qs3_solve_info(ctypes.Structure):
     _fields_ = [("iterations", I32), ("restarts", I32), ("converged", I32), ("refine_iterations", I32),
-                ("max_residual", F64), ("seconds", F64)]
+                ("max_residual", F64), ("seconds", F64), ("hphi_nnz", U64), ("hphi_seconds", F64),
+                ("hphi_calls", I32), ("pad_", I32)]
 
 
 # name -> (argtypes, restype); every entry point declared in include/qs3.h
@@ -50,6 +51,7 @@ SIGNATURES = {
     "qs3_strerror": ([I32], ctypes.c_char_p),
     "qs3_last_error": ([], ctypes.c_char_p),
     "qs3_version": ([], ctypes.c_char_p),
+    "qs3_kernel_launches": ([], U64),
 }
 
 _lib = None

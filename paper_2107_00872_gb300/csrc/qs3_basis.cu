@@ -16,6 +16,7 @@
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -39,6 +40,9 @@ int set_err(int code, const char *fmt, ...) {
 }
 
 void clear_err() { g_err[0] = 0; }
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 const char *last_err() { return g_err; }
 
@@ -208,7 +212,7 @@ static int build_reps_nd(Basis &B, int s) {
     int grid = (int)std::min<uint64_t>(want ? want : 1, (uint64_t)nsm * 8);
     k_enum_reps<ND><<<grid, NTHREADS, smem>>>(B.lv, K[0], K[1], K[2], nc, 0, cnt.as<unsigned long long>(),
                                               nullptr, nullptr);
-    QS3_CUDA(cudaGetLastError());
+    QS3_LAUNCHED();
     unsigned long long d = 0;
     QS3_CUDA(cudaMemcpy(&d, cnt.p, sizeof(d), cudaMemcpyDeviceToHost));
     if (d >= (1ull << 32)) return set_err(QS3_ERR_OVERFLOW, "sector dimension %llu exceeds 2^32", d);
@@ -218,7 +222,7 @@ static int build_reps_nd(Basis &B, int s) {
     QS3_CUDA(cudaMemset(cnt.p, 0, sizeof(unsigned long long)));
     k_enum_reps<ND><<<grid, NTHREADS, smem>>>(B.lv, K[0], K[1], K[2], nc, 1, cnt.as<unsigned long long>(),
                                               kin.as<uint64_t>(), vin.as<uint8_t>());
-    QS3_CUDA(cudaGetLastError());
+    QS3_LAUNCHED();
     QS3_TRY(kout.alloc(d * 8));
     QS3_TRY(vout.alloc(d));
     if (d > 0) {
@@ -242,11 +246,11 @@ static int build_reps_nd(Basis &B, int s) {
         QS3_CUDA(cudaFuncSetAttribute(k_prefix<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
         int g2 = (int)std::min<uint64_t>((d + 255) / 256, (uint64_t)nsm * 8);
         k_prefix<ND><<<g2, 256, sm2>>>(B.lv, kout.as<uint64_t>(), d, P.as<uint32_t>());
-        QS3_CUDA(cudaGetLastError());
+        QS3_LAUNCHED();
     }
     int g3 = (int)std::min<uint64_t>((np + 256) / 256, (uint64_t)nsm * 8);
     k_pidx<<<g3, 256>>>(P.as<uint32_t>(), d, np, pidx.as<uint32_t>());
-    QS3_CUDA(cudaGetLastError());
+    QS3_LAUNCHED();
     QS3_CUDA(cudaDeviceSynchronize());
     B.dims[s] = d;
     B.d_sigma[s] = std::move(kout);
@@ -456,14 +460,17 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     }
     B.offs.assign(nsec + 1, 0);
     B.tile0.assign(nsec + 1, 0);
+    B.chunk0.assign(nsec + 1, 0);
     for (int s = 0; s < nsec; ++s) {
         B.offs[s + 1] = B.offs[s] + B.dims[s];
         uint64_t nt = (B.dims[s] + TILE - 1) / TILE;
         if ((uint64_t)B.tile0[s] + nt > (1ull << 31) - 1) return set_err(QS3_ERR_OVERFLOW, "too many rows");
         B.tile0[s + 1] = B.tile0[s] + (int)nt;
+        B.chunk0[s + 1] = B.chunk0[s] + (int)((B.dims[s] + BROWS - 1) / BROWS);
     }
     B.total = B.offs[nsec];
     B.ntiles = B.tile0[nsec];
+    B.nchunks = B.chunk0[nsec];
     B.secs.resize(nsec);
     for (int s = 0; s < nsec; ++s) {
         SecView &v = B.secs[s];
@@ -477,6 +484,7 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     }
     QS3_TRY(B.d_secs.upload(B.secs.data(), B.secs.size() * sizeof(SecView)));
     QS3_TRY(B.d_tile0.upload(B.tile0.data(), B.tile0.size() * 4));
+    QS3_TRY(B.d_chunk0.upload(B.chunk0.data(), B.chunk0.size() * 4));
     B.smem_bytes = row_kernel_smem(B, 0);
     if (B.smem_bytes > 200 * 1024)
         return set_err(QS3_ERR_OVERFLOW, "lattice tables need %zu bytes of shared memory", B.smem_bytes);
@@ -541,11 +549,7 @@ int qs3_basis_ranks(qs3_basis_t b, int32_t s, uint64_t *ranks, uint8_t *stab) {
 int qs3_basis_nnz(qs3_basis_t b, uint64_t *nnz) {
     clear_err();
     if (!b || !nnz) return set_err(QS3_ERR_INVALID_ARG, "NULL argument");
-    if (!b->B.nnz_valid) {
-        QS3_TRY(count_nnz(b->B, &b->B.nnz));
-        b->B.nnz_valid = true;
-    }
-    *nnz = b->B.nnz;
+    QS3_TRY(count_nnz(b->B, nnz));
     return QS3_OK;
 }
 
@@ -567,5 +571,7 @@ const char *qs3_strerror(int status) {
 }
 
 const char *qs3_version(void) { return "qs3-gb300 0.1 (sm_103a)"; }
+
+uint64_t qs3_kernel_launches(void) { return qs3::g_launches.load(); }
 
 }  // extern "C"

@@ -95,7 +95,8 @@ __device__ __forceinline__ void fill_phases(const LatView &L, const int *K, CT *
 template <int ND, typename VT, bool KS>
 __global__ void __launch_bounds__(NTHREADS) k_hphi(LatView L, const SecView *__restrict__ secs,
                                                    const int *__restrict__ tile0, int S, int ntiles,
-                                                   const VT *__restrict__ phi, VT *__restrict__ psi) {
+                                                   const VT *__restrict__ phi, VT *__restrict__ psi,
+                                                   const int *__restrict__ active) {
     using R = typename VTr<VT>::R;
     using CT = typename VTr<VT>::C;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(NTHREADS) k_hphi(LatView L, const SecView *__r
     int cur = -1;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int s = (S == 1) ? 0 : sector_of_tile(tile0, S, t);
+        if (active && !active[s]) continue;
         const SecView sv = secs[s];
         if (KS && s != cur) {
             __syncthreads();
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(NTHREADS) k_hphi(LatView L, const SecView *__r
     }
 }
 
-// nnz count: the diagonal plus every hop that lands on a member of the sector
+// nnz count per sector: the diagonal plus every hop that lands on a member of the sector
 template <int ND, bool KS>
 __global__ void __launch_bounds__(NTHREADS) k_count(LatView L, const SecView *__restrict__ secs,
                                                     const int *__restrict__ tile0, int S, int ntiles,
@@ -187,41 +189,44 @@ __global__ void __launch_bounds__(NTHREADS) k_count(LatView L, const SecView *__
     SmemLayout sm = carve(L, smem);
     stage_tables(L, sm.sC, KS ? sm.sxyz : nullptr);
     __syncthreads();
-    unsigned long long cnt = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int s = (S == 1) ? 0 : sector_of_tile(tile0, S, t);
         const SecView sv = secs[s];
         const uint64_t row = (uint64_t)(t - sv.tile0) * TILE + threadIdx.x;
-        if (row >= sv.dim) continue;
-        const uint64_t rank = KS ? sv.sigma[row] : row;
-        int c[ND];
-        unrank(rank, sm.sC, L.np1, c);
-        cnt += 1;
+        unsigned long long cnt = 0;
+        if (row < sv.dim) {
+            const uint64_t rank = KS ? sv.sigma[row] : row;
+            int c[ND];
+            unrank(rank, sm.sC, L.np1, c);
+            cnt = 1;
 #pragma unroll
-        for (int m = 0; m < ND; ++m) {
-            const int i = c[m];
-            for (int q = L.adj_ptr[i]; q < L.adj_ptr[i + 1]; ++q) {
-                const int j = L.adj_nbr[q];
-                bool occ = false;
+            for (int m = 0; m < ND; ++m) {
+                const int i = c[m];
+                for (int q = L.adj_ptr[i]; q < L.adj_ptr[i + 1]; ++q) {
+                    const int j = L.adj_nbr[q];
+                    bool occ = false;
 #pragma unroll
-                for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
-                if (occ) continue;
-                if constexpr (!KS) { ++cnt; continue; } else {
-                int tt[ND];
+                    for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
+                    if (occ) continue;
+                    if constexpr (!KS) {
+                        ++cnt;
+                    } else {
+                        int tt[ND];
 #pragma unroll
-                for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
-                sort_net(tt);
-                int rep[ND];
-                int ax, by, cz;
-                const uint64_t r2 = canon(tt, L, sm.sxyz, sm.sC, rep, ax, by, cz);
-                uint32_t idx;
-                if (sigma_find(sv, prefix_of(rep, sm.sC, L.np1), r2, idx)) ++cnt;
+                        for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
+                        sort_net(tt);
+                        int rep[ND];
+                        int ax, by, cz;
+                        const uint64_t r2 = canon(tt, L, sm.sxyz, sm.sC, rep, ax, by, cz);
+                        uint32_t idx;
+                        if (sigma_find(sv, prefix_of(rep, sm.sC, L.np1), r2, idx)) ++cnt;
+                    }
                 }
             }
         }
+        for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out + s, cnt);
     }
-    for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
 }
 
 // N_down = 0: H is the constant c0 on the single vacuum state of each sector
@@ -263,7 +268,7 @@ static int launch_rows(KF kern, Basis &B, size_t smem, int &cached_blocks, cudaS
 }
 
 template <int ND, typename VT, bool KS>
-static int hphi_nd(Basis &B, const void *phi, void *psi, cudaStream_t st) {
+static int hphi_nd(Basis &B, const void *phi, void *psi, cudaStream_t st, const int *active) {
     static int cached = 0;
     static size_t cached_smem = 0;
     if (cached_smem != B.smem_bytes) { cached = 0; cached_smem = B.smem_bytes; }
@@ -271,27 +276,27 @@ static int hphi_nd(Basis &B, const void *phi, void *psi, cudaStream_t st) {
     QS3_TRY(launch_rows(k_hphi<ND, VT, KS>, B, B.smem_bytes, cached, st, &grid));
     if (B.ntiles == 0) return QS3_OK;
     k_hphi<ND, VT, KS><<<grid, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S,
-                                                              B.ntiles, (const VT *)phi, (VT *)psi);
-    QS3_CUDA(cudaGetLastError());
+                                                              B.ntiles, (const VT *)phi, (VT *)psi, active);
+    QS3_LAUNCHED();
     return QS3_OK;
 }
 
 template <typename VT, bool KS>
-static int hphi_vt(Basis &B, const void *phi, void *psi, cudaStream_t st) {
+static int hphi_vt(Basis &B, const void *phi, void *psi, cudaStream_t st, const int *a) {
     switch (B.nd) {
-        case 1: return hphi_nd<1, VT, KS>(B, phi, psi, st);
-        case 2: return hphi_nd<2, VT, KS>(B, phi, psi, st);
-        case 3: return hphi_nd<3, VT, KS>(B, phi, psi, st);
-        case 4: return hphi_nd<4, VT, KS>(B, phi, psi, st);
-        case 5: return hphi_nd<5, VT, KS>(B, phi, psi, st);
-        case 6: return hphi_nd<6, VT, KS>(B, phi, psi, st);
-        case 7: return hphi_nd<7, VT, KS>(B, phi, psi, st);
-        case 8: return hphi_nd<8, VT, KS>(B, phi, psi, st);
+        case 1: return hphi_nd<1, VT, KS>(B, phi, psi, st, a);
+        case 2: return hphi_nd<2, VT, KS>(B, phi, psi, st, a);
+        case 3: return hphi_nd<3, VT, KS>(B, phi, psi, st, a);
+        case 4: return hphi_nd<4, VT, KS>(B, phi, psi, st, a);
+        case 5: return hphi_nd<5, VT, KS>(B, phi, psi, st, a);
+        case 6: return hphi_nd<6, VT, KS>(B, phi, psi, st, a);
+        case 7: return hphi_nd<7, VT, KS>(B, phi, psi, st, a);
+        case 8: return hphi_nd<8, VT, KS>(B, phi, psi, st, a);
         default: return set_err(QS3_ERR_INVALID_ARG, "n_down %d", B.nd);
     }
 }
 
-int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t st) {
+int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t st, const int *active) {
     if (!phi || !psi) return set_err(QS3_ERR_INVALID_ARG, "NULL vector");
     if (phi == psi) return set_err(QS3_ERR_INVALID_ARG, "phi and psi alias");
     if (B.has_k && (dt == QS3_F32 || dt == QS3_F64))
@@ -306,17 +311,17 @@ int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t
             case QS3_C128: k_diag0<double2><<<grid, 256, 0, st>>>(B.lv.c0, B.total, (const double2 *)phi, (double2 *)psi); break;
             default: return set_err(QS3_ERR_INVALID_ARG, "dtype %d", (int)dt);
         }
-        QS3_CUDA(cudaGetLastError());
+        QS3_LAUNCHED();
         return QS3_OK;
     }
     if (B.has_k) {
-        if (dt == QS3_C64) return hphi_vt<float2, true>(B, phi, psi, st);
-        if (dt == QS3_C128) return hphi_vt<double2, true>(B, phi, psi, st);
+        if (dt == QS3_C64) return hphi_vt<float2, true>(B, phi, psi, st, active);
+        if (dt == QS3_C128) return hphi_vt<double2, true>(B, phi, psi, st, active);
     } else {
-        if (dt == QS3_F32) return hphi_vt<float, false>(B, phi, psi, st);
-        if (dt == QS3_F64) return hphi_vt<double, false>(B, phi, psi, st);
-        if (dt == QS3_C64) return hphi_vt<float2, false>(B, phi, psi, st);
-        if (dt == QS3_C128) return hphi_vt<double2, false>(B, phi, psi, st);
+        if (dt == QS3_F32) return hphi_vt<float, false>(B, phi, psi, st, active);
+        if (dt == QS3_F64) return hphi_vt<double, false>(B, phi, psi, st, active);
+        if (dt == QS3_C64) return hphi_vt<float2, false>(B, phi, psi, st, active);
+        if (dt == QS3_C128) return hphi_vt<double2, false>(B, phi, psi, st, active);
     }
     return set_err(QS3_ERR_INVALID_ARG, "dtype %d", (int)dt);
 }
@@ -330,7 +335,7 @@ static int count_nd(Basis &B, unsigned long long *d_out) {
     QS3_TRY(launch_rows(k_count<ND, KS>, B, B.smem_bytes, cached, 0, &grid));
     k_count<ND, KS><<<grid, NTHREADS, B.smem_bytes>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S,
                                                        B.ntiles, d_out);
-    QS3_CUDA(cudaGetLastError());
+    QS3_LAUNCHED();
     return QS3_OK;
 }
 
@@ -350,17 +355,23 @@ static int count_ks(Basis &B, unsigned long long *d_out) {
 }
 
 int count_nnz(Basis &B, uint64_t *nnz) {
-    if (B.nd == 0 || B.total == 0) {
-        *nnz = B.total;
-        return QS3_OK;
+    if (!B.nnz_valid) {
+        B.nnz_sec.assign(B.S, 0);
+        if (B.nd == 0 || B.total == 0) {
+            for (int s = 0; s < B.S; ++s) B.nnz_sec[s] = B.dims[s];
+        } else {
+            DevBuf d;
+            QS3_TRY(d.alloc(8 * (size_t)B.S));
+            QS3_CUDA(cudaMemset(d.p, 0, 8 * (size_t)B.S));
+            QS3_TRY(B.has_k ? count_ks<true>(B, d.as<unsigned long long>())
+                            : count_ks<false>(B, d.as<unsigned long long>()));
+            QS3_CUDA(cudaMemcpy(B.nnz_sec.data(), d.p, 8 * (size_t)B.S, cudaMemcpyDeviceToHost));
+        }
+        B.nnz = 0;
+        for (uint64_t v : B.nnz_sec) B.nnz += v;
+        B.nnz_valid = true;
     }
-    DevBuf d;
-    QS3_TRY(d.alloc(8));
-    QS3_CUDA(cudaMemset(d.p, 0, 8));
-    QS3_TRY(B.has_k ? count_ks<true>(B, d.as<unsigned long long>()) : count_ks<false>(B, d.as<unsigned long long>()));
-    unsigned long long v = 0;
-    QS3_CUDA(cudaMemcpy(&v, d.p, 8, cudaMemcpyDeviceToHost));
-    *nnz = v;
+    *nnz = B.nnz;
     return QS3_OK;
 }
 

@@ -15,6 +15,7 @@ namespace qs3 {
 constexpr int MAXND = QS3_MAX_NDOWN;
 constexpr int TILE = 256;          // rows per tile (one thread per row)
 constexpr int NTHREADS = 256;
+constexpr int BROWS = 2048;        // rows per chunk of the vector kernels (8 per thread)
 
 // ------------------------------------------------------------------ errors
 int set_err(int code, const char *fmt, ...);
@@ -27,6 +28,15 @@ void clear_err();
             return ::qs3::set_err(e_ == cudaErrorMemoryAllocation ? QS3_ERR_OOM : QS3_ERR_CUDA,   \
                                   "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,       \
                                   __LINE__);                                                       \
+    } while (0)
+
+// every kernel launch of the library is followed by QS3_LAUNCHED(): it counts
+// the launch (qs3_kernel_launches) and turns a launch error into a status
+void count_launch();
+#define QS3_LAUNCHED()                                                                             \
+    do {                                                                                           \
+        ::qs3::count_launch();                                                                     \
+        QS3_CUDA(cudaGetLastError());                                                              \
     } while (0)
 
 #define QS3_TRY(expr)                                                                              \
@@ -95,6 +105,8 @@ struct Basis {
     uint64_t total = 0;
     std::vector<int> tile0;                 // S + 1
     int ntiles = 0;
+    std::vector<int> chunk0;                // S + 1, chunks of BROWS rows (vector kernels)
+    int nchunks = 0;
     // host copies of the model
     std::vector<int> bi, bj;
     std::vector<double> jxy, jz, h, pos;
@@ -102,10 +114,11 @@ struct Basis {
     // device data
     DevBuf d_binom, d_adj_ptr, d_adj_nbr, d_adj_jxy, d_adj_jz, d_adj_jxy_f, d_u, d_xyz;
     std::vector<DevBuf> d_sigma, d_stab, d_pidx;
-    DevBuf d_secs, d_tile0;
+    DevBuf d_secs, d_tile0, d_chunk0;
     LatView lv{};
     std::vector<SecView> secs;
-    uint64_t nnz = 0;
+    uint64_t nnz = 0;                       // structural non-zeros (count_nnz), total and per sector
+    std::vector<uint64_t> nnz_sec;
     bool nnz_valid = false;
     size_t smem_bytes = 0;                  // dynamic shared memory of the row kernels
 };
@@ -292,7 +305,8 @@ size_t row_kernel_smem(const Basis &B, int extra_nd);
 
 // -------------------------------------------------------------- entry points
 // implemented in qs3_hphi.cu
-int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t st);
+int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t st,
+                const int *active = nullptr);
 int count_nnz(Basis &B, uint64_t *nnz);
 // implemented in qs3_basis.cu
 int build_sector_reps(Basis &B, int s);

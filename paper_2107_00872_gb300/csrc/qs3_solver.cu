@@ -1,9 +1,1217 @@
-// qs3_solver.cu -- Lanczos / thick-restart Lanczos (placeholder entry points)
+// qs3_solver.cu -- conventional Lanczos and thick-restart Lanczos (Alg. 10),
+// batched over the sectors of a basis.
+//
+// All sectors advance in lock step on one concatenated vector: every kernel
+// covers all sectors in one launch, reductions are per sector (fixed-order
+// two-stage trees, so results are deterministic), and a per-sector active
+// flag removes converged sectors from every launch.  The Lanczos vectors
+// Psi live in one device array (vector j at offset j * total_dim).
+//
+// One Lanczos step (Alg. 10 lines 5-11) for x: v = H psi_x is written into
+// psi_{x+1}; classical Gram-Schmidt run twice against psi_0..psi_x (the
+// reorthogonalisation; its first pass yields alpha_x = psi_x^dag v and the
+// three-term coefficients); beta_x = |v|; psi_{x+1} = v / beta_x.  Dot
+// products, norms and the Gram-Schmidt coefficients are fp64 even when the
+// vectors are fp32.  The small tridiagonal / arrowhead matrices T are
+// diagonalised on the host (Sturm bisection + inverse iteration for
+// tridiagonal T, cyclic Jacobi for the arrowhead T of the thick restart).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
 #include "qs3_internal.cuh"
 
-extern "C" int qs3_lanczos(qs3_basis_t, const qs3_solve_opts *, double *, void *, qs3_solve_info *, void *) {
-    return qs3::set_err(QS3_ERR_STATE, "not built yet");
+namespace qs3 {
+
+// ------------------------------------------------------------ element access
+__device__ __forceinline__ double2 ld2(const float *p) { return make_double2((double)*p, 0.0); }
+__device__ __forceinline__ double2 ld2(const double *p) { return make_double2(*p, 0.0); }
+__device__ __forceinline__ double2 ld2(const float2 *p) { float2 v = *p; return make_double2(v.x, v.y); }
+__device__ __forceinline__ double2 ld2(const double2 *p) { return *p; }
+__device__ __forceinline__ void st2(float *p, double2 v) { *p = (float)v.x; }
+__device__ __forceinline__ void st2(double *p, double2 v) { *p = v.x; }
+__device__ __forceinline__ void st2(float2 *p, double2 v) { *p = make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ void st2(double2 *p, double2 v) { *p = v; }
+// conj(a) * b
+__device__ __forceinline__ double2 cdot(double2 a, double2 b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
-extern "C" int qs3_trlanczos(qs3_basis_t, const qs3_solve_opts *, double *, void *, qs3_solve_info *, void *) {
-    return qs3::set_err(QS3_ERR_STATE, "not built yet");
+__device__ __forceinline__ double2 cmad(double2 acc, double2 a, double2 b) {   // acc + a * b
+    return make_double2(acc.x + a.x * b.x - a.y * b.y, acc.y + a.x * b.y + a.y * b.x);
 }
+
+template <typename VT> struct Is64 { static constexpr bool v = false; };
+template <> struct Is64<double> { static constexpr bool v = true; };
+template <> struct Is64<double2> { static constexpr bool v = true; };
+template <typename VT> struct IsC { static constexpr bool v = false; };
+template <> struct IsC<float2> { static constexpr bool v = true; };
+template <> struct IsC<double2> { static constexpr bool v = true; };
+template <typename VT> struct Wide { using T = double; };
+template <> struct Wide<float2> { using T = double2; };
+template <> struct Wide<double2> { using T = double2; };
+
+struct ChunkInfo {
+    int s;
+    uint64_t base;   // first row of the chunk in the concatenated vector
+    int n;           // rows in the chunk
+};
+
+__device__ __forceinline__ ChunkInfo chunk_info(const SecView *secs, const int *chunk0, int S, int c) {
+    ChunkInfo ci;
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (chunk0[mid] <= c) lo = mid; else hi = mid - 1;
+    }
+    ci.s = lo;
+    const uint64_t r0 = (uint64_t)(c - chunk0[lo]) * BROWS;
+    ci.base = secs[lo].off + r0;
+    const uint64_t rem = secs[lo].dim - r0;
+    ci.n = (int)(rem < (uint64_t)BROWS ? rem : (uint64_t)BROWS);
+    return ci;
+}
+
+constexpr int RPT = BROWS / NTHREADS;   // rows per thread
+constexpr int JB = 32;                  // dot products per reduction batch
+
+__device__ __forceinline__ double2 warp_sum2(double2 v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+// part[c * m + j] = sum over the chunk's rows of conj(V_{j0+j}) w
+template <typename VT>
+__global__ void __launch_bounds__(NTHREADS) k_mdot(const VT *__restrict__ V, uint64_t D, int j0, int m,
+                                                   const VT *__restrict__ w, const SecView *__restrict__ secs,
+                                                   const int *__restrict__ chunk0, int S,
+                                                   const int *__restrict__ active, double2 *__restrict__ part) {
+    __shared__ double2 red[NTHREADS / 32][JB];
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    double2 wv[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        wv[k] = (r < ci.n) ? ld2(w + ci.base + r) : make_double2(0.0, 0.0);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int jb = 0; jb < m; jb += JB) {
+        const int nj = min(JB, m - jb);
+        for (int jj = 0; jj < nj; ++jj) {
+            const VT *vj = V + (uint64_t)(j0 + jb + jj) * D + ci.base;
+            double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int r = threadIdx.x + k * NTHREADS;
+                if (r < ci.n) {
+                    const double2 a = ld2(vj + r), d = cdot(a, wv[k]);
+                    acc.x += d.x;
+                    acc.y += d.y;
+                }
+            }
+            acc = warp_sum2(acc);
+            if (lane == 0) red[warp][jj] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x < nj) {
+            double2 t = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int q = 0; q < NTHREADS / 32; ++q) { t.x += red[q][threadIdx.x].x; t.y += red[q][threadIdx.x].y; }
+            part[(uint64_t)blockIdx.x * m + jb + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// out[s * ldo + j] = sum of part[c * m + j] over the chunks of sector s (one block per (j, s))
+__global__ void k_reduce(const double2 *__restrict__ part, int m, const int *__restrict__ chunk0,
+                         const int *__restrict__ active, double2 *__restrict__ out, int ldo) {
+    const int j = blockIdx.x, s = blockIdx.y;
+    if (active && !active[s]) return;
+    __shared__ double2 red[NTHREADS / 32];
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = chunk0[s] + threadIdx.x; c < chunk0[s + 1]; c += blockDim.x) {
+        double2 v = part[(uint64_t)c * m + j];
+        acc.x += v.x;
+        acc.y += v.y;
+    }
+    acc = warp_sum2(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int q = 0; q < NTHREADS / 32; ++q) { t.x += red[q].x; t.y += red[q].y; }
+        out[(uint64_t)s * ldo + j] = t;
+    }
+}
+
+// w -= sum_j V_{j0+j} coef[s][j]; optionally part[c] = sum |w|^2 over the chunk
+template <typename VT>
+__global__ void __launch_bounds__(NTHREADS) k_mupdate(VT *__restrict__ w, const VT *__restrict__ V, uint64_t D,
+                                                      int j0, int m, const double2 *__restrict__ coef, int ldc,
+                                                      const SecView *__restrict__ secs,
+                                                      const int *__restrict__ chunk0, int S,
+                                                      const int *__restrict__ active, double2 *__restrict__ part) {
+    extern __shared__ double2 sco[];
+    __shared__ double red[NTHREADS / 32];
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) sco[j] = coef[(uint64_t)ci.s * ldc + j];
+    __syncthreads();
+    double nrm = 0.0;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r < ci.n) {
+            double2 acc = ld2(w + ci.base + r);
+            const VT *vp = V + (uint64_t)j0 * D + ci.base + r;
+            for (int j = 0; j < m; ++j) {
+                const double2 a = ld2(vp + (uint64_t)j * D), c = sco[j];
+                acc.x -= a.x * c.x - a.y * c.y;
+                acc.y -= a.x * c.y + a.y * c.x;
+            }
+            st2(w + ci.base + r, acc);
+            const double2 q = ld2(w + ci.base + r);   // norm of the stored (rounded) value
+            nrm += q.x * q.x + q.y * q.y;
+        }
+    }
+    if (part) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < NTHREADS / 32; ++q) t += red[q];
+            part[blockIdx.x] = make_double2(t, 0.0);
+        }
+    }
+}
+
+// per-sector scalars after a step: alpha_x, beta_x (with breakdown), 1/beta
+__global__ void k_step_scalars(int S, int x, int cap, const double2 *__restrict__ h, const double2 *__restrict__ nrm2,
+                               const int *__restrict__ active, double *__restrict__ alpha, double *__restrict__ beta,
+                               double *__restrict__ inv, double brk) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S || (active && !active[s])) return;
+    const double a = h[(uint64_t)s * cap + x].x;
+    double b = sqrt(fmax(nrm2[s].x, 0.0));
+    const double bprev = x > 0 ? beta[(uint64_t)s * cap + x - 1] : 0.0;
+    if (!(b > brk * (fabs(a) + bprev)) || !isfinite(b)) b = 0.0;      // invariant subspace reached
+    alpha[(uint64_t)s * cap + x] = a;
+    beta[(uint64_t)s * cap + x] = b;
+    inv[s] = b > 0.0 ? 1.0 / b : 0.0;
+}
+
+// w *= inv[s] (per sector)
+template <typename VT>
+__global__ void __launch_bounds__(NTHREADS) k_scale(VT *__restrict__ w, const double *__restrict__ inv,
+                                                    const SecView *__restrict__ secs, const int *__restrict__ chunk0,
+                                                    int S, const int *__restrict__ active) {
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    const double f = inv[ci.s];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r < ci.n) {
+            double2 v = ld2(w + ci.base + r);
+            v.x *= f;
+            v.y *= f;
+            st2(w + ci.base + r, v);
+        }
+    }
+}
+
+// sum |w|^2 per chunk
+template <typename VT>
+__global__ void __launch_bounds__(NTHREADS) k_norm2(const VT *__restrict__ w, const SecView *__restrict__ secs,
+                                                    const int *__restrict__ chunk0, int S,
+                                                    const int *__restrict__ active, double2 *__restrict__ part) {
+    __shared__ double red[NTHREADS / 32];
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    double nrm = 0.0;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r < ci.n) {
+            const double2 q = ld2(w + ci.base + r);
+            nrm += q.x * q.x + q.y * q.y;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < NTHREADS / 32; ++q) t += red[q];
+        part[blockIdx.x] = make_double2(t, 0.0);
+    }
+}
+
+__global__ void k_inv_sqrt(int S, const double2 *__restrict__ n2, double *__restrict__ inv) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) inv[s] = n2[s].x > 0.0 ? 1.0 / sqrt(n2[s].x) : 0.0;
+}
+
+// SplitMix64 output function (Steele, Lea, Flood 2014)
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Box-Muller normal from counters 2i, 2i+1 of the stream seeded by `seed`
+__device__ __forceinline__ double gauss(uint64_t seed, uint64_t i) {
+    const double u1 = ((double)(splitmix64(seed ^ (2 * i)) >> 11) + 1.0) * 0x1.0p-53;
+    const double u2 = ((double)(splitmix64(seed ^ (2 * i + 1)) >> 11) + 1.0) * 0x1.0p-53;
+    return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// start vector of sector s: seed + s, element i (imaginary part from counters offset by dim)
+template <typename VT>
+__global__ void __launch_bounds__(NTHREADS) k_random(VT *__restrict__ w, uint64_t seed,
+                                                     const SecView *__restrict__ secs,
+                                                     const int *__restrict__ chunk0, int S) {
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    const uint64_t sseed = seed + (uint64_t)ci.s;
+    const uint64_t r0 = ci.base - secs[ci.s].off;
+    const uint64_t d = secs[ci.s].dim;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r < ci.n) {
+            const uint64_t i = r0 + r;
+            double2 v = make_double2(gauss(sseed, i), 0.0);
+            if (IsC<VT>::v) v.y = gauss(sseed, d + i);
+            st2(w + ci.base + r, v);
+        }
+    }
+}
+
+// dst = (VT) src for the rows of active sectors
+template <typename VT, typename ST>
+__global__ void __launch_bounds__(NTHREADS) k_convert(VT *__restrict__ dst, const ST *__restrict__ src,
+                                                      const SecView *__restrict__ secs,
+                                                      const int *__restrict__ chunk0, int S,
+                                                      const int *__restrict__ active) {
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r < ci.n) st2(dst + ci.base + r, ld2(src + ci.base + r));
+    }
+}
+
+// out_y[r] = sum_x V_x[r] C[s][x][y] (y < nout <= 16), rows of sectors with mask[s] != 0
+constexpr int MAXOUT = 16;
+template <typename VT, typename OT>
+__global__ void __launch_bounds__(NTHREADS) k_combine(OT *__restrict__ out, uint64_t ldo, const VT *__restrict__ V,
+                                                      uint64_t D, int nin, int nout, const double *__restrict__ C,
+                                                      int ldc, const SecView *__restrict__ secs,
+                                                      const int *__restrict__ chunk0, int S,
+                                                      const int *__restrict__ mask) {
+    extern __shared__ double sc[];
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (mask && !mask[ci.s]) return;
+    const double *Cs = C + (uint64_t)ci.s * ldc;
+    for (int i = threadIdx.x; i < nin * nout; i += blockDim.x) sc[i] = Cs[i];
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r >= ci.n) continue;
+        double2 acc[MAXOUT];
+#pragma unroll
+        for (int y = 0; y < MAXOUT; ++y) acc[y] = make_double2(0.0, 0.0);
+        for (int x = 0; x < nin; ++x) {
+            const double2 a = ld2(V + (uint64_t)x * D + ci.base + r);
+#pragma unroll
+            for (int y = 0; y < MAXOUT; ++y)
+                if (y < nout) {
+                    const double c = sc[x * nout + y];
+                    acc[y].x += a.x * c;
+                    acc[y].y += a.y * c;
+                }
+        }
+#pragma unroll
+        for (int y = 0; y < MAXOUT; ++y)
+            if (y < nout) st2(out + (uint64_t)y * ldo + ci.base + r, acc[y]);
+    }
+}
+
+// part[c] = sum |t - e_s v|^2 (residual of an eigenpair)
+template <typename WT>
+__global__ void __launch_bounds__(NTHREADS) k_resid(const WT *__restrict__ t, const WT *__restrict__ v,
+                                                    const double *__restrict__ e, const SecView *__restrict__ secs,
+                                                    const int *__restrict__ chunk0, int S, double2 *__restrict__ part) {
+    __shared__ double red[NTHREADS / 32];
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    const double es = e[ci.s];
+    double acc = 0.0;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r < ci.n) {
+            const double2 a = ld2(t + ci.base + r), b = ld2(v + ci.base + r);
+            const double dx = a.x - es * b.x, dy = a.y - es * b.y;
+            acc += dx * dx + dy * dy;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < NTHREADS / 32; ++q) s += red[q];
+        part[blockIdx.x] = make_double2(s, 0.0);
+    }
+}
+
+// ----------------------------------------------------- small host eigensolvers
+
+// number of eigenvalues of the symmetric tridiagonal (a, b) below x (Sturm count)
+static int sturm_count(int n, const double *a, const double *b, double x) {
+    int cnt = 0;
+    double q = 1.0;
+    for (int i = 0; i < n; ++i) {
+        const double bb = i ? b[i - 1] * b[i - 1] : 0.0;
+        q = a[i] - x - (i ? bb / q : 0.0);
+        if (q == 0.0) q = -1e-300;
+        if (q < 0) ++cnt;
+    }
+    return cnt;
+}
+
+// k-th smallest eigenvalue (0-based) of the tridiagonal by bisection
+static double tri_eig_k(int n, const double *a, const double *b, int k) {
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < n; ++i) {
+        const double r = (i ? std::fabs(b[i - 1]) : 0.0) + (i < n - 1 ? std::fabs(b[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    const double w = std::max(hi - lo, 1e-300);
+    lo -= 1e-3 * w;
+    hi += 1e-3 * w;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (sturm_count(n, a, b, mid) > k) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// eigenvector of the tridiagonal for eigenvalue e by inverse iteration
+// (Gaussian elimination with partial pivoting on T - e I)
+static void tri_eigvec(int n, const double *a, const double *b, double e, std::vector<double> &v) {
+    v.assign(n, 1.0);
+    if (n == 1) return;
+    double scale = 0.0;
+    for (int i = 0; i < n; ++i) scale = std::max(scale, std::fabs(a[i]) + (i < n - 1 ? std::fabs(b[i]) : 0.0));
+    const double pert = std::max(scale, 1e-300) * 1e-14;
+    std::vector<double> d(n), du(n), du2(n), dl(n), x(n);
+    std::vector<int> piv(n);
+    for (int it = 0; it < 3; ++it) {
+        for (int i = 0; i < n; ++i) { d[i] = a[i] - e - pert; du[i] = i < n - 1 ? b[i] : 0.0; dl[i] = i < n - 1 ? b[i] : 0.0; du2[i] = 0.0; }
+        // LU with partial pivoting of the tridiagonal (LAPACK gttrf-style layout, own code)
+        for (int i = 0; i < n - 1; ++i) {
+            if (std::fabs(d[i]) >= std::fabs(dl[i])) {
+                piv[i] = 0;
+                if (d[i] == 0.0) d[i] = 1e-300;
+                const double f = dl[i] / d[i];
+                dl[i] = f;
+                d[i + 1] -= f * du[i];
+            } else {
+                piv[i] = 1;
+                const double f = d[i] / dl[i];
+                d[i] = dl[i];
+                dl[i] = f;
+                const double t = du[i];
+                du[i] = d[i + 1];
+                d[i + 1] = t - f * d[i + 1];
+                if (i < n - 2) { du2[i] = du[i + 1]; du[i + 1] = -f * du[i + 1]; }
+            }
+        }
+        if (d[n - 1] == 0.0) d[n - 1] = 1e-300;
+        // solve L U x = v
+        x = v;
+        for (int i = 0; i < n - 1; ++i) {
+            if (piv[i] == 0) x[i + 1] -= dl[i] * x[i];
+            else { const double t = x[i]; x[i] = x[i + 1]; x[i + 1] = t - dl[i] * x[i + 1]; }
+        }
+        x[n - 1] /= d[n - 1];
+        if (n > 1) x[n - 2] = (x[n - 2] - du[n - 2] * x[n - 1]) / d[n - 2];
+        for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) / d[i];
+        double nr = 0.0;
+        for (double t : x) nr += t * t;
+        nr = std::sqrt(nr);
+        if (!(nr > 0) || !std::isfinite(nr)) break;
+        for (int i = 0; i < n; ++i) v[i] = x[i] / nr;
+    }
+    // sign convention: largest component positive
+    int im = 0;
+    for (int i = 1; i < n; ++i) if (std::fabs(v[i]) > std::fabs(v[im])) im = i;
+    if (v[im] < 0) for (double &t : v) t = -t;
+}
+
+// cyclic Jacobi for a dense symmetric n x n matrix (row-major A, destroyed);
+// eigenvalues ascending in w, eigenvectors in the columns of Z (row-major)
+static void jacobi_eig(int n, std::vector<double> &A, std::vector<double> &w, std::vector<double> &Z) {
+    Z.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Z[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const double v = A[(size_t)i * n + j] * A[(size_t)i * n + j];
+                tot += v;
+                if (i != j) off += v;
+            }
+        if (off <= 1e-32 * tot || off == 0.0) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {       // A <- A J (columns p, q)
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - s * akq;
+                    A[(size_t)k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {       // A <- J^T A (rows p, q)
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - s * aqk;
+                    A[(size_t)q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {       // Z <- Z J
+                    const double zkp = Z[(size_t)k * n + p], zkq = Z[(size_t)k * n + q];
+                    Z[(size_t)k * n + p] = c * zkp - s * zkq;
+                    Z[(size_t)k * n + q] = s * zkp + c * zkq;
+                }
+            }
+    }
+    std::vector<int> ord(n);
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int x, int y) { return A[(size_t)x * n + x] < A[(size_t)y * n + y]; });
+    w.resize(n);
+    std::vector<double> Z2((size_t)n * n);
+    for (int j = 0; j < n; ++j) {
+        w[j] = A[(size_t)ord[j] * n + ord[j]];
+        for (int i = 0; i < n; ++i) Z2[(size_t)i * n + j] = Z[(size_t)i * n + ord[j]];
+    }
+    Z.swap(Z2);
+}
+
+// ------------------------------------------------------------------- engine
+
+// QS3_LOG=1 in the environment prints one line per convergence check to stderr
+static bool log_on() {
+    static int v = -1;
+    if (v < 0) { const char *e = getenv("QS3_LOG"); v = (e && *e && *e != '0') ? 1 : 0; }
+    return v == 1;
+}
+
+// H Phi work and device time of a solve: CUDA events around every H Phi
+// launch on the solve's stream, read back at the solver's sync points
+struct HphiStats {
+    uint64_t nnz = 0;
+    double sec = 0.0;
+    int calls = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend, freel;
+    ~HphiStats() {
+        for (auto &p : pend) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+        for (auto &p : freel) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+    }
+    int pair(std::pair<cudaEvent_t, cudaEvent_t> &p) {
+        if (!freel.empty()) { p = freel.back(); freel.pop_back(); return QS3_OK; }
+        QS3_CUDA(cudaEventCreate(&p.first));
+        QS3_CUDA(cudaEventCreate(&p.second));
+        return QS3_OK;
+    }
+    // call after the stream has been synchronised
+    int harvest() {
+        for (auto &p : pend) {
+            float ms = 0.f;
+            QS3_CUDA(cudaEventElapsedTime(&ms, p.first, p.second));
+            sec += 1e-3 * ms;
+            freel.push_back(p);
+        }
+        pend.clear();
+        return QS3_OK;
+    }
+};
+
+template <typename VT>
+struct Engine {
+    using WT = typename Wide<VT>::T;       // fp64 vector type of the same kind
+    Basis &B;
+    cudaStream_t st;
+    HphiStats *stats;
+    int cap = 0, nscr = 0;
+    uint64_t D = 0;
+    DevBuf V, part, h1, h2, alpha, beta, nrm, inv, active;
+    std::vector<int> h_active;
+    double brk;
+
+    Engine(Basis &b, cudaStream_t s, HphiStats *hs) : B(b), st(s), stats(hs) { brk = Is64<VT>::v ? 1e-12 : 1e-6; }
+
+    qs3_dtype dtype() const {
+        if (sizeof(VT) == 4) return QS3_F32;
+        if (sizeof(VT) == 8) return Is64<VT>::v ? QS3_F64 : QS3_C64;
+        return QS3_C128;
+    }
+    VT *vec(int j) { return V.as<VT>() + (uint64_t)j * D; }
+    const SecView *secs() { return B.d_secs.as<SecView>(); }
+    const int *c0() { return B.d_chunk0.as<int>(); }
+    int *act() { return active.as<int>(); }
+
+    int init(int cap_, int nscratch) {
+        cap = cap_;
+        nscr = nscratch;
+        D = B.total;
+        QS3_TRY(V.alloc((uint64_t)(cap + nscr) * D * sizeof(VT)));
+        QS3_TRY(part.alloc((uint64_t)std::max(B.nchunks, 1) * cap * sizeof(double2)));
+        QS3_TRY(h1.alloc((uint64_t)B.S * cap * sizeof(double2)));
+        QS3_TRY(h2.alloc((uint64_t)B.S * cap * sizeof(double2)));
+        QS3_TRY(alpha.alloc((uint64_t)B.S * cap * sizeof(double)));
+        QS3_TRY(beta.alloc((uint64_t)B.S * cap * sizeof(double)));
+        QS3_TRY(nrm.alloc((uint64_t)B.S * sizeof(double2)));
+        QS3_TRY(inv.alloc((uint64_t)B.S * sizeof(double)));
+        QS3_TRY(active.alloc((uint64_t)B.S * sizeof(int)));
+        QS3_CUDA(cudaMemsetAsync(alpha.p, 0, alpha.n, st));
+        QS3_CUDA(cudaMemsetAsync(beta.p, 0, beta.n, st));
+        h_active.assign(B.S, 0);
+        for (int s = 0; s < B.S; ++s) h_active[s] = B.dims[s] > 0;
+        return push_active();
+    }
+    int push_active() {
+        QS3_CUDA(cudaMemcpyAsync(active.p, h_active.data(), B.S * sizeof(int), cudaMemcpyHostToDevice, st));
+        return QS3_OK;
+    }
+    bool any_active() const {
+        for (int a : h_active) if (a) return true;
+        return false;
+    }
+    int grid() const { return std::max(B.nchunks, 1); }
+
+    // reduce part[.. m] into out (S x ldo)
+    int reduce(int m, double2 *out, int ldo) {
+        dim3 g(m, B.S);
+        k_reduce<<<g, NTHREADS, 0, st>>>(part.as<double2>(), m, c0(), act(), out, ldo);
+        QS3_LAUNCHED();
+        return QS3_OK;
+    }
+    int mdot(int j0, int m, const VT *w, double2 *out, int ldo) {
+        if (B.nchunks == 0) return QS3_OK;
+        k_mdot<VT><<<grid(), NTHREADS, 0, st>>>(V.as<VT>(), D, j0, m, w, secs(), c0(), B.S, act(), part.as<double2>());
+        QS3_LAUNCHED();
+        return reduce(m, out, ldo);
+    }
+    int mupdate(VT *w, int j0, int m, const double2 *cf, int ldc, bool norm) {
+        if (B.nchunks == 0) return QS3_OK;
+        k_mupdate<VT><<<grid(), NTHREADS, m * sizeof(double2), st>>>(w, V.as<VT>(), D, j0, m, cf, ldc, secs(), c0(), B.S,
+                                                                     act(), norm ? part.as<double2>() : nullptr);
+        QS3_LAUNCHED();
+        if (norm) return reduce(1, nrm.as<double2>(), 1);
+        return QS3_OK;
+    }
+    // normalise vector j per sector
+    int normalise(int j) {
+        if (B.nchunks == 0) return QS3_OK;
+        k_norm2<VT><<<grid(), NTHREADS, 0, st>>>(vec(j), secs(), c0(), B.S, act(), part.as<double2>());
+        QS3_LAUNCHED();
+        QS3_TRY(reduce(1, nrm.as<double2>(), 1));
+        k_inv_sqrt<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, nrm.as<double2>(), inv.as<double>());
+        QS3_LAUNCHED();
+        k_scale<VT><<<grid(), NTHREADS, 0, st>>>(vec(j), inv.as<double>(), secs(), c0(), B.S, act());
+        QS3_LAUNCHED();
+        return QS3_OK;
+    }
+    int start_random(uint64_t seed) {
+        if (B.nchunks == 0) return QS3_OK;
+        k_random<VT><<<grid(), NTHREADS, 0, st>>>(vec(0), seed, secs(), c0(), B.S);
+        QS3_LAUNCHED();
+        return normalise(0);
+    }
+    int start_from(const WT *src) {
+        if (B.nchunks == 0) return QS3_OK;
+        k_convert<VT, WT><<<grid(), NTHREADS, 0, st>>>(vec(0), src, secs(), c0(), B.S, nullptr);
+        QS3_LAUNCHED();
+        return normalise(0);
+    }
+    // Alg. 10 lines 5-11 for step x: psi_{x+1} from H psi_x
+    int step(int x) {
+        VT *w = vec(x + 1);
+        std::pair<cudaEvent_t, cudaEvent_t> ev;
+        QS3_TRY(stats->pair(ev));
+        QS3_CUDA(cudaEventRecord(ev.first, st));
+        QS3_TRY(hphi_launch(B, dtype(), vec(x), w, st, act()));
+        QS3_CUDA(cudaEventRecord(ev.second, st));
+        stats->pend.push_back(ev);
+        stats->calls += 1;
+        for (int s = 0; s < B.S; ++s)
+            if (h_active[s]) stats->nnz += B.nnz_sec[s];
+        QS3_TRY(mdot(0, x + 1, w, h1.as<double2>(), cap));
+        QS3_TRY(mupdate(w, 0, x + 1, h1.as<double2>(), cap, false));
+        QS3_TRY(mdot(0, x + 1, w, h2.as<double2>(), cap));
+        QS3_TRY(mupdate(w, 0, x + 1, h2.as<double2>(), cap, true));
+        k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, x, cap, h1.as<double2>(), nrm.as<double2>(), act(),
+                                                         alpha.as<double>(), beta.as<double>(), inv.as<double>(), brk);
+        QS3_LAUNCHED();
+        if (B.nchunks) {
+            k_scale<VT><<<grid(), NTHREADS, 0, st>>>(w, inv.as<double>(), secs(), c0(), B.S, act());
+            QS3_LAUNCHED();
+        }
+        return QS3_OK;
+    }
+    int fetch(std::vector<double> &a, std::vector<double> &b) {
+        a.resize((size_t)B.S * cap);
+        b.resize((size_t)B.S * cap);
+        QS3_CUDA(cudaMemcpyAsync(a.data(), alpha.p, a.size() * 8, cudaMemcpyDeviceToHost, st));
+        QS3_CUDA(cudaMemcpyAsync(b.data(), beta.p, b.size() * 8, cudaMemcpyDeviceToHost, st));
+        QS3_CUDA(cudaStreamSynchronize(st));
+        return stats->harvest();
+    }
+    // out_y = sum_x psi_x C[s][x][y] for sectors with mask; C host, S x (nin*nout)
+    template <typename OT>
+    int combine(OT *out, uint64_t ldo, int nin, int nout, const std::vector<double> &C, const std::vector<int> &mask) {
+        if (B.nchunks == 0) return QS3_OK;
+        if (nout > MAXOUT) return set_err(QS3_ERR_INVALID_ARG, "at most %d vectors per combination", MAXOUT);
+        const int ldc = nin * nout;
+        DevBuf dC, dm;
+        QS3_TRY(dC.alloc(C.size() * 8));
+        QS3_TRY(dm.alloc(mask.size() * 4));
+        QS3_CUDA(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, st));
+        QS3_CUDA(cudaMemcpyAsync(dm.p, mask.data(), mask.size() * 4, cudaMemcpyHostToDevice, st));
+        k_combine<VT, OT><<<grid(), NTHREADS, ldc * sizeof(double), st>>>(out, ldo, V.as<VT>(), D, nin, nout,
+                                                                          dC.as<double>(), ldc, secs(), c0(), B.S,
+                                                                          dm.as<int>());
+        QS3_LAUNCHED();
+        QS3_CUDA(cudaStreamSynchronize(st));     // dC/dm are released on return
+        return QS3_OK;
+    }
+};
+
+// residual |H v - e v| of fp64 vectors (one per sector, concatenated); returns max over sectors
+template <typename WT>
+static int residuals(Basis &B, const WT *v, const std::vector<double> &e, cudaStream_t st, double &rmax,
+                     std::vector<double> *per = nullptr) {
+    rmax = 0.0;
+    if (B.nchunks == 0) return QS3_OK;
+    DevBuf t, de, part, out;
+    QS3_TRY(t.alloc(B.total * sizeof(WT)));
+    QS3_TRY(de.alloc(B.S * 8));
+    QS3_TRY(part.alloc((uint64_t)B.nchunks * sizeof(double2)));
+    QS3_TRY(out.alloc(B.S * sizeof(double2)));
+    QS3_CUDA(cudaMemcpyAsync(de.p, e.data(), B.S * 8, cudaMemcpyHostToDevice, st));
+    const qs3_dtype dt = sizeof(WT) == 8 ? QS3_F64 : QS3_C128;
+    QS3_TRY(hphi_launch(B, dt, v, t.p, st, nullptr));
+    k_resid<WT><<<B.nchunks, NTHREADS, 0, st>>>(t.as<WT>(), v, de.as<double>(), B.d_secs.as<SecView>(),
+                                                B.d_chunk0.as<int>(), B.S, part.as<double2>());
+    QS3_LAUNCHED();
+    dim3 g(1, B.S);
+    k_reduce<<<g, NTHREADS, 0, st>>>(part.as<double2>(), 1, B.d_chunk0.as<int>(), nullptr, out.as<double2>(), 1);
+    QS3_LAUNCHED();
+    std::vector<double2> h(B.S);
+    QS3_CUDA(cudaMemcpyAsync(h.data(), out.p, B.S * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    QS3_CUDA(cudaStreamSynchronize(st));
+    if (per) per->assign(B.S, 0.0);
+    for (int s = 0; s < B.S; ++s) {
+        if (!B.dims[s]) continue;
+        const double r = std::sqrt(std::max(h[s].x, 0.0));
+        rmax = std::max(rmax, r);
+        if (per) (*per)[s] = r;
+    }
+    return QS3_OK;
+}
+
+// ------------------------------------------------------- conventional Lanczos
+
+struct LzResult {
+    std::vector<double> e;       // per sector
+    std::vector<int> conv;
+    int steps = 0;
+};
+
+// Lanczos to the lowest eigenpair of each sector; out (fp64, total dim) gets the vectors.
+template <typename VT>
+static int lanczos_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T *start,
+                       typename Wide<VT>::T *out, cudaStream_t st, LzResult &R, HphiStats &hs) {
+    Engine<VT> E(B, st, &hs);
+    const int nmax = std::max(2, o.n_max);
+    QS3_TRY(E.init(nmax + 1, 0));
+    if (start) QS3_TRY(E.start_from(start)); else QS3_TRY(E.start_random(o.seed));
+    const int S = B.S;
+    R.e.assign(S, NAN);
+    R.conv.assign(S, 0);
+    std::vector<double> eprev(S, NAN), a, b;
+    std::vector<int> msize(S, 0);
+    for (int s = 0; s < S; ++s)
+        if (!B.dims[s]) R.conv[s] = 1;
+    const int every = std::max(1, o.check_every);
+    int x = 0;
+    for (; x < nmax && E.any_active(); ++x) {
+        QS3_TRY(E.step(x));
+        const int n = x + 1;
+        if (!((n >= o.min_iter && n % every == 0) || n == nmax)) continue;
+        QS3_TRY(E.fetch(a, b));
+        std::vector<int> newly(S, 0);
+        bool any = false;
+        for (int s = 0; s < S; ++s) {
+            if (!E.h_active[s]) continue;
+            const double *as = &a[(size_t)s * E.cap], *bs = &b[(size_t)s * E.cap];
+            int m = n;
+            bool brk = false;
+            for (int k = 0; k < n; ++k)
+                if (bs[k] == 0.0) { m = k + 1; brk = true; break; }
+            const double e = tri_eig_k(m, as, bs, 0);
+            bool ok = brk || (std::isfinite(eprev[s]) && std::fabs(e - eprev[s]) <= o.eps * std::fabs(e));
+            double rres = 0.0;
+            if (ok && !brk && o.res_tol > 0) {
+                // Ritz residual |H y - e y| = beta_{m-1} |c_{m-1}| (full reorthogonalisation keeps it exact)
+                std::vector<double> c;
+                tri_eigvec(m, as, bs, e, c);
+                rres = std::fabs(bs[m - 1] * c[m - 1]);
+                ok = rres <= o.res_tol * std::max(std::fabs(e), 1.0);
+            }
+            if (log_on())
+                fprintf(stderr, "[qs3] lanczos vt=%zu n=%d s=%d m=%d e=%.17g de=%.3g beta=%.3g rres=%.3g ok=%d\n",
+                        sizeof(VT), n, s, m, e, e - eprev[s], bs[m - 1], rres, (int)ok);
+            eprev[s] = e;
+            R.e[s] = e;
+            msize[s] = m;
+            if (ok || n == nmax) {
+                newly[s] = 1;
+                any = true;
+                R.conv[s] = ok;
+            }
+        }
+        if (any) {
+            // eigenvectors of the newly finished sectors: psi = sum_x c_x psi_x
+            std::vector<double> C((size_t)S * E.cap, 0.0);
+            for (int s = 0; s < S; ++s) {
+                if (!newly[s]) continue;
+                std::vector<double> c;
+                tri_eigvec(msize[s], &a[(size_t)s * E.cap], &b[(size_t)s * E.cap], R.e[s], c);
+                for (int k = 0; k < msize[s]; ++k) C[(size_t)s * E.cap + k] = c[k];
+            }
+            QS3_TRY(E.template combine<typename Wide<VT>::T>(out, B.total, E.cap, 1, C, newly));
+            for (int s = 0; s < S; ++s)
+                if (newly[s]) E.h_active[s] = 0;
+            QS3_TRY(E.push_active());
+        }
+    }
+    R.steps = x;
+    return QS3_OK;
+}
+
+// --------------------------------------------------- thick-restart Lanczos
+
+struct TrlResult {
+    std::vector<double> e;       // S x n_eig
+    std::vector<int> conv;
+    int steps = 0, restarts = 0;
+};
+
+template <typename VT>
+static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T *start,
+                   typename Wide<VT>::T *out, cudaStream_t st, TrlResult &R, HphiStats &hs) {
+    using WT = typename Wide<VT>::T;
+    const int S = B.S;
+    const int NM = std::max(2, o.n_max);
+    const int NK = std::max(1, std::min(o.n_keep, NM - 1));
+    const int NE = std::max(1, std::min(o.n_eig, NK));
+    if (NK > MAXOUT) return set_err(QS3_ERR_INVALID_ARG, "n_keep %d > %d", NK, MAXOUT);
+    Engine<VT> E(B, st, &hs);
+    QS3_TRY(E.init(NM + 1, NK));
+    if (start) QS3_TRY(E.start_from(start)); else QS3_TRY(E.start_random(o.seed));
+    R.e.assign((size_t)S * NE, NAN);
+    R.conv.assign(S, 0);
+    for (int s = 0; s < S; ++s)
+        if (!B.dims[s]) R.conv[s] = 1;
+    std::vector<double> a, b;
+    std::vector<std::vector<double>> ev(S), Cm(S), eprev(S), bK(S);
+    std::vector<int> msize(S, NM);
+    int steps = 0;
+    // finish the sectors in `done`: write their NE lowest Ritz vectors
+    auto finish = [&](const std::vector<int> &done) -> int {
+        bool any = false;
+        for (int v : done) any |= v != 0;
+        if (!any) return QS3_OK;
+        std::vector<double> C((size_t)S * E.cap * NE, 0.0);
+        for (int s = 0; s < S; ++s) {
+            if (!done[s]) continue;
+            const int m = msize[s];
+            for (int x = 0; x < m; ++x)
+                for (int y = 0; y < NE && y < m; ++y) C[(size_t)s * E.cap * NE + x * NE + y] = Cm[s][(size_t)x * m + y];
+            for (int y = 0; y < NE; ++y) R.e[(size_t)s * NE + y] = y < m ? ev[s][y] : NAN;
+        }
+        QS3_TRY(E.template combine<WT>(out, B.total, E.cap, NE, C, done));
+        for (int s = 0; s < S; ++s)
+            if (done[s]) E.h_active[s] = 0;
+        return E.push_active();
+    };
+    // first part of Alg. 10: N_M Lanczos steps
+    for (int x = 0; x < NM; ++x) { QS3_TRY(E.step(x)); ++steps; }
+    QS3_TRY(E.fetch(a, b));
+    {
+        std::vector<int> done(S, 0);
+        for (int s = 0; s < S; ++s) {
+            if (!E.h_active[s]) continue;
+            const double *as = &a[(size_t)s * E.cap], *bs = &b[(size_t)s * E.cap];
+            int m = NM;
+            for (int k = 0; k < NM - 1; ++k)
+                if (bs[k] == 0.0) { m = k + 1; break; }
+            msize[s] = m;
+            std::vector<double> T((size_t)m * m, 0.0);
+            for (int i = 0; i < m; ++i) {
+                T[(size_t)i * m + i] = as[i];
+                if (i + 1 < m) T[(size_t)i * m + i + 1] = T[(size_t)(i + 1) * m + i] = bs[i];
+            }
+            jacobi_eig(m, T, ev[s], Cm[s]);
+            if (m < NM || bs[NM - 1] == 0.0) { done[s] = 1; R.conv[s] = 1; }   // Krylov space exhausted
+        }
+        QS3_TRY(finish(done));
+    }
+    int I = 1;
+    for (; I <= o.max_iter && E.any_active(); ++I) {
+        std::vector<int> done(S, 0);
+        bool anyc = false;
+        for (int s = 0; s < S; ++s) {
+            if (!E.h_active[s]) continue;
+            if (I > 1) {
+                double dmax = 0.0;
+                for (int y = 0; y < NK; ++y) dmax = std::max(dmax, std::fabs(eprev[s][y] / ev[s][y] - 1.0));
+                if (dmax < o.eps) { done[s] = 1; R.conv[s] = 1; anyc = true; }
+            }
+            eprev[s].assign(ev[s].begin(), ev[s].begin() + NK);
+        }
+        if (anyc) QS3_TRY(finish(done));
+        if (!E.any_active()) break;
+        // restart (lines 14-19): psi_y = Psi C[:, y] for y < N_K; psi_{N_K} = psi_{N_M}
+        std::vector<double> C((size_t)S * NM * NK, 0.0);
+        for (int s = 0; s < S; ++s) {
+            if (!E.h_active[s]) continue;
+            bK[s].assign(NK, 0.0);
+            const double bNM = b[(size_t)s * E.cap + NM - 1];
+            for (int y = 0; y < NK; ++y) bK[s][y] = bNM * Cm[s][(size_t)(NM - 1) * NM + y];
+            for (int x = 0; x < NM; ++x)
+                for (int y = 0; y < NK; ++y) C[(size_t)s * NM * NK + x * NK + y] = Cm[s][(size_t)x * NM + y];
+        }
+        QS3_TRY(E.template combine<VT>(E.vec(E.cap), B.total, NM, NK, C, E.h_active));
+        QS3_CUDA(cudaMemcpyAsync(E.vec(0), E.vec(E.cap), (size_t)NK * B.total * sizeof(VT), cudaMemcpyDeviceToDevice, st));
+        QS3_CUDA(cudaMemcpyAsync(E.vec(NK), E.vec(NM), (size_t)B.total * sizeof(VT), cudaMemcpyDeviceToDevice, st));
+        // lines 20-26: Lanczos steps from psi_{N_K} (the Gram-Schmidt against psi_0..psi_{N_K}
+        // removes the arrowhead couplings beta_y psi_y)
+        for (int x = NK; x < NM; ++x) { QS3_TRY(E.step(x)); ++steps; }
+        QS3_TRY(E.fetch(a, b));
+        // lines 27-30: arrowhead T and its eigen-decomposition
+        for (int s = 0; s < S; ++s) {
+            if (!E.h_active[s]) continue;
+            const double *as = &a[(size_t)s * E.cap], *bs = &b[(size_t)s * E.cap];
+            int m = NM;
+            for (int k = NK; k < NM - 1; ++k)
+                if (bs[k] == 0.0) { m = k + 1; break; }
+            std::vector<double> T((size_t)m * m, 0.0);
+            for (int y = 0; y < NK; ++y) {
+                T[(size_t)y * m + y] = ev[s][y];
+                T[(size_t)y * m + NK] = T[(size_t)NK * m + y] = bK[s][y];
+            }
+            for (int x = NK; x < m; ++x) {
+                T[(size_t)x * m + x] = as[x];
+                if (x + 1 < m) T[(size_t)x * m + x + 1] = T[(size_t)(x + 1) * m + x] = bs[x];
+            }
+            std::vector<double> w2, Z2;
+            jacobi_eig(m, T, w2, Z2);
+            if (m < NM) {            // invariant subspace: the Ritz values are exact
+                msize[s] = m;
+                ev[s] = w2;
+                Cm[s] = Z2;
+                std::vector<int> d1(S, 0);
+                d1[s] = 1;
+                R.conv[s] = 1;
+                QS3_TRY(finish(d1));
+                continue;
+            }
+            ev[s] = w2;
+            Cm[s] = Z2;
+        }
+        R.restarts = I;
+    }
+    // sectors still running: return their current Ritz pairs
+    {
+        std::vector<int> rest(S, 0);
+        for (int s = 0; s < S; ++s) rest[s] = E.h_active[s];
+        QS3_TRY(finish(rest));
+    }
+    R.steps = steps;
+    return QS3_OK;
+}
+
+// ------------------------------------------------------------- entry points
+
+static bool all_conv(const std::vector<int> &c) {
+    for (int v : c) if (!v) return false;
+    return true;
+}
+
+template <typename V32, typename V64>
+static int lanczos_entry(Basis &B, const qs3_solve_opts &o, double *evals, void *evecs, qs3_solve_info *info,
+                         cudaStream_t st) {
+    auto t0 = std::chrono::steady_clock::now();
+    uint64_t nz = 0;
+    QS3_TRY(count_nnz(B, &nz));
+    HphiStats hs;
+    DevBuf own;
+    V64 *out = (V64 *)evecs;
+    if (!out) {
+        QS3_TRY(own.alloc(B.total * sizeof(V64)));
+        out = own.as<V64>();
+    }
+    QS3_CUDA(cudaMemsetAsync(out, 0, B.total * sizeof(V64), st));
+    LzResult R;
+    int iters = 0, refine = 0;
+    if (o.precision == QS3_F32) {
+        // the fp32 phase stops at fp32 resolution; the fp64 refinement takes it from there
+        qs3_solve_opts o1 = o;
+        o1.eps = std::max(o.eps, 2e-7);
+        o1.res_tol = o.res_tol > 0 ? std::max(o.res_tol, 1e-5) : 0.0;
+        QS3_TRY(lanczos_run<V32>(B, o1, nullptr, out, st, R, hs));
+        iters += R.steps;
+        qs3_solve_opts o2 = o;
+        o2.min_iter = std::max(2, std::min(o.min_iter, o.check_every));
+        LzResult R2;
+        QS3_TRY(lanczos_run<V64>(B, o2, out, out, st, R2, hs));
+        refine = R2.steps;
+        iters += R2.steps;
+        R = R2;
+    } else {
+        QS3_TRY(lanczos_run<V64>(B, o, nullptr, out, st, R, hs));
+        iters += R.steps;
+    }
+    for (int s = 0; s < B.S; ++s) evals[s] = R.e[s];
+    double rmax = 0.0;
+    QS3_TRY(residuals<V64>(B, out, R.e, st, rmax));
+    if (info) {
+        info->iterations = iters;
+        info->restarts = 0;
+        int c = 0;
+        for (int v : R.conv) c += v;
+        info->converged = c;
+        info->refine_iterations = refine;
+        info->max_residual = rmax;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        QS3_CUDA(cudaStreamSynchronize(st));
+        QS3_TRY(hs.harvest());
+        info->hphi_nnz = hs.nnz;
+        info->hphi_seconds = hs.sec;
+        info->hphi_calls = hs.calls;
+    }
+    return all_conv(R.conv) ? QS3_OK : set_err(QS3_ERR_NOT_CONVERGED, "Lanczos did not converge in %d steps", o.n_max);
+}
+
+template <typename V32, typename V64>
+static int trl_entry(Basis &B, const qs3_solve_opts &o, double *evals, void *evecs, qs3_solve_info *info,
+                     cudaStream_t st) {
+    auto t0 = std::chrono::steady_clock::now();
+    uint64_t nz = 0;
+    QS3_TRY(count_nnz(B, &nz));
+    HphiStats hs;
+    const int NM = std::max(2, o.n_max);
+    const int NK = std::max(1, std::min(o.n_keep, NM - 1));
+    const int NE = std::max(1, std::min(o.n_eig, NK));
+    if (o.n_eig > NK) return set_err(QS3_ERR_INVALID_ARG, "n_eig %d > n_keep %d", o.n_eig, NK);
+    DevBuf own;
+    V64 *out = (V64 *)evecs;
+    if (!out) {
+        QS3_TRY(own.alloc((uint64_t)NE * B.total * sizeof(V64)));
+        out = own.as<V64>();
+    }
+    QS3_CUDA(cudaMemsetAsync(out, 0, (uint64_t)NE * B.total * sizeof(V64), st));
+    TrlResult R;
+    int iters = 0, refine = 0, restarts = 0;
+    if (o.precision == QS3_F32) {
+        QS3_TRY(trl_run<V32>(B, o, nullptr, out, st, R, hs));
+        iters += R.steps;
+        restarts += R.restarts;
+        // fp64 refinement: restart the fp64 iteration from the sum of the fp32 Ritz vectors
+        DevBuf sum;
+        QS3_TRY(sum.alloc(B.total * sizeof(V64)));
+        QS3_CUDA(cudaMemcpyAsync(sum.p, out, B.total * sizeof(V64), cudaMemcpyDeviceToDevice, st));
+        if (NE > 1) {
+            std::vector<double> C((size_t)B.S * NE, 1.0);
+            std::vector<int> all(B.S, 1);
+            // sum of the NE vectors: a combination kernel over the output block
+            DevBuf dC, dm;
+            QS3_TRY(dC.alloc(C.size() * 8));
+            QS3_TRY(dm.alloc(all.size() * 4));
+            QS3_CUDA(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, st));
+            QS3_CUDA(cudaMemcpyAsync(dm.p, all.data(), all.size() * 4, cudaMemcpyHostToDevice, st));
+            if (B.nchunks) {
+                k_combine<V64, V64><<<B.nchunks, NTHREADS, NE * sizeof(double), st>>>(
+                    sum.as<V64>(), B.total, out, B.total, NE, 1, dC.as<double>(), NE, B.d_secs.as<SecView>(),
+                    B.d_chunk0.as<int>(), B.S, dm.as<int>());
+                QS3_LAUNCHED();
+            }
+            QS3_CUDA(cudaStreamSynchronize(st));
+        }
+        TrlResult R2;
+        QS3_TRY(trl_run<V64>(B, o, sum.as<V64>(), out, st, R2, hs));
+        refine = R2.steps;
+        iters += R2.steps;
+        restarts += R2.restarts;
+        R = R2;
+    } else {
+        QS3_TRY(trl_run<V64>(B, o, nullptr, out, st, R, hs));
+        iters += R.steps;
+        restarts += R.restarts;
+    }
+    for (size_t i = 0; i < R.e.size(); ++i) evals[i] = R.e[i];
+    double rmax = 0.0;
+    for (int y = 0; y < NE; ++y) {
+        std::vector<double> ey(B.S);
+        for (int s = 0; s < B.S; ++s) ey[s] = std::isfinite(R.e[(size_t)s * NE + y]) ? R.e[(size_t)s * NE + y] : 0.0;
+        double r = 0.0;
+        QS3_TRY(residuals<V64>(B, out + (uint64_t)y * B.total, ey, st, r));
+        rmax = std::max(rmax, r);
+    }
+    if (info) {
+        info->iterations = iters;
+        info->restarts = restarts;
+        int c = 0;
+        for (int v : R.conv) c += v;
+        info->converged = c;
+        info->refine_iterations = refine;
+        info->max_residual = rmax;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        QS3_CUDA(cudaStreamSynchronize(st));
+        QS3_TRY(hs.harvest());
+        info->hphi_nnz = hs.nnz;
+        info->hphi_seconds = hs.sec;
+        info->hphi_calls = hs.calls;
+    }
+    return all_conv(R.conv) ? QS3_OK
+                            : set_err(QS3_ERR_NOT_CONVERGED, "thick-restart Lanczos did not converge in %d restarts",
+                                      o.max_iter);
+}
+
+static int check_opts(const qs3_solve_opts *o) {
+    if (!o) return set_err(QS3_ERR_INVALID_ARG, "options are NULL");
+    if (o->n_max < 2 || o->n_max > 2048) return set_err(QS3_ERR_INVALID_ARG, "n_max %d outside [2, 2048]", o->n_max);
+    if (o->check_every < 1) return set_err(QS3_ERR_INVALID_ARG, "check_every %d", o->check_every);
+    if (!(o->eps > 0)) return set_err(QS3_ERR_INVALID_ARG, "eps %g", o->eps);
+    if (o->precision != QS3_F32 && o->precision != QS3_F64)
+        return set_err(QS3_ERR_INVALID_ARG, "precision %d", o->precision);
+    return QS3_OK;
+}
+
+}  // namespace qs3
+
+using namespace qs3;
+
+extern "C" int qs3_lanczos(qs3_basis_t b, const qs3_solve_opts *o, double *evals, void *evecs, qs3_solve_info *info,
+                           void *stream) {
+    clear_err();
+    if (!b || !evals) return set_err(QS3_ERR_INVALID_ARG, "NULL argument");
+    QS3_TRY(check_opts(o));
+    if (info) memset(info, 0, sizeof(*info));
+    Basis &B = b->B;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (B.has_k) return lanczos_entry<float2, double2>(B, *o, evals, evecs, info, st);
+    return lanczos_entry<float, double>(B, *o, evals, evecs, info, st);
+}
+
+extern "C" int qs3_trlanczos(qs3_basis_t b, const qs3_solve_opts *o, double *evals, void *evecs, qs3_solve_info *info,
+                             void *stream) {
+    clear_err();
+    if (!b || !evals) return set_err(QS3_ERR_INVALID_ARG, "NULL argument");
+    QS3_TRY(check_opts(o));
+    if (o->n_keep < 1 || o->n_keep >= o->n_max || o->n_keep > MAXOUT)
+        return set_err(QS3_ERR_INVALID_ARG, "n_keep %d (need 1 <= n_keep < n_max, n_keep <= %d)", o->n_keep, MAXOUT);
+    if (o->n_eig < 1 || o->n_eig > o->n_keep) return set_err(QS3_ERR_INVALID_ARG, "n_eig %d", o->n_eig);
+    if (info) memset(info, 0, sizeof(*info));
+    Basis &B = b->B;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (B.has_k) return trl_entry<float2, double2>(B, *o, evals, evecs, info, st);
+    return trl_entry<float, double>(B, *o, evals, evecs, info, st);
+}
+
+// ------------------------------------------- dynamical structure factor
+// Eq. (cfe): for every momentum q_n, psi_1 = S^-_q |gs> / |S^-_q gs| in the
+// target sector n, n_iter Lanczos steps with full reorthogonalisation (Alg.
+// 10 lines 3-11) batched over the n_q sectors, then the continued fraction
+// evaluated on the omega grid by a device kernel.
+namespace qs3 {
+
+int cfrac_launch(int nq, int cap, const double *alpha, const double *beta, const int *msz, const double *norm2,
+                 double e0, double h, double eta, const double *omega, int nw, double *out, cudaStream_t st);
+
+int dsf_run(Basis &S, int ss, const void *gs, double e0, Basis &Dd, int nq, const int *Q, int n_iter, double eta,
+            double h, int nw, const double *omega, double *s_qw, double *alpha, double *beta, double *norm2,
+            cudaStream_t st) {
+    uint64_t nz = 0;
+    QS3_TRY(count_nnz(Dd, &nz));
+    HphiStats hs;
+    Engine<double2> E(Dd, st, &hs);
+    QS3_TRY(E.init(n_iter + 1, 0));
+    for (int n = 0; n < nq; ++n)
+        QS3_TRY(smq_launch(S, ss, gs, Dd, n, Q + 3 * n, E.vec(0) + Dd.offs[n], st));
+    QS3_TRY(E.normalise(0));
+    std::vector<double2> n2(nq);
+    QS3_CUDA(cudaMemcpyAsync(n2.data(), E.nrm.p, nq * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    QS3_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> nrm2(nq);
+    for (int n = 0; n < nq; ++n) {
+        nrm2[n] = Dd.dims[n] ? n2[n].x : 0.0;
+        if (!(nrm2[n] > 0.0)) E.h_active[n] = 0;
+        if (norm2) norm2[n] = nrm2[n];
+    }
+    QS3_TRY(E.push_active());
+    for (int x = 0; x < n_iter && E.any_active(); ++x) QS3_TRY(E.step(x));
+    std::vector<double> a, b;
+    QS3_TRY(E.fetch(a, b));
+    std::vector<int> msz(nq, 0);
+    for (int n = 0; n < nq; ++n) {
+        if (!(nrm2[n] > 0.0)) continue;
+        int m = n_iter;
+        for (int k = 0; k < n_iter - 1; ++k)
+            if (b[(size_t)n * E.cap + k] == 0.0) { m = k + 1; break; }
+        msz[n] = m;
+        for (int x = 0; x < n_iter; ++x) {
+            if (alpha) alpha[(size_t)n * n_iter + x] = x < m ? a[(size_t)n * E.cap + x] : 0.0;
+            if (beta) beta[(size_t)n * n_iter + x] = x == 0 ? std::sqrt(nrm2[n])
+                                                            : (x < m ? b[(size_t)n * E.cap + x - 1] : 0.0);
+        }
+    }
+    if (s_qw && nw > 0) {
+        DevBuf dm, dn, dw, dout;
+        QS3_TRY(dm.upload(msz.data(), nq * sizeof(int)));
+        QS3_TRY(dn.upload(nrm2.data(), nq * sizeof(double)));
+        QS3_TRY(dw.upload(omega, nw * sizeof(double)));
+        QS3_TRY(dout.alloc((size_t)nq * nw * sizeof(double)));
+        QS3_TRY(cfrac_launch(nq, E.cap, E.alpha.as<double>(), E.beta.as<double>(), dm.as<int>(), dn.as<double>(), e0,
+                             h, eta, dw.as<double>(), nw, dout.as<double>(), st));
+        QS3_CUDA(cudaMemcpyAsync(s_qw, dout.p, (size_t)nq * nw * sizeof(double), cudaMemcpyDeviceToHost, st));
+        QS3_CUDA(cudaStreamSynchronize(st));
+    }
+    return QS3_OK;
+}
+
+}  // namespace qs3
