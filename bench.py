@@ -220,6 +220,7 @@ def run_ours(args, rank, world):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "lowest_E": float(np.min(evals)),
+        "_evals": evals[:, 0].tolist(),
         "lanczos_steps_per_solve": [int(i["iterations"]) for i in infos],
         "max_residual": max(i["max_residual"] for i in infos),
     }
@@ -256,23 +257,28 @@ def e2e_ours(args, spec, nd, Ks):
             "includes": "basis build from host arrays + solve + eigenvector D2H"}
 
 
-def fp32_vs_fp64(args, basis):
-    """Batched fp32 H Phi + fp64 recurrences/refinement against plain fp64."""
+def fp32_vs_fp64(args, basis, e_ref):
+    """Batched fp32 H Phi + fp64 recurrences/refinement against plain fp64,
+    both run to |dE| <= 1e-9 |E| (Ritz value stable to 1e-10 relative); the
+    achieved |dE| is measured against the tightly converged fp64 solve of the
+    timed steps (Ritz residual <= 1e-12 |E|)."""
     import torch
 
     import paper_2107_00872_gb300 as qs3
-    res = {}
-    ev = {}
+    res = {"target": "|dE| <= 1e-9 |E| in every sector"}
     for prec in ("f64", "f32"):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e, _, info = basis.lanczos(qs3.SolveOpts(n_max=args.n_max, eps=1e-14, res_tol=1e-12, precision=prec,
-                                                 seed=3), vectors=False)
+        # same stopping rule for both: Ritz value stable to 1e-10 and Ritz
+        # residual <= 1e-9 |E| (near-degenerate sectors need the residual well
+        # below the gap); the fp32 run refines in fp64
+        o = qs3.SolveOpts(n_max=args.n_max, eps=1e-10, res_tol=1e-9, precision=prec, refine_tol=1e-9, seed=3)
+        e, _, info = basis.lanczos(o, vectors=False)
         torch.cuda.synchronize()
         res[prec] = {"seconds": round(time.perf_counter() - t0, 4), "steps": int(info["iterations"]),
-                     "refine_steps": int(info["refine_iterations"]), "status": info["status"]}
-        ev[prec] = e[:, 0]
-    res["max_rel_dE"] = float(np.max(np.abs(ev["f32"] - ev["f64"]) / np.abs(ev["f64"])))
+                     "refine_steps": int(info["refine_iterations"]), "status": info["status"],
+                     "max_rel_dE": float(np.max(np.abs(e[:, 0] - e_ref) / np.abs(e_ref)))}
+    res["speedup_f32_over_f64"] = round(res["f64"]["seconds"] / res["f32"]["seconds"], 3)
     return res
 
 
@@ -409,7 +415,7 @@ def main():
     out, basis, spec, nd, Ks = run_ours(args, rank, world)
     if rank == 0 and not args.no_extras:
         out["e2e"] = e2e_ours(args, spec, nd, Ks)
-        out["fp32_vs_fp64"] = fp32_vs_fp64(args, basis)
+        out["fp32_vs_fp64"] = fp32_vs_fp64(args, basis, np.array(out["_evals"]))
         rate, cores, desc = oracle_sample(args)
         out["cpu_baseline"] = {"value": round(rate, 6), "unit": "Gnnz/s", "cores": cores, "kind": "oracle",
                                "sample": desc}
@@ -417,6 +423,7 @@ def main():
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+    out.pop("_evals", None)
     if rank == 0:
         print(json.dumps(out), flush=True)
 

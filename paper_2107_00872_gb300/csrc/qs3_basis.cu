@@ -72,15 +72,15 @@ int DevBuf::upload(const void *src, size_t bytes) {
     return QS3_OK;
 }
 
-// must match carve() in qs3_hphi.cu: binomial rows 0..nd+2, coordinates,
-// sqrt table (18 doubles), per-axis phase tables (complex fp64)
+// must match carve() in qs3_hphi.cu: binomial rows 0..nd+2, coordinates (k
+// only), sqrt table (18 doubles), per-site phase table (k only, complex fp64)
 size_t row_kernel_smem(const Basis &B, int /*extra_nd*/) {
     size_t s = (size_t)(B.nd + 3) * (B.N + 1) * sizeof(uint64_t);
-    s += (size_t)B.N * sizeof(uint32_t);
+    if (B.has_k) s += (size_t)B.N * sizeof(uint32_t);
     s = (s + 15) & ~(size_t)15;
     s += 18 * sizeof(double);
     s = (s + 15) & ~(size_t)15;
-    s += (size_t)(B.L[0] + B.L[1] + B.L[2]) * 2 * sizeof(double);
+    if (B.has_k) s += (size_t)B.N * 2 * sizeof(double);
     return s;
 }
 

@@ -59,15 +59,17 @@ template <> __device__ __forceinline__ const double *jxy_table<double2>(const La
 struct SmemLayout {
     uint64_t *sC;
     uint32_t *sxyz;
-    void *sph;      // phase tables, Lx + Ly + Lz complex entries of the vector precision
+    void *sph;      // k-sectors: per-site phase table, N complex entries of the vector precision
     void *snorm;    // sqrt table: [0..8] sqrt(s), [9..17] 1/sqrt(s)
 };
 
+// layout (must match row_kernel_smem): binomial rows 0..nd+2 | coordinates
+// (k only) | sqrt table | per-site phases (k only)
 __device__ __forceinline__ SmemLayout carve(const LatView &L, unsigned char *smem) {
     SmemLayout s;
     s.sC = (uint64_t *)smem;
     s.sxyz = (uint32_t *)(s.sC + (L.nd + 3) * L.np1);
-    size_t off = (size_t)(L.nd + 3) * L.np1 * 8 + (size_t)L.N * 4;
+    size_t off = (size_t)(L.nd + 3) * L.np1 * 8 + (L.has_k ? (size_t)L.N * 4 : 0);
     off = (off + 15) & ~(size_t)15;
     s.snorm = smem + off;
     off += 18 * sizeof(double);
@@ -76,24 +78,26 @@ __device__ __forceinline__ SmemLayout carve(const LatView &L, unsigned char *sme
     return s;
 }
 
+// ph[r] = exp(-2 pi i sum_alpha K_alpha r_alpha / L_alpha) for the coordinates
+// r_alpha of site r: the phase e^{ik.t} of the translation t = -(r_x, r_y, r_z)
+// that moves site r to the origin.  The angle is reduced exactly in integers.
 template <typename CT, typename R>
-__device__ __forceinline__ void fill_phases(const LatView &L, const int *K, CT *ph) {
-    // ph[alpha-offset + v] = exp(-2 pi i K_alpha v / L_alpha): the phase e^{ik.t} of
-    // the translation t = -v along alpha that moves coordinate v to the origin
-    const int tot = L.L[0] + L.L[1] + L.L[2];
-    for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-        int a = (i < L.L[0]) ? 0 : (i < L.L[0] + L.L[1] ? 1 : 2);
-        int v = i - (a == 0 ? 0 : (a == 1 ? L.L[0] : L.L[0] + L.L[1]));
-        long long num = (long long)K[a] * v % L.L[a];
+__device__ __forceinline__ void fill_phases(const LatView &L, const uint32_t *sxyz, const int *K, CT *ph) {
+    const int N = L.N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const uint32_t p = sxyz[i];
+        const long long num = ((long long)K[0] * (p & 2047u) * (N / L.L[0]) +
+                               (long long)K[1] * ((p >> 11) & 2047u) * (N / L.L[1]) +
+                               (long long)K[2] * (p >> 22) * (N / L.L[2])) % N;
         double sn, cs;
-        sincospi(-2.0 * (double)num / (double)L.L[a], &sn, &cs);
+        sincospi(-2.0 * (double)num / (double)N, &sn, &cs);
         ph[i].x = (R)cs;
         ph[i].y = (R)sn;
     }
 }
 
 template <int ND, typename VT, bool KS>
-__global__ void __launch_bounds__(NTHREADS) k_hphi(LatView L, const SecView *__restrict__ secs,
+__global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *__restrict__ secs,
                                                    const int *__restrict__ tile0, int S, int ntiles,
                                                    const VT *__restrict__ phi, VT *__restrict__ psi,
                                                    const int *__restrict__ active) {
@@ -108,7 +112,6 @@ __global__ void __launch_bounds__(NTHREADS) k_hphi(LatView L, const SecView *__r
         snorm[9 + threadIdx.x] = threadIdx.x ? (R)(1.0 / sqrt((double)threadIdx.x)) : (R)0;
     }
     CT *ph = (CT *)sm.sph;
-    const CT *phx = ph, *phy = ph + L.L[0], *phz = ph + L.L[0] + L.L[1];
     const R *jxy = jxy_table<VT>(L);
     __syncthreads();
     int cur = -1;
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(NTHREADS) k_hphi(LatView L, const SecView *__r
         const SecView sv = secs[s];
         if (KS && s != cur) {
             __syncthreads();
-            fill_phases<CT, R>(L, sv.K, ph);
+            fill_phases<CT, R>(L, sm.sxyz, sv.K, ph);
             __syncthreads();
             cur = s;
         }
@@ -130,7 +133,11 @@ __global__ void __launch_bounds__(NTHREADS) k_hphi(LatView L, const SecView *__r
         const VT *ph_in = phi + sv.off;
         const VT x0 = ph_in[row];
         R rs = 0;
-        if constexpr (KS) rs = snorm[9 + sv.stab[row]];
+        int st_row = 1;
+        if constexpr (KS) {
+            st_row = sv.stab[row];
+            rs = snorm[9 + st_row];
+        }
         double e = L.c0, dd = 0.0;
         CT acc;
         acc.x = 0; acc.y = 0;
@@ -151,9 +158,9 @@ __global__ void __launch_bounds__(NTHREADS) k_hphi(LatView L, const SecView *__r
                 int tt[ND];
 #pragma unroll
                 for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
-                sort_net(tt);
                 const R jh = (R)0.5 * __ldg(jxy + q);
                 if constexpr (!KS) {
+                    sort_net(tt);
                     const uint64_t r2 = rank_of(tt, sm.sC, L.np1);
                     CT cf;
                     cf.x = jh; cf.y = 0;
@@ -164,8 +171,9 @@ __global__ void __launch_bounds__(NTHREADS) k_hphi(LatView L, const SecView *__r
                     const uint64_t r2 = canon(tt, L, sm.sxyz, sm.sC, rep, ax, by, cz);
                     uint32_t idx;
                     if (!sigma_find(sv, prefix_of(rep, sm.sC, L.np1), r2, idx)) continue;
-                    CT p = cmul(cmul(phx[ax], phy[by]), phz[cz]);
-                    const R w = jh * snorm[__ldg(sv.stab + idx)] * rs;
+                    CT p = ph[ax + L.L[0] * (by + L.L[1] * cz)];
+                    const int st = __ldg(sv.stab + idx);
+                    const R w = (st == st_row) ? jh : jh * snorm[st] * rs;
                     p.x *= w;
                     p.y *= w;
                     acc_add(acc, p, ph_in[idx]);
@@ -214,7 +222,6 @@ __global__ void __launch_bounds__(NTHREADS) k_count(LatView L, const SecView *__
                         int tt[ND];
 #pragma unroll
                         for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
-                        sort_net(tt);
                         int rep[ND];
                         int ax, by, cz;
                         const uint64_t r2 = canon(tt, L, sm.sxyz, sm.sC, rep, ax, by, cz);

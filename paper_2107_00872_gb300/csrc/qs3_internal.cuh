@@ -195,13 +195,24 @@ __device__ __forceinline__ bool seen_before(const int (&a)[ND], int i, int v) {
     return s;
 }
 
-// Minimum-rank translate of the ascending site list t (the representative of
-// its orbit, Alg. 7).  Exact candidate pruning: the representative has a
-// down spin at x = 0, one at y = 0 and one at z = 0 (otherwise a -1 shift
-// along that axis lowers every site index and hence the rank), so only the
-// translations (-x_a, -y_b, -z_c) over spins a, b, c are tried.  On return
-// rep holds the sorted representative, (ax, by, cz) the coordinates moved to
-// the origin, and the function returns its rank0.
+// Minimum-rank translate of the site list t (the representative of its
+// orbit, Alg. 7), found without trying every translation.
+//
+// The rank order is the lexicographic order of the descending list of site
+// indices r = x + Lx (y + Ly z), so a representative first minimises its
+// largest site, which is the (z, y, x)-largest spin.  Hence, exactly:
+//  - a representative has a spin at x = 0, one at y = 0 and one at z = 0
+//    (otherwise a -1 shift along that axis lowers every site index), so the
+//    shifts along each axis are taken from the spins' coordinates;
+//  - level z: keep the z-shifts that minimise max z' over all spins;
+//  - level y: for those, keep the y-shifts that minimise max y' over the
+//    spins at the top z';
+//  - level x: likewise max x' over the spins at the top (z', y').
+// Every surviving translation gives the same largest site; the full keys
+// (sorted lists) of the survivors -- usually one -- decide.  On return rep
+// holds the sorted representative, (ax, by, cz) the coordinates moved to the
+// origin (T^t a' = rep with t = -(ax, by, cz)), and the function returns its
+// rank0.
 template <int ND>
 __device__ __forceinline__ uint64_t canon(const int (&t)[ND], const LatView &L, const uint32_t *__restrict__ sxyz,
                                           const uint64_t *__restrict__ sC, int (&rep)[ND], int &ax, int &by,
@@ -215,37 +226,113 @@ __device__ __forceinline__ uint64_t canon(const int (&t)[ND], const LatView &L, 
         Z[m] = p >> 22;
     }
     const int Lx = L.L[0], Ly = L.L[1], Lz = L.L[2];
-    const int LxLy = Lx * Ly;
     const int kb = L.key_bits;
-    uint64_t best = ~0ull;
-    int bc = 0, bb = 0, ba = 0;
-#pragma unroll 1
-    for (int c = 0; c < ND; ++c) {
-        const int zc = pick(Z, c);
-        if (seen_before(Z, c, zc)) continue;
-#pragma unroll 1
-        for (int b = 0; b < ND; ++b) {
-            const int yb = pick(Y, b);
-            if (seen_before(Y, b, yb)) continue;
-            int yz[ND];
+    // level z
+    uint32_t mz = 1u;
+    int bz = 0;
+    if (Lz > 1) {
+        bz = 0x7fffffff;
+        mz = 0u;
+#pragma unroll
+        for (int c = 0; c < ND; ++c) {
+            bool dup = false;
+#pragma unroll
+            for (int k = 0; k < c; ++k) dup |= (Z[k] == Z[c]);
+            int mx = 0;
 #pragma unroll
             for (int m = 0; m < ND; ++m) {
-                int zz = Z[m] - zc;
-                zz += (zz < 0) ? Lz : 0;
-                int yy = Y[m] - yb;
-                yy += (yy < 0) ? Ly : 0;
-                yz[m] = yy * Lx + zz * LxLy;
+                int d = Z[m] - Z[c];
+                d += (d < 0) ? Lz : 0;
+                mx = max(mx, d);
             }
-#pragma unroll 1
-            for (int a = 0; a < ND; ++a) {
+            if (!dup) {
+                if (mx < bz) { bz = mx; mz = 1u << c; }
+                else if (mx == bz) mz |= 1u << c;
+            }
+        }
+    }
+    uint64_t best = ~0ull;
+    int bc = 0, bb = 0, ba = 0;
+    for (uint32_t m1 = mz; m1; m1 &= m1 - 1) {
+        const int c = __ffs(m1) - 1;
+        const int zc = pick(Z, c);
+        int zz[ND];
+        uint32_t tz = 0u;
+#pragma unroll
+        for (int m = 0; m < ND; ++m) {
+            int d = Z[m] - zc;
+            d += (d < 0) ? Lz : 0;
+            zz[m] = d;
+            tz |= (d == bz ? 1u : 0u) << m;
+        }
+        // level y over the top-z spins
+        uint32_t my = 1u;
+        int byv = 0;
+        if (Ly > 1) {
+            byv = 0x7fffffff;
+            my = 0u;
+#pragma unroll
+            for (int b = 0; b < ND; ++b) {
+                bool dup = false;
+#pragma unroll
+                for (int k = 0; k < b; ++k) dup |= (Y[k] == Y[b]);
+                int mx = -1;
+#pragma unroll
+                for (int m = 0; m < ND; ++m) {
+                    int d = Y[m] - Y[b];
+                    d += (d < 0) ? Ly : 0;
+                    mx = ((tz >> m) & 1u) ? max(mx, d) : mx;
+                }
+                if (!dup) {
+                    if (mx < byv) { byv = mx; my = 1u << b; }
+                    else if (mx == byv) my |= 1u << b;
+                }
+            }
+        }
+        for (uint32_t m2 = my; m2; m2 &= m2 - 1) {
+            const int b = __ffs(m2) - 1;
+            const int yb = pick(Y, b);
+            int yy[ND];
+            uint32_t ty = 0u;
+#pragma unroll
+            for (int m = 0; m < ND; ++m) {
+                int d = Y[m] - yb;
+                d += (d < 0) ? Ly : 0;
+                yy[m] = d;
+                ty |= (((tz >> m) & 1u) && d == byv ? 1u : 0u) << m;
+            }
+            // level x over the top-(z, y) spins
+            uint32_t mx3 = 1u;
+            if (Lx > 1) {
+                int bxv = 0x7fffffff;
+                mx3 = 0u;
+#pragma unroll
+                for (int a = 0; a < ND; ++a) {
+                    bool dup = false;
+#pragma unroll
+                    for (int k = 0; k < a; ++k) dup |= (X[k] == X[a]);
+                    int mx = -1;
+#pragma unroll
+                    for (int m = 0; m < ND; ++m) {
+                        int d = X[m] - X[a];
+                        d += (d < 0) ? Lx : 0;
+                        mx = ((ty >> m) & 1u) ? max(mx, d) : mx;
+                    }
+                    if (!dup) {
+                        if (mx < bxv) { bxv = mx; mx3 = 1u << a; }
+                        else if (mx == bxv) mx3 |= 1u << a;
+                    }
+                }
+            }
+            for (uint32_t m3 = mx3; m3; m3 &= m3 - 1) {
+                const int a = __ffs(m3) - 1;
                 const int xa = pick(X, a);
-                if (seen_before(X, a, xa)) continue;
                 int s[ND];
 #pragma unroll
                 for (int m = 0; m < ND; ++m) {
-                    int xx = X[m] - xa;
-                    xx += (xx < 0) ? Lx : 0;
-                    s[m] = yz[m] + xx;
+                    int d = X[m] - xa;
+                    d += (d < 0) ? Lx : 0;
+                    s[m] = d + Lx * (yy[m] + Ly * zz[m]);
                 }
                 sort_net(s);
                 uint64_t key;
@@ -256,22 +343,19 @@ __device__ __forceinline__ uint64_t canon(const int (&t)[ND], const LatView &L, 
                 } else {
                     key = rank_of(s, sC, L.np1);
                 }
-                if (key < best) { best = key; bc = c; bb = b; ba = a; }
+                if (key < best) {
+                    best = key;
+                    bc = c; bb = b; ba = a;
+#pragma unroll
+                    for (int m = 0; m < ND; ++m) rep[m] = s[m];
+                }
             }
         }
     }
     ax = pick(X, ba);
     by = pick(Y, bb);
     cz = pick(Z, bc);
-#pragma unroll
-    for (int m = 0; m < ND; ++m) {
-        int xx = X[m] - ax; xx += (xx < 0) ? Lx : 0;
-        int yy = Y[m] - by; yy += (yy < 0) ? Ly : 0;
-        int zz = Z[m] - cz; zz += (zz < 0) ? Lz : 0;
-        rep[m] = xx + Lx * yy + LxLy * zz;
-    }
-    sort_net(rep);
-    return rank_of(rep, sC, L.np1);
+    return kb ? rank_of(rep, sC, L.np1) : best;
 }
 
 // prefix of a sorted list used by the two-level index over sigma: the colex

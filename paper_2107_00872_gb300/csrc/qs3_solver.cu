@@ -211,6 +211,155 @@ __global__ void k_step_scalars(int S, int x, int cap, const double2 *__restrict_
     inv[s] = b > 0.0 ? 1.0 / b : 0.0;
 }
 
+// ---------------------------------------------- fp32 vectors, fp64-accurate
+// For fp32 / complex64 vectors the dot products and the Gram-Schmidt updates
+// are carried on the fp32 units in double-float form (a value is hi + lo,
+// two floats): products of two floats are exact as p + e with e =
+// fma(a, b, -p), sums use the error-free two-sum.  This keeps ~48 bits, i.e.
+// fp64-class accumulation, at fp32 throughput (GB300 executes fp64 at a
+// small fraction of its fp32 rate).  Partial sums leave each thread in fp64.
+struct dfl { float hi, lo; };
+
+__device__ __forceinline__ dfl df_add(dfl a, float b) {     // (a.hi + a.lo) + b
+    const float s = a.hi + b;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b - bb);
+    const float lo = e + a.lo;
+    const float hi = s + lo;
+    return {hi, lo - (hi - s)};
+}
+// a += x * y (float * float, exact product)
+__device__ __forceinline__ dfl df_fma(dfl a, float x, float y) {
+    const float p = x * y;
+    const float e = fmaf(x, y, -p);
+    dfl r = df_add(a, p);
+    r.lo += e;
+    return r;
+}
+// a += x * (y.hi + y.lo)  (float times double-float)
+__device__ __forceinline__ dfl df_fma2(dfl a, float x, float yh, float yl) {
+    const float p = x * yh;
+    const float e = fmaf(x, yh, -p) + x * yl;
+    dfl r = df_add(a, p);
+    r.lo += e;
+    return r;
+}
+__device__ __forceinline__ double df_d(dfl a) { return (double)a.hi + (double)a.lo; }
+
+template <typename VT> struct F32c { static constexpr bool v = false; };
+template <> struct F32c<float2> { static constexpr bool v = true; };
+
+__device__ __forceinline__ float2 ldf(const float *p) { return make_float2(*p, 0.f); }
+__device__ __forceinline__ float2 ldf(const float2 *p) { return *p; }
+
+// part[c * m + j] = conj(V_{j0+j}) . w over the chunk, double-float per thread
+template <typename VT>
+__global__ void __launch_bounds__(NTHREADS) k_mdot32(const VT *__restrict__ V, uint64_t D, int j0, int m,
+                                                     const VT *__restrict__ w, const SecView *__restrict__ secs,
+                                                     const int *__restrict__ chunk0, int S,
+                                                     const int *__restrict__ active, double2 *__restrict__ part) {
+    __shared__ double2 red[NTHREADS / 32][JB];
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    float2 wv[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        wv[k] = (r < ci.n) ? ldf(w + ci.base + r) : make_float2(0.f, 0.f);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int jb = 0; jb < m; jb += JB) {
+        const int nj = min(JB, m - jb);
+        for (int jj = 0; jj < nj; ++jj) {
+            const VT *vj = V + (uint64_t)(j0 + jb + jj) * D + ci.base;
+            dfl re = {0.f, 0.f}, im = {0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int r = threadIdx.x + k * NTHREADS;
+                if (r < ci.n) {
+                    const float2 a = ldf(vj + r), b = wv[k];
+                    // conj(a) b = (a.x b.x + a.y b.y) + i (a.x b.y - a.y b.x)
+                    re = df_fma(re, a.x, b.x);
+                    if (F32c<VT>::v) {
+                        re = df_fma(re, a.y, b.y);
+                        im = df_fma(im, a.x, b.y);
+                        im = df_fma(im, -a.y, b.x);
+                    }
+                }
+            }
+            double2 acc = make_double2(df_d(re), df_d(im));
+            acc = warp_sum2(acc);
+            if (lane == 0) red[warp][jj] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x < nj) {
+            double2 t = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int q = 0; q < NTHREADS / 32; ++q) { t.x += red[q][threadIdx.x].x; t.y += red[q][threadIdx.x].y; }
+            part[(uint64_t)blockIdx.x * m + jb + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// w -= sum_j V_{j0+j} coef[s][j] in double-float, rounded once to fp32;
+// optionally part[c] = sum |w|^2 over the chunk
+template <typename VT>
+__global__ void __launch_bounds__(NTHREADS) k_mupdate32(VT *__restrict__ w, const VT *__restrict__ V, uint64_t D,
+                                                        int j0, int m, const double2 *__restrict__ coef, int ldc,
+                                                        const SecView *__restrict__ secs,
+                                                        const int *__restrict__ chunk0, int S,
+                                                        const int *__restrict__ active, double2 *__restrict__ part) {
+    extern __shared__ float4 scf[];   // per j: (re.hi, re.lo, im.hi, im.lo)
+    __shared__ double red[NTHREADS / 32];
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        const double2 c = coef[(uint64_t)ci.s * ldc + j];
+        const float rh = (float)c.x, ih = (float)c.y;
+        scf[j] = make_float4(rh, (float)(c.x - (double)rh), ih, (float)(c.y - (double)ih));
+    }
+    __syncthreads();
+    dfl nr = {0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r < ci.n) {
+            const float2 w0 = ldf(w + ci.base + r);
+            dfl re = {w0.x, 0.f}, im = {w0.y, 0.f};
+            const VT *vp = V + (uint64_t)j0 * D + ci.base + r;
+            for (int j = 0; j < m; ++j) {
+                const float2 a = ldf(vp + (uint64_t)j * D);
+                const float4 c = scf[j];
+                // w -= a * c: re -= a.x c.x - a.y c.y ; im -= a.x c.y + a.y c.x
+                re = df_fma2(re, -a.x, c.x, c.y);
+                if (F32c<VT>::v) {
+                    re = df_fma2(re, a.y, c.z, c.w);
+                    im = df_fma2(im, -a.x, c.z, c.w);
+                    im = df_fma2(im, -a.y, c.x, c.y);
+                }
+            }
+            const float2 out = make_float2(re.hi + re.lo, im.hi + im.lo);
+            if (F32c<VT>::v) ((float2 *)w)[ci.base + r] = out;
+            else ((float *)w)[ci.base + r] = out.x;
+            nr = df_fma(nr, out.x, out.x);
+            nr = df_fma(nr, out.y, out.y);
+        }
+    }
+    if (part) {
+        double v = df_d(nr);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < NTHREADS / 32; ++q) t += red[q];
+            part[blockIdx.x] = make_double2(t, 0.0);
+        }
+    }
+}
+
 // w *= inv[s] (per sector)
 template <typename VT>
 __global__ void __launch_bounds__(NTHREADS) k_scale(VT *__restrict__ w, const double *__restrict__ inv,
@@ -620,14 +769,21 @@ struct Engine {
     }
     int mdot(int j0, int m, const VT *w, double2 *out, int ldo) {
         if (B.nchunks == 0) return QS3_OK;
-        k_mdot<VT><<<grid(), NTHREADS, 0, st>>>(V.as<VT>(), D, j0, m, w, secs(), c0(), B.S, act(), part.as<double2>());
+        if constexpr (Is64<VT>::v)
+            k_mdot<VT><<<grid(), NTHREADS, 0, st>>>(V.as<VT>(), D, j0, m, w, secs(), c0(), B.S, act(), part.as<double2>());
+        else
+            k_mdot32<VT><<<grid(), NTHREADS, 0, st>>>(V.as<VT>(), D, j0, m, w, secs(), c0(), B.S, act(), part.as<double2>());
         QS3_LAUNCHED();
         return reduce(m, out, ldo);
     }
     int mupdate(VT *w, int j0, int m, const double2 *cf, int ldc, bool norm) {
         if (B.nchunks == 0) return QS3_OK;
-        k_mupdate<VT><<<grid(), NTHREADS, m * sizeof(double2), st>>>(w, V.as<VT>(), D, j0, m, cf, ldc, secs(), c0(), B.S,
-                                                                     act(), norm ? part.as<double2>() : nullptr);
+        if constexpr (Is64<VT>::v)
+            k_mupdate<VT><<<grid(), NTHREADS, m * sizeof(double2), st>>>(w, V.as<VT>(), D, j0, m, cf, ldc, secs(), c0(),
+                                                                         B.S, act(), norm ? part.as<double2>() : nullptr);
+        else
+            k_mupdate32<VT><<<grid(), NTHREADS, m * sizeof(float4), st>>>(w, V.as<VT>(), D, j0, m, cf, ldc, secs(), c0(),
+                                                                          B.S, act(), norm ? part.as<double2>() : nullptr);
         QS3_LAUNCHED();
         if (norm) return reduce(1, nrm.as<double2>(), 1);
         return QS3_OK;
@@ -657,7 +813,13 @@ struct Engine {
         return normalise(0);
     }
     // Alg. 10 lines 5-11 for step x: psi_{x+1} from H psi_x
-    int step(int x) {
+    // full2: two Gram-Schmidt passes against all of psi_0..psi_x (the first
+    // step after a thick restart, where v also has the large arrowhead
+    // components beta_y psi_y).  Otherwise the large components of v lie
+    // along psi_{x-1}, psi_x only: they are removed first (the three-term
+    // recurrence, coefficients by dot product), then one classical
+    // Gram-Schmidt pass against every kept vector removes the O(eps) rest.
+    int step(int x, bool full2 = false) {
         VT *w = vec(x + 1);
         std::pair<cudaEvent_t, cudaEvent_t> ev;
         QS3_TRY(stats->pair(ev));
@@ -668,8 +830,9 @@ struct Engine {
         stats->calls += 1;
         for (int s = 0; s < B.S; ++s)
             if (h_active[s]) stats->nnz += B.nnz_sec[s];
-        QS3_TRY(mdot(0, x + 1, w, h1.as<double2>(), cap));
-        QS3_TRY(mupdate(w, 0, x + 1, h1.as<double2>(), cap, false));
+        const int j0 = full2 ? 0 : std::max(0, x - 1);
+        QS3_TRY(mdot(j0, x + 1 - j0, w, h1.as<double2>() + j0, cap));
+        QS3_TRY(mupdate(w, j0, x + 1 - j0, h1.as<double2>() + j0, cap, false));
         QS3_TRY(mdot(0, x + 1, w, h2.as<double2>(), cap));
         QS3_TRY(mupdate(w, 0, x + 1, h2.as<double2>(), cap, true));
         k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, x, cap, h1.as<double2>(), nrm.as<double2>(), act(),
@@ -920,7 +1083,7 @@ static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T
         QS3_CUDA(cudaMemcpyAsync(E.vec(NK), E.vec(NM), (size_t)B.total * sizeof(VT), cudaMemcpyDeviceToDevice, st));
         // lines 20-26: Lanczos steps from psi_{N_K} (the Gram-Schmidt against psi_0..psi_{N_K}
         // removes the arrowhead couplings beta_y psi_y)
-        for (int x = NK; x < NM; ++x) { QS3_TRY(E.step(x)); ++steps; }
+        for (int x = NK; x < NM; ++x) { QS3_TRY(E.step(x, x == NK)); ++steps; }
         QS3_TRY(E.fetch(a, b));
         // lines 27-30: arrowhead T and its eigen-decomposition
         for (int s = 0; s < S; ++s) {
@@ -995,8 +1158,11 @@ static int lanczos_entry(Basis &B, const qs3_solve_opts &o, double *evals, void 
         o1.res_tol = o.res_tol > 0 ? std::max(o.res_tol, 1e-5) : 0.0;
         QS3_TRY(lanczos_run<V32>(B, o1, nullptr, out, st, R, hs));
         iters += R.steps;
+        // fp64 refinement from the fp32 Ritz vector, until the Ritz value is
+        // stable to refine_tol (or eps) and the caller's residual test holds
         qs3_solve_opts o2 = o;
         o2.min_iter = std::max(2, std::min(o.min_iter, o.check_every));
+        if (o.refine_tol > 0) o2.eps = std::max(o.eps, 0.1 * o.refine_tol);
         LzResult R2;
         QS3_TRY(lanczos_run<V64>(B, o2, out, out, st, R2, hs));
         refine = R2.steps;
@@ -1073,7 +1239,9 @@ static int trl_entry(Basis &B, const qs3_solve_opts &o, double *evals, void *eve
             QS3_CUDA(cudaStreamSynchronize(st));
         }
         TrlResult R2;
-        QS3_TRY(trl_run<V64>(B, o, sum.as<V64>(), out, st, R2, hs));
+        qs3_solve_opts o2 = o;
+        if (o.refine_tol > 0) o2.eps = std::max(o.eps, 0.1 * o.refine_tol);
+        QS3_TRY(trl_run<V64>(B, o2, sum.as<V64>(), out, st, R2, hs));
         refine = R2.steps;
         iters += R2.steps;
         restarts += R2.restarts;

@@ -32,9 +32,10 @@ def test_lanczos_chain16_ground_state(prec):
     assert info["status"] == "QS3_OK", info
     tol = 1e-12 if prec == "f64" else 1e-9
     assert abs(e[0, 0] - ev[0]) <= tol * abs(ev[0]), (e, ev[0])
-    assert info["max_residual"] <= 1e-10 * abs(ev[0]), info
+    # fp64: residual <= 1e-12 |E| (res_tol); fp32 + refinement: |dE| <= 1e-9 |E| needs ~sqrt of that
+    assert info["max_residual"] <= (1e-11 if prec == "f64" else 1e-4) * abs(ev[0]), info
     v = vec.cpu().numpy()
-    assert abs(abs(np.dot(v, U[:, 0])) - 1.0) < 1e-10
+    assert abs(abs(np.dot(v, U[:, 0])) - 1.0) < (1e-10 if prec == "f64" else 1e-7)
     if prec == "f32":
         assert info["refine_iterations"] > 0
 
