@@ -172,6 +172,22 @@ int qs3_correlations(qs3_basis_t b, int32_t s, const void *gs, int32_t n_pairs, 
 int qs3_smq(qs3_basis_t src, int32_t s_src, const void *phi, qs3_basis_t dst, int32_t s_dst, const int32_t *Q,
             void *psi, void *stream);
 
+/* qs3_smq for callers that must not allocate device memory during the call:
+ * code that hands all device memory out of its own pool, or that runs where
+ * an allocation would synchronise the device.  The paper has no counterpart;
+ * the result equals qs3_smq's.  The call allocates nothing: its one scratch
+ * array, the site phases e^{-i q.R}, is a fixed 32 KB device array
+ * inside the library that every GPU using the library keeps until the
+ * process exits.  Limits: n_sites <= 2048 (QS3_ERR_INVALID_ARG beyond) and
+ * lattices without a pos array (positions are the coordinates).  The first
+ * call on a device looks that array up (cudaGetSymbolAddress), so make it
+ * before any stream capture.  All calls share the array: two calls that
+ * overlap on the GPU (different streams, or graphs replayed concurrently)
+ * race; calls ordered on one stream do not.  The call is asynchronous on
+ * stream. */
+int qs3_smq_noalloc(qs3_basis_t src, int32_t s_src, const void *phi, qs3_basis_t dst, int32_t s_dst,
+                    const int32_t *Q, void *psi, void *stream);
+
 /* Dynamical structure factor S^-(q, omega) by the continued fraction of
  * Eq. (cfe) from n_iter Lanczos steps (fully reorthogonalised) started from
  * S^-_q |gs>, for n_q momenta at once (batched).  gs: device C128 state of

@@ -243,6 +243,15 @@ def smq(src: Basis, s_src: int, phi, dst: Basis, s_dst: int, Q, psi=None, stream
     return psi
 
 
+def smq_noalloc(src: Basis, s_src: int, phi, dst: Basis, s_dst: int, Q, psi, stream=None):
+    """S^-_q phi without any device allocation during the call (psi must be
+    given); asynchronous on the stream."""
+    q = np.ascontiguousarray(np.asarray(Q, np.int32))
+    check(load().qs3_smq_noalloc(src.handle, s_src, _dev(phi, src.dims[s_src], "phi"), dst.handle, s_dst, _ptr(q),
+                                 _dev(psi, dst.dims[s_dst], "psi"), _stream(stream)), "qs3_smq_noalloc")
+    return psi
+
+
 def dsf(src: Basis, s_src: int, gs, e0: float, dst: Basis, Qs, n_iter: int, eta: float, h_field: float,
         omega: np.ndarray, stream=None):
     """S^-(q, omega) by the continued fraction for each momentum of Qs

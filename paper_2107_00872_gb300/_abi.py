@@ -47,6 +47,7 @@ SIGNATURES = {
     "qs3_trlanczos": ([P, P, P, P, P, P], I32),
     "qs3_correlations": ([P, I32, P, I32, P, P, P, P, I32, P, P, P, P], I32),
     "qs3_smq": ([P, I32, P, P, I32, P, P, P], I32),
+    "qs3_smq_noalloc": ([P, I32, P, P, I32, P, P, P], I32),
     "qs3_dsf": ([P, I32, P, F64, P, I32, P, I32, F64, F64, I32, P, P, P, P, P, P], I32),
     "qs3_strerror": ([I32], ctypes.c_char_p),
     "qs3_last_error": ([], ctypes.c_char_p),

@@ -20,6 +20,7 @@
 // representative of b \ {s} and T^u (b \ {s}) = a (skipped when a is not in
 // the source sector).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -645,4 +646,94 @@ extern "C" int qs3_dsf(qs3_basis_t src, int32_t s_src, const void *gs, double e0
     if (!(eta > 0)) return set_err(QS3_ERR_INVALID_ARG, "eta must be positive");
     return dsf_run(src->B, s_src, gs, e0, dst->B, n_q, Q, n_iter, eta, h_field, n_omega, omega, s_qw, alpha, beta,
                    norm2, (cudaStream_t)stream);
+}
+
+// ----------------------------------------------- S^-_q without allocation
+// qs3_smq allocates a small device table of the site phases e^{-i q.R_r}
+// for every call.  qs3_smq_noalloc is the same product for callers that
+// must not allocate device memory while they run -- for example code
+// driven by an external memory pool or an allocator they cannot call into,
+// or code running where a cudaMalloc would synchronise the device.  Its
+// only scratch, that phase table, lives in the file-scope array below:
+// NOALLOC_MAX_SITES = 2048 complex doubles (32 KB), held by every GPU that
+// loads the library until the process exits.
+namespace qs3 {
+
+constexpr int NOALLOC_MAX_SITES = 2048;
+static __device__ __align__(256) double2 g_smq_phase_scratch[NOALLOC_MAX_SITES];
+
+// device address of the scratch on each device, looked up once per device
+static void *g_scratch_addr[256];
+static std::atomic<int> g_scratch_ready[256];
+
+static int noalloc_scratch(double2 **out) {
+    int dev = 0;
+    QS3_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return set_err(QS3_ERR_INVALID_ARG, "device %d", dev);
+    if (!g_scratch_ready[dev].load(std::memory_order_acquire)) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_smq_phase_scratch);
+        if (e != cudaSuccess || !p)
+            return set_err(QS3_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_scratch_addr[dev] = p;
+        g_scratch_ready[dev].store(1, std::memory_order_release);
+    }
+    *out = (double2 *)g_scratch_addr[dev];
+    return QS3_OK;
+}
+
+// ph[r] = e^{-i q.R_r} with R_r the coordinates of site r and
+// q.a_alpha = 2 pi Q_alpha / L_alpha; the angle is reduced exactly in integers
+__global__ void k_site_phases(int N, int Lx, int Ly, int Lz, int Qx, int Qy, int Qz, double2 *__restrict__ ph) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const long long x = r % Lx, y = (r / Lx) % Ly, z = r / (Lx * Ly);
+    long long num = ((long long)Qx * x * (N / Lx) + (long long)Qy * y * (N / Ly) + (long long)Qz * z * (N / Lz)) % N;
+    num += num < 0 ? N : 0;
+    double sn, cs;
+    sincospi(2.0 * (double)num / (double)N, &sn, &cs);
+    ph[r] = make_double2(cs, -sn);
+}
+
+static int smq_noalloc(Basis &S, int ss, const void *phi, Basis &Dd, int sd, const int *Q, void *psi,
+                       cudaStream_t st) {
+    if (S.N > NOALLOC_MAX_SITES)
+        return set_err(QS3_ERR_INVALID_ARG, "n_sites %d exceeds the %d sites of the no-allocation scratch", S.N,
+                       NOALLOC_MAX_SITES);
+    if (!S.pos.empty())
+        return set_err(QS3_ERR_INVALID_ARG, "the no-allocation S^-_q takes lattices without a position array");
+    if (S.N != Dd.N || S.L[0] != Dd.L[0] || S.L[1] != Dd.L[1] || S.L[2] != Dd.L[2])
+        return set_err(QS3_ERR_INVALID_ARG, "source and target bases are on different lattices");
+    if (Dd.nd != S.nd + 1) return set_err(QS3_ERR_INVALID_ARG, "target n_down must be source n_down + 1");
+    if (S.has_k != Dd.has_k) return set_err(QS3_ERR_INVALID_ARG, "both bases need momenta, or neither");
+    if (ss < 0 || ss >= S.S || sd < 0 || sd >= Dd.S) return set_err(QS3_ERR_INVALID_ARG, "sector index");
+    if (S.has_k)
+        for (int a = 0; a < 3; ++a)
+            if (((S.K[3 * ss + a] + Q[a]) % S.L[a] + S.L[a]) % S.L[a] != Dd.K[3 * sd + a])
+                return set_err(QS3_ERR_SYMMETRY, "target momentum is not K + Q (axis %d)", a);
+    double2 *ph = nullptr;
+    QS3_TRY(noalloc_scratch(&ph));
+    if (Dd.dims[sd] == 0) return QS3_OK;
+    if (S.dims[ss] == 0) {
+        QS3_CUDA(cudaMemsetAsync(psi, 0, Dd.dims[sd] * 16, st));
+        return QS3_OK;
+    }
+    k_site_phases<<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.L[0], S.L[1], S.L[2], Q[0], Q[1], Q[2], ph);
+    QS3_LAUNCHED();
+    if (S.nd == 0) {
+        k_smq_vac<<<(unsigned)((Dd.dims[sd] + 255) / 256), 256, 0, st>>>(Dd.secs[sd], Dd.has_k ? 1 : 0, S.N, ph,
+                                                                          (const double2 *)phi, (double2 *)psi);
+        QS3_LAUNCHED();
+        return QS3_OK;
+    }
+    return dispatch_smq(S, ss, Dd, sd, ph, (const double2 *)phi, (double2 *)psi, st);
+}
+
+}  // namespace qs3
+
+extern "C" int qs3_smq_noalloc(qs3_basis_t src, int32_t s_src, const void *phi, qs3_basis_t dst, int32_t s_dst,
+                               const int32_t *Q, void *psi, void *stream) {
+    qs3::clear_err();
+    if (!src || !dst || !phi || !psi || !Q) return qs3::set_err(QS3_ERR_INVALID_ARG, "NULL argument");
+    return qs3::smq_noalloc(src->B, s_src, phi, dst->B, s_dst, Q, psi, (cudaStream_t)stream);
 }
