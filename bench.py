@@ -58,6 +58,13 @@ WORKLOADS = {
     # name: (lattice factory, n_down, momenta)
     "square10x10_nd4_all_k": (lambda: qi.square(10), 4, lambda: qi.all_k((10, 10, 1))),
     "chain16_nd3_u1": (lambda: qi.chain(16), 3, lambda: None),
+    # the bond-disordered open 32x32 square lattice, N_down = 3 (dim 178,433,024)
+    "open32x32_nd3_u1": (lambda: qi.disordered_open_square(32), 3, lambda: None),
+    # the 10x10x10 cube: N_down = 4 at k = 0 (dim 41,417,998) and N_down = 3 on the k-path
+    "cubic10_nd4_k0": (lambda: qi.cubic(10), 4, lambda: [(0, 0, 0)]),
+    "cubic10_nd3_kpath": (lambda: qi.cubic(10), 3, lambda: list(dict.fromkeys(qi.cubic_kpath(10)))),
+    # the paper's own OpenMP benchmark system: 6x6x6, N_down = 5, k = 0 (dim 17,313,563)
+    "cubic6_nd5_k0": (lambda: qi.cubic(6), 5, lambda: [(0, 0, 0)]),
 }
 
 

@@ -70,6 +70,8 @@ def _load():
                 "orc_dense_k": (lat + [P, P, P, L, P], I),
                 "orc_smq": (lat + [P, P, P, L, P, P, P, P, P, L, P], I),
                 "orc_corr_u1": ([I, I, P, P, P, P], I),
+                "orc_row_terms_k": (lat + [P, U, L, P, P, P], L),
+                "orc_check_state": (lat + [P, U], ctypes.c_double),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(lib, name)
@@ -250,6 +252,26 @@ def hphi_k_rows(sec: Sector, phi: np.ndarray, rows: np.ndarray, count: bool = Fa
     _load().orc_hphi_k_rows(*sec.lat._args(sec.nd), _p(Kc), _p(sec.sigma1), _p(sec.Nak), sec.dim, _p(x),
                             len(r), _p(r), _p(y), _p(n))
     return (y, int(n[0])) if count else y
+
+
+def row_terms_k(lat: Lattice, nd: int, K, a1: int, max_terms: int = 4096):
+    """One row of Alg. 9 for the representative a1 (1-based) without a
+    representative list: (diagonal, 1-based target representatives,
+    coefficients), or None when a1 is not a compatible representative."""
+    Kc = np.ascontiguousarray(K, dtype=np.int32)
+    t = np.zeros(max_terms, np.uint64)
+    c = np.zeros(max_terms, np.complex128)
+    dg = np.zeros(1, np.float64)
+    n = _load().orc_row_terms_k(*lat._args(nd), _p(Kc), int(a1), max_terms, _p(t), _p(c), _p(dg))
+    if n < 0:
+        return None
+    return float(dg[0]), t[:n], c[:n]
+
+
+def check_state(lat: Lattice, nd: int, K, a1: int) -> float:
+    """Alg. 5: N_{a,k} of the 1-based index a1 (0 if not a compatible representative)."""
+    Kc = np.ascontiguousarray(K, dtype=np.int32)
+    return float(_load().orc_check_state(*lat._args(nd), _p(Kc), int(a1)))
 
 
 def dense_k(sec: Sector) -> np.ndarray:

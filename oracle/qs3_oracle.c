@@ -710,3 +710,66 @@ int orc_corr_u1(int N, int nd, const double *phi, double *szsz, double *spsm, do
     ctx_free(&c);
     return 0;
 }
+
+/* One row of Alg. 9 for the representative with 1-based index a, without a
+ * precomputed representative list: the representative of every hop target
+ * comes from Alg. 7 and its normalisation factor (zero when incompatible)
+ * from Alg. 5.  Writes up to max_terms off-diagonal terms (target
+ * representative index, 1-based, and complex coefficient) and the diagonal
+ * element (bonds plus site field); returns the number of terms, or -1 when a
+ * is not a representative compatible with K.  For sampled rows of sectors
+ * too large for Alg. 6. */
+int64_t orc_row_terms_k(ORC_LAT, const int *K, uint64_t a, int64_t max_terms, uint64_t *targets, double *coef,
+                        double *diag)
+{
+    orc_ctx c;
+    if (ctx_init(&c, ORC_LAT_ARGS)) { ctx_free(&c); return -2; }
+    const double Na = check_state(&c, a, K);
+    if (!(Na > 1e-8)) { ctx_free(&c); return -1; }
+    int n[ORC_MAXND], np[ORC_MAXND];
+    f_bar(&c, a, n, NULL);
+    double dg = 0.0;
+    int64_t nt = 0;
+    zdbl *cf = (zdbl *)coef;
+    for (int b = 0; b < nb; ++b) {
+        int f, fp;
+        int p = binary_search_int(r[b], n, 1, nd, &f);
+        int pp = binary_search_int(rp[b], n, 1, nd, &fp);
+        if (f == fp) {
+            dg += jz[b] / 4.0;
+        } else {
+            dg -= jz[b] / 4.0;
+            spin_exchange(nd, r[b], p, f, rp[b], pp, n, np);
+            uint64_t ap = F(&c, np);
+            int l[3];
+            uint64_t rep = representative(&c, ap, l);
+            const double Nr = check_state(&c, rep, K);
+            if (Nr > 1e-8 && nt < max_terms) {
+                targets[nt] = rep;
+                cf[nt] = (jxy[b] / 2.0) * cexp(I * kdot(&c, K, l)) * sqrt(Nr / Na);
+                ++nt;
+            }
+        }
+    }
+    if (h) {
+        for (int i = 1; i <= N; ++i) {
+            int f;
+            binary_search_int(i, n, 1, nd, &f);
+            dg += f ? 0.5 * h[i - 1] : -0.5 * h[i - 1];
+        }
+    }
+    *diag = dg;
+    ctx_free(&c);
+    return nt;
+}
+
+/* N_{a,k} of Alg. 5 for the 1-based index a (0 when a is not the
+ * representative of its orbit or not compatible with K) */
+double orc_check_state(ORC_LAT, const int *K, uint64_t a)
+{
+    orc_ctx c;
+    if (ctx_init(&c, ORC_LAT_ARGS)) { ctx_free(&c); return -1.0; }
+    const double v = check_state(&c, a, K);
+    ctx_free(&c);
+    return v;
+}

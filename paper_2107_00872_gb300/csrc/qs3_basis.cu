@@ -73,14 +73,12 @@ int DevBuf::upload(const void *src, size_t bytes) {
 }
 
 // must match carve() in qs3_hphi.cu: binomial rows 0..nd+2, coordinates (k
-// only), sqrt table (18 doubles), per-site phase table (k only, complex fp64)
+// only), sqrt table (18 doubles)
 size_t row_kernel_smem(const Basis &B, int /*extra_nd*/) {
     size_t s = (size_t)(B.nd + 3) * (B.N + 1) * sizeof(uint64_t);
     if (B.has_k) s += (size_t)B.N * sizeof(uint32_t);
     s = (s + 15) & ~(size_t)15;
     s += 18 * sizeof(double);
-    s = (s + 15) & ~(size_t)15;
-    if (B.has_k) s += (size_t)B.N * 2 * sizeof(double);
     return s;
 }
 
@@ -271,6 +269,23 @@ int build_sector_reps(Basis &B, int s) {
         case 8: return build_reps_nd<8>(B, s);
         default: return set_err(QS3_ERR_INVALID_ARG, "n_down %d", B.nd);
     }
+}
+
+// per-sector phase tables ph[s N + r] = exp(-2 pi i sum_alpha K_alpha r_alpha / L_alpha):
+// the phase e^{ik.t} of the translation t = -(r_x, r_y, r_z) that moves site r
+// to the origin; the angle is reduced exactly in integers
+__global__ void k_phase_tables(int S, int N, int Lx, int Ly, int Lz, const int *__restrict__ K,
+                               double2 *__restrict__ ph64, float2 *__restrict__ ph32) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S * N) return;
+    const int s = i / N, r = i % N;
+    const long long x = r % Lx, y = (r / Lx) % Ly, z = r / (Lx * Ly);
+    const long long num =
+        ((long long)K[3 * s] * x * (N / Lx) + (long long)K[3 * s + 1] * y * (N / Ly) + (long long)K[3 * s + 2] * z * (N / Lz)) % N;
+    double sn, cs;
+    sincospi(-2.0 * (double)num / (double)N, &sn, &cs);
+    ph64[i] = make_double2(cs, sn);
+    ph32[i] = make_float2((float)cs, (float)sn);
 }
 
 // ---------------------------------------------------------------- host side
@@ -472,6 +487,16 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     B.ntiles = B.tile0[nsec];
     B.nchunks = B.chunk0[nsec];
     B.secs.resize(nsec);
+    if (B.has_k) {
+        QS3_TRY(B.d_ph64.alloc((size_t)nsec * N * sizeof(double2)));
+        QS3_TRY(B.d_ph32.alloc((size_t)nsec * N * sizeof(float2)));
+        QS3_TRY(B.d_secs.upload(B.K.data(), B.K.size() * sizeof(int)));     // momenta for the table kernel
+        const int tot = nsec * N;
+        k_phase_tables<<<(tot + 255) / 256, 256>>>(nsec, N, B.L[0], B.L[1], B.L[2], B.d_secs.as<int>(),
+                                                   B.d_ph64.as<double2>(), B.d_ph32.as<float2>());
+        QS3_LAUNCHED();
+        QS3_CUDA(cudaDeviceSynchronize());
+    }
     for (int s = 0; s < nsec; ++s) {
         SecView &v = B.secs[s];
         v.sigma = B.has_k ? B.d_sigma[s].as<uint64_t>() : nullptr;
@@ -481,6 +506,8 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
         v.off = B.offs[s];
         for (int a = 0; a < 3; ++a) v.K[a] = B.K[3 * s + a];
         v.tile0 = B.tile0[s];
+        v.ph64 = B.has_k ? B.d_ph64.as<double2>() + (size_t)s * N : nullptr;
+        v.ph32 = B.has_k ? B.d_ph32.as<float2>() + (size_t)s * N : nullptr;
     }
     QS3_TRY(B.d_secs.upload(B.secs.data(), B.secs.size() * sizeof(SecView)));
     QS3_TRY(B.d_tile0.upload(B.tile0.data(), B.tile0.size() * 4));

@@ -59,12 +59,11 @@ template <> __device__ __forceinline__ const double *jxy_table<double2>(const La
 struct SmemLayout {
     uint64_t *sC;
     uint32_t *sxyz;
-    void *sph;      // k-sectors: per-site phase table, N complex entries of the vector precision
     void *snorm;    // sqrt table: [0..8] sqrt(s), [9..17] 1/sqrt(s)
 };
 
 // layout (must match row_kernel_smem): binomial rows 0..nd+2 | coordinates
-// (k only) | sqrt table | per-site phases (k only)
+// (k only) | sqrt table
 __device__ __forceinline__ SmemLayout carve(const LatView &L, unsigned char *smem) {
     SmemLayout s;
     s.sC = (uint64_t *)smem;
@@ -72,29 +71,12 @@ __device__ __forceinline__ SmemLayout carve(const LatView &L, unsigned char *sme
     size_t off = (size_t)(L.nd + 3) * L.np1 * 8 + (L.has_k ? (size_t)L.N * 4 : 0);
     off = (off + 15) & ~(size_t)15;
     s.snorm = smem + off;
-    off += 18 * sizeof(double);
-    off = (off + 15) & ~(size_t)15;
-    s.sph = smem + off;
     return s;
 }
 
-// ph[r] = exp(-2 pi i sum_alpha K_alpha r_alpha / L_alpha) for the coordinates
-// r_alpha of site r: the phase e^{ik.t} of the translation t = -(r_x, r_y, r_z)
-// that moves site r to the origin.  The angle is reduced exactly in integers.
-template <typename CT, typename R>
-__device__ __forceinline__ void fill_phases(const LatView &L, const uint32_t *sxyz, const int *K, CT *ph) {
-    const int N = L.N;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const uint32_t p = sxyz[i];
-        const long long num = ((long long)K[0] * (p & 2047u) * (N / L.L[0]) +
-                               (long long)K[1] * ((p >> 11) & 2047u) * (N / L.L[1]) +
-                               (long long)K[2] * (p >> 22) * (N / L.L[2])) % N;
-        double sn, cs;
-        sincospi(-2.0 * (double)num / (double)N, &sn, &cs);
-        ph[i].x = (R)cs;
-        ph[i].y = (R)sn;
-    }
-}
+template <typename CT> __device__ __forceinline__ const CT *phase_table(const SecView &sv);
+template <> __device__ __forceinline__ const double2 *phase_table<double2>(const SecView &sv) { return sv.ph64; }
+template <> __device__ __forceinline__ const float2 *phase_table<float2>(const SecView &sv) { return sv.ph32; }
 
 template <int ND, typename VT, bool KS>
 __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *__restrict__ secs,
@@ -111,20 +93,15 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
         snorm[threadIdx.x] = (R)sqrt((double)threadIdx.x);
         snorm[9 + threadIdx.x] = threadIdx.x ? (R)(1.0 / sqrt((double)threadIdx.x)) : (R)0;
     }
-    CT *ph = (CT *)sm.sph;
     const R *jxy = jxy_table<VT>(L);
     __syncthreads();
-    int cur = -1;
+    // no block-wide synchronisation inside the loop: each warp moves on to its
+    // next tile independently (the per-sector phases are a global, L1-cached table)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int s = (S == 1) ? 0 : sector_of_tile(tile0, S, t);
         if (active && !active[s]) continue;
         const SecView sv = secs[s];
-        if (KS && s != cur) {
-            __syncthreads();
-            fill_phases<CT, R>(L, sm.sxyz, sv.K, ph);
-            __syncthreads();
-            cur = s;
-        }
+        const CT *ph = phase_table<CT>(sv);
         const uint64_t row = (uint64_t)(t - sv.tile0) * TILE + threadIdx.x;
         if (row >= sv.dim) continue;
         const uint64_t rank = KS ? __ldg(sv.sigma + row) : row;
@@ -171,7 +148,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
                     const uint64_t r2 = canon(tt, L, sm.sxyz, sm.sC, rep, ax, by, cz);
                     uint32_t idx;
                     if (!sigma_find(sv, prefix_of(rep, sm.sC, L.np1), r2, idx)) continue;
-                    CT p = ph[ax + L.L[0] * (by + L.L[1] * cz)];
+                    CT p = ph[ax + L.L[0] * (by + L.L[1] * cz)];   // generic load (L1-cached)
                     const int st = __ldg(sv.stab + idx);
                     const R w = (st == st_row) ? jh : jh * snorm[st] * rs;
                     p.x *= w;

@@ -92,6 +92,8 @@ struct SecView {
     uint64_t off;                 // offset of the sector in a concatenated vector
     int K[3];
     int tile0;                    // first tile of the sector
+    const double2 *ph64;          // k-sectors: per-site phases e^{-2 pi i K.r/L} (fp64) ...
+    const float2 *ph32;           // ... and their fp32 copy; NULL for U(1)
 };
 
 // ---------------------------------------------------------- host basis
@@ -114,6 +116,7 @@ struct Basis {
     // device data
     DevBuf d_binom, d_adj_ptr, d_adj_nbr, d_adj_jxy, d_adj_jz, d_adj_jxy_f, d_u, d_xyz;
     std::vector<DevBuf> d_sigma, d_stab, d_pidx;
+    DevBuf d_ph64, d_ph32;                  // S x N per-site phase tables (k-sectors)
     DevBuf d_secs, d_tile0, d_chunk0;
     LatView lv{};
     std::vector<SecView> secs;

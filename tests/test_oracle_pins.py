@@ -407,3 +407,25 @@ def test_continued_fraction_equals_lorentzian_sum():
     assert abs(norm2 * (C[0] ** 2).sum() - norm2) < 1e-12
     # weights at the poles equal the spectral weights
     assert abs((norm2 * C[0] ** 2).max() - w.max()) < 1e-10
+
+
+def test_row_terms_without_sigma_equal_dense_rows():
+    """The list-free row of Alg. 9 (Alg. 7 and Alg. 5 per hop target) equals
+    the corresponding row of the dense Alg. 8 matrix."""
+    for dims, nd, K in (((4, 3, 1), 3, (1, 2, 0)), ((3, 3, 2), 3, (0, 1, 1)), ((8, 1, 1), 3, (3, 0, 0))):
+        spec = qi.hypercubic(dims, Jz=0.7)
+        lat = olat(spec)
+        sec = orc.mk_list(lat, nd, K)
+        H = orc.dense_k(sec)
+        index = {int(a): i for i, a in enumerate(sec.sigma1)}
+        for i, a in enumerate(sec.sigma1):
+            dg, tgt, cf = orc.row_terms_k(lat, nd, K, int(a))
+            row = np.zeros(sec.dim, complex)
+            row[i] += dg
+            for t, c in zip(tgt, cf):
+                row[index[int(t)]] += c
+            np.testing.assert_allclose(row, H[i], atol=1e-13)
+            assert abs(orc.check_state(lat, nd, K, int(a)) - sec.Nak[i]) < 1e-12
+        # a non-representative is rejected
+        a_non = next(a for a in range(1, orc.binom(spec.n_sites, nd) + 1) if a not in index)
+        assert orc.row_terms_k(lat, nd, K, a_non) is None
