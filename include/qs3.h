@@ -150,6 +150,19 @@ int qs3_lanczos(qs3_basis_t b, const qs3_solve_opts *o, double *evals, void *eve
 int qs3_trlanczos(qs3_basis_t b, const qs3_solve_opts *o, double *evals, void *evecs, qs3_solve_info *info,
                   void *stream);
 
+/* Lowest eigenpair of every sector of n independent bases (different
+ * lattices, N_down and momenta), solved concurrently with the options of
+ * qs3_lanczos: host workers each drive their own CUDA stream, take the
+ * instances largest first, and start one only when its Lanczos storage fits
+ * the device's free memory next to those in flight.  evals: host, the
+ * instances' sectors one after another (sum of n_sectors doubles).  evecs:
+ * NULL or n device pointers (each NULL or an fp64 vector of that basis'
+ * total dimension).  infos: NULL or n entries.  max_concurrent <= 0 means 16.
+ * Returns the first failure (text in qs3_last_error), NOT_CONVERGED if any
+ * instance did not converge. */
+int qs3_batch_solve(int32_t n, const qs3_basis_t *bases, const qs3_solve_opts *o, double *evals,
+                    void *const *evecs, qs3_solve_info *infos, int32_t max_concurrent);
+
 /* Two-point functions of a state gs (device, fp64: F64 on a U(1)-only basis,
  * C128 otherwise) living in sector s of b (Sec. "Calculating expectation
  * values").  For k-sectors the translation-symmetrised operators are used, so

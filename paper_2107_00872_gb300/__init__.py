@@ -232,6 +232,25 @@ def hphi(basis: Basis, phi, psi=None, stream=None):
     return basis.hphi(phi, psi, stream)
 
 
+def batch_solve(bases: list, opts: SolveOpts | None = None, max_concurrent: int = 16):
+    """Lowest eigenvalue of every sector of many independent bases, solved
+    concurrently (qs3_batch_solve).  Returns (list of per-basis eigenvalue
+    arrays, list of info dicts, status name)."""
+    n = len(bases)
+    o = (opts or SolveOpts()).c()
+    tot = sum(b.n_sectors for b in bases)
+    evals = np.zeros(max(tot, 1), np.float64)
+    hs = (ctypes.c_void_p * max(n, 1))(*[b.handle for b in bases])
+    infos = (_abi.qs3_solve_info * max(n, 1))()
+    st = load().qs3_batch_solve(n, hs, ctypes.byref(o), _ptr(evals), None, infos, int(max_concurrent))
+    check(st, "qs3_batch_solve", allow=(-6,))
+    out, k = [], 0
+    for b in bases:
+        out.append(evals[k:k + b.n_sectors].copy())
+        k += b.n_sectors
+    return out, [_info_dict(infos[i]) for i in range(n)], _abi.STATUS.get(st, st)
+
+
 def smq(src: Basis, s_src: int, phi, dst: Basis, s_dst: int, Q, psi=None, stream=None):
     """S^-_q phi (Alg. 11, pull form) from sector s_src of src into sector s_dst of dst."""
     torch = _torch()

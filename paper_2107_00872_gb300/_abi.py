@@ -45,6 +45,7 @@ SIGNATURES = {
     "qs3_hphi": ([P, I32, P, P, P], I32),
     "qs3_lanczos": ([P, P, P, P, P, P], I32),
     "qs3_trlanczos": ([P, P, P, P, P, P], I32),
+    "qs3_batch_solve": ([I32, P, P, P, P, P, I32], I32),
     "qs3_correlations": ([P, I32, P, I32, P, P, P, P, I32, P, P, P, P], I32),
     "qs3_smq": ([P, I32, P, P, I32, P, P, P], I32),
     "qs3_smq_noalloc": ([P, I32, P, P, I32, P, P, P], I32),

@@ -73,12 +73,14 @@ int DevBuf::upload(const void *src, size_t bytes) {
 }
 
 // must match carve() in qs3_hphi.cu: binomial rows 0..nd+2, coordinates (k
-// only), sqrt table (18 doubles)
+// only), sqrt table (18 doubles), the current sector's phases (k only)
 size_t row_kernel_smem(const Basis &B, int /*extra_nd*/) {
     size_t s = (size_t)(B.nd + 3) * (B.N + 1) * sizeof(uint64_t);
     if (B.has_k) s += (size_t)B.N * sizeof(uint32_t);
     s = (s + 15) & ~(size_t)15;
     s += 18 * sizeof(double);
+    s = (s + 15) & ~(size_t)15;
+    if (B.has_k) s += (size_t)B.N * 2 * sizeof(double);
     return s;
 }
 
@@ -199,7 +201,7 @@ static int build_reps_nd(Basis &B, int s) {
     QS3_CUDA(cudaMemcpy(hb.data(), B.d_binom.p, hb.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     const uint64_t nc = hb[(size_t)(ND - 1) * (B.N + 1) + (B.N - 1)];
     const size_t smem = (size_t)(B.nd + 3) * (B.N + 1) * 8 + (size_t)B.N * 4;
-    QS3_CUDA(cudaFuncSetAttribute(k_enum_reps<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    QS3_CUDA(cudaFuncSetAttribute(k_enum_reps<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
     DevBuf cnt;
     QS3_TRY(cnt.alloc(sizeof(unsigned long long)));
     QS3_CUDA(cudaMemset(cnt.p, 0, sizeof(unsigned long long)));
@@ -241,7 +243,7 @@ static int build_reps_nd(Basis &B, int s) {
     QS3_TRY(pidx.alloc(((size_t)np + 1) * 4));
     if (d > 0) {
         const size_t sm2 = (size_t)(B.nd + 3) * (B.N + 1) * 8;
-        QS3_CUDA(cudaFuncSetAttribute(k_prefix<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+        QS3_CUDA(cudaFuncSetAttribute(k_prefix<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
         int g2 = (int)std::min<uint64_t>((d + 255) / 256, (uint64_t)nsm * 8);
         k_prefix<ND><<<g2, 256, sm2>>>(B.lv, kout.as<uint64_t>(), d, P.as<uint32_t>());
         QS3_LAUNCHED();
@@ -425,6 +427,9 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     QS3_TRY(B.d_adj_jz.upload(ajz.data(), ajz.size() * 8));
     QS3_TRY(B.d_adj_jxy_f.upload(ajxyf.data(), ajxyf.size() * 4));
     QS3_TRY(B.d_u.upload(u.data(), u.size() * 8));
+    std::vector<float> uf(u.begin(), u.end()), ajzf(ajz.begin(), ajz.end());
+    QS3_TRY(B.d_u_f.upload(uf.data(), uf.size() * 4));
+    QS3_TRY(B.d_adj_jz_f.upload(ajzf.data(), ajzf.size() * 4));
     std::vector<uint32_t> xyz(N);
     for (int r = 0; r < N; ++r) {
         int x = r % B.L[0], y = (r / B.L[0]) % B.L[1], z = r / (B.L[0] * B.L[1]);
@@ -450,6 +455,9 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     L.adj_jxy_f = B.d_adj_jxy_f.as<float>();
     L.u = B.d_u.as<double>();
     L.c0 = c0;
+    L.c0f = (float)c0;
+    L.u_f = B.d_u_f.as<float>();
+    L.adj_jz_f = B.d_adj_jz_f.as<float>();
     L.xyz = B.d_xyz.as<uint32_t>();
 
     // sectors

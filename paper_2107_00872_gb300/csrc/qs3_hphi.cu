@@ -16,6 +16,7 @@
 //     the two-level index over sigma (k-sectors, Alg. 7-9);
 //   - accumulate in the vector's precision (fp32 or fp64), write psi once.
 #include <algorithm>
+#include <atomic>
 
 #include "qs3_internal.cuh"
 
@@ -60,10 +61,11 @@ struct SmemLayout {
     uint64_t *sC;
     uint32_t *sxyz;
     void *snorm;    // sqrt table: [0..8] sqrt(s), [9..17] 1/sqrt(s)
+    void *sph;      // k-sectors: the current sector's per-site phases (vector precision)
 };
 
 // layout (must match row_kernel_smem): binomial rows 0..nd+2 | coordinates
-// (k only) | sqrt table
+// (k only) | sqrt table | per-site phases (k only)
 __device__ __forceinline__ SmemLayout carve(const LatView &L, unsigned char *smem) {
     SmemLayout s;
     s.sC = (uint64_t *)smem;
@@ -71,8 +73,21 @@ __device__ __forceinline__ SmemLayout carve(const LatView &L, unsigned char *sme
     size_t off = (size_t)(L.nd + 3) * L.np1 * 8 + (L.has_k ? (size_t)L.N * 4 : 0);
     off = (off + 15) & ~(size_t)15;
     s.snorm = smem + off;
+    off += 18 * sizeof(double);
+    off = (off + 15) & ~(size_t)15;
+    s.sph = smem + off;
     return s;
 }
+
+template <typename R> __device__ __forceinline__ R diag_c0(const LatView &L);
+template <> __device__ __forceinline__ double diag_c0<double>(const LatView &L) { return L.c0; }
+template <> __device__ __forceinline__ float diag_c0<float>(const LatView &L) { return L.c0f; }
+template <typename R> __device__ __forceinline__ R diag_u(const LatView &L, int i);
+template <> __device__ __forceinline__ double diag_u<double>(const LatView &L, int i) { return __ldg(L.u + i); }
+template <> __device__ __forceinline__ float diag_u<float>(const LatView &L, int i) { return __ldg(L.u_f + i); }
+template <typename R> __device__ __forceinline__ R diag_jz(const LatView &L, int q);
+template <> __device__ __forceinline__ double diag_jz<double>(const LatView &L, int q) { return __ldg(L.adj_jz + q); }
+template <> __device__ __forceinline__ float diag_jz<float>(const LatView &L, int q) { return __ldg(L.adj_jz_f + q); }
 
 template <typename CT> __device__ __forceinline__ const CT *phase_table(const SecView &sv);
 template <> __device__ __forceinline__ const double2 *phase_table<double2>(const SecView &sv) { return sv.ph64; }
@@ -95,13 +110,22 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
     }
     const R *jxy = jxy_table<VT>(L);
     __syncthreads();
-    // no block-wide synchronisation inside the loop: each warp moves on to its
-    // next tile independently (the per-sector phases are a global, L1-cached table)
+    // persistent grid striding over the tiles of all sectors (better balanced
+    // than contiguous per-block ranges, measured); a block restages the phase
+    // table of its tile's sector when the sector changes
+    CT *ph = (CT *)sm.sph;
+    int cur = -1;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int s = (S == 1) ? 0 : sector_of_tile(tile0, S, t);
         if (active && !active[s]) continue;
         const SecView sv = secs[s];
-        const CT *ph = phase_table<CT>(sv);
+        if (KS && s != cur) {
+            __syncthreads();
+            const CT *g = phase_table<CT>(sv);
+            for (int i = threadIdx.x; i < L.N; i += blockDim.x) ph[i] = g[i];
+            __syncthreads();
+            cur = s;
+        }
         const uint64_t row = (uint64_t)(t - sv.tile0) * TILE + threadIdx.x;
         if (row >= sv.dim) continue;
         const uint64_t rank = KS ? __ldg(sv.sigma + row) : row;
@@ -115,13 +139,17 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
             st_row = sv.stab[row];
             rs = snorm[9 + st_row];
         }
-        double e = L.c0, dd = 0.0;
+        // diagonal in the vector precision: fp32 kernels keep off the fp64 unit
+        R e = diag_c0<R>(L), dd = 0;
         CT acc;
         acc.x = 0; acc.y = 0;
-#pragma unroll
+        // the k-sector hop body (with the representative search) stays rolled:
+        // unrolled N_down times it overflows the instruction cache (measured)
+        constexpr int UNR = KS ? 1 : ND;
+#pragma unroll UNR
         for (int m = 0; m < ND; ++m) {
-            const int i = c[m];
-            e += __ldg(L.u + i);
+            const int i = pick(c, m);
+            e += diag_u<R>(L, i);
             const int e0 = __ldg(L.adj_ptr + i), e1 = __ldg(L.adj_ptr + i + 1);
             for (int q = e0; q < e1; ++q) {
                 const int j = __ldg(L.adj_nbr + q);
@@ -129,7 +157,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
 #pragma unroll
                 for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
                 if (occ) {
-                    dd += __ldg(L.adj_jz + q);
+                    dd += diag_jz<R>(L, q);
                     continue;
                 }
                 int tt[ND];
@@ -137,8 +165,16 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
                 for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
                 const R jh = (R)0.5 * __ldg(jxy + q);
                 if constexpr (!KS) {
-                    sort_net(tt);
-                    const uint64_t r2 = rank_of(tt, sm.sC, L.np1);
+                    // j keeps position m when it stays between the neighbours of
+                    // c_m: only the m-th term of the rank changes
+                    const bool inplace = (m == 0 || j > c[m > 0 ? m - 1 : 0]) && (m == ND - 1 || j < c[m + 1 < ND ? m + 1 : m]);
+                    uint64_t r2;
+                    if (inplace) {
+                        r2 = rank - sm.sC[(m + 1) * L.np1 + c[m]] + sm.sC[(m + 1) * L.np1 + j];
+                    } else {
+                        sort_net(tt);
+                        r2 = rank_of(tt, sm.sC, L.np1);
+                    }
                     CT cf;
                     cf.x = jh; cf.y = 0;
                     acc_add(acc, cf, ph_in[r2]);
@@ -158,7 +194,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
             }
         }
         CT dg;
-        dg.x = (R)(e + 0.5 * dd);
+        dg.x = e + (R)0.5 * dd;
         dg.y = 0;
         acc_add(acc, dg, x0);
         store(psi + sv.off + row, acc);
@@ -226,38 +262,45 @@ __global__ void k_diag0(double c0, uint64_t n, const VT *__restrict__ phi, VT *_
     }
 }
 
-static int g_nsm = 0;
+static std::atomic<int> g_nsm{0};
 
 static int num_sms() {
-    if (!g_nsm) {
+    int n = g_nsm.load(std::memory_order_relaxed);
+    if (!n) {
         int dev = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (g_nsm <= 0) g_nsm = 1;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+        g_nsm.store(n, std::memory_order_relaxed);
     }
-    return g_nsm;
+    return n;
 }
 
+// persistent grid: resident blocks per SM x SMs, capped by the tile count.
+// cache packs (smem + 1) << 32 | blocks per SM, so concurrent callers read a
+// consistent pair; the shared-memory attribute is always MAX_DYN_SMEM.
 template <typename KF>
-static int launch_rows(KF kern, Basis &B, size_t smem, int &cached_blocks, cudaStream_t st, int *grid_out) {
-    if (cached_blocks <= 0) {
-        QS3_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        int nb = 0;
+static int launch_rows(KF kern, Basis &B, size_t smem, std::atomic<unsigned long long> &cache, int *grid_out) {
+    const unsigned long long c = cache.load(std::memory_order_acquire);
+    int nb;
+    if ((c >> 32) != (unsigned long long)smem + 1) {
+        QS3_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
         QS3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NTHREADS, smem));
-        cached_blocks = std::max(nb, 1);
+        nb = std::max(nb, 1);
+        cache.store(((unsigned long long)smem + 1) << 32 | (unsigned)nb, std::memory_order_release);
+    } else {
+        nb = (int)(c & 0xffffffffu);
     }
-    int grid = std::min(B.ntiles, cached_blocks * num_sms());
+    int grid = std::min(B.ntiles, nb * num_sms());
     *grid_out = std::max(grid, 1);
     return QS3_OK;
 }
 
 template <int ND, typename VT, bool KS>
 static int hphi_nd(Basis &B, const void *phi, void *psi, cudaStream_t st, const int *active) {
-    static int cached = 0;
-    static size_t cached_smem = 0;
-    if (cached_smem != B.smem_bytes) { cached = 0; cached_smem = B.smem_bytes; }
+    static std::atomic<unsigned long long> cache{0};
     int grid = 1;
-    QS3_TRY(launch_rows(k_hphi<ND, VT, KS>, B, B.smem_bytes, cached, st, &grid));
+    QS3_TRY(launch_rows(k_hphi<ND, VT, KS>, B, B.smem_bytes, cache, &grid));
     if (B.ntiles == 0) return QS3_OK;
     k_hphi<ND, VT, KS><<<grid, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S,
                                                               B.ntiles, (const VT *)phi, (VT *)psi, active);
@@ -312,11 +355,9 @@ int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t
 
 template <int ND, bool KS>
 static int count_nd(Basis &B, unsigned long long *d_out) {
-    static int cached = 0;
-    static size_t cached_smem = 0;
-    if (cached_smem != B.smem_bytes) { cached = 0; cached_smem = B.smem_bytes; }
+    static std::atomic<unsigned long long> cache{0};
     int grid = 1;
-    QS3_TRY(launch_rows(k_count<ND, KS>, B, B.smem_bytes, cached, 0, &grid));
+    QS3_TRY(launch_rows(k_count<ND, KS>, B, B.smem_bytes, cache, &grid));
     k_count<ND, KS><<<grid, NTHREADS, B.smem_bytes>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S,
                                                        B.ntiles, d_out);
     QS3_LAUNCHED();

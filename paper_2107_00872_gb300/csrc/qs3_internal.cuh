@@ -16,10 +16,15 @@ constexpr int MAXND = QS3_MAX_NDOWN;
 constexpr int TILE = 256;          // rows per tile (one thread per row)
 constexpr int NTHREADS = 256;
 constexpr int BROWS = 2048;        // rows per chunk of the vector kernels (8 per thread)
+// every kernel with dynamic shared memory gets this one limit (bases larger
+// than it are rejected at creation), so concurrent host threads setting the
+// attribute never disagree
+constexpr int MAX_DYN_SMEM = 200 * 1024;
 
 // ------------------------------------------------------------------ errors
 int set_err(int code, const char *fmt, ...);
 void clear_err();
+const char *last_err();
 
 #define QS3_CUDA(call)                                                                             \
     do {                                                                                           \
@@ -81,6 +86,9 @@ struct LatView {
     const float *adj_jxy_f;       // fp32 copy of adj_jxy
     const double *u;              // N: -(1/2) sum_j Jz_ij + h_i
     double c0;                    // sum_b Jz_b / 4 - (1/2) sum_i h_i
+    const float *u_f;             // fp32 copies of u, c0 and adj_jz for the fp32 kernels
+    float c0f;
+    const float *adj_jz_f;
     const uint32_t *xyz;          // N: x | y << 11 | z << 22
 };
 
@@ -115,6 +123,7 @@ struct Basis {
     bool has_h = false;
     // device data
     DevBuf d_binom, d_adj_ptr, d_adj_nbr, d_adj_jxy, d_adj_jz, d_adj_jxy_f, d_u, d_xyz;
+    DevBuf d_u_f, d_adj_jz_f;
     std::vector<DevBuf> d_sigma, d_stab, d_pidx;
     DevBuf d_ph64, d_ph32;                  // S x N per-site phase tables (k-sectors)
     DevBuf d_secs, d_tile0, d_chunk0;
@@ -162,6 +171,36 @@ __device__ __forceinline__ uint64_t rank_of(const int (&c)[ND], const uint64_t *
     return r;
 }
 
+// largest x in [m-1, hi] with C(x, m) <= r (col = column m of the table).
+// C(x, m) ~ (x - (m-1)/2)^m / m! gives a float estimate of x; the exact table
+// values then correct it by a step or two, with a binary search as fallback,
+// so the result is exact for every r.
+__device__ __forceinline__ int col_search(const uint64_t *__restrict__ col, int m, int hi, uint64_t r) {
+    // log2(m!) for m = 0..8
+    constexpr float lf[9] = {0.f, 0.f, 1.f, 2.5849625f, 4.5849625f, 6.9068906f, 9.4918531f, 12.299208f, 15.299208f};
+    int x = m - 1;
+    if (r > 0) {
+        // uint64 -> float through two 32-bit halves (a 64-bit conversion would use the fp64 unit)
+        const float rf = (float)(uint32_t)(r >> 32) * 4294967296.f + (float)(uint32_t)r;
+        const float e = exp2f((__log2f(rf) + lf[m]) / (float)m) + 0.5f * (float)(m - 1);
+        x = (int)e;
+    }
+    x = max(m - 1, min(x, hi));
+#pragma unroll 1
+    for (int it = 0; it < 3 && x < hi && col[x + 1] <= r; ++it) ++x;
+#pragma unroll 1
+    for (int it = 0; it < 3 && col[x] > r; ++it) --x;
+    if (col[x] > r || (x < hi && col[x + 1] <= r)) {
+        int lo = m - 1, h = hi;
+        while (lo < h) {
+            const int mid = (lo + h + 1) >> 1;
+            if (col[mid] <= r) lo = mid; else h = mid - 1;
+        }
+        x = lo;
+    }
+    return x;
+}
+
 // inverse of rank_of (Alg. 1): greedy largest-first column search
 template <int ND>
 __device__ __forceinline__ void unrank(uint64_t r, const uint64_t *__restrict__ sC, int np1, int (&c)[ND]) {
@@ -169,14 +208,10 @@ __device__ __forceinline__ void unrank(uint64_t r, const uint64_t *__restrict__ 
 #pragma unroll
     for (int m = ND; m >= 2; --m) {
         const uint64_t *col = sC + m * np1;
-        int lo = m - 1, h = hi;
-        while (lo < h) {
-            int mid = (lo + h + 1) >> 1;
-            if (col[mid] <= r) lo = mid; else h = mid - 1;
-        }
-        c[m - 1] = lo;
-        r -= col[lo];
-        hi = lo - 1;
+        const int x = col_search(col, m, hi, r);
+        c[m - 1] = x;
+        r -= col[x];
+        hi = x - 1;
     }
     if (ND >= 1) c[0] = (int)r;
 }

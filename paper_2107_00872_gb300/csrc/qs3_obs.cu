@@ -344,13 +344,13 @@ static int grid_for(uint64_t n) {
 template <int ND>
 static int corr_u1_nd(Basis &B, const double *phi, bool pm, double *G, double2 *M, double *nrm, cudaStream_t st) {
     const size_t sm1 = (size_t)(B.nd + 3) * (B.N + 1) * 8 + (size_t)(B.N + 1) * 8;
-    QS3_CUDA(cudaFuncSetAttribute(k_occ_u1<ND, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+    QS3_CUDA(cudaFuncSetAttribute(k_occ_u1<ND, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
     const int g = grid_for(B.total);
     k_occ_u1<ND, double><<<g, NTHREADS, sm1, st>>>(B.lv, B.total, phi, 0, G, nrm);
     QS3_LAUNCHED();
     if (pm) {
         const size_t sm2 = (size_t)(B.nd + 3) * (B.N + 1) * 8;
-        QS3_CUDA(cudaFuncSetAttribute(k_spsm_u1<ND, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+        QS3_CUDA(cudaFuncSetAttribute(k_spsm_u1<ND, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
         k_spsm_u1<ND, double><<<g, NTHREADS, sm2, st>>>(B.lv, B.total, phi, M);
         QS3_LAUNCHED();
     }
@@ -362,7 +362,7 @@ static int corr_k_nd(Basis &B, int s, const double2 *phi, bool pm, double2 *hzz,
                      cudaStream_t st) {
     const size_t smem = obs_smem_bytes(B.nd + 3, B.N, B.L, true);
     if (smem > 200 * 1024) return set_err(QS3_ERR_OVERFLOW, "correlation tables need %zu bytes of shared memory", smem);
-    QS3_CUDA(cudaFuncSetAttribute(k_corr_k<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    QS3_CUDA(cudaFuncSetAttribute(k_corr_k<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
     k_corr_k<ND><<<grid_for(B.dims[s]), NTHREADS, smem, st>>>(B.lv, B.secs[s], phi, pm ? 1 : 0, hzz, hpm, nrm);
     QS3_LAUNCHED();
     return QS3_OK;
@@ -378,11 +378,11 @@ static int smq_nd(Basis &S, int ss, Basis &Dd, int sd, const double2 *phs, const
         if (smem > 200 * 1024) return set_err(QS3_ERR_OVERFLOW, "S^-_q tables need %zu bytes of shared memory", smem);
         const double isn = 1.0 / std::sqrt((double)S.N);
         if (S.has_k) {
-            QS3_CUDA(cudaFuncSetAttribute(k_smq<ND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            QS3_CUDA(cudaFuncSetAttribute(k_smq<ND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
             k_smq<ND, true><<<grid_for(Dd.dims[sd]), NTHREADS, smem, st>>>(S.lv, S.secs[ss], Dd.secs[sd], phs, isn,
                                                                             phi, psi);
         } else {
-            QS3_CUDA(cudaFuncSetAttribute(k_smq<ND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            QS3_CUDA(cudaFuncSetAttribute(k_smq<ND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
             k_smq<ND, false><<<grid_for(Dd.dims[sd]), NTHREADS, smem, st>>>(S.lv, S.secs[ss], Dd.secs[sd], phs, isn,
                                                                              phi, psi);
         }

@@ -967,15 +967,16 @@ static int lanczos_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT
             }
         }
         if (any) {
-            // eigenvectors of the newly finished sectors: psi = sum_x c_x psi_x
-            std::vector<double> C((size_t)S * E.cap, 0.0);
+            // eigenvectors of the newly finished sectors: psi = sum_x c_x psi_x over
+            // the n computed vectors only (later slots are uninitialised memory)
+            std::vector<double> C((size_t)S * n, 0.0);
             for (int s = 0; s < S; ++s) {
                 if (!newly[s]) continue;
                 std::vector<double> c;
                 tri_eigvec(msize[s], &a[(size_t)s * E.cap], &b[(size_t)s * E.cap], R.e[s], c);
-                for (int k = 0; k < msize[s]; ++k) C[(size_t)s * E.cap + k] = c[k];
+                for (int k = 0; k < msize[s]; ++k) C[(size_t)s * n + k] = c[k];
             }
-            QS3_TRY(E.template combine<typename Wide<VT>::T>(out, B.total, E.cap, 1, C, newly));
+            QS3_TRY(E.template combine<typename Wide<VT>::T>(out, B.total, n, 1, C, newly));
             for (int s = 0; s < S; ++s)
                 if (newly[s]) E.h_active[s] = 0;
             QS3_TRY(E.push_active());
@@ -1018,15 +1019,15 @@ static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T
         bool any = false;
         for (int v : done) any |= v != 0;
         if (!any) return QS3_OK;
-        std::vector<double> C((size_t)S * E.cap * NE, 0.0);
+        std::vector<double> C((size_t)S * NM * NE, 0.0);     // m <= N_M vectors per sector
         for (int s = 0; s < S; ++s) {
             if (!done[s]) continue;
             const int m = msize[s];
             for (int x = 0; x < m; ++x)
-                for (int y = 0; y < NE && y < m; ++y) C[(size_t)s * E.cap * NE + x * NE + y] = Cm[s][(size_t)x * m + y];
+                for (int y = 0; y < NE && y < m; ++y) C[(size_t)s * NM * NE + x * NE + y] = Cm[s][(size_t)x * m + y];
             for (int y = 0; y < NE; ++y) R.e[(size_t)s * NE + y] = y < m ? ev[s][y] : NAN;
         }
-        QS3_TRY(E.template combine<WT>(out, B.total, E.cap, NE, C, done));
+        QS3_TRY(E.template combine<WT>(out, B.total, NM, NE, C, done));
         for (int s = 0; s < S; ++s)
             if (done[s]) E.h_active[s] = 0;
         return E.push_active();
@@ -1383,3 +1384,114 @@ int dsf_run(Basis &S, int ss, const void *gs, double e0, Basis &Dd, int nq, cons
 }
 
 }  // namespace qs3
+
+// ------------------------------------------------------ batched instances
+// Many independent, uneven instances (different lattices, N_down, momenta):
+// a pool of host workers, each driving its own non-blocking CUDA stream, takes
+// the instances largest first and runs the batched-sector Lanczos of each; the
+// GPU overlaps the instances' kernels.  An instance starts only when its
+// Lanczos storage fits the memory budget next to the ones in flight (a single
+// instance larger than the budget runs alone).
+#include <condition_variable>
+#include <mutex>
+#include <thread>
+
+namespace qs3 {
+
+static size_t solve_mem_estimate(const Basis &B, const qs3_solve_opts &o) {
+    const size_t ev = o.precision == QS3_F32 ? (B.has_k ? 8 : 4) : (B.has_k ? 16 : 8);
+    const size_t ev64 = B.has_k ? 16 : 8;
+    const size_t cap = (size_t)std::max(2, o.n_max) + 1;
+    size_t m = cap * B.total * ev + 2 * B.total * ev64 + (size_t)std::max(B.nchunks, 1) * cap * 16;
+    if (o.precision == QS3_F32) m += cap * B.total * ev64;   // the fp64 refinement
+    return m;
+}
+
+static int batch_solve(int n, const qs3_basis_t *bases, const qs3_solve_opts &o, double *evals, void *const *evecs,
+                       qs3_solve_info *infos, int maxc) {
+    std::vector<size_t> off(n + 1, 0), mem(n);
+    for (int i = 0; i < n; ++i) {
+        if (!bases[i]) return set_err(QS3_ERR_INVALID_ARG, "basis %d is NULL", i);
+        off[i + 1] = off[i] + bases[i]->B.S;
+        mem[i] = solve_mem_estimate(bases[i]->B, o);
+        uint64_t nz;
+        QS3_TRY(count_nnz(bases[i]->B, &nz));        // on the calling thread, before the workers start
+    }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return mem[a] > mem[b]; });
+    int dev = 0;
+    QS3_CUDA(cudaGetDevice(&dev));
+    size_t freeb = 0, totb = 0;
+    QS3_CUDA(cudaMemGetInfo(&freeb, &totb));
+    const size_t budget = (size_t)(0.85 * (double)freeb);
+    std::mutex mu;
+    std::condition_variable cv;
+    size_t inflight = 0;
+    int nrun = 0, next = 0, first_err = QS3_OK;
+    std::string err_text;
+    std::vector<qs3_solve_info> inf(n);
+    std::vector<int> status(n, QS3_OK);
+    auto worker = [&]() {
+        cudaSetDevice(dev);
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            std::lock_guard<std::mutex> lk(mu);
+            if (first_err == QS3_OK) { first_err = QS3_ERR_CUDA; err_text = "stream creation failed"; }
+            return;
+        }
+        for (;;) {
+            int i;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                if (next >= n || first_err != QS3_OK) break;
+                i = order[next];
+                cv.wait(lk, [&] { return first_err != QS3_OK || nrun == 0 || inflight + mem[i] <= budget; });
+                if (first_err != QS3_OK) break;
+                if (order[next] != i) continue;      // another worker took it meanwhile
+                ++next;
+                inflight += mem[i];
+                ++nrun;
+            }
+            Basis &B = bases[i]->B;
+            qs3_solve_info info{};
+            int s = B.has_k ? lanczos_entry<float2, double2>(B, o, evals + off[i], evecs ? evecs[i] : nullptr, &info, st)
+                            : lanczos_entry<float, double>(B, o, evals + off[i], evecs ? evecs[i] : nullptr, &info, st);
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                inf[i] = info;
+                status[i] = s;
+                inflight -= mem[i];
+                --nrun;
+                if (s != QS3_OK && s != QS3_ERR_NOT_CONVERGED && first_err == QS3_OK) {
+                    first_err = s;
+                    err_text = last_err();
+                }
+            }
+            cv.notify_all();
+        }
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    };
+    const int nw = std::max(1, std::min(n, maxc > 0 ? maxc : 16));
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
+    for (auto &t : pool) t.join();
+    if (infos)
+        for (int i = 0; i < n; ++i) infos[i] = inf[i];
+    if (first_err != QS3_OK) return set_err(first_err, "batch: %s", err_text.c_str());
+    for (int i = 0; i < n; ++i)
+        if (status[i] == QS3_ERR_NOT_CONVERGED) return set_err(QS3_ERR_NOT_CONVERGED, "batch: instance %d did not converge", i);
+    return QS3_OK;
+}
+
+}  // namespace qs3
+
+extern "C" int qs3_batch_solve(int32_t n, const qs3_basis_t *bases, const qs3_solve_opts *o, double *evals,
+                               void *const *evecs, qs3_solve_info *infos, int32_t max_concurrent) {
+    qs3::clear_err();
+    if (n < 0 || (n > 0 && (!bases || !evals))) return qs3::set_err(QS3_ERR_INVALID_ARG, "NULL argument");
+    QS3_TRY(qs3::check_opts(o));
+    if (n == 0) return QS3_OK;
+    return qs3::batch_solve(n, bases, *o, evals, evecs, infos, max_concurrent);
+}
