@@ -87,9 +87,10 @@ __device__ __forceinline__ double2 warp_sum2(double2 v) {
     return v;
 }
 
-// part[c * m + j] = sum over the chunk's rows of conj(V_{j0+j}) w
+// part[c * m + j] = sum over the chunk's rows of conj(V_{j0+j}) w; vector j
+// starts at V + j * ld (ld may be negative)
 template <typename VT>
-__global__ void __launch_bounds__(NTHREADS) k_mdot(const VT *__restrict__ V, uint64_t D, int j0, int m,
+__global__ void __launch_bounds__(NTHREADS) k_mdot(const VT *__restrict__ V, int64_t ld, int j0, int m,
                                                    const VT *__restrict__ w, const SecView *__restrict__ secs,
                                                    const int *__restrict__ chunk0, int S,
                                                    const int *__restrict__ active, double2 *__restrict__ part) {
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(NTHREADS) k_mdot(const VT *__restrict__ V, uin
     for (int jb = 0; jb < m; jb += JB) {
         const int nj = min(JB, m - jb);
         for (int jj = 0; jj < nj; ++jj) {
-            const VT *vj = V + (uint64_t)(j0 + jb + jj) * D + ci.base;
+            const VT *vj = V + (int64_t)(j0 + jb + jj) * ld + ci.base;
             double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
@@ -155,7 +156,7 @@ __global__ void k_reduce(const double2 *__restrict__ part, int m, const int *__r
 
 // w -= sum_j V_{j0+j} coef[s][j]; optionally part[c] = sum |w|^2 over the chunk
 template <typename VT>
-__global__ void __launch_bounds__(NTHREADS) k_mupdate(VT *__restrict__ w, const VT *__restrict__ V, uint64_t D,
+__global__ void __launch_bounds__(NTHREADS) k_mupdate(VT *__restrict__ w, const VT *__restrict__ V, int64_t ld,
                                                       int j0, int m, const double2 *__restrict__ coef, int ldc,
                                                       const SecView *__restrict__ secs,
                                                       const int *__restrict__ chunk0, int S,
@@ -172,9 +173,9 @@ __global__ void __launch_bounds__(NTHREADS) k_mupdate(VT *__restrict__ w, const 
         const int r = threadIdx.x + k * NTHREADS;
         if (r < ci.n) {
             double2 acc = ld2(w + ci.base + r);
-            const VT *vp = V + (uint64_t)j0 * D + ci.base + r;
+            const VT *vp = V + (int64_t)j0 * ld + ci.base + r;
             for (int j = 0; j < m; ++j) {
-                const double2 a = ld2(vp + (uint64_t)j * D), c = sco[j];
+                const double2 a = ld2(vp + (int64_t)j * ld), c = sco[j];
                 acc.x -= a.x * c.x - a.y * c.y;
                 acc.y -= a.x * c.y + a.y * c.x;
             }
@@ -473,11 +474,18 @@ __global__ void __launch_bounds__(NTHREADS) k_combine(OT *__restrict__ out, uint
                                                       const int *__restrict__ chunk0, int S,
                                                       const int *__restrict__ mask) {
     extern __shared__ double sc[];
+    __shared__ int nx;
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
     if (mask && !mask[ci.s]) return;
     const double *Cs = C + (uint64_t)ci.s * ldc;
-    for (int i = threadIdx.x; i < nin * nout; i += blockDim.x) sc[i] = Cs[i];
+    if (threadIdx.x == 0) nx = 0;
     __syncthreads();
+    for (int i = threadIdx.x; i < nin * nout; i += blockDim.x) {
+        sc[i] = Cs[i];
+        if (Cs[i] != 0.0) atomicMax(&nx, i / nout + 1);
+    }
+    __syncthreads();
+    nin = nx;      // vectors past the sector's last nonzero coefficient may be unwritten
 #pragma unroll 1
     for (int k = 0; k < RPT; ++k) {
         const int r = threadIdx.x + k * NTHREADS;
@@ -498,6 +506,337 @@ __global__ void __launch_bounds__(NTHREADS) k_combine(OT *__restrict__ out, uint
 #pragma unroll
         for (int y = 0; y < MAXOUT; ++y)
             if (y < nout) st2(out + (uint64_t)y * ldo + ci.base + r, acc[y]);
+    }
+}
+
+// ------------------------------------ fp64 Lanczos vectors, double-float store
+// The Krylov basis of an fp64 solve is stored as double-float pairs: an
+// element v is kept as hi = fl32(v), lo = fl32(v - hi), 48 significant bits
+// in the same 8 bytes.  The Gram-Schmidt pass over all kept vectors (the
+// reorthogonalisation of Alg. 10) then runs on the fp32 units with
+// error-free products (fma) and two-sums; the fp64 unit -- a small fraction
+// of the fp32 rate on this GPU -- only sees one conversion per row and
+// kernel.  H psi_x and the three-term part of each step use exact fp64
+// copies of psi_{x-1}, psi_x, so alpha_x and beta_x are fp64 results; the
+// 2^-48 rounding of the stored basis only bounds how far below fp64 epsilon
+// the orthogonality of the basis can be pushed.
+template <typename VT> struct DfS { using T = VT; };     // fp32 vectors: stored as they are
+template <> struct DfS<double> { using T = float2; };    // (hi, lo)
+template <> struct DfS<double2> { using T = float4; };   // (re.hi, re.lo, im.hi, im.lo)
+
+__device__ __forceinline__ float4 ld_df(const float2 *p) { const float2 v = *p; return make_float4(v.x, v.y, 0.f, 0.f); }
+__device__ __forceinline__ float4 ld_df(const float4 *p) { return *p; }
+__device__ __forceinline__ float2 split_d(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+__device__ __forceinline__ float4 split2(double2 v) {
+    const float2 a = split_d(v.x), b = split_d(v.y);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st_df(float2 *p, float4 v) { *p = make_float2(v.x, v.y); }
+__device__ __forceinline__ void st_df(float4 *p, float4 v) { *p = v; }
+
+// acc += (ah + al)(bh + bl), dropping al*bl (2^-48 relative); acc is left
+// unnormalised (|lo| grows by at most a few ulp of hi per call)
+__device__ __forceinline__ void df_mac(dfl &acc, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float s = acc.hi + p;
+    const float bb = s - acc.hi;
+    const float t = (acc.hi - (s - bb)) + (p - bb);
+    acc.hi = s;
+    acc.lo += t + e;
+}
+__device__ __forceinline__ dfl df_norm(dfl a) {
+    const float s = a.hi + a.lo;
+    return {s, a.lo - (s - a.hi)};
+}
+__device__ __forceinline__ dfl df_sum(dfl a, dfl b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float t = (a.hi - (s - bb)) + (b.hi - bb);
+    return df_norm({s, t + a.lo + b.lo});
+}
+__device__ __forceinline__ dfl warp_sum_df(dfl a) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        dfl b;
+        b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+        b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+        a = df_sum(a, b);
+    }
+    return a;
+}
+
+// part[c * m + j] = conj(V_{j0+j}) . w over the chunk as double-float
+// (re.hi, re.lo, im.hi, im.lo); V double-float, w fp64.  Vectors go in groups
+// of 8: every thread leaves its partial sums in shared memory, then warp q
+// reduces vector q of the group (one shuffle tree per vector and block
+// instead of one per vector and warp).
+constexpr int GDF = NTHREADS / 32;
+template <typename VT>
+__global__ void __launch_bounds__(NTHREADS) k_mdot_df(const typename DfS<VT>::T *__restrict__ V, uint64_t D, int j0,
+                                                      int m, const VT *__restrict__ w,
+                                                      const SecView *__restrict__ secs,
+                                                      const int *__restrict__ chunk0, int S,
+                                                      const int *__restrict__ active, float4 *__restrict__ part) {
+    using ST = typename DfS<VT>::T;
+    __shared__ float4 red[GDF][NTHREADS];
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    float4 wv[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        wv[k] = (r < ci.n) ? split2(ld2(w + ci.base + r)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int jb = 0; jb < m; jb += GDF) {
+        const int nj = min(GDF, m - jb);
+        for (int jj = 0; jj < nj; ++jj) {
+            const ST *vj = V + (uint64_t)(j0 + jb + jj) * D + ci.base;
+            dfl re = {0.f, 0.f}, im = {0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int r = threadIdx.x + k * NTHREADS;
+                if (r < ci.n) {
+                    const float4 a = ld_df(vj + r), b = wv[k];
+                    // conj(a) b = (a.r b.r + a.i b.i) + i (a.r b.i - a.i b.r)
+                    df_mac(re, a.x, a.y, b.x, b.y);
+                    if (IsC<VT>::v) {
+                        df_mac(re, a.z, a.w, b.z, b.w);
+                        df_mac(im, a.x, a.y, b.z, b.w);
+                        df_mac(im, -a.z, -a.w, b.x, b.y);
+                    }
+                }
+            }
+            re = df_norm(re);
+            im = df_norm(im);
+            red[jj][threadIdx.x] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+        __syncthreads();
+        if (warp < nj) {
+            dfl tr = {0.f, 0.f}, ti = {0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < NTHREADS / 32; ++q) {
+                const float4 v = red[warp][lane + 32 * q];
+                tr = df_sum(tr, {v.x, v.y});
+                ti = df_sum(ti, {v.z, v.w});
+            }
+            tr = warp_sum_df(tr);
+            if (IsC<VT>::v) ti = warp_sum_df(ti);
+            if (lane == 0) part[(uint64_t)blockIdx.x * m + jb + warp] = make_float4(tr.hi, tr.lo, ti.hi, ti.lo);
+        }
+        __syncthreads();
+    }
+}
+
+// k_reduce for double-float chunk partials
+__global__ void k_reduce_df(const float4 *__restrict__ part, int m, const int *__restrict__ chunk0,
+                            const int *__restrict__ active, double2 *__restrict__ out, int ldo) {
+    const int j = blockIdx.x, s = blockIdx.y;
+    if (active && !active[s]) return;
+    __shared__ double2 red[NTHREADS / 32];
+    double2 acc = make_double2(0.0, 0.0);
+    for (int c = chunk0[s] + threadIdx.x; c < chunk0[s + 1]; c += blockDim.x) {
+        const float4 v = part[(uint64_t)c * m + j];
+        acc.x += (double)v.x + (double)v.y;
+        acc.y += (double)v.z + (double)v.w;
+    }
+    acc = warp_sum2(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int q = 0; q < NTHREADS / 32; ++q) { t.x += red[q].x; t.y += red[q].y; }
+        out[(uint64_t)s * ldo + j] = t;
+    }
+}
+
+// w -= sum_j V_{j0+j} coef[s][j], subtracted from the fp64 w; optionally
+// part[c] = sum |w|^2.  The sum u is formed in double-float over the stored
+// basis; when the sector's coefficients are all below 2^-40 |w| (wn2 = |w|^2
+// before this update; the second Gram-Schmidt pass, whose coefficients are
+// O(eps |w|)), u is formed in plain fp32 from the hi words instead: its
+// error, 2^-24 |u| <= 2^-24 * 2^-40 * sqrt(m) |w|, is below fp64 rounding of w.
+template <typename VT>
+__global__ void __launch_bounds__(NTHREADS) k_mupdate_df(VT *__restrict__ w, const typename DfS<VT>::T *__restrict__ V,
+                                                         uint64_t D, int j0, int m, const double2 *__restrict__ coef,
+                                                         int ldc, const SecView *__restrict__ secs,
+                                                         const int *__restrict__ chunk0, int S,
+                                                         const int *__restrict__ active,
+                                                         const double2 *__restrict__ wn2, double2 *__restrict__ part) {
+    using ST = typename DfS<VT>::T;
+    extern __shared__ float4 scf[];   // per j: split coefficient (re.hi, re.lo, im.hi, im.lo)
+    __shared__ double red[NTHREADS / 32];
+    __shared__ unsigned cbits;
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    if (threadIdx.x == 0) cbits = 0u;
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        const double2 c = coef[(uint64_t)ci.s * ldc + j];
+        scf[j] = split2(c);
+        atomicMax(&cbits, __float_as_uint((float)(c.x * c.x + c.y * c.y)));   // non-negative: bits order as values
+    }
+    __syncthreads();
+    const bool lite = wn2 && (double)__uint_as_float(cbits) <= 0x1p-80 * wn2[ci.s].x;
+    double2 u[RPT];
+    if (lite) {
+        float2 uf[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) uf[k] = make_float2(0.f, 0.f);
+        for (int j = 0; j < m; ++j) {
+            const float4 c = scf[j];
+            const ST *vj = V + (uint64_t)(j0 + j) * D + ci.base;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int r = threadIdx.x + k * NTHREADS;
+                if (r < ci.n) {
+                    const float4 a = ld_df(vj + r);
+                    uf[k].x = fmaf(a.x, c.x, uf[k].x);
+                    if (IsC<VT>::v) {
+                        uf[k].x = fmaf(-a.z, c.z, uf[k].x);
+                        uf[k].y = fmaf(a.x, c.z, uf[k].y);
+                        uf[k].y = fmaf(a.z, c.x, uf[k].y);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) u[k] = make_double2((double)uf[k].x, (double)uf[k].y);
+    } else {
+        dfl ur[RPT], ui[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) ur[k] = ui[k] = {0.f, 0.f};
+        for (int j = 0; j < m; ++j) {
+            const float4 c = scf[j];
+            const ST *vj = V + (uint64_t)(j0 + j) * D + ci.base;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int r = threadIdx.x + k * NTHREADS;
+                if (r < ci.n) {
+                    const float4 a = ld_df(vj + r);
+                    // u += a c: re += a.r c.r - a.i c.i ; im += a.r c.i + a.i c.r
+                    df_mac(ur[k], a.x, a.y, c.x, c.y);
+                    if (IsC<VT>::v) {
+                        df_mac(ur[k], -a.z, -a.w, c.z, c.w);
+                        df_mac(ui[k], a.x, a.y, c.z, c.w);
+                        df_mac(ui[k], a.z, a.w, c.x, c.y);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+            u[k] = make_double2((double)ur[k].hi + (double)ur[k].lo, (double)ui[k].hi + (double)ui[k].lo);
+    }
+    double nrm = 0.0;
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r < ci.n) {
+            double2 v = ld2(w + ci.base + r);
+            v.x -= u[k].x;
+            if (IsC<VT>::v) v.y -= u[k].y;
+            st2(w + ci.base + r, v);
+            nrm += v.x * v.x + v.y * v.y;
+        }
+    }
+    if (part) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < NTHREADS / 32; ++q) t += red[q];
+            part[blockIdx.x] = make_double2(t, 0.0);
+        }
+    }
+}
+
+// w *= inv[s]; out = double-float copy of the scaled w
+template <typename VT>
+__global__ void __launch_bounds__(NTHREADS) k_scale_split(VT *__restrict__ w, typename DfS<VT>::T *__restrict__ out,
+                                                          const double *__restrict__ inv,
+                                                          const SecView *__restrict__ secs,
+                                                          const int *__restrict__ chunk0, int S,
+                                                          const int *__restrict__ active) {
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    const double f = inv[ci.s];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r < ci.n) {
+            double2 v = ld2(w + ci.base + r);
+            v.x *= f;
+            v.y *= f;
+            st2(w + ci.base + r, v);
+            st_df(out + ci.base + r, split2(v));
+        }
+    }
+}
+
+__device__ __forceinline__ void st_comb(double *p, dfl re, dfl) { *p = (double)re.hi + (double)re.lo; }
+__device__ __forceinline__ void st_comb(double2 *p, dfl re, dfl im) {
+    *p = make_double2((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
+}
+__device__ __forceinline__ void st_comb(float2 *p, dfl re, dfl) { re = df_norm(re); *p = make_float2(re.hi, re.lo); }
+__device__ __forceinline__ void st_comb(float4 *p, dfl re, dfl im) {
+    re = df_norm(re);
+    im = df_norm(im);
+    *p = make_float4(re.hi, re.lo, im.hi, im.lo);
+}
+
+// out_y[r] = sum_x V_x[r] C[s][x][y] (y < nout <= 16) over a double-float
+// basis, for the rows of sectors with mask[s] != 0; OT is fp64 (a result) or
+// the double-float store itself (the thick restart)
+template <typename VT, typename OT>
+__global__ void __launch_bounds__(NTHREADS) k_combine_df(OT *__restrict__ out, uint64_t ldo,
+                                                         const typename DfS<VT>::T *__restrict__ V, uint64_t D,
+                                                         int nin, int nout, const double *__restrict__ C, int ldc,
+                                                         const SecView *__restrict__ secs,
+                                                         const int *__restrict__ chunk0, int S,
+                                                         const int *__restrict__ mask) {
+    extern __shared__ float2 scc[];
+    __shared__ int nx;
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (mask && !mask[ci.s]) return;
+    const double *Cs = C + (uint64_t)ci.s * ldc;
+    if (threadIdx.x == 0) nx = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nin * nout; i += blockDim.x) {
+        scc[i] = split_d(Cs[i]);
+        if (Cs[i] != 0.0) atomicMax(&nx, i / nout + 1);
+    }
+    __syncthreads();
+    nin = nx;      // vectors past the sector's last nonzero coefficient may be unwritten
+#pragma unroll 1
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r >= ci.n) continue;
+        dfl re[MAXOUT], im[MAXOUT];
+#pragma unroll
+        for (int y = 0; y < MAXOUT; ++y) re[y] = im[y] = {0.f, 0.f};
+#pragma unroll 4
+        for (int x = 0; x < nin; ++x) {
+            const float4 a = ld_df(V + (uint64_t)x * D + ci.base + r);
+#pragma unroll
+            for (int y = 0; y < MAXOUT; ++y)
+                if (y < nout) {
+                    const float2 c = scc[x * nout + y];
+                    df_mac(re[y], a.x, a.y, c.x, c.y);
+                    if (IsC<VT>::v) df_mac(im[y], a.z, a.w, c.x, c.y);
+                }
+        }
+#pragma unroll
+        for (int y = 0; y < MAXOUT; ++y)
+            if (y < nout) st_comb(out + (uint64_t)y * ldo + ci.base + r, re[y], im[y]);
     }
 }
 
@@ -710,23 +1049,35 @@ struct HphiStats {
 template <typename VT>
 struct Engine {
     using WT = typename Wide<VT>::T;       // fp64 vector type of the same kind
+    using ST = typename DfS<VT>::T;        // storage type of the Krylov basis
+    static constexpr bool DF = Is64<VT>::v;
     Basis &B;
     cudaStream_t st;
     HphiStats *stats;
     int cap = 0, nscr = 0;
     uint64_t D = 0;
-    DevBuf V, part, h1, h2, alpha, beta, nrm, inv, active;
+    DevBuf V, ring, part, h1, h2, alpha, beta, nrm, nrm1, inv, active;
+    int rp = 0, rc = 1, rw = 2;           // fp64 ring: psi_{x-1}, psi_x, work (DF only)
     std::vector<int> h_active;
     double brk;
 
-    Engine(Basis &b, cudaStream_t s, HphiStats *hs) : B(b), st(s), stats(hs) { brk = Is64<VT>::v ? 1e-12 : 1e-6; }
+    Engine(Basis &b, cudaStream_t s, HphiStats *hs) : B(b), st(s), stats(hs) { brk = DF ? 1e-12 : 1e-6; }
 
     qs3_dtype dtype() const {
         if (sizeof(VT) == 4) return QS3_F32;
-        if (sizeof(VT) == 8) return Is64<VT>::v ? QS3_F64 : QS3_C64;
+        if (sizeof(VT) == 8) return DF ? QS3_F64 : QS3_C64;
         return QS3_C128;
     }
-    VT *vec(int j) { return V.as<VT>() + (uint64_t)j * D; }
+    // stored basis vector j (slots cap .. cap + nscr - 1 are scratch)
+    ST *svec(int j) { return V.as<ST>() + (uint64_t)j * D; }
+    VT *rvec(int i) { return ring.as<VT>() + (uint64_t)i * D; }
+    // the vector H is applied to at step x, and where H psi_x goes
+    VT *hin(int x) {
+        if constexpr (DF) return rvec(rc); else return svec(x);
+    }
+    VT *hout(int x) {
+        if constexpr (DF) return rvec(rw); else return svec(x + 1);
+    }
     const SecView *secs() { return B.d_secs.as<SecView>(); }
     const int *c0() { return B.d_chunk0.as<int>(); }
     int *act() { return active.as<int>(); }
@@ -735,13 +1086,15 @@ struct Engine {
         cap = cap_;
         nscr = nscratch;
         D = B.total;
-        QS3_TRY(V.alloc((uint64_t)(cap + nscr) * D * sizeof(VT)));
+        QS3_TRY(V.alloc((uint64_t)(cap + nscr) * D * sizeof(ST)));
+        if (DF) QS3_TRY(ring.alloc(3 * D * sizeof(VT)));
         QS3_TRY(part.alloc((uint64_t)std::max(B.nchunks, 1) * cap * sizeof(double2)));
         QS3_TRY(h1.alloc((uint64_t)B.S * cap * sizeof(double2)));
         QS3_TRY(h2.alloc((uint64_t)B.S * cap * sizeof(double2)));
         QS3_TRY(alpha.alloc((uint64_t)B.S * cap * sizeof(double)));
         QS3_TRY(beta.alloc((uint64_t)B.S * cap * sizeof(double)));
         QS3_TRY(nrm.alloc((uint64_t)B.S * sizeof(double2)));
+        QS3_TRY(nrm1.alloc((uint64_t)B.S * sizeof(double2)));
         QS3_TRY(inv.alloc((uint64_t)B.S * sizeof(double)));
         QS3_TRY(active.alloc((uint64_t)B.S * sizeof(int)));
         QS3_CUDA(cudaMemsetAsync(alpha.p, 0, alpha.n, st));
@@ -761,56 +1114,89 @@ struct Engine {
     int grid() const { return std::max(B.nchunks, 1); }
 
     // reduce part[.. m] into out (S x ldo)
-    int reduce(int m, double2 *out, int ldo) {
+    int reduce(int m, double2 *out, int ldo, bool df = false) {
         dim3 g(m, B.S);
-        k_reduce<<<g, NTHREADS, 0, st>>>(part.as<double2>(), m, c0(), act(), out, ldo);
+        if (df) k_reduce_df<<<g, NTHREADS, 0, st>>>((const float4 *)part.p, m, c0(), act(), out, ldo);
+        else k_reduce<<<g, NTHREADS, 0, st>>>(part.as<double2>(), m, c0(), act(), out, ldo);
         QS3_LAUNCHED();
         return QS3_OK;
     }
+    // dot products / update against the stored basis vectors j0 .. j0 + m - 1
     int mdot(int j0, int m, const VT *w, double2 *out, int ldo) {
         if (B.nchunks == 0) return QS3_OK;
-        if constexpr (Is64<VT>::v)
-            k_mdot<VT><<<grid(), NTHREADS, 0, st>>>(V.as<VT>(), D, j0, m, w, secs(), c0(), B.S, act(), part.as<double2>());
+        if constexpr (DF)
+            k_mdot_df<VT><<<grid(), NTHREADS, 0, st>>>(V.as<ST>(), D, j0, m, w, secs(), c0(), B.S, act(),
+                                                       (float4 *)part.p);
         else
             k_mdot32<VT><<<grid(), NTHREADS, 0, st>>>(V.as<VT>(), D, j0, m, w, secs(), c0(), B.S, act(), part.as<double2>());
         QS3_LAUNCHED();
-        return reduce(m, out, ldo);
+        return reduce(m, out, ldo, DF);
     }
-    int mupdate(VT *w, int j0, int m, const double2 *cf, int ldc, bool norm) {
+    // nrm_out (optional): per-sector |w|^2 after the update; wn2 (DF, optional):
+    // |w|^2 before it, which lets small-coefficient updates run in plain fp32
+    int mupdate(VT *w, int j0, int m, const double2 *cf, int ldc, double2 *nrm_out, const double2 *wn2 = nullptr) {
         if (B.nchunks == 0) return QS3_OK;
-        if constexpr (Is64<VT>::v)
-            k_mupdate<VT><<<grid(), NTHREADS, m * sizeof(double2), st>>>(w, V.as<VT>(), D, j0, m, cf, ldc, secs(), c0(),
-                                                                         B.S, act(), norm ? part.as<double2>() : nullptr);
+        double2 *pp = nrm_out ? part.as<double2>() : nullptr;
+        if constexpr (DF)
+            k_mupdate_df<VT><<<grid(), NTHREADS, m * sizeof(float4), st>>>(w, V.as<ST>(), D, j0, m, cf, ldc, secs(), c0(),
+                                                                         B.S, act(), wn2, pp);
         else
             k_mupdate32<VT><<<grid(), NTHREADS, m * sizeof(float4), st>>>(w, V.as<VT>(), D, j0, m, cf, ldc, secs(), c0(),
-                                                                          B.S, act(), norm ? part.as<double2>() : nullptr);
+                                                                          B.S, act(), pp);
         QS3_LAUNCHED();
-        if (norm) return reduce(1, nrm.as<double2>(), 1);
+        if (nrm_out) return reduce(1, nrm_out, 1);
         return QS3_OK;
     }
-    // normalise vector j per sector
-    int normalise(int j) {
+    // the same against the exact fp64 psi_{x-1}, psi_x of the ring (DF only);
+    // h gets the coefficients at h + j0, j0 = max(0, x - 1); n2 the new |w|^2
+    int ring_pass(int x, VT *w, double2 *h, double2 *n2) {
         if (B.nchunks == 0) return QS3_OK;
-        k_norm2<VT><<<grid(), NTHREADS, 0, st>>>(vec(j), secs(), c0(), B.S, act(), part.as<double2>());
+        const int m = x > 0 ? 2 : 1;
+        const VT *v0 = x > 0 ? rvec(rp) : rvec(rc);
+        const int64_t ld = (int64_t)(rvec(rc) - rvec(rp));
+        const int j0 = std::max(0, x - 1);
+        if constexpr (DF) {
+            k_mdot<VT><<<grid(), NTHREADS, 0, st>>>(v0, ld, 0, m, w, secs(), c0(), B.S, act(), part.as<double2>());
+            QS3_LAUNCHED();
+            QS3_TRY(reduce(m, h + j0, cap));
+            k_mupdate<VT><<<grid(), NTHREADS, m * sizeof(double2), st>>>(w, v0, ld, 0, m, h + j0, cap, secs(), c0(), B.S,
+                                                                        act(), part.as<double2>());
+            QS3_LAUNCHED();
+            QS3_TRY(reduce(1, n2, 1));
+        }
+        return QS3_OK;
+    }
+    // scale w by inv per sector; DF: also store its double-float copy as basis vector j
+    int scale_store(VT *w, int j) {
+        if (B.nchunks == 0) return QS3_OK;
+        if constexpr (DF)
+            k_scale_split<VT><<<grid(), NTHREADS, 0, st>>>(w, svec(j), inv.as<double>(), secs(), c0(), B.S, act());
+        else
+            k_scale<VT><<<grid(), NTHREADS, 0, st>>>(w, inv.as<double>(), secs(), c0(), B.S, act());
+        QS3_LAUNCHED();
+        return QS3_OK;
+    }
+    // normalise the start vector hin(0) per sector (and store it as basis vector 0)
+    int normalise_start() {
+        if (B.nchunks == 0) return QS3_OK;
+        k_norm2<VT><<<grid(), NTHREADS, 0, st>>>(hin(0), secs(), c0(), B.S, act(), part.as<double2>());
         QS3_LAUNCHED();
         QS3_TRY(reduce(1, nrm.as<double2>(), 1));
         k_inv_sqrt<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, nrm.as<double2>(), inv.as<double>());
         QS3_LAUNCHED();
-        k_scale<VT><<<grid(), NTHREADS, 0, st>>>(vec(j), inv.as<double>(), secs(), c0(), B.S, act());
-        QS3_LAUNCHED();
-        return QS3_OK;
+        return scale_store(hin(0), 0);
     }
     int start_random(uint64_t seed) {
         if (B.nchunks == 0) return QS3_OK;
-        k_random<VT><<<grid(), NTHREADS, 0, st>>>(vec(0), seed, secs(), c0(), B.S);
+        k_random<VT><<<grid(), NTHREADS, 0, st>>>(hin(0), seed, secs(), c0(), B.S);
         QS3_LAUNCHED();
-        return normalise(0);
+        return normalise_start();
     }
     int start_from(const WT *src) {
         if (B.nchunks == 0) return QS3_OK;
-        k_convert<VT, WT><<<grid(), NTHREADS, 0, st>>>(vec(0), src, secs(), c0(), B.S, nullptr);
+        k_convert<VT, WT><<<grid(), NTHREADS, 0, st>>>(hin(0), src, secs(), c0(), B.S, nullptr);
         QS3_LAUNCHED();
-        return normalise(0);
+        return normalise_start();
     }
     // Alg. 10 lines 5-11 for step x: psi_{x+1} from H psi_x
     // full2: two Gram-Schmidt passes against all of psi_0..psi_x (the first
@@ -820,27 +1206,35 @@ struct Engine {
     // recurrence, coefficients by dot product), then one classical
     // Gram-Schmidt pass against every kept vector removes the O(eps) rest.
     int step(int x, bool full2 = false) {
-        VT *w = vec(x + 1);
+        VT *w = hout(x);
         std::pair<cudaEvent_t, cudaEvent_t> ev;
         QS3_TRY(stats->pair(ev));
         QS3_CUDA(cudaEventRecord(ev.first, st));
-        QS3_TRY(hphi_launch(B, dtype(), vec(x), w, st, act()));
+        QS3_TRY(hphi_launch(B, dtype(), hin(x), w, st, act()));
         QS3_CUDA(cudaEventRecord(ev.second, st));
         stats->pend.push_back(ev);
         stats->calls += 1;
         for (int s = 0; s < B.S; ++s)
             if (h_active[s]) stats->nnz += B.nnz_sec[s];
         const int j0 = full2 ? 0 : std::max(0, x - 1);
-        QS3_TRY(mdot(j0, x + 1 - j0, w, h1.as<double2>() + j0, cap));
-        QS3_TRY(mupdate(w, j0, x + 1 - j0, h1.as<double2>() + j0, cap, false));
+        double2 *n1 = DF ? nrm1.as<double2>() : nullptr;
+        if (DF && !full2) {
+            QS3_TRY(ring_pass(x, w, h1.as<double2>(), n1));
+        } else {
+            QS3_TRY(mdot(j0, x + 1 - j0, w, h1.as<double2>() + j0, cap));
+            QS3_TRY(mupdate(w, j0, x + 1 - j0, h1.as<double2>() + j0, cap, n1));
+        }
         QS3_TRY(mdot(0, x + 1, w, h2.as<double2>(), cap));
-        QS3_TRY(mupdate(w, 0, x + 1, h2.as<double2>(), cap, true));
+        QS3_TRY(mupdate(w, 0, x + 1, h2.as<double2>(), cap, nrm.as<double2>(), n1));
         k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, x, cap, h1.as<double2>(), nrm.as<double2>(), act(),
                                                          alpha.as<double>(), beta.as<double>(), inv.as<double>(), brk);
         QS3_LAUNCHED();
-        if (B.nchunks) {
-            k_scale<VT><<<grid(), NTHREADS, 0, st>>>(w, inv.as<double>(), secs(), c0(), B.S, act());
-            QS3_LAUNCHED();
+        QS3_TRY(scale_store(w, x + 1));
+        if (DF) {                            // psi_{x+1} becomes the current ring vector
+            const int o = rp;
+            rp = rc;
+            rc = rw;
+            rw = o;
         }
         return QS3_OK;
     }
@@ -852,7 +1246,8 @@ struct Engine {
         QS3_CUDA(cudaStreamSynchronize(st));
         return stats->harvest();
     }
-    // out_y = sum_x psi_x C[s][x][y] for sectors with mask; C host, S x (nin*nout)
+    // out_y = sum_x psi_x C[s][x][y] (x < nin) for sectors with mask; C host,
+    // S x (nin*nout); OT is WT (a result) or ST (into the scratch slots)
     template <typename OT>
     int combine(OT *out, uint64_t ldo, int nin, int nout, const std::vector<double> &C, const std::vector<int> &mask) {
         if (B.nchunks == 0) return QS3_OK;
@@ -863,9 +1258,14 @@ struct Engine {
         QS3_TRY(dm.alloc(mask.size() * 4));
         QS3_CUDA(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, st));
         QS3_CUDA(cudaMemcpyAsync(dm.p, mask.data(), mask.size() * 4, cudaMemcpyHostToDevice, st));
-        k_combine<VT, OT><<<grid(), NTHREADS, ldc * sizeof(double), st>>>(out, ldo, V.as<VT>(), D, nin, nout,
-                                                                          dC.as<double>(), ldc, secs(), c0(), B.S,
-                                                                          dm.as<int>());
+        if constexpr (DF)
+            k_combine_df<VT, OT><<<grid(), NTHREADS, ldc * sizeof(float2), st>>>(out, ldo, V.as<ST>(), D, nin, nout,
+                                                                                 dC.as<double>(), ldc, secs(), c0(),
+                                                                                 B.S, dm.as<int>());
+        else
+            k_combine<VT, OT><<<grid(), NTHREADS, ldc * sizeof(double), st>>>(out, ldo, V.as<VT>(), D, nin, nout,
+                                                                              dC.as<double>(), ldc, secs(), c0(), B.S,
+                                                                              dm.as<int>());
         QS3_LAUNCHED();
         QS3_CUDA(cudaStreamSynchronize(st));     // dC/dm are released on return
         return QS3_OK;
@@ -925,7 +1325,8 @@ static int lanczos_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT
     R.e.assign(S, NAN);
     R.conv.assign(S, 0);
     std::vector<double> eprev(S, NAN), a, b;
-    std::vector<int> msize(S, 0);
+    std::vector<int> msize(S, 0), fin(S, 0);
+    std::vector<std::vector<double>> coef(S);
     for (int s = 0; s < S; ++s)
         if (!B.dims[s]) R.conv[s] = 1;
     const int every = std::max(1, o.check_every);
@@ -967,20 +1368,28 @@ static int lanczos_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT
             }
         }
         if (any) {
-            // eigenvectors of the newly finished sectors: psi = sum_x c_x psi_x over
-            // the n computed vectors only (later slots are uninitialised memory)
-            std::vector<double> C((size_t)S * n, 0.0);
+            // Ritz vector coefficients of the newly finished sectors; the sectors
+            // leave every launch, so their stored basis stays intact until the
+            // single combination at the end
             for (int s = 0; s < S; ++s) {
                 if (!newly[s]) continue;
-                std::vector<double> c;
-                tri_eigvec(msize[s], &a[(size_t)s * E.cap], &b[(size_t)s * E.cap], R.e[s], c);
-                for (int k = 0; k < msize[s]; ++k) C[(size_t)s * n + k] = c[k];
+                tri_eigvec(msize[s], &a[(size_t)s * E.cap], &b[(size_t)s * E.cap], R.e[s], coef[s]);
+                E.h_active[s] = 0;
+                fin[s] = 1;
             }
-            QS3_TRY(E.template combine<typename Wide<VT>::T>(out, B.total, n, 1, C, newly));
-            for (int s = 0; s < S; ++s)
-                if (newly[s]) E.h_active[s] = 0;
             QS3_TRY(E.push_active());
         }
+    }
+    // psi = sum_x c_x psi_x over the computed vectors (later slots are uninitialised)
+    int nin = 0;
+    for (int s = 0; s < S; ++s)
+        if (fin[s]) nin = std::max(nin, msize[s]);
+    if (nin > 0) {
+        std::vector<double> C((size_t)S * nin, 0.0);
+        for (int s = 0; s < S; ++s)
+            if (fin[s])
+                for (int k = 0; k < msize[s]; ++k) C[(size_t)s * nin + k] = coef[s][k];
+        QS3_TRY(E.template combine<typename Wide<VT>::T>(out, B.total, nin, 1, C, fin));
     }
     R.steps = x;
     return QS3_OK;
@@ -1079,9 +1488,11 @@ static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T
             for (int x = 0; x < NM; ++x)
                 for (int y = 0; y < NK; ++y) C[(size_t)s * NM * NK + x * NK + y] = Cm[s][(size_t)x * NM + y];
         }
-        QS3_TRY(E.template combine<VT>(E.vec(E.cap), B.total, NM, NK, C, E.h_active));
-        QS3_CUDA(cudaMemcpyAsync(E.vec(0), E.vec(E.cap), (size_t)NK * B.total * sizeof(VT), cudaMemcpyDeviceToDevice, st));
-        QS3_CUDA(cudaMemcpyAsync(E.vec(NK), E.vec(NM), (size_t)B.total * sizeof(VT), cudaMemcpyDeviceToDevice, st));
+        // (the fp64 ring of a DF engine already holds psi_{N_M} as its current vector)
+        using ST = typename Engine<VT>::ST;
+        QS3_TRY(E.template combine<ST>(E.svec(E.cap), B.total, NM, NK, C, E.h_active));
+        QS3_CUDA(cudaMemcpyAsync(E.svec(0), E.svec(E.cap), (size_t)NK * B.total * sizeof(ST), cudaMemcpyDeviceToDevice, st));
+        QS3_CUDA(cudaMemcpyAsync(E.svec(NK), E.svec(NM), (size_t)B.total * sizeof(ST), cudaMemcpyDeviceToDevice, st));
         // lines 20-26: Lanczos steps from psi_{N_K} (the Gram-Schmidt against psi_0..psi_{N_K}
         // removes the arrowhead couplings beta_y psi_y)
         for (int x = NK; x < NM; ++x) { QS3_TRY(E.step(x, x == NK)); ++steps; }
@@ -1341,8 +1752,8 @@ int dsf_run(Basis &S, int ss, const void *gs, double e0, Basis &Dd, int nq, cons
     Engine<double2> E(Dd, st, &hs);
     QS3_TRY(E.init(n_iter + 1, 0));
     for (int n = 0; n < nq; ++n)
-        QS3_TRY(smq_launch(S, ss, gs, Dd, n, Q + 3 * n, E.vec(0) + Dd.offs[n], st));
-    QS3_TRY(E.normalise(0));
+        QS3_TRY(smq_launch(S, ss, gs, Dd, n, Q + 3 * n, E.hin(0) + Dd.offs[n], st));
+    QS3_TRY(E.normalise_start());
     std::vector<double2> n2(nq);
     QS3_CUDA(cudaMemcpyAsync(n2.data(), E.nrm.p, nq * sizeof(double2), cudaMemcpyDeviceToHost, st));
     QS3_CUDA(cudaStreamSynchronize(st));
@@ -1404,6 +1815,7 @@ static size_t solve_mem_estimate(const Basis &B, const qs3_solve_opts &o) {
     const size_t cap = (size_t)std::max(2, o.n_max) + 1;
     size_t m = cap * B.total * ev + 2 * B.total * ev64 + (size_t)std::max(B.nchunks, 1) * cap * 16;
     if (o.precision == QS3_F32) m += cap * B.total * ev64;   // the fp64 refinement
+    m += 3 * B.total * ev64;                                 // fp64 ring of the fp64 engine
     return m;
 }
 
