@@ -143,11 +143,86 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
         R e = diag_c0<R>(L), dd = 0;
         CT acc;
         acc.x = 0; acc.y = 0;
+        // U(1), fp32, N_down <= 4: per occupied site, the ranks of its first
+        // DEGB hop targets are formed first and their gathers then issue
+        // together, so a thread keeps several independent loads in flight
+        // (measured: 5% faster for fp32; the fp64 kernels run slower this way)
+        constexpr bool BATCH = !KS && ND <= 4 && sizeof(R) == 4;
+        constexpr int DEGB = 6;
+        if constexpr (BATCH) {
+#pragma unroll
+            for (int m = 0; m < ND; ++m) {
+                const int i = c[m];
+                e += diag_u<R>(L, i);
+                const int e0 = __ldg(L.adj_ptr + i), e1 = __ldg(L.adj_ptr + i + 1);
+                uint64_t r2b[DEGB];
+                R cfb[DEGB];
+#pragma unroll
+                for (int b = 0; b < DEGB; ++b) {
+                    const int q = e0 + b;
+                    cfb[b] = 0;
+                    r2b[b] = 0;
+                    if (q < e1) {
+                        const int j = __ldg(L.adj_nbr + q);
+                        bool occ = false;
+#pragma unroll
+                        for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
+                        if (occ) {
+                            dd += diag_jz<R>(L, q);
+                        } else {
+                            const bool inplace = (m == 0 || j > c[m > 0 ? m - 1 : 0]) &&
+                                                 (m == ND - 1 || j < c[m + 1 < ND ? m + 1 : m]);
+                            if (inplace) {
+                                r2b[b] = rank - sm.sC[(m + 1) * L.np1 + c[m]] + sm.sC[(m + 1) * L.np1 + j];
+                            } else {
+                                int tt[ND];
+#pragma unroll
+                                for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
+                                sort_net(tt);
+                                r2b[b] = rank_of(tt, sm.sC, L.np1);
+                            }
+                            cfb[b] = (R)0.5 * __ldg(jxy + q);
+                        }
+                    }
+                }
+                VT vb[DEGB];
+#pragma unroll
+                for (int b = 0; b < DEGB; ++b)
+                    if (cfb[b] != (R)0) vb[b] = ph_in[r2b[b]];
+#pragma unroll
+                for (int b = 0; b < DEGB; ++b)
+                    if (cfb[b] != (R)0) {
+                        CT cf;
+                        cf.x = cfb[b];
+                        cf.y = 0;
+                        acc_add(acc, cf, vb[b]);
+                    }
+                // sites with more than DEGB neighbours: the rest one at a time
+                for (int q = e0 + DEGB; q < e1; ++q) {
+                    const int j = __ldg(L.adj_nbr + q);
+                    bool occ = false;
+#pragma unroll
+                    for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
+                    if (occ) {
+                        dd += diag_jz<R>(L, q);
+                        continue;
+                    }
+                    int tt[ND];
+#pragma unroll
+                    for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
+                    sort_net(tt);
+                    CT cf;
+                    cf.x = (R)0.5 * __ldg(jxy + q);
+                    cf.y = 0;
+                    acc_add(acc, cf, ph_in[rank_of(tt, sm.sC, L.np1)]);
+                }
+            }
+        }
         // the k-sector hop body (with the representative search) stays rolled:
         // unrolled N_down times it overflows the instruction cache (measured)
         constexpr int UNR = KS ? 1 : ND;
 #pragma unroll UNR
-        for (int m = 0; m < ND; ++m) {
+        for (int m = 0; m < (BATCH ? 0 : ND); ++m) {
             const int i = pick(c, m);
             e += diag_u<R>(L, i);
             const int e0 = __ldg(L.adj_ptr + i), e1 = __ldg(L.adj_ptr + i + 1);

@@ -594,28 +594,48 @@ __global__ void __launch_bounds__(NTHREADS) k_mdot_df(const typename DfS<VT>::T 
         wv[k] = (r < ci.n) ? split2(ld2(w + ci.base + r)) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // rows past the chunk end read the chunk's last row (always written) and
+    // meet w = 0 there, so every load is unconditional and all of a pair of
+    // vectors' loads are in flight together
+    int ro[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) ro[k] = min((int)threadIdx.x + k * NTHREADS, ci.n - 1);
     for (int jb = 0; jb < m; jb += GDF) {
         const int nj = min(GDF, m - jb);
-        for (int jj = 0; jj < nj; ++jj) {
-            const ST *vj = V + (uint64_t)(j0 + jb + jj) * D + ci.base;
-            dfl re = {0.f, 0.f}, im = {0.f, 0.f};
+        for (int jj = 0; jj < nj; jj += 2) {
+            const bool two = jj + 1 < nj;
+            const ST *v0 = V + (uint64_t)(j0 + jb + jj) * D + ci.base;
+            const ST *v1 = two ? v0 + D : v0;
+            float4 a0[RPT], a1[RPT];
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
-                const int r = threadIdx.x + k * NTHREADS;
-                if (r < ci.n) {
-                    const float4 a = ld_df(vj + r), b = wv[k];
-                    // conj(a) b = (a.r b.r + a.i b.i) + i (a.r b.i - a.i b.r)
-                    df_mac(re, a.x, a.y, b.x, b.y);
-                    if (IsC<VT>::v) {
-                        df_mac(re, a.z, a.w, b.z, b.w);
-                        df_mac(im, a.x, a.y, b.z, b.w);
-                        df_mac(im, -a.z, -a.w, b.x, b.y);
-                    }
+                a0[k] = ld_df(v0 + ro[k]);
+                a1[k] = ld_df(v1 + ro[k]);
+            }
+            dfl re0 = {0.f, 0.f}, im0 = {0.f, 0.f}, re1 = {0.f, 0.f}, im1 = {0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const float4 b = wv[k];
+                // conj(a) b = (a.r b.r + a.i b.i) + i (a.r b.i - a.i b.r)
+                df_mac(re0, a0[k].x, a0[k].y, b.x, b.y);
+                df_mac(re1, a1[k].x, a1[k].y, b.x, b.y);
+                if (IsC<VT>::v) {
+                    df_mac(re0, a0[k].z, a0[k].w, b.z, b.w);
+                    df_mac(im0, a0[k].x, a0[k].y, b.z, b.w);
+                    df_mac(im0, -a0[k].z, -a0[k].w, b.x, b.y);
+                    df_mac(re1, a1[k].z, a1[k].w, b.z, b.w);
+                    df_mac(im1, a1[k].x, a1[k].y, b.z, b.w);
+                    df_mac(im1, -a1[k].z, -a1[k].w, b.x, b.y);
                 }
             }
-            re = df_norm(re);
-            im = df_norm(im);
-            red[jj][threadIdx.x] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            re0 = df_norm(re0);
+            im0 = df_norm(im0);
+            red[jj][threadIdx.x] = make_float4(re0.hi, re0.lo, im0.hi, im0.lo);
+            if (two) {
+                re1 = df_norm(re1);
+                im1 = df_norm(im1);
+                red[jj + 1][threadIdx.x] = make_float4(re1.hi, re1.lo, im1.hi, im1.lo);
+            }
         }
         __syncthreads();
         if (warp < nj) {
