@@ -60,8 +60,8 @@ N_SMS = 152
 # workloads: warp instructions (smsp__inst_executed.sum) and DRAM bytes
 # (dram__bytes_read.sum + dram__bytes_write.sum); see the named summary
 HPHI_PROFILE = {
-    "square10x10_nd4_all_k": {"kernel": "k_hphi<4, complex128, k-sector>", "warp_inst": 1522234344,
-                              "dram_bytes": 99634944 + 38677248,
+    "square10x10_nd4_all_k": {"kernel": "k_hphi<4, complex128, k-sector>", "warp_inst": 1520286294,
+                              "dram_bytes": 98942208 + 38492928,
                               "profile": "profiles/k_hphi_c128_square10x10_nd4_all_k.md"},
 }
 

@@ -412,9 +412,9 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
         int i = B.bi[b], j = B.bj[b];
         int p = fill[i]++, q = fill[j]++;
         nbr[p] = j; nbr[q] = i;
-        ajxy[p] = ajxy[q] = B.jxy[b];
+        ajxy[p] = ajxy[q] = 0.5 * B.jxy[b];            // hop amplitude J^xy / 2 of Eq. (1)
         ajz[p] = ajz[q] = B.jz[b];
-        ajxyf[p] = ajxyf[q] = (float)B.jxy[b];
+        ajxyf[p] = ajxyf[q] = (float)(0.5 * B.jxy[b]);
         u[i] -= 0.5 * B.jz[b];
         u[j] -= 0.5 * B.jz[b];
         c0 += 0.25 * B.jz[b];

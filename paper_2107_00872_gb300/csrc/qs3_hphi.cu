@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
                                 sort_net(tt);
                                 r2b[b] = rank_of(tt, sm.sC, L.np1);
                             }
-                            cfb[b] = (R)0.5 * __ldg(jxy + q);
+                            cfb[b] = __ldg(jxy + q);
                         }
                     }
                 }
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
                     for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
                     sort_net(tt);
                     CT cf;
-                    cf.x = (R)0.5 * __ldg(jxy + q);
+                    cf.x = __ldg(jxy + q);
                     cf.y = 0;
                     acc_add(acc, cf, ph_in[rank_of(tt, sm.sC, L.np1)]);
                 }
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
                 int tt[ND];
 #pragma unroll
                 for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
-                const R jh = (R)0.5 * __ldg(jxy + q);
+                const R jh = __ldg(jxy + q);
                 if constexpr (!KS) {
                     // j keeps position m when it stays between the neighbours of
                     // c_m: only the m-th term of the rank changes

@@ -81,7 +81,7 @@ struct LatView {
     const uint64_t *binom;
     const int *adj_ptr;           // N + 1
     const int *adj_nbr;           // 2 n_bonds
-    const double *adj_jxy;        // 2 n_bonds
+    const double *adj_jxy;        // 2 n_bonds: hop amplitude J^xy / 2 of the bond
     const double *adj_jz;         // 2 n_bonds
     const float *adj_jxy_f;       // fp32 copy of adj_jxy
     const double *u;              // N: -(1/2) sum_j Jz_ij + h_i
