@@ -98,6 +98,23 @@ int qs3_basis_ranks(qs3_basis_t b, int32_t s, uint64_t *ranks, uint8_t *stab);
  * off-diagonal term of Alg. 9 that lands on a member of the sector.  Counted
  * once on the device and cached. */
 int qs3_basis_nnz(qs3_basis_t b, uint64_t *nnz);
+/* Representative table of a k-sector basis.  The representative search of
+ * Alg. 7 (with the sigma lookup of Alg. 9) is a fixed function of the state;
+ * for lattices whose C(N, N_down) states fit a 4-byte table it can be
+ * tabulated once: for every state, by rank0, its orbit and the translation
+ * to the representative, plus per sector the row of every orbit.  H Phi then
+ * uses two table loads per hop target instead of the search; the results are
+ * identical.  The table is built at qs3_basis_create when it needs at most
+ * 1 GiB and an eighth of the free device memory.
+ *   mode = 1: build it (any size that fits); OVERFLOW when C(N, N_down) >= 2^32
+ *             or there are 2^20 orbits or more, OOM when it does not fit,
+ *             STATE on a U(1)-only basis or N_down = 0;
+ *   mode = 0: release it (H Phi runs the search);
+ *   mode = -1: query only.
+ * *active (may be NULL) receives 1 if the table is in use afterwards.  The
+ * table occupies C(N, N_down) * 4 + n_sectors * n_orbits * 4 bytes of device
+ * memory, library-owned, released with the basis. */
+int qs3_basis_rep_table(qs3_basis_t b, int32_t mode, int32_t *active);
 
 /* psi = H phi (Alg. 9, pull form, one row per thread, no atomics).
  * dtype: F32/F64 on a U(1)-only basis (real H); C64/C128 on any basis.

@@ -165,6 +165,12 @@ class Basis:
             self._nnz = v.value
         return self._nnz
 
+    def rep_table(self, mode: int = -1) -> bool:
+        """Representative table of H Phi: 1 build, 0 release, -1 query; returns whether it is in use."""
+        a = ctypes.c_int32()
+        check(load().qs3_basis_rep_table(self._h, int(mode), ctypes.byref(a)), "qs3_basis_rep_table")
+        return bool(a.value)
+
     # ---------------------------------------------------------- operations
 
     def hphi(self, phi, psi=None, stream=None):

@@ -22,6 +22,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <string>
 #include <utility>
 
 #include "qs3_internal.cuh"
@@ -193,11 +194,13 @@ __global__ void k_pidx(const uint32_t *__restrict__ P, uint64_t d, uint32_t np, 
     }
 }
 
+// the representatives of momentum K (each orbit once, compatible ones only),
+// sorted by rank0, with |Stab|: d of them in kout / vout
 template <int ND>
-static int build_reps_nd(Basis &B, int s) {
-    const int *K = &B.K[3 * s];
+static int enum_sorted_reps(Basis &B, const int *K, DevBuf &kout, DevBuf &vout, uint64_t &d,
+                            std::vector<uint64_t> &hb, int &nsm) {
     // C(N-1, ND-1) candidates
-    std::vector<uint64_t> hb((size_t)(B.nd + 3) * (B.N + 1));
+    hb.resize((size_t)(B.nd + 3) * (B.N + 1));
     QS3_CUDA(cudaMemcpy(hb.data(), B.d_binom.p, hb.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     const uint64_t nc = hb[(size_t)(ND - 1) * (B.N + 1) + (B.N - 1)];
     const size_t smem = (size_t)(B.nd + 3) * (B.N + 1) * 8 + (size_t)B.N * 4;
@@ -205,7 +208,7 @@ static int build_reps_nd(Basis &B, int s) {
     DevBuf cnt;
     QS3_TRY(cnt.alloc(sizeof(unsigned long long)));
     QS3_CUDA(cudaMemset(cnt.p, 0, sizeof(unsigned long long)));
-    int dev = 0, nsm = 0;
+    int dev = 0;
     QS3_CUDA(cudaGetDevice(&dev));
     QS3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     uint64_t want = (nc + NTHREADS - 1) / NTHREADS;
@@ -213,10 +216,10 @@ static int build_reps_nd(Basis &B, int s) {
     k_enum_reps<ND><<<grid, NTHREADS, smem>>>(B.lv, K[0], K[1], K[2], nc, 0, cnt.as<unsigned long long>(),
                                               nullptr, nullptr);
     QS3_LAUNCHED();
-    unsigned long long d = 0;
+    d = 0;
     QS3_CUDA(cudaMemcpy(&d, cnt.p, sizeof(d), cudaMemcpyDeviceToHost));
-    if (d >= (1ull << 32)) return set_err(QS3_ERR_OVERFLOW, "sector dimension %llu exceeds 2^32", d);
-    DevBuf kin, vin, kout, vout;
+    if (d >= (1ull << 32)) return set_err(QS3_ERR_OVERFLOW, "sector dimension %llu exceeds 2^32", (unsigned long long)d);
+    DevBuf kin, vin;
     QS3_TRY(kin.alloc(d * 8));
     QS3_TRY(vin.alloc(d));
     QS3_CUDA(cudaMemset(cnt.p, 0, sizeof(unsigned long long)));
@@ -236,6 +239,17 @@ static int build_reps_nd(Basis &B, int s) {
                                                  kout.as<unsigned long long>(), vin.as<uint8_t>(),
                                                  vout.as<uint8_t>(), (int64_t)d));
     }
+    return QS3_OK;
+}
+
+template <int ND>
+static int build_reps_nd(Basis &B, int s) {
+    const int *K = &B.K[3 * s];
+    std::vector<uint64_t> hb;
+    int nsm = 0;
+    uint64_t d = 0;
+    DevBuf kout, vout;
+    QS3_TRY(enum_sorted_reps<ND>(B, K, kout, vout, d, hb, nsm));
     // prefix index
     const uint32_t np = (ND >= 2) ? (uint32_t)hb[2 * (size_t)(B.N + 1) + B.N] : (uint32_t)B.N;   // number of prefixes
     DevBuf P, pidx;
@@ -271,6 +285,141 @@ int build_sector_reps(Basis &B, int s) {
         case 8: return build_reps_nd<8>(B, s);
         default: return set_err(QS3_ERR_INVALID_ARG, "n_down %d", B.nd);
     }
+}
+
+// ---------------------------------------------------- representative table
+// For lattices whose C(N, N_down) states fit a 4-byte-per-state table, the
+// result of the representative search of Alg. 7 for every state is tabulated
+// once: orb[rank0(a)] = g << 12 | u with a = T_u (rep_g).  A hop target then
+// costs one rank and two table loads instead of the search and the binary
+// search in sigma.  It is the same function: where several translations reach
+// the representative (a non-trivial stabiliser) they differ by a stabiliser
+// element, whose phase is 1 on every sector that holds the representative.
+
+// orb[rank0(T_u rep_g)] = g << 12 | u for every orbit g and translation u
+template <int ND>
+__global__ void __launch_bounds__(NTHREADS) k_orbit_fill(LatView L, const uint64_t *__restrict__ reps, uint64_t n,
+                                                         uint32_t *__restrict__ orb) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *sC = (uint64_t *)smem;
+    uint32_t *sxyz = (uint32_t *)(sC + (L.nd + 3) * L.np1);
+    const int nC = (L.nd + 3) * L.np1;
+    for (int i = threadIdx.x; i < nC; i += blockDim.x) sC[i] = L.binom[i];
+    for (int i = threadIdx.x; i < L.N; i += blockDim.x) sxyz[i] = L.xyz[i];
+    __syncthreads();
+    const int Lx = L.L[0], Ly = L.L[1], Lz = L.L[2], N = L.N;
+    const uint64_t total = n * (uint64_t)N;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t g = i / (uint64_t)N;
+        const int u = (int)(i - g * (uint64_t)N);
+        int c[ND];
+        unrank(reps[g], sC, L.np1, c);
+        const uint32_t pu = sxyz[u];
+        const int ux = pu & 2047u, uy = (pu >> 11) & 2047u, uz = pu >> 22;
+        int t[ND];
+#pragma unroll
+        for (int m = 0; m < ND; ++m) {
+            const uint32_t p = sxyz[c[m]];
+            int x = (int)(p & 2047u) + ux, y = (int)((p >> 11) & 2047u) + uy, z = (int)(p >> 22) + uz;
+            x -= (x >= Lx) ? Lx : 0;
+            y -= (y >= Ly) ? Ly : 0;
+            z -= (z >= Lz) ? Lz : 0;
+            t[m] = x + Lx * (y + Ly * z);
+        }
+        sort_net(t);
+        orb[rank_of(t, sC, L.np1)] = ((uint32_t)g << 12) | (uint32_t)u;
+    }
+}
+
+// t2[s n + g] = row of representative g in sector s, -1 if the sector lacks it
+__global__ void k_orbit_rows(const SecView *__restrict__ secs, int S, const uint64_t *__restrict__ reps, uint64_t n,
+                             int32_t *__restrict__ t2) {
+    const uint64_t total = n * (uint64_t)S;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(i / n);
+        const uint64_t g = i - (uint64_t)s * n;
+        const uint64_t r = reps[g];
+        const uint64_t *sig = secs[s].sigma;
+        uint64_t lo = 0, hi = secs[s].dim;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (sig[mid] < r) lo = mid + 1; else hi = mid;
+        }
+        t2[i] = (lo < secs[s].dim && sig[lo] == r) ? (int32_t)lo : -1;
+    }
+}
+
+template <int ND>
+static int build_table_nd(Basis &B, size_t max_bytes) {
+    std::vector<uint64_t> hb((size_t)(B.nd + 3) * (B.N + 1));
+    QS3_CUDA(cudaMemcpy(hb.data(), B.d_binom.p, hb.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    const uint64_t ns = hb[(size_t)ND * (B.N + 1) + B.N];           // C(N, N_down)
+    if (ns >= (1ull << 32)) return set_err(QS3_ERR_OVERFLOW, "C(N, N_down) = %llu states: no table", (unsigned long long)ns);
+    const uint64_t n_est = ns / (uint64_t)B.N + 1;                 // orbits, about C(N, N_down) / N
+    if (ns * 4 + n_est * 4 * (uint64_t)B.S > max_bytes)
+        return set_err(QS3_ERR_OOM, "representative table of ~%llu bytes exceeds the limit",
+                       (unsigned long long)(ns * 4 + n_est * 4 * (uint64_t)B.S));
+    const int K0[3] = {0, 0, 0};                                   // every representative is compatible at k = 0
+    DevBuf reps, stab;
+    uint64_t n = 0;
+    int nsm = 0;
+    std::vector<uint64_t> hb2;
+    QS3_TRY(enum_sorted_reps<ND>(B, K0, reps, stab, n, hb2, nsm));
+    if (n >= (1ull << 20)) return set_err(QS3_ERR_OVERFLOW, "%llu orbits exceed the table's 20-bit index", (unsigned long long)n);
+    if (ns * 4 + n * 4 * (uint64_t)B.S > max_bytes)
+        return set_err(QS3_ERR_OOM, "representative table exceeds the limit");
+    DevBuf orb, t2;
+    QS3_TRY(orb.alloc(ns * 4));
+    QS3_TRY(t2.alloc(n * 4 * (uint64_t)B.S));
+    QS3_CUDA(cudaMemset(orb.p, 0xff, ns * 4));
+    const size_t smem = (size_t)(B.nd + 3) * (B.N + 1) * 8 + (size_t)B.N * 4;
+    QS3_CUDA(cudaFuncSetAttribute(k_orbit_fill<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
+    const uint64_t tot = n * (uint64_t)B.N;
+    int grid = (int)std::min<uint64_t>((tot + NTHREADS - 1) / NTHREADS, (uint64_t)nsm * 8);
+    k_orbit_fill<ND><<<std::max(grid, 1), NTHREADS, smem>>>(B.lv, reps.as<uint64_t>(), n, orb.as<uint32_t>());
+    QS3_LAUNCHED();
+    const uint64_t tot2 = n * (uint64_t)B.S;
+    int grid2 = (int)std::min<uint64_t>((tot2 + 255) / 256, (uint64_t)nsm * 8);
+    k_orbit_rows<<<std::max(grid2, 1), 256>>>(B.d_secs.as<SecView>(), B.S, reps.as<uint64_t>(), n, t2.as<int32_t>());
+    QS3_LAUNCHED();
+    QS3_CUDA(cudaDeviceSynchronize());
+    B.d_orb = std::move(orb);
+    B.d_t2 = std::move(t2);
+    B.n_orb = n;
+    B.lv.orb = B.d_orb.as<uint32_t>();
+    B.lv.n_orb = (uint32_t)n;
+    for (int s = 0; s < B.S; ++s) B.secs[s].t2 = B.d_t2.as<int32_t>() + (size_t)s * n;
+    QS3_TRY(B.d_secs.upload(B.secs.data(), B.secs.size() * sizeof(SecView)));
+    return QS3_OK;
+}
+
+int build_rep_table(Basis &B, size_t max_bytes) {
+    if (!B.has_k || B.nd == 0 || B.total == 0) return set_err(QS3_ERR_STATE, "the table serves k-sector bases only");
+    if (B.N > 4096) return set_err(QS3_ERR_OVERFLOW, "N > 4096");
+    if (B.lv.orb) return QS3_OK;
+    switch (B.nd) {
+        case 1: return build_table_nd<1>(B, max_bytes);
+        case 2: return build_table_nd<2>(B, max_bytes);
+        case 3: return build_table_nd<3>(B, max_bytes);
+        case 4: return build_table_nd<4>(B, max_bytes);
+        case 5: return build_table_nd<5>(B, max_bytes);
+        case 6: return build_table_nd<6>(B, max_bytes);
+        case 7: return build_table_nd<7>(B, max_bytes);
+        case 8: return build_table_nd<8>(B, max_bytes);
+        default: return set_err(QS3_ERR_INVALID_ARG, "n_down %d", B.nd);
+    }
+}
+
+void drop_rep_table(Basis &B) {
+    B.lv.orb = nullptr;
+    B.lv.n_orb = 0;
+    for (auto &v : B.secs) v.t2 = nullptr;
+    B.d_orb.release();
+    B.d_t2.release();
+    B.n_orb = 0;
+    if (!B.secs.empty()) B.d_secs.upload(B.secs.data(), B.secs.size() * sizeof(SecView));
 }
 
 // per-sector phase tables ph[s N + r] = exp(-2 pi i sum_alpha K_alpha r_alpha / L_alpha):
@@ -459,6 +608,12 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     L.u_f = B.d_u_f.as<float>();
     L.adj_jz_f = B.d_adj_jz_f.as<float>();
     L.xyz = B.d_xyz.as<uint32_t>();
+    L.jh_uniform = 0.0;
+    if (nb > 0) {
+        bool same = true;
+        for (int b = 1; b < nb; ++b) same &= B.jxy[b] == B.jxy[0];
+        if (same) L.jh_uniform = 0.5 * B.jxy[0];
+    }
 
     // sectors
     B.dims.assign(nsec, 0);
@@ -523,6 +678,17 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     B.smem_bytes = row_kernel_smem(B, 0);
     if (B.smem_bytes > 200 * 1024)
         return set_err(QS3_ERR_OVERFLOW, "lattice tables need %zu bytes of shared memory", B.smem_bytes);
+    // the representative table when it is small (a bounded fraction of the
+    // device memory); otherwise H Phi runs the representative search
+    if (B.has_k && nd > 0 && B.total > 0 && N <= 4096) {
+        size_t fr = 0, tt = 0;
+        QS3_CUDA(cudaMemGetInfo(&fr, &tt));
+        const size_t lim = std::min<size_t>(REP_TABLE_AUTO_BYTES, fr / 8);
+        if (build_rep_table(B, lim) != QS3_OK) {
+            drop_rep_table(B);
+            clear_err();
+        }
+    }
     return QS3_OK;
 }
 
@@ -586,6 +752,27 @@ int qs3_basis_nnz(qs3_basis_t b, uint64_t *nnz) {
     if (!b || !nnz) return set_err(QS3_ERR_INVALID_ARG, "NULL argument");
     QS3_TRY(count_nnz(b->B, nnz));
     return QS3_OK;
+}
+
+int qs3_basis_rep_table(qs3_basis_t b, int32_t mode, int32_t *active) {
+    clear_err();
+    if (!b) return set_err(QS3_ERR_INVALID_ARG, "basis is NULL");
+    if (mode < -1 || mode > 1) return set_err(QS3_ERR_INVALID_ARG, "mode %d", mode);
+    int st = QS3_OK;
+    if (mode == 0) {
+        drop_rep_table(b->B);
+    } else if (mode == 1) {
+        size_t fr = 0, tt = 0;
+        QS3_CUDA(cudaMemGetInfo(&fr, &tt));
+        st = build_rep_table(b->B, fr - fr / 16);
+        if (st != QS3_OK) {
+            std::string msg = last_err();
+            drop_rep_table(b->B);
+            set_err(st, "%s", msg.c_str());
+        }
+    }
+    if (active) *active = b->B.lv.orb ? 1 : 0;
+    return st;
 }
 
 const char *qs3_last_error(void) { return qs3::last_err(); }

@@ -35,17 +35,31 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
     return r;
 }
 
-// acc += coef * x for the four vector types
+// acc += coef * x: complex coefficient (explicit fma chains: four fused
+// multiply-adds per complex product instead of multiply, fma and add per part)
 __device__ __forceinline__ void acc_add(float2 &acc, float2 coef, float2 x) {
-    acc.x += coef.x * x.x - coef.y * x.y;
-    acc.y += coef.x * x.y + coef.y * x.x;
+    acc.x = fmaf(coef.x, x.x, acc.x);
+    acc.x = fmaf(-coef.y, x.y, acc.x);
+    acc.y = fmaf(coef.x, x.y, acc.y);
+    acc.y = fmaf(coef.y, x.x, acc.y);
 }
 __device__ __forceinline__ void acc_add(double2 &acc, double2 coef, double2 x) {
-    acc.x += coef.x * x.x - coef.y * x.y;
-    acc.y += coef.x * x.y + coef.y * x.x;
+    acc.x = fma(coef.x, x.x, acc.x);
+    acc.x = fma(-coef.y, x.y, acc.x);
+    acc.y = fma(coef.x, x.y, acc.y);
+    acc.y = fma(coef.y, x.x, acc.y);
 }
-__device__ __forceinline__ void acc_add(float2 &acc, float2 coef, float x) { acc.x += coef.x * x; acc.y += coef.y * x; }
-__device__ __forceinline__ void acc_add(double2 &acc, double2 coef, double x) { acc.x += coef.x * x; acc.y += coef.y * x; }
+// acc += c * x with a real coefficient; a real x touches acc.x only
+__device__ __forceinline__ void madd_r(float2 &acc, float c, float x) { acc.x = fmaf(c, x, acc.x); }
+__device__ __forceinline__ void madd_r(double2 &acc, double c, double x) { acc.x = fma(c, x, acc.x); }
+__device__ __forceinline__ void madd_r(float2 &acc, float c, float2 x) {
+    acc.x = fmaf(c, x.x, acc.x);
+    acc.y = fmaf(c, x.y, acc.y);
+}
+__device__ __forceinline__ void madd_r(double2 &acc, double c, double2 x) {
+    acc.x = fma(c, x.x, acc.x);
+    acc.y = fma(c, x.y, acc.y);
+}
 __device__ __forceinline__ void store(float *p, float2 v) { *p = v.x; }
 __device__ __forceinline__ void store(double *p, double2 v) { *p = v.x; }
 __device__ __forceinline__ void store(float2 *p, float2 v) { *p = v; }
@@ -93,7 +107,9 @@ template <typename CT> __device__ __forceinline__ const CT *phase_table(const Se
 template <> __device__ __forceinline__ const double2 *phase_table<double2>(const SecView &sv) { return sv.ph64; }
 template <> __device__ __forceinline__ const float2 *phase_table<float2>(const SecView &sv) { return sv.ph32; }
 
-template <int ND, typename VT, bool KS>
+// TB (k-sectors): representative and row from the representative table
+// (LatView::orb, SecView::t2) instead of the search and sigma lookup
+template <int ND, typename VT, bool KS, bool TB = false>
 __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *__restrict__ secs,
                                                    const int *__restrict__ tile0, int S, int ntiles,
                                                    const VT *__restrict__ phi, VT *__restrict__ psi,
@@ -143,6 +159,13 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
         R e = diag_c0<R>(L), dd = 0;
         CT acc;
         acc.x = 0; acc.y = 0;
+        // k-sectors with one hop amplitude on every bond: sum phase x phi over
+        // the hops and multiply by the amplitude once (two fp64 multiplies
+        // fewer per hop)
+        const R juni = (R)L.jh_uniform;
+        const bool uni = KS && juni != (R)0;
+        CT acch;
+        acch.x = 0; acch.y = 0;
         // U(1), fp32, N_down <= 4: per occupied site, the ranks of its first
         // DEGB hop targets are formed first and their gathers then issue
         // together, so a thread keeps several independent loads in flight
@@ -191,12 +214,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
                     if (cfb[b] != (R)0) vb[b] = ph_in[r2b[b]];
 #pragma unroll
                 for (int b = 0; b < DEGB; ++b)
-                    if (cfb[b] != (R)0) {
-                        CT cf;
-                        cf.x = cfb[b];
-                        cf.y = 0;
-                        acc_add(acc, cf, vb[b]);
-                    }
+                    if (cfb[b] != (R)0) madd_r(acc, cfb[b], vb[b]);
                 // sites with more than DEGB neighbours: the rest one at a time
                 for (int q = e0 + DEGB; q < e1; ++q) {
                     const int j = __ldg(L.adj_nbr + q);
@@ -211,10 +229,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
 #pragma unroll
                     for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
                     sort_net(tt);
-                    CT cf;
-                    cf.x = __ldg(jxy + q);
-                    cf.y = 0;
-                    acc_add(acc, cf, ph_in[rank_of(tt, sm.sC, L.np1)]);
+                    madd_r(acc, __ldg(jxy + q), ph_in[rank_of(tt, sm.sC, L.np1)]);
                 }
             }
         }
@@ -250,28 +265,46 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
                         sort_net(tt);
                         r2 = rank_of(tt, sm.sC, L.np1);
                     }
-                    CT cf;
-                    cf.x = jh; cf.y = 0;
-                    acc_add(acc, cf, ph_in[r2]);
+                    madd_r(acc, jh, ph_in[r2]);
                 } else {
-                    int rep[ND];
-                    int ax, by, cz;
-                    const uint64_t r2 = canon(tt, L, sm.sxyz, sm.sC, rep, ax, by, cz);
                     uint32_t idx;
-                    if (!sigma_find(sv, prefix_of(rep, sm.sC, L.np1), r2, idx)) continue;
-                    CT p = ph[ax + L.L[0] * (by + L.L[1] * cz)];   // generic load (L1-cached)
+                    int u;
+                    if constexpr (TB) {
+                        sort_net(tt);
+                        const uint32_t e = __ldg(L.orb + rank_of(tt, sm.sC, L.np1));
+                        if ((e >> 12) >= L.n_orb) continue;     // never for a complete table
+                        const int32_t row2 = __ldg(sv.t2 + (e >> 12));
+                        if (row2 < 0) continue;
+                        idx = (uint32_t)row2;
+                        u = (int)(e & 4095u);
+                    } else {
+                        int rep[ND];
+                        int ax, by, cz;
+                        const uint64_t r2 = canon(tt, L, sm.sxyz, sm.sC, rep, ax, by, cz);
+                        if (!sigma_find(sv, prefix_of(rep, sm.sC, L.np1), r2, idx)) continue;
+                        u = ax + L.L[0] * (by + L.L[1] * cz);
+                    }
+                    CT p = ph[u];   // generic load (L1-cached)
                     const int st = __ldg(sv.stab + idx);
-                    const R w = (st == st_row) ? jh : jh * snorm[st] * rs;
-                    p.x *= w;
-                    p.y *= w;
-                    acc_add(acc, p, ph_in[idx]);
+                    if (uni) {
+                        // uniform J^xy: the amplitude is applied once per row below
+                        if (st != st_row) {
+                            const R f = snorm[st] * rs;
+                            p.x *= f;
+                            p.y *= f;
+                        }
+                        acc_add(acch, p, ph_in[idx]);
+                    } else {
+                        const R w = (st == st_row) ? jh : jh * snorm[st] * rs;
+                        p.x *= w;
+                        p.y *= w;
+                        acc_add(acc, p, ph_in[idx]);
+                    }
                 }
             }
         }
-        CT dg;
-        dg.x = e + (R)0.5 * dd;
-        dg.y = 0;
-        acc_add(acc, dg, x0);
+        if (KS && uni) madd_r(acc, juni, acch);
+        madd_r(acc, e + (R)0.5 * dd, x0);
         store(psi + sv.off + row, acc);
     }
 }
@@ -331,8 +364,7 @@ __global__ void k_diag0(double c0, uint64_t n, const VT *__restrict__ phi, VT *_
     using CT = typename VTr<VT>::C;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         CT acc; acc.x = 0; acc.y = 0;
-        CT d; d.x = (R)c0; d.y = 0;
-        acc_add(acc, d, phi[i]);
+        madd_r(acc, (R)c0, phi[i]);
         store(psi + i, acc);
     }
 }
@@ -371,16 +403,24 @@ static int launch_rows(KF kern, Basis &B, size_t smem, std::atomic<unsigned long
     return QS3_OK;
 }
 
-template <int ND, typename VT, bool KS>
-static int hphi_nd(Basis &B, const void *phi, void *psi, cudaStream_t st, const int *active) {
+template <int ND, typename VT, bool KS, bool TB>
+static int hphi_ndt(Basis &B, const void *phi, void *psi, cudaStream_t st, const int *active) {
     static std::atomic<unsigned long long> cache{0};
     int grid = 1;
-    QS3_TRY(launch_rows(k_hphi<ND, VT, KS>, B, B.smem_bytes, cache, &grid));
+    QS3_TRY(launch_rows(k_hphi<ND, VT, KS, TB>, B, B.smem_bytes, cache, &grid));
     if (B.ntiles == 0) return QS3_OK;
-    k_hphi<ND, VT, KS><<<grid, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S,
-                                                              B.ntiles, (const VT *)phi, (VT *)psi, active);
+    k_hphi<ND, VT, KS, TB><<<grid, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(),
+                                                                  B.S, B.ntiles, (const VT *)phi, (VT *)psi, active);
     QS3_LAUNCHED();
     return QS3_OK;
+}
+
+template <int ND, typename VT, bool KS>
+static int hphi_nd(Basis &B, const void *phi, void *psi, cudaStream_t st, const int *active) {
+    if constexpr (KS) {
+        if (B.lv.orb) return hphi_ndt<ND, VT, true, true>(B, phi, psi, st, active);
+    }
+    return hphi_ndt<ND, VT, KS, false>(B, phi, psi, st, active);
 }
 
 template <typename VT, bool KS>

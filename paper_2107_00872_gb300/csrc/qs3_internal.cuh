@@ -90,6 +90,13 @@ struct LatView {
     float c0f;
     const float *adj_jz_f;
     const uint32_t *xyz;          // N: x | y << 11 | z << 22
+    // representative table (k-sectors, optional): for every state a, by its
+    // rank0, orb[rank0] = g << 12 | u, where the orbit's representative is the
+    // g-th of the sorted list of all representatives and a = T_u (rep): the
+    // translation by -u (u the flat site index) takes a to its representative
+    const uint32_t *orb;
+    uint32_t n_orb;               // orbits in the table (entries >= n_orb << 12 are invalid)
+    double jh_uniform;            // the hop amplitude J^xy / 2 when every bond has the same one, else 0
 };
 
 struct SecView {
@@ -102,6 +109,7 @@ struct SecView {
     int tile0;                    // first tile of the sector
     const double2 *ph64;          // k-sectors: per-site phases e^{-2 pi i K.r/L} (fp64) ...
     const float2 *ph32;           // ... and their fp32 copy; NULL for U(1)
+    const int32_t *t2;            // with the representative table: orbit g -> row of this sector, -1 if absent
 };
 
 // ---------------------------------------------------------- host basis
@@ -133,6 +141,8 @@ struct Basis {
     std::vector<uint64_t> nnz_sec;
     bool nnz_valid = false;
     size_t smem_bytes = 0;                  // dynamic shared memory of the row kernels
+    DevBuf d_orb, d_t2;                     // representative table (LatView::orb, SecView::t2)
+    uint64_t n_orb = 0;                     // orbits (all representatives) when the table exists
 };
 
 // sector of tile t (binary search over tile0[0..S])
@@ -430,6 +440,10 @@ size_t row_kernel_smem(const Basis &B, int extra_nd);
 int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t st,
                 const int *active = nullptr);
 int count_nnz(Basis &B, uint64_t *nnz);
+// representative table: build (QS3_OK, or an error when it cannot be built) / release
+int build_rep_table(Basis &B, size_t max_bytes);
+constexpr size_t REP_TABLE_AUTO_BYTES = (size_t)1 << 30;   // built at basis creation up to this size
+void drop_rep_table(Basis &B);
 // implemented in qs3_basis.cu
 int build_sector_reps(Basis &B, int s);
 // implemented in qs3_obs.cu
