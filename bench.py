@@ -57,11 +57,11 @@ def load_peaks():
 N_SMS = 152
 
 # ncu figures of one full k_hphi launch (all sectors active) of the solve
-# workloads: warp instructions (smsp__inst_executed.sum) and DRAM bytes
-# (dram__bytes_read.sum + dram__bytes_write.sum); see the named summary
+# workloads: DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and the
+# fp64 pipe's active cycles; see the named summary
 HPHI_PROFILE = {
-    "square10x10_nd4_all_k": {"kernel": "k_hphi<4, complex128, k-sector>", "warp_inst": 1520286294,
-                              "dram_bytes": 98942208 + 38492928,
+    "square10x10_nd4_all_k": {"kernel": "k_hphi<4, complex128, k-sector, representative table>",
+                              "dram_bytes": 121114368 + 39834880, "fp64_pipe_active": 0.809,
                               "profile": "profiles/k_hphi_c128_square10x10_nd4_all_k.md"},
 }
 
@@ -155,7 +155,9 @@ def run_ours(args, rank, world):
     basis = qs3.Basis(spec, nd, Ks)
     nnz_h = basis.nnz()
     stream = torch.cuda.current_stream()
-    opts = qs3.SolveOpts(n_max=args.n_max, min_iter=20, check_every=5, eps=1e-14, res_tol=1e-12,
+    # direct launches (no CUDA graphs) so every H Phi launch is timed for the
+    # roofline; the graphs leg below times the same solve with graph replay
+    opts = qs3.SolveOpts(use_graphs=False, n_max=args.n_max, min_iter=20, check_every=5, eps=1e-14, res_tol=1e-12,
                          precision="f64", seed=1 + rank)
 
     def step(seed):
@@ -220,17 +222,19 @@ def run_ours(args, rank, world):
            "frac": round(B_alg / t_launch / 1e9 / peaks.get("hbm_gbs"), 4)}
     prof = HPHI_PROFILE.get(args.workload) if args.sectors <= 0 else None
     if prof is not None:
-        # the k-sector H Phi is bound by instruction issue (integer ALU + fp64
-        # pipes, gathers served by L2): achieved = warp instructions of a full
-        # launch (ncu count) x work fraction / live launch time; peak = 4
-        # schedulers x 152 SMs x max SM clock, one warp instruction each per clock
-        peak_inst = 4 * N_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
-        ach = prof["warp_inst"] * frac_work / t_launch / 1e9
-        roof = {"kernel": prof["kernel"], "bound": "alu", "achieved": round(ach, 1), "peak": round(peak_inst, 1),
-                "unit": "Ginst/s (warp instructions issued)", "frac": round(ach / peak_inst, 4),
+        # the k-sector complex128 H Phi is bound by the fp64 pipe (gathers are
+        # served by L2): achieved = algorithmic fp64 flops of the launch (one
+        # complex multiply-add, 8 flops, per off-diagonal term; a real x complex
+        # diagonal, 4 flops, per row) over the live launch time; peak = 2 fp64
+        # FMA per clock per SM x 152 SMs x max SM clock
+        flops = frac_work * (8.0 * (nnz_h - D) + 4.0 * D)
+        peak_fp64 = 2 * 2 * N_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = flops / t_launch / 1e12
+        roof = {"kernel": prof["kernel"], "bound": "alu", "achieved": round(ach, 4), "peak": round(peak_fp64, 4),
+                "unit": "TFLOP/s (fp64)", "frac": round(ach / peak_fp64, 4),
                 "traffic": int(prof["dram_bytes"] * frac_work), "traffic_source": prof["profile"],
-                "peak_source": "derived: 4 issue slots/clock/SM x 152 SMs x sm_max_mhz (MEASURED_PEAKS.json)",
-                "hbm_alg_bytes": hbm}
+                "peak_source": "derived: 2 fp64 FMA/clock/SM x 152 SMs x sm_max_mhz (MEASURED_PEAKS.json)",
+                "fp64_pipe_active_ncu": prof["fp64_pipe_active"], "hbm_alg_bytes": hbm}
     else:
         roof = {"kernel": "k_hphi", "bound": "hbm", **hbm, "traffic": None}
     roof["peak_hbm_source"] = (f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
@@ -285,7 +289,7 @@ def e2e_ours(args, spec, nd, Ks):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         B = qs3.Basis(spec, nd, Ks)
-        ev, vec, info = B.lanczos(qs3.SolveOpts(n_max=args.n_max, eps=1e-14, res_tol=1e-12, seed=7 + k),
+        ev, vec, info = B.lanczos(qs3.SolveOpts(use_graphs=False, n_max=args.n_max, eps=1e-14, res_tol=1e-12, seed=7 + k),
                                   vectors=True, stream=stream)
         host = vec.cpu().numpy()
         torch.cuda.synchronize()
@@ -321,6 +325,33 @@ def fp32_vs_fp64(args, basis, e_ref):
                      "refine_steps": int(info["refine_iterations"]), "status": info["status"],
                      "max_rel_dE": float(np.max(np.abs(e[:, 0] - e_ref) / np.abs(e_ref)))}
     res["speedup_f32_over_f64"] = round(res["f64"]["seconds"] / res["f32"]["seconds"], 3)
+    return res
+
+
+def graphs_leg(args, basis):
+    """fp64 Lanczos with every step after the first replayed as a CUDA graph,
+    against direct launches: one solve of the workload, and the 16-site chain
+    (N_down = 3, dim 560), where launch overhead dominates a step."""
+    import torch
+
+    import paper_2107_00872_gb300 as qs3
+    res = {}
+    for name, b, reps in (("workload", basis, 2), ("chain16_nd3_u1", qs3.Basis(qi.chain(16), 3, None), 20)):
+        r = {}
+        for g in (False, True):
+            o = qs3.SolveOpts(use_graphs=g, n_max=args.n_max, min_iter=20, check_every=5, eps=1e-14, res_tol=1e-12,
+                              precision="f64", seed=1)
+            b.lanczos(o, vectors=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                _, _, info = b.lanczos(o, vectors=False)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / reps
+            r["graphs" if g else "direct"] = {"seconds_per_solve": round(dt, 5), "steps": int(info["iterations"]),
+                                             "lanczos_steps_per_s": round(info["iterations"] / dt, 1)}
+        r["speedup"] = round(r["direct"]["seconds_per_solve"] / r["graphs"]["seconds_per_solve"], 3)
+        res[name] = r
     return res
 
 
@@ -506,6 +537,7 @@ def main():
     if rank == 0 and not args.no_extras:
         out["e2e"] = e2e_ours(args, spec, nd, Ks)
         out["fp32_vs_fp64"] = fp32_vs_fp64(args, basis, np.array(out["_evals"]))
+        out["graphs"] = graphs_leg(args, basis)
         rate, cores, desc = oracle_sample(args)
         out["cpu_baseline"] = {"value": round(rate, 6), "unit": "Gnnz/s", "cores": cores, "kind": "oracle",
                                "sample": desc}

@@ -132,7 +132,8 @@ typedef struct {
     int32_t check_every;  /* itrint: steps between convergence checks */
     double eps;           /* lnc_ene_conv: relative Ritz-value change for convergence */
     int32_t precision;    /* QS3_F64: plain fp64; QS3_F32: fp32 H Phi + fp64 recurrences + fp64 refinement */
-    int32_t use_graphs;   /* capture the Lanczos steps of a cycle in a CUDA graph */
+    int32_t use_graphs;   /* fp64 solves: replay each Lanczos step (after the first) as a CUDA graph
+                             captured once per vector-ring phase; fp32 vectors ignore it */
     uint64_t seed;        /* start vector: seeded Gaussian (SplitMix64 + Box-Muller) */
     double refine_tol;    /* fp32 mode: refine until |dE| <= refine_tol |E| (e.g. 1e-9) */
     double res_tol;       /* qs3_lanczos also needs the Ritz residual beta_m |c_m| <= res_tol max(|E|, 1); 0 = off */
@@ -146,9 +147,9 @@ typedef struct {
     double max_residual;  /* max over sectors/eigenpairs of ||H v - E v|| (fp64, unit v) */
     double seconds;       /* wall time of the call */
     uint64_t hphi_nnz;    /* structural non-zeros applied by the H Phi launches (active sectors only) */
-    double hphi_seconds;  /* device time of those launches (CUDA events on the call's stream) */
+    double hphi_seconds;  /* device time of the H Phi launches outside CUDA graphs (CUDA events on the call's stream) */
     int32_t hphi_calls;   /* H Phi launches */
-    int32_t pad_;
+    int32_t hphi_graph_calls; /* of which replayed inside CUDA graphs (not in hphi_seconds) */
 } qs3_solve_info;
 
 /* Conventional Lanczos with full reorthogonalisation (Alg. 10 lines 2-12)

@@ -43,7 +43,7 @@ int set_err(int code, const char *fmt, ...) {
 void clear_err() { g_err[0] = 0; }
 
 static std::atomic<unsigned long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 const char *last_err() { return g_err; }
 

@@ -37,7 +37,7 @@ const char *last_err();
 
 // every kernel launch of the library is followed by QS3_LAUNCHED(): it counts
 // the launch (qs3_kernel_launches) and turns a launch error into a status
-void count_launch();
+void count_launch(long long n = 1);   // n < 0 takes back launches that were only captured
 #define QS3_LAUNCHED()                                                                             \
     do {                                                                                           \
         ::qs3::count_launch();                                                                     \

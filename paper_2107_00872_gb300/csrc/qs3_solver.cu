@@ -75,6 +75,10 @@ __device__ __forceinline__ ChunkInfo chunk_info(const SecView *secs, const int *
     return ci;
 }
 
+// graph mode: the step index lives in device memory
+__global__ void k_setx(int *dx, int x) { *dx = x; }
+__global__ void k_advance(int *dx) { *dx += 1; }
+
 constexpr int RPT = BROWS / NTHREADS;   // rows per thread
 constexpr int JB = 32;                  // dot products per reduction batch
 
@@ -93,8 +97,12 @@ template <typename VT>
 __global__ void __launch_bounds__(NTHREADS) k_mdot(const VT *__restrict__ V, int64_t ld, int j0, int m,
                                                    const VT *__restrict__ w, const SecView *__restrict__ secs,
                                                    const int *__restrict__ chunk0, int S,
-                                                   const int *__restrict__ active, double2 *__restrict__ part) {
+                                                   const int *__restrict__ active, double2 *__restrict__ part,
+                                                   const int *__restrict__ dx = nullptr) {
     __shared__ double2 red[NTHREADS / 32][JB];
+    if (dx) {                         // graph mode: psi_{x-1}, psi_x, or psi_0 alone at x = 0
+        if (*dx == 0) { V += ld; m = 1; } else { m = 2; }
+    }
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
     if (active && !active[ci.s]) return;
     double2 wv[RPT];
@@ -133,24 +141,37 @@ __global__ void __launch_bounds__(NTHREADS) k_mdot(const VT *__restrict__ V, int
 }
 
 // out[s * ldo + j] = sum of part[c * m + j] over the chunks of sector s (one block per (j, s))
+// out[s * ldo + j] = sum of part[c * m + j] over the chunks of sector s; block
+// (x, s) takes j = x, x + gridDim.x, ...  Graph mode (dx): ring = the
+// three-term pass (m = 1 at x = 0, else 2, out at x - 1), otherwise the full
+// pass (m = x + 1)
 __global__ void k_reduce(const double2 *__restrict__ part, int m, const int *__restrict__ chunk0,
-                         const int *__restrict__ active, double2 *__restrict__ out, int ldo) {
-    const int j = blockIdx.x, s = blockIdx.y;
+                         const int *__restrict__ active, double2 *__restrict__ out, int ldo,
+                         const int *__restrict__ dx = nullptr, bool ring = false) {
+    const int s = blockIdx.y;
+    if (dx) {
+        const int x = *dx;
+        m = ring ? (x > 0 ? 2 : 1) : x + 1;
+        if (ring) out += max(0, x - 1);
+    }
     if (active && !active[s]) return;
     __shared__ double2 red[NTHREADS / 32];
-    double2 acc = make_double2(0.0, 0.0);
-    for (int c = chunk0[s] + threadIdx.x; c < chunk0[s + 1]; c += blockDim.x) {
-        double2 v = part[(uint64_t)c * m + j];
-        acc.x += v.x;
-        acc.y += v.y;
-    }
-    acc = warp_sum2(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double2 t = make_double2(0.0, 0.0);
-        for (int q = 0; q < NTHREADS / 32; ++q) { t.x += red[q].x; t.y += red[q].y; }
-        out[(uint64_t)s * ldo + j] = t;
+    for (int j = blockIdx.x; j < m; j += gridDim.x) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int c = chunk0[s] + threadIdx.x; c < chunk0[s + 1]; c += blockDim.x) {
+            double2 v = part[(uint64_t)c * m + j];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        acc = warp_sum2(acc);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double2 t = make_double2(0.0, 0.0);
+            for (int q = 0; q < NTHREADS / 32; ++q) { t.x += red[q].x; t.y += red[q].y; }
+            out[(uint64_t)s * ldo + j] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -160,9 +181,14 @@ __global__ void __launch_bounds__(NTHREADS) k_mupdate(VT *__restrict__ w, const 
                                                       int j0, int m, const double2 *__restrict__ coef, int ldc,
                                                       const SecView *__restrict__ secs,
                                                       const int *__restrict__ chunk0, int S,
-                                                      const int *__restrict__ active, double2 *__restrict__ part) {
+                                                      const int *__restrict__ active, double2 *__restrict__ part,
+                                                      const int *__restrict__ dx = nullptr) {
     extern __shared__ double2 sco[];
     __shared__ double red[NTHREADS / 32];
+    if (dx) {                         // graph mode: psi_{x-1}, psi_x, or psi_0 alone at x = 0
+        if (*dx == 0) { V += ld; m = 1; } else { m = 2; }
+        coef += max(0, *dx - 1);
+    }
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
     if (active && !active[ci.s]) return;
     for (int j = threadIdx.x; j < m; j += blockDim.x) sco[j] = coef[(uint64_t)ci.s * ldc + j];
@@ -200,7 +226,8 @@ __global__ void __launch_bounds__(NTHREADS) k_mupdate(VT *__restrict__ w, const 
 // per-sector scalars after a step: alpha_x, beta_x (with breakdown), 1/beta
 __global__ void k_step_scalars(int S, int x, int cap, const double2 *__restrict__ h, const double2 *__restrict__ nrm2,
                                const int *__restrict__ active, double *__restrict__ alpha, double *__restrict__ beta,
-                               double *__restrict__ inv, double brk) {
+                               double *__restrict__ inv, double brk, const int *__restrict__ dx = nullptr) {
+    if (dx) x = *dx;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S || (active && !active[s])) return;
     const double a = h[(uint64_t)s * cap + x].x;
@@ -582,9 +609,11 @@ __global__ void __launch_bounds__(NTHREADS) k_mdot_df(const typename DfS<VT>::T 
                                                       int m, const VT *__restrict__ w,
                                                       const SecView *__restrict__ secs,
                                                       const int *__restrict__ chunk0, int S,
-                                                      const int *__restrict__ active, float4 *__restrict__ part) {
+                                                      const int *__restrict__ active, float4 *__restrict__ part,
+                                                      const int *__restrict__ dx = nullptr) {
     using ST = typename DfS<VT>::T;
     __shared__ float4 red[GDF][NTHREADS];
+    if (dx) m = *dx + 1;
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
     if (active && !active[ci.s]) return;
     float4 wv[RPT];
@@ -654,25 +683,30 @@ __global__ void __launch_bounds__(NTHREADS) k_mdot_df(const typename DfS<VT>::T 
     }
 }
 
-// k_reduce for double-float chunk partials
+// k_reduce for double-float chunk partials (graph mode: m = x + 1)
 __global__ void k_reduce_df(const float4 *__restrict__ part, int m, const int *__restrict__ chunk0,
-                            const int *__restrict__ active, double2 *__restrict__ out, int ldo) {
-    const int j = blockIdx.x, s = blockIdx.y;
+                            const int *__restrict__ active, double2 *__restrict__ out, int ldo,
+                            const int *__restrict__ dx = nullptr) {
+    const int s = blockIdx.y;
+    if (dx) m = *dx + 1;
     if (active && !active[s]) return;
     __shared__ double2 red[NTHREADS / 32];
-    double2 acc = make_double2(0.0, 0.0);
-    for (int c = chunk0[s] + threadIdx.x; c < chunk0[s + 1]; c += blockDim.x) {
-        const float4 v = part[(uint64_t)c * m + j];
-        acc.x += (double)v.x + (double)v.y;
-        acc.y += (double)v.z + (double)v.w;
-    }
-    acc = warp_sum2(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double2 t = make_double2(0.0, 0.0);
-        for (int q = 0; q < NTHREADS / 32; ++q) { t.x += red[q].x; t.y += red[q].y; }
-        out[(uint64_t)s * ldo + j] = t;
+    for (int j = blockIdx.x; j < m; j += gridDim.x) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int c = chunk0[s] + threadIdx.x; c < chunk0[s + 1]; c += blockDim.x) {
+            const float4 v = part[(uint64_t)c * m + j];
+            acc.x += (double)v.x + (double)v.y;
+            acc.y += (double)v.z + (double)v.w;
+        }
+        acc = warp_sum2(acc);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double2 t = make_double2(0.0, 0.0);
+            for (int q = 0; q < NTHREADS / 32; ++q) { t.x += red[q].x; t.y += red[q].y; }
+            out[(uint64_t)s * ldo + j] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -688,8 +722,10 @@ __global__ void __launch_bounds__(NTHREADS) k_mupdate_df(VT *__restrict__ w, con
                                                          int ldc, const SecView *__restrict__ secs,
                                                          const int *__restrict__ chunk0, int S,
                                                          const int *__restrict__ active,
-                                                         const double2 *__restrict__ wn2, double2 *__restrict__ part) {
+                                                         const double2 *__restrict__ wn2, double2 *__restrict__ part,
+                                                         const int *__restrict__ dx = nullptr) {
     using ST = typename DfS<VT>::T;
+    if (dx) m = *dx + 1;
     extern __shared__ float4 scf[];   // per j: split coefficient (re.hi, re.lo, im.hi, im.lo)
     __shared__ double red[NTHREADS / 32];
     __shared__ unsigned cbits;
@@ -785,7 +821,9 @@ __global__ void __launch_bounds__(NTHREADS) k_scale_split(VT *__restrict__ w, ty
                                                           const double *__restrict__ inv,
                                                           const SecView *__restrict__ secs,
                                                           const int *__restrict__ chunk0, int S,
-                                                          const int *__restrict__ active) {
+                                                          const int *__restrict__ active,
+                                                          const int *__restrict__ dx = nullptr, uint64_t D = 0) {
+    if (dx) out += (uint64_t)(*dx + 1) * D;     // graph mode: out is the store's base, vector x + 1
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
     if (active && !active[ci.s]) return;
     const double f = inv[ci.s];
@@ -1042,6 +1080,7 @@ struct HphiStats {
     uint64_t nnz = 0;
     double sec = 0.0;
     int calls = 0;
+    int graph_calls = 0;                  // calls replayed inside CUDA graphs (not in sec)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend, freel;
     ~HphiStats() {
         for (auto &p : pend) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
@@ -1080,8 +1119,29 @@ struct Engine {
     int rp = 0, rc = 1, rw = 2;           // fp64 ring: psi_{x-1}, psi_x, work (DF only)
     std::vector<int> h_active;
     double brk;
+    // CUDA graphs (DF engine): one captured step per ring phase (indexed by
+    // rc); its kernels take the step index x from device memory (xdev)
+    bool graphs = false;
+    DevBuf xdev;
+    int xdev_val = -1;                    // value the device holds after the work queued so far
+    cudaStream_t cs = nullptr;            // capture stream
+    cudaGraphExec_t gx[3] = {nullptr, nullptr, nullptr};
+    long long gnodes[3] = {0, 0, 0};
 
     Engine(Basis &b, cudaStream_t s, HphiStats *hs) : B(b), st(s), stats(hs) { brk = DF ? 1e-12 : 1e-6; }
+    ~Engine() {
+        for (auto &g : gx)
+            if (g) cudaGraphExecDestroy(g);
+        if (cs) cudaStreamDestroy(cs);
+    }
+    Engine(const Engine &) = delete;
+    Engine &operator=(const Engine &) = delete;
+    // replay Lanczos steps as CUDA graphs (fp64 engine; ignored otherwise)
+    int enable_graphs(bool on) {
+        graphs = on && DF && B.nchunks > 0;
+        if (graphs && !xdev.p) QS3_TRY(xdev.alloc(sizeof(int)));
+        return QS3_OK;
+    }
 
     qs3_dtype dtype() const {
         if (sizeof(VT) == 4) return QS3_F32;
@@ -1218,6 +1278,85 @@ struct Engine {
         QS3_LAUNCHED();
         return normalise_start();
     }
+    // one step on stream st with every x-dependent count and offset taken
+    // from xdev (the body of the captured graphs; DF engine, not full2)
+    int step_body_dev() {
+        const int *dx = xdev.as<int>();
+        VT *w = rvec(rw);
+        QS3_TRY(hphi_launch(B, dtype(), rvec(rc), w, st, act()));
+        const int64_t ld = (int64_t)(rvec(rc) - rvec(rp));
+        double2 *hh1 = h1.as<double2>(), *n1 = nrm1.as<double2>();
+        if constexpr (DF) {
+            k_mdot<VT><<<grid(), NTHREADS, 0, st>>>(rvec(rp), ld, 0, 2, w, secs(), c0(), B.S, act(), part.as<double2>(),
+                                                    dx);
+            QS3_LAUNCHED();
+            k_reduce<<<dim3(2, B.S), NTHREADS, 0, st>>>(part.as<double2>(), 2, c0(), act(), hh1, cap, dx, true);
+            QS3_LAUNCHED();
+            k_mupdate<VT><<<grid(), NTHREADS, 2 * sizeof(double2), st>>>(w, rvec(rp), ld, 0, 2, hh1, cap, secs(), c0(),
+                                                                        B.S, act(), part.as<double2>(), dx);
+            QS3_LAUNCHED();
+            k_reduce<<<dim3(1, B.S), NTHREADS, 0, st>>>(part.as<double2>(), 1, c0(), act(), n1, 1);
+            QS3_LAUNCHED();
+            k_mdot_df<VT><<<grid(), NTHREADS, 0, st>>>(V.as<ST>(), D, 0, cap, w, secs(), c0(), B.S, act(),
+                                                       (float4 *)part.p, dx);
+            QS3_LAUNCHED();
+            k_reduce_df<<<dim3(std::min(cap, 64), B.S), NTHREADS, 0, st>>>((const float4 *)part.p, cap, c0(), act(),
+                                                                           h2.as<double2>(), cap, dx);
+            QS3_LAUNCHED();
+            k_mupdate_df<VT><<<grid(), NTHREADS, cap * sizeof(float4), st>>>(w, V.as<ST>(), D, 0, cap, h2.as<double2>(),
+                                                                           cap, secs(), c0(), B.S, act(), n1,
+                                                                           part.as<double2>(), dx);
+            QS3_LAUNCHED();
+            k_reduce<<<dim3(1, B.S), NTHREADS, 0, st>>>(part.as<double2>(), 1, c0(), act(), nrm.as<double2>(), 1);
+            QS3_LAUNCHED();
+            k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, 0, cap, hh1, nrm.as<double2>(), act(),
+                                                             alpha.as<double>(), beta.as<double>(), inv.as<double>(),
+                                                             brk, dx);
+            QS3_LAUNCHED();
+            k_scale_split<VT><<<grid(), NTHREADS, 0, st>>>(w, V.as<ST>(), inv.as<double>(), secs(), c0(), B.S, act(), dx,
+                                                           D);
+            QS3_LAUNCHED();
+            k_advance<<<1, 1, 0, st>>>(xdev.as<int>());
+            QS3_LAUNCHED();
+        }
+        return QS3_OK;
+    }
+    // the graph of the current ring phase, captured on first use
+    int graph_step(int x) {
+        if (!cs) QS3_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        if (!gx[rc]) {
+            cudaStream_t keep = st;
+            st = cs;
+            cudaGraph_t g = nullptr;
+            QS3_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            const int r = step_body_dev();
+            const cudaError_t e = cudaStreamEndCapture(cs, &g);
+            st = keep;
+            if (r != QS3_OK) {
+                if (g) cudaGraphDestroy(g);
+                return r;
+            }
+            if (e != cudaSuccess) return set_err(QS3_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+            size_t nn = 0;
+            cudaGraphGetNodes(g, nullptr, &nn);
+            const cudaError_t ei = cudaGraphInstantiate(&gx[rc], g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                gx[rc] = nullptr;
+                return set_err(QS3_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+            }
+            gnodes[rc] = (long long)nn;
+            count_launch(-(long long)nn);   // the capture ran nothing
+        }
+        if (xdev_val != x) {
+            k_setx<<<1, 1, 0, st>>>(xdev.as<int>(), x);
+            QS3_LAUNCHED();
+        }
+        QS3_CUDA(cudaGraphLaunch(gx[rc], st));
+        count_launch(gnodes[rc]);
+        xdev_val = x + 1;
+        return QS3_OK;
+    }
     // Alg. 10 lines 5-11 for step x: psi_{x+1} from H psi_x
     // full2: two Gram-Schmidt passes against all of psi_0..psi_x (the first
     // step after a thick restart, where v also has the large arrowhead
@@ -1226,6 +1365,19 @@ struct Engine {
     // recurrence, coefficients by dot product), then one classical
     // Gram-Schmidt pass against every kept vector removes the O(eps) rest.
     int step(int x, bool full2 = false) {
+        if (DF && graphs && !full2 && x >= 1) {
+            // H Phi inside a graph is not timed separately
+            stats->calls += 1;
+            stats->graph_calls += 1;
+            for (int s = 0; s < B.S; ++s)
+                if (h_active[s]) stats->nnz += B.nnz_sec[s];
+            QS3_TRY(graph_step(x));
+            const int o = rp;
+            rp = rc;
+            rc = rw;
+            rw = o;
+            return QS3_OK;
+        }
         VT *w = hout(x);
         std::pair<cudaEvent_t, cudaEvent_t> ev;
         QS3_TRY(stats->pair(ev));
@@ -1340,6 +1492,7 @@ static int lanczos_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT
     Engine<VT> E(B, st, &hs);
     const int nmax = std::max(2, o.n_max);
     QS3_TRY(E.init(nmax + 1, 0));
+    QS3_TRY(E.enable_graphs(o.use_graphs != 0));
     if (start) QS3_TRY(E.start_from(start)); else QS3_TRY(E.start_random(o.seed));
     const int S = B.S;
     R.e.assign(S, NAN);
@@ -1434,6 +1587,7 @@ static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T
     if (NK > MAXOUT) return set_err(QS3_ERR_INVALID_ARG, "n_keep %d > %d", NK, MAXOUT);
     Engine<VT> E(B, st, &hs);
     QS3_TRY(E.init(NM + 1, NK));
+    QS3_TRY(E.enable_graphs(o.use_graphs != 0));
     if (start) QS3_TRY(E.start_from(start)); else QS3_TRY(E.start_random(o.seed));
     R.e.assign((size_t)S * NE, NAN);
     R.conv.assign(S, 0);
@@ -1621,6 +1775,7 @@ static int lanczos_entry(Basis &B, const qs3_solve_opts &o, double *evals, void 
         info->hphi_nnz = hs.nnz;
         info->hphi_seconds = hs.sec;
         info->hphi_calls = hs.calls;
+        info->hphi_graph_calls = hs.graph_calls;
     }
     return all_conv(R.conv) ? QS3_OK : set_err(QS3_ERR_NOT_CONVERGED, "Lanczos did not converge in %d steps", o.n_max);
 }
@@ -1706,6 +1861,7 @@ static int trl_entry(Basis &B, const qs3_solve_opts &o, double *evals, void *eve
         info->hphi_nnz = hs.nnz;
         info->hphi_seconds = hs.sec;
         info->hphi_calls = hs.calls;
+        info->hphi_graph_calls = hs.graph_calls;
     }
     return all_conv(R.conv) ? QS3_OK
                             : set_err(QS3_ERR_NOT_CONVERGED, "thick-restart Lanczos did not converge in %d restarts",
