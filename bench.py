@@ -264,6 +264,7 @@ def run_ours(args, rank, world):
                    "parallelism": f"replicas x{world} (independent sectors per GPU)"},
         "roofline": roof,
         "gpu_launches": int(launches),
+        "tuning": basis.tuning(),
         "clocks": clocks,
         "lowest_E": float(np.min(evals)),
         "_evals": evals[:, 0].tolist(),

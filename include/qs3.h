@@ -115,6 +115,19 @@ int qs3_basis_nnz(qs3_basis_t b, uint64_t *nnz);
  * table occupies C(N, N_down) * 4 + n_sectors * n_orbits * 4 bytes of device
  * memory, library-owned, released with the basis. */
 int qs3_basis_rep_table(qs3_basis_t b, int32_t mode, int32_t *active);
+/* Autotuned launch choices of a basis (no counterpart in the paper).  On the
+ * first direct (not stream-captured) use, the library times:
+ *   - H Phi with 1..4 fewer resident 256-row blocks per SM than the occupancy
+ *     limit (the persistent grid, i.e. rows in flight per SM), per vector
+ *     dtype, and keeps the fastest;
+ *   - the double-float dot products of the fp64 Lanczos Gram-Schmidt pass
+ *     with 1, 2 or 4 basis vectors per pass (loads in flight together).
+ * set = 0: write the current choices (0 = not tuned yet) to
+ *          hphi_blocks_per_sm[4] (indexed by qs3_dtype) and *dot_vectors;
+ * set = 1: impose them (0 = tune again at the next use; blocks per SM above
+ *          the occupancy limit are clamped; dot_vectors in {0, 1, 2, 4}).
+ * Either pointer may be NULL.  Results do not depend on the choices. */
+int qs3_basis_tuning(qs3_basis_t b, int32_t set, int32_t *hphi_blocks_per_sm, int32_t *dot_vectors);
 
 /* psi = H phi (Alg. 9, pull form, one row per thread, no atomics).
  * dtype: F32/F64 on a U(1)-only basis (real H); C64/C128 on any basis.

@@ -165,6 +165,22 @@ class Basis:
             self._nnz = v.value
         return self._nnz
 
+    def tuning(self, hphi_blocks_per_sm=None, dot_vectors=None) -> dict:
+        """Autotuned launch choices: query (no arguments) or impose them
+        (hphi_blocks_per_sm: 4 values indexed by dtype code; 0 = tune again)."""
+        hb = (ctypes.c_int32 * 4)()
+        dv = ctypes.c_int32(0)
+        if hphi_blocks_per_sm is not None or dot_vectors is not None:
+            check(load().qs3_basis_tuning(self._h, 0, hb, ctypes.byref(dv)), "qs3_basis_tuning")
+            if hphi_blocks_per_sm is not None:
+                for i, v in enumerate(hphi_blocks_per_sm):
+                    hb[i] = int(v)
+            if dot_vectors is not None:
+                dv.value = int(dot_vectors)
+            check(load().qs3_basis_tuning(self._h, 1, hb, ctypes.byref(dv)), "qs3_basis_tuning")
+        check(load().qs3_basis_tuning(self._h, 0, hb, ctypes.byref(dv)), "qs3_basis_tuning")
+        return {"hphi_blocks_per_sm": list(hb), "dot_vectors": dv.value}
+
     def rep_table(self, mode: int = -1) -> bool:
         """Representative table of H Phi: 1 build, 0 release, -1 query; returns whether it is in use."""
         a = ctypes.c_int32()

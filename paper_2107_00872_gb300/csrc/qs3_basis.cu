@@ -775,6 +775,27 @@ int qs3_basis_rep_table(qs3_basis_t b, int32_t mode, int32_t *active) {
     return st;
 }
 
+int qs3_basis_tuning(qs3_basis_t b, int32_t set, int32_t *hphi_blocks_per_sm, int32_t *dot_vectors) {
+    clear_err();
+    if (!b) return set_err(QS3_ERR_INVALID_ARG, "basis is NULL");
+    Basis &B = b->B;
+    if (set) {
+        if (hphi_blocks_per_sm)
+            for (int i = 0; i < 4; ++i)
+                if (hphi_blocks_per_sm[i] < 0) return set_err(QS3_ERR_INVALID_ARG, "blocks per SM %d", hphi_blocks_per_sm[i]);
+        if (dot_vectors && !(*dot_vectors == 0 || *dot_vectors == 1 || *dot_vectors == 2 || *dot_vectors == 4))
+            return set_err(QS3_ERR_INVALID_ARG, "dot vectors per pass %d", *dot_vectors);
+        if (hphi_blocks_per_sm)
+            for (int i = 0; i < 4; ++i) B.tune_hphi[i] = hphi_blocks_per_sm[i];
+        if (dot_vectors) B.tune_nv = *dot_vectors;
+    } else {
+        if (hphi_blocks_per_sm)
+            for (int i = 0; i < 4; ++i) hphi_blocks_per_sm[i] = B.tune_hphi[i];
+        if (dot_vectors) *dot_vectors = B.tune_nv;
+    }
+    return QS3_OK;
+}
+
 const char *qs3_last_error(void) { return qs3::last_err(); }
 
 const char *qs3_strerror(int status) {

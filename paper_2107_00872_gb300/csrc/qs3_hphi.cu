@@ -387,7 +387,8 @@ static int num_sms() {
 // cache packs (smem + 1) << 32 | blocks per SM, so concurrent callers read a
 // consistent pair; the shared-memory attribute is always MAX_DYN_SMEM.
 template <typename KF>
-static int launch_rows(KF kern, Basis &B, size_t smem, std::atomic<unsigned long long> &cache, int *grid_out) {
+static int launch_rows(KF kern, Basis &B, size_t smem, std::atomic<unsigned long long> &cache, int *grid_out,
+                       int *occ_out = nullptr) {
     const unsigned long long c = cache.load(std::memory_order_acquire);
     int nb;
     if ((c >> 32) != (unsigned long long)smem + 1) {
@@ -400,15 +401,71 @@ static int launch_rows(KF kern, Basis &B, size_t smem, std::atomic<unsigned long
     }
     int grid = std::min(B.ntiles, nb * num_sms());
     *grid_out = std::max(grid, 1);
+    if (occ_out) *occ_out = nb;
+    return QS3_OK;
+}
+
+template <typename VT> struct DtIdx;
+template <> struct DtIdx<float> { static constexpr int v = QS3_F32; };
+template <> struct DtIdx<double> { static constexpr int v = QS3_F64; };
+template <> struct DtIdx<float2> { static constexpr int v = QS3_C64; };
+template <> struct DtIdx<double2> { static constexpr int v = QS3_C128; };
+
+// autotuner for the persistent grid: on the first direct launch for a basis
+// and vector type, time the kernel with 1..4 fewer resident blocks per SM
+// than the occupancy limit (rows in flight per SM) and keep the fastest.
+// H Phi is a pure function of phi, so the trial launches only rewrite psi.
+template <typename VT, typename KF>
+static int tune_grid(KF kern, Basis &B, int occ, cudaStream_t st, const VT *phi, VT *psi, const int *active,
+                     int &best_bps) {
+    const int nsm = num_sms();
+    best_bps = occ;
+    if (B.ntiles < 2 * nsm || occ <= 1) return QS3_OK;
+    cudaEvent_t e0, e1;
+    QS3_CUDA(cudaEventCreate(&e0));
+    QS3_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int rc = QS3_OK;
+    for (int b = occ; b >= std::max(1, occ - 3) && rc == QS3_OK; --b) {
+        const int grid = std::min(B.ntiles, b * nsm);
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, st);
+            kern<<<grid, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S, B.ntiles,
+                                                       phi, psi, active);
+            count_launch();
+            if (cudaGetLastError() != cudaSuccess) { rc = QS3_ERR_CUDA; break; }
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = QS3_ERR_CUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 || b < occ) tmin = std::min(tmin, ms);   // the very first launch warms up
+        }
+        if (tmin < best) { best = tmin; best_bps = b; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != QS3_OK) return set_err(rc, "H Phi autotuning launch failed");
     return QS3_OK;
 }
 
 template <int ND, typename VT, bool KS, bool TB>
 static int hphi_ndt(Basis &B, const void *phi, void *psi, cudaStream_t st, const int *active) {
     static std::atomic<unsigned long long> cache{0};
-    int grid = 1;
-    QS3_TRY(launch_rows(k_hphi<ND, VT, KS, TB>, B, B.smem_bytes, cache, &grid));
+    int grid = 1, occ = 1;
+    QS3_TRY(launch_rows(k_hphi<ND, VT, KS, TB>, B, B.smem_bytes, cache, &grid, &occ));
     if (B.ntiles == 0) return QS3_OK;
+    int &bps = B.tune_hphi[DtIdx<VT>::v];
+    if (bps == 0) {
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        QS3_CUDA(cudaStreamIsCapturing(st, &cst));
+        if (cst == cudaStreamCaptureStatusNone) {
+            int b = occ;
+            QS3_TRY(tune_grid(k_hphi<ND, VT, KS, TB>, B, occ, st, (const VT *)phi, (VT *)psi, active, b));
+            bps = b;
+        }
+    }
+    if (bps > 0) grid = std::max(1, std::min(B.ntiles, std::min(bps, occ) * num_sms()));
     k_hphi<ND, VT, KS, TB><<<grid, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(),
                                                                   B.S, B.ntiles, (const VT *)phi, (VT *)psi, active);
     QS3_LAUNCHED();

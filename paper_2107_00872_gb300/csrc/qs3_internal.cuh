@@ -143,6 +143,11 @@ struct Basis {
     size_t smem_bytes = 0;                  // dynamic shared memory of the row kernels
     DevBuf d_orb, d_t2;                     // representative table (LatView::orb, SecView::t2)
     uint64_t n_orb = 0;                     // orbits (all representatives) when the table exists
+    // autotuned launch choices, 0 = not yet tuned: resident H Phi blocks per
+    // SM per vector dtype (the persistent grid, i.e. rows in flight per SM),
+    // and basis vectors per pass of the double-float dot products
+    int tune_hphi[4] = {0, 0, 0, 0};
+    int tune_nv = 0;
 };
 
 // sector of tile t (binary search over tile0[0..S])

@@ -602,9 +602,10 @@ __device__ __forceinline__ dfl warp_sum_df(dfl a) {
 // (re.hi, re.lo, im.hi, im.lo); V double-float, w fp64.  Vectors go in groups
 // of 8: every thread leaves its partial sums in shared memory, then warp q
 // reduces vector q of the group (one shuffle tree per vector and block
-// instead of one per vector and warp).
+// instead of one per vector and warp).  NV vectors per pass have all their
+// loads in flight together (the staging depth, chosen by the autotuner).
 constexpr int GDF = NTHREADS / 32;
-template <typename VT>
+template <typename VT, int NV>
 __global__ void __launch_bounds__(NTHREADS) k_mdot_df(const typename DfS<VT>::T *__restrict__ V, uint64_t D, int j0,
                                                       int m, const VT *__restrict__ w,
                                                       const SecView *__restrict__ secs,
@@ -612,6 +613,7 @@ __global__ void __launch_bounds__(NTHREADS) k_mdot_df(const typename DfS<VT>::T 
                                                       const int *__restrict__ active, float4 *__restrict__ part,
                                                       const int *__restrict__ dx = nullptr) {
     using ST = typename DfS<VT>::T;
+    static_assert(GDF % NV == 0, "vectors per pass must divide the group");
     __shared__ float4 red[GDF][NTHREADS];
     if (dx) m = *dx + 1;
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
@@ -624,46 +626,40 @@ __global__ void __launch_bounds__(NTHREADS) k_mdot_df(const typename DfS<VT>::T 
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // rows past the chunk end read the chunk's last row (always written) and
-    // meet w = 0 there, so every load is unconditional and all of a pair of
-    // vectors' loads are in flight together
+    // meet w = 0 there, so every load is unconditional
     int ro[RPT];
 #pragma unroll
     for (int k = 0; k < RPT; ++k) ro[k] = min((int)threadIdx.x + k * NTHREADS, ci.n - 1);
     for (int jb = 0; jb < m; jb += GDF) {
         const int nj = min(GDF, m - jb);
-        for (int jj = 0; jj < nj; jj += 2) {
-            const bool two = jj + 1 < nj;
-            const ST *v0 = V + (uint64_t)(j0 + jb + jj) * D + ci.base;
-            const ST *v1 = two ? v0 + D : v0;
-            float4 a0[RPT], a1[RPT];
+        for (int jj = 0; jj < nj; jj += NV) {
+            const ST *vb = V + (uint64_t)(j0 + jb + jj) * D + ci.base;
+            float4 a[NV][RPT];
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                a0[k] = ld_df(v0 + ro[k]);
-                a1[k] = ld_df(v1 + ro[k]);
+            for (int v = 0; v < NV; ++v) {
+                const ST *vv = (jj + v < nj) ? vb + (uint64_t)v * D : vb;   // past the group: a repeat, discarded
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) a[v][k] = ld_df(vv + ro[k]);
             }
-            dfl re0 = {0.f, 0.f}, im0 = {0.f, 0.f}, re1 = {0.f, 0.f}, im1 = {0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const float4 b = wv[k];
-                // conj(a) b = (a.r b.r + a.i b.i) + i (a.r b.i - a.i b.r)
-                df_mac(re0, a0[k].x, a0[k].y, b.x, b.y);
-                df_mac(re1, a1[k].x, a1[k].y, b.x, b.y);
-                if (IsC<VT>::v) {
-                    df_mac(re0, a0[k].z, a0[k].w, b.z, b.w);
-                    df_mac(im0, a0[k].x, a0[k].y, b.z, b.w);
-                    df_mac(im0, -a0[k].z, -a0[k].w, b.x, b.y);
-                    df_mac(re1, a1[k].z, a1[k].w, b.z, b.w);
-                    df_mac(im1, a1[k].x, a1[k].y, b.z, b.w);
-                    df_mac(im1, -a1[k].z, -a1[k].w, b.x, b.y);
+            for (int v = 0; v < NV; ++v) {
+                dfl re = {0.f, 0.f}, im = {0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    const float4 b = wv[k], x = a[v][k];
+                    // conj(a) b = (a.r b.r + a.i b.i) + i (a.r b.i - a.i b.r)
+                    df_mac(re, x.x, x.y, b.x, b.y);
+                    if (IsC<VT>::v) {
+                        df_mac(re, x.z, x.w, b.z, b.w);
+                        df_mac(im, x.x, x.y, b.z, b.w);
+                        df_mac(im, -x.z, -x.w, b.x, b.y);
+                    }
                 }
-            }
-            re0 = df_norm(re0);
-            im0 = df_norm(im0);
-            red[jj][threadIdx.x] = make_float4(re0.hi, re0.lo, im0.hi, im0.lo);
-            if (two) {
-                re1 = df_norm(re1);
-                im1 = df_norm(im1);
-                red[jj + 1][threadIdx.x] = make_float4(re1.hi, re1.lo, im1.hi, im1.lo);
+                if (jj + v < nj) {
+                    re = df_norm(re);
+                    im = df_norm(im);
+                    red[jj + v][threadIdx.x] = make_float4(re.hi, re.lo, im.hi, im.lo);
+                }
             }
         }
         __syncthreads();
@@ -1181,7 +1177,8 @@ struct Engine {
         QS3_CUDA(cudaMemsetAsync(beta.p, 0, beta.n, st));
         h_active.assign(B.S, 0);
         for (int s = 0; s < B.S; ++s) h_active[s] = B.dims[s] > 0;
-        return push_active();
+        QS3_TRY(push_active());
+        return tune_dots();
     }
     int push_active() {
         QS3_CUDA(cudaMemcpyAsync(active.p, h_active.data(), B.S * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -1205,12 +1202,66 @@ struct Engine {
     int mdot(int j0, int m, const VT *w, double2 *out, int ldo) {
         if (B.nchunks == 0) return QS3_OK;
         if constexpr (DF)
-            k_mdot_df<VT><<<grid(), NTHREADS, 0, st>>>(V.as<ST>(), D, j0, m, w, secs(), c0(), B.S, act(),
-                                                       (float4 *)part.p);
+            QS3_TRY(mdot_df(B.tune_nv, j0, m, w, nullptr));
         else
             k_mdot32<VT><<<grid(), NTHREADS, 0, st>>>(V.as<VT>(), D, j0, m, w, secs(), c0(), B.S, act(), part.as<double2>());
         QS3_LAUNCHED();
         return reduce(m, out, ldo, DF);
+    }
+    // k_mdot_df with nv basis vectors per pass (1, 2 or 4; other values: 2)
+    int mdot_df(int nv, int j0, int m, const VT *w, const int *dx) {
+        if constexpr (DF) {
+            const ST *v = V.as<ST>();
+            float4 *pp = (float4 *)part.p;
+            if (nv == 1)
+                k_mdot_df<VT, 1><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx);
+            else if (nv == 4)
+                k_mdot_df<VT, 4><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx);
+            else
+                k_mdot_df<VT, 2><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx);
+            QS3_LAUNCHED();
+        }
+        return QS3_OK;
+    }
+    // autotuner for the staging depth of the dot products: time 1, 2 and 4
+    // vectors per pass on min(cap, 16) stored vectors (their contents do not
+    // matter for the timing; the partial sums are discarded) and keep the
+    // fastest for this basis
+    int tune_dots() {
+        if constexpr (DF) {
+            if (B.tune_nv != 0 || B.nchunks == 0) return QS3_OK;
+            cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+            QS3_CUDA(cudaStreamIsCapturing(st, &cst));
+            if (cst != cudaStreamCaptureStatusNone) return QS3_OK;
+            const int m = std::min(cap, 16);
+            cudaEvent_t e0, e1;
+            QS3_CUDA(cudaEventCreate(&e0));
+            QS3_CUDA(cudaEventCreate(&e1));
+            float best = 1e30f;
+            int bnv = 2;
+            int rc2 = QS3_OK;
+            for (int nv : {1, 2, 4}) {
+                float tmin = 1e30f;
+                for (int rep = 0; rep < 3 && rc2 == QS3_OK; ++rep) {
+                    if (cudaEventRecord(e0, st) != cudaSuccess) { rc2 = QS3_ERR_CUDA; break; }
+                    rc2 = mdot_df(nv, 0, m, rvec(rw), nullptr);
+                    if (rc2 != QS3_OK) break;
+                    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                        rc2 = QS3_ERR_CUDA;
+                        break;
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) tmin = std::min(tmin, ms);     // the first run warms up
+                }
+                if (tmin < best) { best = tmin; bnv = nv; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (rc2 != QS3_OK) return set_err(rc2, "dot-product autotuning failed");
+            B.tune_nv = bnv;
+        }
+        return QS3_OK;
     }
     // nrm_out (optional): per-sector |w|^2 after the update; wn2 (DF, optional):
     // |w|^2 before it, which lets small-coefficient updates run in plain fp32
@@ -1297,9 +1348,7 @@ struct Engine {
             QS3_LAUNCHED();
             k_reduce<<<dim3(1, B.S), NTHREADS, 0, st>>>(part.as<double2>(), 1, c0(), act(), n1, 1);
             QS3_LAUNCHED();
-            k_mdot_df<VT><<<grid(), NTHREADS, 0, st>>>(V.as<ST>(), D, 0, cap, w, secs(), c0(), B.S, act(),
-                                                       (float4 *)part.p, dx);
-            QS3_LAUNCHED();
+            QS3_TRY(mdot_df(B.tune_nv, 0, cap, w, dx));
             k_reduce_df<<<dim3(std::min(cap, 64), B.S), NTHREADS, 0, st>>>((const float4 *)part.p, cap, c0(), act(),
                                                                            h2.as<double2>(), cap, dx);
             QS3_LAUNCHED();
