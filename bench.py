@@ -459,6 +459,97 @@ def run_hphi_only(args):
             "hbm_frac": round(b_alg / t / 1e9 / peaks["hbm_gbs"], 4), "peak_source": kind}
 
 
+def run_trl(args):
+    """Thick-restart Lanczos (Alg. 10) on the 10x10x10 cube's k-path at
+    N_down = 3 (28 distinct sectors, 4,652,676 rows): the 4 lowest eigenpairs
+    of every sector with N_K = 8 kept and N_M = 32 Lanczos vectors, plain fp64
+    against fp32 H Phi with fp64 recurrences and fp64 refinement."""
+    import torch
+
+    import paper_2107_00872_gb300 as qs3
+    mk, nd, ks = WORKLOADS["cubic10_nd3_kpath"]
+    spec = mk()
+    Ks = sector_subset(ks(), args.sectors)
+    t0 = time.perf_counter()
+    basis = qs3.Basis(spec, nd, Ks)
+    t_build = time.perf_counter() - t0
+    out = {"mode": "trl", "workload": "cubic10_nd3_kpath", "sectors": basis.n_sectors, "total_dim": basis.total_dim,
+           "n_eig": 4, "n_keep": 8, "n_max": 32, "basis_build_s": round(t_build, 3)}
+    ref = None
+    for prec in ("f64", "f32"):
+        # convergence: the paper's criterion over the N_K kept values, at 1e-10
+        o = qs3.SolveOpts(n_eig=4, n_keep=8, n_max=32, max_iter=4000, eps=1e-10, precision=prec, refine_tol=1e-9,
+                          seed=11)
+        basis.trlanczos(o, vectors=False)          # warm-up (tuning, module load)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e, _, info = basis.trlanczos(o, vectors=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        r = {"seconds": round(dt, 4), "steps": int(info["iterations"]), "restarts": int(info["restarts"]),
+             "refine_steps": int(info["refine_iterations"]), "status": info["status"],
+             "max_residual": info["max_residual"], "hphi_calls": int(info["hphi_calls"]),
+             "gnnz_s": round(info["hphi_nnz"] / dt / 1e9, 3),
+             "ms_per_restart": round(1e3 * dt / max(1, int(info["restarts"])), 3)}
+        if ref is None:
+            ref = e
+            r["lowest_E"] = float(np.min(e))
+        else:
+            # lowest eigenvalue per sector; the other kept values may pick up a
+            # different copy of a degenerate level from another start
+            r["max_rel_dE_lowest_vs_f64"] = float(np.max(np.abs(e[:, 0] - ref[:, 0]) / np.abs(ref[:, 0])))
+        out[prec] = r
+    out["speedup_f32_over_f64"] = round(out["f64"]["seconds"] / out["f32"]["seconds"], 3)
+    return out
+
+
+def run_dsf(args):
+    """Dynamical structure factor of the 10x10 square lattice (Eq. (cfe)):
+    the N_down = 4 ground state (lowest over the 100 momenta), S^-_q of it for
+    all 100 q into the N_down = 5 sectors at k0 + q (752,875 rows each), 200
+    Lanczos steps with full reorthogonalisation per q, and the continued
+    fraction on omega = 0:0.005:8 with eta = 0.05 and h = 4.  The q values are
+    taken in groups so the Krylov store stays within device memory."""
+    import torch
+
+    import paper_2107_00872_gb300 as qs3
+    L, nd = 10, 4
+    spec = qi.square(L)
+    Ks = qi.all_k((L, L, 1))
+    src = qs3.Basis(spec, nd, Ks)
+    ev, vec, info = src.lanczos(qs3.SolveOpts(n_max=args.n_max, eps=1e-14, res_tol=1e-12, seed=1), vectors=True)
+    s0 = int(np.argmin(ev[:, 0]))
+    E0 = float(ev[s0, 0])
+    k0 = Ks[s0]
+    gs = vec[src.offsets[s0]:src.offsets[s0 + 1]].clone()
+    src1 = qs3.Basis(spec, nd, [k0])
+    omega = np.arange(0.0, 8.0 + 1e-9, 0.005)
+    group = max(1, args.q_group)
+    n_iter, eta, h = 200, 0.05, 4.0
+    t_total = 0.0
+    rows = 0
+    peaks = []
+    sq = []
+    for g0 in range(0, len(Ks), group):
+        Qs = Ks[g0:g0 + group]
+        K2 = [tuple((k0[a] + Q[a]) % (L if a < 2 else 1) for a in range(3)) for Q in Qs]
+        dst = qs3.Basis(spec, nd + 1, K2)
+        rows += dst.total_dim
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S, al, be, n2 = qs3.dsf(src1, 0, gs, E0, dst, Qs, n_iter, eta, h, omega)
+        torch.cuda.synchronize()
+        t_total += time.perf_counter() - t0
+        peaks += [float(np.max(S[i])) for i in range(len(Qs))]
+        sq += [float(v) for v in n2]
+        del dst
+    return {"mode": "dsf", "workload": "square10x10_nd4_to_nd5_all_q", "E0": E0, "k0": list(k0), "q_points": len(Ks),
+            "rows_all_q": rows, "cf_steps": n_iter, "omega_points": len(omega), "eta": eta, "h": h,
+            "q_group": group, "seconds": round(t_total, 3), "seconds_per_q": round(t_total / len(Ks), 4),
+            "lanczos_steps_per_s": round(len(Ks) * n_iter / t_total, 1),
+            "max_peak": max(peaks), "sum_sq_pm": sum(sq)}
+
+
 def run_batch(args):
     """The uneven instance mix: 64 seeded XXZ instances (chains, squares,
     cubes; half with a random momentum) solved to their lowest eigenvalue in
@@ -506,7 +597,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="solve", choices=["solve", "hphi", "batch"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "hphi", "batch", "trl", "dsf"])
+    ap.add_argument("--q-group", dest="q_group", type=int, default=25, help="--mode dsf: q values per call")
     ap.add_argument("--n-instances", dest="n_instances", type=int, default=64, help="--mode batch")
     ap.add_argument("--concurrency", type=int, default=16, help="--mode batch")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64", "f64", "f32"], help="--mode hphi only")
@@ -523,6 +615,12 @@ def main():
         return
     if args.mode == "batch":
         print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.mode == "trl":
+        print(json.dumps(run_trl(args)), flush=True)
+        return
+    if args.mode == "dsf":
+        print(json.dumps(run_dsf(args)), flush=True)
         return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
