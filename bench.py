@@ -135,6 +135,21 @@ class ClockSampler:
 
 # --------------------------------------------------------------- our arm
 
+def reduce_ranks(t_local: float, units: float, world: int, device):
+    """Whole-job figures of a replicated run: the slowest rank's time and the
+    units (non-zeros applied) of all ranks.  No data-path collective: each
+    rank solves its own replica; only these two scalars are exchanged."""
+    if world <= 1:
+        return t_local, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_local], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([units], device=device, dtype=torch.float64)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 def sector_subset(Ks, n):
     """The first n momenta of a workload (all of them for n <= 0 or a U(1) workload)."""
     if Ks is None or n <= 0:
@@ -195,15 +210,7 @@ def run_ours(args, rank, world):
     hphi_s = sum(i["hphi_seconds"] for i in infos)
     hphi_calls = sum(i["hphi_calls"] for i in infos)
     t_local = ms_total / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        n = torch.tensor([float(nnz_steps)], device=dev, dtype=torch.float64)
-        dist.all_reduce(n, op=dist.ReduceOp.SUM)
-        t_max, nnz_all = float(t.item()), float(n.item())
-    else:
-        t_max, nnz_all = t_local, float(nnz_steps)
+    t_max, nnz_all = reduce_ranks(t_local, float(nnz_steps), world, dev)
     value = nnz_all / t_max / 1e9
 
     # roofline of the H Phi launches (dominant kernel of the step)
