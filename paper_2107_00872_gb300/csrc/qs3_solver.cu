@@ -1850,26 +1850,33 @@ static int trl_entry(Basis &B, const qs3_solve_opts &o, double *evals, void *eve
     TrlResult R;
     int iters = 0, refine = 0, restarts = 0;
     if (o.precision == QS3_F32) {
-        QS3_TRY(trl_run<V32>(B, o, nullptr, out, st, R, hs));
+        // fp32 phase to fp32 resolution, keeping all N_K Ritz vectors: the
+        // criterion covers the N_K kept values, so the fp64 refinement starts
+        // from the sum of all of them (its first Krylov space then holds the
+        // whole kept set, not only the wanted n_eig)
+        qs3_solve_opts o1 = o;
+        o1.eps = std::max(o.eps, 2e-7);
+        o1.n_eig = NK;
+        DevBuf kept;
+        QS3_TRY(kept.alloc((uint64_t)NK * B.total * sizeof(V64)));
+        QS3_CUDA(cudaMemsetAsync(kept.p, 0, (uint64_t)NK * B.total * sizeof(V64), st));
+        QS3_TRY(trl_run<V32>(B, o1, nullptr, kept.as<V64>(), st, R, hs));
         iters += R.steps;
         restarts += R.restarts;
-        // fp64 refinement: restart the fp64 iteration from the sum of the fp32 Ritz vectors
         DevBuf sum;
         QS3_TRY(sum.alloc(B.total * sizeof(V64)));
-        QS3_CUDA(cudaMemcpyAsync(sum.p, out, B.total * sizeof(V64), cudaMemcpyDeviceToDevice, st));
-        if (NE > 1) {
-            std::vector<double> C((size_t)B.S * NE, 1.0);
+        {
+            std::vector<double> C((size_t)B.S * NK, 1.0);
             std::vector<int> all(B.S, 1);
-            // sum of the NE vectors: a combination kernel over the output block
             DevBuf dC, dm;
             QS3_TRY(dC.alloc(C.size() * 8));
             QS3_TRY(dm.alloc(all.size() * 4));
             QS3_CUDA(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, st));
             QS3_CUDA(cudaMemcpyAsync(dm.p, all.data(), all.size() * 4, cudaMemcpyHostToDevice, st));
             if (B.nchunks) {
-                k_combine<V64, V64><<<B.nchunks, NTHREADS, NE * sizeof(double), st>>>(
-                    sum.as<V64>(), B.total, out, B.total, NE, 1, dC.as<double>(), NE, B.d_secs.as<SecView>(),
-                    B.d_chunk0.as<int>(), B.S, dm.as<int>());
+                k_combine<V64, V64><<<B.nchunks, NTHREADS, NK * sizeof(double), st>>>(
+                    sum.as<V64>(), B.total, kept.as<V64>(), B.total, NK, 1, dC.as<double>(), NK,
+                    B.d_secs.as<SecView>(), B.d_chunk0.as<int>(), B.S, dm.as<int>());
                 QS3_LAUNCHED();
             }
             QS3_CUDA(cudaStreamSynchronize(st));
