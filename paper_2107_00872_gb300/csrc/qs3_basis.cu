@@ -552,6 +552,8 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     // adjacency (CSR, both directions), diagonal constants
     std::vector<int> deg(N + 1, 0);
     for (int b = 0; b < nb; ++b) { deg[B.bi[b] + 1]++; deg[B.bj[b] + 1]++; }
+    B.max_degree = 0;
+    for (int i = 0; i < N; ++i) B.max_degree = std::max(B.max_degree, deg[i + 1]);
     for (int i = 0; i < N; ++i) deg[i + 1] += deg[i];
     std::vector<int> nbr(2 * (size_t)nb), fill(deg.begin(), deg.end() - 1);
     std::vector<double> ajxy(2 * (size_t)nb), ajz(2 * (size_t)nb), u(N, 0.0);
@@ -678,6 +680,7 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     B.smem_bytes = row_kernel_smem(B, 0);
     if (B.smem_bytes > 200 * 1024)
         return set_err(QS3_ERR_OVERFLOW, "lattice tables need %zu bytes of shared memory", B.smem_bytes);
+    B.narrow_ranks = !B.has_k && nd >= 1 && B.total > 0 && B.total < (1ull << 32);
     // the representative table when it is small (a bounded fraction of the
     // device memory); otherwise H Phi runs the representative search
     if (B.has_k && nd > 0 && B.total > 0 && N <= 4096) {

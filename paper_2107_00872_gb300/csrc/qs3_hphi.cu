@@ -309,6 +309,101 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
     }
 }
 
+// U(1) H Phi with 32-bit ranks, for C(N, N_down) < 2^32, N_down <= 4 and fp32
+// vectors: the binomial rows 0..N_down as a 32-bit table in shared memory
+// (a third of the 64-bit layout, so more blocks fit an SM), one thread per
+// row striding over the single sector, and per occupied site the ranks of its
+// first DEGB hop targets (DEGB = the lattice's largest degree, 4 or 6)
+// formed before their gathers issue together.  With DEGB = 4 the kernel fits
+// 40 registers, so six blocks reside per SM (more gathers in flight).  Same
+// signature as k_hphi (the launch and the autotuner treat both alike).
+template <int ND, typename VT, int DEGB>
+__global__ void __launch_bounds__(NTHREADS, DEGB <= 4 ? 6 : 4) k_hphi_u1n(LatView L, const SecView *__restrict__ secs,
+                                                      const int *__restrict__ tile0, int S, int ntiles,
+                                                      const VT *__restrict__ phi, VT *__restrict__ psi,
+                                                      const int *__restrict__ active) {
+    using R = typename VTr<VT>::R;
+    using CT = typename VTr<VT>::C;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *sC = (uint32_t *)smem;
+    const int np1 = L.np1;
+    for (int i = threadIdx.x; i < (ND + 1) * np1; i += blockDim.x) sC[i] = (uint32_t)L.binom[i];
+    __syncthreads();
+    if (active && !active[0]) return;
+    const uint64_t dim = secs[0].dim;     // < 2^32
+    const R *jxy = jxy_table<VT>(L);
+    for (uint64_t rw = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; rw < dim; rw += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t row = (uint32_t)rw;
+        int c[ND];
+        unrank32(row, sC, np1, c);
+        const VT x0 = phi[row];
+        R e = diag_c0<R>(L), dd = 0;
+        CT acc;
+        acc.x = 0; acc.y = 0;
+#pragma unroll
+        for (int m = 0; m < ND; ++m) {
+            const int i = c[m];
+            e += diag_u<R>(L, i);
+            const int e0 = __ldg(L.adj_ptr + i), e1 = __ldg(L.adj_ptr + i + 1);
+            const uint32_t base = row - sC[(m + 1) * np1 + i];
+            uint32_t r2b[DEGB];
+            R cfb[DEGB];
+#pragma unroll
+            for (int b = 0; b < DEGB; ++b) {
+                const int q = e0 + b;
+                cfb[b] = 0;
+                r2b[b] = 0;
+                if (q < e1) {
+                    const int j = __ldg(L.adj_nbr + q);
+                    bool occ = false;
+#pragma unroll
+                    for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
+                    if (occ) {
+                        dd += diag_jz<R>(L, q);
+                    } else {
+                        const bool inplace = (m == 0 || j > c[m > 0 ? m - 1 : 0]) &&
+                                             (m == ND - 1 || j < c[m + 1 < ND ? m + 1 : m]);
+                        if (inplace) {
+                            r2b[b] = base + sC[(m + 1) * np1 + j];
+                        } else {
+                            int tt[ND];
+#pragma unroll
+                            for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
+                            sort_net(tt);
+                            r2b[b] = rank_of32(tt, sC, np1);
+                        }
+                        cfb[b] = __ldg(jxy + q);
+                    }
+                }
+            }
+            VT vb[DEGB];
+#pragma unroll
+            for (int b = 0; b < DEGB; ++b)
+                if (cfb[b] != (R)0) vb[b] = phi[r2b[b]];
+#pragma unroll
+            for (int b = 0; b < DEGB; ++b)
+                if (cfb[b] != (R)0) madd_r(acc, cfb[b], vb[b]);
+            for (int q = e0 + DEGB; q < e1; ++q) {
+                const int j = __ldg(L.adj_nbr + q);
+                bool occ = false;
+#pragma unroll
+                for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
+                if (occ) {
+                    dd += diag_jz<R>(L, q);
+                    continue;
+                }
+                int tt[ND];
+#pragma unroll
+                for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
+                sort_net(tt);
+                madd_r(acc, __ldg(jxy + q), phi[rank_of32(tt, sC, np1)]);
+            }
+        }
+        madd_r(acc, e + (R)0.5 * dd, x0);
+        store(psi + row, acc);
+    }
+}
+
 // nnz count per sector: the diagonal plus every hop that lands on a member of the sector
 template <int ND, bool KS>
 __global__ void __launch_bounds__(NTHREADS) k_count(LatView L, const SecView *__restrict__ secs,
@@ -417,7 +512,8 @@ template <> struct DtIdx<double2> { static constexpr int v = QS3_C128; };
 // H Phi is a pure function of phi, so the trial launches only rewrite psi.
 template <typename VT, typename KF>
 static int tune_grid(KF kern, Basis &B, int occ, cudaStream_t st, const VT *phi, VT *psi, const int *active,
-                     int &best_bps) {
+                     int &best_bps, size_t smem = (size_t)-1) {
+    if (smem == (size_t)-1) smem = B.smem_bytes;
     const int nsm = num_sms();
     best_bps = occ;
     if (B.ntiles < 2 * nsm || occ <= 1) return QS3_OK;
@@ -431,8 +527,8 @@ static int tune_grid(KF kern, Basis &B, int occ, cudaStream_t st, const VT *phi,
         float tmin = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
             cudaEventRecord(e0, st);
-            kern<<<grid, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S, B.ntiles,
-                                                       phi, psi, active);
+            kern<<<grid, NTHREADS, smem, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S, B.ntiles, phi,
+                                               psi, active);
             count_launch();
             if (cudaGetLastError() != cudaSuccess) { rc = QS3_ERR_CUDA; break; }
             cudaEventRecord(e1, st);
@@ -472,10 +568,38 @@ static int hphi_ndt(Basis &B, const void *phi, void *psi, cudaStream_t st, const
     return QS3_OK;
 }
 
+template <int ND, typename VT, int DEGB>
+static int hphi_u1n(Basis &B, const void *phi, void *psi, cudaStream_t st, const int *active) {
+    static std::atomic<unsigned long long> cache{0};
+    const size_t smem = (size_t)(ND + 1) * (B.N + 1) * sizeof(uint32_t);
+    int grid = 1, occ = 1;
+    QS3_TRY(launch_rows(k_hphi_u1n<ND, VT, DEGB>, B, smem, cache, &grid, &occ));
+    if (B.ntiles == 0) return QS3_OK;
+    int &bps = B.tune_hphi[DtIdx<VT>::v];
+    if (bps == 0) {
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        QS3_CUDA(cudaStreamIsCapturing(st, &cst));
+        if (cst == cudaStreamCaptureStatusNone) {
+            int b = occ;
+            QS3_TRY(tune_grid(k_hphi_u1n<ND, VT, DEGB>, B, occ, st, (const VT *)phi, (VT *)psi, active, b, smem));
+            bps = b;
+        }
+    }
+    if (bps > 0) grid = std::max(1, std::min(B.ntiles, std::min(bps, occ) * num_sms()));
+    k_hphi_u1n<ND, VT, DEGB><<<grid, NTHREADS, smem, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S,
+                                                           B.ntiles, (const VT *)phi, (VT *)psi, active);
+    QS3_LAUNCHED();
+    return QS3_OK;
+}
+
 template <int ND, typename VT, bool KS>
 static int hphi_nd(Basis &B, const void *phi, void *psi, cudaStream_t st, const int *active) {
     if constexpr (KS) {
         if (B.lv.orb) return hphi_ndt<ND, VT, true, true>(B, phi, psi, st, active);
+    } else if constexpr (ND <= 4 && sizeof(typename VTr<VT>::R) == 4) {
+        if (B.narrow_ranks)
+            return B.max_degree <= 4 ? hphi_u1n<ND, VT, 4>(B, phi, psi, st, active)
+                                     : hphi_u1n<ND, VT, 6>(B, phi, psi, st, active);
     }
     return hphi_ndt<ND, VT, KS, false>(B, phi, psi, st, active);
 }

@@ -148,6 +148,8 @@ struct Basis {
     // and basis vectors per pass of the double-float dot products
     int tune_hphi[4] = {0, 0, 0, 0};
     int tune_nv = 0;
+    bool narrow_ranks = false;              // U(1) with C(N, N_down) < 2^32: 32-bit rank kernels apply
+    int max_degree = 0;                     // largest number of adjacency entries of a site
 };
 
 // sector of tile t (binary search over tile0[0..S])
@@ -224,6 +226,50 @@ __device__ __forceinline__ void unrank(uint64_t r, const uint64_t *__restrict__ 
     for (int m = ND; m >= 2; --m) {
         const uint64_t *col = sC + m * np1;
         const int x = col_search(col, m, hi, r);
+        c[m - 1] = x;
+        r -= col[x];
+        hi = x - 1;
+    }
+    if (ND >= 1) c[0] = (int)r;
+}
+
+// 32-bit forms for state spaces with C(N, N_down) < 2^32: every binomial a
+// rank needs (rows 0..N_down) then fits 32 bits
+template <int ND>
+__device__ __forceinline__ uint32_t rank_of32(const int (&c)[ND], const uint32_t *__restrict__ sC, int np1) {
+    uint32_t r = 0;
+#pragma unroll
+    for (int m = 0; m < ND; ++m) r += sC[(m + 1) * np1 + c[m]];
+    return r;
+}
+
+__device__ __forceinline__ int col_search32(const uint32_t *__restrict__ col, int m, int hi, uint32_t r) {
+    constexpr float lf[9] = {0.f, 0.f, 1.f, 2.5849625f, 4.5849625f, 6.9068906f, 9.4918531f, 12.299208f, 15.299208f};
+    int x = m - 1;
+    if (r > 0) x = (int)(exp2f((__log2f((float)r) + lf[m]) / (float)m) + 0.5f * (float)(m - 1));
+    x = max(m - 1, min(x, hi));
+#pragma unroll 1
+    for (int it = 0; it < 3 && x < hi && col[x + 1] <= r; ++it) ++x;
+#pragma unroll 1
+    for (int it = 0; it < 3 && col[x] > r; ++it) --x;
+    if (col[x] > r || (x < hi && col[x + 1] <= r)) {
+        int lo = m - 1, h = hi;
+        while (lo < h) {
+            const int mid = (lo + h + 1) >> 1;
+            if (col[mid] <= r) lo = mid; else h = mid - 1;
+        }
+        x = lo;
+    }
+    return x;
+}
+
+template <int ND>
+__device__ __forceinline__ void unrank32(uint32_t r, const uint32_t *__restrict__ sC, int np1, int (&c)[ND]) {
+    int hi = np1 - 2;
+#pragma unroll
+    for (int m = ND; m >= 2; --m) {
+        const uint32_t *col = sC + m * np1;
+        const int x = col_search32(col, m, hi, r);
         c[m - 1] = x;
         r -= col[x];
         hi = x - 1;
