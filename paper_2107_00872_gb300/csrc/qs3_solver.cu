@@ -606,7 +606,7 @@ __device__ __forceinline__ dfl warp_sum_df(dfl a) {
 // loads in flight together (the staging depth, chosen by the autotuner).
 constexpr int GDF = NTHREADS / 32;
 template <typename VT, int NV>
-__global__ void __launch_bounds__(NTHREADS) k_mdot_df(const typename DfS<VT>::T *__restrict__ V, uint64_t D, int j0,
+__global__ void __launch_bounds__(NTHREADS, NV == 2 ? 3 : 1) k_mdot_df(const typename DfS<VT>::T *__restrict__ V, uint64_t D, int j0,
                                                       int m, const VT *__restrict__ w,
                                                       const SecView *__restrict__ secs,
                                                       const int *__restrict__ chunk0, int S,
