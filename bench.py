@@ -61,7 +61,7 @@ N_SMS = 152
 # fp64 pipe's active cycles; see the named summary
 HPHI_PROFILE = {
     "square10x10_nd4_all_k": {"kernel": "k_hphi<4, complex128, k-sector, representative table>",
-                              "dram_bytes": 121114368 + 39834880, "fp64_pipe_active": 0.809,
+                              "dram_bytes": 122385664 + 40377856, "fp64_pipe_active": 0.809,
                               "profile": "profiles/k_hphi_c128_square10x10_nd4_all_k.md"},
 }
 
