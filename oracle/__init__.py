@@ -337,6 +337,68 @@ def fold(sec: Sector, phi_u: np.ndarray) -> np.ndarray:
     return out
 
 
+# ------------------------------------------- S^alpha_q from its definition
+# "In the same manner" as Alg. 11 the paper also applies S^+_q and S^z_q
+# (input_dynamic: spsmsz = 1 for S^+, 2 for S^-, 3 for S^z).  Written here
+# from S^alpha_q = N^{-1/2} sum_j e^{-i q.R_j} S^alpha_j and each S^alpha_j's
+# action on one U(1) state, then carried to a momentum sector by unfold/fold.
+
+OP_SPLUS, OP_SMINUS, OP_SZ = 1, 2, 3
+
+
+def site_phases_q(N: int, L, Q, pos: np.ndarray | None = None) -> np.ndarray:
+    """e^{-i q.R_j} for every site j with q.a_alpha = 2 pi Q_alpha / L_alpha;
+    R_j = (x, y, z) of the site index j = x + Lx (y + Ly z), or pos[j]."""
+    L = np.array(L if tuple(L) != (0, 0, 0) else (N, 1, 1), dtype=np.int64)
+    if pos is None:
+        j = np.arange(N)
+        R = np.stack([j % L[0], (j // L[0]) % L[1], j // (L[0] * L[1])], -1).astype(np.float64)
+    else:
+        R = np.asarray(pos, np.float64).reshape(N, 3)
+    return np.exp(-2j * np.pi * (R * (np.asarray(Q, np.float64) / L)).sum(1))
+
+
+def sq_apply_u1(N: int, nd: int, op: int, phi_u: np.ndarray, Q, L, pos: np.ndarray | None = None) -> np.ndarray:
+    """S^alpha_q phi on a U(1) vector of nd down spins (0-based rank order):
+    S^+_j removes the down spin at j (zero if j is up), S^-_j puts one at an
+    up site j, S^z_j multiplies by 1/2 - n_j.  The result has nd - 1 (S^+),
+    nd + 1 (S^-) or nd (S^z) down spins."""
+    states = unrank_all(N, nd)
+    ph = site_phases_q(N, L, Q, pos)
+    nd2 = nd - 1 if op == OP_SPLUS else (nd + 1 if op == OP_SMINUS else nd)
+    if nd2 < 0 or nd2 > N:
+        raise ValueError("operator leaves the state space")
+    out = np.zeros(binom(N, nd2), np.complex128)
+
+    def idx(sites):
+        return F(N, [v + 1 for v in sites]) - 1 if sites else 0
+
+    for a in range(len(phi_u)):
+        x = phi_u[a]
+        if x == 0:
+            continue
+        down = set(int(v) for v in states[a]) if nd > 0 else set()
+        if op == OP_SZ:
+            out[a] += x * sum(ph[j] * (0.5 - (1.0 if j in down else 0.0)) for j in range(N))
+        elif op == OP_SPLUS:
+            for j in down:
+                out[idx(sorted(down - {j}))] += ph[j] * x
+        else:
+            for j in range(N):
+                if j not in down:
+                    out[idx(sorted(down | {j}))] += ph[j] * x
+    return out / np.sqrt(N)
+
+
+def sq_apply_k(src: Sector, phi_k: np.ndarray, op: int, Q, dst: Sector, pos: np.ndarray | None = None) -> np.ndarray:
+    """S^alpha_q on a vector of sector (nd, K) into sector dst (nd2, K + Q):
+    unfold to the U(1) basis, apply sq_apply_u1, project onto dst."""
+    lat = src.lat
+    u = unfold(src, np.asarray(phi_k, np.complex128))
+    v = sq_apply_u1(lat.n_sites, src.nd, op, u, Q, lat.L, pos)
+    return fold(dst, v)
+
+
 # ------------------------------------------------------ Lanczos, Alg. 10, CF
 
 

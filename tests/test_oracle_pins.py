@@ -429,3 +429,72 @@ def test_row_terms_without_sigma_equal_dense_rows():
         # a non-representative is rejected
         a_non = next(a for a in range(1, orc.binom(spec.n_sites, nd) + 1) if a not in index)
         assert orc.row_terms_k(lat, nd, K, a_non) is None
+
+
+# ------------------------------------------------ S^+_q and S^z_q (spsmsz 1, 3)
+
+@pytest.mark.parametrize("dims,nd", [((8, 1, 1), 2), ((4, 3, 1), 2), ((3, 2, 2), 2)])
+def test_sq_apply_sminus_equals_alg11(dims, nd):
+    """The definition-based operator code reproduces Alg. 11 (the C push form)."""
+    lat = olat(qi.hypercubic(dims))
+    for K in qi.all_k(dims)[:2]:
+        src = orc.mk_list(lat, nd, K)
+        phi = qi.gaussian_start(9, src.dim, True)
+        for Q in qi.all_k(dims)[:3]:
+            dst = orc.mk_list(lat, nd + 1, tuple((K[a] + Q[a]) % dims[a] for a in range(3)))
+            np.testing.assert_allclose(orc.sq_apply_k(src, phi, orc.OP_SMINUS, Q, dst), orc.smq(src, phi, Q, dst),
+                                       atol=1e-12)
+
+
+@pytest.mark.parametrize("dims,nd", [((8, 1, 1), 2), ((4, 3, 1), 2), ((3, 2, 2), 1)])
+def test_splus_is_the_adjoint_of_sminus(dims, nd):
+    """<chi, S^-_q phi> = <S^+_{-q} chi, phi>, with S^-_q from Alg. 11."""
+    lat = olat(qi.hypercubic(dims))
+    for K in qi.all_k(dims)[:2]:
+        src = orc.mk_list(lat, nd, K)
+        phi = qi.gaussian_start(4, src.dim, True)
+        for Q in qi.all_k(dims)[:3]:
+            K2 = tuple((K[a] + Q[a]) % dims[a] for a in range(3))
+            dst = orc.mk_list(lat, nd + 1, K2)
+            chi = qi.gaussian_start(5, dst.dim, True)
+            mq = tuple((-Q[a]) % dims[a] for a in range(3))
+            lhs = np.vdot(chi, orc.smq(src, phi, Q, dst))
+            rhs = np.vdot(orc.sq_apply_k(dst, chi, orc.OP_SPLUS, mq, src), phi)
+            assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs)), (K, Q)
+
+
+@pytest.mark.parametrize("dims,nd", [((8, 1, 1), 3), ((4, 3, 1), 2)])
+def test_sz_adjoint_and_zero_momentum(dims, nd):
+    """(S^z_q)^dag = S^z_{-q}, and S^z_{q=0} phi = (N/2 - N_down) N^{-1/2} phi."""
+    lat = olat(qi.hypercubic(dims))
+    N = lat.n_sites
+    for K in qi.all_k(dims)[:2]:
+        src = orc.mk_list(lat, nd, K)
+        phi = qi.gaussian_start(6, src.dim, True)
+        np.testing.assert_allclose(orc.sq_apply_k(src, phi, orc.OP_SZ, (0, 0, 0), src),
+                                   (N / 2 - nd) / np.sqrt(N) * phi, atol=1e-12)
+        for Q in qi.all_k(dims)[1:3]:
+            K2 = tuple((K[a] + Q[a]) % dims[a] for a in range(3))
+            dst = orc.mk_list(lat, nd, K2)
+            chi = qi.gaussian_start(7, dst.dim, True)
+            mq = tuple((-Q[a]) % dims[a] for a in range(3))
+            lhs = np.vdot(chi, orc.sq_apply_k(src, phi, orc.OP_SZ, Q, dst))
+            rhs = np.vdot(orc.sq_apply_k(dst, chi, orc.OP_SZ, mq, src), phi)
+            assert abs(lhs - rhs) < 1e-12 * max(1.0, abs(lhs)), (K, Q)
+
+
+def test_sq_sum_rules_u1():
+    """Parseval over all q: sum_q |S^z_q phi|^2 = N/4, sum_q |S^+_q phi|^2 =
+    N_down, sum_q |S^-_q phi|^2 = N - N_down (unit phi)."""
+    N, nd = 10, 3
+    rng = np.random.default_rng(1)
+    phi = rng.normal(size=comb(N, nd)) + 1j * rng.normal(size=comb(N, nd))
+    phi /= np.linalg.norm(phi)
+    tot = {orc.OP_SZ: 0.0, orc.OP_SPLUS: 0.0, orc.OP_SMINUS: 0.0}
+    for q in range(N):
+        for op in tot:
+            v = orc.sq_apply_u1(N, nd, op, phi, (q, 0, 0), (N, 1, 1))
+            tot[op] += np.vdot(v, v).real
+    assert abs(tot[orc.OP_SZ] - N / 4) < 1e-12
+    assert abs(tot[orc.OP_SPLUS] - nd) < 1e-12
+    assert abs(tot[orc.OP_SMINUS] - (N - nd)) < 1e-12
