@@ -516,7 +516,9 @@ def run_dsf(args):
     all 100 q into the N_down = 5 sectors at k0 + q (752,875 rows each), 200
     Lanczos steps with full reorthogonalisation per q, and the continued
     fraction on omega = 0:0.005:8 with eta = 0.05 and h = 4.  The q values are
-    taken in groups so the Krylov store stays within device memory."""
+    taken in groups so the Krylov store stays within device memory.  --op sz
+    or splus computes S^z (same N_down, trivial q = 0 peak subtracted) or S^+
+    (N_down - 1) instead."""
     import torch
 
     import paper_2107_00872_gb300 as qs3
@@ -533,6 +535,8 @@ def run_dsf(args):
     omega = np.arange(0.0, 8.0 + 1e-9, 0.005)
     group = max(1, args.q_group)
     n_iter, eta, h = 200, 0.05, 4.0
+    op = {"sminus": 2, "splus": 1, "sz": 3}[args.op]
+    dn = {2: 1, 1: -1, 3: 0}[op]
     t_total = 0.0
     rows = 0
     peaks = []
@@ -540,21 +544,23 @@ def run_dsf(args):
     for g0 in range(0, len(Ks), group):
         Qs = Ks[g0:g0 + group]
         K2 = [tuple((k0[a] + Q[a]) % (L if a < 2 else 1) for a in range(3)) for Q in Qs]
-        dst = qs3.Basis(spec, nd + 1, K2)
+        dst = qs3.Basis(spec, nd + dn, K2)
         rows += dst.total_dim
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        S, al, be, n2 = qs3.dsf(src1, 0, gs, E0, dst, Qs, n_iter, eta, h, omega)
+        S, al, be, n2 = qs3.dsf(src1, 0, gs, E0, dst, Qs, n_iter, eta, h, omega, op=op, subtract_trivial=(op == 3))
         torch.cuda.synchronize()
         t_total += time.perf_counter() - t0
         peaks += [float(np.max(S[i])) for i in range(len(Qs))]
         sq += [float(v) for v in n2]
         del dst
-    return {"mode": "dsf", "workload": "square10x10_nd4_to_nd5_all_q", "E0": E0, "k0": list(k0), "q_points": len(Ks),
+    return {"mode": "dsf", "operator": args.op, "workload": f"square10x10_nd4_to_nd{nd + dn}_all_q", "E0": E0,
+            "k0": list(k0), "q_points": len(Ks),
             "rows_all_q": rows, "cf_steps": n_iter, "omega_points": len(omega), "eta": eta, "h": h,
             "q_group": group, "seconds": round(t_total, 3), "seconds_per_q": round(t_total / len(Ks), 4),
             "lanczos_steps_per_s": round(len(Ks) * n_iter / t_total, 1),
-            "max_peak": max(peaks), "sum_sq_pm": sum(sq)}
+            "max_peak": max(peaks), "sum_norm2": sum(sq),
+            "sum_rule": {"sminus": "N - N_down = 96", "splus": "N_down = 4", "sz": "N/4 = 25"}[args.op]}
 
 
 def run_batch(args):
@@ -606,6 +612,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="solve", choices=["solve", "hphi", "batch", "trl", "dsf"])
     ap.add_argument("--q-group", dest="q_group", type=int, default=25, help="--mode dsf: q values per call")
+    ap.add_argument("--op", default="sminus", choices=["sminus", "splus", "sz"], help="--mode dsf: S^alpha_q")
     ap.add_argument("--n-instances", dest="n_instances", type=int, default=64, help="--mode batch")
     ap.add_argument("--concurrency", type=int, default=16, help="--mode batch")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64", "f64", "f32"], help="--mode hphi only")

@@ -57,6 +57,9 @@ enum {
 
 typedef enum { QS3_F32 = 0, QS3_F64 = 1, QS3_C64 = 2, QS3_C128 = 3 } qs3_dtype;
 
+/* S^alpha_q operators, numbered as the paper's input parameter spsmsz. */
+typedef enum { QS3_OP_SPLUS = 1, QS3_OP_SMINUS = 2, QS3_OP_SZ = 3 } qs3_sq_op;
+
 /* Lattice and couplings of Eq. (1): H = sum_b [Jxy_b (s^x s^x + s^y s^y) +
  * Jz_b s^z s^z] - sum_i h_i s^z_i.  Bond b joins sites bi[b] != bj[b]; a
  * repeated pair adds its couplings.  h may be NULL (no field).  L = {0,0,0}
@@ -244,6 +247,35 @@ int qs3_smq_noalloc(qs3_basis_t src, int32_t s_src, const void *phi, qs3_basis_t
 int qs3_dsf(qs3_basis_t src, int32_t s_src, const void *gs, double e0, qs3_basis_t dst, int32_t n_q,
             const int32_t *Q, int32_t n_iter, double eta, double h_field, int32_t n_omega, const double *omega,
             double *s_qw, double *alpha, double *beta, double *norm2, void *stream);
+
+/* S^alpha_q phi for alpha = op (qs3_sq_op), with S^alpha_q = N^{-1/2}
+ * sum_j e^{-i q.R_j} S^alpha_j (Eq. sq_phi; the paper applies S^+_q and S^z_q
+ * "in the same manner" as Alg. 11).  src sector s_src (N_down, K) -> dst
+ * sector s_dst (N_down - 1 for S^+, N_down + 1 for S^-, N_down for S^z;
+ * momentum K + Q).  Pull forms: S^z_q keeps the representative, a row b
+ * taking N^{-1/2} (sum_j e^{-iq.R_j}/2 - sum_{j in b} e^{-iq.R_j}) phi_b (0 if
+ * b is not in the source sector); S^+_q sums a row over its up sites s with
+ * the representative of b + {s}, its translation phase and norm ratio.
+ * op = QS3_OP_SMINUS is qs3_smq.  phi, psi: device C128 vectors of the
+ * sector dimensions (NULL allowed for an empty sector); the call
+ * synchronises stream.  Errors: INVALID_ARG
+ * (operator, N_down or lattice mismatch, sector index), SYMMETRY (momentum
+ * not K + Q). */
+int qs3_sq_apply(int32_t op, qs3_basis_t src, int32_t s_src, const void *phi, qs3_basis_t dst, int32_t s_dst,
+                 const int32_t *Q, void *psi, void *stream);
+
+/* qs3_dsf for any S^alpha_q (op as in qs3_sq_apply): dst holds, in order,
+ * the n_q sectors (N_down + dN, K + Q_n) with dN = -1, +1, 0 for S^+, S^-,
+ * S^z.  The field enters the resolvent as the Zeeman shift h_field * dN
+ * (poles at E_n - e0 + h_field dN).  subtract_trivial != 0 with op = S^z
+ * removes, at every q equivalent to 0, the ground state's own delta peak
+ * broadened to eta / (pi (omega^2 + eta^2)) M^2 / N with M = N/2 - N_down
+ * (the paper's longitudinal factor with the trivial component subtracted).
+ * Other arguments, outputs and errors as qs3_dsf. */
+int qs3_dsf_op(int32_t op, int32_t subtract_trivial, qs3_basis_t src, int32_t s_src, const void *gs, double e0,
+               qs3_basis_t dst, int32_t n_q, const int32_t *Q, int32_t n_iter, double eta, double h_field,
+               int32_t n_omega, const double *omega, double *s_qw, double *alpha, double *beta, double *norm2,
+               void *stream);
 
 /* Text of a status code, and of the last failure on the calling thread. */
 const char *qs3_strerror(int status);

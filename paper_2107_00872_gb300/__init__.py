@@ -293,10 +293,23 @@ def smq_noalloc(src: Basis, s_src: int, phi, dst: Basis, s_dst: int, Q, psi, str
     return psi
 
 
+OP_SPLUS, OP_SMINUS, OP_SZ = 1, 2, 3
+
+
+def sq_apply(op: int, src: Basis, s_src: int, phi, dst: Basis, s_dst: int, Q, psi=None, stream=None):
+    """S^alpha_q phi (op 1 = S^+, 2 = S^-, 3 = S^z) from sector s_src of src into sector s_dst of dst."""
+    if psi is None:
+        psi = _torch().zeros(dst.dims[s_dst], dtype=_torch().complex128, device="cuda")
+    Qc = np.ascontiguousarray(np.asarray(Q, np.int32).reshape(3))
+    check(load().qs3_sq_apply(int(op), src.handle, s_src, _dev(phi, src.dims[s_src], "phi"), dst.handle, s_dst,
+                              _ptr(Qc), _dev(psi, dst.dims[s_dst], "psi"), _stream(stream)), "qs3_sq_apply")
+    return psi
+
+
 def dsf(src: Basis, s_src: int, gs, e0: float, dst: Basis, Qs, n_iter: int, eta: float, h_field: float,
-        omega: np.ndarray, stream=None):
-    """S^-(q, omega) by the continued fraction for each momentum of Qs
-    (dst holds the matching sectors, in order)."""
+        omega: np.ndarray, stream=None, op: int = OP_SMINUS, subtract_trivial: bool = False):
+    """S^alpha(q, omega) by the continued fraction for each momentum of Qs
+    (dst holds the matching sectors, in order); op 1 = S^+, 2 = S^-, 3 = S^z."""
     Q = np.ascontiguousarray(np.asarray(Qs, np.int32).reshape(-1, 3))
     nq = len(Q)
     om = np.ascontiguousarray(omega, np.float64)
@@ -304,7 +317,13 @@ def dsf(src: Basis, s_src: int, gs, e0: float, dst: Basis, Qs, n_iter: int, eta:
     al = np.zeros(nq * n_iter)
     be = np.zeros(nq * n_iter)
     n2 = np.zeros(nq)
-    check(load().qs3_dsf(src.handle, s_src, _dev(gs, src.dims[s_src], "gs"), float(e0), dst.handle, nq, _ptr(Q),
-                         int(n_iter), float(eta), float(h_field), len(om), _ptr(om), _ptr(s), _ptr(al), _ptr(be),
-                         _ptr(n2), _stream(stream)), "qs3_dsf")
+    if op == OP_SMINUS and not subtract_trivial:
+        check(load().qs3_dsf(src.handle, s_src, _dev(gs, src.dims[s_src], "gs"), float(e0), dst.handle, nq, _ptr(Q),
+                             int(n_iter), float(eta), float(h_field), len(om), _ptr(om), _ptr(s), _ptr(al), _ptr(be),
+                             _ptr(n2), _stream(stream)), "qs3_dsf")
+    else:
+        check(load().qs3_dsf_op(int(op), int(bool(subtract_trivial)), src.handle, s_src,
+                                _dev(gs, src.dims[s_src], "gs"), float(e0), dst.handle, nq, _ptr(Q), int(n_iter),
+                                float(eta), float(h_field), len(om), _ptr(om), _ptr(s), _ptr(al), _ptr(be), _ptr(n2),
+                                _stream(stream)), "qs3_dsf_op")
     return s.reshape(nq, len(om)), al.reshape(nq, n_iter), be.reshape(nq, n_iter), n2

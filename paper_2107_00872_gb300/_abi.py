@@ -52,6 +52,8 @@ SIGNATURES = {
     "qs3_smq": ([P, I32, P, P, I32, P, P, P], I32),
     "qs3_smq_noalloc": ([P, I32, P, P, I32, P, P, P], I32),
     "qs3_dsf": ([P, I32, P, F64, P, I32, P, I32, F64, F64, I32, P, P, P, P, P, P], I32),
+    "qs3_sq_apply": ([I32, P, I32, P, P, I32, P, P, P], I32),
+    "qs3_dsf_op": ([I32, I32, P, I32, P, F64, P, I32, P, I32, F64, F64, I32, P, P, P, P, P, P], I32),
     "qs3_strerror": ([I32], ctypes.c_char_p),
     "qs3_last_error": ([], ctypes.c_char_p),
     "qs3_version": ([], ctypes.c_char_p),

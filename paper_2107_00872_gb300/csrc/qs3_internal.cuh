@@ -498,6 +498,8 @@ void drop_rep_table(Basis &B);
 // implemented in qs3_basis.cu
 int build_sector_reps(Basis &B, int s);
 // implemented in qs3_obs.cu
+int sq_launch(int op, Basis &src, int s_src, const void *phi, Basis &dst, int s_dst, const int *Q, void *psi,
+              cudaStream_t st);
 int smq_launch(Basis &src, int s_src, const void *phi, Basis &dst, int s_dst, const int *Q, void *psi,
                cudaStream_t st);
 

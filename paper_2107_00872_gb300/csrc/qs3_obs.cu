@@ -307,6 +307,138 @@ __global__ void k_smq_vac(SecView svd, int ks, int N, const double2 *__restrict_
     psi[row] = make_double2(f * (p.x * x.x - p.y * x.y), f * (p.x * x.y + p.y * x.x));
 }
 
+// ------------------------------------------------- S^z_q and S^+_q
+// The paper applies S^+_q and S^z_q "in the same manner" as Alg. 11
+// (spsmsz = 1, 3).  Pull forms, with S^alpha_q = N^{-1/2} sum_s e^{-iq.R_s}
+// S^alpha_s:
+//  S^z_q: N_down and the representative are kept, k -> k + q.  A row b of the
+//    target sector takes psi'_b = N^{-1/2} (sum_s e^{-iq.R_s} / 2 - sum_{s in b}
+//    e^{-iq.R_s}) phi_b when b is also a representative of the source sector
+//    (s^z_s = 1/2 - n_s; no translation, norm ratio 1), else 0.
+//  S^+_q: N_down -> N_down - 1.  A row b sums over the up sites s of b:
+//    psi'_b = N^{-1/2} sum_{s not in b} sqrt(|Stab a| / |Stab b|) e^{ik.u}
+//    e^{-iq.R_s} phi_a, with a the representative of b + {s} and
+//    T^u (b + {s}) = a (skipped when a is not in the source sector).
+template <int ND, bool KS>
+__global__ void __launch_bounds__(NTHREADS) k_szq(LatView Ls, SecView svs, SecView svd,
+                                                  const double2 *__restrict__ phsite, double2 half_sum,
+                                                  double inv_sqrt_n, const double2 *__restrict__ phi,
+                                                  double2 *__restrict__ psi) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    ObsSmem sm = obs_carve(Ls, smem, false);
+    __syncthreads();
+    for (uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; row < svd.dim;
+         row += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t rank = KS ? __ldg(svd.sigma + row) : row;
+        int c[ND];
+        unrank(rank, sm.sC, Ls.np1, c);
+        uint64_t idx = row;
+        if constexpr (KS) {
+            uint32_t i32;
+            if (!sigma_find(svs, prefix_of(c, sm.sC, Ls.np1), rank, i32)) {
+                psi[row] = make_double2(0.0, 0.0);
+                continue;
+            }
+            idx = i32;
+        }
+        double2 f = half_sum;
+#pragma unroll
+        for (int m = 0; m < ND; ++m) {
+            const double2 p = phsite[c[m]];
+            f.x -= p.x;
+            f.y -= p.y;
+        }
+        const double2 x = phi[idx];
+        psi[row] = make_double2(inv_sqrt_n * (f.x * x.x - f.y * x.y), inv_sqrt_n * (f.x * x.y + f.y * x.x));
+    }
+}
+
+// ND is the target N_down (>= 1); the tables staged are the source basis'
+template <int ND, bool KS>
+__global__ void __launch_bounds__(NTHREADS) k_spq(LatView Ls, SecView svs, SecView svd,
+                                                  const double2 *__restrict__ phsite, double inv_sqrt_n,
+                                                  const double2 *__restrict__ phi, double2 *__restrict__ psi) {
+    constexpr int NS = ND + 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    ObsSmem sm = obs_carve(Ls, smem, false);
+    if (KS) fill_axis_phases(Ls.L, svs.K, sm.phk);
+    __syncthreads();
+    const double2 *phk = sm.phk, *phy = sm.phk + Ls.L[0], *phz = sm.phk + Ls.L[0] + Ls.L[1];
+    for (uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; row < svd.dim;
+         row += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t rank = KS ? __ldg(svd.sigma + row) : row;
+        int c[ND];
+        unrank(rank, sm.sC, Ls.np1, c);
+        const double rb = KS ? sm.snorm[9 + __ldg(svd.stab + row)] : 1.0;
+        double2 acc = make_double2(0.0, 0.0);
+#pragma unroll 1
+        for (int sidx = 0; sidx < Ls.N; ++sidx) {
+            bool occ = false;
+#pragma unroll
+            for (int k = 0; k < ND; ++k) occ |= (c[k] == sidx);
+            if (occ) continue;
+            int t[NS];
+#pragma unroll
+            for (int k = 0; k < ND; ++k) t[k] = c[k];
+            t[ND] = sidx;
+            sort_net(t);
+            double2 coef = phsite[sidx];
+            uint64_t idx;
+            if constexpr (KS) {
+                int rep[NS];
+                int ax, by, cz;
+                const uint64_t r2 = canon(t, Ls, sm.sxyz, sm.sC, rep, ax, by, cz);
+                uint32_t i32;
+                if (!sigma_find(svs, prefix_of(rep, sm.sC, Ls.np1), r2, i32)) continue;
+                idx = i32;
+                coef = cmul2(coef, cmul2(cmul2(phk[ax], phy[by]), phz[cz]));
+                const double w = sm.snorm[__ldg(svs.stab + idx)] * rb;
+                coef.x *= w;
+                coef.y *= w;
+            } else {
+                idx = rank_of(t, sm.sC, Ls.np1);
+            }
+            const double2 x = phi[idx];
+            acc.x += coef.x * x.x - coef.y * x.y;
+            acc.y += coef.x * x.y + coef.y * x.x;
+        }
+        psi[row] = make_double2(acc.x * inv_sqrt_n, acc.y * inv_sqrt_n);
+    }
+}
+
+// S^+_q from N_down = 1 to the vacuum (one row): psi' = N^{-1/2} sum_s e^{-iq.R_s}
+// [U(1): phi_s; k: e^{ik.R_s} sqrt(1/N) phi_0, the source's single representative
+// being {0} with |Stab| = 1 and the vacuum's |Stab| = N]
+__global__ void k_spq_vac(int N, int Lx, int Ly, int ks, int Kx, int Ky, int Kz, int Lz,
+                          const double2 *__restrict__ phsite, const double2 *__restrict__ phi,
+                          double2 *__restrict__ psi) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int s = 0; s < N; ++s) {
+        double2 c = phsite[s];
+        double2 x;
+        if (ks) {
+            const int x0 = s % Lx, y0 = (s / Lx) % Ly, z0 = s / (Lx * Ly);
+            // e^{ik.u} with the translation moving s to the origin, as the per-axis tables
+            const long long num = ((long long)Kx * x0 * (N / Lx) + (long long)Ky * y0 * (N / Ly) +
+                                   (long long)Kz * z0 * (N / Lz)) % N;
+            double sn, cs;
+            sincospi(-2.0 * (double)num / (double)N, &sn, &cs);
+            c = cmul2(c, make_double2(cs, sn));
+            const double w = 1.0 / sqrt((double)N);
+            c.x *= w;
+            c.y *= w;
+            x = phi[0];
+        } else {
+            x = phi[s];
+        }
+        acc.x += c.x * x.x - c.y * x.y;
+        acc.y += c.x * x.y + c.y * x.x;
+    }
+    const double f = 1.0 / sqrt((double)N);
+    psi[0] = make_double2(acc.x * f, acc.y * f);
+}
+
 // S(q, omega) = -(1/pi) Im[ norm2 / (z - a_0 - b_0^2 / (z - a_1 - ...)) ],
 // z = omega + e0 - h + i eta, evaluated from the deepest level up (Eq. cfe)
 __global__ void k_cfrac(int nq, int cap, const double *__restrict__ alpha, const double *__restrict__ beta,
@@ -422,7 +554,8 @@ static std::vector<double2> site_phases(const Basis &B, const int *Q) {
         double p[3];
         site_pos(B, r, p);
         double t = 0.0;
-        for (int a = 0; a < 3; ++a) t += 2.0 * M_PI * Q[a] * p[a] / B.L[a];
+        for (int a = 0; a < 3; ++a)
+            if (B.L[a] > 0) t += 2.0 * M_PI * Q[a] * p[a] / B.L[a];    // no translation group: q = 0
         ph[r] = make_double2(std::cos(t), -std::sin(t));
     }
     return ph;
@@ -454,6 +587,120 @@ int smq_launch(Basis &S, int ss, const void *phi, Basis &Dd, int sd, const int *
         QS3_LAUNCHED();
     } else {
         QS3_TRY(dispatch_smq(S, ss, Dd, sd, dph.as<double2>(), (const double2 *)phi, (double2 *)psi, st));
+    }
+    QS3_CUDA(cudaStreamSynchronize(st));     // dph is released on return
+    return QS3_OK;
+}
+
+template <int ND>
+static int szq_nd(Basis &S, int ss, Basis &Dd, int sd, const double2 *phs, double2 half_sum, const double2 *phi,
+                  double2 *psi, cudaStream_t st) {
+    const size_t smem = obs_smem_bytes(S.nd + 3, S.N, S.L, false);
+    if (smem > 200 * 1024) return set_err(QS3_ERR_OVERFLOW, "S^z_q tables need %zu bytes of shared memory", smem);
+    const double isn = 1.0 / std::sqrt((double)S.N);
+    if (S.has_k) {
+        QS3_CUDA(cudaFuncSetAttribute(k_szq<ND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
+        k_szq<ND, true><<<grid_for(Dd.dims[sd]), NTHREADS, smem, st>>>(S.lv, S.secs[ss], Dd.secs[sd], phs, half_sum,
+                                                                        isn, phi, psi);
+    } else {
+        QS3_CUDA(cudaFuncSetAttribute(k_szq<ND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
+        k_szq<ND, false><<<grid_for(Dd.dims[sd]), NTHREADS, smem, st>>>(S.lv, S.secs[ss], Dd.secs[sd], phs, half_sum,
+                                                                         isn, phi, psi);
+    }
+    QS3_LAUNCHED();
+    return QS3_OK;
+}
+
+template <int ND>
+static int spq_nd(Basis &S, int ss, Basis &Dd, int sd, const double2 *phs, const double2 *phi, double2 *psi,
+                  cudaStream_t st) {
+    const size_t smem = obs_smem_bytes(S.nd + 3, S.N, S.L, false);
+    if (smem > 200 * 1024) return set_err(QS3_ERR_OVERFLOW, "S^+_q tables need %zu bytes of shared memory", smem);
+    const double isn = 1.0 / std::sqrt((double)S.N);
+    if (S.has_k) {
+        QS3_CUDA(cudaFuncSetAttribute(k_spq<ND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
+        k_spq<ND, true><<<grid_for(Dd.dims[sd]), NTHREADS, smem, st>>>(S.lv, S.secs[ss], Dd.secs[sd], phs, isn, phi,
+                                                                        psi);
+    } else {
+        QS3_CUDA(cudaFuncSetAttribute(k_spq<ND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
+        k_spq<ND, false><<<grid_for(Dd.dims[sd]), NTHREADS, smem, st>>>(S.lv, S.secs[ss], Dd.secs[sd], phs, isn, phi,
+                                                                         psi);
+    }
+    QS3_LAUNCHED();
+    return QS3_OK;
+}
+
+#define QS3_ND_SWITCH(nd, CALL)                                            \
+    switch (nd) {                                                          \
+        case 1: return CALL(1);                                            \
+        case 2: return CALL(2);                                            \
+        case 3: return CALL(3);                                            \
+        case 4: return CALL(4);                                            \
+        case 5: return CALL(5);                                            \
+        case 6: return CALL(6);                                            \
+        case 7: return CALL(7);                                            \
+        case 8: return CALL(8);                                            \
+        default: return set_err(QS3_ERR_INVALID_ARG, "n_down %d", (nd)); \
+    }
+
+static int dispatch_szq(Basis &S, int ss, Basis &Dd, int sd, const double2 *phs, double2 hs, const double2 *phi,
+                        double2 *psi, cudaStream_t st) {
+#define QS3_SZQ(n) szq_nd<n>(S, ss, Dd, sd, phs, hs, phi, psi, st)
+    QS3_ND_SWITCH(S.nd, QS3_SZQ)
+#undef QS3_SZQ
+}
+
+static int dispatch_spq(Basis &S, int ss, Basis &Dd, int sd, const double2 *phs, const double2 *phi, double2 *psi,
+                        cudaStream_t st) {
+#define QS3_SPQ(n) spq_nd<n>(S, ss, Dd, sd, phs, phi, psi, st)
+    QS3_ND_SWITCH(Dd.nd, QS3_SPQ)
+#undef QS3_SPQ
+}
+
+// S^alpha_q phi (alpha by the paper's spsmsz code: 1 S^+, 2 S^-, 3 S^z) from
+// sector ss of S into sector sd of Dd
+int sq_launch(int op, Basis &S, int ss, const void *phi, Basis &Dd, int sd, const int *Q, void *psi,
+              cudaStream_t st) {
+    if (op == QS3_OP_SMINUS) return smq_launch(S, ss, phi, Dd, sd, Q, psi, st);
+    if (op != QS3_OP_SPLUS && op != QS3_OP_SZ) return set_err(QS3_ERR_INVALID_ARG, "operator %d", op);
+    if (S.N != Dd.N || S.L[0] != Dd.L[0] || S.L[1] != Dd.L[1] || S.L[2] != Dd.L[2])
+        return set_err(QS3_ERR_INVALID_ARG, "source and target bases are on different lattices");
+    const int want = op == QS3_OP_SPLUS ? S.nd - 1 : S.nd;
+    if (Dd.nd != want || want < 0)
+        return set_err(QS3_ERR_INVALID_ARG, "target n_down must be source n_down %s", op == QS3_OP_SPLUS ? "- 1" : "");
+    if (S.has_k != Dd.has_k) return set_err(QS3_ERR_INVALID_ARG, "both bases need momenta, or neither");
+    if (ss < 0 || ss >= S.S || sd < 0 || sd >= Dd.S) return set_err(QS3_ERR_INVALID_ARG, "sector index");
+    if (S.has_k)
+        for (int a = 0; a < 3; ++a)
+            if (((S.K[3 * ss + a] + Q[a]) % S.L[a] + S.L[a]) % S.L[a] != Dd.K[3 * sd + a])
+                return set_err(QS3_ERR_SYMMETRY, "target momentum is not K + Q (axis %d)", a);
+    if (Dd.dims[sd] == 0) return QS3_OK;
+    std::vector<double2> ph = site_phases(S, Q);
+    double2 hs = make_double2(0.0, 0.0);
+    for (const double2 &v : ph) { hs.x += 0.5 * v.x; hs.y += 0.5 * v.y; }
+    DevBuf dph;
+    QS3_TRY(dph.upload(ph.data(), ph.size() * sizeof(double2)));
+    if (S.dims[ss] == 0) {
+        QS3_CUDA(cudaMemsetAsync(psi, 0, Dd.dims[sd] * 16, st));
+    } else if (op == QS3_OP_SZ) {
+        if (S.nd == 0) {
+            // the vacuum: S^z_q |0> = N^{-1/2} (sum_s e^{-iq.R_s} / 2) |0>
+            const double f = 1.0 / std::sqrt((double)S.N);
+            double2 x;
+            QS3_CUDA(cudaMemcpyAsync(&x, phi, sizeof(double2), cudaMemcpyDeviceToHost, st));
+            QS3_CUDA(cudaStreamSynchronize(st));
+            const double2 y = make_double2(f * (hs.x * x.x - hs.y * x.y), f * (hs.x * x.y + hs.y * x.x));
+            QS3_CUDA(cudaMemcpyAsync(psi, &y, sizeof(double2), cudaMemcpyHostToDevice, st));
+        } else {
+            QS3_TRY(dispatch_szq(S, ss, Dd, sd, dph.as<double2>(), hs, (const double2 *)phi, (double2 *)psi, st));
+        }
+    } else if (Dd.nd == 0) {
+        k_spq_vac<<<1, 32, 0, st>>>(S.N, S.L[0], S.L[1], S.has_k ? 1 : 0, S.has_k ? S.K[3 * ss] : 0,
+                                    S.has_k ? S.K[3 * ss + 1] : 0, S.has_k ? S.K[3 * ss + 2] : 0, S.L[2],
+                                    dph.as<double2>(), (const double2 *)phi, (double2 *)psi);
+        QS3_LAUNCHED();
+    } else {
+        QS3_TRY(dispatch_spq(S, ss, Dd, sd, dph.as<double2>(), (const double2 *)phi, (double2 *)psi, st));
     }
     QS3_CUDA(cudaStreamSynchronize(st));     // dph is released on return
     return QS3_OK;
@@ -623,9 +870,9 @@ extern "C" int qs3_smq(qs3_basis_t src, int32_t s_src, const void *phi, qs3_basi
 
 // implemented in qs3_solver.cu (uses the Lanczos engine)
 namespace qs3 {
-int dsf_run(Basis &S, int ss, const void *gs, double e0, Basis &Dd, int nq, const int *Q, int n_iter, double eta,
-            double h, int nw, const double *omega, double *s_qw, double *alpha, double *beta, double *norm2,
-            cudaStream_t st);
+int dsf_run(int op, Basis &S, int ss, const void *gs, double e0, Basis &Dd, int nq, const int *Q, int n_iter,
+            double eta, double h, int nw, const double *omega, double *s_qw, double *alpha, double *beta,
+            double *norm2, cudaStream_t st);
 int cfrac_launch(int nq, int cap, const double *alpha, const double *beta, const int *msz, const double *norm2,
                  double e0, double h, double eta, const double *omega, int nw, double *out, cudaStream_t st) {
     const int n = nq * nw;
@@ -644,8 +891,50 @@ extern "C" int qs3_dsf(qs3_basis_t src, int32_t s_src, const void *gs, double e0
     if (n_q < 1 || n_q != dst->B.S) return set_err(QS3_ERR_INVALID_ARG, "n_q %d must equal the target sectors %d", n_q, dst->B.S);
     if (n_iter < 1 || n_iter > 2047) return set_err(QS3_ERR_INVALID_ARG, "n_iter %d outside [1, 2047]", n_iter);
     if (!(eta > 0)) return set_err(QS3_ERR_INVALID_ARG, "eta must be positive");
-    return dsf_run(src->B, s_src, gs, e0, dst->B, n_q, Q, n_iter, eta, h_field, n_omega, omega, s_qw, alpha, beta,
-                   norm2, (cudaStream_t)stream);
+    return dsf_run(QS3_OP_SMINUS, src->B, s_src, gs, e0, dst->B, n_q, Q, n_iter, eta, h_field, n_omega, omega, s_qw,
+                   alpha, beta, norm2, (cudaStream_t)stream);
+}
+
+extern "C" int qs3_sq_apply(int32_t op, qs3_basis_t src, int32_t s_src, const void *phi, qs3_basis_t dst,
+                            int32_t s_dst, const int32_t *Q, void *psi, void *stream) {
+    clear_err();
+    if (!src || !dst || !Q) return set_err(QS3_ERR_INVALID_ARG, "NULL argument");
+    if (s_src < 0 || s_src >= src->B.S || s_dst < 0 || s_dst >= dst->B.S)
+        return set_err(QS3_ERR_INVALID_ARG, "sector index");
+    // a vector of an empty sector may be NULL
+    if ((!phi && src->B.dims[s_src] > 0) || (!psi && dst->B.dims[s_dst] > 0))
+        return set_err(QS3_ERR_INVALID_ARG, "NULL vector");
+    return sq_launch(op, src->B, s_src, phi, dst->B, s_dst, Q, psi, (cudaStream_t)stream);
+}
+
+extern "C" int qs3_dsf_op(int32_t op, int32_t subtract_trivial, qs3_basis_t src, int32_t s_src, const void *gs,
+                          double e0, qs3_basis_t dst, int32_t n_q, const int32_t *Q, int32_t n_iter, double eta,
+                          double h_field, int32_t n_omega, const double *omega, double *s_qw, double *alpha,
+                          double *beta, double *norm2, void *stream) {
+    clear_err();
+    if (op != QS3_OP_SPLUS && op != QS3_OP_SMINUS && op != QS3_OP_SZ)
+        return set_err(QS3_ERR_INVALID_ARG, "operator %d", op);
+    if (!src || !dst || !gs || !Q || (n_omega > 0 && !omega)) return set_err(QS3_ERR_INVALID_ARG, "NULL argument");
+    if (n_q < 1 || n_q != dst->B.S) return set_err(QS3_ERR_INVALID_ARG, "n_q %d must equal the target sectors %d", n_q, dst->B.S);
+    if (n_iter < 1 || n_iter > 2047) return set_err(QS3_ERR_INVALID_ARG, "n_iter %d outside [1, 2047]", n_iter);
+    if (!(eta > 0)) return set_err(QS3_ERR_INVALID_ARG, "eta must be positive");
+    QS3_TRY(dsf_run(op, src->B, s_src, gs, e0, dst->B, n_q, Q, n_iter, eta, h_field, n_omega, omega, s_qw, alpha,
+                    beta, norm2, (cudaStream_t)stream));
+    if (op == QS3_OP_SZ && subtract_trivial && s_qw && n_omega > 0) {
+        const Basis &S = src->B;
+        const double M = 0.5 * S.N - S.nd;
+        for (int n = 0; n < n_q; ++n) {
+            bool zero = true;
+            for (int a = 0; a < 3; ++a) {
+                const int La = std::max(S.L[a], 1);
+                zero &= ((Q[3 * n + a] % La) + La) % La == 0;
+            }
+            if (!zero) continue;
+            for (int w = 0; w < n_omega; ++w)
+                s_qw[(size_t)n * n_omega + w] -= eta / (M_PI * (omega[w] * omega[w] + eta * eta)) * M * M / S.N;
+        }
+    }
+    return QS3_OK;
 }
 
 // ----------------------------------------------- S^-_q without allocation

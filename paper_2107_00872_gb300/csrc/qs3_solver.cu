@@ -1975,16 +1975,16 @@ namespace qs3 {
 int cfrac_launch(int nq, int cap, const double *alpha, const double *beta, const int *msz, const double *norm2,
                  double e0, double h, double eta, const double *omega, int nw, double *out, cudaStream_t st);
 
-int dsf_run(Basis &S, int ss, const void *gs, double e0, Basis &Dd, int nq, const int *Q, int n_iter, double eta,
-            double h, int nw, const double *omega, double *s_qw, double *alpha, double *beta, double *norm2,
-            cudaStream_t st) {
+int dsf_run(int op, Basis &S, int ss, const void *gs, double e0, Basis &Dd, int nq, const int *Q, int n_iter,
+            double eta, double h, int nw, const double *omega, double *s_qw, double *alpha, double *beta,
+            double *norm2, cudaStream_t st) {
     uint64_t nz = 0;
     QS3_TRY(count_nnz(Dd, &nz));
     HphiStats hs;
     Engine<double2> E(Dd, st, &hs);
     QS3_TRY(E.init(n_iter + 1, 0));
     for (int n = 0; n < nq; ++n)
-        QS3_TRY(smq_launch(S, ss, gs, Dd, n, Q + 3 * n, E.hin(0) + Dd.offs[n], st));
+        QS3_TRY(sq_launch(op, S, ss, gs, Dd, n, Q + 3 * n, E.hin(0) + Dd.offs[n], st));
     QS3_TRY(E.normalise_start());
     std::vector<double2> n2(nq);
     QS3_CUDA(cudaMemcpyAsync(n2.data(), E.nrm.p, nq * sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -2018,8 +2018,9 @@ int dsf_run(Basis &S, int ss, const void *gs, double e0, Basis &Dd, int nq, cons
         QS3_TRY(dn.upload(nrm2.data(), nq * sizeof(double)));
         QS3_TRY(dw.upload(omega, nw * sizeof(double)));
         QS3_TRY(dout.alloc((size_t)nq * nw * sizeof(double)));
+        // Zeeman shift of the resolvent: h times the change of N_down
         QS3_TRY(cfrac_launch(nq, E.cap, E.alpha.as<double>(), E.beta.as<double>(), dm.as<int>(), dn.as<double>(), e0,
-                             h, eta, dw.as<double>(), nw, dout.as<double>(), st));
+                             h * (double)(Dd.nd - S.nd), eta, dw.as<double>(), nw, dout.as<double>(), st));
         QS3_CUDA(cudaMemcpyAsync(s_qw, dout.p, (size_t)nq * nw * sizeof(double), cudaMemcpyDeviceToHost, st));
         QS3_CUDA(cudaStreamSynchronize(st));
     }
