@@ -438,6 +438,13 @@ def run_hphi_only(args):
     spec = mk()
     Ks = ks()
     B = qs3.Basis(spec, nd, Ks)
+    t_store = None
+    if args.stored:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.store_terms(1)
+        torch.cuda.synchronize()
+        t_store = time.perf_counter() - t0
     dt = {"c128": torch.complex128, "c64": torch.complex64, "f64": torch.float64, "f32": torch.float32}[args.dtype]
     if Ks and not dt.is_complex:
         raise SystemExit("k-sectors need complex vectors")
@@ -459,8 +466,12 @@ def run_hphi_only(args):
     s = phi.element_size()
     D = B.total_dim
     b_alg = D * s + (nnz - D) * s + D * s + (D * 8 + (nnz - D) * 8 if Ks else 0)
+    if args.stored:
+        # per term: target row + code (8 B) and one gather; per row: x0, psi, diagonal, row pointer
+        b_alg = D * s + (nnz - D) * s + D * s + (nnz - D) * 8 + D * 16
     peaks, kind = load_peaks()
-    return {"mode": "hphi", "workload": args.workload, "dtype": args.dtype, "total_dim": D, "nnz": nnz,
+    return {"mode": "hphi", "workload": args.workload, "dtype": args.dtype, "stored_terms": bool(args.stored),
+            "store_seconds": None if t_store is None else round(t_store, 3), "total_dim": D, "nnz": nnz,
             "ms_per_launch": round(1e3 * t, 4), "gnnz_s": round(nnz / t / 1e9, 3),
             "alg_bytes_per_launch": int(b_alg), "alg_gbs": round(b_alg / t / 1e9, 1),
             "hbm_frac": round(b_alg / t / 1e9 / peaks["hbm_gbs"], 4), "peak_source": kind}
@@ -613,6 +624,7 @@ def main():
     ap.add_argument("--mode", default="solve", choices=["solve", "hphi", "batch", "trl", "dsf"])
     ap.add_argument("--q-group", dest="q_group", type=int, default=25, help="--mode dsf: q values per call")
     ap.add_argument("--op", default="sminus", choices=["sminus", "splus", "sz"], help="--mode dsf: S^alpha_q")
+    ap.add_argument("--stored", action="store_true", help="--mode hphi: stored-term H Phi (k-sectors)")
     ap.add_argument("--n-instances", dest="n_instances", type=int, default=64, help="--mode batch")
     ap.add_argument("--concurrency", type=int, default=16, help="--mode batch")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64", "f64", "f32"], help="--mode hphi only")

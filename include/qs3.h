@@ -131,6 +131,19 @@ int qs3_basis_rep_table(qs3_basis_t b, int32_t mode, int32_t *active);
  *          the occupancy limit are clamped; dot_vectors in {0, 1, 2, 4}).
  * Either pointer may be NULL.  Results do not depend on the choices. */
 int qs3_basis_tuning(qs3_basis_t b, int32_t set, int32_t *hphi_blocks_per_sm, int32_t *dot_vectors);
+/* Stored terms of a k-sector basis (an opt-in variant of Alg. 9, which the
+ * paper recomputes matrix-free on every product).  mode = 1 enumerates every
+ * off-diagonal term once -- its target row, the translation to the target's
+ * representative, the target's |Stab| and the bond -- in the order H Phi
+ * visits them, plus each row's diagonal; later qs3_hphi calls (and the
+ * solvers) then gather from this list instead of searching representatives.
+ * C128 results are identical bit for bit to the matrix-free product; C64
+ * rounds the stored fp64 diagonal once.  Memory: 8 bytes per term + 16 bytes
+ * per row, library-owned, at most half the free device memory (OOM beyond).
+ * mode = 0 releases it, mode = -1 queries.  *bytes (may be NULL) receives the
+ * device bytes held.  Errors: STATE (U(1)-only basis or N_down = 0),
+ * OVERFLOW (N > 4096 or 32768 bonds or more), OOM. */
+int qs3_basis_store_terms(qs3_basis_t b, int32_t mode, uint64_t *bytes);
 
 /* psi = H phi (Alg. 9, pull form, one row per thread, no atomics).
  * dtype: F32/F64 on a U(1)-only basis (real H); C64/C128 on any basis.

@@ -181,6 +181,12 @@ class Basis:
         check(load().qs3_basis_tuning(self._h, 0, hb, ctypes.byref(dv)), "qs3_basis_tuning")
         return {"hphi_blocks_per_sm": list(hb), "dot_vectors": dv.value}
 
+    def store_terms(self, mode: int = -1) -> int:
+        """Stored-term H Phi: 1 build, 0 release, -1 query; returns the device bytes held (0 = off)."""
+        v = ctypes.c_uint64()
+        check(load().qs3_basis_store_terms(self._h, int(mode), ctypes.byref(v)), "qs3_basis_store_terms")
+        return int(v.value)
+
     def rep_table(self, mode: int = -1) -> bool:
         """Representative table of H Phi: 1 build, 0 release, -1 query; returns whether it is in use."""
         a = ctypes.c_int32()

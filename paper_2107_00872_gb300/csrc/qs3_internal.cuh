@@ -149,6 +149,11 @@ struct Basis {
     int tune_hphi[4] = {0, 0, 0, 0};
     int tune_nv = 0;
     bool narrow_ranks = false;              // U(1) with C(N, N_down) < 2^32: 32-bit rank kernels apply
+    // stored terms of the k-sector H Phi (opt-in): row pointers, target rows,
+    // codes (u | st << 12 | q << 16) and per-row diagonals
+    DevBuf d_trp, d_tcol, d_tcode, d_tdiag;
+    uint64_t n_terms = 0;
+    bool stored_terms = false;
     int max_degree = 0;                     // largest number of adjacency entries of a site
 };
 
@@ -493,6 +498,10 @@ int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t
 int count_nnz(Basis &B, uint64_t *nnz);
 // representative table: build (QS3_OK, or an error when it cannot be built) / release
 int build_rep_table(Basis &B, size_t max_bytes);
+// stored-term H Phi of k-sector bases: build (QS3_OK or an error) / release / apply
+int build_terms(Basis &B, size_t max_bytes);
+void drop_terms(Basis &B);
+int hphi_stored_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t st, const int *active);
 constexpr size_t REP_TABLE_AUTO_BYTES = (size_t)1 << 30;   // built at basis creation up to this size
 void drop_rep_table(Basis &B);
 // implemented in qs3_basis.cu
