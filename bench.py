@@ -75,6 +75,8 @@ WORKLOADS = {
     "cubic10_nd4_k0": (lambda: qi.cubic(10), 4, lambda: [(0, 0, 0)]),
     "cubic10_nd3_kpath": (lambda: qi.cubic(10), 3, lambda: list(dict.fromkeys(qi.cubic_kpath(10)))),
     # the paper's own OpenMP benchmark system: 6x6x6, N_down = 5, k = 0 (dim 17,313,563)
+    # a smaller cube for profiling the stored-term kernel (~1 GB of terms)
+    "cubic8_nd4_k0": (lambda: qi.cubic(8), 4, lambda: [(0, 0, 0)]),
     "cubic6_nd5_k0": (lambda: qi.cubic(6), 5, lambda: [(0, 0, 0)]),
 }
 

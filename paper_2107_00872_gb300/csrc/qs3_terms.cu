@@ -137,9 +137,8 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_hphi_st(LatView L, const SecVie
         acc.x = 0; acc.y = 0;
         acch.x = 0; acch.y = 0;
         const uint64_t t1 = rptr[g + 1];
-        for (uint64_t tt = rptr[g]; tt < t1; ++tt) {
-            const uint32_t cd = __ldg(code + tt);
-            const uint32_t idx = __ldg(col + tt);
+        // one term: coefficient from its code, accumulated in list order
+        auto term = [&](uint32_t cd, VT x) {
             CT p = ph[cd & 4095u];
             const int st = (int)((cd >> 12) & 15u);
             if (uni) {
@@ -148,15 +147,32 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_hphi_st(LatView L, const SecVie
                     p.x *= f;
                     p.y *= f;
                 }
-                acc_add(acch, p, ph_in[idx]);
+                acc_add(acch, p, x);
             } else {
                 const R jh = __ldg(jxy + (cd >> 16));
                 const R w = (st == st_row) ? jh : jh * snorm[st] * rs;
                 p.x *= w;
                 p.y *= w;
-                acc_add(acc, p, ph_in[idx]);
+                acc_add(acc, p, x);
             }
+        };
+        // groups of four terms: their index loads and gathers are in flight
+        // together, the sums still run in list order
+        uint64_t tt = rptr[g];
+        for (; tt + 4 <= t1; tt += 4) {
+            uint32_t cd[4], ix[4];
+            VT v[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                cd[j] = __ldg(code + tt + j);
+                ix[j] = __ldg(col + tt + j);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = ph_in[ix[j]];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) term(cd[j], v[j]);
         }
+        for (; tt < t1; ++tt) term(__ldg(code + tt), ph_in[__ldg(col + tt)]);
         if (uni) madd_r(acc, juni, acch);
         madd_r(acc, (R)diag[g], x0);
         store(psi + sv.off + row, acc);
@@ -269,7 +285,7 @@ template <typename VT>
 static int hphi_st_vt(Basis &B, const void *phi, void *psi, cudaStream_t st, const int *active) {
     using CT = typename VTr<VT>::C;
     const size_t smem = 16 * 18 + (size_t)B.N * sizeof(CT);
-    const int grid = grid_tiles(B, 4);
+    const int grid = grid_tiles(B, 8);
     k_hphi_st<VT><<<grid, NTHREADS, smem, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S, B.ntiles,
                                                  B.d_trp.as<uint64_t>(), B.d_tcol.as<uint32_t>(),
                                                  B.d_tcode.as<uint32_t>(), B.d_tdiag.as<double>(), (const VT *)phi,

@@ -70,6 +70,27 @@ def hypercubic(dims: tuple, periodic: bool = True, J: float = 1.0, Jz: float | N
                        np.full(nb, float(Jz)), None, L, name or f"{'x'.join(map(str, dims))}")
 
 
+def triangular(Lx: int, Ly: int | None = None, J: float = 1.0, Jz: float | None = None) -> LatticeSpec:
+    """Periodic Lx x Ly triangular lattice: sites r = x + Lx y on the lattice
+    vectors a1, a2 (60 degrees apart), bonds r -> r + a1, r + a2, r + a1 - a2
+    (six neighbours).  The translation group is that of the Lx x Ly square,
+    and momenta are taken in the a1, a2 coordinates."""
+    Ly = Ly or Lx
+    Jz = J if Jz is None else Jz
+    bi, bj = [], []
+    for y in range(Ly):
+        for x in range(Lx):
+            r = x + Lx * y
+            for dx, dy in ((1, 0), (0, 1), (1, -1)):
+                s = (x + dx) % Lx + Lx * ((y + dy) % Ly)
+                if s != r:
+                    bi.append(r)
+                    bj.append(s)
+    nb = len(bi)
+    return LatticeSpec(Lx * Ly, np.array(bi, np.int32), np.array(bj, np.int32), np.full(nb, float(J)),
+                       np.full(nb, float(Jz)), None, (Lx, Ly, 1), f"triangular{Lx}x{Ly}")
+
+
 def chain(N: int, J: float = 1.0, Jz: float | None = None, periodic: bool = True) -> LatticeSpec:
     return hypercubic((N,), periodic, J, Jz, name=f"chain{N}")
 

@@ -498,3 +498,21 @@ def test_sq_sum_rules_u1():
     assert abs(tot[orc.OP_SZ] - N / 4) < 1e-12
     assert abs(tot[orc.OP_SPLUS] - nd) < 1e-12
     assert abs(tot[orc.OP_SMINUS] - (N - nd)) < 1e-12
+
+
+@pytest.mark.parametrize("Lx,Ly", [(4, 4), (6, 3), (5, 5)])
+def test_triangular_one_magnon_dispersion(Lx, Ly):
+    """One down spin on the periodic triangular lattice (three bond directions
+    a1, a2, a1 - a2, six neighbours): E(k) = sum_b Jz/4 - 6 Jz/2 +
+    J sum_{delta in a1, a2, a1-a2} cos(k.delta)."""
+    J, Jz = 1.0, 0.7
+    spec = qi.triangular(Lx, Ly, J=J, Jz=Jz)
+    lat = olat(spec)
+    nb = len(spec.bi)
+    assert nb == 3 * Lx * Ly
+    for K in qi.all_k((Lx, Ly, 1)):
+        k1, k2 = 2 * np.pi * K[0] / Lx, 2 * np.pi * K[1] / Ly
+        want = nb * Jz / 4 - 6 * Jz / 2 + J * (np.cos(k1) + np.cos(k2) + np.cos(k1 - k2))
+        sec = orc.mk_list(lat, 1, K)
+        assert sec.dim == 1
+        assert abs(orc.dense_k(sec)[0, 0].real - want) < 1e-12
