@@ -399,6 +399,27 @@ def sq_apply_k(src: Sector, phi_k: np.ndarray, op: int, Q, dst: Sector, pos: np.
     return fold(dst, v)
 
 
+# ------------------------------------------- thermal averages, Eq. (ens)
+
+
+def thermal(E: np.ndarray, A: np.ndarray | None, beta: np.ndarray, mult: np.ndarray | None = None):
+    """Eq. (ens) over a list of levels E_nu (all sectors): returns (log Z(beta),
+    <A>(beta)) with Z = sum_nu m_nu e^{-beta E_nu} and <A> = sum_nu m_nu
+    e^{-beta E_nu} A_nu / Z (A = E when None).  Written directly, with the
+    exponents shifted by min E so large beta does not underflow."""
+    E = np.asarray(E, np.float64)
+    A = E if A is None else np.asarray(A, np.float64)
+    m = np.ones_like(E) if mult is None else np.asarray(mult, np.float64)
+    e0 = E.min()
+    logZ, avg = [], []
+    for b in np.atleast_1d(beta):
+        w = m * np.exp(-b * (E - e0))
+        z = w.sum()
+        logZ.append(np.log(z) - b * e0)
+        avg.append((w * A).sum() / z)
+    return np.array(logZ), np.array(avg)
+
+
 # ------------------------------------------------------ Lanczos, Alg. 10, CF
 
 

@@ -516,3 +516,28 @@ def test_triangular_one_magnon_dispersion(Lx, Ly):
         sec = orc.mk_list(lat, 1, K)
         assert sec.dim == 1
         assert abs(orc.dense_k(sec)[0, 0].real - want) < 1e-12
+
+
+def test_thermal_average_over_sectors_equals_full_trace():
+    """Eq. (ens): the levels of every (N_down, k) sector together give the
+    partition function and energy of the whole 2^N space (Kronecker-built
+    Hamiltonian, independent of the sector machinery)."""
+    spec = qi.chain(8, J=1.0, Jz=0.6)
+    lat = olat(spec)
+    levels = []
+    for nd in range(9):
+        for K in qi.all_k((8, 1, 1)):
+            sec = orc.mk_list(lat, nd, K)
+            if sec.dim:
+                levels.append(np.linalg.eigvalsh(orc.dense_k(sec)))
+    E = np.concatenate(levels)
+    assert len(E) == 256
+    Hf = pins.kron_hamiltonian(spec)
+    Ef = np.linalg.eigvalsh(Hf)
+    np.testing.assert_allclose(np.sort(E), Ef, atol=1e-11)
+    beta = np.array([0.1, 1.0, 5.0, 40.0])
+    logZ, eavg = orc.thermal(E, None, beta)
+    for i, b in enumerate(beta):
+        w = np.exp(-b * Ef)
+        assert abs(logZ[i] - np.log(w.sum())) < 1e-12 * max(1.0, abs(logZ[i]))
+        assert abs(eavg[i] - (w * Ef).sum() / w.sum()) < 1e-11
