@@ -290,6 +290,28 @@ int qs3_dsf_op(int32_t op, int32_t subtract_trivial, qs3_basis_t src, int32_t s_
                int32_t n_omega, const double *omega, double *s_qw, double *alpha, double *beta, double *norm2,
                void *stream);
 
+/* Full diagonalisation of sector s of b (Sec. "Full diagonalization", the
+ * paper's ALG = 3): the dense Hermitian block of H in the sector's basis is
+ * assembled column by column from H Phi on unit vectors (only sector s
+ * active) and diagonalised by a library dense eigensolver (cuSOLVER zheevd).
+ * evals: host, dims[s] doubles, ascending.  evecs: NULL, or a caller-owned
+ * device C128 array of dims[s]^2 elements that receives the eigenvectors as
+ * columns (column-major, eigenvector nu at evecs + nu * dims[s]).  Limit:
+ * dims[s] <= 16384 (INVALID_ARG beyond); the call allocates the d^2 matrix
+ * when evecs is NULL (OOM if it does not fit) and synchronises stream.
+ * NOT_CONVERGED if the eigensolver reports failure. */
+int qs3_full_diag(qs3_basis_t b, int32_t s, double *evals, void *evecs, void *stream);
+
+/* Thermal averages of Eq. (ens) over a list of levels E_nu (host arrays of
+ * n_levels; the levels of all sectors wanted, e.g. from qs3_full_diag):
+ * log_z[k] = log sum_nu m_nu e^{-beta_k E_nu} and avg[k] = sum_nu m_nu
+ * e^{-beta_k E_nu} A_nu / Z(beta_k), with A = E when A is NULL and m = 1 when
+ * mult is NULL.  Exponents are shifted by the lowest level, so large beta
+ * does not underflow.  Host arithmetic; log_z or avg may be NULL.
+ * INVALID_ARG for an empty list, a non-finite level or a negative weight. */
+int qs3_thermal(int64_t n_levels, const double *E, const double *A, const double *mult, int32_t n_beta,
+                const double *beta, double *log_z, double *avg);
+
 /* Text of a status code, and of the last failure on the calling thread. */
 const char *qs3_strerror(int status);
 const char *qs3_last_error(void);

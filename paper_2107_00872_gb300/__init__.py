@@ -181,6 +181,18 @@ class Basis:
         check(load().qs3_basis_tuning(self._h, 0, hb, ctypes.byref(dv)), "qs3_basis_tuning")
         return {"hphi_blocks_per_sm": list(hb), "dot_vectors": dv.value}
 
+    def full_diag(self, s: int = 0, vectors: bool = False, stream=None):
+        """All eigenvalues (ascending) of sector s, and optionally the eigenvectors
+        as the columns of a device complex128 (d, d) tensor."""
+        torch = _torch()
+        d = self.dims[s]
+        ev = np.zeros(max(d, 1), np.float64)
+        V = torch.empty((d, d), dtype=torch.complex128, device="cuda") if vectors and d else None
+        check(load().qs3_full_diag(self._h, s, _ptr(ev), None if V is None else ctypes.c_void_p(V.data_ptr()),
+                                   _stream(stream)), "qs3_full_diag")
+        # the library fills column nu contiguously: as a row-major tensor, row nu
+        return ev[:d], (None if V is None else V.T)
+
     def store_terms(self, mode: int = -1) -> int:
         """Stored-term H Phi: 1 build, 0 release, -1 query; returns the device bytes held (0 = off)."""
         v = ctypes.c_uint64()
@@ -297,6 +309,18 @@ def smq_noalloc(src: Basis, s_src: int, phi, dst: Basis, s_dst: int, Q, psi, str
     check(load().qs3_smq_noalloc(src.handle, s_src, _dev(phi, src.dims[s_src], "phi"), dst.handle, s_dst, _ptr(q),
                                  _dev(psi, dst.dims[s_dst], "psi"), _stream(stream)), "qs3_smq_noalloc")
     return psi
+
+
+def thermal(E, beta, A=None, mult=None):
+    """Eq. (ens) over the levels E: (log Z(beta), <A>(beta)); A = E when None."""
+    E = np.ascontiguousarray(E, np.float64)
+    b = np.ascontiguousarray(np.atleast_1d(beta), np.float64)
+    Aa = None if A is None else np.ascontiguousarray(A, np.float64)
+    m = None if mult is None else np.ascontiguousarray(mult, np.float64)
+    lz = np.zeros(len(b))
+    av = np.zeros(len(b))
+    check(load().qs3_thermal(len(E), _ptr(E), _ptr(Aa), _ptr(m), len(b), _ptr(b), _ptr(lz), _ptr(av)), "qs3_thermal")
+    return lz, av
 
 
 OP_SPLUS, OP_SMINUS, OP_SZ = 1, 2, 3

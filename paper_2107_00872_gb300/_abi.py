@@ -45,6 +45,8 @@ SIGNATURES = {
     "qs3_basis_rep_table": ([P, I32, P], I32),
     "qs3_basis_tuning": ([P, I32, P, P], I32),
     "qs3_basis_store_terms": ([P, I32, P], I32),
+    "qs3_full_diag": ([P, I32, P, P, P], I32),
+    "qs3_thermal": ([ctypes.c_int64, P, P, P, I32, P, P, P], I32),
     "qs3_hphi": ([P, I32, P, P, P], I32),
     "qs3_lanczos": ([P, P, P, P, P, P], I32),
     "qs3_trlanczos": ([P, P, P, P, P, P], I32),

@@ -62,7 +62,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list | None =
         objs = list(ex.map(one, srcs))
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcusolver"]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
