@@ -447,25 +447,36 @@ def run_hphi_only(args):
         B.store_terms(1)
         torch.cuda.synchronize()
         t_store = time.perf_counter() - t0
-    dt = {"c128": torch.complex128, "c64": torch.complex64, "f64": torch.float64, "f32": torch.float32}[args.dtype]
+    dfm = args.dtype == "c128df"
+    dt = {"c128": torch.complex128, "c128df": torch.complex128, "c64": torch.complex64, "f64": torch.float64,
+          "f32": torch.float32}[args.dtype]
     if Ks and not dt.is_complex:
         raise SystemExit("k-sectors need complex vectors")
     g = torch.Generator(device="cuda").manual_seed(0)
     phi = torch.randn(B.total_dim, dtype=dt, device="cuda", generator=g)
     psi = torch.empty_like(phi)
     st = torch.cuda.current_stream()
+    if dfm:
+        # double-float input (re.hi, re.lo, im.hi, im.lo): 16 B per element like complex128
+        phi = qs3.split_df(phi, stream=st)
+
+    def apply():
+        if dfm:
+            B.hphi_df(phi, psi, st)
+        else:
+            B.hphi(phi, psi, st)
     for _ in range(args.warmup):
-        B.hphi(phi, psi, st)
+        apply()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
     for _ in range(args.steps):
-        B.hphi(phi, psi, st)
+        apply()
     e1.record(st)
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / args.steps
     nnz = B.nnz()
-    s = phi.element_size()
+    s = psi.element_size()
     D = B.total_dim
     b_alg = D * s + (nnz - D) * s + D * s + (D * 8 + (nnz - D) * 8 if Ks else 0)
     if args.stored:
@@ -629,7 +640,7 @@ def main():
     ap.add_argument("--stored", action="store_true", help="--mode hphi: stored-term H Phi (k-sectors)")
     ap.add_argument("--n-instances", dest="n_instances", type=int, default=64, help="--mode batch")
     ap.add_argument("--concurrency", type=int, default=16, help="--mode batch")
-    ap.add_argument("--dtype", default="c128", choices=["c128", "c64", "f64", "f32"], help="--mode hphi only")
+    ap.add_argument("--dtype", default="c128", choices=["c128", "c128df", "c64", "f64", "f32"], help="--mode hphi only")
     ap.add_argument("--workload", default="square10x10_nd4_all_k", choices=sorted(WORKLOADS))
     ap.add_argument("--n-max", dest="n_max", type=int, default=250)
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / fp32 / cpu_baseline legs")

@@ -55,7 +55,12 @@ enum {
     QS3_ERR_STATE = -8          /* handle in the wrong state / dtype mismatch    */
 };
 
-typedef enum { QS3_F32 = 0, QS3_F64 = 1, QS3_C64 = 2, QS3_C128 = 3 } qs3_dtype;
+/* Vector types of qs3_hphi.  QS3_C128DF: phi holds each complex element in
+ * double-float form, four floats (re.hi, re.lo, im.hi, im.lo) with re =
+ * re.hi + re.lo (qs3_split_df makes it from complex128); psi is complex128;
+ * the product runs in double-float arithmetic (error-free fp32 products and
+ * two-sums, about 48 significant bits), k-sector bases only. */
+typedef enum { QS3_F32 = 0, QS3_F64 = 1, QS3_C64 = 2, QS3_C128 = 3, QS3_C128DF = 4 } qs3_dtype;
 
 /* S^alpha_q operators, numbered as the paper's input parameter spsmsz. */
 typedef enum { QS3_OP_SPLUS = 1, QS3_OP_SMINUS = 2, QS3_OP_SZ = 3 } qs3_sq_op;
@@ -126,7 +131,7 @@ int qs3_basis_rep_table(qs3_basis_t b, int32_t mode, int32_t *active);
  *   - the double-float dot products of the fp64 Lanczos Gram-Schmidt pass
  *     with 1, 2 or 4 basis vectors per pass (loads in flight together).
  * set = 0: write the current choices (0 = not tuned yet) to
- *          hphi_blocks_per_sm[4] (indexed by qs3_dtype) and *dot_vectors;
+ *          hphi_blocks_per_sm[5] (indexed by qs3_dtype) and *dot_vectors;
  * set = 1: impose them (0 = tune again at the next use; blocks per SM above
  *          the occupancy limit are clamped; dot_vectors in {0, 1, 2, 4}).
  * Either pointer may be NULL.  Results do not depend on the choices. */
@@ -146,10 +151,18 @@ int qs3_basis_tuning(qs3_basis_t b, int32_t set, int32_t *hphi_blocks_per_sm, in
 int qs3_basis_store_terms(qs3_basis_t b, int32_t mode, uint64_t *bytes);
 
 /* psi = H phi (Alg. 9, pull form, one row per thread, no atomics).
- * dtype: F32/F64 on a U(1)-only basis (real H); C64/C128 on any basis.
+ * dtype: F32/F64 on a U(1)-only basis (real H); C64/C128 on any basis;
+ * C128DF (phi double-float, psi complex128) on a basis with momentum
+ * sectors, within a few 2^-48 relative of the exact product per term.
  * phi and psi are device vectors of the basis' total dimension and must not
- * alias.  F32/C64 use fp32 matrix elements and fp32 row accumulation. */
+ * alias.  F32/C64 use fp32 matrix elements and fp32 row accumulation.
+ * Errors: STATE (real dtype on a k-sector basis, C128DF on a U(1)-only one). */
 int qs3_hphi(qs3_basis_t b, qs3_dtype dtype, const void *phi, void *psi, void *stream);
+
+/* x_df[r] = double-float split of the complex128 x[r], r < n: re.hi =
+ * fl32(re), re.lo = fl32(re - re.hi), the same for im (device pointers, the
+ * layout QS3_C128DF reads). */
+int qs3_split_df(const void *x, void *x_df, uint64_t n, void *stream);
 
 /* Options of the eigensolvers (input_lancz / input_TRLan of the paper). */
 typedef struct {
@@ -166,6 +179,10 @@ typedef struct {
     uint64_t seed;        /* start vector: seeded Gaussian (SplitMix64 + Box-Muller) */
     double refine_tol;    /* fp32 mode: refine until |dE| <= refine_tol |E| (e.g. 1e-9) */
     double res_tol;       /* qs3_lanczos also needs the Ritz residual beta_m |c_m| <= res_tol max(|E|, 1); 0 = off */
+    int32_t hphi_ieee;    /* fp64 solves on k-sector bases: 0 applies H to the double-float copy of each
+                             Lanczos vector in double-float arithmetic (QS3_C128DF); 1 uses IEEE
+                             complex128 H Phi (QS3_C128).  Residuals are always IEEE complex128. */
+    int32_t reserved;     /* 0 */
 } qs3_solve_opts;
 
 typedef struct {

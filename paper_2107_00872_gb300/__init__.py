@@ -10,9 +10,9 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import QS3_C64, QS3_C128, QS3_F32, QS3_F64, QS3Error, check, load
+from ._abi import QS3_C64, QS3_C128, QS3_C128DF, QS3_F32, QS3_F64, QS3Error, check, load
 
-__all__ = ["Basis", "QS3Error", "load", "hphi", "dtype_code", "SolveOpts"]
+__all__ = ["Basis", "QS3Error", "load", "hphi", "dtype_code", "SolveOpts", "split_df"]
 
 
 def _torch():
@@ -55,11 +55,11 @@ class SolveOpts:
     """Fields of qs3_solve_opts with the paper's defaults (input_lancz / input_TRLan)."""
 
     def __init__(self, n_eig=1, n_keep=8, n_max=32, max_iter=10000, min_iter=20, check_every=5, eps=1e-14,
-                 precision="f64", use_graphs=True, seed=1, refine_tol=1e-9, res_tol=1e-12):
+                 precision="f64", use_graphs=True, seed=1, refine_tol=1e-9, res_tol=1e-12, hphi_ieee=False):
         self.n_eig, self.n_keep, self.n_max, self.max_iter = n_eig, n_keep, n_max, max_iter
         self.min_iter, self.check_every, self.eps = min_iter, check_every, eps
         self.precision, self.use_graphs, self.seed, self.refine_tol = precision, use_graphs, seed, refine_tol
-        self.res_tol = res_tol
+        self.res_tol, self.hphi_ieee = res_tol, hphi_ieee
 
     def c(self) -> _abi.qs3_solve_opts:
         o = _abi.qs3_solve_opts()
@@ -68,7 +68,20 @@ class SolveOpts:
         o.precision = QS3_F32 if self.precision in ("f32", QS3_F32) else QS3_F64
         o.use_graphs, o.seed, o.refine_tol = int(bool(self.use_graphs)), int(self.seed), float(self.refine_tol)
         o.res_tol = float(self.res_tol)
+        o.hphi_ieee = int(bool(self.hphi_ieee))
         return o
+
+
+def split_df(x, out=None, stream=None):
+    """Double-float split of a complex128 device vector (qs3_split_df): a
+    float32 tensor of 4 x len(x) values (re.hi, re.lo, im.hi, im.lo)."""
+    torch = _torch()
+    if x.dtype != torch.complex128:
+        raise TypeError("x must be complex128")
+    if out is None:
+        out = torch.empty(4 * x.numel(), dtype=torch.float32, device=x.device)
+    check(load().qs3_split_df(_dev(x), _dev(out, 4 * x.numel(), "out"), x.numel(), _stream(stream)), "qs3_split_df")
+    return out
 
 
 def _info_dict(info: _abi.qs3_solve_info) -> dict:
@@ -167,8 +180,8 @@ class Basis:
 
     def tuning(self, hphi_blocks_per_sm=None, dot_vectors=None) -> dict:
         """Autotuned launch choices: query (no arguments) or impose them
-        (hphi_blocks_per_sm: 4 values indexed by dtype code; 0 = tune again)."""
-        hb = (ctypes.c_int32 * 4)()
+        (hphi_blocks_per_sm: up to 5 values indexed by dtype code; 0 = tune again)."""
+        hb = (ctypes.c_int32 * 5)()
         dv = ctypes.c_int32(0)
         if hphi_blocks_per_sm is not None or dot_vectors is not None:
             check(load().qs3_basis_tuning(self._h, 0, hb, ctypes.byref(dv)), "qs3_basis_tuning")
@@ -212,6 +225,21 @@ class Basis:
         if psi is None:
             psi = _torch().empty_like(phi)
         check(load().qs3_hphi(self._h, dtype_code(phi), _dev(phi, self.total_dim, "phi"),
+                              _dev(psi, self.total_dim, "psi"), _stream(stream)), "qs3_hphi")
+        return psi
+
+    def hphi_df(self, phi_df, psi=None, stream=None):
+        """psi = H phi for phi in double-float form (float32 tensor of 4 x the
+        total dimension: re.hi, re.lo, im.hi, im.lo per element, see
+        split_df); psi is complex128 (allocated when omitted)."""
+        torch = _torch()
+        if phi_df.dtype != torch.float32:
+            raise TypeError("phi_df must be float32 (double-float layout)")
+        if psi is None:
+            psi = torch.empty(self.total_dim, dtype=torch.complex128, device=phi_df.device)
+        if psi.dtype != torch.complex128:
+            raise TypeError("psi must be complex128")
+        check(load().qs3_hphi(self._h, QS3_C128DF, _dev(phi_df, 4 * self.total_dim, "phi_df"),
                               _dev(psi, self.total_dim, "psi"), _stream(stream)), "qs3_hphi")
         return psi
 

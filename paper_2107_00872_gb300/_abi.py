@@ -11,7 +11,7 @@ I32 = ctypes.c_int32
 U64 = ctypes.c_uint64
 F64 = ctypes.c_double
 
-QS3_F32, QS3_F64, QS3_C64, QS3_C128 = 0, 1, 2, 3
+QS3_F32, QS3_F64, QS3_C64, QS3_C128, QS3_C128DF = 0, 1, 2, 3, 4
 STATUS = {0: "QS3_OK", -1: "QS3_ERR_INVALID_ARG", -2: "QS3_ERR_OVERFLOW", -3: "QS3_ERR_SYMMETRY",
           -4: "QS3_ERR_OOM", -5: "QS3_ERR_CUDA", -6: "QS3_ERR_NOT_CONVERGED", -7: "QS3_ERR_TIMEOUT",
           -8: "QS3_ERR_STATE"}
@@ -25,7 +25,7 @@ class qs3_lattice(ctypes.Structure):
 class qs3_solve_opts(ctypes.Structure):
     _fields_ = [("n_eig", I32), ("n_keep", I32), ("n_max", I32), ("max_iter", I32), ("min_iter", I32),
                 ("check_every", I32), ("eps", F64), ("precision", I32), ("use_graphs", I32), ("seed", U64),
-                ("refine_tol", F64), ("res_tol", F64)]
+                ("refine_tol", F64), ("res_tol", F64), ("hphi_ieee", I32), ("reserved", I32)]
 
 
 class qs3_solve_info(ctypes.Structure):
@@ -48,6 +48,7 @@ SIGNATURES = {
     "qs3_full_diag": ([P, I32, P, P, P], I32),
     "qs3_thermal": ([ctypes.c_int64, P, P, P, I32, P, P, P], I32),
     "qs3_hphi": ([P, I32, P, P, P], I32),
+    "qs3_split_df": ([P, P, U64, P], I32),
     "qs3_lanczos": ([P, P, P, P, P, P], I32),
     "qs3_trlanczos": ([P, P, P, P, P, P], I32),
     "qs3_batch_solve": ([I32, P, P, P, P, P, I32], I32),

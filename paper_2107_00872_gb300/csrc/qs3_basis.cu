@@ -581,6 +581,18 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     std::vector<float> uf(u.begin(), u.end()), ajzf(ajz.begin(), ajz.end());
     QS3_TRY(B.d_u_f.upload(uf.data(), uf.size() * 4));
     QS3_TRY(B.d_adj_jz_f.upload(ajzf.data(), ajzf.size() * 4));
+    {
+        // double-float remainders (v - fl32(v), rounded to fp32)
+        auto rem = [](const std::vector<double> &v, const std::vector<float> &h) {
+            std::vector<float> r(v.size());
+            for (size_t i = 0; i < v.size(); ++i) r[i] = (float)(v[i] - (double)h[i]);
+            return r;
+        };
+        const std::vector<float> a = rem(ajxy, ajxyf), bu = rem(u, uf), cz = rem(ajz, ajzf);
+        QS3_TRY(B.d_adj_jxy_lo.upload(a.data(), a.size() * 4));
+        QS3_TRY(B.d_u_lo.upload(bu.data(), bu.size() * 4));
+        QS3_TRY(B.d_adj_jz_lo.upload(cz.data(), cz.size() * 4));
+    }
     std::vector<uint32_t> xyz(N);
     for (int r = 0; r < N; ++r) {
         int x = r % B.L[0], y = (r / B.L[0]) % B.L[1], z = r / (B.L[0] * B.L[1]);
@@ -609,6 +621,10 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     L.c0f = (float)c0;
     L.u_f = B.d_u_f.as<float>();
     L.adj_jz_f = B.d_adj_jz_f.as<float>();
+    L.adj_jxy_lo = B.d_adj_jxy_lo.as<float>();
+    L.u_lo = B.d_u_lo.as<float>();
+    L.adj_jz_lo = B.d_adj_jz_lo.as<float>();
+    L.c0lo = (float)(c0 - (double)(float)c0);
     L.xyz = B.d_xyz.as<uint32_t>();
     L.jh_uniform = 0.0;
     if (nb > 0) {
@@ -789,11 +805,11 @@ int qs3_basis_tuning(qs3_basis_t b, int32_t set, int32_t *hphi_blocks_per_sm, in
         if (dot_vectors && !(*dot_vectors == 0 || *dot_vectors == 1 || *dot_vectors == 2 || *dot_vectors == 4))
             return set_err(QS3_ERR_INVALID_ARG, "dot vectors per pass %d", *dot_vectors);
         if (hphi_blocks_per_sm)
-            for (int i = 0; i < 4; ++i) B.tune_hphi[i] = hphi_blocks_per_sm[i];
+            for (int i = 0; i < 5; ++i) B.tune_hphi[i] = hphi_blocks_per_sm[i];
         if (dot_vectors) B.tune_nv = *dot_vectors;
     } else {
         if (hphi_blocks_per_sm)
-            for (int i = 0; i < 4; ++i) hphi_blocks_per_sm[i] = B.tune_hphi[i];
+            for (int i = 0; i < 5; ++i) hphi_blocks_per_sm[i] = B.tune_hphi[i];
         if (dot_vectors) *dot_vectors = B.tune_nv;
     }
     return QS3_OK;

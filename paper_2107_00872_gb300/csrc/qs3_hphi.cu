@@ -380,41 +380,6 @@ __global__ void k_diag0(double c0, uint64_t n, const VT *__restrict__ phi, VT *_
     }
 }
 
-static std::atomic<int> g_nsm{0};
-
-static int num_sms() {
-    int n = g_nsm.load(std::memory_order_relaxed);
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-        g_nsm.store(n, std::memory_order_relaxed);
-    }
-    return n;
-}
-
-// persistent grid: resident blocks per SM x SMs, capped by the tile count.
-// cache packs (smem + 1) << 32 | blocks per SM, so concurrent callers read a
-// consistent pair; the shared-memory attribute is always MAX_DYN_SMEM.
-template <typename KF>
-static int launch_rows(KF kern, Basis &B, size_t smem, std::atomic<unsigned long long> &cache, int *grid_out,
-                       int *occ_out = nullptr) {
-    const unsigned long long c = cache.load(std::memory_order_acquire);
-    int nb;
-    if ((c >> 32) != (unsigned long long)smem + 1) {
-        QS3_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
-        QS3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NTHREADS, smem));
-        nb = std::max(nb, 1);
-        cache.store(((unsigned long long)smem + 1) << 32 | (unsigned)nb, std::memory_order_release);
-    } else {
-        nb = (int)(c & 0xffffffffu);
-    }
-    int grid = std::min(B.ntiles, nb * num_sms());
-    *grid_out = std::max(grid, 1);
-    if (occ_out) *occ_out = nb;
-    return QS3_OK;
-}
 
 template <typename VT> struct DtIdx;
 template <> struct DtIdx<float> { static constexpr int v = QS3_F32; };
@@ -422,43 +387,14 @@ template <> struct DtIdx<double> { static constexpr int v = QS3_F64; };
 template <> struct DtIdx<float2> { static constexpr int v = QS3_C64; };
 template <> struct DtIdx<double2> { static constexpr int v = QS3_C128; };
 
-// autotuner for the persistent grid: on the first direct launch for a basis
-// and vector type, time the kernel with 1..4 fewer resident blocks per SM
-// than the occupancy limit (rows in flight per SM) and keep the fastest.
-// H Phi is a pure function of phi, so the trial launches only rewrite psi.
 template <typename VT, typename KF>
 static int tune_grid(KF kern, Basis &B, int occ, cudaStream_t st, const VT *phi, VT *psi, const int *active,
                      int &best_bps, size_t smem = (size_t)-1) {
     if (smem == (size_t)-1) smem = B.smem_bytes;
-    const int nsm = num_sms();
-    best_bps = occ;
-    if (B.ntiles < 2 * nsm || occ <= 1) return QS3_OK;
-    cudaEvent_t e0, e1;
-    QS3_CUDA(cudaEventCreate(&e0));
-    QS3_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int rc = QS3_OK;
-    for (int b = occ; b >= std::max(1, occ - 3) && rc == QS3_OK; --b) {
-        const int grid = std::min(B.ntiles, b * nsm);
-        float tmin = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
-            cudaEventRecord(e0, st);
-            kern<<<grid, NTHREADS, smem, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S, B.ntiles, phi,
-                                               psi, active);
-            count_launch();
-            if (cudaGetLastError() != cudaSuccess) { rc = QS3_ERR_CUDA; break; }
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = QS3_ERR_CUDA; break; }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0 || b < occ) tmin = std::min(tmin, ms);   // the very first launch warms up
-        }
-        if (tmin < best) { best = tmin; best_bps = b; }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (rc != QS3_OK) return set_err(rc, "H Phi autotuning launch failed");
-    return QS3_OK;
+    return tune_blocks(B, occ, st, best_bps, [&](int grid) {
+        kern<<<grid, NTHREADS, smem, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S, B.ntiles, phi, psi,
+                                           active);
+    });
 }
 
 template <int ND, typename VT, bool KS, bool TB>
@@ -538,6 +474,7 @@ static int hphi_vt(Basis &B, const void *phi, void *psi, cudaStream_t st, const 
 int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t st, const int *active) {
     if (!phi || !psi) return set_err(QS3_ERR_INVALID_ARG, "NULL vector");
     if (phi == psi) return set_err(QS3_ERR_INVALID_ARG, "phi and psi alias");
+    if (dt == QS3_C128DF) return hphi_df_launch(B, phi, nullptr, 0, psi, st, active);
     if (B.has_k && (dt == QS3_F32 || dt == QS3_F64))
         return set_err(QS3_ERR_STATE, "k-sector bases need complex vectors (C64/C128)");
     if (B.total == 0) return QS3_OK;

@@ -4,6 +4,9 @@
 // diagonal constants and coupling tables in the vector's precision.
 #pragma once
 
+#include <algorithm>
+#include <atomic>
+
 #include "qs3_internal.cuh"
 
 namespace qs3 {
@@ -92,5 +95,80 @@ template <> __device__ __forceinline__ float diag_jz<float>(const LatView &L, in
 template <typename CT> __device__ __forceinline__ const CT *phase_table(const SecView &sv);
 template <> __device__ __forceinline__ const double2 *phase_table<double2>(const SecView &sv) { return sv.ph64; }
 template <> __device__ __forceinline__ const float2 *phase_table<float2>(const SecView &sv) { return sv.ph32; }
+
+// ------------------------------------------------ host: launch shape
+
+// SM count of the current device (the one the basis lives on)
+static inline int num_sms() {
+    static std::atomic<int> nsm{0};
+    int n = nsm.load(std::memory_order_relaxed);
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+        nsm.store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
+// persistent grid: resident blocks per SM x SMs, capped by the tile count.
+// cache packs (smem + 1) << 32 | blocks per SM, so concurrent callers read a
+// consistent pair; the shared-memory attribute is always MAX_DYN_SMEM.
+template <typename KF>
+static int launch_rows(KF kern, Basis &B, size_t smem, std::atomic<unsigned long long> &cache, int *grid_out,
+                       int *occ_out = nullptr) {
+    const unsigned long long c = cache.load(std::memory_order_acquire);
+    int nb;
+    if ((c >> 32) != (unsigned long long)smem + 1) {
+        QS3_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
+        QS3_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NTHREADS, smem));
+        nb = std::max(nb, 1);
+        cache.store(((unsigned long long)smem + 1) << 32 | (unsigned)nb, std::memory_order_release);
+    } else {
+        nb = (int)(c & 0xffffffffu);
+    }
+    int grid = std::min(B.ntiles, nb * num_sms());
+    *grid_out = std::max(grid, 1);
+    if (occ_out) *occ_out = nb;
+    return QS3_OK;
+}
+
+// autotuner for the persistent grid: on the first direct launch for a basis
+// and vector type, time the kernel with 1..4 fewer resident blocks per SM
+// than the occupancy limit (rows in flight per SM) and keep the fastest.
+// H Phi is a pure function of phi, so the trial launches only rewrite psi.
+// launch(grid) enqueues one launch on st.
+template <typename LF>
+static int tune_blocks(Basis &B, int occ, cudaStream_t st, int &best_bps, LF launch) {
+    const int nsm = num_sms();
+    best_bps = occ;
+    if (B.ntiles < 2 * nsm || occ <= 1) return QS3_OK;
+    cudaEvent_t e0, e1;
+    QS3_CUDA(cudaEventCreate(&e0));
+    QS3_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int rc = QS3_OK;
+    for (int b = occ; b >= std::max(1, occ - 3) && rc == QS3_OK; --b) {
+        const int grid = std::min(B.ntiles, b * nsm);
+        float tmin = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, st);
+            launch(grid);
+            count_launch();
+            if (cudaGetLastError() != cudaSuccess) { rc = QS3_ERR_CUDA; break; }
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = QS3_ERR_CUDA; break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 || b < occ) tmin = std::min(tmin, ms);   // the very first launch warms up
+        }
+        if (tmin < best) { best = tmin; best_bps = b; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != QS3_OK) return set_err(rc, "H Phi autotuning launch failed");
+    return QS3_OK;
+}
 
 }  // namespace qs3

@@ -89,6 +89,12 @@ struct LatView {
     const float *u_f;             // fp32 copies of u, c0 and adj_jz for the fp32 kernels
     float c0f;
     const float *adj_jz_f;
+    // the fp32 remainders v - fl32(v) of adj_jxy, u, adj_jz and c0: with the
+    // fp32 copies they are the double-float constants of the C128DF product
+    const float *adj_jxy_lo;
+    const float *u_lo;
+    const float *adj_jz_lo;
+    float c0lo;
     const uint32_t *xyz;          // N: x | y << 11 | z << 22
     // representative table (k-sectors, optional): for every state a, by its
     // rank0, orb[rank0] = g << 12 | u, where the orbit's representative is the
@@ -132,6 +138,7 @@ struct Basis {
     // device data
     DevBuf d_binom, d_adj_ptr, d_adj_nbr, d_adj_jxy, d_adj_jz, d_adj_jxy_f, d_u, d_xyz;
     DevBuf d_u_f, d_adj_jz_f;
+    DevBuf d_adj_jxy_lo, d_u_lo, d_adj_jz_lo;
     std::vector<DevBuf> d_sigma, d_stab, d_pidx;
     DevBuf d_ph64, d_ph32;                  // S x N per-site phase tables (k-sectors)
     DevBuf d_secs, d_tile0, d_chunk0;
@@ -146,7 +153,7 @@ struct Basis {
     // autotuned launch choices, 0 = not yet tuned: resident H Phi blocks per
     // SM per vector dtype (the persistent grid, i.e. rows in flight per SM),
     // and basis vectors per pass of the double-float dot products
-    int tune_hphi[4] = {0, 0, 0, 0};
+    int tune_hphi[5] = {0, 0, 0, 0, 0};     // indexed by qs3_dtype
     int tune_nv = 0;
     bool narrow_ranks = false;              // U(1) with C(N, N_down) < 2^32: 32-bit rank kernels apply
     // stored terms of the k-sector H Phi (opt-in): row pointers, target rows,
@@ -495,6 +502,10 @@ size_t row_kernel_smem(const Basis &B, int extra_nd);
 // implemented in qs3_hphi.cu
 int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t st,
                 const int *active = nullptr);
+// C128DF product: phi in double-float form (float4 per element), or phi +
+// (*dx) ld when dx (device) is given; psi complex128
+int hphi_df_launch(Basis &B, const void *phi, const int *dx, uint64_t ld, void *psi, cudaStream_t st,
+                   const int *active = nullptr);
 int count_nnz(Basis &B, uint64_t *nnz);
 // representative table: build (QS3_OK, or an error when it cannot be built) / release
 int build_rep_table(Basis &B, size_t max_bytes);

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "qs3_internal.cuh"
+#include "qs3_df.cuh"
 
 namespace qs3 {
 
@@ -246,33 +247,6 @@ __global__ void k_step_scalars(int S, int x, int cap, const double2 *__restrict_
 // fma(a, b, -p), sums use the error-free two-sum.  This keeps ~48 bits, i.e.
 // fp64-class accumulation, at fp32 throughput (GB300 executes fp64 at a
 // small fraction of its fp32 rate).  Partial sums leave each thread in fp64.
-struct dfl { float hi, lo; };
-
-__device__ __forceinline__ dfl df_add(dfl a, float b) {     // (a.hi + a.lo) + b
-    const float s = a.hi + b;
-    const float bb = s - a.hi;
-    const float e = (a.hi - (s - bb)) + (b - bb);
-    const float lo = e + a.lo;
-    const float hi = s + lo;
-    return {hi, lo - (hi - s)};
-}
-// a += x * y (float * float, exact product)
-__device__ __forceinline__ dfl df_fma(dfl a, float x, float y) {
-    const float p = x * y;
-    const float e = fmaf(x, y, -p);
-    dfl r = df_add(a, p);
-    r.lo += e;
-    return r;
-}
-// a += x * (y.hi + y.lo)  (float times double-float)
-__device__ __forceinline__ dfl df_fma2(dfl a, float x, float yh, float yl) {
-    const float p = x * yh;
-    const float e = fmaf(x, yh, -p) + x * yl;
-    dfl r = df_add(a, p);
-    r.lo += e;
-    return r;
-}
-__device__ __forceinline__ double df_d(dfl a) { return (double)a.hi + (double)a.lo; }
 
 template <typename VT> struct F32c { static constexpr bool v = false; };
 template <> struct F32c<float2> { static constexpr bool v = true; };
@@ -553,50 +527,9 @@ template <> struct DfS<double2> { using T = float4; };   // (re.hi, re.lo, im.hi
 
 __device__ __forceinline__ float4 ld_df(const float2 *p) { const float2 v = *p; return make_float4(v.x, v.y, 0.f, 0.f); }
 __device__ __forceinline__ float4 ld_df(const float4 *p) { return *p; }
-__device__ __forceinline__ float2 split_d(double v) {
-    const float h = __double2float_rn(v);
-    return make_float2(h, __double2float_rn(v - (double)h));
-}
-__device__ __forceinline__ float4 split2(double2 v) {
-    const float2 a = split_d(v.x), b = split_d(v.y);
-    return make_float4(a.x, a.y, b.x, b.y);
-}
 __device__ __forceinline__ void st_df(float2 *p, float4 v) { *p = make_float2(v.x, v.y); }
 __device__ __forceinline__ void st_df(float4 *p, float4 v) { *p = v; }
 
-// acc += (ah + al)(bh + bl), dropping al*bl (2^-48 relative); acc is left
-// unnormalised (|lo| grows by at most a few ulp of hi per call)
-__device__ __forceinline__ void df_mac(dfl &acc, float ah, float al, float bh, float bl) {
-    const float p = ah * bh;
-    float e = fmaf(ah, bh, -p);
-    e = fmaf(ah, bl, e);
-    e = fmaf(al, bh, e);
-    const float s = acc.hi + p;
-    const float bb = s - acc.hi;
-    const float t = (acc.hi - (s - bb)) + (p - bb);
-    acc.hi = s;
-    acc.lo += t + e;
-}
-__device__ __forceinline__ dfl df_norm(dfl a) {
-    const float s = a.hi + a.lo;
-    return {s, a.lo - (s - a.hi)};
-}
-__device__ __forceinline__ dfl df_sum(dfl a, dfl b) {
-    const float s = a.hi + b.hi;
-    const float bb = s - a.hi;
-    const float t = (a.hi - (s - bb)) + (b.hi - bb);
-    return df_norm({s, t + a.lo + b.lo});
-}
-__device__ __forceinline__ dfl warp_sum_df(dfl a) {
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        dfl b;
-        b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
-        b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
-        a = df_sum(a, b);
-    }
-    return a;
-}
 
 // part[c * m + j] = conj(V_{j0+j}) . w over the chunk as double-float
 // (re.hi, re.lo, im.hi, im.lo); V double-float, w fp64.  Vectors go in groups
@@ -1133,6 +1066,10 @@ struct Engine {
     Engine(const Engine &) = delete;
     Engine &operator=(const Engine &) = delete;
     // replay Lanczos steps as CUDA graphs (fp64 engine; ignored otherwise)
+    // fp64 k-sector engine: apply H to the double-float copy svec(x) of psi_x
+    // (QS3_C128DF) instead of the fp64 ring vector
+    bool dfh = false;
+    void use_df_hphi(bool on) { dfh = on && DF && IsC<VT>::v && B.has_k && B.nd > 0; }
     int enable_graphs(bool on) {
         graphs = on && DF && B.nchunks > 0;
         if (graphs && !xdev.p) QS3_TRY(xdev.alloc(sizeof(int)));
@@ -1334,7 +1271,10 @@ struct Engine {
     int step_body_dev() {
         const int *dx = xdev.as<int>();
         VT *w = rvec(rw);
-        QS3_TRY(hphi_launch(B, dtype(), rvec(rc), w, st, act()));
+        if (dfh)
+            QS3_TRY(hphi_df_launch(B, V.p, dx, D, w, st, act()));
+        else
+            QS3_TRY(hphi_launch(B, dtype(), rvec(rc), w, st, act()));
         const int64_t ld = (int64_t)(rvec(rc) - rvec(rp));
         double2 *hh1 = h1.as<double2>(), *n1 = nrm1.as<double2>();
         if constexpr (DF) {
@@ -1431,7 +1371,10 @@ struct Engine {
         std::pair<cudaEvent_t, cudaEvent_t> ev;
         QS3_TRY(stats->pair(ev));
         QS3_CUDA(cudaEventRecord(ev.first, st));
-        QS3_TRY(hphi_launch(B, dtype(), hin(x), w, st, act()));
+        if (dfh)
+            QS3_TRY(hphi_df_launch(B, svec(x), nullptr, 0, w, st, act()));
+        else
+            QS3_TRY(hphi_launch(B, dtype(), hin(x), w, st, act()));
         QS3_CUDA(cudaEventRecord(ev.second, st));
         stats->pend.push_back(ev);
         stats->calls += 1;
@@ -1542,6 +1485,7 @@ static int lanczos_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT
     const int nmax = std::max(2, o.n_max);
     QS3_TRY(E.init(nmax + 1, 0));
     QS3_TRY(E.enable_graphs(o.use_graphs != 0));
+    E.use_df_hphi(o.hphi_ieee == 0);
     if (start) QS3_TRY(E.start_from(start)); else QS3_TRY(E.start_random(o.seed));
     const int S = B.S;
     R.e.assign(S, NAN);
@@ -1552,6 +1496,7 @@ static int lanczos_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT
     for (int s = 0; s < S; ++s)
         if (!B.dims[s]) R.conv[s] = 1;
     const int every = std::max(1, o.check_every);
+    const auto tl0 = std::chrono::steady_clock::now();
     int x = 0;
     for (; x < nmax && E.any_active(); ++x) {
         QS3_TRY(E.step(x));
@@ -1570,16 +1515,17 @@ static int lanczos_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT
             const double e = tri_eig_k(m, as, bs, 0);
             bool ok = brk || (std::isfinite(eprev[s]) && std::fabs(e - eprev[s]) <= o.eps * std::fabs(e));
             double rres = 0.0;
-            if (ok && !brk && o.res_tol > 0) {
+            if ((ok || log_on()) && !brk && o.res_tol > 0) {
                 // Ritz residual |H y - e y| = beta_{m-1} |c_{m-1}| (full reorthogonalisation keeps it exact)
                 std::vector<double> c;
                 tri_eigvec(m, as, bs, e, c);
                 rres = std::fabs(bs[m - 1] * c[m - 1]);
-                ok = rres <= o.res_tol * std::max(std::fabs(e), 1.0);
+                ok = ok && rres <= o.res_tol * std::max(std::fabs(e), 1.0);
             }
             if (log_on())
-                fprintf(stderr, "[qs3] lanczos vt=%zu n=%d s=%d m=%d e=%.17g de=%.3g beta=%.3g rres=%.3g ok=%d\n",
-                        sizeof(VT), n, s, m, e, e - eprev[s], bs[m - 1], rres, (int)ok);
+                fprintf(stderr, "[qs3] lanczos vt=%zu n=%d s=%d m=%d e=%.17g de=%.3g beta=%.3g rres=%.3g ok=%d t=%.4f\n",
+                        sizeof(VT), n, s, m, e, e - eprev[s], bs[m - 1], rres, (int)ok,
+                        std::chrono::duration<double>(std::chrono::steady_clock::now() - tl0).count());
             eprev[s] = e;
             R.e[s] = e;
             msize[s] = m;
@@ -1637,6 +1583,7 @@ static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T
     Engine<VT> E(B, st, &hs);
     QS3_TRY(E.init(NM + 1, NK));
     QS3_TRY(E.enable_graphs(o.use_graphs != 0));
+    E.use_df_hphi(o.hphi_ieee == 0);
     if (start) QS3_TRY(E.start_from(start)); else QS3_TRY(E.start_random(o.seed));
     R.e.assign((size_t)S * NE, NAN);
     R.conv.assign(S, 0);
@@ -1983,6 +1930,7 @@ int dsf_run(int op, Basis &S, int ss, const void *gs, double e0, Basis &Dd, int 
     HphiStats hs;
     Engine<double2> E(Dd, st, &hs);
     QS3_TRY(E.init(n_iter + 1, 0));
+    E.use_df_hphi(true);
     for (int n = 0; n < nq; ++n)
         QS3_TRY(sq_launch(op, S, ss, gs, Dd, n, Q + 3 * n, E.hin(0) + Dd.offs[n], st));
     QS3_TRY(E.normalise_start());

@@ -61,7 +61,16 @@ def test_disordered_open_square_32x32_full_u1():
     assert np.all(np.abs(out["sz"]) <= 0.5 + 1e-12)
 
 
-@pytest.mark.parametrize("dt", ["c128", "c64"])
+def _apply(B, x, dt):
+    """H x through qs3_hphi as complex128, complex64 or double-float (C128DF)."""
+    import paper_2107_00872_gb300 as qs3
+    torch = torch_cuda()
+    if dt == "c128df":
+        return B.hphi_df(qs3.split_df(to_dev(x, torch.complex128))).cpu().numpy()
+    return B.hphi(to_dev(x, torch.complex128 if dt == "c128" else torch.complex64)).cpu().numpy().astype(complex)
+
+
+@pytest.mark.parametrize("dt", ["c128", "c128df", "c64"])
 def test_cubic10_nd4_gamma_sector_full(dt):
     """Config 3's largest sector: 10x10x10, N_down = 4, k = 0: the dimension
     equals the character-sum closed form, sampled representatives are valid,
@@ -74,7 +83,7 @@ def test_cubic10_nd4_gamma_sector_full(dt):
     assert d == pins.sector_dim_closed_form((10, 10, 10), 4, K)
     rng = np.random.default_rng(3)
     x = rng.standard_normal(d) + 1j * rng.standard_normal(d)
-    got = B.hphi(to_dev(x, torch.complex128 if dt == "c128" else torch.complex64)).cpu().numpy().astype(complex)
+    got = _apply(B, x, dt)
     rows = np.concatenate([[0, d - 1], rng.integers(0, d, 60)])
     _check_k_rows(spec, 4, K, B, 0, x, got, rows, dt == "c64")
 
@@ -98,17 +107,19 @@ def test_cubic10_nd3_kpath_sectors():
         _check_k_rows(spec, 3, Ks[s], B, s, x, got, rows, False)
 
 
-def test_square10_nd4_all_sectors_batched_rows():
+@pytest.mark.parametrize("dt", ["c128", "c128df"])
+def test_square10_nd4_all_sectors_batched_rows(dt):
     """Config 2: all 100 sectors of the 10x10 square lattice at N_down = 4 in
-    one batched H Phi; sampled rows of several sectors."""
-    torch = torch_cuda()
+    one batched H Phi (complex128 and double-float); sampled rows of several
+    sectors."""
+    torch_cuda()
     spec = qi.square(10)
     Ks = qi.all_k((10, 10, 1))
     B = lib_basis(spec, 4, Ks)
     assert sum(B.dims) == comb(100, 4)
     rng = np.random.default_rng(9)
     x = rng.standard_normal(B.total_dim) + 1j * rng.standard_normal(B.total_dim)
-    got = B.hphi(to_dev(x, torch.complex128)).cpu().numpy()
+    got = _apply(B, x, dt)
     for s in (0, 1, 11, 55, 99):
         rows = np.concatenate([[0, B.dims[s] - 1], rng.integers(0, B.dims[s], 50)])
         _check_k_rows(spec, 4, Ks[s], B, s, x, got, rows, False)
