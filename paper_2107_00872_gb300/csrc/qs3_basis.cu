@@ -426,7 +426,7 @@ void drop_rep_table(Basis &B) {
 // the phase e^{ik.t} of the translation t = -(r_x, r_y, r_z) that moves site r
 // to the origin; the angle is reduced exactly in integers
 __global__ void k_phase_tables(int S, int N, int Lx, int Ly, int Lz, const int *__restrict__ K,
-                               double2 *__restrict__ ph64, float2 *__restrict__ ph32) {
+                               double2 *__restrict__ ph64, float2 *__restrict__ ph32, float4 *__restrict__ phdf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S * N) return;
     const int s = i / N, r = i % N;
@@ -437,6 +437,8 @@ __global__ void k_phase_tables(int S, int N, int Lx, int Ly, int Lz, const int *
     sincospi(-2.0 * (double)num / (double)N, &sn, &cs);
     ph64[i] = make_double2(cs, sn);
     ph32[i] = make_float2((float)cs, (float)sn);
+    const float ch = __double2float_rn(cs), sh = __double2float_rn(sn);
+    phdf[i] = make_float4(ch, __double2float_rn(cs - (double)ch), sh, __double2float_rn(sn - (double)sh));
 }
 
 // ---------------------------------------------------------------- host side
@@ -671,10 +673,12 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     if (B.has_k) {
         QS3_TRY(B.d_ph64.alloc((size_t)nsec * N * sizeof(double2)));
         QS3_TRY(B.d_ph32.alloc((size_t)nsec * N * sizeof(float2)));
+        QS3_TRY(B.d_phdf.alloc((size_t)nsec * N * sizeof(float4)));
         QS3_TRY(B.d_secs.upload(B.K.data(), B.K.size() * sizeof(int)));     // momenta for the table kernel
         const int tot = nsec * N;
         k_phase_tables<<<(tot + 255) / 256, 256>>>(nsec, N, B.L[0], B.L[1], B.L[2], B.d_secs.as<int>(),
-                                                   B.d_ph64.as<double2>(), B.d_ph32.as<float2>());
+                                                   B.d_ph64.as<double2>(), B.d_ph32.as<float2>(),
+                                                   B.d_phdf.as<float4>());
         QS3_LAUNCHED();
         QS3_CUDA(cudaDeviceSynchronize());
     }
@@ -689,6 +693,7 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
         v.tile0 = B.tile0[s];
         v.ph64 = B.has_k ? B.d_ph64.as<double2>() + (size_t)s * N : nullptr;
         v.ph32 = B.has_k ? B.d_ph32.as<float2>() + (size_t)s * N : nullptr;
+        v.phdf = B.has_k ? B.d_phdf.as<float4>() + (size_t)s * N : nullptr;
     }
     QS3_TRY(B.d_secs.upload(B.secs.data(), B.secs.size() * sizeof(SecView)));
     QS3_TRY(B.d_tile0.upload(B.tile0.data(), B.tile0.size() * 4));

@@ -64,6 +64,14 @@ __device__ __forceinline__ dfl df_norm(dfl a) {
     const float s = a.hi + a.lo;
     return {s, a.lo - (s - a.hi)};
 }
+// (a.hi + a.lo)(b.hi + b.lo), renormalised, dropping a.lo * b.lo
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_norm({p, e});
+}
 __device__ __forceinline__ dfl df_sum(dfl a, dfl b) {
     const float s = a.hi + b.hi;
     const float bb = s - a.hi;

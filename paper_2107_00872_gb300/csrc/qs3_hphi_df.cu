@@ -22,14 +22,6 @@ namespace qs3 {
 
 struct dfc { dfl re, im; };
 
-// (a.hi + a.lo)(b.hi + b.lo), renormalised, dropping a.lo * b.lo
-__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
-    const float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    return df_norm({p, e});
-}
 // complex double-float p times a real double-float f
 __device__ __forceinline__ float4 dfc_scale(float4 p, dfl f) {
     const dfl r = df_mul({p.x, p.y}, f), i = df_mul({p.z, p.w}, f);
@@ -48,11 +40,13 @@ __device__ __forceinline__ double2 dfc_out(const dfc &a) {
 
 // one thread per row, persistent grid over the tiles of all sectors (the
 // structure of k_hphi); phi may be phi + (*dx) ld when dx is given (the
-// solvers' CUDA graphs take the Krylov index from device memory)
-template <int ND, bool TB>
+// solvers' CUDA graphs take the Krylov index from device memory).  ODF:
+// psi is written in double-float form too (float4, renormalised), else as
+// complex128.
+template <int ND, bool TB, bool ODF>
 __global__ void __launch_bounds__(NTHREADS, 3) k_hphi_df(LatView L, const SecView *__restrict__ secs,
                                                       const int *__restrict__ tile0, int S, int ntiles,
-                                                      const float4 *__restrict__ phi, double2 *__restrict__ psi,
+                                                      const float4 *__restrict__ phi, void *__restrict__ psi,
                                                       const int *__restrict__ active, const int *__restrict__ dx,
                                                       uint64_t ld) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -78,7 +72,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi_df(LatView L, const SecVie
         const SecView sv = secs[s];
         if (s != cur) {
             __syncthreads();
-            for (int i = threadIdx.x; i < L.N; i += blockDim.x) ph[i] = split2(sv.ph64[i]);
+            for (int i = threadIdx.x; i < L.N; i += blockDim.x) ph[i] = sv.phdf[i];
             __syncthreads();
             cur = s;
         }
@@ -154,7 +148,12 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi_df(LatView L, const SecVie
         e = df_sum(e, {0.5f * dd.hi, 0.5f * dd.lo});
         df_mac(acc.re, e.hi, e.lo, x0.x, x0.y);
         df_mac(acc.im, e.hi, e.lo, x0.z, x0.w);
-        psi[sv.off + row] = dfc_out(acc);
+        if constexpr (ODF) {
+            const dfl re = df_norm(acc.re), im = df_norm(acc.im);
+            ((float4 *)psi)[sv.off + row] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        } else {
+            ((double2 *)psi)[sv.off + row] = dfc_out(acc);
+        }
     }
 }
 
@@ -171,16 +170,16 @@ __global__ void k_split_df(const double2 *__restrict__ x, float4 *__restrict__ y
         y[i] = split2(x[i]);
 }
 
-template <int ND, bool TB>
-static int hphi_df_ndt(Basis &B, const float4 *phi, const int *dx, uint64_t ld, double2 *psi, cudaStream_t st,
+template <int ND, bool TB, bool ODF>
+static int hphi_df_ndt(Basis &B, const float4 *phi, const int *dx, uint64_t ld, void *psi, cudaStream_t st,
                        const int *active) {
     static std::atomic<unsigned long long> cache{0};
     int grid = 1, occ = 1;
-    QS3_TRY(launch_rows(k_hphi_df<ND, TB>, B, B.smem_bytes, cache, &grid, &occ));
+    QS3_TRY(launch_rows(k_hphi_df<ND, TB, ODF>, B, B.smem_bytes, cache, &grid, &occ));
     if (B.ntiles == 0) return QS3_OK;
     auto launch = [&](int g) {
-        k_hphi_df<ND, TB><<<g, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S,
-                                                               B.ntiles, phi, psi, active, dx, ld);
+        k_hphi_df<ND, TB, ODF><<<g, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(),
+                                                                    B.S, B.ntiles, phi, psi, active, dx, ld);
     };
     int &bps = B.tune_hphi[QS3_C128DF];
     if (bps == 0) {
@@ -199,36 +198,39 @@ static int hphi_df_ndt(Basis &B, const float4 *phi, const int *dx, uint64_t ld, 
 }
 
 template <int ND>
-static int hphi_df_nd(Basis &B, const float4 *phi, const int *dx, uint64_t ld, double2 *psi, cudaStream_t st,
-                      const int *active) {
-    if (B.lv.orb) return hphi_df_ndt<ND, true>(B, phi, dx, ld, psi, st, active);
-    return hphi_df_ndt<ND, false>(B, phi, dx, ld, psi, st, active);
+static int hphi_df_nd(Basis &B, const float4 *phi, const int *dx, uint64_t ld, void *psi, bool out_df,
+                      cudaStream_t st, const int *active) {
+    if (out_df)
+        return B.lv.orb ? hphi_df_ndt<ND, true, true>(B, phi, dx, ld, psi, st, active)
+                        : hphi_df_ndt<ND, false, true>(B, phi, dx, ld, psi, st, active);
+    return B.lv.orb ? hphi_df_ndt<ND, true, false>(B, phi, dx, ld, psi, st, active)
+                    : hphi_df_ndt<ND, false, false>(B, phi, dx, ld, psi, st, active);
 }
 
 int hphi_df_launch(Basis &B, const void *phi, const int *dx, uint64_t ld, void *psi, cudaStream_t st,
-                   const int *active) {
+                   const int *active, bool out_df) {
     if (!phi || !psi) return set_err(QS3_ERR_INVALID_ARG, "NULL vector");
     if (phi == psi) return set_err(QS3_ERR_INVALID_ARG, "phi and psi alias");
     if (!B.has_k) return set_err(QS3_ERR_STATE, "C128DF needs a basis with momentum sectors");
     if (B.total == 0) return QS3_OK;
     const float4 *p = (const float4 *)phi;
-    double2 *q = (double2 *)psi;
+    void *q = psi;
     if (B.nd == 0) {
-        if (dx) return set_err(QS3_ERR_INVALID_ARG, "device-indexed C128DF needs N_down > 0");
+        if (dx || out_df) return set_err(QS3_ERR_INVALID_ARG, "double-float output or device index needs N_down > 0");
         const int grid = (int)std::min<uint64_t>((B.total + 255) / 256, 1024);
-        k_diag0_df<<<grid, 256, 0, st>>>(B.lv.c0, B.total, p, q);
+        k_diag0_df<<<grid, 256, 0, st>>>(B.lv.c0, B.total, p, (double2 *)q);
         QS3_LAUNCHED();
         return QS3_OK;
     }
     switch (B.nd) {
-        case 1: return hphi_df_nd<1>(B, p, dx, ld, q, st, active);
-        case 2: return hphi_df_nd<2>(B, p, dx, ld, q, st, active);
-        case 3: return hphi_df_nd<3>(B, p, dx, ld, q, st, active);
-        case 4: return hphi_df_nd<4>(B, p, dx, ld, q, st, active);
-        case 5: return hphi_df_nd<5>(B, p, dx, ld, q, st, active);
-        case 6: return hphi_df_nd<6>(B, p, dx, ld, q, st, active);
-        case 7: return hphi_df_nd<7>(B, p, dx, ld, q, st, active);
-        case 8: return hphi_df_nd<8>(B, p, dx, ld, q, st, active);
+        case 1: return hphi_df_nd<1>(B, p, dx, ld, q, out_df, st, active);
+        case 2: return hphi_df_nd<2>(B, p, dx, ld, q, out_df, st, active);
+        case 3: return hphi_df_nd<3>(B, p, dx, ld, q, out_df, st, active);
+        case 4: return hphi_df_nd<4>(B, p, dx, ld, q, out_df, st, active);
+        case 5: return hphi_df_nd<5>(B, p, dx, ld, q, out_df, st, active);
+        case 6: return hphi_df_nd<6>(B, p, dx, ld, q, out_df, st, active);
+        case 7: return hphi_df_nd<7>(B, p, dx, ld, q, out_df, st, active);
+        case 8: return hphi_df_nd<8>(B, p, dx, ld, q, out_df, st, active);
         default: return set_err(QS3_ERR_INVALID_ARG, "n_down %d", B.nd);
     }
 }

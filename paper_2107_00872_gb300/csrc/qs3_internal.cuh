@@ -115,6 +115,7 @@ struct SecView {
     int tile0;                    // first tile of the sector
     const double2 *ph64;          // k-sectors: per-site phases e^{-2 pi i K.r/L} (fp64) ...
     const float2 *ph32;           // ... and their fp32 copy; NULL for U(1)
+    const float4 *phdf;           // ... and their double-float split (re.hi, re.lo, im.hi, im.lo)
     const int32_t *t2;            // with the representative table: orbit g -> row of this sector, -1 if absent
 };
 
@@ -140,7 +141,7 @@ struct Basis {
     DevBuf d_u_f, d_adj_jz_f;
     DevBuf d_adj_jxy_lo, d_u_lo, d_adj_jz_lo;
     std::vector<DevBuf> d_sigma, d_stab, d_pidx;
-    DevBuf d_ph64, d_ph32;                  // S x N per-site phase tables (k-sectors)
+    DevBuf d_ph64, d_ph32, d_phdf;          // S x N per-site phase tables (k-sectors)
     DevBuf d_secs, d_tile0, d_chunk0;
     LatView lv{};
     std::vector<SecView> secs;
@@ -503,9 +504,9 @@ size_t row_kernel_smem(const Basis &B, int extra_nd);
 int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t st,
                 const int *active = nullptr);
 // C128DF product: phi in double-float form (float4 per element), or phi +
-// (*dx) ld when dx (device) is given; psi complex128
+// (*dx) ld when dx (device) is given; psi complex128, or double-float when out_df
 int hphi_df_launch(Basis &B, const void *phi, const int *dx, uint64_t ld, void *psi, cudaStream_t st,
-                   const int *active = nullptr);
+                   const int *active = nullptr, bool out_df = false);
 int count_nnz(Basis &B, uint64_t *nnz);
 // representative table: build (QS3_OK, or an error when it cannot be built) / release
 int build_rep_table(Basis &B, size_t max_bytes);

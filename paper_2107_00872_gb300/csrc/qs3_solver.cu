@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "qs3_internal.cuh"
@@ -529,6 +530,18 @@ __device__ __forceinline__ float4 ld_df(const float2 *p) { const float2 v = *p; 
 __device__ __forceinline__ float4 ld_df(const float4 *p) { return *p; }
 __device__ __forceinline__ void st_df(float2 *p, float4 v) { *p = make_float2(v.x, v.y); }
 __device__ __forceinline__ void st_df(float4 *p, float4 v) { *p = v; }
+// the working vector w of a Gram-Schmidt pass: fp64 (split on load) or
+// already double-float (the double-float engine of complex k-sector solves)
+__device__ __forceinline__ float4 ld_w(const double *p) { return split2(ld2(p)); }
+__device__ __forceinline__ float4 ld_w(const double2 *p) { return split2(ld2(p)); }
+__device__ __forceinline__ float4 ld_w(const float4 *p) { return *p; }
+// graph mode (dx): the three-term pass takes vectors x - 1, x (m = 2, x >= 1),
+// the full pass vectors 0 .. x
+__device__ __forceinline__ void graph_range(const int *dx, int ring, int &j0, int &m) {
+    if (!dx) return;
+    if (ring) { j0 = *dx - 1; m = 2; }
+    else { j0 = 0; m = *dx + 1; }
+}
 
 
 // part[c * m + j] = conj(V_{j0+j}) . w over the chunk as double-float
@@ -538,24 +551,24 @@ __device__ __forceinline__ void st_df(float4 *p, float4 v) { *p = v; }
 // instead of one per vector and warp).  NV vectors per pass have all their
 // loads in flight together (the staging depth, chosen by the autotuner).
 constexpr int GDF = NTHREADS / 32;
-template <typename VT, int NV>
+template <typename VT, int NV, typename WV = VT>
 __global__ void __launch_bounds__(NTHREADS, NV == 2 ? 3 : 1) k_mdot_df(const typename DfS<VT>::T *__restrict__ V, uint64_t D, int j0,
-                                                      int m, const VT *__restrict__ w,
+                                                      int m, const WV *__restrict__ w,
                                                       const SecView *__restrict__ secs,
                                                       const int *__restrict__ chunk0, int S,
                                                       const int *__restrict__ active, float4 *__restrict__ part,
-                                                      const int *__restrict__ dx = nullptr) {
+                                                      const int *__restrict__ dx = nullptr, int ring = 0) {
     using ST = typename DfS<VT>::T;
     static_assert(GDF % NV == 0, "vectors per pass must divide the group");
     __shared__ float4 red[GDF][NTHREADS];
-    if (dx) m = *dx + 1;
+    graph_range(dx, ring, j0, m);
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
     if (active && !active[ci.s]) return;
     float4 wv[RPT];
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
         const int r = threadIdx.x + k * NTHREADS;
-        wv[k] = (r < ci.n) ? split2(ld2(w + ci.base + r)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        wv[k] = (r < ci.n) ? ld_w(w + ci.base + r) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // rows past the chunk end read the chunk's last row (always written) and
@@ -612,12 +625,17 @@ __global__ void __launch_bounds__(NTHREADS, NV == 2 ? 3 : 1) k_mdot_df(const typ
     }
 }
 
-// k_reduce for double-float chunk partials (graph mode: m = x + 1)
+// k_reduce for double-float chunk partials (graph mode: the range of graph_range,
+// written from out + j0)
 __global__ void k_reduce_df(const float4 *__restrict__ part, int m, const int *__restrict__ chunk0,
                             const int *__restrict__ active, double2 *__restrict__ out, int ldo,
-                            const int *__restrict__ dx = nullptr) {
+                            const int *__restrict__ dx = nullptr, int ring = 0) {
     const int s = blockIdx.y;
-    if (dx) m = *dx + 1;
+    if (dx) {
+        int j0 = 0;
+        graph_range(dx, ring, j0, m);
+        out += j0;
+    }
     if (active && !active[s]) return;
     __shared__ double2 red[NTHREADS / 32];
     for (int j = blockIdx.x; j < m; j += gridDim.x) {
@@ -645,16 +663,22 @@ __global__ void k_reduce_df(const float4 *__restrict__ part, int m, const int *_
 // before this update; the second Gram-Schmidt pass, whose coefficients are
 // O(eps |w|)), u is formed in plain fp32 from the hi words instead: its
 // error, 2^-24 |u| <= 2^-24 * 2^-40 * sqrt(m) |w|, is below fp64 rounding of w.
-template <typename VT>
-__global__ void __launch_bounds__(NTHREADS) k_mupdate_df(VT *__restrict__ w, const typename DfS<VT>::T *__restrict__ V,
+// WV = float4: w itself is double-float (the double-float engine); the
+// update and |w|^2 then stay on the fp32 units as well.
+template <typename VT, typename WV = VT>
+__global__ void __launch_bounds__(NTHREADS) k_mupdate_df(WV *__restrict__ w, const typename DfS<VT>::T *__restrict__ V,
                                                          uint64_t D, int j0, int m, const double2 *__restrict__ coef,
                                                          int ldc, const SecView *__restrict__ secs,
                                                          const int *__restrict__ chunk0, int S,
                                                          const int *__restrict__ active,
                                                          const double2 *__restrict__ wn2, double2 *__restrict__ part,
-                                                         const int *__restrict__ dx = nullptr) {
+                                                         const int *__restrict__ dx = nullptr, int ring = 0) {
     using ST = typename DfS<VT>::T;
-    if (dx) m = *dx + 1;
+    constexpr bool WD = std::is_same<WV, float4>::value;
+    if (dx) {
+        graph_range(dx, ring, j0, m);
+        if (ring) coef += j0;
+    }
     extern __shared__ float4 scf[];   // per j: split coefficient (re.hi, re.lo, im.hi, im.lo)
     __shared__ double red[NTHREADS / 32];
     __shared__ unsigned cbits;
@@ -669,7 +693,9 @@ __global__ void __launch_bounds__(NTHREADS) k_mupdate_df(VT *__restrict__ w, con
     }
     __syncthreads();
     const bool lite = wn2 && (double)__uint_as_float(cbits) <= 0x1p-80 * wn2[ci.s].x;
-    double2 u[RPT];
+    dfl ur[RPT], ui[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) ur[k] = ui[k] = {0.f, 0.f};
     if (lite) {
         float2 uf[RPT];
 #pragma unroll
@@ -692,11 +718,11 @@ __global__ void __launch_bounds__(NTHREADS) k_mupdate_df(VT *__restrict__ w, con
             }
         }
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) u[k] = make_double2((double)uf[k].x, (double)uf[k].y);
+        for (int k = 0; k < RPT; ++k) {
+            ur[k].hi = uf[k].x;
+            ui[k].hi = uf[k].y;
+        }
     } else {
-        dfl ur[RPT], ui[RPT];
-#pragma unroll
-        for (int k = 0; k < RPT; ++k) ur[k] = ui[k] = {0.f, 0.f};
         for (int j = 0; j < m; ++j) {
             const float4 c = scf[j];
             const ST *vj = V + (uint64_t)(j0 + j) * D + ci.base;
@@ -715,20 +741,35 @@ __global__ void __launch_bounds__(NTHREADS) k_mupdate_df(VT *__restrict__ w, con
                 }
             }
         }
-#pragma unroll
-        for (int k = 0; k < RPT; ++k)
-            u[k] = make_double2((double)ur[k].hi + (double)ur[k].lo, (double)ui[k].hi + (double)ui[k].lo);
     }
     double nrm = 0.0;
+    if constexpr (WD) {
+        // w - u in double-float, |w|^2 accumulated per thread in double-float
+        dfl n2 = {0.f, 0.f};
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int r = threadIdx.x + k * NTHREADS;
-        if (r < ci.n) {
-            double2 v = ld2(w + ci.base + r);
-            v.x -= u[k].x;
-            if (IsC<VT>::v) v.y -= u[k].y;
-            st2(w + ci.base + r, v);
-            nrm += v.x * v.x + v.y * v.y;
+        for (int k = 0; k < RPT; ++k) {
+            const int r = threadIdx.x + k * NTHREADS;
+            if (r < ci.n) {
+                const float4 v = w[ci.base + r];
+                const dfl re = df_sum({v.x, v.y}, {-ur[k].hi, -ur[k].lo});
+                const dfl im = df_sum({v.z, v.w}, {-ui[k].hi, -ui[k].lo});
+                w[ci.base + r] = make_float4(re.hi, re.lo, im.hi, im.lo);
+                df_mac(n2, re.hi, re.lo, re.hi, re.lo);
+                df_mac(n2, im.hi, im.lo, im.hi, im.lo);
+            }
+        }
+        nrm = df_d(n2);
+    } else {
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int r = threadIdx.x + k * NTHREADS;
+            if (r < ci.n) {
+                double2 v = ld2(w + ci.base + r);
+                v.x -= (double)ur[k].hi + (double)ur[k].lo;
+                if (IsC<VT>::v) v.y -= (double)ui[k].hi + (double)ui[k].lo;
+                st2(w + ci.base + r, v);
+                nrm += v.x * v.x + v.y * v.y;
+            }
         }
     }
     if (part) {
@@ -765,6 +806,29 @@ __global__ void __launch_bounds__(NTHREADS) k_scale_split(VT *__restrict__ w, ty
             v.y *= f;
             st2(w + ci.base + r, v);
             st_df(out + ci.base + r, split2(v));
+        }
+    }
+}
+
+// double-float engine: basis vector x + 1 = w * inv[s], all in double-float
+__global__ void __launch_bounds__(NTHREADS) k_scale_df(const float4 *__restrict__ w, float4 *__restrict__ out,
+                                                       const double *__restrict__ inv,
+                                                       const SecView *__restrict__ secs,
+                                                       const int *__restrict__ chunk0, int S,
+                                                       const int *__restrict__ active,
+                                                       const int *__restrict__ dx = nullptr, uint64_t D = 0) {
+    if (dx) out += (uint64_t)(*dx + 1) * D;     // graph mode: out is the store's base, vector x + 1
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    const float2 fs = split_d(inv[ci.s]);
+    const dfl f = {fs.x, fs.y};
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r < ci.n) {
+            const float4 v = w[ci.base + r];
+            const dfl re = df_mul({v.x, v.y}, f), im = df_mul({v.z, v.w}, f);
+            out[ci.base + r] = make_float4(re.hi, re.lo, im.hi, im.lo);
         }
     }
 }
@@ -1065,11 +1129,16 @@ struct Engine {
     }
     Engine(const Engine &) = delete;
     Engine &operator=(const Engine &) = delete;
-    // replay Lanczos steps as CUDA graphs (fp64 engine; ignored otherwise)
-    // fp64 k-sector engine: apply H to the double-float copy svec(x) of psi_x
-    // (QS3_C128DF) instead of the fp64 ring vector
+    // double-float engine (fp64 complex k-sector solves; set before init):
+    // H is applied to the stored double-float psi_x (QS3_C128DF) and w = H
+    // psi_x, its three-term and Gram-Schmidt updates and the scaling into
+    // psi_{x+1} all stay in double-float (float4 per element, wdf) on the
+    // fp32 units; the fp64 ring then only carries the start vector
     bool dfh = false;
+    DevBuf wdf;
+    float4 *wd() { return wdf.as<float4>(); }
     void use_df_hphi(bool on) { dfh = on && DF && IsC<VT>::v && B.has_k && B.nd > 0; }
+    // replay Lanczos steps as CUDA graphs (fp64 engine; ignored otherwise)
     int enable_graphs(bool on) {
         graphs = on && DF && B.nchunks > 0;
         if (graphs && !xdev.p) QS3_TRY(xdev.alloc(sizeof(int)));
@@ -1101,6 +1170,10 @@ struct Engine {
         D = B.total;
         QS3_TRY(V.alloc((uint64_t)(cap + nscr) * D * sizeof(ST)));
         if (DF) QS3_TRY(ring.alloc(3 * D * sizeof(VT)));
+        if (dfh) {
+            QS3_TRY(wdf.alloc(D * sizeof(float4)));
+            QS3_CUDA(cudaMemsetAsync(wdf.p, 0, wdf.n, st));
+        }
         QS3_TRY(part.alloc((uint64_t)std::max(B.nchunks, 1) * cap * sizeof(double2)));
         QS3_TRY(h1.alloc((uint64_t)B.S * cap * sizeof(double2)));
         QS3_TRY(h2.alloc((uint64_t)B.S * cap * sizeof(double2)));
@@ -1136,26 +1209,31 @@ struct Engine {
         return QS3_OK;
     }
     // dot products / update against the stored basis vectors j0 .. j0 + m - 1
-    int mdot(int j0, int m, const VT *w, double2 *out, int ldo) {
+    // (w: VT, or float4 for the double-float engine)
+    template <typename WV>
+    int mdot(int j0, int m, const WV *w, double2 *out, int ldo) {
         if (B.nchunks == 0) return QS3_OK;
         if constexpr (DF)
             QS3_TRY(mdot_df(B.tune_nv, j0, m, w, nullptr));
         else
-            k_mdot32<VT><<<grid(), NTHREADS, 0, st>>>(V.as<VT>(), D, j0, m, w, secs(), c0(), B.S, act(), part.as<double2>());
+            k_mdot32<VT><<<grid(), NTHREADS, 0, st>>>(V.as<VT>(), D, j0, m, (const VT *)w, secs(), c0(), B.S, act(),
+                                                      part.as<double2>());
         QS3_LAUNCHED();
         return reduce(m, out, ldo, DF);
     }
-    // k_mdot_df with nv basis vectors per pass (1, 2 or 4; other values: 2)
-    int mdot_df(int nv, int j0, int m, const VT *w, const int *dx) {
+    // k_mdot_df with nv basis vectors per pass (1, 2 or 4; other values: 2);
+    // graph mode (dx): ring selects the three-term range (see graph_range)
+    template <typename WV>
+    int mdot_df(int nv, int j0, int m, const WV *w, const int *dx, int ring = 0) {
         if constexpr (DF) {
             const ST *v = V.as<ST>();
             float4 *pp = (float4 *)part.p;
             if (nv == 1)
-                k_mdot_df<VT, 1><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx);
+                k_mdot_df<VT, 1, WV><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx, ring);
             else if (nv == 4)
-                k_mdot_df<VT, 4><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx);
+                k_mdot_df<VT, 4, WV><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx, ring);
             else
-                k_mdot_df<VT, 2><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx);
+                k_mdot_df<VT, 2, WV><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx, ring);
             QS3_LAUNCHED();
         }
         return QS3_OK;
@@ -1181,7 +1259,8 @@ struct Engine {
                 float tmin = 1e30f;
                 for (int rep = 0; rep < 3 && rc2 == QS3_OK; ++rep) {
                     if (cudaEventRecord(e0, st) != cudaSuccess) { rc2 = QS3_ERR_CUDA; break; }
-                    rc2 = mdot_df(nv, 0, m, rvec(rw), nullptr);
+                    rc2 = dfh ? mdot_df(nv, 0, m, (const float4 *)wd(), nullptr)
+                              : mdot_df(nv, 0, m, (const VT *)rvec(rw), nullptr);
                     if (rc2 != QS3_OK) break;
                     if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
                         rc2 = QS3_ERR_CUDA;
@@ -1202,15 +1281,16 @@ struct Engine {
     }
     // nrm_out (optional): per-sector |w|^2 after the update; wn2 (DF, optional):
     // |w|^2 before it, which lets small-coefficient updates run in plain fp32
-    int mupdate(VT *w, int j0, int m, const double2 *cf, int ldc, double2 *nrm_out, const double2 *wn2 = nullptr) {
+    template <typename WV>
+    int mupdate(WV *w, int j0, int m, const double2 *cf, int ldc, double2 *nrm_out, const double2 *wn2 = nullptr) {
         if (B.nchunks == 0) return QS3_OK;
         double2 *pp = nrm_out ? part.as<double2>() : nullptr;
         if constexpr (DF)
-            k_mupdate_df<VT><<<grid(), NTHREADS, m * sizeof(float4), st>>>(w, V.as<ST>(), D, j0, m, cf, ldc, secs(), c0(),
-                                                                         B.S, act(), wn2, pp);
+            k_mupdate_df<VT, WV><<<grid(), NTHREADS, m * sizeof(float4), st>>>(w, V.as<ST>(), D, j0, m, cf, ldc, secs(),
+                                                                             c0(), B.S, act(), wn2, pp);
         else
-            k_mupdate32<VT><<<grid(), NTHREADS, m * sizeof(float4), st>>>(w, V.as<VT>(), D, j0, m, cf, ldc, secs(), c0(),
-                                                                          B.S, act(), pp);
+            k_mupdate32<VT><<<grid(), NTHREADS, m * sizeof(float4), st>>>((VT *)w, V.as<VT>(), D, j0, m, cf, ldc, secs(),
+                                                                          c0(), B.S, act(), pp);
         QS3_LAUNCHED();
         if (nrm_out) return reduce(1, nrm_out, 1);
         return QS3_OK;
@@ -1270,6 +1350,9 @@ struct Engine {
     // from xdev (the body of the captured graphs; DF engine, not full2)
     int step_body_dev() {
         const int *dx = xdev.as<int>();
+        if constexpr (DF) {
+            if (dfh) return step_body_dev_df(dx);
+        }
         VT *w = rvec(rw);
         if (dfh)
             QS3_TRY(hphi_df_launch(B, V.p, dx, D, w, st, act()));
@@ -1310,10 +1393,48 @@ struct Engine {
         }
         return QS3_OK;
     }
-    // the graph of the current ring phase, captured on first use
+    // the double-float engine's step with x from xdev (x >= 1)
+    int step_body_dev_df(const int *dx) {
+        float4 *w = wd();
+        const ST *v = V.as<ST>();
+        double2 *hh1 = h1.as<double2>(), *n1 = nrm1.as<double2>();
+        QS3_TRY(hphi_df_launch(B, V.p, dx, D, w, st, act(), true));
+        // three-term part against psi_{x-1}, psi_x
+        QS3_TRY(mdot_df(B.tune_nv, 0, 2, (const float4 *)w, dx, 1));
+        k_reduce_df<<<dim3(2, B.S), NTHREADS, 0, st>>>((const float4 *)part.p, 2, c0(), act(), hh1, cap, dx, 1);
+        QS3_LAUNCHED();
+        k_mupdate_df<VT, float4><<<grid(), NTHREADS, 2 * sizeof(float4), st>>>(w, v, D, 0, 2, hh1, cap, secs(), c0(),
+                                                                              B.S, act(), nullptr, part.as<double2>(),
+                                                                              dx, 1);
+        QS3_LAUNCHED();
+        k_reduce<<<dim3(1, B.S), NTHREADS, 0, st>>>(part.as<double2>(), 1, c0(), act(), n1, 1);
+        QS3_LAUNCHED();
+        // one Gram-Schmidt pass against psi_0 .. psi_x
+        QS3_TRY(mdot_df(B.tune_nv, 0, cap, (const float4 *)w, dx, 0));
+        k_reduce_df<<<dim3(std::min(cap, 64), B.S), NTHREADS, 0, st>>>((const float4 *)part.p, cap, c0(), act(),
+                                                                       h2.as<double2>(), cap, dx, 0);
+        QS3_LAUNCHED();
+        k_mupdate_df<VT, float4><<<grid(), NTHREADS, cap * sizeof(float4), st>>>(w, v, D, 0, cap, h2.as<double2>(), cap,
+                                                                                secs(), c0(), B.S, act(), n1,
+                                                                                part.as<double2>(), dx, 0);
+        QS3_LAUNCHED();
+        k_reduce<<<dim3(1, B.S), NTHREADS, 0, st>>>(part.as<double2>(), 1, c0(), act(), nrm.as<double2>(), 1);
+        QS3_LAUNCHED();
+        k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, 0, cap, hh1, nrm.as<double2>(), act(), alpha.as<double>(),
+                                                         beta.as<double>(), inv.as<double>(), brk, dx);
+        QS3_LAUNCHED();
+        k_scale_df<<<grid(), NTHREADS, 0, st>>>(w, V.as<float4>(), inv.as<double>(), secs(), c0(), B.S, act(), dx, D);
+        QS3_LAUNCHED();
+        k_advance<<<1, 1, 0, st>>>(xdev.as<int>());
+        QS3_LAUNCHED();
+        return QS3_OK;
+    }
+    // the graph of the current ring phase (one graph for the double-float
+    // engine, whose step does not rotate the ring), captured on first use
     int graph_step(int x) {
         if (!cs) QS3_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        if (!gx[rc]) {
+        const int gi = dfh ? 0 : rc;
+        if (!gx[gi]) {
             cudaStream_t keep = st;
             st = cs;
             cudaGraph_t g = nullptr;
@@ -1328,21 +1449,21 @@ struct Engine {
             if (e != cudaSuccess) return set_err(QS3_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
             size_t nn = 0;
             cudaGraphGetNodes(g, nullptr, &nn);
-            const cudaError_t ei = cudaGraphInstantiate(&gx[rc], g, 0);
+            const cudaError_t ei = cudaGraphInstantiate(&gx[gi], g, 0);
             cudaGraphDestroy(g);
             if (ei != cudaSuccess) {
-                gx[rc] = nullptr;
+                gx[gi] = nullptr;
                 return set_err(QS3_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ei));
             }
-            gnodes[rc] = (long long)nn;
+            gnodes[gi] = (long long)nn;
             count_launch(-(long long)nn);   // the capture ran nothing
         }
         if (xdev_val != x) {
             k_setx<<<1, 1, 0, st>>>(xdev.as<int>(), x);
             QS3_LAUNCHED();
         }
-        QS3_CUDA(cudaGraphLaunch(gx[rc], st));
-        count_launch(gnodes[rc]);
+        QS3_CUDA(cudaGraphLaunch(gx[gi], st));
+        count_launch(gnodes[gi]);
         xdev_val = x + 1;
         return QS3_OK;
     }
@@ -1361,11 +1482,16 @@ struct Engine {
             for (int s = 0; s < B.S; ++s)
                 if (h_active[s]) stats->nnz += B.nnz_sec[s];
             QS3_TRY(graph_step(x));
-            const int o = rp;
-            rp = rc;
-            rc = rw;
-            rw = o;
+            if (!dfh) {
+                const int o = rp;
+                rp = rc;
+                rc = rw;
+                rw = o;
+            }
             return QS3_OK;
+        }
+        if constexpr (DF) {
+            if (dfh) return step_df(x, full2);
         }
         VT *w = hout(x);
         std::pair<cudaEvent_t, cudaEvent_t> ev;
@@ -1399,6 +1525,36 @@ struct Engine {
             rp = rc;
             rc = rw;
             rw = o;
+        }
+        return QS3_OK;
+    }
+    // the double-float engine's step (see dfh)
+    int step_df(int x, bool full2) {
+        float4 *w = wd();
+        std::pair<cudaEvent_t, cudaEvent_t> ev;
+        QS3_TRY(stats->pair(ev));
+        QS3_CUDA(cudaEventRecord(ev.first, st));
+        QS3_TRY(hphi_df_launch(B, svec(x), nullptr, 0, w, st, act(), true));
+        QS3_CUDA(cudaEventRecord(ev.second, st));
+        stats->pend.push_back(ev);
+        stats->calls += 1;
+        for (int s = 0; s < B.S; ++s)
+            if (h_active[s]) stats->nnz += B.nnz_sec[s];
+        // three-term part (full2: all of psi_0 .. psi_x), then one Gram-Schmidt pass
+        const int j0 = full2 ? 0 : std::max(0, x - 1);
+        double2 *n1 = nrm1.as<double2>();
+        QS3_TRY(mdot(j0, x + 1 - j0, (const float4 *)w, h1.as<double2>() + j0, cap));
+        QS3_TRY(mupdate(w, j0, x + 1 - j0, h1.as<double2>() + j0, cap, n1));
+        QS3_TRY(mdot(0, x + 1, (const float4 *)w, h2.as<double2>(), cap));
+        QS3_TRY(mupdate(w, 0, x + 1, h2.as<double2>(), cap, nrm.as<double2>(), n1));
+        k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, x, cap, h1.as<double2>(), nrm.as<double2>(), act(),
+                                                         alpha.as<double>(), beta.as<double>(), inv.as<double>(), brk);
+        QS3_LAUNCHED();
+        if constexpr (std::is_same<ST, float4>::value) {
+            if (B.nchunks > 0) {
+                k_scale_df<<<grid(), NTHREADS, 0, st>>>(w, svec(x + 1), inv.as<double>(), secs(), c0(), B.S, act());
+                QS3_LAUNCHED();
+            }
         }
         return QS3_OK;
     }
@@ -1483,9 +1639,9 @@ static int lanczos_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT
                        typename Wide<VT>::T *out, cudaStream_t st, LzResult &R, HphiStats &hs) {
     Engine<VT> E(B, st, &hs);
     const int nmax = std::max(2, o.n_max);
+    E.use_df_hphi(o.hphi_ieee == 0);
     QS3_TRY(E.init(nmax + 1, 0));
     QS3_TRY(E.enable_graphs(o.use_graphs != 0));
-    E.use_df_hphi(o.hphi_ieee == 0);
     if (start) QS3_TRY(E.start_from(start)); else QS3_TRY(E.start_random(o.seed));
     const int S = B.S;
     R.e.assign(S, NAN);
@@ -1581,9 +1737,9 @@ static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T
     const int NE = std::max(1, std::min(o.n_eig, NK));
     if (NK > MAXOUT) return set_err(QS3_ERR_INVALID_ARG, "n_keep %d > %d", NK, MAXOUT);
     Engine<VT> E(B, st, &hs);
+    E.use_df_hphi(o.hphi_ieee == 0);
     QS3_TRY(E.init(NM + 1, NK));
     QS3_TRY(E.enable_graphs(o.use_graphs != 0));
-    E.use_df_hphi(o.hphi_ieee == 0);
     if (start) QS3_TRY(E.start_from(start)); else QS3_TRY(E.start_random(o.seed));
     R.e.assign((size_t)S * NE, NAN);
     R.conv.assign(S, 0);
@@ -1929,8 +2085,8 @@ int dsf_run(int op, Basis &S, int ss, const void *gs, double e0, Basis &Dd, int 
     QS3_TRY(count_nnz(Dd, &nz));
     HphiStats hs;
     Engine<double2> E(Dd, st, &hs);
-    QS3_TRY(E.init(n_iter + 1, 0));
     E.use_df_hphi(true);
+    QS3_TRY(E.init(n_iter + 1, 0));
     for (int n = 0; n < nq; ++n)
         QS3_TRY(sq_launch(op, S, ss, gs, Dd, n, Q + 3 * n, E.hin(0) + Dd.offs[n], st));
     QS3_TRY(E.normalise_start());
@@ -1997,6 +2153,7 @@ static size_t solve_mem_estimate(const Basis &B, const qs3_solve_opts &o) {
     size_t m = cap * B.total * ev + 2 * B.total * ev64 + (size_t)std::max(B.nchunks, 1) * cap * 16;
     if (o.precision == QS3_F32) m += cap * B.total * ev64;   // the fp64 refinement
     m += 3 * B.total * ev64;                                 // fp64 ring of the fp64 engine
+    if (B.has_k && !o.hphi_ieee) m += B.total * 16;          // double-float w of that engine
     return m;
 }
 
