@@ -56,13 +56,18 @@ def load_peaks():
 
 N_SMS = 152
 
-# ncu figures of one full k_hphi launch (all sectors active) of the solve
-# workloads: DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and the
-# fp64 pipe's active cycles; see the named summary
+# ncu figures of the solve's two largest kernels (see the named summaries).
+# GS_PROFILE: one captured launch of the double-float Gram-Schmidt dot pass,
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) over the launch's
+# algorithmic bytes (stored vectors + w read); the ratio scales to the launches
+# of a run.  HPHI_PROFILE: one full launch of the double-float H Phi (all
+# sectors active): DRAM bytes and warp instructions executed.
+GS_PROFILE = {"kernel": "k_mdot_df<complex, double-float w> (Gram-Schmidt dot products)",
+              "dram_over_alg": None, "profile": "profiles/k_mdot_df_k_mupdate_df_square10x10_nd4_40k.md"}
 HPHI_PROFILE = {
-    "square10x10_nd4_all_k": {"kernel": "k_hphi<4, complex128, k-sector, representative table>",
-                              "dram_bytes": 122385664 + 40377856, "fp64_pipe_active": 0.809,
-                              "profile": "profiles/k_hphi_c128_square10x10_nd4_all_k.md"},
+    "square10x10_nd4_all_k": {"kernel": "k_hphi_df<4, representative table> (double-float H Phi)",
+                              "dram_bytes": None, "warp_inst": None,
+                              "profile": "profiles/k_hphi_df_square10x10_nd4_all_k.md"},
 }
 
 WORKLOADS = {
@@ -215,41 +220,46 @@ def run_ours(args, rank, world):
     t_max, nnz_all = reduce_ranks(t_local, float(nnz_steps), world, dev)
     value = nnz_all / t_max / 1e9
 
-    # roofline of the H Phi launches (dominant kernel of the step)
+    # H Phi launches: per full launch (sectors drop out of the launches as
+    # they converge, so figures scale by the average work per launch)
     peaks, peak_kind = load_peaks()
+    hbm_peak = peaks.get("hbm_gbs")
     D = basis.total_dim
     s_phi = 16
     per_launch_nnz = nnz_steps / max(hphi_calls, 1)
-    # sectors drop out of the launches as they converge: scale full-launch
-    # figures by the average work per launch
     frac_work = per_launch_nnz / nnz_h
     t_launch = hphi_s / max(hphi_calls, 1)
     # algorithmic bytes of one full launch: diagonal read, one gather per term,
     # psi write, sigma row rank, one sigma probe per term
     B_alg = frac_work * (D * s_phi + (nnz_h - D) * s_phi + D * s_phi + D * 8 + (nnz_h - D) * 8)
-    hbm = {"achieved": round(B_alg / t_launch / 1e9, 1), "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-           "frac": round(B_alg / t_launch / 1e9 / peaks.get("hbm_gbs"), 4)}
+    hphi = {"launch_ms": round(1e3 * t_launch, 4), "launch_gnnz_s": round(per_launch_nnz / t_launch / 1e9, 2),
+            "alg_gbs": round(B_alg / t_launch / 1e9, 1), "hbm_frac_alg": round(B_alg / t_launch / 1e9 / hbm_peak, 4),
+            "share_of_step": round(hphi_s / t_local, 3)}
     prof = HPHI_PROFILE.get(args.workload) if args.sectors <= 0 else None
-    if prof is not None:
-        # the k-sector complex128 H Phi is bound by the fp64 pipe (gathers are
-        # served by L2): achieved = algorithmic fp64 flops of the launch (one
-        # complex multiply-add, 8 flops, per off-diagonal term; a real x complex
-        # diagonal, 4 flops, per row) over the live launch time; peak = 2 fp64
-        # FMA per clock per SM x 152 SMs x max SM clock
-        flops = frac_work * (8.0 * (nnz_h - D) + 4.0 * D)
-        peak_fp64 = 2 * 2 * N_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        ach = flops / t_launch / 1e12
-        roof = {"kernel": prof["kernel"], "bound": "alu", "achieved": round(ach, 4), "peak": round(peak_fp64, 4),
-                "unit": "TFLOP/s (fp64)", "frac": round(ach / peak_fp64, 4),
-                "traffic": int(prof["dram_bytes"] * frac_work), "traffic_source": prof["profile"],
-                "peak_source": "derived: 2 fp64 FMA/clock/SM x 152 SMs x sm_max_mhz (MEASURED_PEAKS.json)",
-                "fp64_pipe_active_ncu": prof["fp64_pipe_active"], "hbm_alg_bytes": hbm}
+    if prof is not None and prof["warp_inst"]:
+        # issue-slot roof: 4 warp instructions per clock per SM
+        issue_peak = 4 * N_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6
+        hphi.update({"kernel": prof["kernel"], "bound": "alu (issue)",
+                     "issue_frac": round(prof["warp_inst"] * frac_work / t_launch / issue_peak, 4),
+                     "traffic": int(prof["dram_bytes"] * frac_work), "traffic_source": prof["profile"]})
+    # the Gram-Schmidt dot pass (timed by the library around its launches)
+    gs_s = sum(i["gs_dot_seconds"] for i in infos)
+    gs_b = sum(i["gs_dot_bytes"] for i in infos)
+    gs_calls = sum(i["gs_dot_calls"] for i in infos)
+    if gs_s > hphi_s and gs_calls > 0:
+        ach = gs_b / gs_s / 1e9
+        ratio = GS_PROFILE["dram_over_alg"]
+        roof = {"kernel": GS_PROFILE["kernel"], "bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak,
+                "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+                "traffic": int(ratio * gs_b / gs_calls) if ratio else None,
+                "traffic_source": GS_PROFILE["profile"] + " (DRAM / algorithmic bytes of a captured launch x the "
+                                                            "run's algorithmic bytes per launch)",
+                "alg_bytes_per_launch": int(gs_b / gs_calls), "launch_ms": round(1e3 * gs_s / gs_calls, 4),
+                "share_of_step": round(gs_s / t_local, 3), "hphi": hphi}
     else:
-        roof = {"kernel": "k_hphi", "bound": "hbm", **hbm, "traffic": None}
-    roof["peak_hbm_source"] = (f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                               else "fallback")
-    roof.update({"launch_ms": round(1e3 * t_launch, 4), "launch_gnnz_s": round(per_launch_nnz / t_launch / 1e9, 2),
-                 "hphi_share_of_step": round(hphi_s / (t_local), 3)})
+        roof = {"kernel": "k_hphi_df", "bound": "hbm", "achieved": hphi["alg_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": hphi["hbm_frac_alg"], "traffic": hphi.get("traffic"), "hphi": hphi}
+    roof["peak_source"] = (f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback")
 
     out = {
         "metric": "H Phi Gnnz/s (batched Lanczos ground-state solve)",
@@ -262,13 +272,14 @@ def run_ours(args, rank, world):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "c128",
+        "dtype": "c128 (double-float: pairs of fp32)",
         "data": "synthetic",
         "config": {"workload": args.workload + (f"_first{args.sectors}k" if args.sectors > 0 else ""),
                    "lattice": spec.name, "n_sites": spec.n_sites, "n_down": nd,
                    "sectors": basis.n_sectors, "total_dim": D, "nnz_per_hphi": nnz_h,
-                   "solver": "Lanczos with full reorthogonalisation every step: fp64 H Phi and three-term "
-                             "part, Gram-Schmidt over a double-float (48-bit) store of the Krylov basis",
+                   "solver": "Lanczos with full reorthogonalisation every step, double-float (48-bit) "
+                             "arithmetic on the fp32 units: H Phi, three-term part and Gram-Schmidt over the "
+                             "double-float store of the Krylov basis; fp64 scalars and IEEE fp64 residuals",
                    "l2": "working set > L2 (Krylov basis of ~100 vectors x 63 MB)",
                    "parallelism": f"replicas x{world} (independent sectors per GPU)"},
         "roofline": roof,

@@ -196,6 +196,10 @@ typedef struct {
     double hphi_seconds;  /* device time of the H Phi launches outside CUDA graphs (CUDA events on the call's stream) */
     int32_t hphi_calls;   /* H Phi launches */
     int32_t hphi_graph_calls; /* of which replayed inside CUDA graphs (not in hphi_seconds) */
+    double gs_dot_seconds;    /* device time of the Gram-Schmidt dot-product launches outside CUDA graphs */
+    uint64_t gs_dot_bytes;    /* their algorithmic bytes: stored basis vectors and w read, active sectors */
+    int32_t gs_dot_calls;     /* those launches */
+    int32_t reserved;
 } qs3_solve_info;
 
 /* Conventional Lanczos with full reorthogonalisation (Alg. 10 lines 2-12)

@@ -31,7 +31,8 @@ class qs3_solve_opts(ctypes.Structure):
 class qs3_solve_info(ctypes.Structure):
     _fields_ = [("iterations", I32), ("restarts", I32), ("converged", I32), ("refine_iterations", I32),
                 ("max_residual", F64), ("seconds", F64), ("hphi_nnz", U64), ("hphi_seconds", F64),
-                ("hphi_calls", I32), ("hphi_graph_calls", I32)]
+                ("hphi_calls", I32), ("hphi_graph_calls", I32), ("gs_dot_seconds", F64), ("gs_dot_bytes", U64),
+                ("gs_dot_calls", I32), ("reserved", I32)]
 
 
 # name -> (argtypes, restype); every entry point declared in include/qs3.h

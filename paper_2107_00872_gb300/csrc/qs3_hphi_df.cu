@@ -42,9 +42,12 @@ __device__ __forceinline__ double2 dfc_out(const dfc &a) {
 // structure of k_hphi); phi may be phi + (*dx) ld when dx is given (the
 // solvers' CUDA graphs take the Krylov index from device memory).  ODF:
 // psi is written in double-float form too (float4, renormalised), else as
-// complex128.
-template <int ND, bool TB, bool ODF>
-__global__ void __launch_bounds__(NTHREADS, 3) k_hphi_df(LatView L, const SecView *__restrict__ secs,
+// complex128.  DEGB > 0 (representative table only): per occupied site the
+// first DEGB hops go in stages -- all target ranks, then all table entries,
+// then all rows, then all gathers -- so each stage's independent loads are in
+// flight together instead of one dependent chain per hop.
+template <int ND, bool TB, bool ODF, int DEGB>
+__global__ void __launch_bounds__(NTHREADS, DEGB == 4 ? 4 : 3) k_hphi_df(LatView L, const SecView *__restrict__ secs,
                                                       const int *__restrict__ tile0, int S, int ntiles,
                                                       const float4 *__restrict__ phi, void *__restrict__ psi,
                                                       const int *__restrict__ active, const int *__restrict__ dx,
@@ -86,12 +89,74 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi_df(LatView L, const SecVie
         const int st_row = sv.stab[row];
         dfl e = {L.c0f, L.c0lo}, dd = {0.f, 0.f};
         dfc acc = {{0.f, 0.f}, {0.f, 0.f}}, acch = {{0.f, 0.f}, {0.f, 0.f}};
+        // one hop's term: bond q, target translation u, |Stab| st, phi at the target
+        auto add_hop = [&](int q, int u, int st, float4 xv) {
+            float4 p = ph[u];
+            if (uni) {
+                // uniform J^xy: the amplitude multiplies the row's hop sum once
+                if (st != st_row) {
+                    const float2 r = srt[st * 9 + st_row];
+                    p = dfc_scale(p, {r.x, r.y});
+                }
+                dfc_mac(acch, p, xv);
+            } else {
+                dfl w = {__ldg(L.adj_jxy_f + q), __ldg(L.adj_jxy_lo + q)};
+                if (st != st_row) {
+                    const float2 r = srt[st * 9 + st_row];
+                    w = df_mul(w, {r.x, r.y});
+                }
+                dfc_mac(acc, dfc_scale(p, w), xv);
+            }
+        };
 #pragma unroll 1
         for (int m = 0; m < ND; ++m) {
             const int i = pick(c, m);
             e = df_sum(e, {__ldg(L.u_f + i), __ldg(L.u_lo + i)});
             const int e0 = __ldg(L.adj_ptr + i), e1 = __ldg(L.adj_ptr + i + 1);
-            for (int q = e0; q < e1; ++q) {
+            int qs = e0;
+            if constexpr (TB && DEGB > 0) {
+                uint32_t key[DEGB];
+#pragma unroll
+                for (int b = 0; b < DEGB; ++b) {
+                    const int q = e0 + b;
+                    key[b] = 0xffffffffu;
+                    if (q < e1) {
+                        const int j = __ldg(L.adj_nbr + q);
+                        bool occ = false;
+#pragma unroll
+                        for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
+                        if (occ) {
+                            dd = df_sum(dd, {__ldg(L.adj_jz_f + q), __ldg(L.adj_jz_lo + q)});
+                        } else {
+                            int tt[ND];
+#pragma unroll
+                            for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
+                            sort_net(tt);
+                            key[b] = (uint32_t)rank_of(tt, sm.sC, L.np1);   // table ranks are below 2^32
+                        }
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < DEGB; ++b)
+                    if (key[b] != 0xffffffffu) key[b] = __ldg(L.orb + key[b]);
+                int32_t row2[DEGB];
+#pragma unroll
+                for (int b = 0; b < DEGB; ++b)
+                    row2[b] = (key[b] != 0xffffffffu && (key[b] >> 12) < L.n_orb) ? __ldg(sv.t2 + (key[b] >> 12)) : -1;
+                float4 xv[DEGB];
+                int stv[DEGB];
+#pragma unroll
+                for (int b = 0; b < DEGB; ++b)
+                    if (row2[b] >= 0) {
+                        xv[b] = ph_in[row2[b]];
+                        stv[b] = __ldg(sv.stab + row2[b]);
+                    }
+#pragma unroll
+                for (int b = 0; b < DEGB; ++b)
+                    if (row2[b] >= 0) add_hop(e0 + b, (int)(key[b] & 4095u), stv[b], xv[b]);
+                qs = e0 + DEGB;
+            }
+            for (int q = qs; q < e1; ++q) {
                 const int j = __ldg(L.adj_nbr + q);
                 bool occ = false;
 #pragma unroll
@@ -120,24 +185,7 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi_df(LatView L, const SecVie
                     if (!sigma_find(sv, prefix_of(rep, sm.sC, L.np1), r2, idx)) continue;
                     u = ax + L.L[0] * (by + L.L[1] * cz);
                 }
-                float4 p = ph[u];
-                const int st = __ldg(sv.stab + idx);
-                const float4 xv = ph_in[idx];
-                if (uni) {
-                    // uniform J^xy: the amplitude multiplies the row's hop sum once
-                    if (st != st_row) {
-                        const float2 r = srt[st * 9 + st_row];
-                        p = dfc_scale(p, {r.x, r.y});
-                    }
-                    dfc_mac(acch, p, xv);
-                } else {
-                    dfl w = {__ldg(L.adj_jxy_f + q), __ldg(L.adj_jxy_lo + q)};
-                    if (st != st_row) {
-                        const float2 r = srt[st * 9 + st_row];
-                        w = df_mul(w, {r.x, r.y});
-                    }
-                    dfc_mac(acc, dfc_scale(p, w), xv);
-                }
+                add_hop(q, u, __ldg(sv.stab + idx), ph_in[idx]);
             }
         }
         if (uni) {
@@ -170,16 +218,17 @@ __global__ void k_split_df(const double2 *__restrict__ x, float4 *__restrict__ y
         y[i] = split2(x[i]);
 }
 
-template <int ND, bool TB, bool ODF>
+template <int ND, bool TB, bool ODF, int DEGB>
 static int hphi_df_ndt(Basis &B, const float4 *phi, const int *dx, uint64_t ld, void *psi, cudaStream_t st,
                        const int *active) {
     static std::atomic<unsigned long long> cache{0};
     int grid = 1, occ = 1;
-    QS3_TRY(launch_rows(k_hphi_df<ND, TB, ODF>, B, B.smem_bytes, cache, &grid, &occ));
+    QS3_TRY(launch_rows(k_hphi_df<ND, TB, ODF, DEGB>, B, B.smem_bytes, cache, &grid, &occ));
     if (B.ntiles == 0) return QS3_OK;
     auto launch = [&](int g) {
-        k_hphi_df<ND, TB, ODF><<<g, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(),
-                                                                    B.S, B.ntiles, phi, psi, active, dx, ld);
+        k_hphi_df<ND, TB, ODF, DEGB><<<g, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(),
+                                                                          B.d_tile0.as<int>(), B.S, B.ntiles, phi, psi,
+                                                                          active, dx, ld);
     };
     int &bps = B.tune_hphi[QS3_C128DF];
     if (bps == 0) {
@@ -200,11 +249,16 @@ static int hphi_df_ndt(Basis &B, const float4 *phi, const int *dx, uint64_t ld, 
 template <int ND>
 static int hphi_df_nd(Basis &B, const float4 *phi, const int *dx, uint64_t ld, void *psi, bool out_df,
                       cudaStream_t st, const int *active) {
-    if (out_df)
-        return B.lv.orb ? hphi_df_ndt<ND, true, true>(B, phi, dx, ld, psi, st, active)
-                        : hphi_df_ndt<ND, false, true>(B, phi, dx, ld, psi, st, active);
-    return B.lv.orb ? hphi_df_ndt<ND, true, false>(B, phi, dx, ld, psi, st, active)
-                    : hphi_df_ndt<ND, false, false>(B, phi, dx, ld, psi, st, active);
+    // table: hops staged DEGB = 4 (square, chain) or 6 (cubic, triangular) at a time
+    if (B.lv.orb) {
+        if (B.max_degree <= 4)
+            return out_df ? hphi_df_ndt<ND, true, true, 4>(B, phi, dx, ld, psi, st, active)
+                          : hphi_df_ndt<ND, true, false, 4>(B, phi, dx, ld, psi, st, active);
+        return out_df ? hphi_df_ndt<ND, true, true, 6>(B, phi, dx, ld, psi, st, active)
+                      : hphi_df_ndt<ND, true, false, 6>(B, phi, dx, ld, psi, st, active);
+    }
+    return out_df ? hphi_df_ndt<ND, false, true, 0>(B, phi, dx, ld, psi, st, active)
+                  : hphi_df_ndt<ND, false, false, 0>(B, phi, dx, ld, psi, st, active);
 }
 
 int hphi_df_launch(Basis &B, const void *phi, const int *dx, uint64_t ld, void *psi, cudaStream_t st,

@@ -526,10 +526,29 @@ template <typename VT> struct DfS { using T = VT; };     // fp32 vectors: stored
 template <> struct DfS<double> { using T = float2; };    // (hi, lo)
 template <> struct DfS<double2> { using T = float4; };   // (re.hi, re.lo, im.hi, im.lo)
 
-__device__ __forceinline__ float4 ld_df(const float2 *p) { const float2 v = *p; return make_float4(v.x, v.y, 0.f, 0.f); }
-__device__ __forceinline__ float4 ld_df(const float4 *p) { return *p; }
-__device__ __forceinline__ void st_df(float2 *p, float4 v) { *p = make_float2(v.x, v.y); }
-__device__ __forceinline__ void st_df(float4 *p, float4 v) { *p = v; }
+// Layout of a stored vector (a slot of D elements).  Real: (hi, lo) pairs.
+// Complex: two planes, the D hi pairs (re.hi, im.hi) then the D lo pairs
+// (re.lo, im.lo), so a pass that needs only the hi words (the update with
+// O(eps) coefficients) reads half the bytes.  Values are handed around as
+// float4 (re.hi, re.lo, im.hi, im.lo).
+__device__ __forceinline__ float4 ld_st(const float2 *slot, uint64_t, uint64_t r) {
+    const float2 v = slot[r];
+    return make_float4(v.x, v.y, 0.f, 0.f);
+}
+__device__ __forceinline__ float4 ld_st(const float4 *slot, uint64_t D, uint64_t r) {
+    const float2 *h = (const float2 *)slot;
+    const float2 a = h[r], b = h[D + r];
+    return make_float4(a.x, b.x, a.y, b.y);
+}
+// the hi words only: (re.hi, im.hi)
+__device__ __forceinline__ float2 ld_st_hi(const float2 *slot, uint64_t, uint64_t r) { return make_float2(slot[r].x, 0.f); }
+__device__ __forceinline__ float2 ld_st_hi(const float4 *slot, uint64_t, uint64_t r) { return ((const float2 *)slot)[r]; }
+__device__ __forceinline__ void st_st(float2 *slot, uint64_t, uint64_t r, float4 v) { slot[r] = make_float2(v.x, v.y); }
+__device__ __forceinline__ void st_st(float4 *slot, uint64_t D, uint64_t r, float4 v) {
+    float2 *h = (float2 *)slot;
+    h[r] = make_float2(v.x, v.z);
+    h[D + r] = make_float2(v.y, v.w);
+}
 // the working vector w of a Gram-Schmidt pass: fp64 (split on load) or
 // already double-float (the double-float engine of complex k-sector solves)
 __device__ __forceinline__ float4 ld_w(const double *p) { return split2(ld2(p)); }
@@ -579,13 +598,13 @@ __global__ void __launch_bounds__(NTHREADS, NV == 2 ? 3 : 1) k_mdot_df(const typ
     for (int jb = 0; jb < m; jb += GDF) {
         const int nj = min(GDF, m - jb);
         for (int jj = 0; jj < nj; jj += NV) {
-            const ST *vb = V + (uint64_t)(j0 + jb + jj) * D + ci.base;
+            const ST *vb = V + (uint64_t)(j0 + jb + jj) * D;
             float4 a[NV][RPT];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 const ST *vv = (jj + v < nj) ? vb + (uint64_t)v * D : vb;   // past the group: a repeat, discarded
 #pragma unroll
-                for (int k = 0; k < RPT; ++k) a[v][k] = ld_df(vv + ro[k]);
+                for (int k = 0; k < RPT; ++k) a[v][k] = ld_st(vv, D, ci.base + ro[k]);
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -702,17 +721,17 @@ __global__ void __launch_bounds__(NTHREADS) k_mupdate_df(WV *__restrict__ w, con
         for (int k = 0; k < RPT; ++k) uf[k] = make_float2(0.f, 0.f);
         for (int j = 0; j < m; ++j) {
             const float4 c = scf[j];
-            const ST *vj = V + (uint64_t)(j0 + j) * D + ci.base;
+            const ST *vj = V + (uint64_t)(j0 + j) * D;
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 const int r = threadIdx.x + k * NTHREADS;
                 if (r < ci.n) {
-                    const float4 a = ld_df(vj + r);
+                    const float2 a = ld_st_hi(vj, D, ci.base + r);     // (re.hi, im.hi)
                     uf[k].x = fmaf(a.x, c.x, uf[k].x);
                     if (IsC<VT>::v) {
-                        uf[k].x = fmaf(-a.z, c.z, uf[k].x);
+                        uf[k].x = fmaf(-a.y, c.z, uf[k].x);
                         uf[k].y = fmaf(a.x, c.z, uf[k].y);
-                        uf[k].y = fmaf(a.z, c.x, uf[k].y);
+                        uf[k].y = fmaf(a.y, c.x, uf[k].y);
                     }
                 }
             }
@@ -725,12 +744,12 @@ __global__ void __launch_bounds__(NTHREADS) k_mupdate_df(WV *__restrict__ w, con
     } else {
         for (int j = 0; j < m; ++j) {
             const float4 c = scf[j];
-            const ST *vj = V + (uint64_t)(j0 + j) * D + ci.base;
+            const ST *vj = V + (uint64_t)(j0 + j) * D;
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 const int r = threadIdx.x + k * NTHREADS;
                 if (r < ci.n) {
-                    const float4 a = ld_df(vj + r);
+                    const float4 a = ld_st(vj, D, ci.base + r);
                     // u += a c: re += a.r c.r - a.i c.i ; im += a.r c.i + a.i c.r
                     df_mac(ur[k], a.x, a.y, c.x, c.y);
                     if (IsC<VT>::v) {
@@ -786,13 +805,16 @@ __global__ void __launch_bounds__(NTHREADS) k_mupdate_df(WV *__restrict__ w, con
 }
 
 // w *= inv[s]; out = double-float copy of the scaled w
+// (and, when hin is given, an interleaved double-float copy: the input of the
+// double-float H Phi); D = the store's slot length
 template <typename VT>
 __global__ void __launch_bounds__(NTHREADS) k_scale_split(VT *__restrict__ w, typename DfS<VT>::T *__restrict__ out,
                                                           const double *__restrict__ inv,
                                                           const SecView *__restrict__ secs,
                                                           const int *__restrict__ chunk0, int S,
                                                           const int *__restrict__ active,
-                                                          const int *__restrict__ dx = nullptr, uint64_t D = 0) {
+                                                          const int *__restrict__ dx, uint64_t D,
+                                                          float4 *__restrict__ hin = nullptr) {
     if (dx) out += (uint64_t)(*dx + 1) * D;     // graph mode: out is the store's base, vector x + 1
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
     if (active && !active[ci.s]) return;
@@ -805,18 +827,21 @@ __global__ void __launch_bounds__(NTHREADS) k_scale_split(VT *__restrict__ w, ty
             v.x *= f;
             v.y *= f;
             st2(w + ci.base + r, v);
-            st_df(out + ci.base + r, split2(v));
+            const float4 q = split2(v);
+            st_st(out, D, ci.base + r, q);
+            if (hin) hin[ci.base + r] = q;
         }
     }
 }
 
 // double-float engine: basis vector x + 1 = w * inv[s], all in double-float
+// (the store's slot x + 1, and hin, the interleaved input of the next H Phi)
 __global__ void __launch_bounds__(NTHREADS) k_scale_df(const float4 *__restrict__ w, float4 *__restrict__ out,
-                                                       const double *__restrict__ inv,
+                                                       float4 *__restrict__ hin, const double *__restrict__ inv,
                                                        const SecView *__restrict__ secs,
                                                        const int *__restrict__ chunk0, int S,
                                                        const int *__restrict__ active,
-                                                       const int *__restrict__ dx = nullptr, uint64_t D = 0) {
+                                                       const int *__restrict__ dx, uint64_t D) {
     if (dx) out += (uint64_t)(*dx + 1) * D;     // graph mode: out is the store's base, vector x + 1
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
     if (active && !active[ci.s]) return;
@@ -828,20 +853,28 @@ __global__ void __launch_bounds__(NTHREADS) k_scale_df(const float4 *__restrict_
         if (r < ci.n) {
             const float4 v = w[ci.base + r];
             const dfl re = df_mul({v.x, v.y}, f), im = df_mul({v.z, v.w}, f);
-            out[ci.base + r] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            const float4 q = make_float4(re.hi, re.lo, im.hi, im.lo);
+            st_st(out, D, ci.base + r, q);
+            hin[ci.base + r] = q;
         }
     }
 }
 
-__device__ __forceinline__ void st_comb(double *p, dfl re, dfl) { *p = (double)re.hi + (double)re.lo; }
-__device__ __forceinline__ void st_comb(double2 *p, dfl re, dfl im) {
-    *p = make_double2((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
+// element r of an output vector starting at p (slot length D for the store)
+__device__ __forceinline__ void st_comb(double *p, uint64_t, uint64_t r, dfl re, dfl) {
+    p[r] = (double)re.hi + (double)re.lo;
 }
-__device__ __forceinline__ void st_comb(float2 *p, dfl re, dfl) { re = df_norm(re); *p = make_float2(re.hi, re.lo); }
-__device__ __forceinline__ void st_comb(float4 *p, dfl re, dfl im) {
+__device__ __forceinline__ void st_comb(double2 *p, uint64_t, uint64_t r, dfl re, dfl im) {
+    p[r] = make_double2((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
+}
+__device__ __forceinline__ void st_comb(float2 *p, uint64_t D, uint64_t r, dfl re, dfl) {
+    re = df_norm(re);
+    st_st(p, D, r, make_float4(re.hi, re.lo, 0.f, 0.f));
+}
+__device__ __forceinline__ void st_comb(float4 *p, uint64_t D, uint64_t r, dfl re, dfl im) {
     re = df_norm(re);
     im = df_norm(im);
-    *p = make_float4(re.hi, re.lo, im.hi, im.lo);
+    st_st(p, D, r, make_float4(re.hi, re.lo, im.hi, im.lo));
 }
 
 // out_y[r] = sum_x V_x[r] C[s][x][y] (y < nout <= 16) over a double-float
@@ -876,7 +909,7 @@ __global__ void __launch_bounds__(NTHREADS) k_combine_df(OT *__restrict__ out, u
         for (int y = 0; y < MAXOUT; ++y) re[y] = im[y] = {0.f, 0.f};
 #pragma unroll 4
         for (int x = 0; x < nin; ++x) {
-            const float4 a = ld_df(V + (uint64_t)x * D + ci.base + r);
+            const float4 a = ld_st(V + (uint64_t)x * D, D, ci.base + r);
 #pragma unroll
             for (int y = 0; y < MAXOUT; ++y)
                 if (y < nout) {
@@ -887,7 +920,7 @@ __global__ void __launch_bounds__(NTHREADS) k_combine_df(OT *__restrict__ out, u
         }
 #pragma unroll
         for (int y = 0; y < MAXOUT; ++y)
-            if (y < nout) st_comb(out + (uint64_t)y * ldo + ci.base + r, re[y], im[y]);
+            if (y < nout) st_comb(out + (uint64_t)y * ldo, ldo, ci.base + r, re[y], im[y]);
     }
 }
 
@@ -1074,9 +1107,15 @@ struct HphiStats {
     double sec = 0.0;
     int calls = 0;
     int graph_calls = 0;                  // calls replayed inside CUDA graphs (not in sec)
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend, freel;
+    // the Gram-Schmidt dot-product pass (outside graphs): device time, launches,
+    // algorithmic bytes (stored vectors read + w read)
+    double gs_sec = 0.0;
+    int gs_calls = 0;
+    uint64_t gs_bytes = 0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend, pend_gs, freel;
     ~HphiStats() {
         for (auto &p : pend) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
+        for (auto &p : pend_gs) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
         for (auto &p : freel) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
     }
     int pair(std::pair<cudaEvent_t, cudaEvent_t> &p) {
@@ -1094,6 +1133,13 @@ struct HphiStats {
             freel.push_back(p);
         }
         pend.clear();
+        for (auto &p : pend_gs) {
+            float ms = 0.f;
+            QS3_CUDA(cudaEventElapsedTime(&ms, p.first, p.second));
+            gs_sec += 1e-3 * ms;
+            freel.push_back(p);
+        }
+        pend_gs.clear();
         return QS3_OK;
     }
 };
@@ -1135,8 +1181,9 @@ struct Engine {
     // psi_{x+1} all stay in double-float (float4 per element, wdf) on the
     // fp32 units; the fp64 ring then only carries the start vector
     bool dfh = false;
-    DevBuf wdf;
+    DevBuf wdf, hdf;                      // w, and the interleaved copy of psi_x that H reads
     float4 *wd() { return wdf.as<float4>(); }
+    float4 *hd() { return hdf.as<float4>(); }
     void use_df_hphi(bool on) { dfh = on && DF && IsC<VT>::v && B.has_k && B.nd > 0; }
     // replay Lanczos steps as CUDA graphs (fp64 engine; ignored otherwise)
     int enable_graphs(bool on) {
@@ -1172,6 +1219,7 @@ struct Engine {
         if (DF) QS3_TRY(ring.alloc(3 * D * sizeof(VT)));
         if (dfh) {
             QS3_TRY(wdf.alloc(D * sizeof(float4)));
+            QS3_TRY(hdf.alloc(D * sizeof(float4)));
             QS3_CUDA(cudaMemsetAsync(wdf.p, 0, wdf.n, st));
         }
         QS3_TRY(part.alloc((uint64_t)std::max(B.nchunks, 1) * cap * sizeof(double2)));
@@ -1318,7 +1366,8 @@ struct Engine {
     int scale_store(VT *w, int j) {
         if (B.nchunks == 0) return QS3_OK;
         if constexpr (DF)
-            k_scale_split<VT><<<grid(), NTHREADS, 0, st>>>(w, svec(j), inv.as<double>(), secs(), c0(), B.S, act());
+            k_scale_split<VT><<<grid(), NTHREADS, 0, st>>>(w, svec(j), inv.as<double>(), secs(), c0(), B.S, act(),
+                                                           nullptr, D, dfh ? hd() : nullptr);
         else
             k_scale<VT><<<grid(), NTHREADS, 0, st>>>(w, inv.as<double>(), secs(), c0(), B.S, act());
         QS3_LAUNCHED();
@@ -1354,10 +1403,7 @@ struct Engine {
             if (dfh) return step_body_dev_df(dx);
         }
         VT *w = rvec(rw);
-        if (dfh)
-            QS3_TRY(hphi_df_launch(B, V.p, dx, D, w, st, act()));
-        else
-            QS3_TRY(hphi_launch(B, dtype(), rvec(rc), w, st, act()));
+        QS3_TRY(hphi_launch(B, dtype(), rvec(rc), w, st, act()));
         const int64_t ld = (int64_t)(rvec(rc) - rvec(rp));
         double2 *hh1 = h1.as<double2>(), *n1 = nrm1.as<double2>();
         if constexpr (DF) {
@@ -1398,7 +1444,7 @@ struct Engine {
         float4 *w = wd();
         const ST *v = V.as<ST>();
         double2 *hh1 = h1.as<double2>(), *n1 = nrm1.as<double2>();
-        QS3_TRY(hphi_df_launch(B, V.p, dx, D, w, st, act(), true));
+        QS3_TRY(hphi_df_launch(B, hd(), nullptr, 0, w, st, act(), true));
         // three-term part against psi_{x-1}, psi_x
         QS3_TRY(mdot_df(B.tune_nv, 0, 2, (const float4 *)w, dx, 1));
         k_reduce_df<<<dim3(2, B.S), NTHREADS, 0, st>>>((const float4 *)part.p, 2, c0(), act(), hh1, cap, dx, 1);
@@ -1423,7 +1469,8 @@ struct Engine {
         k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, 0, cap, hh1, nrm.as<double2>(), act(), alpha.as<double>(),
                                                          beta.as<double>(), inv.as<double>(), brk, dx);
         QS3_LAUNCHED();
-        k_scale_df<<<grid(), NTHREADS, 0, st>>>(w, V.as<float4>(), inv.as<double>(), secs(), c0(), B.S, act(), dx, D);
+        k_scale_df<<<grid(), NTHREADS, 0, st>>>(w, V.as<float4>(), hd(), inv.as<double>(), secs(), c0(), B.S, act(),
+                                                dx, D);
         QS3_LAUNCHED();
         k_advance<<<1, 1, 0, st>>>(xdev.as<int>());
         QS3_LAUNCHED();
@@ -1497,10 +1544,7 @@ struct Engine {
         std::pair<cudaEvent_t, cudaEvent_t> ev;
         QS3_TRY(stats->pair(ev));
         QS3_CUDA(cudaEventRecord(ev.first, st));
-        if (dfh)
-            QS3_TRY(hphi_df_launch(B, svec(x), nullptr, 0, w, st, act()));
-        else
-            QS3_TRY(hphi_launch(B, dtype(), hin(x), w, st, act()));
+        QS3_TRY(hphi_launch(B, dtype(), hin(x), w, st, act()));
         QS3_CUDA(cudaEventRecord(ev.second, st));
         stats->pend.push_back(ev);
         stats->calls += 1;
@@ -1514,7 +1558,7 @@ struct Engine {
             QS3_TRY(mdot(j0, x + 1 - j0, w, h1.as<double2>() + j0, cap));
             QS3_TRY(mupdate(w, j0, x + 1 - j0, h1.as<double2>() + j0, cap, n1));
         }
-        QS3_TRY(mdot(0, x + 1, w, h2.as<double2>(), cap));
+        QS3_TRY(gs_dots(x, (const VT *)w, h2.as<double2>()));
         QS3_TRY(mupdate(w, 0, x + 1, h2.as<double2>(), cap, nrm.as<double2>(), n1));
         k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, x, cap, h1.as<double2>(), nrm.as<double2>(), act(),
                                                          alpha.as<double>(), beta.as<double>(), inv.as<double>(), brk);
@@ -1534,7 +1578,7 @@ struct Engine {
         std::pair<cudaEvent_t, cudaEvent_t> ev;
         QS3_TRY(stats->pair(ev));
         QS3_CUDA(cudaEventRecord(ev.first, st));
-        QS3_TRY(hphi_df_launch(B, svec(x), nullptr, 0, w, st, act(), true));
+        QS3_TRY(hphi_df_launch(B, hd(), nullptr, 0, w, st, act(), true));
         QS3_CUDA(cudaEventRecord(ev.second, st));
         stats->pend.push_back(ev);
         stats->calls += 1;
@@ -1545,17 +1589,34 @@ struct Engine {
         double2 *n1 = nrm1.as<double2>();
         QS3_TRY(mdot(j0, x + 1 - j0, (const float4 *)w, h1.as<double2>() + j0, cap));
         QS3_TRY(mupdate(w, j0, x + 1 - j0, h1.as<double2>() + j0, cap, n1));
-        QS3_TRY(mdot(0, x + 1, (const float4 *)w, h2.as<double2>(), cap));
+        QS3_TRY(gs_dots(x, (const float4 *)w, h2.as<double2>()));
         QS3_TRY(mupdate(w, 0, x + 1, h2.as<double2>(), cap, nrm.as<double2>(), n1));
         k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, x, cap, h1.as<double2>(), nrm.as<double2>(), act(),
                                                          alpha.as<double>(), beta.as<double>(), inv.as<double>(), brk);
         QS3_LAUNCHED();
         if constexpr (std::is_same<ST, float4>::value) {
             if (B.nchunks > 0) {
-                k_scale_df<<<grid(), NTHREADS, 0, st>>>(w, svec(x + 1), inv.as<double>(), secs(), c0(), B.S, act());
+                k_scale_df<<<grid(), NTHREADS, 0, st>>>(w, svec(x + 1), hd(), inv.as<double>(), secs(), c0(), B.S,
+                                                        act(), nullptr, D);
                 QS3_LAUNCHED();
             }
         }
+        return QS3_OK;
+    }
+    // the Gram-Schmidt dot pass against psi_0 .. psi_x, timed with events
+    template <typename WV>
+    int gs_dots(int x, const WV *w, double2 *out) {
+        std::pair<cudaEvent_t, cudaEvent_t> ev;
+        QS3_TRY(stats->pair(ev));
+        QS3_CUDA(cudaEventRecord(ev.first, st));
+        QS3_TRY(mdot(0, x + 1, w, out, cap));
+        QS3_CUDA(cudaEventRecord(ev.second, st));
+        stats->pend_gs.push_back(ev);
+        stats->gs_calls += 1;
+        uint64_t rows = 0;
+        for (int s = 0; s < B.S; ++s)
+            if (h_active[s]) rows += B.dims[s];
+        stats->gs_bytes += rows * ((uint64_t)(x + 1) * sizeof(ST) + sizeof(WV));
         return QS3_OK;
     }
     int fetch(std::vector<double> &a, std::vector<double> &b) {
@@ -1928,6 +1989,9 @@ static int lanczos_entry(Basis &B, const qs3_solve_opts &o, double *evals, void 
         info->hphi_seconds = hs.sec;
         info->hphi_calls = hs.calls;
         info->hphi_graph_calls = hs.graph_calls;
+        info->gs_dot_seconds = hs.gs_sec;
+        info->gs_dot_bytes = hs.gs_bytes;
+        info->gs_dot_calls = hs.gs_calls;
     }
     return all_conv(R.conv) ? QS3_OK : set_err(QS3_ERR_NOT_CONVERGED, "Lanczos did not converge in %d steps", o.n_max);
 }
@@ -2021,6 +2085,9 @@ static int trl_entry(Basis &B, const qs3_solve_opts &o, double *evals, void *eve
         info->hphi_seconds = hs.sec;
         info->hphi_calls = hs.calls;
         info->hphi_graph_calls = hs.graph_calls;
+        info->gs_dot_seconds = hs.gs_sec;
+        info->gs_dot_bytes = hs.gs_bytes;
+        info->gs_dot_calls = hs.gs_calls;
     }
     return all_conv(R.conv) ? QS3_OK
                             : set_err(QS3_ERR_NOT_CONVERGED, "thick-restart Lanczos did not converge in %d restarts",
