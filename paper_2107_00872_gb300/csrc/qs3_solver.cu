@@ -255,56 +255,6 @@ template <> struct F32c<float2> { static constexpr bool v = true; };
 __device__ __forceinline__ float2 ldf(const float *p) { return make_float2(*p, 0.f); }
 __device__ __forceinline__ float2 ldf(const float2 *p) { return *p; }
 
-// part[c * m + j] = conj(V_{j0+j}) . w over the chunk, double-float per thread
-template <typename VT>
-__global__ void __launch_bounds__(NTHREADS) k_mdot32(const VT *__restrict__ V, uint64_t D, int j0, int m,
-                                                     const VT *__restrict__ w, const SecView *__restrict__ secs,
-                                                     const int *__restrict__ chunk0, int S,
-                                                     const int *__restrict__ active, double2 *__restrict__ part) {
-    __shared__ double2 red[NTHREADS / 32][JB];
-    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
-    if (active && !active[ci.s]) return;
-    float2 wv[RPT];
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int r = threadIdx.x + k * NTHREADS;
-        wv[k] = (r < ci.n) ? ldf(w + ci.base + r) : make_float2(0.f, 0.f);
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int jb = 0; jb < m; jb += JB) {
-        const int nj = min(JB, m - jb);
-        for (int jj = 0; jj < nj; ++jj) {
-            const VT *vj = V + (uint64_t)(j0 + jb + jj) * D + ci.base;
-            dfl re = {0.f, 0.f}, im = {0.f, 0.f};
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const int r = threadIdx.x + k * NTHREADS;
-                if (r < ci.n) {
-                    const float2 a = ldf(vj + r), b = wv[k];
-                    // conj(a) b = (a.x b.x + a.y b.y) + i (a.x b.y - a.y b.x)
-                    re = df_fma(re, a.x, b.x);
-                    if (F32c<VT>::v) {
-                        re = df_fma(re, a.y, b.y);
-                        im = df_fma(im, a.x, b.y);
-                        im = df_fma(im, -a.y, b.x);
-                    }
-                }
-            }
-            double2 acc = make_double2(df_d(re), df_d(im));
-            acc = warp_sum2(acc);
-            if (lane == 0) red[warp][jj] = acc;
-        }
-        __syncthreads();
-        if (threadIdx.x < nj) {
-            double2 t = make_double2(0.0, 0.0);
-#pragma unroll
-            for (int q = 0; q < NTHREADS / 32; ++q) { t.x += red[q][threadIdx.x].x; t.y += red[q][threadIdx.x].y; }
-            part[(uint64_t)blockIdx.x * m + jb + threadIdx.x] = t;
-        }
-        __syncthreads();
-    }
-}
-
 // w -= sum_j V_{j0+j} coef[s][j] in double-float, rounded once to fp32;
 // optionally part[c] = sum |w|^2 over the chunk
 template <typename VT>
@@ -554,6 +504,9 @@ __device__ __forceinline__ void st_st(float4 *slot, uint64_t D, uint64_t r, floa
 __device__ __forceinline__ float4 ld_w(const double *p) { return split2(ld2(p)); }
 __device__ __forceinline__ float4 ld_w(const double2 *p) { return split2(ld2(p)); }
 __device__ __forceinline__ float4 ld_w(const float4 *p) { return *p; }
+// fp32 vectors (the fp32 engine) are double-float values with lo = 0
+__device__ __forceinline__ float4 ld_w(const float *p) { return make_float4(*p, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ float4 ld_w(const float2 *p) { const float2 v = *p; return make_float4(v.x, 0.f, v.y, 0.f); }
 // graph mode (dx): the three-term pass takes vectors x - 1, x (m = 2, x >= 1),
 // the full pass vectors 0 .. x
 __device__ __forceinline__ void graph_range(const int *dx, int ring, int &j0, int &m) {
@@ -604,7 +557,10 @@ __global__ void __launch_bounds__(NTHREADS, NV == 2 ? 3 : 1) k_mdot_df(const typ
             for (int v = 0; v < NV; ++v) {
                 const ST *vv = (jj + v < nj) ? vb + (uint64_t)v * D : vb;   // past the group: a repeat, discarded
 #pragma unroll
-                for (int k = 0; k < RPT; ++k) a[v][k] = ld_st(vv, D, ci.base + ro[k]);
+                for (int k = 0; k < RPT; ++k) {
+                    if constexpr (Is64<VT>::v) a[v][k] = ld_st(vv, D, ci.base + ro[k]);
+                    else a[v][k] = ld_w(vv + ci.base + ro[k]);      // fp32 store: lo = 0
+                }
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
@@ -921,6 +877,57 @@ __global__ void __launch_bounds__(NTHREADS) k_combine_df(OT *__restrict__ out, u
 #pragma unroll
         for (int y = 0; y < MAXOUT; ++y)
             if (y < nout) st_comb(out + (uint64_t)y * ldo, ldo, ci.base + r, re[y], im[y]);
+    }
+}
+
+// one output vector (nout = 1, the Lanczos Ritz vector): out[r] = sum_x V_x[r]
+// C[s][x], double-float accumulation, each thread's RPT rows in registers so
+// every pass over a stored vector has all of a thread's loads in flight.
+// DFS: the store is double-float (slots of D elements, see ld_st); else the
+// fp32 vectors of the fp32 engine.
+__device__ __forceinline__ float4 ld_comb(const float *p) { return make_float4(*p, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ float4 ld_comb(const float2 *p) { const float2 v = *p; return make_float4(v.x, 0.f, v.y, 0.f); }
+template <typename VT, typename SV, typename OT, bool DFS>
+__global__ void __launch_bounds__(NTHREADS) k_combine1(OT *__restrict__ out, uint64_t ldo, const SV *__restrict__ V,
+                                                       uint64_t D, int nin, const double *__restrict__ C, int ldc,
+                                                       const SecView *__restrict__ secs,
+                                                       const int *__restrict__ chunk0, int S,
+                                                       const int *__restrict__ mask) {
+    extern __shared__ float2 scc[];
+    __shared__ int nx;
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (mask && !mask[ci.s]) return;
+    const double *Cs = C + (uint64_t)ci.s * ldc;
+    if (threadIdx.x == 0) nx = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nin; i += blockDim.x) {
+        scc[i] = split_d(Cs[i]);
+        if (Cs[i] != 0.0) atomicMax(&nx, i + 1);
+    }
+    __syncthreads();
+    nin = nx;      // vectors past the sector's last nonzero coefficient may be unwritten
+    dfl re[RPT], im[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) re[k] = im[k] = {0.f, 0.f};
+    for (int x = 0; x < nin; ++x) {
+        const float2 c = scc[x];
+        const SV *slot = V + (uint64_t)x * D;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int r = threadIdx.x + k * NTHREADS;
+            if (r < ci.n) {
+                float4 a;
+                if constexpr (DFS) a = ld_st(slot, D, ci.base + r);
+                else a = ld_comb(slot + ci.base + r);
+                df_mac(re[k], a.x, a.y, c.x, c.y);
+                if (IsC<VT>::v) df_mac(im[k], a.z, a.w, c.x, c.y);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r < ci.n) st_comb(out, ldo, ci.base + r, re[k], im[k]);
     }
 }
 
@@ -1261,21 +1268,17 @@ struct Engine {
     template <typename WV>
     int mdot(int j0, int m, const WV *w, double2 *out, int ldo) {
         if (B.nchunks == 0) return QS3_OK;
-        if constexpr (DF)
-            QS3_TRY(mdot_df(B.tune_nv, j0, m, w, nullptr));
-        else
-            k_mdot32<VT><<<grid(), NTHREADS, 0, st>>>(V.as<VT>(), D, j0, m, (const VT *)w, secs(), c0(), B.S, act(),
-                                                      part.as<double2>());
-        QS3_LAUNCHED();
-        return reduce(m, out, ldo, DF);
+        QS3_TRY(mdot_df(B.tune_nv, j0, m, w, nullptr));
+        return reduce(m, out, ldo, true);
     }
     // k_mdot_df with nv basis vectors per pass (1, 2 or 4; other values: 2);
     // graph mode (dx): ring selects the three-term range (see graph_range)
     template <typename WV>
     int mdot_df(int nv, int j0, int m, const WV *w, const int *dx, int ring = 0) {
-        if constexpr (DF) {
+        {
             const ST *v = V.as<ST>();
             float4 *pp = (float4 *)part.p;
+            if (ring || (!dx && m <= 2)) nv = std::min(nv, 2);      // the three-term pass: 2 vectors
             if (nv == 1)
                 k_mdot_df<VT, 1, WV><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx, ring);
             else if (nv == 4)
@@ -1287,7 +1290,7 @@ struct Engine {
         return QS3_OK;
     }
     // autotuner for the staging depth of the dot products: time 1, 2 and 4
-    // vectors per pass on min(cap, 16) stored vectors (their contents do not
+    // vectors per pass on min(cap, 48) stored vectors (their contents do not
     // matter for the timing; the partial sums are discarded) and keep the
     // fastest for this basis
     int tune_dots() {
@@ -1296,7 +1299,7 @@ struct Engine {
             cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
             QS3_CUDA(cudaStreamIsCapturing(st, &cst));
             if (cst != cudaStreamCaptureStatusNone) return QS3_OK;
-            const int m = std::min(cap, 16);
+            const int m = std::min(cap, 48);
             cudaEvent_t e0, e1;
             QS3_CUDA(cudaEventCreate(&e0));
             QS3_CUDA(cudaEventCreate(&e1));
@@ -1305,7 +1308,7 @@ struct Engine {
             int rc2 = QS3_OK;
             for (int nv : {1, 2, 4}) {
                 float tmin = 1e30f;
-                for (int rep = 0; rep < 3 && rc2 == QS3_OK; ++rep) {
+                for (int rep = 0; rep < 4 && rc2 == QS3_OK; ++rep) {
                     if (cudaEventRecord(e0, st) != cudaSuccess) { rc2 = QS3_ERR_CUDA; break; }
                     rc2 = dfh ? mdot_df(nv, 0, m, (const float4 *)wd(), nullptr)
                               : mdot_df(nv, 0, m, (const VT *)rvec(rw), nullptr);
@@ -1639,7 +1642,14 @@ struct Engine {
         QS3_TRY(dm.alloc(mask.size() * 4));
         QS3_CUDA(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, st));
         QS3_CUDA(cudaMemcpyAsync(dm.p, mask.data(), mask.size() * 4, cudaMemcpyHostToDevice, st));
-        if constexpr (DF)
+        // one fp64 result, or one double-float stored vector
+        constexpr bool one_ok = DF || std::is_same<OT, WT>::value;
+        if (one_ok && nout == 1) {
+            if constexpr (one_ok)
+                k_combine1<VT, ST, OT, DF><<<grid(), NTHREADS, ldc * sizeof(float2), st>>>(out, ldo, V.as<ST>(), D, nin,
+                                                                                          dC.as<double>(), ldc, secs(),
+                                                                                          c0(), B.S, dm.as<int>());
+        } else if constexpr (DF)
             k_combine_df<VT, OT><<<grid(), NTHREADS, ldc * sizeof(float2), st>>>(out, ldo, V.as<ST>(), D, nin, nout,
                                                                                  dC.as<double>(), ldc, secs(), c0(),
                                                                                  B.S, dm.as<int>());
