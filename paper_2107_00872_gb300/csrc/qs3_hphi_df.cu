@@ -115,6 +115,10 @@ __global__ void __launch_bounds__(NTHREADS, DEGB == 4 ? 4 : 3) k_hphi_df(LatView
             const int e0 = __ldg(L.adj_ptr + i), e1 = __ldg(L.adj_ptr + i + 1);
             int qs = e0;
             if constexpr (TB && DEGB > 0) {
+                // neighbours of c_m in the sorted list: j keeps position m when
+                // lo < j < hi, and then only the m-th term of the rank changes
+                const int lo = m > 0 ? pick(c, m - 1) : -1, hi = m < ND - 1 ? pick(c, m + 1) : L.N;
+                const uint64_t rank_m = rank - sm.sC[(m + 1) * L.np1 + i];
                 uint32_t key[DEGB];
 #pragma unroll
                 for (int b = 0; b < DEGB; ++b) {
@@ -127,12 +131,14 @@ __global__ void __launch_bounds__(NTHREADS, DEGB == 4 ? 4 : 3) k_hphi_df(LatView
                         for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
                         if (occ) {
                             dd = df_sum(dd, {__ldg(L.adj_jz_f + q), __ldg(L.adj_jz_lo + q)});
+                        } else if (j > lo && j < hi) {
+                            key[b] = (uint32_t)(rank_m + sm.sC[(m + 1) * L.np1 + j]);   // table ranks are below 2^32
                         } else {
                             int tt[ND];
 #pragma unroll
                             for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
                             sort_net(tt);
-                            key[b] = (uint32_t)rank_of(tt, sm.sC, L.np1);   // table ranks are below 2^32
+                            key[b] = (uint32_t)rank_of(tt, sm.sC, L.np1);
                         }
                     }
                 }
