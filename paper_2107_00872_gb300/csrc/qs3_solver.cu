@@ -524,7 +524,7 @@ __device__ __forceinline__ void graph_range(const int *dx, int ring, int &j0, in
 // loads in flight together (the staging depth, chosen by the autotuner).
 constexpr int GDF = NTHREADS / 32;
 template <typename VT, int NV, typename WV = VT>
-__global__ void __launch_bounds__(NTHREADS, NV == 2 ? 3 : 1) k_mdot_df(const typename DfS<VT>::T *__restrict__ V, uint64_t D, int j0,
+__global__ void __launch_bounds__(NTHREADS, NV == 1 ? 4 : NV == 2 ? 2 : 1) k_mdot_df(const typename DfS<VT>::T *__restrict__ V, uint64_t D, int j0,
                                                       int m, const WV *__restrict__ w,
                                                       const SecView *__restrict__ secs,
                                                       const int *__restrict__ chunk0, int S,
@@ -536,18 +536,18 @@ __global__ void __launch_bounds__(NTHREADS, NV == 2 ? 3 : 1) k_mdot_df(const typ
     graph_range(dx, ring, j0, m);
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
     if (active && !active[ci.s]) return;
+    // w's rows stay in registers (NV > 1) or are re-read through L1 for each
+    // vector (NV = 1: fewer registers, more resident blocks)
     float4 wv[RPT];
 #pragma unroll
     for (int k = 0; k < RPT; ++k) {
         const int r = threadIdx.x + k * NTHREADS;
-        wv[k] = (r < ci.n) ? ld_w(w + ci.base + r) : make_float4(0.f, 0.f, 0.f, 0.f);
+        wv[k] = (NV > 1 && r < ci.n) ? ld_w(w + ci.base + r) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // rows past the chunk end read the chunk's last row (always written) and
-    // meet w = 0 there, so every load is unconditional
-    int ro[RPT];
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) ro[k] = min((int)threadIdx.x + k * NTHREADS, ci.n - 1);
+    // a thread's rows are threadIdx.x + k NTHREADS: one base pointer per
+    // vector and constant offsets (rows past the chunk end load zero)
+    const int nk = (ci.n - (int)threadIdx.x + NTHREADS - 1) / NTHREADS;     // rows of this thread
     for (int jb = 0; jb < m; jb += GDF) {
         const int nj = min(GDF, m - jb);
         for (int jj = 0; jj < nj; jj += NV) {
@@ -556,10 +556,14 @@ __global__ void __launch_bounds__(NTHREADS, NV == 2 ? 3 : 1) k_mdot_df(const typ
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 const ST *vv = (jj + v < nj) ? vb + (uint64_t)v * D : vb;   // past the group: a repeat, discarded
+                const uint64_t r0 = ci.base + threadIdx.x;
 #pragma unroll
                 for (int k = 0; k < RPT; ++k) {
-                    if constexpr (Is64<VT>::v) a[v][k] = ld_st(vv, D, ci.base + ro[k]);
-                    else a[v][k] = ld_w(vv + ci.base + ro[k]);      // fp32 store: lo = 0
+                    a[v][k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (k < nk) {
+                        if constexpr (Is64<VT>::v) a[v][k] = ld_st(vv, D, r0 + k * NTHREADS);
+                        else a[v][k] = ld_w(vv + r0 + k * NTHREADS);      // fp32 store: lo = 0
+                    }
                 }
             }
 #pragma unroll
@@ -567,7 +571,10 @@ __global__ void __launch_bounds__(NTHREADS, NV == 2 ? 3 : 1) k_mdot_df(const typ
                 dfl re = {0.f, 0.f}, im = {0.f, 0.f};
 #pragma unroll
                 for (int k = 0; k < RPT; ++k) {
-                    const float4 b = wv[k], x = a[v][k];
+                    float4 b = wv[k];
+                    if constexpr (NV == 1)
+                        if (k < nk) b = ld_w(w + ci.base + threadIdx.x + k * NTHREADS);
+                    const float4 x = a[v][k];
                     // conj(a) b = (a.r b.r + a.i b.i) + i (a.r b.i - a.i b.r)
                     df_mac(re, x.x, x.y, b.x, b.y);
                     if (IsC<VT>::v) {
