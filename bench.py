@@ -63,7 +63,7 @@ N_SMS = 152
 # of a run.  HPHI_PROFILE: one full launch of the double-float H Phi (all
 # sectors active): DRAM bytes and warp instructions executed.
 GS_PROFILE = {"kernel": "k_mdot_df<complex, double-float w> (Gram-Schmidt dot products)",
-              "dram_over_alg": 1.003, "profile": "profiles/k_mdot_df_k_mupdate_df_square10x10_nd4_40k.md"}
+              "dram_over_alg": 1.004, "profile": "profiles/k_mdot_df_k_mupdate_df_square10x10_nd4_40k.md"}
 HPHI_PROFILE = {
     "square10x10_nd4_all_k": {"kernel": "k_hphi_df<4, representative table> (double-float H Phi)",
                               "dram_bytes": None, "warp_inst": None,

@@ -682,6 +682,7 @@ __global__ void __launch_bounds__(NTHREADS) k_mupdate_df(WV *__restrict__ w, con
         float2 uf[RPT];
 #pragma unroll
         for (int k = 0; k < RPT; ++k) uf[k] = make_float2(0.f, 0.f);
+#pragma unroll 2
         for (int j = 0; j < m; ++j) {
             const float4 c = scf[j];
             const ST *vj = V + (uint64_t)(j0 + j) * D;
@@ -705,6 +706,7 @@ __global__ void __launch_bounds__(NTHREADS) k_mupdate_df(WV *__restrict__ w, con
             ui[k].hi = uf[k].y;
         }
     } else {
+#pragma unroll 2
         for (int j = 0; j < m; ++j) {
             const float4 c = scf[j];
             const ST *vj = V + (uint64_t)(j0 + j) * D;
