@@ -85,10 +85,11 @@ __global__ void __launch_bounds__(NTHREADS, DEGB == 4 ? 4 : 3) k_hphi_df(LatView
         int c[ND];
         unrank(rank, sm.sC, L.np1, c);
         const float4 *ph_in = phi + sv.off;
-        const float4 x0 = ph_in[row];
         const int st_row = sv.stab[row];
         dfl e = {L.c0f, L.c0lo}, dd = {0.f, 0.f};
-        dfc acc = {{0.f, 0.f}, {0.f, 0.f}}, acch = {{0.f, 0.f}, {0.f, 0.f}};
+        // the hop terms: phase x phi (uniform J^xy, multiplied in once at the
+        // end) or coupling x phase x phi
+        dfc acch = {{0.f, 0.f}, {0.f, 0.f}};
         // one hop's term: bond q, target translation u, |Stab| st, phi at the target
         auto add_hop = [&](int q, int u, int st, float4 xv) {
             float4 p = ph[u];
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(NTHREADS, DEGB == 4 ? 4 : 3) k_hphi_df(LatView
                     const float2 r = srt[st * 9 + st_row];
                     w = df_mul(w, {r.x, r.y});
                 }
-                dfc_mac(acc, dfc_scale(p, w), xv);
+                dfc_mac(acch, dfc_scale(p, w), xv);
             }
         };
 #pragma unroll 1
@@ -194,11 +195,14 @@ __global__ void __launch_bounds__(NTHREADS, DEGB == 4 ? 4 : 3) k_hphi_df(LatView
                 add_hop(q, u, __ldg(sv.stab + idx), ph_in[idx]);
             }
         }
+        dfc acc = acch;
         if (uni) {
             const dfl hr = df_norm(acch.re), hi = df_norm(acch.im);
+            acc = {{0.f, 0.f}, {0.f, 0.f}};
             df_mac(acc.re, juni.hi, juni.lo, hr.hi, hr.lo);
             df_mac(acc.im, juni.hi, juni.lo, hi.hi, hi.lo);
         }
+        const float4 x0 = ph_in[row];
         e = df_sum(e, {0.5f * dd.hi, 0.5f * dd.lo});
         df_mac(acc.re, e.hi, e.lo, x0.x, x0.y);
         df_mac(acc.im, e.hi, e.lo, x0.z, x0.w);
