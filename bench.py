@@ -61,12 +61,13 @@ N_SMS = 152
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) over the launch's
 # algorithmic bytes (stored vectors + w read); the ratio scales to the launches
 # of a run.  HPHI_PROFILE: one full launch of the double-float H Phi (all
-# sectors active): DRAM bytes and warp instructions executed.
+# sectors active): DRAM bytes and warp instructions executed, from a launch
+# over the first 40 momenta scaled by rows (x 2.5).
 GS_PROFILE = {"kernel": "k_mdot_df<complex, double-float w> (Gram-Schmidt dot products)",
               "dram_over_alg": 1.004, "profile": "profiles/k_mdot_df_k_mupdate_df_square10x10_nd4_40k.md"}
 HPHI_PROFILE = {
     "square10x10_nd4_all_k": {"kernel": "k_hphi_df<4, representative table> (double-float H Phi)",
-                              "dram_bytes": None, "warp_inst": None,
+                              "dram_bytes": int(2.5 * (47262720 + 2511872)), "warp_inst": int(2.5 * 128122828),
                               "profile": "profiles/k_hphi_df_square10x10_nd4_all_k.md"},
 }
 
