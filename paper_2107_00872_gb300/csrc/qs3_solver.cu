@@ -619,23 +619,17 @@ __global__ void k_reduce_df(const float4 *__restrict__ part, int m, const int *_
         out += j0;
     }
     if (active && !active[s]) return;
-    __shared__ double2 red[NTHREADS / 32];
-    for (int j = blockIdx.x; j < m; j += gridDim.x) {
+    // one warp per coefficient j: its lanes stride over the sector's chunks
+    const int wpb = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < m; j += gridDim.x * wpb) {
         double2 acc = make_double2(0.0, 0.0);
-        for (int c = chunk0[s] + threadIdx.x; c < chunk0[s + 1]; c += blockDim.x) {
+        for (int c = chunk0[s] + lane; c < chunk0[s + 1]; c += 32) {
             const float4 v = part[(uint64_t)c * m + j];
             acc.x += (double)v.x + (double)v.y;
             acc.y += (double)v.z + (double)v.w;
         }
         acc = warp_sum2(acc);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double2 t = make_double2(0.0, 0.0);
-            for (int q = 0; q < NTHREADS / 32; ++q) { t.x += red[q].x; t.y += red[q].y; }
-            out[(uint64_t)s * ldo + j] = t;
-        }
-        __syncthreads();
+        if (lane == 0) out[(uint64_t)s * ldo + j] = acc;
     }
 }
 
@@ -1267,7 +1261,7 @@ struct Engine {
     // reduce part[.. m] into out (S x ldo)
     int reduce(int m, double2 *out, int ldo, bool df = false) {
         dim3 g(m, B.S);
-        if (df) k_reduce_df<<<g, NTHREADS, 0, st>>>((const float4 *)part.p, m, c0(), act(), out, ldo);
+        if (df) k_reduce_df<<<dim3((m + 7) / 8, B.S), NTHREADS, 0, st>>>((const float4 *)part.p, m, c0(), act(), out, ldo);
         else k_reduce<<<g, NTHREADS, 0, st>>>(part.as<double2>(), m, c0(), act(), out, ldo);
         QS3_LAUNCHED();
         return QS3_OK;
@@ -1430,7 +1424,7 @@ struct Engine {
             k_reduce<<<dim3(1, B.S), NTHREADS, 0, st>>>(part.as<double2>(), 1, c0(), act(), n1, 1);
             QS3_LAUNCHED();
             QS3_TRY(mdot_df(B.tune_nv, 0, cap, w, dx));
-            k_reduce_df<<<dim3(std::min(cap, 64), B.S), NTHREADS, 0, st>>>((const float4 *)part.p, cap, c0(), act(),
+            k_reduce_df<<<dim3(std::min((cap + 7) / 8, 8), B.S), NTHREADS, 0, st>>>((const float4 *)part.p, cap, c0(), act(),
                                                                            h2.as<double2>(), cap, dx);
             QS3_LAUNCHED();
             k_mupdate_df<VT><<<grid(), NTHREADS, cap * sizeof(float4), st>>>(w, V.as<ST>(), D, 0, cap, h2.as<double2>(),
@@ -1459,7 +1453,7 @@ struct Engine {
         QS3_TRY(hphi_df_launch(B, hd(), nullptr, 0, w, st, act(), true));
         // three-term part against psi_{x-1}, psi_x
         QS3_TRY(mdot_df(B.tune_nv, 0, 2, (const float4 *)w, dx, 1));
-        k_reduce_df<<<dim3(2, B.S), NTHREADS, 0, st>>>((const float4 *)part.p, 2, c0(), act(), hh1, cap, dx, 1);
+        k_reduce_df<<<dim3(1, B.S), NTHREADS, 0, st>>>((const float4 *)part.p, 2, c0(), act(), hh1, cap, dx, 1);
         QS3_LAUNCHED();
         k_mupdate_df<VT, float4><<<grid(), NTHREADS, 2 * sizeof(float4), st>>>(w, v, D, 0, 2, hh1, cap, secs(), c0(),
                                                                               B.S, act(), nullptr, part.as<double2>(),
@@ -1469,7 +1463,7 @@ struct Engine {
         QS3_LAUNCHED();
         // one Gram-Schmidt pass against psi_0 .. psi_x
         QS3_TRY(mdot_df(B.tune_nv, 0, cap, (const float4 *)w, dx, 0));
-        k_reduce_df<<<dim3(std::min(cap, 64), B.S), NTHREADS, 0, st>>>((const float4 *)part.p, cap, c0(), act(),
+        k_reduce_df<<<dim3(std::min((cap + 7) / 8, 8), B.S), NTHREADS, 0, st>>>((const float4 *)part.p, cap, c0(), act(),
                                                                        h2.as<double2>(), cap, dx, 0);
         QS3_LAUNCHED();
         k_mupdate_df<VT, float4><<<grid(), NTHREADS, cap * sizeof(float4), st>>>(w, v, D, 0, cap, h2.as<double2>(), cap,
