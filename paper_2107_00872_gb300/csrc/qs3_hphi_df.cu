@@ -39,8 +39,9 @@ __device__ __forceinline__ double2 dfc_out(const dfc &a) {
 }
 
 // one thread per row, persistent grid over the tiles of all sectors (the
-// structure of k_hphi); phi may be phi + (*dx) ld when dx is given (the
-// solvers' CUDA graphs take the Krylov index from device memory).  ODF:
+// structure of k_hphi); phi may be phi + (*dx) ld when dx is given (a vector
+// of a stored set chosen by an index in device memory, as inside a captured
+// CUDA graph).  ODF:
 // psi is written in double-float form too (float4, renormalised), else as
 // complex128.  DEGB > 0 (representative table only): per occupied site the
 // first DEGB hops go in stages -- all target ranks, then all table entries,

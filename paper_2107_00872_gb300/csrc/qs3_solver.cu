@@ -793,6 +793,83 @@ __global__ void __launch_bounds__(NTHREADS) k_scale_split(VT *__restrict__ w, ty
     }
 }
 
+// double-float engine, three-term update: w -= c_0 psi_{j0} + c_1 psi_{j0+1}
+// (m = 1 or 2 stored vectors, coefficients coef[s ldc + j]), |w|^2 per block
+// in part.  Four rows at a time with all their loads (both vectors' planes
+// and w) issued together, so a block waits for memory twice instead of once
+// per vector and again for w.  Graph mode (dx): vectors x - 1, x.
+__global__ void __launch_bounds__(NTHREADS) k_ring_df(float4 *__restrict__ w, const float4 *__restrict__ V, uint64_t D,
+                                                      int j0, int m, const double2 *__restrict__ coef, int ldc,
+                                                      const SecView *__restrict__ secs,
+                                                      const int *__restrict__ chunk0, int S,
+                                                      const int *__restrict__ active, double2 *__restrict__ part,
+                                                      const int *__restrict__ dx = nullptr) {
+    if (dx) {
+        graph_range(dx, 1, j0, m);
+        coef += j0;
+    }
+    __shared__ float4 cf[2];
+    __shared__ double red[NTHREADS / 32];
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    if (threadIdx.x < 2)
+        cf[threadIdx.x] = threadIdx.x < m ? split2(coef[(uint64_t)ci.s * ldc + threadIdx.x]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    const float4 c0 = cf[0], c1 = cf[1];
+    const float2 *h0 = (const float2 *)(V + (uint64_t)j0 * D), *l0 = h0 + D;
+    const float2 *h1 = m > 1 ? (const float2 *)(V + (uint64_t)(j0 + 1) * D) : h0, *l1 = h1 + D;
+    const int nk = (ci.n - (int)threadIdx.x + NTHREADS - 1) / NTHREADS;
+    const uint64_t r0 = ci.base + threadIdx.x;
+    dfl n2 = {0.f, 0.f};
+#pragma unroll
+    for (int kb = 0; kb < RPT; kb += 4) {
+        float2 a0h[4], a0l[4], a1h[4], a1l[4];
+        float4 wv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint64_t r = r0 + (uint64_t)(kb + u) * NTHREADS;
+            if (kb + u < nk) {
+                a0h[u] = h0[r];
+                a0l[u] = l0[r];
+                a1h[u] = h1[r];
+                a1l[u] = l1[r];
+                wv[u] = w[r];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (kb + u >= nk) continue;
+            dfl ur = {0.f, 0.f}, ui = {0.f, 0.f};
+            // u = c0 v0 + c1 v1: re += a.r c.r - a.i c.i ; im += a.r c.i + a.i c.r
+            df_mac(ur, a0h[u].x, a0l[u].x, c0.x, c0.y);
+            df_mac(ur, -a0h[u].y, -a0l[u].y, c0.z, c0.w);
+            df_mac(ui, a0h[u].x, a0l[u].x, c0.z, c0.w);
+            df_mac(ui, a0h[u].y, a0l[u].y, c0.x, c0.y);
+            if (m > 1) {
+                df_mac(ur, a1h[u].x, a1l[u].x, c1.x, c1.y);
+                df_mac(ur, -a1h[u].y, -a1l[u].y, c1.z, c1.w);
+                df_mac(ui, a1h[u].x, a1l[u].x, c1.z, c1.w);
+                df_mac(ui, a1h[u].y, a1l[u].y, c1.x, c1.y);
+            }
+            const dfl re = df_sum({wv[u].x, wv[u].y}, {-ur.hi, -ur.lo});
+            const dfl im = df_sum({wv[u].z, wv[u].w}, {-ui.hi, -ui.lo});
+            w[r0 + (uint64_t)(kb + u) * NTHREADS] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            df_mac(n2, re.hi, re.lo, re.hi, re.lo);
+            df_mac(n2, im.hi, im.lo, im.hi, im.lo);
+        }
+    }
+    double nrm = df_d(n2);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < NTHREADS / 32; ++q) t += red[q];
+        part[blockIdx.x] = make_double2(t, 0.0);
+    }
+}
+
 // double-float engine: basis vector x + 1 = w * inv[s], all in double-float
 // (the store's slot x + 1, and hin, the interleaved input of the next H Phi)
 __global__ void __launch_bounds__(NTHREADS) k_scale_df(const float4 *__restrict__ w, float4 *__restrict__ out,
@@ -1455,9 +1532,8 @@ struct Engine {
         QS3_TRY(mdot_df(B.tune_nv, 0, 2, (const float4 *)w, dx, 1));
         k_reduce_df<<<dim3(1, B.S), NTHREADS, 0, st>>>((const float4 *)part.p, 2, c0(), act(), hh1, cap, dx, 1);
         QS3_LAUNCHED();
-        k_mupdate_df<VT, float4><<<grid(), NTHREADS, 2 * sizeof(float4), st>>>(w, v, D, 0, 2, hh1, cap, secs(), c0(),
-                                                                              B.S, act(), nullptr, part.as<double2>(),
-                                                                              dx, 1);
+        k_ring_df<<<grid(), NTHREADS, 0, st>>>(w, V.as<float4>(), D, 0, 2, hh1, cap, secs(), c0(), B.S, act(),
+                                               part.as<double2>(), dx);
         QS3_LAUNCHED();
         k_reduce<<<dim3(1, B.S), NTHREADS, 0, st>>>(part.as<double2>(), 1, c0(), act(), n1, 1);
         QS3_LAUNCHED();
@@ -1594,7 +1670,14 @@ struct Engine {
         const int j0 = full2 ? 0 : std::max(0, x - 1);
         double2 *n1 = nrm1.as<double2>();
         QS3_TRY(mdot(j0, x + 1 - j0, (const float4 *)w, h1.as<double2>() + j0, cap));
-        QS3_TRY(mupdate(w, j0, x + 1 - j0, h1.as<double2>() + j0, cap, n1));
+        if (full2 || B.nchunks == 0) {
+            QS3_TRY(mupdate(w, j0, x + 1 - j0, h1.as<double2>() + j0, cap, n1));
+        } else if constexpr (std::is_same<ST, float4>::value) {
+            k_ring_df<<<grid(), NTHREADS, 0, st>>>(w, V.as<float4>(), D, j0, x + 1 - j0, h1.as<double2>() + j0, cap,
+                                                   secs(), c0(), B.S, act(), part.as<double2>());
+            QS3_LAUNCHED();
+            QS3_TRY(reduce(1, n1, 1));
+        }
         QS3_TRY(gs_dots(x, (const float4 *)w, h2.as<double2>()));
         QS3_TRY(mupdate(w, 0, x + 1, h2.as<double2>(), cap, nrm.as<double2>(), n1));
         k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, x, cap, h1.as<double2>(), nrm.as<double2>(), act(),
