@@ -2316,7 +2316,7 @@ static size_t solve_mem_estimate(const Basis &B, const qs3_solve_opts &o) {
     size_t m = cap * B.total * ev + 2 * B.total * ev64 + (size_t)std::max(B.nchunks, 1) * cap * 16;
     if (o.precision == QS3_F32) m += cap * B.total * ev64;   // the fp64 refinement
     m += 3 * B.total * ev64;                                 // fp64 ring of the fp64 engine
-    if (B.has_k && !o.hphi_ieee) m += B.total * 16;          // double-float w of that engine
+    if (B.has_k && !o.hphi_ieee) m += 2 * B.total * 16;      // double-float w and H's input copy
     return m;
 }
 
