@@ -7,12 +7,13 @@
 // flag removes converged sectors from every launch.  The Lanczos vectors
 // Psi live in one device array (vector j at offset j * total_dim).
 //
-// One Lanczos step (Alg. 10 lines 5-11) for x: v = H psi_x is written into
-// psi_{x+1}; classical Gram-Schmidt run twice against psi_0..psi_x (the
-// reorthogonalisation; its first pass yields alpha_x = psi_x^dag v and the
-// three-term coefficients); beta_x = |v|; psi_{x+1} = v / beta_x.  Dot
-// products, norms and the Gram-Schmidt coefficients are fp64 even when the
-// vectors are fp32.  The small tridiagonal / arrowhead matrices T are
+// One Lanczos step (Alg. 10 lines 5-11) for x: v = H psi_x; the three-term
+// part removes the components along psi_{x-1}, psi_x (coefficients by dot
+// product, alpha_x among them), then one classical Gram-Schmidt pass against
+// psi_0..psi_x removes the O(eps) rest (two full passes on the first step
+// after a thick restart); beta_x = |v|; psi_{x+1} = v / beta_x.  Dot
+// products, norms and the Gram-Schmidt coefficients are fp64-accurate (fp64
+// or double-float sums) even when the vectors are fp32.  The small tridiagonal / arrowhead matrices T are
 // diagonalised on the host (Sturm bisection + inverse iteration for
 // tridiagonal T, cyclic Jacobi for the arrowhead T of the thick restart).
 #include <algorithm>
@@ -468,10 +469,12 @@ __global__ void __launch_bounds__(NTHREADS) k_combine(OT *__restrict__ out, uint
 // reorthogonalisation of Alg. 10) then runs on the fp32 units with
 // error-free products (fma) and two-sums; the fp64 unit -- a small fraction
 // of the fp32 rate on this GPU -- only sees one conversion per row and
-// kernel.  H psi_x and the three-term part of each step use exact fp64
-// copies of psi_{x-1}, psi_x, so alpha_x and beta_x are fp64 results; the
-// 2^-48 rounding of the stored basis only bounds how far below fp64 epsilon
-// the orthogonality of the basis can be pushed.
+// kernel.  Complex k-sector solves (the double-float engine, Engine::dfh)
+// keep w = H psi_x in double-float as well and run H (k_hphi_df), the
+// three-term part and the scaling on the fp32 units; real and U(1) solves
+// apply H and the three-term part to exact fp64 copies of psi_{x-1}, psi_x.
+// The 2^-48 rounding only bounds how far below fp64 epsilon the
+// orthogonality of the basis can be pushed.
 template <typename VT> struct DfS { using T = VT; };     // fp32 vectors: stored as they are
 template <> struct DfS<double> { using T = float2; };    // (hi, lo)
 template <> struct DfS<double2> { using T = float4; };   // (re.hi, re.lo, im.hi, im.lo)
