@@ -30,6 +30,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -379,6 +380,27 @@ def graphs_leg(args, basis):
 
 # --------------------------------------------------------- oracle timing
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm
+    implementer and part codes), for the oracle baseline's record."""
+    try:
+        lines = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.machine()
+    for key in ("model name", "Model name", "Hardware"):
+        for line in lines:
+            if line.startswith(key) and ":" in line:
+                return line.split(":", 1)[1].strip()
+    codes = {}
+    for line in lines:
+        for key in ("CPU implementer", "CPU part"):
+            if line.startswith(key) and key not in codes:
+                codes[key] = line.split(":", 1)[1].strip()
+    if codes:
+        return f"{platform.machine()} implementer {codes.get('CPU implementer')} part {codes.get('CPU part')}"
+    return platform.machine()
+
+
 def oracle_sample(args, seconds_budget: float = 15.0, threads: int | None = None):
     """Oracle H Phi (Alg. 9 literally) on sampled rows of one sector of the
     workload; returns (Gnnz/s, cores, description)."""
@@ -437,7 +459,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload},
             "cpu_baseline": {"value": round(value, 6), "unit": "Gnnz/s", "cores": cores, "kind": "oracle",
-                             "sample": desc},
+                             "sample": desc, "cpu": cpu_model()},
             "e2e": {"value": round(value, 6), "unit": "Gnnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -690,7 +712,7 @@ def main():
         out["graphs"] = graphs_leg(args, basis)
         rate, cores, desc = oracle_sample(args)
         out["cpu_baseline"] = {"value": round(rate, 6), "unit": "Gnnz/s", "cores": cores, "kind": "oracle",
-                               "sample": desc}
+                               "sample": desc, "cpu": cpu_model()}
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
