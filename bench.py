@@ -711,8 +711,10 @@ def main():
         out["fp32_vs_fp64"] = fp32_vs_fp64(args, basis, np.array(out["_evals"]))
         out["graphs"] = graphs_leg(args, basis)
         rate, cores, desc = oracle_sample(args)
+        rate1, _, desc1 = oracle_sample(args, seconds_budget=5.0, threads=1)
         out["cpu_baseline"] = {"value": round(rate, 6), "unit": "Gnnz/s", "cores": cores, "kind": "oracle",
-                               "sample": desc, "cpu": cpu_model()}
+                               "sample": desc, "cpu": cpu_model(),
+                               "one_thread": {"value": round(rate1, 6), "sample": desc1}}
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
