@@ -134,50 +134,55 @@ static int64_t binary_search_u64(uint64_t s0, const uint64_t *s, int64_t ls, int
     return lo;
 }
 
-/* Alg. 2 over the column {C(k, m)}_{1 <= k <= j} of the binomial table. */
-static int binary_search_col(uint64_t s0, const orc_ctx *c, int m, int j)
-{
-    int lo = 0, hi = j;             /* C(0,m) = 0 <= s0 for m >= 1 */
-    while (lo < hi) {
-        int mid = lo + (hi - lo + 1) / 2;
-        if (Cb(c, mid, m) <= s0) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-/* Alg. 1: n = F_bar(a); optionally records s after each column step. */
+/* Inverse of Eq. (a_of_n) (the paper's F_bar, Alg. 1): the sorted list n
+ * with F(n) = a.  Every list whose largest site is below r has an index
+ * below 1 + C(r - 1, Nd), so the largest site of n is the largest r with
+ * C(r - 1, Nd) <= a - 1; the remaining sites are the inverse, for Nd - 1
+ * sites below r, of what is left of a - 1.  Each site is found by scanning
+ * down from the previous one.  trace (optional) records the paper's running
+ * value s = (what is left) + 1 after each of the sites n_Nd .. n_2. */
 static void f_bar(const orc_ctx *c, uint64_t a, int *n, uint64_t *trace)
 {
-    uint64_t s = a;
-    int j = c->N;
+    uint64_t left = a - 1;
+    int top = c->N;
     int t = 0;
-    for (int m = c->nd; m >= 2; --m) {
-        int j0 = binary_search_col(s - 1, c, m, j);
-        j = j0;
-        n[m - 1] = j0 + 1;
-        s -= Cb(c, j, m);
-        if (trace) trace[t++] = s;
+    for (int m = c->nd; m >= 1; --m) {
+        int r = top;
+        while (r > m && Cb(c, r - 1, m) > left) --r;
+        n[m - 1] = r;
+        left -= Cb(c, r - 1, m);
+        top = r - 1;
+        if (trace && m >= 2) trace[t++] = left + 1;
     }
-    if (c->nd >= 1) n[0] = (int)s;
 }
 
-/* Alg. 3 (reading R3): r < r', exactly one of them is in n. */
-static void spin_exchange(int nd, int r, int p, int f, int rp, int pp, const int *n, int *np)
+/* membership of site r in the sorted list n */
+static int contains(const int *n, int nd, int r)
 {
+    for (int i = 0; i < nd; ++i)
+        if (n[i] == r) return 1;
+    return 0;
+}
+
+/* Alg. 3 by its definition (reading R3): on a bond (r, r') with exactly one
+ * down spin, the exchange moves that spin to the other end.  np = the list
+ * without the site it leaves, with the site it enters, in ascending order.
+ * Returns 0 (np untouched) when both ends or neither end hold a down spin. */
+static int hop_target(int nd, const int *n, int r, int rp, int *np)
+{
+    const int in_r = contains(n, nd, r), in_rp = contains(n, nd, rp);
+    if (in_r == in_rp) return 0;
+    const int leave = in_r ? r : rp, enter = in_r ? rp : r;
     int k = 0;
-    if (!f) {
-        /* r enters after n_p, r' = n_{p'} leaves */
-        for (int i = 1; i <= p; ++i) np[k++] = n[i - 1];
-        np[k++] = r;
-        for (int i = p + 1; i <= pp - 1; ++i) np[k++] = n[i - 1];
-        for (int i = pp + 1; i <= nd; ++i) np[k++] = n[i - 1];
-    } else {
-        /* r = n_p leaves, r' enters after n_{p'} */
-        for (int i = 1; i <= p - 1; ++i) np[k++] = n[i - 1];
-        for (int i = p + 1; i <= pp; ++i) np[k++] = n[i - 1];
-        np[k++] = rp;
-        for (int i = pp + 1; i <= nd; ++i) np[k++] = n[i - 1];
+    for (int i = 0; i < nd; ++i)
+        if (n[i] != leave) np[k++] = n[i];
+    np[k] = enter;
+    for (int i = 1; i < nd; ++i) {            /* insertion sort */
+        int v = np[i], j = i - 1;
+        while (j >= 0 && np[j] > v) { np[j + 1] = np[j]; --j; }
+        np[j + 1] = v;
     }
+    return 1;
 }
 
 /* --------------------------------------------------------------- translations */
@@ -273,14 +278,14 @@ static double diag_elem(const orc_ctx *c, const int *n)
     double e = 0.0;
     for (int b = 0; b < c->nb; ++b) {
         int f, fp;
-        binary_search_int(c->r[b], n, 1, c->nd, &f);
-        binary_search_int(c->rp[b], n, 1, c->nd, &fp);
+        f = contains(n, c->nd, c->r[b]);
+        fp = contains(n, c->nd, c->rp[b]);
         e += (f == fp) ? c->jz[b] / 4.0 : -c->jz[b] / 4.0;
     }
     if (c->h) {
         for (int i = 1; i <= c->N; ++i) {
             int f;
-            binary_search_int(i, n, 1, c->nd, &f);
+            f = contains(n, c->nd, i);
             e += f ? 0.5 * c->h[i - 1] : -0.5 * c->h[i - 1];
         }
     }
@@ -353,10 +358,10 @@ uint64_t orc_spin_exchange(int N, int nd, const int *n, int r, int rp)
     orc_ctx c;
     if (ctx_init(&c, N, nd, 0, NULL, NULL, NULL, NULL, NULL, NULL)) { ctx_free(&c); return 0; }
     int f, fp, np[ORC_MAXND];
-    int p = binary_search_int(r, n, 1, nd, &f);
-    int pp = binary_search_int(rp, n, 1, nd, &fp);
+    f = contains(n, nd, r);
+    fp = contains(n, nd, rp);
     uint64_t a = 0;
-    if (f != fp) { spin_exchange(nd, r, p, f, rp, pp, n, np); a = F(&c, np); }
+    if (f != fp) { hop_target(nd, n, r, rp, np); a = F(&c, np); }
     ctx_free(&c);
     return a;
 }
@@ -373,13 +378,13 @@ int orc_dense_u1(ORC_LAT, double *H)
         f_bar(&c, a, n, NULL);
         for (int b = 0; b < nb; ++b) {
             int f, fp;
-            int p = binary_search_int(r[b], n, 1, nd, &f);
-            int pp = binary_search_int(rp[b], n, 1, nd, &fp);
+            f = contains(n, nd, r[b]);
+            fp = contains(n, nd, rp[b]);
             if (f == fp) {
                 H[(a - 1) * D + (a - 1)] += jz[b] / 4.0;
             } else {
                 H[(a - 1) * D + (a - 1)] -= jz[b] / 4.0;
-                spin_exchange(nd, r[b], p, f, rp[b], pp, n, np);
+                hop_target(nd, n, r[b], rp[b], np);
                 uint64_t ap = F(&c, np);
                 H[(a - 1) * D + (ap - 1)] += jxy[b] / 2.0;
             }
@@ -387,7 +392,7 @@ int orc_dense_u1(ORC_LAT, double *H)
         if (h) {
             for (int i = 1; i <= N; ++i) {
                 int f;
-                binary_search_int(i, n, 1, nd, &f);
+                f = contains(n, nd, i);
                 H[(a - 1) * D + (a - 1)] += f ? 0.5 * h[i - 1] : -0.5 * h[i - 1];
             }
         }
@@ -405,10 +410,10 @@ static zdbl hphi_u1_row(const orc_ctx *c, uint64_t a, const zdbl *phi, int64_t *
     *terms += 1;
     for (int b = 0; b < c->nb; ++b) {
         int f, fp;
-        int p = binary_search_int(c->r[b], n, 1, c->nd, &f);
-        int pp = binary_search_int(c->rp[b], n, 1, c->nd, &fp);
+        f = contains(n, c->nd, c->r[b]);
+        fp = contains(n, c->nd, c->rp[b]);
         if (f != fp) {
-            spin_exchange(c->nd, c->r[b], p, f, c->rp[b], pp, n, np);
+            hop_target(c->nd, n, c->r[b], c->rp[b], np);
             uint64_t ap = F(c, np);
             acc += (c->jxy[b] / 2.0) * phi[ap - 1];
             *terms += 1;
@@ -507,13 +512,13 @@ static zdbl hphi_k_row(const orc_ctx *c, const int *K, const uint64_t *sigma, co
     *terms += 1;
     for (int b = 0; b < c->nb; ++b) {
         int f, fp;
-        int p = binary_search_int(c->r[b], n, 1, c->nd, &f);
-        int pp = binary_search_int(c->rp[b], n, 1, c->nd, &fp);
+        f = contains(n, c->nd, c->r[b]);
+        fp = contains(n, c->nd, c->rp[b]);
         if (f == fp) {
             acc += (c->jz[b] / 4.0) * phi[row - 1];
         } else {
             acc -= (c->jz[b] / 4.0) * phi[row - 1];
-            spin_exchange(c->nd, c->r[b], p, f, c->rp[b], pp, n, np);
+            hop_target(c->nd, n, c->r[b], c->rp[b], np);
             uint64_t ap = F(c, np);
             int l[3];
             uint64_t rep = representative(c, ap, l);
@@ -530,7 +535,7 @@ static zdbl hphi_k_row(const orc_ctx *c, const int *K, const uint64_t *sigma, co
         double e = 0.0;
         for (int i = 1; i <= c->N; ++i) {
             int f;
-            binary_search_int(i, n, 1, c->nd, &f);
+            f = contains(n, c->nd, i);
             e += f ? 0.5 * c->h[i - 1] : -0.5 * c->h[i - 1];
         }
         acc += e * phi[row - 1];
@@ -580,13 +585,13 @@ int orc_dense_k(ORC_LAT, const int *K, const uint64_t *sigma, const double *Nak,
         f_bar(&c, sigma[row - 1], n, NULL);
         for (int b = 0; b < nb; ++b) {
             int f, fp;
-            int p = binary_search_int(r[b], n, 1, nd, &f);
-            int pp = binary_search_int(rp[b], n, 1, nd, &fp);
+            f = contains(n, nd, r[b]);
+            fp = contains(n, nd, rp[b]);
             if (f == fp) {
                 H[(row - 1) * d + (row - 1)] += jz[b] / 4.0;
             } else {
                 H[(row - 1) * d + (row - 1)] -= jz[b] / 4.0;
-                spin_exchange(nd, r[b], p, f, rp[b], pp, n, np);
+                hop_target(nd, n, r[b], rp[b], np);
                 uint64_t ap = F(&c, np);
                 int l[3];
                 uint64_t rep = representative(&c, ap, l);
@@ -601,7 +606,7 @@ int orc_dense_k(ORC_LAT, const int *K, const uint64_t *sigma, const double *Nak,
             double e = 0.0;
             for (int i = 1; i <= N; ++i) {
                 int f;
-                binary_search_int(i, n, 1, nd, &f);
+                f = contains(n, nd, i);
                 e += f ? 0.5 * h[i - 1] : -0.5 * h[i - 1];
             }
             H[(row - 1) * d + (row - 1)] += e;
@@ -683,7 +688,7 @@ int orc_corr_u1(int N, int nd, const double *phi, double *szsz, double *spsm, do
         double w = creal(p[a - 1] * conj(p[a - 1]));
         for (int i = 1; i <= N; ++i) {
             int f;
-            binary_search_int(i, n, 1, nd, &f);
+            f = contains(n, nd, i);
             szv[i - 1] = f ? -0.5 : 0.5;
         }
         for (int i = 0; i < N; ++i) {
@@ -733,13 +738,13 @@ int64_t orc_row_terms_k(ORC_LAT, const int *K, uint64_t a, int64_t max_terms, ui
     zdbl *cf = (zdbl *)coef;
     for (int b = 0; b < nb; ++b) {
         int f, fp;
-        int p = binary_search_int(r[b], n, 1, nd, &f);
-        int pp = binary_search_int(rp[b], n, 1, nd, &fp);
+        f = contains(n, nd, r[b]);
+        fp = contains(n, nd, rp[b]);
         if (f == fp) {
             dg += jz[b] / 4.0;
         } else {
             dg -= jz[b] / 4.0;
-            spin_exchange(nd, r[b], p, f, rp[b], pp, n, np);
+            hop_target(nd, n, r[b], rp[b], np);
             uint64_t ap = F(&c, np);
             int l[3];
             uint64_t rep = representative(&c, ap, l);
@@ -754,7 +759,7 @@ int64_t orc_row_terms_k(ORC_LAT, const int *K, uint64_t a, int64_t max_terms, ui
     if (h) {
         for (int i = 1; i <= N; ++i) {
             int f;
-            binary_search_int(i, n, 1, nd, &f);
+            f = contains(n, nd, i);
             dg += f ? 0.5 * h[i - 1] : -0.5 * h[i - 1];
         }
     }
