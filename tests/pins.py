@@ -7,7 +7,8 @@ path): nothing here calls the oracle or the GPU library.
   spin matrices, and an equivalent bit-string construction;
 - translations of site sets by coordinate arithmetic;
 - closed forms: sector dimensions by a character sum over the translation
-  group, the one-magnon dispersion.
+  group, the one-magnon dispersion, the two-magnon chain spectrum from the
+  two-body problem in the relative coordinate.
 """
 from __future__ import annotations
 
@@ -131,3 +132,32 @@ def one_magnon_energy(spec, K) -> float:
     z = 2 * D
     hop = sum(2 * np.cos(2 * np.pi * K[a] / L[a]) for a in range(3) if L[a] > 1)
     return nb * Jz / 4 - z * Jz / 2 + J / 2 * hop
+
+
+def two_magnon_chain_spectrum(N: int, J: float, Jz: float) -> np.ndarray:
+    """All C(N, 2) levels of two down spins on the uniform periodic chain of
+    odd length N, from the two-body problem in the relative coordinate.
+
+    For total momentum K = 2 pi n / N the states |K, r> = N^{-1/2} sum_x
+    e^{iKx} |{x, x+r}> (r = 1..R, R = (N-1)/2) are orthonormal, and
+    |K, N-r> = e^{iKr} |K, r>.  Each down spin hops with amplitude J/2: the
+    spin at x moves to x -/+ 1 (separation r +/- 1, phase e^{+/-iK}), the one
+    at x + r to x + r +/- 1, so H|K,r> = d(r)|K,r> + (J/2)[(1 + e^{iK})|K,r+1>
+    + (1 + e^{-iK})|K,r-1>], with no |K,0> (hard core) and |K,R+1> =
+    e^{iKR}|K,R>.  The diagonal is the ferromagnetic energy N Jz/4 minus Jz
+    per flipped spin's two broken bonds, -2 Jz, plus Jz when the two spins are
+    neighbours (r = 1: their common bond stays satisfied)."""
+    assert N % 2 == 1 and N >= 5
+    R = (N - 1) // 2
+    out = []
+    for n in range(N):
+        K = 2 * np.pi * n / N
+        M = np.zeros((R, R), np.complex128)
+        for r in range(1, R + 1):
+            M[r - 1, r - 1] = N * Jz / 4 - 2 * Jz + (Jz if r == 1 else 0.0)
+            if r < R:
+                M[r, r - 1] += J / 2 * (1 + np.exp(1j * K))          # <K, r+1| H |K, r>
+                M[r - 1, r] += J / 2 * (1 + np.exp(-1j * K))         # <K, r| H |K, r+1>
+        M[R - 1, R - 1] += J / 2 * (1 + np.exp(1j * K)) * np.exp(1j * K * R)
+        out.extend(np.linalg.eigvalsh(M))
+    return np.sort(np.array(out))

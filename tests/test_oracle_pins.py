@@ -140,6 +140,16 @@ def test_one_and_two_magnon_chain_against_closed_forms():
                                atol=1e-12)
 
 
+@pytest.mark.parametrize("N,Jz", [(15, 1.0), (13, 0.6), (11, -0.5), (9, 2.0)])
+def test_two_magnon_chain_against_two_body_problem(N, Jz):
+    """The oracle's N_down = 2 block of the periodic XXZ chain against the
+    two-body problem in the relative coordinate (total momentum conserved,
+    hard-core nearest-neighbour pair): every one of the C(N, 2) levels."""
+    spec = qi.chain(N, J=1.0, Jz=Jz)
+    e = np.sort(np.linalg.eigvalsh(orc.dense_u1(olat(spec), 2)))
+    np.testing.assert_allclose(e, pins.two_magnon_chain_spectrum(N, 1.0, Jz), atol=1e-12, rtol=0)
+
+
 # ------------------------------------------------------- Alg 5-7, dimensions
 
 
