@@ -128,14 +128,18 @@ int qs3_basis_rep_table(qs3_basis_t b, int32_t mode, int32_t *active);
  *   - H Phi with 1..4 fewer resident 256-row blocks per SM than the occupancy
  *     limit (the persistent grid, i.e. rows in flight per SM), per vector
  *     dtype, and keeps the fastest;
- *   - the double-float dot products of the fp64 Lanczos Gram-Schmidt pass
- *     with 1, 2 or 4 basis vectors per pass (loads in flight together).
+ *   - the dot products of the Gram-Schmidt pass with 1, 2 or 4 basis vectors
+ *     per pass (loads in flight together): dot_vectors for the double-float
+ *     engine and the fp32 phase, dot_vectors64 for the binary64 engine.
  * set = 0: write the current choices (0 = not tuned yet) to
- *          hphi_blocks_per_sm[5] (indexed by qs3_dtype) and *dot_vectors;
+ *          hphi_blocks_per_sm[5] (indexed by qs3_dtype), *dot_vectors and
+ *          *dot_vectors64;
  * set = 1: impose them (0 = tune again at the next use; blocks per SM above
- *          the occupancy limit are clamped; dot_vectors in {0, 1, 2, 4}).
- * Either pointer may be NULL.  Results do not depend on the choices. */
-int qs3_basis_tuning(qs3_basis_t b, int32_t set, int32_t *hphi_blocks_per_sm, int32_t *dot_vectors);
+ *          the occupancy limit are clamped; vectors per pass in {0, 1, 2, 4};
+ *          INVALID_ARG otherwise).
+ * Any pointer may be NULL.  Results do not depend on the choices. */
+int qs3_basis_tuning(qs3_basis_t b, int32_t set, int32_t *hphi_blocks_per_sm, int32_t *dot_vectors,
+                     int32_t *dot_vectors64);
 /* Stored terms of a k-sector basis (an opt-in variant of Alg. 9, which the
  * paper recomputes matrix-free on every product).  mode = 1 enumerates every
  * off-diagonal term once -- its target row, the translation to the target's
@@ -173,16 +177,28 @@ typedef struct {
     int32_t min_iter;     /* minitr: Lanczos steps before the first check */
     int32_t check_every;  /* itrint: steps between convergence checks */
     double eps;           /* lnc_ene_conv: relative Ritz-value change for convergence */
-    int32_t precision;    /* QS3_F64: plain fp64; QS3_F32: fp32 H Phi + fp64 recurrences + fp64 refinement */
+    int32_t precision;    /* QS3_F64: IEEE binary64 throughout (complex double on k-sector bases): Lanczos
+                             vectors stored as binary64, H Phi, dot products and updates on binary64
+                             FMAs (see strict64);
+                             QS3_F32: fp32 vectors and H Phi with fp32 row sums, fp64 alpha/beta and
+                             dot products (double-float sums of exact fp32 products), then a QS3_F64
+                             refinement from the fp32 Ritz vectors;
+                             QS3_C128DF: the double-float engine, a faster variant below binary64: the
+                             Krylov basis stored as pairs of fp32 (about 48 significant bits, fp32
+                             exponent range) and, on k-sector bases, H Phi, three-term part and
+                             Gram-Schmidt in double-float arithmetic on the fp32 units */
     int32_t use_graphs;   /* fp64 solves: replay each Lanczos step (after the first) as a CUDA graph
                              captured once per vector-ring phase; fp32 vectors ignore it */
     uint64_t seed;        /* start vector: seeded Gaussian (SplitMix64 + Box-Muller) */
     double refine_tol;    /* fp32 mode: refine until |dE| <= refine_tol |E| (e.g. 1e-9) */
     double res_tol;       /* qs3_lanczos also needs the Ritz residual beta_m |c_m| <= res_tol max(|E|, 1); 0 = off */
-    int32_t hphi_ieee;    /* fp64 solves on k-sector bases: 0 applies H to the double-float copy of each
-                             Lanczos vector in double-float arithmetic (QS3_C128DF); 1 uses IEEE
-                             complex128 H Phi (QS3_C128).  Residuals are always IEEE complex128. */
-    int32_t reserved;     /* 0 */
+    int32_t hphi_ieee;    /* precision QS3_C128DF on k-sector bases: 0 applies H to the double-float copy
+                             of each Lanczos vector in double-float arithmetic; 1 uses the IEEE
+                             complex128 H Phi.  Residuals are always IEEE binary64. */
+    int32_t strict64;     /* QS3_F64 engine: 0 lets the Gram-Schmidt update whose coefficients are all
+                             below 2^-36 |w| in sum form its correction in fp32 from the stored values'
+                             high words (error below 2^-55 |w|, less than binary64 rounding of w);
+                             1 keeps every update on binary64 FMAs */
 } qs3_solve_opts;
 
 typedef struct {
@@ -200,6 +216,8 @@ typedef struct {
     uint64_t gs_dot_bytes;    /* their algorithmic bytes: stored basis vectors and w read, active sectors */
     int32_t gs_dot_calls;     /* those launches */
     int32_t reserved;
+    uint64_t gs_dot_fma;      /* binary64 engine: fused multiply-adds of those launches (4 per complex
+                                 element and stored vector, 1 per real one); 0 for the other engines */
 } qs3_solve_info;
 
 /* Conventional Lanczos with full reorthogonalisation (Alg. 10 lines 2-12)
@@ -248,8 +266,9 @@ int qs3_correlations(qs3_basis_t b, int32_t s, const void *gs, int32_t n_pairs, 
  * src (N_down, K) -> sector s_dst of basis dst (N_down + 1, K + Q), with
  * Q[3] the integer momentum of q (q.a_alpha = 2 pi Q_alpha / L_alpha).
  * phi, psi: device C128 vectors of the respective sector dimensions.  For a
- * U(1)-only pair of bases Q still fixes q (the lattice needs L) or, with L =
- * {0,0,0}, q = 0. */
+ * U(1)-only pair of bases Q still fixes q through L; a lattice given with
+ * L = {0,0,0} is numbered as a chain (L = {N,1,1}), so Q[0] then gives
+ * q = 2 pi Q[0] / N along the site index, and Q = {0,0,0} gives q = 0. */
 int qs3_smq(qs3_basis_t src, int32_t s_src, const void *phi, qs3_basis_t dst, int32_t s_dst, const int32_t *Q,
             void *psi, void *stream);
 
@@ -332,6 +351,33 @@ int qs3_full_diag(qs3_basis_t b, int32_t s, double *evals, void *evecs, void *st
  * INVALID_ARG for an empty list, a non-finite level or a negative weight. */
 int qs3_thermal(int64_t n_levels, const double *E, const double *A, const double *mult, int32_t n_beta,
                 const double *beta, double *log_z, double *avg);
+
+/* Measured throughput of this GPU's arithmetic pipes (no counterpart in the
+ * paper: the denominators of the ALU rooflines of the benchmark).  Each probe
+ * runs 8 blocks of 256 threads per SM, every thread 8 independent chains of
+ * one instruction kind, timed with CUDA events on stream (second of two
+ * launches, about 10-30 ms each):
+ *   fp64_fma_per_s  fp64 fused multiply-adds per second (thread operations),
+ *   fp32_fma_per_s  fp32 fused multiply-adds per second,
+ *   int_mad_per_s   32-bit integer multiply-adds per second,
+ *   int_alu_per_s   32-bit integer xor / add operations per second,
+ *   issue_per_s     warp instructions per second of the fp32 probe (one
+ *                   instruction per 32 lanes; a lower bound of the issue rate),
+ *   n_sms           multiprocessors of the current device.
+ * Errors: INVALID_ARG (NULL out), OOM, CUDA.  Synchronises stream. */
+typedef struct {
+    double fp64_fma_per_s, fp32_fma_per_s, int_mad_per_s, int_alu_per_s, issue_per_s;
+    int32_t n_sms, reserved;
+} qs3_peaks;
+int qs3_probe_peaks(qs3_peaks *out, void *stream);
+
+/* Allocation fault injection for tests of the error paths (no counterpart
+ * in the paper).  after >= 0: the next `after` device allocations of the
+ * library succeed as usual, every later one fails with QS3_ERR_OOM without
+ * calling the CUDA allocator, until the next call; after < 0 switches the
+ * injection off.  Process-wide (all threads).  Returns the previous setting
+ * (-1 = off).  Calls that fail this way release what they allocated. */
+int64_t qs3_inject_alloc_failure(int64_t after);
 
 /* Text of a status code, and of the last failure on the calling thread. */
 const char *qs3_strerror(int status);

@@ -12,7 +12,8 @@ import numpy as np
 from . import _abi
 from ._abi import QS3_C64, QS3_C128, QS3_C128DF, QS3_F32, QS3_F64, QS3Error, check, load
 
-__all__ = ["Basis", "QS3Error", "load", "hphi", "dtype_code", "SolveOpts", "split_df"]
+__all__ = ["Basis", "QS3Error", "load", "hphi", "dtype_code", "SolveOpts", "split_df", "probe_peaks",
+           "inject_alloc_failure"]
 
 
 def _torch():
@@ -51,24 +52,35 @@ def _dev(t, n: int | None = None, what: str = "vector"):
     return ctypes.c_void_p(t.data_ptr())
 
 
+_PRECISION = {"f64": QS3_F64, "f32": QS3_F32, "df": QS3_C128DF, QS3_F64: QS3_F64, QS3_F32: QS3_F32,
+              QS3_C128DF: QS3_C128DF}
+
+
 class SolveOpts:
-    """Fields of qs3_solve_opts with the paper's defaults (input_lancz / input_TRLan)."""
+    """Fields of qs3_solve_opts with the paper's defaults (input_lancz / input_TRLan).
+
+    precision: "f64" (IEEE binary64 engine), "f32" (fp32 H Phi + binary64
+    refinement) or "df" (the double-float engine)."""
 
     def __init__(self, n_eig=1, n_keep=8, n_max=32, max_iter=10000, min_iter=20, check_every=5, eps=1e-14,
-                 precision="f64", use_graphs=True, seed=1, refine_tol=1e-9, res_tol=1e-12, hphi_ieee=False):
+                 precision="f64", use_graphs=True, seed=1, refine_tol=1e-9, res_tol=1e-12, hphi_ieee=False,
+                 strict64=False):
+        if precision not in _PRECISION:
+            raise ValueError(f"precision {precision!r}: use 'f64', 'f32' or 'df'")
         self.n_eig, self.n_keep, self.n_max, self.max_iter = n_eig, n_keep, n_max, max_iter
         self.min_iter, self.check_every, self.eps = min_iter, check_every, eps
         self.precision, self.use_graphs, self.seed, self.refine_tol = precision, use_graphs, seed, refine_tol
-        self.res_tol, self.hphi_ieee = res_tol, hphi_ieee
+        self.res_tol, self.hphi_ieee, self.strict64 = res_tol, hphi_ieee, strict64
 
     def c(self) -> _abi.qs3_solve_opts:
         o = _abi.qs3_solve_opts()
         o.n_eig, o.n_keep, o.n_max, o.max_iter = self.n_eig, self.n_keep, self.n_max, self.max_iter
         o.min_iter, o.check_every, o.eps = self.min_iter, self.check_every, self.eps
-        o.precision = QS3_F32 if self.precision in ("f32", QS3_F32) else QS3_F64
+        o.precision = _PRECISION[self.precision]
         o.use_graphs, o.seed, o.refine_tol = int(bool(self.use_graphs)), int(self.seed), float(self.refine_tol)
         o.res_tol = float(self.res_tol)
         o.hphi_ieee = int(bool(self.hphi_ieee))
+        o.strict64 = int(bool(self.strict64))
         return o
 
 
@@ -82,6 +94,22 @@ def split_df(x, out=None, stream=None):
         out = torch.empty(4 * x.numel(), dtype=torch.float32, device=x.device)
     check(load().qs3_split_df(_dev(x), _dev(out, 4 * x.numel(), "out"), x.numel(), _stream(stream)), "qs3_split_df")
     return out
+
+
+def probe_peaks(stream=None) -> dict:
+    """Measured throughput of the GPU's arithmetic pipes (qs3_probe_peaks):
+    fp64 / fp32 FMA, integer multiply-add and xor/add per second (thread
+    operations), warp instructions issued per second and the SM count."""
+    p = _abi.qs3_peaks()
+    check(load().qs3_probe_peaks(ctypes.byref(p), _stream(stream)), "qs3_probe_peaks")
+    return {f: getattr(p, f) for f, _ in p._fields_ if f != "reserved"}
+
+
+def inject_alloc_failure(after: int) -> int:
+    """qs3_inject_alloc_failure: let `after` more device allocations of the
+    library succeed and fail every later one with QS3_ERR_OOM (after < 0:
+    off).  Returns the previous setting."""
+    return int(load().qs3_inject_alloc_failure(int(after)))
 
 
 def _info_dict(info: _abi.qs3_solve_info) -> dict:
@@ -178,21 +206,26 @@ class Basis:
             self._nnz = v.value
         return self._nnz
 
-    def tuning(self, hphi_blocks_per_sm=None, dot_vectors=None) -> dict:
+    def tuning(self, hphi_blocks_per_sm=None, dot_vectors=None, dot_vectors64=None) -> dict:
         """Autotuned launch choices: query (no arguments) or impose them
-        (hphi_blocks_per_sm: up to 5 values indexed by dtype code; 0 = tune again)."""
+        (hphi_blocks_per_sm: up to 5 values indexed by dtype code; 0 = tune again;
+        dot_vectors: double-float dot products; dot_vectors64: binary64 ones)."""
         hb = (ctypes.c_int32 * 5)()
         dv = ctypes.c_int32(0)
-        if hphi_blocks_per_sm is not None or dot_vectors is not None:
-            check(load().qs3_basis_tuning(self._h, 0, hb, ctypes.byref(dv)), "qs3_basis_tuning")
+        dv64 = ctypes.c_int32(0)
+        args = (hb, ctypes.byref(dv), ctypes.byref(dv64))
+        if hphi_blocks_per_sm is not None or dot_vectors is not None or dot_vectors64 is not None:
+            check(load().qs3_basis_tuning(self._h, 0, *args), "qs3_basis_tuning")
             if hphi_blocks_per_sm is not None:
                 for i, v in enumerate(hphi_blocks_per_sm):
                     hb[i] = int(v)
             if dot_vectors is not None:
                 dv.value = int(dot_vectors)
-            check(load().qs3_basis_tuning(self._h, 1, hb, ctypes.byref(dv)), "qs3_basis_tuning")
-        check(load().qs3_basis_tuning(self._h, 0, hb, ctypes.byref(dv)), "qs3_basis_tuning")
-        return {"hphi_blocks_per_sm": list(hb), "dot_vectors": dv.value}
+            if dot_vectors64 is not None:
+                dv64.value = int(dot_vectors64)
+            check(load().qs3_basis_tuning(self._h, 1, *args), "qs3_basis_tuning")
+        check(load().qs3_basis_tuning(self._h, 0, *args), "qs3_basis_tuning")
+        return {"hphi_blocks_per_sm": list(hb), "dot_vectors": dv.value, "dot_vectors64": dv64.value}
 
     def full_diag(self, s: int = 0, vectors: bool = False, stream=None):
         """All eigenvalues (ascending) of sector s, and optionally the eigenvectors

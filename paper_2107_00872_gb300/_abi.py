@@ -25,14 +25,19 @@ class qs3_lattice(ctypes.Structure):
 class qs3_solve_opts(ctypes.Structure):
     _fields_ = [("n_eig", I32), ("n_keep", I32), ("n_max", I32), ("max_iter", I32), ("min_iter", I32),
                 ("check_every", I32), ("eps", F64), ("precision", I32), ("use_graphs", I32), ("seed", U64),
-                ("refine_tol", F64), ("res_tol", F64), ("hphi_ieee", I32), ("reserved", I32)]
+                ("refine_tol", F64), ("res_tol", F64), ("hphi_ieee", I32), ("strict64", I32)]
 
 
 class qs3_solve_info(ctypes.Structure):
     _fields_ = [("iterations", I32), ("restarts", I32), ("converged", I32), ("refine_iterations", I32),
                 ("max_residual", F64), ("seconds", F64), ("hphi_nnz", U64), ("hphi_seconds", F64),
                 ("hphi_calls", I32), ("hphi_graph_calls", I32), ("gs_dot_seconds", F64), ("gs_dot_bytes", U64),
-                ("gs_dot_calls", I32), ("reserved", I32)]
+                ("gs_dot_calls", I32), ("reserved", I32), ("gs_dot_fma", U64)]
+
+
+class qs3_peaks(ctypes.Structure):
+    _fields_ = [("fp64_fma_per_s", F64), ("fp32_fma_per_s", F64), ("int_mad_per_s", F64), ("int_alu_per_s", F64),
+                ("issue_per_s", F64), ("n_sms", I32), ("reserved", I32)]
 
 
 # name -> (argtypes, restype); every entry point declared in include/qs3.h
@@ -44,7 +49,7 @@ SIGNATURES = {
     "qs3_basis_ranks": ([P, I32, P, P], I32),
     "qs3_basis_nnz": ([P, P], I32),
     "qs3_basis_rep_table": ([P, I32, P], I32),
-    "qs3_basis_tuning": ([P, I32, P, P], I32),
+    "qs3_basis_tuning": ([P, I32, P, P, P], I32),
     "qs3_basis_store_terms": ([P, I32, P], I32),
     "qs3_full_diag": ([P, I32, P, P, P], I32),
     "qs3_thermal": ([ctypes.c_int64, P, P, P, I32, P, P, P], I32),
@@ -59,6 +64,8 @@ SIGNATURES = {
     "qs3_dsf": ([P, I32, P, F64, P, I32, P, I32, F64, F64, I32, P, P, P, P, P, P], I32),
     "qs3_sq_apply": ([I32, P, I32, P, P, I32, P, P, P], I32),
     "qs3_dsf_op": ([I32, I32, P, I32, P, F64, P, I32, P, I32, F64, F64, I32, P, P, P, P, P, P], I32),
+    "qs3_probe_peaks": ([P, P], I32),
+    "qs3_inject_alloc_failure": ([ctypes.c_int64], ctypes.c_int64),
     "qs3_strerror": ([I32], ctypes.c_char_p),
     "qs3_last_error": ([], ctypes.c_char_p),
     "qs3_version": ([], ctypes.c_char_p),

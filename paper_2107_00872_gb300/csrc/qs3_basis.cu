@@ -53,9 +53,17 @@ void DevBuf::release() {
     n = 0;
 }
 
+// allocation fault injection (qs3_inject_alloc_failure): the number of
+// allocations still allowed to succeed, or -1 when off
+static std::atomic<long long> g_alloc_budget{-1};
+
 int DevBuf::alloc(size_t bytes) {
     release();
     if (bytes == 0) bytes = 16;
+    for (long long b = g_alloc_budget.load(); b >= 0;) {
+        if (b == 0) return set_err(QS3_ERR_OOM, "device allocation of %zu bytes refused (injected failure)", bytes);
+        if (g_alloc_budget.compare_exchange_weak(b, b - 1)) break;
+    }
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -799,25 +807,33 @@ int qs3_basis_rep_table(qs3_basis_t b, int32_t mode, int32_t *active) {
     return st;
 }
 
-int qs3_basis_tuning(qs3_basis_t b, int32_t set, int32_t *hphi_blocks_per_sm, int32_t *dot_vectors) {
+int qs3_basis_tuning(qs3_basis_t b, int32_t set, int32_t *hphi_blocks_per_sm, int32_t *dot_vectors,
+                     int32_t *dot_vectors64) {
     clear_err();
     if (!b) return set_err(QS3_ERR_INVALID_ARG, "basis is NULL");
     Basis &B = b->B;
+    auto nv_ok = [](const int32_t *v) { return !v || *v == 0 || *v == 1 || *v == 2 || *v == 4; };
     if (set) {
         if (hphi_blocks_per_sm)
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 5; ++i)
                 if (hphi_blocks_per_sm[i] < 0) return set_err(QS3_ERR_INVALID_ARG, "blocks per SM %d", hphi_blocks_per_sm[i]);
-        if (dot_vectors && !(*dot_vectors == 0 || *dot_vectors == 1 || *dot_vectors == 2 || *dot_vectors == 4))
-            return set_err(QS3_ERR_INVALID_ARG, "dot vectors per pass %d", *dot_vectors);
+        if (!nv_ok(dot_vectors)) return set_err(QS3_ERR_INVALID_ARG, "dot vectors per pass %d", *dot_vectors);
+        if (!nv_ok(dot_vectors64)) return set_err(QS3_ERR_INVALID_ARG, "dot vectors per pass %d", *dot_vectors64);
         if (hphi_blocks_per_sm)
             for (int i = 0; i < 5; ++i) B.tune_hphi[i] = hphi_blocks_per_sm[i];
         if (dot_vectors) B.tune_nv = *dot_vectors;
+        if (dot_vectors64) B.tune_nv64 = *dot_vectors64;
     } else {
         if (hphi_blocks_per_sm)
             for (int i = 0; i < 5; ++i) hphi_blocks_per_sm[i] = B.tune_hphi[i];
         if (dot_vectors) *dot_vectors = B.tune_nv;
+        if (dot_vectors64) *dot_vectors64 = B.tune_nv64;
     }
     return QS3_OK;
+}
+
+int64_t qs3_inject_alloc_failure(int64_t after) {
+    return (int64_t)qs3::g_alloc_budget.exchange(after < 0 ? -1 : (long long)after);
 }
 
 const char *qs3_last_error(void) { return qs3::last_err(); }

@@ -1,0 +1,728 @@
+// qs3_engine64.cuh -- the IEEE binary64 Lanczos engine of fp64 solves
+// (included by qs3_solver.cu after the kernels it reuses).
+//
+// Alg. 10 in the paper's arithmetic, complex double (k-sectors) or double
+// (U(1)-only bases): every Lanczos vector, every product H psi_x and every
+// Gram-Schmidt operand is an IEEE binary64 value, and every operation on
+// them is a binary64 fused multiply-add (the fp64 pipe).
+//
+// Layout.  The Krylov basis is kept as binary64 values split into their high
+// and low 32-bit words, stored in two planes per vector (word-planar): slot j
+// holds D high words (complex: (re.hi, im.hi) pairs) and then D low words.
+// A value is reassembled bit for bit from its two words; the planes only let
+// a pass that needs no more than the high words read half the bytes.  The
+// product H psi_x reads an interleaved copy of psi_x (hin) written together
+// with slot x.
+//
+// One step (Alg. 10 lines 5-11, full reorthogonalisation):
+//   w = H psi_x;  three-term part: c_j = psi_j^H w for j = x-1, x (alpha_x
+//   among them), w -= sum_j c_j psi_j;  one classical Gram-Schmidt pass:
+//   g_j = psi_j^H w for j = 0..x, w -= sum_j g_j psi_j;  beta_x = |w|;
+//   psi_{x+1} = w / beta_x.
+// Dot products and updates are binary64 FMA chains per thread, reduced in a
+// fixed order (deterministic).  The one exception is the Gram-Schmidt
+// update whose coefficients are all tiny: when sum_j |g_j| <= 2^-36 |w|
+// (the normal case: w is already orthogonal to the basis to O(eps)), the
+// correction u = sum_j g_j psi_j is summed in fp32 from the high words
+// (20-bit significands, relative error < 2^-19 per term), so |error of u| <=
+// 2^-19 * 2^-36 |w| = 2^-55 |w|, below half an ulp of binary64 applied to
+// |w|; w - u is then formed in binary64.  The solve option strict64 keeps
+// that update on binary64 FMAs as well.
+#pragma once
+
+namespace qs3 {
+
+template <typename VT> struct PlS { using T = uint32_t; };     // real: one word per plane
+template <> struct PlS<double2> { using T = uint2; };          // complex: (re, im) words per plane
+
+__device__ __forceinline__ double2 pl_ld(const uint2 *slot, uint64_t D, uint64_t r) {
+    const uint2 h = slot[r], l = slot[D + r];
+    return make_double2(__hiloint2double((int)h.x, (int)l.x), __hiloint2double((int)h.y, (int)l.y));
+}
+__device__ __forceinline__ double2 pl_ld(const uint32_t *slot, uint64_t D, uint64_t r) {
+    return make_double2(__hiloint2double((int)slot[r], (int)slot[D + r]), 0.0);
+}
+__device__ __forceinline__ void pl_st(uint2 *slot, uint64_t D, uint64_t r, double2 v) {
+    slot[r] = make_uint2((unsigned)__double2hiint(v.x), (unsigned)__double2hiint(v.y));
+    slot[D + r] = make_uint2((unsigned)__double2loint(v.x), (unsigned)__double2loint(v.y));
+}
+__device__ __forceinline__ void pl_st(uint32_t *slot, uint64_t D, uint64_t r, double2 v) {
+    slot[r] = (unsigned)__double2hiint(v.x);
+    slot[D + r] = (unsigned)__double2loint(v.x);
+}
+// the high word of a binary64 as binary32: sign, exponent rebiased from 1023
+// to 127, the 20 significand bits it holds (truncated); magnitudes outside
+// the binary32 normal range give 0 (Lanczos vectors have norm 1, so only
+// values below 2^-126 do, and they are dropped with an error below 2^-126)
+__device__ __forceinline__ float hi_f(uint32_t h) {
+    const uint32_t e = (h >> 20) & 0x7ffu;
+    const uint32_t f = (((h & 0x7fffffffu) << 3) - (896u << 23)) | (h & 0x80000000u);
+    return (e - 897u < 254u) ? __uint_as_float(f) : 0.f;
+}
+__device__ __forceinline__ float2 pl_ld_hi(const uint2 *slot, uint64_t r) {
+    const uint2 h = slot[r];
+    return make_float2(hi_f(h.x), hi_f(h.y));
+}
+__device__ __forceinline__ float2 pl_ld_hi(const uint32_t *slot, uint64_t r) { return make_float2(hi_f(slot[r]), 0.f); }
+
+// part[c * m + j] = conj(V_{j0+j}) . w over chunk c (binary64 FMAs); V the
+// word-planar store (slots of 2D words-per-element units), w interleaved.
+// Vectors go in groups of 8 (partial sums of a group meet in shared memory,
+// warp q reduces vector q); NV vectors per pass have their loads in flight
+// together.  Graph mode (dx): the range of graph_range.
+template <typename VT, int NV>
+__global__ void __launch_bounds__(NTHREADS, NV == 1 ? 3 : NV == 2 ? 2 : 1)
+    k_dot64(const typename PlS<VT>::T *__restrict__ V, uint64_t D, int j0, int m, const VT *__restrict__ w,
+            const SecView *__restrict__ secs, const int *__restrict__ chunk0, int S, const int *__restrict__ active,
+            double2 *__restrict__ part, const int *__restrict__ dx = nullptr, int ring = 0) {
+    using T = typename PlS<VT>::T;
+    constexpr bool CX = IsC<VT>::v;
+    __shared__ double2 red[GDF][NTHREADS];
+    graph_range(dx, ring, j0, m);
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (ci.n - (int)threadIdx.x + NTHREADS - 1) / NTHREADS;     // rows of this thread
+    const uint64_t r0 = ci.base + threadIdx.x;
+    double2 wv[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) wv[k] = k < nk ? ld2(w + r0 + (uint64_t)k * NTHREADS) : make_double2(0.0, 0.0);
+    for (int jb = 0; jb < m; jb += GDF) {
+        const int nj = min(GDF, m - jb);
+        for (int jj = 0; jj < nj; jj += NV) {
+            double2 a[NV][RPT];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const int jv = jj + v < nj ? jj + v : nj - 1;      // past the group: a repeat, discarded
+                const T *slot = V + (uint64_t)(j0 + jb + jv) * 2 * D;
+#pragma unroll
+                for (int k = 0; k < RPT; ++k)
+                    a[v][k] = k < nk ? pl_ld(slot, D, r0 + (uint64_t)k * NTHREADS) : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+                for (int k = 0; k < RPT; ++k) {
+                    const double2 x = a[v][k], b = wv[k];
+                    // conj(x) b = (x.r b.r + x.i b.i) + i (x.r b.i - x.i b.r)
+                    acc.x = fma(x.x, b.x, acc.x);
+                    if (CX) {
+                        acc.x = fma(x.y, b.y, acc.x);
+                        acc.y = fma(x.x, b.y, acc.y);
+                        acc.y = fma(-x.y, b.x, acc.y);
+                    }
+                }
+                if (jj + v < nj) red[jj + v][threadIdx.x] = acc;
+            }
+        }
+        __syncthreads();
+        if (warp < nj) {
+            double2 t = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int q = 0; q < NTHREADS / 32; ++q) {
+                const double2 v = red[warp][lane + 32 * q];
+                t.x += v.x;
+                t.y += v.y;
+            }
+            t = warp_sum2(t);
+            if (lane == 0) part[(uint64_t)blockIdx.x * m + jb + warp] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// out[s * ldo + j] = sum over the chunks of sector s of part[c * m + j], one
+// warp per coefficient (graph mode: the range of graph_range, written from
+// out + j0)
+__global__ void k_reduce64(const double2 *__restrict__ part, int m, const int *__restrict__ chunk0,
+                           const int *__restrict__ active, double2 *__restrict__ out, int ldo,
+                           const int *__restrict__ dx = nullptr, int ring = 0) {
+    const int s = blockIdx.y;
+    if (dx) {
+        int j0 = 0;
+        graph_range(dx, ring, j0, m);
+        out += j0;
+    }
+    if (active && !active[s]) return;
+    const int wpb = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < m; j += gridDim.x * wpb) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int c = chunk0[s] + lane; c < chunk0[s + 1]; c += 32) {
+            const double2 v = part[(uint64_t)c * m + j];
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+        acc = warp_sum2(acc);
+        if (lane == 0) out[(uint64_t)s * ldo + j] = acc;
+    }
+}
+
+// w -= sum_j V_{j0+j} coef[s][j] (binary64 FMAs from w), and part[c] = |w|^2
+// over chunk c.  With wn2 (|w|^2 before the update) and strict == 0, a sector
+// whose coefficients satisfy (sum_j |re c_j| + |im c_j|)^2 <= 2^-72 |w|^2
+// forms the correction in fp32 from the high words instead (see the file
+// head for the bound).  Graph mode (dx): the range of graph_range, and for
+// the three-term pass (ring) the coefficients from coef + j0.
+template <typename VT>
+__global__ void __launch_bounds__(NTHREADS)
+    k_upd64(VT *__restrict__ w, const typename PlS<VT>::T *__restrict__ V, uint64_t D, int j0, int m,
+            const double2 *__restrict__ coef, int ldc, const SecView *__restrict__ secs,
+            const int *__restrict__ chunk0, int S, const int *__restrict__ active, const double2 *__restrict__ wn2,
+            int strict, double2 *__restrict__ part, const int *__restrict__ dx = nullptr, int ring = 0) {
+    using T = typename PlS<VT>::T;
+    constexpr bool CX = IsC<VT>::v;
+    if (dx) {
+        graph_range(dx, ring, j0, m);
+        if (ring) coef += j0;
+    }
+    extern __shared__ double2 scd[];              // m coefficients, then m fp32 copies
+    float2 *scf = (float2 *)(scd + m);
+    __shared__ double red[NTHREADS / 32];
+    __shared__ int lite_s;
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double cs = 0.0;
+    for (int j = threadIdx.x; j < m; j += NTHREADS) {
+        const double2 c = coef[(uint64_t)ci.s * ldc + j];
+        scd[j] = c;
+        scf[j] = make_float2((float)c.x, (float)c.y);
+        cs += fabs(c.x) + fabs(c.y);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+    if (lane == 0) red[warp] = cs;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < NTHREADS / 32; ++q) t += red[q];
+        lite_s = (!strict && wn2 && t * t <= 0x1p-72 * wn2[ci.s].x) ? 1 : 0;
+    }
+    __syncthreads();
+    const bool lite = lite_s != 0;
+    const int nk = (ci.n - (int)threadIdx.x + NTHREADS - 1) / NTHREADS;
+    const uint64_t r0 = ci.base + threadIdx.x;
+    double nrm = 0.0;
+    if (lite) {
+        float2 u[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) u[k] = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int j = 0; j < m; ++j) {
+            const float2 c = scf[j];
+            const T *slot = V + (uint64_t)(j0 + j) * 2 * D;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                if (k < nk) {
+                    const float2 a = pl_ld_hi(slot, r0 + (uint64_t)k * NTHREADS);
+                    // u += a c: re += a.r c.r - a.i c.i ; im += a.r c.i + a.i c.r
+                    u[k].x = fmaf(a.x, c.x, u[k].x);
+                    if (CX) {
+                        u[k].x = fmaf(-a.y, c.y, u[k].x);
+                        u[k].y = fmaf(a.x, c.y, u[k].y);
+                        u[k].y = fmaf(a.y, c.x, u[k].y);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (k < nk) {
+                const uint64_t r = r0 + (uint64_t)k * NTHREADS;
+                double2 v = ld2(w + r);
+                v.x -= (double)u[k].x;
+                if (CX) v.y -= (double)u[k].y;
+                st2(w + r, v);
+                nrm = fma(v.x, v.x, nrm);
+                if (CX) nrm = fma(v.y, v.y, nrm);
+            }
+        }
+    } else {
+        double2 acc[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) acc[k] = k < nk ? ld2(w + r0 + (uint64_t)k * NTHREADS) : make_double2(0.0, 0.0);
+#pragma unroll 2
+        for (int j = 0; j < m; ++j) {
+            const double2 c = scd[j];
+            const T *slot = V + (uint64_t)(j0 + j) * 2 * D;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                if (k < nk) {
+                    const double2 a = pl_ld(slot, D, r0 + (uint64_t)k * NTHREADS);
+                    // w -= a c: re -= a.r c.r - a.i c.i ; im -= a.r c.i + a.i c.r
+                    acc[k].x = fma(-a.x, c.x, acc[k].x);
+                    if (CX) {
+                        acc[k].x = fma(a.y, c.y, acc[k].x);
+                        acc[k].y = fma(-a.x, c.y, acc[k].y);
+                        acc[k].y = fma(-a.y, c.x, acc[k].y);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (k < nk) {
+                st2(w + r0 + (uint64_t)k * NTHREADS, acc[k]);
+                nrm = fma(acc[k].x, acc[k].x, nrm);
+                if (CX) nrm = fma(acc[k].y, acc[k].y, nrm);
+            }
+        }
+    }
+    if (part) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        __syncthreads();                          // red is reused
+        if (lane == 0) red[warp] = nrm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < NTHREADS / 32; ++q) t += red[q];
+            part[blockIdx.x] = make_double2(t, 0.0);
+        }
+    }
+}
+
+// psi_{x+1} = w * inv[s]: into the store's slot (graph mode: slot *dx + 1 of
+// the store at out) and into hin, the interleaved input of the next H Phi.
+// w may alias hin (the start vector is normalised in place).
+template <typename VT>
+__global__ void __launch_bounds__(NTHREADS)
+    k_scale64(const VT *w, typename PlS<VT>::T *__restrict__ out, VT *hin, const double *__restrict__ inv,
+              const SecView *__restrict__ secs, const int *__restrict__ chunk0, int S, const int *__restrict__ active,
+              const int *__restrict__ dx, uint64_t D) {
+    if (dx) out += (uint64_t)(*dx + 1) * 2 * D;
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    const double f = inv[ci.s];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r < ci.n) {
+            double2 v = ld2(w + ci.base + r);
+            v.x *= f;
+            v.y *= f;
+            pl_st(out, D, ci.base + r, v);
+            st2(hin + ci.base + r, v);
+        }
+    }
+}
+
+// out_y[r] = sum_x V_x[r] C[s][x][y] (binary64 FMAs), y < nout <= MAXOUT, for
+// the rows of sectors with mask[s] != 0.  PLO: out is the store (output y in
+// slot y of out); else out holds interleaved fp64 vectors ldo apart.
+template <typename VT, bool PLO>
+__global__ void __launch_bounds__(NTHREADS)
+    k_comb64(void *__restrict__ outp, uint64_t ldo, const typename PlS<VT>::T *__restrict__ V, uint64_t D, int nin,
+             int nout, const double *__restrict__ C, int ldc, const SecView *__restrict__ secs,
+             const int *__restrict__ chunk0, int S, const int *__restrict__ mask) {
+    using T = typename PlS<VT>::T;
+    extern __shared__ double sc[];
+    __shared__ int nx;
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (mask && !mask[ci.s]) return;
+    const double *Cs = C + (uint64_t)ci.s * ldc;
+    if (threadIdx.x == 0) nx = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nin * nout; i += blockDim.x) {
+        sc[i] = Cs[i];
+        if (Cs[i] != 0.0) atomicMax(&nx, i / nout + 1);
+    }
+    __syncthreads();
+    nin = nx;      // vectors past the sector's last nonzero coefficient may be unwritten
+    if (nout == 1) {
+        // one output: each thread's rows in registers, all their loads of a
+        // stored vector in flight together
+        const int nk = (ci.n - (int)threadIdx.x + NTHREADS - 1) / NTHREADS;
+        const uint64_t r0 = ci.base + threadIdx.x;
+        double2 acc[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) acc[k] = make_double2(0.0, 0.0);
+        for (int x = 0; x < nin; ++x) {
+            const double c = sc[x];
+            const T *slot = V + (uint64_t)x * 2 * D;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                if (k < nk) {
+                    const double2 a = pl_ld(slot, D, r0 + (uint64_t)k * NTHREADS);
+                    acc[k].x = fma(a.x, c, acc[k].x);
+                    acc[k].y = fma(a.y, c, acc[k].y);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            if (k < nk) {
+                const uint64_t r = r0 + (uint64_t)k * NTHREADS;
+                if constexpr (PLO) pl_st((T *)outp, D, r, acc[k]);
+                else st2((VT *)outp + r, acc[k]);
+            }
+        }
+        return;
+    }
+#pragma unroll 1
+    for (int k = 0; k < RPT; ++k) {
+        const int r = threadIdx.x + k * NTHREADS;
+        if (r >= ci.n) continue;
+        double2 acc[MAXOUT];
+#pragma unroll
+        for (int y = 0; y < MAXOUT; ++y) acc[y] = make_double2(0.0, 0.0);
+        for (int x = 0; x < nin; ++x) {
+            const double2 a = pl_ld(V + (uint64_t)x * 2 * D, D, ci.base + r);
+#pragma unroll
+            for (int y = 0; y < MAXOUT; ++y)
+                if (y < nout) {
+                    const double c = sc[x * nout + y];
+                    acc[y].x = fma(a.x, c, acc[y].x);
+                    acc[y].y = fma(a.y, c, acc[y].y);
+                }
+        }
+#pragma unroll
+        for (int y = 0; y < MAXOUT; ++y)
+            if (y < nout) {
+                if constexpr (PLO) pl_st((T *)outp + (uint64_t)y * 2 * D, D, ci.base + r, acc[y]);
+                else st2((VT *)outp + (uint64_t)y * ldo + ci.base + r, acc[y]);
+            }
+    }
+}
+
+// ------------------------------------------------------------------ engine
+template <typename VT>
+struct Engine64 {
+    using WT = VT;                         // result vectors are binary64 as well
+    using ST = typename PlS<VT>::T;        // word of the planar store
+    Basis &B;
+    cudaStream_t st;
+    HphiStats *stats;
+    int cap = 0, nscr = 0;
+    uint64_t D = 0;
+    DevBuf V, wbuf, hinb, part, h1, h2, alpha, beta, nrm, nrm1, inv, active;
+    std::vector<int> h_active;
+    double brk = 1e-12;
+    int strict = 0;                        // 1: every update on binary64 FMAs
+    bool graphs = false;
+    DevBuf xdev;
+    int xdev_val = -1;
+    cudaStream_t cs = nullptr;
+    cudaGraphExec_t gx = nullptr;
+    long long gnodes = 0;
+
+    Engine64(Basis &b, cudaStream_t s, HphiStats *hs) : B(b), st(s), stats(hs) {}
+    ~Engine64() {
+        if (gx) cudaGraphExecDestroy(gx);
+        if (cs) cudaStreamDestroy(cs);
+    }
+    Engine64(const Engine64 &) = delete;
+    Engine64 &operator=(const Engine64 &) = delete;
+    void use_df_hphi(bool) {}
+    void set_strict(bool on) { strict = on ? 1 : 0; }
+    int enable_graphs(bool on) {
+        graphs = on && B.nchunks > 0;
+        if (graphs && !xdev.p) QS3_TRY(xdev.alloc(sizeof(int)));
+        return QS3_OK;
+    }
+    qs3_dtype dtype() const { return IsC<VT>::v ? QS3_C128 : QS3_F64; }
+    // slot j of the store (2 D words-per-element units)
+    ST *svec(int j) { return V.as<ST>() + (uint64_t)j * 2 * D; }
+    size_t slot_bytes() const { return (size_t)D * sizeof(VT); }
+    VT *hin(int) { return hinb.as<VT>(); }
+    VT *wv() { return wbuf.as<VT>(); }
+    const SecView *secs() { return B.d_secs.as<SecView>(); }
+    const int *c0() { return B.d_chunk0.as<int>(); }
+    int *act() { return active.as<int>(); }
+    int grid() const { return std::max(B.nchunks, 1); }
+
+    int init(int cap_, int nscratch) {
+        cap = cap_;
+        nscr = nscratch;
+        D = B.total;
+        QS3_TRY(V.alloc((uint64_t)(cap + nscr) * D * sizeof(VT)));
+        QS3_TRY(wbuf.alloc(std::max<uint64_t>(D, 1) * sizeof(VT)));
+        QS3_TRY(hinb.alloc(std::max<uint64_t>(D, 1) * sizeof(VT)));
+        QS3_TRY(part.alloc((uint64_t)std::max(B.nchunks, 1) * cap * sizeof(double2)));
+        QS3_TRY(h1.alloc((uint64_t)B.S * cap * sizeof(double2)));
+        QS3_TRY(h2.alloc((uint64_t)B.S * cap * sizeof(double2)));
+        QS3_TRY(alpha.alloc((uint64_t)B.S * cap * sizeof(double)));
+        QS3_TRY(beta.alloc((uint64_t)B.S * cap * sizeof(double)));
+        QS3_TRY(nrm.alloc((uint64_t)B.S * sizeof(double2)));
+        QS3_TRY(nrm1.alloc((uint64_t)B.S * sizeof(double2)));
+        QS3_TRY(inv.alloc((uint64_t)B.S * sizeof(double)));
+        QS3_TRY(active.alloc((uint64_t)B.S * sizeof(int)));
+        QS3_CUDA(cudaMemsetAsync(alpha.p, 0, alpha.n, st));
+        QS3_CUDA(cudaMemsetAsync(beta.p, 0, beta.n, st));
+        h_active.assign(B.S, 0);
+        for (int s = 0; s < B.S; ++s) h_active[s] = B.dims[s] > 0;
+        QS3_TRY(push_active());
+        return tune_dots();
+    }
+    int push_active() {
+        QS3_CUDA(cudaMemcpyAsync(active.p, h_active.data(), B.S * sizeof(int), cudaMemcpyHostToDevice, st));
+        return QS3_OK;
+    }
+    bool any_active() const {
+        for (int a : h_active) if (a) return true;
+        return false;
+    }
+    int reduce(int m, double2 *out, int ldo, const int *dx = nullptr, int ring = 0, int mgrid = 0) {
+        const int mg = mgrid > 0 ? mgrid : m;
+        k_reduce64<<<dim3((mg + 7) / 8, B.S), NTHREADS, 0, st>>>(part.as<double2>(), m, c0(), act(), out, ldo, dx,
+                                                                 ring);
+        QS3_LAUNCHED();
+        return QS3_OK;
+    }
+    // k_dot64 with nv stored vectors per pass (1, 2 or 4)
+    int dot_launch(int nv, int j0, int m, const int *dx = nullptr, int ring = 0) {
+        const ST *v = V.as<ST>();
+        double2 *pp = part.as<double2>();
+        const VT *w = wv();
+        if (ring || (!dx && m <= 2)) nv = std::min(nv, 2);
+        if (nv == 1)
+            k_dot64<VT, 1><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx, ring);
+        else if (nv == 4)
+            k_dot64<VT, 4><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx, ring);
+        else
+            k_dot64<VT, 2><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx, ring);
+        QS3_LAUNCHED();
+        return QS3_OK;
+    }
+    // dot products of w against stored vectors j0 .. j0 + m - 1 into out (S x ldo)
+    int mdot(int j0, int m, double2 *out, int ldo) {
+        if (B.nchunks == 0) return QS3_OK;
+        QS3_TRY(dot_launch(B.tune_nv64 > 0 ? B.tune_nv64 : 2, j0, m));
+        return reduce(m, out, ldo);
+    }
+    // the staging depth of k_dot64: time 1, 2 and 4 vectors per pass on
+    // min(cap, 48) zeroed slots and keep the fastest for this basis
+    int tune_dots() {
+        if (B.tune_nv64 != 0 || B.nchunks == 0) return QS3_OK;
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        QS3_CUDA(cudaStreamIsCapturing(st, &cst));
+        if (cst != cudaStreamCaptureStatusNone) return QS3_OK;
+        const int m = std::min(cap, 48);
+        QS3_CUDA(cudaMemsetAsync(V.p, 0, (size_t)m * slot_bytes(), st));
+        QS3_CUDA(cudaMemsetAsync(wbuf.p, 0, wbuf.n, st));
+        cudaEvent_t e0, e1;
+        QS3_CUDA(cudaEventCreate(&e0));
+        QS3_CUDA(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int bnv = 2, rc = QS3_OK;
+        for (int nv : {1, 2, 4}) {
+            float tmin = 1e30f;
+            for (int rep = 0; rep < 4 && rc == QS3_OK; ++rep) {
+                if (cudaEventRecord(e0, st) != cudaSuccess) { rc = QS3_ERR_CUDA; break; }
+                rc = dot_launch(nv, 0, m);
+                if (rc != QS3_OK) break;
+                if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = QS3_ERR_CUDA;
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tmin = std::min(tmin, ms);
+            }
+            if (tmin < best) { best = tmin; bnv = nv; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc != QS3_OK) return set_err(rc, "dot-product autotuning failed");
+        B.tune_nv64 = bnv;
+        return QS3_OK;
+    }
+    // w -= sum_j psi_{j0+j} cf[s][j]; nrm_out: per-sector |w|^2 after it;
+    // wn2: |w|^2 before it (enables the fp32 correction of tiny coefficients)
+    int mupdate(int j0, int m, const double2 *cf, int ldc, double2 *nrm_out, const double2 *wn2 = nullptr) {
+        if (B.nchunks == 0) return QS3_OK;
+        k_upd64<VT><<<grid(), NTHREADS, (size_t)m * (sizeof(double2) + sizeof(float2)), st>>>(
+            wv(), V.as<ST>(), D, j0, m, cf, ldc, secs(), c0(), B.S, act(), wn2, strict, part.as<double2>());
+        QS3_LAUNCHED();
+        return reduce(1, nrm_out, 1);
+    }
+    // psi_j = w * inv (per sector) into slot j and hin
+    int scale_store(const VT *w, int j) {
+        if (B.nchunks == 0) return QS3_OK;
+        k_scale64<VT><<<grid(), NTHREADS, 0, st>>>(w, svec(j), hin(0), inv.as<double>(), secs(), c0(), B.S, act(),
+                                                   nullptr, D);
+        QS3_LAUNCHED();
+        return QS3_OK;
+    }
+    // normalise the start vector in hin per sector and store it as psi_0
+    int normalise_start() {
+        if (B.nchunks == 0) return QS3_OK;
+        k_norm2<VT><<<grid(), NTHREADS, 0, st>>>(hin(0), secs(), c0(), B.S, act(), part.as<double2>());
+        QS3_LAUNCHED();
+        QS3_TRY(reduce(1, nrm.as<double2>(), 1));
+        k_inv_sqrt<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, nrm.as<double2>(), inv.as<double>());
+        QS3_LAUNCHED();
+        return scale_store(hin(0), 0);
+    }
+    int start_random(uint64_t seed) {
+        if (B.nchunks == 0) return QS3_OK;
+        k_random<VT><<<grid(), NTHREADS, 0, st>>>(hin(0), seed, secs(), c0(), B.S);
+        QS3_LAUNCHED();
+        return normalise_start();
+    }
+    int start_from(const WT *src) {
+        if (B.nchunks == 0) return QS3_OK;
+        k_convert<VT, WT><<<grid(), NTHREADS, 0, st>>>(hin(0), src, secs(), c0(), B.S, nullptr);
+        QS3_LAUNCHED();
+        return normalise_start();
+    }
+    void count_hphi() {
+        stats->calls += 1;
+        for (int s = 0; s < B.S; ++s)
+            if (h_active[s]) stats->nnz += B.nnz_sec[s];
+    }
+    // the Gram-Schmidt dot pass against psi_0 .. psi_x, timed with events
+    int gs_dots(int x) {
+        std::pair<cudaEvent_t, cudaEvent_t> ev;
+        QS3_TRY(stats->pair(ev));
+        QS3_CUDA(cudaEventRecord(ev.first, st));
+        QS3_TRY(mdot(0, x + 1, h2.as<double2>(), cap));
+        QS3_CUDA(cudaEventRecord(ev.second, st));
+        stats->pend_gs.push_back(ev);
+        stats->gs_calls += 1;
+        uint64_t rows = 0;
+        for (int s = 0; s < B.S; ++s)
+            if (h_active[s]) rows += B.dims[s];
+        stats->gs_bytes += rows * ((uint64_t)(x + 2) * sizeof(VT));
+        stats->gs_fma += rows * (uint64_t)(x + 1) * (IsC<VT>::v ? 4 : 1);
+        return QS3_OK;
+    }
+    // one step with every x-dependent count and offset taken from xdev (the
+    // body of the captured graph; x >= 1, one Gram-Schmidt pass)
+    int step_body_dev() {
+        const int *dx = xdev.as<int>();
+        VT *w = wv();
+        double2 *hh1 = h1.as<double2>(), *n1 = nrm1.as<double2>();
+        QS3_TRY(hphi_launch(B, dtype(), hin(0), w, st, act()));
+        QS3_TRY(dot_launch(2, 0, 2, dx, 1));
+        QS3_TRY(reduce(2, hh1, cap, dx, 1, 2));
+        k_upd64<VT><<<grid(), NTHREADS, 2 * (sizeof(double2) + sizeof(float2)), st>>>(
+            w, V.as<ST>(), D, 0, 2, hh1, cap, secs(), c0(), B.S, act(), nullptr, strict, part.as<double2>(), dx, 1);
+        QS3_LAUNCHED();
+        QS3_TRY(reduce(1, n1, 1));
+        QS3_TRY(dot_launch(B.tune_nv64 > 0 ? B.tune_nv64 : 2, 0, cap, dx, 0));
+        QS3_TRY(reduce(cap, h2.as<double2>(), cap, dx, 0, cap));
+        k_upd64<VT><<<grid(), NTHREADS, (size_t)cap * (sizeof(double2) + sizeof(float2)), st>>>(
+            w, V.as<ST>(), D, 0, cap, h2.as<double2>(), cap, secs(), c0(), B.S, act(), n1, strict,
+            part.as<double2>(), dx, 0);
+        QS3_LAUNCHED();
+        QS3_TRY(reduce(1, nrm.as<double2>(), 1));
+        k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, 0, cap, hh1, nrm.as<double2>(), act(),
+                                                         alpha.as<double>(), beta.as<double>(), inv.as<double>(), brk,
+                                                         dx);
+        QS3_LAUNCHED();
+        k_scale64<VT><<<grid(), NTHREADS, 0, st>>>(w, V.as<ST>(), hin(0), inv.as<double>(), secs(), c0(), B.S, act(),
+                                                   dx, D);
+        QS3_LAUNCHED();
+        k_advance<<<1, 1, 0, st>>>(xdev.as<int>());
+        QS3_LAUNCHED();
+        return QS3_OK;
+    }
+    int graph_step(int x) {
+        if (!cs) QS3_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        if (!gx) {
+            cudaStream_t keep = st;
+            st = cs;
+            cudaGraph_t g = nullptr;
+            QS3_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            const int r = step_body_dev();
+            const cudaError_t e = cudaStreamEndCapture(cs, &g);
+            st = keep;
+            if (r != QS3_OK) {
+                if (g) cudaGraphDestroy(g);
+                return r;
+            }
+            if (e != cudaSuccess) return set_err(QS3_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+            size_t nn = 0;
+            cudaGraphGetNodes(g, nullptr, &nn);
+            const cudaError_t ei = cudaGraphInstantiate(&gx, g, 0);
+            cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                gx = nullptr;
+                return set_err(QS3_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ei));
+            }
+            gnodes = (long long)nn;
+            count_launch(-(long long)nn);   // the capture ran nothing
+        }
+        if (xdev_val != x) {
+            k_setx<<<1, 1, 0, st>>>(xdev.as<int>(), x);
+            QS3_LAUNCHED();
+        }
+        QS3_CUDA(cudaGraphLaunch(gx, st));
+        count_launch(gnodes);
+        xdev_val = x + 1;
+        return QS3_OK;
+    }
+    // Alg. 10 lines 5-11 for step x (full2: the first step after a thick
+    // restart, whose w has the arrowhead components beta_y psi_y: the first
+    // pass then runs against all of psi_0 .. psi_x)
+    int step(int x, bool full2 = false) {
+        if (graphs && !full2 && x >= 1) {
+            stats->graph_calls += 1;
+            count_hphi();
+            return graph_step(x);
+        }
+        VT *w = wv();
+        std::pair<cudaEvent_t, cudaEvent_t> ev;
+        QS3_TRY(stats->pair(ev));
+        QS3_CUDA(cudaEventRecord(ev.first, st));
+        QS3_TRY(hphi_launch(B, dtype(), hin(x), w, st, act()));
+        QS3_CUDA(cudaEventRecord(ev.second, st));
+        stats->pend.push_back(ev);
+        count_hphi();
+        const int j0 = full2 ? 0 : std::max(0, x - 1);
+        double2 *n1 = nrm1.as<double2>();
+        QS3_TRY(mdot(j0, x + 1 - j0, h1.as<double2>() + j0, cap));
+        QS3_TRY(mupdate(j0, x + 1 - j0, h1.as<double2>() + j0, cap, n1));
+        QS3_TRY(gs_dots(x));
+        QS3_TRY(mupdate(0, x + 1, h2.as<double2>(), cap, nrm.as<double2>(), n1));
+        k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, x, cap, h1.as<double2>(), nrm.as<double2>(), act(),
+                                                         alpha.as<double>(), beta.as<double>(), inv.as<double>(), brk);
+        QS3_LAUNCHED();
+        return scale_store(w, x + 1);
+    }
+    int fetch(std::vector<double> &a, std::vector<double> &b) {
+        a.resize((size_t)B.S * cap);
+        b.resize((size_t)B.S * cap);
+        QS3_CUDA(cudaMemcpyAsync(a.data(), alpha.p, a.size() * 8, cudaMemcpyDeviceToHost, st));
+        QS3_CUDA(cudaMemcpyAsync(b.data(), beta.p, b.size() * 8, cudaMemcpyDeviceToHost, st));
+        QS3_CUDA(cudaStreamSynchronize(st));
+        return stats->harvest();
+    }
+    // out_y = sum_x psi_x C[s][x][y] (x < nin, y < nout) for the sectors in
+    // mask; C on the host, S x (nin nout).  PLO: into store slots from out.
+    template <bool PLO>
+    int combine_to(void *out, uint64_t ldo, int nin, int nout, const std::vector<double> &C,
+                   const std::vector<int> &mask) {
+        if (B.nchunks == 0) return QS3_OK;
+        if (nout > MAXOUT) return set_err(QS3_ERR_INVALID_ARG, "at most %d vectors per combination", MAXOUT);
+        const int ldc = nin * nout;
+        DevBuf dC, dm;
+        QS3_TRY(dC.alloc(C.size() * 8));
+        QS3_TRY(dm.alloc(mask.size() * 4));
+        QS3_CUDA(cudaMemcpyAsync(dC.p, C.data(), C.size() * 8, cudaMemcpyHostToDevice, st));
+        QS3_CUDA(cudaMemcpyAsync(dm.p, mask.data(), mask.size() * 4, cudaMemcpyHostToDevice, st));
+        k_comb64<VT, PLO><<<grid(), NTHREADS, ldc * sizeof(double), st>>>(out, ldo, V.as<ST>(), D, nin, nout,
+                                                                          dC.as<double>(), ldc, secs(), c0(), B.S,
+                                                                          dm.as<int>());
+        QS3_LAUNCHED();
+        QS3_CUDA(cudaStreamSynchronize(st));     // dC/dm are released on return
+        return QS3_OK;
+    }
+    template <typename OT>
+    int combine(OT *out, uint64_t ldo, int nin, int nout, const std::vector<double> &C, const std::vector<int> &mask) {
+        static_assert(std::is_same<OT, WT>::value, "results are binary64 vectors");
+        return combine_to<false>(out, ldo, nin, nout, C, mask);
+    }
+    // thick restart (Alg. 10 lines 14-19): psi_y = Psi C[:, y] for y < NK
+    // (through the scratch slots), psi_NK = psi_NM; hin already holds psi_NM
+    int thick_restart(int NM, int NK, const std::vector<double> &C) {
+        QS3_TRY(combine_to<true>(svec(cap), 0, NM, NK, C, h_active));
+        QS3_CUDA(cudaMemcpyAsync(svec(0), svec(cap), (size_t)NK * slot_bytes(), cudaMemcpyDeviceToDevice, st));
+        QS3_CUDA(cudaMemcpyAsync(svec(NK), svec(NM), slot_bytes(), cudaMemcpyDeviceToDevice, st));
+        return QS3_OK;
+    }
+};
+
+}  // namespace qs3

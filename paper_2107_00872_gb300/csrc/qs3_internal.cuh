@@ -156,6 +156,7 @@ struct Basis {
     // and basis vectors per pass of the double-float dot products
     int tune_hphi[5] = {0, 0, 0, 0, 0};     // indexed by qs3_dtype
     int tune_nv = 0;
+    int tune_nv64 = 0;                      // the same for the binary64 dot products (IEEE engine)
     bool narrow_ranks = false;              // U(1) with C(N, N_down) < 2^32: 32-bit rank kernels apply
     // stored terms of the k-sector H Phi (opt-in): row pointers, target rows,
     // codes (u | st << 12 | q << 16) and per-row diagonals

@@ -1202,6 +1202,7 @@ struct HphiStats {
     double gs_sec = 0.0;
     int gs_calls = 0;
     uint64_t gs_bytes = 0;
+    uint64_t gs_fma = 0;                  // binary64 FMAs of those launches (binary64 engine)
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pend, pend_gs, freel;
     ~HphiStats() {
         for (auto &p : pend) { cudaEventDestroy(p.first); cudaEventDestroy(p.second); }
@@ -1275,6 +1276,7 @@ struct Engine {
     float4 *wd() { return wdf.as<float4>(); }
     float4 *hd() { return hdf.as<float4>(); }
     void use_df_hphi(bool on) { dfh = on && DF && IsC<VT>::v && B.has_k && B.nd > 0; }
+    void set_strict(bool) {}
     // replay Lanczos steps as CUDA graphs (fp64 engine; ignored otherwise)
     int enable_graphs(bool on) {
         graphs = on && DF && B.nchunks > 0;
@@ -1750,7 +1752,22 @@ struct Engine {
         QS3_CUDA(cudaStreamSynchronize(st));     // dC/dm are released on return
         return QS3_OK;
     }
+    // thick restart (Alg. 10 lines 14-19): psi_y = Psi C[:, y] for y < NK
+    // (through the scratch slots), psi_NK = psi_NM (the fp64 ring of a DF
+    // engine, or H's double-float input, already holds psi_NM)
+    int thick_restart(int NM, int NK, const std::vector<double> &C) {
+        QS3_TRY(combine<ST>(svec(cap), B.total, NM, NK, C, h_active));
+        QS3_CUDA(cudaMemcpyAsync(svec(0), svec(cap), (size_t)NK * B.total * sizeof(ST), cudaMemcpyDeviceToDevice, st));
+        QS3_CUDA(cudaMemcpyAsync(svec(NK), svec(NM), (size_t)B.total * sizeof(ST), cudaMemcpyDeviceToDevice, st));
+        return QS3_OK;
+    }
 };
+
+}  // namespace qs3
+
+#include "qs3_engine64.cuh"
+
+namespace qs3 {
 
 // residual |H v - e v| of fp64 vectors (one per sector, concatenated); returns max over sectors
 template <typename WT>
@@ -1794,12 +1811,13 @@ struct LzResult {
 };
 
 // Lanczos to the lowest eigenpair of each sector; out (fp64, total dim) gets the vectors.
-template <typename VT>
+template <typename VT, typename EN = Engine<VT>>
 static int lanczos_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T *start,
                        typename Wide<VT>::T *out, cudaStream_t st, LzResult &R, HphiStats &hs) {
-    Engine<VT> E(B, st, &hs);
+    EN E(B, st, &hs);
     const int nmax = std::max(2, o.n_max);
     E.use_df_hphi(o.hphi_ieee == 0);
+    E.set_strict(o.strict64 != 0);
     QS3_TRY(E.init(nmax + 1, 0));
     QS3_TRY(E.enable_graphs(o.use_graphs != 0));
     if (start) QS3_TRY(E.start_from(start)); else QS3_TRY(E.start_random(o.seed));
@@ -1887,7 +1905,7 @@ struct TrlResult {
     int steps = 0, restarts = 0;
 };
 
-template <typename VT>
+template <typename VT, typename EN = Engine<VT>>
 static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T *start,
                    typename Wide<VT>::T *out, cudaStream_t st, TrlResult &R, HphiStats &hs) {
     using WT = typename Wide<VT>::T;
@@ -1896,8 +1914,9 @@ static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T
     const int NK = std::max(1, std::min(o.n_keep, NM - 1));
     const int NE = std::max(1, std::min(o.n_eig, NK));
     if (NK > MAXOUT) return set_err(QS3_ERR_INVALID_ARG, "n_keep %d > %d", NK, MAXOUT);
-    Engine<VT> E(B, st, &hs);
+    EN E(B, st, &hs);
     E.use_df_hphi(o.hphi_ieee == 0);
+    E.set_strict(o.strict64 != 0);
     QS3_TRY(E.init(NM + 1, NK));
     QS3_TRY(E.enable_graphs(o.use_graphs != 0));
     if (start) QS3_TRY(E.start_from(start)); else QS3_TRY(E.start_random(o.seed));
@@ -1974,11 +1993,7 @@ static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T
             for (int x = 0; x < NM; ++x)
                 for (int y = 0; y < NK; ++y) C[(size_t)s * NM * NK + x * NK + y] = Cm[s][(size_t)x * NM + y];
         }
-        // (the fp64 ring of a DF engine already holds psi_{N_M} as its current vector)
-        using ST = typename Engine<VT>::ST;
-        QS3_TRY(E.template combine<ST>(E.svec(E.cap), B.total, NM, NK, C, E.h_active));
-        QS3_CUDA(cudaMemcpyAsync(E.svec(0), E.svec(E.cap), (size_t)NK * B.total * sizeof(ST), cudaMemcpyDeviceToDevice, st));
-        QS3_CUDA(cudaMemcpyAsync(E.svec(NK), E.svec(NM), (size_t)B.total * sizeof(ST), cudaMemcpyDeviceToDevice, st));
+        QS3_TRY(E.thick_restart(NM, NK, C));
         // lines 20-26: Lanczos steps from psi_{N_K} (the Gram-Schmidt against psi_0..psi_{N_K}
         // removes the arrowhead couplings beta_y psi_y)
         for (int x = NK; x < NM; ++x) { QS3_TRY(E.step(x, x == NK)); ++steps; }
@@ -2062,12 +2077,14 @@ static int lanczos_entry(Basis &B, const qs3_solve_opts &o, double *evals, void 
         o2.min_iter = std::max(2, std::min(o.min_iter, o.check_every));
         if (o.refine_tol > 0) o2.eps = std::max(o.eps, 0.1 * o.refine_tol);
         LzResult R2;
-        QS3_TRY(lanczos_run<V64>(B, o2, out, out, st, R2, hs));
+        QS3_TRY((lanczos_run<V64, Engine64<V64>>(B, o2, out, out, st, R2, hs)));
         refine = R2.steps;
         iters += R2.steps;
         R = R2;
     } else {
-        QS3_TRY(lanczos_run<V64>(B, o, nullptr, out, st, R, hs));
+        // QS3_F64: the IEEE binary64 engine; QS3_C128DF: the double-float engine
+        if (o.precision == QS3_C128DF) QS3_TRY((lanczos_run<V64, Engine<V64>>(B, o, nullptr, out, st, R, hs)));
+        else QS3_TRY((lanczos_run<V64, Engine64<V64>>(B, o, nullptr, out, st, R, hs)));
         iters += R.steps;
     }
     for (int s = 0; s < B.S; ++s) evals[s] = R.e[s];
@@ -2091,6 +2108,7 @@ static int lanczos_entry(Basis &B, const qs3_solve_opts &o, double *evals, void 
         info->gs_dot_seconds = hs.gs_sec;
         info->gs_dot_bytes = hs.gs_bytes;
         info->gs_dot_calls = hs.gs_calls;
+        info->gs_dot_fma = hs.gs_fma;
     }
     return all_conv(R.conv) ? QS3_OK : set_err(QS3_ERR_NOT_CONVERGED, "Lanczos did not converge in %d steps", o.n_max);
 }
@@ -2150,13 +2168,14 @@ static int trl_entry(Basis &B, const qs3_solve_opts &o, double *evals, void *eve
         TrlResult R2;
         qs3_solve_opts o2 = o;
         if (o.refine_tol > 0) o2.eps = std::max(o.eps, 0.1 * o.refine_tol);
-        QS3_TRY(trl_run<V64>(B, o2, sum.as<V64>(), out, st, R2, hs));
+        QS3_TRY((trl_run<V64, Engine64<V64>>(B, o2, sum.as<V64>(), out, st, R2, hs)));
         refine = R2.steps;
         iters += R2.steps;
         restarts += R2.restarts;
         R = R2;
     } else {
-        QS3_TRY(trl_run<V64>(B, o, nullptr, out, st, R, hs));
+        if (o.precision == QS3_C128DF) QS3_TRY((trl_run<V64, Engine<V64>>(B, o, nullptr, out, st, R, hs)));
+        else QS3_TRY((trl_run<V64, Engine64<V64>>(B, o, nullptr, out, st, R, hs)));
         iters += R.steps;
         restarts += R.restarts;
     }
@@ -2187,6 +2206,7 @@ static int trl_entry(Basis &B, const qs3_solve_opts &o, double *evals, void *eve
         info->gs_dot_seconds = hs.gs_sec;
         info->gs_dot_bytes = hs.gs_bytes;
         info->gs_dot_calls = hs.gs_calls;
+        info->gs_dot_fma = hs.gs_fma;
     }
     return all_conv(R.conv) ? QS3_OK
                             : set_err(QS3_ERR_NOT_CONVERGED, "thick-restart Lanczos did not converge in %d restarts",
@@ -2198,7 +2218,7 @@ static int check_opts(const qs3_solve_opts *o) {
     if (o->n_max < 2 || o->n_max > 2048) return set_err(QS3_ERR_INVALID_ARG, "n_max %d outside [2, 2048]", o->n_max);
     if (o->check_every < 1) return set_err(QS3_ERR_INVALID_ARG, "check_every %d", o->check_every);
     if (!(o->eps > 0)) return set_err(QS3_ERR_INVALID_ARG, "eps %g", o->eps);
-    if (o->precision != QS3_F32 && o->precision != QS3_F64)
+    if (o->precision != QS3_F32 && o->precision != QS3_F64 && o->precision != QS3_C128DF)
         return set_err(QS3_ERR_INVALID_ARG, "precision %d", o->precision);
     return QS3_OK;
 }
@@ -2250,8 +2270,7 @@ int dsf_run(int op, Basis &S, int ss, const void *gs, double e0, Basis &Dd, int 
     uint64_t nz = 0;
     QS3_TRY(count_nnz(Dd, &nz));
     HphiStats hs;
-    Engine<double2> E(Dd, st, &hs);
-    E.use_df_hphi(true);
+    Engine64<double2> E(Dd, st, &hs);
     QS3_TRY(E.init(n_iter + 1, 0));
     for (int n = 0; n < nq; ++n)
         QS3_TRY(sq_launch(op, S, ss, gs, Dd, n, Q + 3 * n, E.hin(0) + Dd.offs[n], st));
@@ -2317,9 +2336,9 @@ static size_t solve_mem_estimate(const Basis &B, const qs3_solve_opts &o) {
     const size_t ev64 = B.has_k ? 16 : 8;
     const size_t cap = (size_t)std::max(2, o.n_max) + 1;
     size_t m = cap * B.total * ev + 2 * B.total * ev64 + (size_t)std::max(B.nchunks, 1) * cap * 16;
-    if (o.precision == QS3_F32) m += cap * B.total * ev64;   // the fp64 refinement
-    m += 3 * B.total * ev64;                                 // fp64 ring of the fp64 engine
-    if (B.has_k && !o.hphi_ieee) m += 2 * B.total * 16;      // double-float w and H's input copy
+    if (o.precision == QS3_F32) m += cap * B.total * ev64;   // the binary64 refinement
+    m += 3 * B.total * ev64;                                 // w, H's input copy (and the double-float ring)
+    if (B.has_k && o.precision == QS3_C128DF && !o.hphi_ieee) m += 2 * B.total * 16;   // double-float w and input
     return m;
 }
 

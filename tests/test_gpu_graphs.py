@@ -17,21 +17,23 @@ pytestmark = pytest.mark.gpu
 
 def _opts(graphs, **kw):
     import paper_2107_00872_gb300 as qs3
-    base = dict(n_max=120, eps=1e-14, res_tol=1e-12, precision="f64")
+    base = dict(n_max=120, eps=1e-14, res_tol=1e-12)
+    base.setdefault("precision", "f64")
     base.update(kw)
     return qs3.SolveOpts(use_graphs=graphs, **base)
 
 
+@pytest.mark.parametrize("prec", ["f64", "df"])
 @pytest.mark.parametrize("name,spec,nd,K", [
     ("chain16_u1", qi.chain(16), 3, None),
     ("square6_k", qi.square(6), 3, [(0, 0, 0), (1, 2, 0), (3, 3, 0)]),
     ("cube4_k", qi.hypercubic((4, 4, 4), J=1.0, Jz=0.6), 2, [(0, 0, 0), (1, 0, 2)]),
 ])
-def test_lanczos_graphs_identical(name, spec, nd, K):
+def test_lanczos_graphs_identical(name, spec, nd, K, prec):
     torch = torch_cuda()
     b = lib_basis(spec, nd, K)
-    e0, v0, i0 = b.lanczos(_opts(False))
-    e1, v1, i1 = b.lanczos(_opts(True))
+    e0, v0, i0 = b.lanczos(_opts(False, precision=prec))
+    e1, v1, i1 = b.lanczos(_opts(True, precision=prec))
     torch.cuda.synchronize()
     assert i0["status"] == i1["status"] == "QS3_OK"
     assert i1["hphi_graph_calls"] > 0 and i0["hphi_graph_calls"] == 0
@@ -47,11 +49,12 @@ def test_lanczos_graphs_identical(name, spec, nd, K):
         assert abs(e1[s, 0] - w[0]) <= 1e-12 * max(1.0, abs(w[0]))
 
 
-def test_trl_graphs_identical():
+@pytest.mark.parametrize("prec", ["f64", "df"])
+def test_trl_graphs_identical(prec):
     torch = torch_cuda()
     spec = qi.square(6)
     b = lib_basis(spec, 3, [(0, 0, 0), (2, 1, 0)])
-    kw = dict(n_eig=3, n_keep=6, n_max=24, eps=1e-12)
+    kw = dict(n_eig=3, n_keep=6, n_max=24, eps=1e-12, precision=prec)
     e0, v0, i0 = b.trlanczos(_opts(False, **kw))
     e1, v1, i1 = b.trlanczos(_opts(True, **kw))
     torch.cuda.synchronize()

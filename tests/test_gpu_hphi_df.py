@@ -115,26 +115,32 @@ def test_df_edge_bases():
 
 @pytest.mark.parametrize("solver", ["lanczos", "trl"])
 def test_solvers_df_vs_ieee(solver):
+    """The double-float engine (precision "df", with its double-float or its
+    IEEE H Phi) against the binary64 engine (precision "f64")."""
     torch_cuda()
     import paper_2107_00872_gb300 as qs3
     spec = qi.square(6)
     Ks = [(0, 0, 0), (1, 2, 0), (3, 3, 0), (2, 0, 0)]
     b = lib_basis(spec, 3, Ks)
     res = {}
-    for ieee in (False, True):
+    for mode in ("f64", "df", "df_ieee_hphi"):
+        prec = "f64" if mode == "f64" else "df"
+        ieee = mode == "df_ieee_hphi"
         if solver == "lanczos":
-            o = qs3.SolveOpts(n_max=150, eps=1e-14, res_tol=1e-12, hphi_ieee=ieee)
+            o = qs3.SolveOpts(n_max=150, eps=1e-14, res_tol=1e-12, precision=prec, hphi_ieee=ieee)
             e, _, info = b.lanczos(o, vectors=False)
         else:
-            o = qs3.SolveOpts(n_eig=3, n_keep=8, n_max=32, eps=1e-13, hphi_ieee=ieee)
+            o = qs3.SolveOpts(n_eig=3, n_keep=8, n_max=32, eps=1e-13, precision=prec, hphi_ieee=ieee)
             e, _, info = b.trlanczos(o, vectors=False)
         assert info["status"] == "QS3_OK"
         assert info["max_residual"] <= 1e-10
-        res[ieee] = e
-    scale = float(np.max(np.abs(res[True])))
-    assert float(np.max(np.abs(res[False] - res[True]))) <= 1e-12 * scale
+        res[mode] = e
+    scale = float(np.max(np.abs(res["f64"])))
+    for mode in ("df", "df_ieee_hphi"):
+        assert float(np.max(np.abs(res[mode] - res["f64"]))) <= 1e-12 * scale
     # the lowest level of each sector against the oracle (higher TRL levels
     # may skip a copy of a point-group degenerate level: one start vector)
     for s, K in enumerate(Ks):
         w = np.linalg.eigvalsh(orc.dense_k(orc.mk_list(olat(spec), 3, K)))
-        assert abs(res[False][s, 0] - w[0]) <= 1e-12 * max(1.0, abs(w[0]))
+        for mode in res:
+            assert abs(res[mode][s, 0] - w[0]) <= 1e-12 * max(1.0, abs(w[0]))

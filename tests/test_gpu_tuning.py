@@ -36,16 +36,17 @@ def test_hphi_grid_choices_identical():
         assert b.tuning()["hphi_blocks_per_sm"][C128] == bps
 
 
-def test_dot_staging_choices_identical():
+@pytest.mark.parametrize("prec,key", [("f64", "dot_vectors64"), ("df", "dot_vectors")])
+def test_dot_staging_choices_identical(prec, key):
     torch_cuda()
     import paper_2107_00872_gb300 as qs3
     b = _basis()
-    o = qs3.SolveOpts(n_max=60, eps=1e-12, res_tol=1e-10, use_graphs=False)
+    o = qs3.SolveOpts(n_max=60, eps=1e-12, res_tol=1e-10, use_graphs=False, precision=prec)
     e_auto, _, _ = b.lanczos(o, vectors=False)
-    assert b.tuning()["dot_vectors"] in (1, 2, 4)
+    assert b.tuning()[key] in (1, 2, 4)
     res = []
     for nv in (1, 2, 4):
-        b.tuning(dot_vectors=nv)
+        b.tuning(**{key: nv})
         e, _, info = b.lanczos(o, vectors=False)
         res.append((e, info["iterations"]))
     for e, it in res[1:]:
@@ -60,5 +61,7 @@ def test_tuning_rejects_bad_values():
     b = lib_basis(qi.chain(10), 3)
     with pytest.raises(qs3.QS3Error):
         b.tuning(dot_vectors=3)
+    with pytest.raises(qs3.QS3Error):
+        b.tuning(dot_vectors64=5)
     with pytest.raises(qs3.QS3Error):
         b.tuning(hphi_blocks_per_sm=[-1, 0, 0, 0])
