@@ -603,6 +603,24 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
         QS3_TRY(B.d_u_lo.upload(bu.data(), bu.size() * 4));
         QS3_TRY(B.d_adj_jz_lo.upload(cz.data(), cz.size() * 4));
     }
+    // fixed-width copy of the adjacency for the U(1) fp32 kernel
+    const int padw = B.max_degree <= 4 ? 4 : (B.max_degree <= 6 ? 6 : 0);
+    if (padw) {
+        std::vector<int2> pk((size_t)N * padw);
+        std::vector<float> pz((size_t)N * padw, 0.f);
+        for (int i = 0; i < N; ++i)
+            for (int b = 0; b < padw; ++b) {
+                const int q = deg[i] + b;
+                const bool real = q < deg[i + 1];
+                float jf = real ? ajxyf[q] : 0.f;
+                int bitsf;
+                std::memcpy(&bitsf, &jf, 4);
+                pk[(size_t)i * padw + b] = make_int2(real ? nbr[q] : i, bitsf);
+                pz[(size_t)i * padw + b] = real ? ajzf[q] : 0.f;
+            }
+        QS3_TRY(B.d_adj_pad.upload(pk.data(), pk.size() * sizeof(int2)));
+        QS3_TRY(B.d_adj_jz_pad.upload(pz.data(), pz.size() * 4));
+    }
     std::vector<uint32_t> xyz(N);
     for (int r = 0; r < N; ++r) {
         int x = r % B.L[0], y = (r / B.L[0]) % B.L[1], z = r / (B.L[0] * B.L[1]);
@@ -636,6 +654,9 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     L.adj_jz_lo = B.d_adj_jz_lo.as<float>();
     L.c0lo = (float)(c0 - (double)(float)c0);
     L.xyz = B.d_xyz.as<uint32_t>();
+    L.adj_pad = B.d_adj_pad.as<int2>();
+    L.adj_jz_pad = B.d_adj_jz_pad.as<float>();
+    L.pad_w = padw;
     L.jh_uniform = 0.0;
     if (nb > 0) {
         bool same = true;

@@ -157,14 +157,22 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
             const int i = pick(c, m);
             e += diag_u<R>(L, i);
             const int e0 = __ldg(L.adj_ptr + i), e1 = __ldg(L.adj_ptr + i + 1);
+            // a hop to c_{m-1} < j < c_{m+1} keeps its place in the sorted list
+            // (and lands on an empty site): its rank changes in the m-th term only
+            const int lo = m > 0 ? pick(c, m > 0 ? m - 1 : 0) : -1;
+            const int hi = m < ND - 1 ? pick(c, m < ND - 1 ? m + 1 : m) : L.np1;
+            const uint64_t base = rank - sm.sC[(m + 1) * L.np1 + i];
             for (int q = e0; q < e1; ++q) {
                 const int j = __ldg(L.adj_nbr + q);
-                bool occ = false;
+                const bool inpl = j > lo && j < hi;
+                if (!inpl) {
+                    bool occ = false;
 #pragma unroll
-                for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
-                if (occ) {
-                    dd += diag_jz<R>(L, q);
-                    continue;
+                    for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
+                    if (occ) {
+                        dd += diag_jz<R>(L, q);
+                        continue;
+                    }
                 }
                 int tt[ND];
 #pragma unroll
@@ -186,8 +194,14 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
                     uint32_t idx;
                     int u;
                     if constexpr (TB) {
-                        sort_net(tt);
-                        const uint32_t e = __ldg(L.orb + rank_of(tt, sm.sC, L.np1));
+                        uint64_t r2;
+                        if (inpl) {
+                            r2 = base + sm.sC[(m + 1) * L.np1 + j];
+                        } else {
+                            sort_net(tt);
+                            r2 = rank_of(tt, sm.sC, L.np1);
+                        }
+                        const uint32_t e = __ldg(L.orb + r2);
                         if ((e >> 12) >= L.n_orb) continue;     // never for a complete table
                         const int32_t row2 = __ldg(sv.t2 + (e >> 12));
                         if (row2 < 0) continue;
@@ -225,13 +239,18 @@ __global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *
     }
 }
 
-// U(1) H Phi with 32-bit ranks, for C(N, N_down) < 2^32, N_down <= 4 and fp32
-// vectors: the binomial rows 0..N_down as a 32-bit table in shared memory
-// (a third of the 64-bit layout, so more blocks fit an SM), one thread per
-// row striding over the single sector, and per occupied site the ranks of its
-// first DEGB hop targets (DEGB = the lattice's largest degree, 4 or 6)
-// formed before their gathers issue together.  With DEGB = 4 the kernel fits
-// 40 registers, so six blocks reside per SM (more gathers in flight).  Same
+// U(1) H Phi with 32-bit ranks, for C(N, N_down) < 2^32, N_down <= 4, fp32
+// vectors and lattices of degree <= 6: the binomial rows 0..N_down as a
+// 32-bit table in shared memory, one thread per row striding over the single
+// sector, and the fixed-width adjacency (DEGB = 4 or 6 entries per site, a
+// site with fewer padded with itself and zero couplings), one 8-byte load
+// per entry (neighbour, hop amplitude).  The hop of c_m to j keeps its place
+// in the sorted list when c_{m-1} < j < c_{m+1}; then its rank is the row's
+// rank with C(c_m, m+1) replaced by C(j, m+1) -- two compares and one table
+// read, and a padded entry (j = c_m) lands on the row itself with amplitude
+// 0.  Only the other hops (j occupied, or j passing another down spin) take
+// the occupancy test and the re-sort.  Per occupied site the ranks of its
+// DEGB entries are formed before their gathers issue together.  Same
 // signature as k_hphi (the launch and the autotuner treat both alike).
 template <int ND, typename VT, int DEGB>
 __global__ void __launch_bounds__(NTHREADS, DEGB <= 4 ? 6 : 4) k_hphi_u1n(LatView L, const SecView *__restrict__ secs,
@@ -247,7 +266,7 @@ __global__ void __launch_bounds__(NTHREADS, DEGB <= 4 ? 6 : 4) k_hphi_u1n(LatVie
     __syncthreads();
     if (active && !active[0]) return;
     const uint64_t dim = secs[0].dim;     // < 2^32
-    const R *jxy = jxy_table<VT>(L);
+    const int2 *__restrict__ pad = L.adj_pad;
     for (uint64_t rw = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; rw < dim; rw += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t row = (uint32_t)rw;
         int c[ND];
@@ -260,60 +279,42 @@ __global__ void __launch_bounds__(NTHREADS, DEGB <= 4 ? 6 : 4) k_hphi_u1n(LatVie
         for (int m = 0; m < ND; ++m) {
             const int i = c[m];
             e += diag_u<R>(L, i);
-            const int e0 = __ldg(L.adj_ptr + i), e1 = __ldg(L.adj_ptr + i + 1);
+            const int lo = m > 0 ? c[m > 0 ? m - 1 : 0] : -1;
+            const int hi = m < ND - 1 ? c[m < ND - 1 ? m + 1 : m] : np1;
             const uint32_t base = row - sC[(m + 1) * np1 + i];
+            const uint32_t *col = sC + (m + 1) * np1;
             uint32_t r2b[DEGB];
             R cfb[DEGB];
 #pragma unroll
             for (int b = 0; b < DEGB; ++b) {
-                const int q = e0 + b;
-                cfb[b] = 0;
-                r2b[b] = 0;
-                if (q < e1) {
-                    const int j = __ldg(L.adj_nbr + q);
+                const int2 pk = __ldg(pad + i * DEGB + b);
+                const int j = pk.x;
+                const R cf = (R)__int_as_float(pk.y);
+                r2b[b] = base + col[j];
+                cfb[b] = cf;
+                if (!(j > lo && j < hi)) {
+                    // occupied, or passing another down spin
                     bool occ = false;
 #pragma unroll
                     for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
                     if (occ) {
-                        dd += diag_jz<R>(L, q);
+                        dd += (R)__ldg(L.adj_jz_pad + i * DEGB + b);
+                        cfb[b] = 0;
+                        r2b[b] = row;
                     } else {
-                        const bool inplace = (m == 0 || j > c[m > 0 ? m - 1 : 0]) &&
-                                             (m == ND - 1 || j < c[m + 1 < ND ? m + 1 : m]);
-                        if (inplace) {
-                            r2b[b] = base + sC[(m + 1) * np1 + j];
-                        } else {
-                            int tt[ND];
+                        int tt[ND];
 #pragma unroll
-                            for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
-                            sort_net(tt);
-                            r2b[b] = rank_of32(tt, sC, np1);
-                        }
-                        cfb[b] = __ldg(jxy + q);
+                        for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
+                        sort_net(tt);
+                        r2b[b] = rank_of32(tt, sC, np1);
                     }
                 }
             }
             VT vb[DEGB];
 #pragma unroll
-            for (int b = 0; b < DEGB; ++b)
-                if (cfb[b] != (R)0) vb[b] = phi[r2b[b]];
+            for (int b = 0; b < DEGB; ++b) vb[b] = phi[r2b[b]];
 #pragma unroll
-            for (int b = 0; b < DEGB; ++b)
-                if (cfb[b] != (R)0) madd_r(acc, cfb[b], vb[b]);
-            for (int q = e0 + DEGB; q < e1; ++q) {
-                const int j = __ldg(L.adj_nbr + q);
-                bool occ = false;
-#pragma unroll
-                for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
-                if (occ) {
-                    dd += diag_jz<R>(L, q);
-                    continue;
-                }
-                int tt[ND];
-#pragma unroll
-                for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
-                sort_net(tt);
-                madd_r(acc, __ldg(jxy + q), phi[rank_of32(tt, sC, np1)]);
-            }
+            for (int b = 0; b < DEGB; ++b) madd_r(acc, cfb[b], vb[b]);
         }
         madd_r(acc, e + (R)0.5 * dd, x0);
         store(psi + row, acc);
@@ -449,9 +450,8 @@ static int hphi_nd(Basis &B, const void *phi, void *psi, cudaStream_t st, const 
     if constexpr (KS) {
         if (B.lv.orb) return hphi_ndt<ND, VT, true, true>(B, phi, psi, st, active);
     } else if constexpr (ND <= 4 && sizeof(typename VTr<VT>::R) == 4) {
-        if (B.narrow_ranks)
-            return B.max_degree <= 4 ? hphi_u1n<ND, VT, 4>(B, phi, psi, st, active)
-                                     : hphi_u1n<ND, VT, 6>(B, phi, psi, st, active);
+        if (B.narrow_ranks && B.lv.pad_w == 4) return hphi_u1n<ND, VT, 4>(B, phi, psi, st, active);
+        if (B.narrow_ranks && B.lv.pad_w == 6) return hphi_u1n<ND, VT, 6>(B, phi, psi, st, active);
     }
     return hphi_ndt<ND, VT, KS, false>(B, phi, psi, st, active);
 }

@@ -103,6 +103,12 @@ struct LatView {
     const uint32_t *orb;
     uint32_t n_orb;               // orbits in the table (entries >= n_orb << 12 are invalid)
     double jh_uniform;            // the hop amplitude J^xy / 2 when every bond has the same one, else 0
+    // fixed-width adjacency (largest degree <= 6): pad_w entries per site,
+    // (neighbour, fp32 hop amplitude bits) and fp32 J^z; a site with fewer
+    // neighbours is padded with itself and zero couplings
+    const int2 *adj_pad;
+    const float *adj_jz_pad;
+    int pad_w;                    // 4 or 6; 0 when the table is not built
 };
 
 struct SecView {
@@ -140,6 +146,7 @@ struct Basis {
     DevBuf d_binom, d_adj_ptr, d_adj_nbr, d_adj_jxy, d_adj_jz, d_adj_jxy_f, d_u, d_xyz;
     DevBuf d_u_f, d_adj_jz_f;
     DevBuf d_adj_jxy_lo, d_u_lo, d_adj_jz_lo;
+    DevBuf d_adj_pad, d_adj_jz_pad;         // fixed-width adjacency (LatView::adj_pad)
     std::vector<DevBuf> d_sigma, d_stab, d_pidx;
     DevBuf d_ph64, d_ph32, d_phdf;          // S x N per-site phase tables (k-sectors)
     DevBuf d_secs, d_tile0, d_chunk0;

@@ -26,6 +26,8 @@
 #include <cstring>
 #include <vector>
 
+#include <mutex>
+
 #include "qs3_internal.cuh"
 
 namespace qs3 {
@@ -569,7 +571,7 @@ int smq_launch(Basis &S, int ss, const void *phi, Basis &Dd, int sd, const int *
     if (ss < 0 || ss >= S.S || sd < 0 || sd >= Dd.S) return set_err(QS3_ERR_INVALID_ARG, "sector index");
     if (S.has_k)
         for (int a = 0; a < 3; ++a)
-            if (((S.K[3 * ss + a] + Q[a]) % S.L[a] + S.L[a]) % S.L[a] != Dd.K[3 * sd + a])
+            if ((((long long)S.K[3 * ss + a] + Q[a]) % S.L[a] + S.L[a]) % S.L[a] != Dd.K[3 * sd + a])
                 return set_err(QS3_ERR_SYMMETRY, "target momentum is not K + Q (axis %d)", a);
     if (Dd.dims[sd] == 0) return QS3_OK;
     std::vector<double2> ph = site_phases(S, Q);
@@ -672,7 +674,7 @@ int sq_launch(int op, Basis &S, int ss, const void *phi, Basis &Dd, int sd, cons
     if (ss < 0 || ss >= S.S || sd < 0 || sd >= Dd.S) return set_err(QS3_ERR_INVALID_ARG, "sector index");
     if (S.has_k)
         for (int a = 0; a < 3; ++a)
-            if (((S.K[3 * ss + a] + Q[a]) % S.L[a] + S.L[a]) % S.L[a] != Dd.K[3 * sd + a])
+            if ((((long long)S.K[3 * ss + a] + Q[a]) % S.L[a] + S.L[a]) % S.L[a] != Dd.K[3 * sd + a])
                 return set_err(QS3_ERR_SYMMETRY, "target momentum is not K + Q (axis %d)", a);
     if (Dd.dims[sd] == 0) return QS3_OK;
     std::vector<double2> ph = site_phases(S, Q);
@@ -951,21 +953,53 @@ namespace qs3 {
 constexpr int NOALLOC_MAX_SITES = 2048;
 static __device__ __align__(256) double2 g_smq_phase_scratch[NOALLOC_MAX_SITES];
 
-// device address of the scratch on each device, looked up once per device
+// device address of the scratch on each device, with the CUDA context it
+// was looked up in.  A call that is not being captured into a graph looks it
+// up again (cheap, host side), so a context that was reset and recreated
+// never sees a stale address; a captured call uses the cached address only
+// when the current context is the one it came from.
 static void *g_scratch_addr[256];
+static void *g_scratch_ctx[256];
 static std::atomic<int> g_scratch_ready[256];
+static std::mutex g_scratch_mu;
 
-static int noalloc_scratch(double2 **out) {
+typedef int (*CtxGetCurrentFn)(void **);
+
+static int current_context(void **ctx) {
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)f;
+    });
+    *ctx = nullptr;
+    if (!fn || fn(ctx) != 0) return set_err(QS3_ERR_CUDA, "cuCtxGetCurrent unavailable");
+    return QS3_OK;
+}
+
+static int noalloc_scratch(cudaStream_t st, double2 **out) {
     int dev = 0;
     QS3_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 256) return set_err(QS3_ERR_INVALID_ARG, "device %d", dev);
-    if (!g_scratch_ready[dev].load(std::memory_order_acquire)) {
+    void *ctx = nullptr;
+    QS3_TRY(current_context(&ctx));
+    cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+    QS3_CUDA(cudaStreamIsCapturing(st, &cst));
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (cst == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_smq_phase_scratch);
         if (e != cudaSuccess || !p)
             return set_err(QS3_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
         g_scratch_ready[dev].store(1, std::memory_order_release);
+    } else if (!g_scratch_ready[dev].load(std::memory_order_acquire) || g_scratch_ctx[dev] != ctx) {
+        return set_err(QS3_ERR_STATE, "qs3_smq_noalloc: call it once outside stream capture on this device "
+                                      "(and context) before capturing it");
     }
     *out = (double2 *)g_scratch_addr[dev];
     return QS3_OK;
@@ -998,16 +1032,20 @@ static int smq_noalloc(Basis &S, int ss, const void *phi, Basis &Dd, int sd, con
     if (ss < 0 || ss >= S.S || sd < 0 || sd >= Dd.S) return set_err(QS3_ERR_INVALID_ARG, "sector index");
     if (S.has_k)
         for (int a = 0; a < 3; ++a)
-            if (((S.K[3 * ss + a] + Q[a]) % S.L[a] + S.L[a]) % S.L[a] != Dd.K[3 * sd + a])
+            if ((((long long)S.K[3 * ss + a] + Q[a]) % S.L[a] + S.L[a]) % S.L[a] != Dd.K[3 * sd + a])
                 return set_err(QS3_ERR_SYMMETRY, "target momentum is not K + Q (axis %d)", a);
     double2 *ph = nullptr;
-    QS3_TRY(noalloc_scratch(&ph));
+    QS3_TRY(noalloc_scratch(st, &ph));
     if (Dd.dims[sd] == 0) return QS3_OK;
     if (S.dims[ss] == 0) {
         QS3_CUDA(cudaMemsetAsync(psi, 0, Dd.dims[sd] * 16, st));
         return QS3_OK;
     }
-    k_site_phases<<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.L[0], S.L[1], S.L[2], Q[0], Q[1], Q[2], ph);
+    // Q reduced into [0, L) first: the angle is unchanged and the integer
+    // products of the phase kernel stay far below 2^63
+    int Qr[3];
+    for (int a = 0; a < 3; ++a) Qr[a] = (int)(((long long)Q[a] % S.L[a] + S.L[a]) % S.L[a]);
+    k_site_phases<<<(S.N + 255) / 256, 256, 0, st>>>(S.N, S.L[0], S.L[1], S.L[2], Qr[0], Qr[1], Qr[2], ph);
     QS3_LAUNCHED();
     if (S.nd == 0) {
         k_smq_vac<<<(unsigned)((Dd.dims[sd] + 255) / 256), 256, 0, st>>>(Dd.secs[sd], Dd.has_k ? 1 : 0, S.N, ph,
