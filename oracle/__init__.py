@@ -97,8 +97,10 @@ def set_threads(n: int) -> int:
 class Lattice:
     """Bonds of Eq. (1) with 0-based sites (converted to 1-based inside).
 
-    ``L`` is the translation group (Lx, Ly, Lz); ``(N,1,1)`` for a chain.  It
-    is only used by the k-sector functions and must satisfy Lx*Ly*Lz == N.
+    ``L`` is the translation group (Lx, Ly, Lz) of the unit cells; ``(N,1,1)``
+    for a chain.  ``n_sub`` spins per cell: site r (0-based) is spin
+    r % n_sub of cell r // n_sub, cells numbered x + Lx (y + Ly z).  The group
+    is only used by the k-sector functions and needs n_sub*Lx*Ly*Lz == N.
     """
     n_sites: int
     bi: np.ndarray
@@ -107,6 +109,7 @@ class Lattice:
     jz: np.ndarray
     h: np.ndarray | None = None
     L: tuple = (0, 0, 0)
+    n_sub: int = 1
 
     def _args(self, nd: int):
         lo = np.minimum(self.bi, self.bj).astype(np.int32) + 1
@@ -115,7 +118,8 @@ class Lattice:
                       np.ascontiguousarray(self.jxy, dtype=np.float64),
                       np.ascontiguousarray(self.jz, dtype=np.float64),
                       None if self.h is None else np.ascontiguousarray(self.h, dtype=np.float64),
-                      np.ascontiguousarray(np.array(self.L if self.L != (0, 0, 0) else (self.n_sites, 1, 1),
+                      np.ascontiguousarray(np.array(tuple(self.L if tuple(self.L) != (0, 0, 0)
+                                                          else (self.n_sites, 1, 1)) + (int(self.n_sub),),
                                                     dtype=np.int32))]
         k = self._keep
         return (int(self.n_sites), int(nd), int(len(lo)), _p(k[0]), _p(k[1]), _p(k[2]), _p(k[3]),
@@ -201,7 +205,9 @@ class Sector:
 
     @property
     def stab(self) -> np.ndarray:
-        return np.rint(self.Nak / self.lat.n_sites).astype(np.int64)
+        """|Stab| = N_{a,k} / (number of cell translations)"""
+        L = tuple(self.lat.L) if tuple(self.lat.L) != (0, 0, 0) else (self.lat.n_sites, 1, 1)
+        return np.rint(self.Nak / (L[0] * L[1] * L[2])).astype(np.int64)
 
 
 def mk_list(lat: Lattice, nd: int, K) -> Sector:
@@ -225,9 +231,10 @@ def representative(lat: Lattice, nd: int, a1: int):
 
 
 def orbit(lat: Lattice, nd: int, a1: int) -> np.ndarray:
-    """1-based indices of T^t |a>, t in the order tx fastest."""
-    N = lat.n_sites
-    out = np.zeros(N, np.uint64)
+    """1-based indices of T^t |a>, t over the Lx Ly Lz cell translations in
+    the order tx fastest."""
+    L = tuple(lat.L) if tuple(lat.L) != (0, 0, 0) else (lat.n_sites, 1, 1)
+    out = np.zeros(L[0] * L[1] * L[2], np.uint64)
     _load().orc_orbit(*lat._args(nd), a1, _p(out))
     return out
 

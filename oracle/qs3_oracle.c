@@ -12,8 +12,10 @@
  *     states with the U(1) symmetry");
  *   - the state index a is 1-based, a = F(n) = 1 + sum_m C(n_m - 1, m)
  *     (Eq. a_of_n);
- *   - a site r has coordinates (x, y, z) with r - 1 = x + Lx (y + Ly z), and
- *     the translation T^t moves every site by +t modulo (Lx, Ly, Lz).
+ *   - a site r is spin s of the unit cell at (x, y, z), with
+ *     r - 1 = s + n_sub (x + Lx (y + Ly z)) (n_sub spins per cell, 1 for a
+ *     Bravais lattice), and the translation T^t moves every cell by +t modulo
+ *     (Lx, Ly, Lz), keeping s; the group has Lx Ly Lz elements.
  *   - the momentum sector K = (Kx, Ky, Kz) means k.a_alpha = 2 pi K_alpha/L_alpha
  *     (input parameters KX, KY, KZ).
  *
@@ -55,6 +57,8 @@ typedef struct {
     const double *jxy, *jz;
     const double *h;             /* per-site field or NULL */
     int L[3];
+    int nsub;                    /* spins per unit cell */
+    int ncell;                   /* Lx Ly Lz: the order of the translation group */
     uint64_t *C;                 /* (N+1) x (nd+1) table of binomials */
 } orc_ctx;
 
@@ -92,7 +96,10 @@ static int ctx_init(orc_ctx *c, int N, int nd, int nb, const int *r, const int *
     memset(c, 0, sizeof(*c));
     c->N = N; c->nd = nd; c->nb = nb; c->r = r; c->rp = rp;
     c->jxy = jxy; c->jz = jz; c->h = h;
-    if (L) { c->L[0] = L[0]; c->L[1] = L[1]; c->L[2] = L[2]; }
+    /* L: Lx, Ly, Lz, n_sub (four ints) */
+    c->nsub = 1;
+    if (L) { c->L[0] = L[0]; c->L[1] = L[1]; c->L[2] = L[2]; c->nsub = L[3] > 0 ? L[3] : 1; }
+    c->ncell = c->L[0] * c->L[1] * c->L[2];
     if (nd < 0 || nd > ORC_MAXND || nd > N) return -1;
     return make_binom(c);
 }
@@ -187,16 +194,18 @@ static int hop_target(int nd, const int *n, int r, int rp, int *np)
 
 /* --------------------------------------------------------------- translations */
 
-static void site_xyz(const orc_ctx *c, int r, int *x, int *y, int *z)
+/* site r -> spin s of the cell at (x, y, z) */
+static void site_xyz(const orc_ctx *c, int r, int *s, int *x, int *y, int *z)
 {
     int q = r - 1;
+    *s = q % c->nsub; q /= c->nsub;
     *x = q % c->L[0]; q /= c->L[0];
     *y = q % c->L[1]; *z = q / c->L[1];
 }
 
-static int xyz_site(const orc_ctx *c, int x, int y, int z)
+static int xyz_site(const orc_ctx *c, int s, int x, int y, int z)
 {
-    return 1 + x + c->L[0] * (y + c->L[1] * z);
+    return 1 + s + c->nsub * (x + c->L[0] * (y + c->L[1] * z));
 }
 
 static void insertion_sort(int *n, int nd)
@@ -212,12 +221,12 @@ static void insertion_sort(int *n, int nd)
 static void translate(const orc_ctx *c, const int *n, const int *t, int *out)
 {
     for (int m = 0; m < c->nd; ++m) {
-        int x, y, z;
-        site_xyz(c, n[m], &x, &y, &z);
+        int s, x, y, z;
+        site_xyz(c, n[m], &s, &x, &y, &z);
         x = (x + t[0]) % c->L[0];
         y = (y + t[1]) % c->L[1];
         z = (z + t[2]) % c->L[2];
-        out[m] = xyz_site(c, x, y, z);
+        out[m] = xyz_site(c, s, x, y, z);
     }
     insertion_sort(out, c->nd);
 }
@@ -248,7 +257,7 @@ static double check_state(const orc_ctx *c, uint64_t a, const int *K)
                 if (ap == a) { cs += cexp(I * kdot(c, K, t)); nc += 1; }
             }
     double ab = cabs(cs);
-    return ab * ab * (double)c->N / (double)nc;
+    return ab * ab * (double)c->ncell / (double)nc;
 }
 
 /* Alg. 7: representative (minimum index over all translations) and the
@@ -632,8 +641,8 @@ int orc_smq(ORC_LAT, const int *K, const uint64_t *sigma, const double *Nak, int
     memset(q, 0, sizeof(zdbl) * d2);
     int K2[3] = {K[0] + Q[0], K[1] + Q[1], K[2] + Q[2]};
     for (int rr = 1; rr <= N; ++rr) {
-        int x, y, z;
-        site_xyz(&c, rr, &x, &y, &z);
+        int sb, x, y, z;
+        site_xyz(&c, rr, &sb, &x, &y, &z);
         double qr;
         if (pos) {
             qr = 2.0 * M_PI * (Q[0] * pos[3 * (rr - 1)] / L[0] + Q[1] * pos[3 * (rr - 1) + 1] / L[1] +

@@ -26,13 +26,14 @@ class LatticeSpec:
     jxy: np.ndarray
     jz: np.ndarray
     h: np.ndarray | None = None
-    L: tuple = (0, 0, 0)                 # translation group, (0,0,0) = none
+    L: tuple = (0, 0, 0)                 # translation group of the cells, (0,0,0) = none
     name: str = ""
     pos: np.ndarray | None = field(default=None, repr=False)
+    n_sub: int = 1                       # spins per unit cell (site r: spin r % n_sub of cell r // n_sub)
 
     def as_dict(self) -> dict:
         return dict(n_sites=self.n_sites, bi=self.bi, bj=self.bj, jxy=self.jxy, jz=self.jz,
-                    h=self.h, L=tuple(self.L))
+                    h=self.h, L=tuple(self.L), n_sub=int(self.n_sub))
 
     @property
     def n_bonds(self) -> int:
@@ -112,6 +113,40 @@ def disordered_open_square(L: int = 32, seed: int = 20210702) -> LatticeSpec:
     h = rng.uniform(-0.1, 0.1, base.n_sites)
     return LatticeSpec(base.n_sites, base.bi, base.bj, J, 0.8 * J, h, (0, 0, 0),
                        f"disordered_open_square{L}")
+
+
+def _cell_lattice(Lx: int, Ly: int, nsub: int, bonds, J: float, Jz: float | None, name: str) -> LatticeSpec:
+    """Periodic Lx x Ly lattice of nsub-spin unit cells; bonds = [(s, s2, dx,
+    dy)]: spin s of cell (x, y) to spin s2 of cell (x + dx, y + dy)."""
+    Jz = J if Jz is None else Jz
+    bi, bj = [], []
+    for y in range(Ly):
+        for x in range(Lx):
+            for s, s2, dx, dy in bonds:
+                a = s + nsub * (x + Lx * y)
+                b = s2 + nsub * ((x + dx) % Lx + Lx * ((y + dy) % Ly))
+                bi.append(min(a, b))
+                bj.append(max(a, b))
+    nb = len(bi)
+    N = nsub * Lx * Ly
+    return LatticeSpec(N, np.array(bi, np.int32), np.array(bj, np.int32), np.full(nb, float(J)),
+                       np.full(nb, float(Jz)), None, (Lx, Ly, 1), name, None, nsub)
+
+
+def honeycomb(Lx: int, Ly: int | None = None, J: float = 1.0, Jz: float | None = None) -> LatticeSpec:
+    """Periodic honeycomb lattice of Lx x Ly two-spin cells (A = spin 0, B =
+    spin 1): A(x, y) joins B(x, y), B(x - 1, y) and B(x, y - 1)."""
+    Ly = Ly or Lx
+    return _cell_lattice(Lx, Ly, 2, [(0, 1, 0, 0), (0, 1, -1, 0), (0, 1, 0, -1)], J, Jz, f"honeycomb{Lx}x{Ly}")
+
+
+def kagome(Lx: int, Ly: int | None = None, J: float = 1.0, Jz: float | None = None) -> LatticeSpec:
+    """Periodic kagome lattice of Lx x Ly three-spin cells (A, B, C = spins 0,
+    1, 2 at 0, a1/2, a2/2): the up triangle A-B-C of each cell and the down
+    triangle B(x, y), A(x + 1, y), C(x + 1, y - 1)."""
+    Ly = Ly or Lx
+    return _cell_lattice(Lx, Ly, 3, [(0, 1, 0, 0), (0, 2, 0, 0), (1, 2, 0, 0), (1, 0, 1, 0), (0, 2, 0, -1),
+                                     (1, 2, 1, -1)], J, Jz, f"kagome{Lx}x{Ly}")
 
 
 def random_graph(N: int, n_bonds: int, seed: int, field: bool = True) -> LatticeSpec:

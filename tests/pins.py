@@ -82,16 +82,19 @@ def sector_projector(N: int, nd: int) -> np.ndarray:
     return P
 
 
-def coords(r: int, L) -> tuple:
-    return r % L[0], (r // L[0]) % L[1], r // (L[0] * L[1])
+def coords(r: int, L, nsub: int = 1) -> tuple:
+    """cell coordinates of site r (spin r % nsub of cell r // nsub)"""
+    q = r // nsub
+    return q % L[0], (q // L[0]) % L[1], q // (L[0] * L[1])
 
 
-def translate_set(c, t, L) -> tuple:
+def translate_set(c, t, L, nsub: int = 1) -> tuple:
+    """the site set c with every cell moved by t (each spin keeps its place in the cell)"""
     out = []
     for r in c:
-        x, y, z = coords(r, L)
+        x, y, z = coords(r, L, nsub)
         x, y, z = (x + t[0]) % L[0], (y + t[1]) % L[1], (z + t[2]) % L[2]
-        out.append(x + L[0] * (y + L[1] * z))
+        out.append(r % nsub + nsub * (x + L[0] * (y + L[1] * z)))
     return tuple(sorted(out))
 
 
@@ -106,18 +109,20 @@ def order(t, L) -> int:
     return o
 
 
-def sector_dim_closed_form(L, nd: int, K) -> int:
-    """dim_k = (1/N) sum_t e^{-ik.t} [o(t) | nd] C(N/o(t), nd/o(t)): the number
-    of nd-subsets fixed by t is C(N/o, nd/o) when o divides nd (t acts freely,
-    in N/o cycles of length o), and 0 otherwise."""
-    N = L[0] * L[1] * L[2]
+def sector_dim_closed_form(L, nd: int, K, nsub: int = 1) -> int:
+    """dim_k = (1/G) sum_t e^{-ik.t} [o(t) | nd] C(N/o(t), nd/o(t)) over the G =
+    Lx Ly Lz cell translations t of an N = nsub G site lattice: the number of
+    nd-subsets fixed by t is C(N/o, nd/o) when o divides nd (t moves every
+    site in cycles of length o, N/o of them), and 0 otherwise."""
+    G = L[0] * L[1] * L[2]
+    N = nsub * G
     s = 0j
     for t in group(L):
         o = order(t, L)
         if nd % o == 0:
             ph = np.exp(-2j * np.pi * sum(K[a] * t[a] / L[a] for a in range(3)))
             s += ph * comb(N // o, nd // o)
-    v = s / N
+    v = s / G
     assert abs(v.imag) < 1e-6 and abs(v.real - round(v.real)) < 1e-6
     return int(round(v.real))
 

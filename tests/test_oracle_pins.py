@@ -208,6 +208,66 @@ def test_representatives_are_orbit_minima():
         assert list(sec.sigma1) == sorted(sec.sigma1)
 
 
+@pytest.mark.parametrize("name,nd", [("honeycomb3x2", 3), ("kagome2x2", 3), ("kagome2x2", 4), ("honeycomb2x2", 2)])
+def test_multi_spin_cells_dims_and_representatives(name, nd):
+    """Lattices with several spins per unit cell: translations move cells,
+    each spin keeps its place in the cell.  Sector dimensions against the
+    character sum over the cell group (and their total, C(N, nd)); every
+    representative is the minimum of its orbit under the cell translations,
+    with its stabiliser, compatibility and N_{a,k} = (number of cells) |Stab|."""
+    spec = {"honeycomb3x2": qi.honeycomb(3, 2), "kagome2x2": qi.kagome(2, 2),
+            "honeycomb2x2": qi.honeycomb(2, 2)}[name]
+    L, ns, N = spec.L, spec.n_sub, spec.n_sites
+    G = L[0] * L[1] * L[2]
+    lat = olat(spec)
+    subs = pins.colex_subsets(N, nd)
+    index = {c: k + 1 for k, c in enumerate(subs)}
+    total = 0
+    for K in qi.all_k(L):
+        sec = orc.mk_list(lat, nd, K)
+        assert sec.dim == pins.sector_dim_closed_form(L, nd, K, ns)
+        total += sec.dim
+        reps = set(int(a) for a in sec.sigma1)
+        for c in subs:
+            orb = {pins.translate_set(c, t, L, ns) for t in pins.group(L)}
+            rep = min(index[o] for o in orb)
+            fix = [t for t in pins.group(L) if pins.translate_set(c, t, L, ns) == c]
+            compat = all(abs(np.exp(2j * np.pi * sum(K[a] * t[a] / L[a] for a in range(3))) - 1) < 1e-9 for t in fix)
+            a = index[c]
+            r, l = orc.representative(lat, nd, a)
+            assert r == rep and index[pins.translate_set(c, l, L, ns)] == rep
+            assert (a in reps) == (a == rep and compat)
+            if a in reps:
+                i = list(sec.sigma1).index(a)
+                assert sec.stab[i] == len(fix)
+                assert abs(sec.Nak[i] - G * len(fix)) < 1e-9
+    assert total == comb(N, nd)
+
+
+@pytest.mark.parametrize("name,nd,anis", [("honeycomb3x2", 3, 1.0), ("kagome2x2", 3, 0.6), ("kagome2x2", 4, 1.0)])
+def test_multi_spin_cells_dense_k_unfolds_and_spectra_union(name, nd, anis):
+    """The k-blocks of a multi-spin-cell lattice: Hermitian, H_U U_k = U_k H_k
+    with U_k^H U_k = I, and the union of their spectra equals the spectrum of
+    the N_down block built on bit strings (no translations involved)."""
+    spec = {"honeycomb3x2": qi.honeycomb(3, 2, Jz=anis), "kagome2x2": qi.kagome(2, 2, Jz=anis)}[name]
+    lat = olat(spec)
+    HU = orc.dense_u1(lat, nd)
+    np.testing.assert_allclose(np.linalg.eigvalsh(HU), np.linalg.eigvalsh(pins.bit_hamiltonian_sector(spec, nd)),
+                               atol=1e-12)
+    eig_all = []
+    for K in qi.all_k(spec.L):
+        sec = orc.mk_list(lat, nd, K)
+        if sec.dim == 0:
+            continue
+        Hk = orc.dense_k(sec)
+        np.testing.assert_allclose(Hk, Hk.conj().T, atol=1e-13)
+        U = _unfold_matrix(sec)
+        np.testing.assert_allclose(U.conj().T @ U, np.eye(sec.dim), atol=1e-12)
+        np.testing.assert_allclose(HU @ U, U @ Hk, atol=1e-12)
+        eig_all.append(np.linalg.eigvalsh(Hk))
+    np.testing.assert_allclose(np.sort(np.concatenate(eig_all)), np.linalg.eigvalsh(HU), atol=1e-11)
+
+
 # ----------------------------------------------------------- Alg 8 / 9, Eq.
 
 
