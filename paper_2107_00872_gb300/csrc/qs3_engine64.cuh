@@ -416,6 +416,7 @@ struct Engine64 {
     Engine64 &operator=(const Engine64 &) = delete;
     void use_df_hphi(bool) {}
     void set_strict(bool on) { strict = on ? 1 : 0; }
+    bool loop_graph_ok() const { return graphs; }
     int enable_graphs(bool on) {
         graphs = on && B.nchunks > 0;
         if (graphs && !xdev.p) QS3_TRY(xdev.alloc(sizeof(int)));

@@ -26,7 +26,7 @@ namespace qs3 {
 // TB (k-sectors): representative and row from the representative table
 // (LatView::orb, SecView::t2) instead of the search and sigma lookup
 template <int ND, typename VT, bool KS, bool TB = false>
-__global__ void __launch_bounds__(NTHREADS, 3) k_hphi(LatView L, const SecView *__restrict__ secs,
+__global__ void __launch_bounds__(NTHREADS, (KS && TB && sizeof(VT) == 16) ? 4 : 3) k_hphi(LatView L, const SecView *__restrict__ secs,
                                                    const int *__restrict__ tile0, int S, int ntiles,
                                                    const VT *__restrict__ phi, VT *__restrict__ psi,
                                                    const int *__restrict__ active) {

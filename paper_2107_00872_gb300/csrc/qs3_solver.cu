@@ -12,10 +12,16 @@
 // product, alpha_x among them), then one classical Gram-Schmidt pass against
 // psi_0..psi_x removes the O(eps) rest (two full passes on the first step
 // after a thick restart); beta_x = |v|; psi_{x+1} = v / beta_x.  Dot
-// products, norms and the Gram-Schmidt coefficients are fp64-accurate (fp64
-// or double-float sums) even when the vectors are fp32.  The small tridiagonal / arrowhead matrices T are
-// diagonalised on the host (Sturm bisection + inverse iteration for
-// tridiagonal T, cyclic Jacobi for the arrowhead T of the thick restart).
+// products, norms and the Gram-Schmidt coefficients are fp64-accurate
+// (binary64 or double-float sums) even when the vectors are fp32.
+//
+// Engines: the binary64 engine (qs3_engine64.cuh, precision QS3_F64), the
+// double-float engine (Engine with dfh, precision QS3_C128DF on k-sector
+// bases) and the fp32 engine (Engine<float / float2>, the fp32 phase of
+// precision QS3_F32).  The convergence checks of conventional Lanczos (the
+// tridiagonal T) run on the device (Sturm multisection + inverse
+// iteration), so the whole loop can replay as one CUDA graph; the arrowhead
+// T of the thick restart is diagonalised on the host (cyclic Jacobi).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -1045,91 +1051,6 @@ __global__ void __launch_bounds__(NTHREADS) k_resid(const WT *__restrict__ t, co
 
 // ----------------------------------------------------- small host eigensolvers
 
-// number of eigenvalues of the symmetric tridiagonal (a, b) below x (Sturm count)
-static int sturm_count(int n, const double *a, const double *b, double x) {
-    int cnt = 0;
-    double q = 1.0;
-    for (int i = 0; i < n; ++i) {
-        const double bb = i ? b[i - 1] * b[i - 1] : 0.0;
-        q = a[i] - x - (i ? bb / q : 0.0);
-        if (q == 0.0) q = -1e-300;
-        if (q < 0) ++cnt;
-    }
-    return cnt;
-}
-
-// k-th smallest eigenvalue (0-based) of the tridiagonal by bisection
-static double tri_eig_k(int n, const double *a, const double *b, int k) {
-    double lo = 1e300, hi = -1e300;
-    for (int i = 0; i < n; ++i) {
-        const double r = (i ? std::fabs(b[i - 1]) : 0.0) + (i < n - 1 ? std::fabs(b[i]) : 0.0);
-        lo = std::min(lo, a[i] - r);
-        hi = std::max(hi, a[i] + r);
-    }
-    const double w = std::max(hi - lo, 1e-300);
-    lo -= 1e-3 * w;
-    hi += 1e-3 * w;
-    for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (sturm_count(n, a, b, mid) > k) hi = mid; else lo = mid;
-    }
-    return 0.5 * (lo + hi);
-}
-
-// eigenvector of the tridiagonal for eigenvalue e by inverse iteration
-// (Gaussian elimination with partial pivoting on T - e I)
-static void tri_eigvec(int n, const double *a, const double *b, double e, std::vector<double> &v) {
-    v.assign(n, 1.0);
-    if (n == 1) return;
-    double scale = 0.0;
-    for (int i = 0; i < n; ++i) scale = std::max(scale, std::fabs(a[i]) + (i < n - 1 ? std::fabs(b[i]) : 0.0));
-    const double pert = std::max(scale, 1e-300) * 1e-14;
-    std::vector<double> d(n), du(n), du2(n), dl(n), x(n);
-    std::vector<int> piv(n);
-    for (int it = 0; it < 3; ++it) {
-        for (int i = 0; i < n; ++i) { d[i] = a[i] - e - pert; du[i] = i < n - 1 ? b[i] : 0.0; dl[i] = i < n - 1 ? b[i] : 0.0; du2[i] = 0.0; }
-        // LU with partial pivoting of the tridiagonal (LAPACK gttrf-style layout, own code)
-        for (int i = 0; i < n - 1; ++i) {
-            if (std::fabs(d[i]) >= std::fabs(dl[i])) {
-                piv[i] = 0;
-                if (d[i] == 0.0) d[i] = 1e-300;
-                const double f = dl[i] / d[i];
-                dl[i] = f;
-                d[i + 1] -= f * du[i];
-            } else {
-                piv[i] = 1;
-                const double f = d[i] / dl[i];
-                d[i] = dl[i];
-                dl[i] = f;
-                const double t = du[i];
-                du[i] = d[i + 1];
-                d[i + 1] = t - f * d[i + 1];
-                if (i < n - 2) { du2[i] = du[i + 1]; du[i + 1] = -f * du[i + 1]; }
-            }
-        }
-        if (d[n - 1] == 0.0) d[n - 1] = 1e-300;
-        // solve L U x = v
-        x = v;
-        for (int i = 0; i < n - 1; ++i) {
-            if (piv[i] == 0) x[i + 1] -= dl[i] * x[i];
-            else { const double t = x[i]; x[i] = x[i + 1]; x[i + 1] = t - dl[i] * x[i + 1]; }
-        }
-        x[n - 1] /= d[n - 1];
-        if (n > 1) x[n - 2] = (x[n - 2] - du[n - 2] * x[n - 1]) / d[n - 2];
-        for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) / d[i];
-        double nr = 0.0;
-        for (double t : x) nr += t * t;
-        nr = std::sqrt(nr);
-        if (!(nr > 0) || !std::isfinite(nr)) break;
-        for (int i = 0; i < n; ++i) v[i] = x[i] / nr;
-    }
-    // sign convention: largest component positive
-    int im = 0;
-    for (int i = 1; i < n; ++i) if (std::fabs(v[i]) > std::fabs(v[im])) im = i;
-    if (v[im] < 0) for (double &t : v) t = -t;
-}
-
 // cyclic Jacobi for a dense symmetric n x n matrix (row-major A, destroyed);
 // eigenvalues ascending in w, eigenvectors in the columns of Z (row-major)
 static void jacobi_eig(int n, std::vector<double> &A, std::vector<double> &w, std::vector<double> &Z) {
@@ -1277,6 +1198,9 @@ struct Engine {
     float4 *hd() { return hdf.as<float4>(); }
     void use_df_hphi(bool on) { dfh = on && DF && IsC<VT>::v && B.has_k && B.nd > 0; }
     void set_strict(bool) {}
+    // the whole Lanczos loop as one graph: the double-float engine, whose
+    // step does not rotate a host-side ring
+    bool loop_graph_ok() const { return graphs && dfh; }
     // replay Lanczos steps as CUDA graphs (fp64 engine; ignored otherwise)
     int enable_graphs(bool on) {
         graphs = on && DF && B.nchunks > 0;
@@ -1803,12 +1727,326 @@ static int residuals(Basis &B, const WT *v, const std::vector<double> &e, cudaSt
 }
 
 // ------------------------------------------------------- conventional Lanczos
+// The convergence checks of Alg. 10 (the lowest Ritz value of the
+// tridiagonal T_m and its Ritz residual, the small eigenproblem K8) run on
+// the device, one warp per sector, so the loop needs no host round trip: the
+// step kernels and the check form the body of a CUDA graph WHILE node whose
+// condition the device sets (graph mode), or the host launches them and
+// reads one flag every check_every steps (direct mode).  Both run the same
+// kernels, so their results are identical.
+
+// number of eigenvalues of the symmetric tridiagonal (a, b) below x: the sign
+// changes of the Sturm sequence p_0 = 1, p_i = (a_{i-1} - x) p_{i-1} -
+// b_{i-2}^2 p_{i-2} (the leading principal minors of T - x I).  No division:
+// p_i and p_{i-1} are rescaled together by a power of two when |p_i| leaves
+// [2^-500, 2^500], which keeps every ratio exact.  A vanishing p_i takes the
+// sign opposite to p_{i-1} (one change, as for a zero pivot of T - x I = L D L^T
+// counted negative).
+__device__ int sturm_count_dev(int n, const double *__restrict__ a, const double *__restrict__ b, double x) {
+    int cnt = 0, sp = 1;
+    double pm = 0.0, p = 1.0;
+    for (int i = 0; i < n; ++i) {
+        const double bb = i ? b[i - 1] * b[i - 1] : 0.0;
+        const double pn = fma(a[i] - x, p, -bb * pm);
+        const int sn = pn > 0.0 ? 1 : (pn < 0.0 ? -1 : -sp);
+        cnt += sn != sp;
+        sp = sn;
+        pm = p;
+        p = pn;
+        const double ap = fabs(p);
+        if (ap > 0x1p500 || (ap < 0x1p-500 && ap != 0.0)) {
+            const double f = ap > 1.0 ? 0x1p-500 : 0x1p500;
+            p *= f;
+            pm *= f;
+        }
+    }
+    return cnt;
+}
+
+// lowest eigenvalue of the tridiagonal of order n by multisection: the warp
+// evaluates the Sturm count at 31 interior points of a bracket and keeps
+// the first sub-interval that holds an eigenvalue, until the bracket stops
+// shrinking in fp64 (all lanes return the same value).  The bracket starts
+// around e_prev when given (the lowest Ritz value of a shorter Krylov space,
+// which the new one does not exceed) and falls back to the Gershgorin bounds.
+__device__ double tri_lowest_warp(int n, const double *__restrict__ a, const double *__restrict__ b, double e_prev) {
+    const int lane = threadIdx.x & 31;
+    double lo = 1e300, hi = -1e300;
+    for (int i = lane; i < n; i += 32) {
+        const double r = (i ? fabs(b[i - 1]) : 0.0) + (i < n - 1 ? fabs(b[i]) : 0.0);
+        lo = fmin(lo, a[i] - r);
+        hi = fmax(hi, a[i] + r);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const double w = fmax(hi - lo, 1e-300);
+    lo -= 1e-3 * w;
+    hi += 1e-3 * w;
+    if (isfinite(e_prev) && e_prev > lo && e_prev < hi) {
+        // lane 0 tests e_prev + margin (must hold an eigenvalue below it),
+        // lane 1 e_prev - 1e-6 w (must hold none)
+        const double t = lane == 0 ? e_prev + 1e-12 * w : e_prev - 1e-6 * w;
+        const int c = lane < 2 ? sturm_count_dev(n, a, b, t) : 0;
+        const int c0 = __shfl_sync(0xffffffffu, c, 0), c1 = __shfl_sync(0xffffffffu, c, 1);
+        const double t0 = __shfl_sync(0xffffffffu, t, 0), t1 = __shfl_sync(0xffffffffu, t, 1);
+        if (c0 > 0 && t0 < hi) hi = t0;
+        if (c1 == 0 && t1 > lo) lo = t1;
+    }
+    for (int it = 0; it < 64; ++it) {
+        const double h = (hi - lo) / 32.0;
+        const double xl = lo + h * (double)(lane + 1);
+        const int cnt = (lane < 31 && xl > lo && xl < hi) ? sturm_count_dev(n, a, b, xl) : 0;
+        const unsigned mk = __ballot_sync(0xffffffffu, lane < 31 && cnt > 0);
+        const int j = mk ? __ffs(mk) - 1 : 31;
+        const double nlo = j == 0 ? lo : fmax(lo, lo + h * (double)j);
+        const double nhi = j == 31 ? hi : fmin(hi, lo + h * (double)(j + 1));
+        if (!(nlo > lo || nhi < hi)) break;
+        lo = nlo;
+        hi = nhi;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// eigenvector of the tridiagonal for eigenvalue e by inverse iteration
+// (Gaussian elimination with partial pivoting on T - e I, three sweeps; one
+// thread), largest component positive; ws holds 5 n doubles of workspace
+__device__ void tri_vec_dev(int n, const double *__restrict__ a, const double *__restrict__ b, double e,
+                            double *__restrict__ v, double *__restrict__ ws) {
+    for (int i = 0; i < n; ++i) v[i] = 1.0;
+    if (n == 1) return;
+    double *d = ws, *du = ws + n, *du2 = ws + 2 * n, *dl = ws + 3 * n, *x = ws + 4 * n;
+    double scale = 0.0;
+    for (int i = 0; i < n; ++i) scale = fmax(scale, fabs(a[i]) + (i < n - 1 ? fabs(b[i]) : 0.0));
+    const double pert = fmax(scale, 1e-300) * 1e-14;
+    for (int it = 0; it < 3; ++it) {
+        for (int i = 0; i < n; ++i) {
+            d[i] = a[i] - e - pert;
+            du[i] = i < n - 1 ? b[i] : 0.0;
+            dl[i] = du[i];
+            du2[i] = 0.0;
+        }
+        // x[i] records whether row i was swapped (partial pivoting)
+        for (int i = 0; i < n - 1; ++i) {
+            if (fabs(d[i]) >= fabs(dl[i])) {
+                x[i] = 0.0;
+                if (d[i] == 0.0) d[i] = 1e-300;
+                const double f = dl[i] / d[i];
+                dl[i] = f;
+                d[i + 1] -= f * du[i];
+            } else {
+                x[i] = 1.0;
+                const double f = d[i] / dl[i];
+                d[i] = dl[i];
+                dl[i] = f;
+                const double t = du[i];
+                du[i] = d[i + 1];
+                d[i + 1] = t - f * d[i + 1];
+                if (i < n - 2) { du2[i] = du[i + 1]; du[i + 1] = -f * du[i + 1]; }
+            }
+        }
+        if (d[n - 1] == 0.0) d[n - 1] = 1e-300;
+        // forward sweep in place in v (the right-hand side)
+        for (int i = 0; i < n - 1; ++i) {
+            if (x[i] == 0.0) v[i + 1] -= dl[i] * v[i];
+            else { const double t = v[i]; v[i] = v[i + 1]; v[i + 1] = t - dl[i] * v[i + 1]; }
+        }
+        v[n - 1] /= d[n - 1];
+        v[n - 2] = (v[n - 2] - du[n - 2] * v[n - 1]) / d[n - 2];
+        for (int i = n - 3; i >= 0; --i) v[i] = (v[i] - du[i] * v[i + 1] - du2[i] * v[i + 2]) / d[i];
+        double nr = 0.0;
+        for (int i = 0; i < n; ++i) nr += v[i] * v[i];
+        nr = sqrt(nr);
+        if (!(nr > 0.0) || !isfinite(nr)) {
+            for (int i = 0; i < n; ++i) v[i] = 1.0;
+            break;
+        }
+        for (int i = 0; i < n; ++i) v[i] /= nr;
+    }
+    int im = 0;
+    for (int i = 1; i < n; ++i) if (fabs(v[i]) > fabs(v[im])) im = i;
+    if (v[im] < 0.0) for (int i = 0; i < n; ++i) v[i] = -v[i];
+}
+
+// per-sector state of the convergence checks (device)
+struct LzState {
+    DevBuf eprev, eval, msz, conv, coef, ws, cont, nnz;
+    int init(int S, int cap, cudaStream_t st) {
+        QS3_TRY(eprev.alloc((size_t)S * 8));
+        QS3_TRY(eval.alloc((size_t)S * 8));
+        QS3_TRY(msz.alloc((size_t)S * 4));
+        QS3_TRY(conv.alloc((size_t)S * 4));
+        QS3_TRY(coef.alloc((size_t)S * cap * 8));
+        QS3_TRY(ws.alloc((size_t)S * 5 * cap * 8));
+        QS3_TRY(cont.alloc(4));
+        QS3_TRY(nnz.alloc(8));
+        // eprev = NaN (no previous Ritz value); everything else 0
+        QS3_CUDA(cudaMemsetAsync(eprev.p, 0xff, eprev.n, st));
+        QS3_CUDA(cudaMemsetAsync(eval.p, 0xff, eval.n, st));
+        QS3_CUDA(cudaMemsetAsync(msz.p, 0, msz.n, st));
+        QS3_CUDA(cudaMemsetAsync(conv.p, 0, conv.n, st));
+        QS3_CUDA(cudaMemsetAsync(nnz.p, 0, nnz.n, st));
+        return QS3_OK;
+    }
+};
+
+// after n steps (n = *dx in graph mode): for every active sector count the
+// step's H Phi work, and when a check is due (n >= min_iter and n a multiple
+// of every, or n = nmax) take the lowest Ritz value e of T_m (m = n, or up
+// to the first vanishing beta: an invariant subspace, whose Ritz values are
+// exact).  Converged: |e - e_prev| <= eps |e| and the Ritz residual
+// beta_{m-1} |c_{m-1}| <= res_tol max(|e|, 1).  A converged sector (or any at
+// n = nmax) stores its Ritz coefficients and leaves the active set.
+__global__ void __launch_bounds__(32) k_lz_check(int n_arg, const int *__restrict__ dx, const double *__restrict__ alpha,
+                                                 const double *__restrict__ beta, int cap, int *__restrict__ active,
+                                                 const uint64_t *__restrict__ nnz_sec,
+                                                 unsigned long long *__restrict__ nnz_acc, double *__restrict__ eprev,
+                                                 double *__restrict__ eval, int *__restrict__ msz,
+                                                 int *__restrict__ conv, double *__restrict__ coef,
+                                                 double *__restrict__ ws, double eps, double res_tol, int min_iter,
+                                                 int every, int nmax) {
+    const int s = blockIdx.x, lane = threadIdx.x;
+    const int n = dx ? *dx : n_arg;
+    if (!active[s]) return;
+    if (lane == 0) atomicAdd(nnz_acc, (unsigned long long)nnz_sec[s]);
+    if (!((n >= min_iter && n % every == 0) || n >= nmax)) return;
+    const double *a = alpha + (size_t)s * cap, *b = beta + (size_t)s * cap;
+    // the first vanishing beta ends the Krylov sequence
+    int m = n;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const unsigned z = __ballot_sync(0xffffffffu, k0 + lane < n && b[k0 + lane] == 0.0);
+        if (z) { m = k0 + __ffs(z); break; }
+    }
+    const bool brk = m < n || b[m - 1] == 0.0;
+    const double e = tri_lowest_warp(m, a, b, eprev[s]);
+    if (lane == 0) {
+        const double ep = eprev[s];
+        bool ok = brk || (isfinite(ep) && fabs(e - ep) <= eps * fabs(e));
+        double *v = coef + (size_t)s * cap;
+        bool have_v = false;
+        if (ok && !brk && res_tol > 0.0) {
+            tri_vec_dev(m, a, b, e, v, ws + (size_t)s * 5 * cap);
+            have_v = true;
+            ok = fabs(b[m - 1] * v[m - 1]) <= res_tol * fmax(fabs(e), 1.0);
+        }
+        eprev[s] = e;
+        eval[s] = e;
+        msz[s] = m;
+        if (ok || n >= nmax) {
+            if (!have_v) tri_vec_dev(m, a, b, e, v, ws + (size_t)s * 5 * cap);
+            conv[s] = ok ? 1 : 0;
+            active[s] = 0;
+        }
+    }
+}
+
+// loop condition after n steps: some sector still active and n < nmax;
+// written to *cont and, in graph mode, to the WHILE node's condition
+__global__ void __launch_bounds__(32) k_lz_cond(int n_arg, const int *__restrict__ dx, const int *__restrict__ active,
+                                                int S, int nmax, int *__restrict__ cont,
+                                                cudaGraphConditionalHandle h, int use_h) {
+    const int n = dx ? *dx : n_arg;
+    int any = 0;
+    for (int s = threadIdx.x; s < S; s += 32) any |= active[s];
+    any = __any_sync(0xffffffffu, any);
+    if (threadIdx.x == 0) {
+        const int c = (any && n < nmax) ? 1 : 0;
+        *cont = c;
+        if (use_h) cudaGraphSetConditional(h, c);
+    }
+}
 
 struct LzResult {
     std::vector<double> e;       // per sector
     std::vector<int> conv;
     int steps = 0;
 };
+
+// the Lanczos loop of steps 1 .. (until no sector is active or nmax) as one
+// graph: [k_lz_cond -> WHILE { step, k_lz_check, k_lz_cond }], captured once
+template <typename EN>
+static int lanczos_loop_graph(EN &E, LzState &K, Basis &B, const qs3_solve_opts &o, int nmax, int every,
+                              const uint64_t *nnz_sec, int &steps) {
+    cudaStream_t cs = nullptr;
+    QS3_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t keep = E.st;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t gx = nullptr;
+    int rc = QS3_OK;
+    auto fail = [&](const char *what, cudaError_t e) {
+        rc = set_err(QS3_ERR_CUDA, "Lanczos loop graph, %s: %s", what, cudaGetErrorString(e));
+    };
+    do {
+        cudaError_t e;
+        if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) { fail("create", e); break; }
+        cudaGraphConditionalHandle h;
+        if ((e = cudaGraphConditionalHandleCreate(&h, g, 0, 0)) != cudaSuccess) { fail("handle", e); break; }
+        // prologue: the first condition
+        if ((e = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess) { fail("capture", e); break; }
+        k_lz_cond<<<1, 32, 0, cs>>>(0, E.xdev.template as<int>(), E.act(), B.S, nmax, K.cont.as<int>(), h, 1);
+        cudaStreamCaptureStatus cst;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        if ((e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &nd)) != cudaSuccess) {
+            fail("capture info", e);
+            cudaGraph_t tmp;
+            cudaStreamEndCapture(cs, &tmp);
+            break;
+        }
+        std::vector<cudaGraphNode_t> dv(deps, deps + nd);
+        if ((e = cudaStreamEndCapture(cs, &g)) != cudaSuccess) { fail("end capture", e); break; }
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t wn;
+        if ((e = cudaGraphAddNode(&wn, g, dv.data(), nullptr, dv.size(), &cp)) != cudaSuccess) { fail("while", e); break; }
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        // body: one step (x from xdev, advanced by the step), the check and the condition
+        if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess) { fail("body capture", e); break; }
+        E.st = cs;
+        int r = E.step_body_dev();
+        if (r == QS3_OK) {
+            k_lz_check<<<B.S, 32, 0, cs>>>(0, E.xdev.template as<int>(), E.alpha.template as<double>(),
+                                           E.beta.template as<double>(), E.cap, E.act(), nnz_sec,
+                                           K.nnz.as<unsigned long long>(), K.eprev.as<double>(), K.eval.as<double>(),
+                                           K.msz.as<int>(), K.conv.as<int>(), K.coef.as<double>(), K.ws.as<double>(),
+                                           o.eps, o.res_tol, o.min_iter, every, nmax);
+            k_lz_cond<<<1, 32, 0, cs>>>(0, E.xdev.template as<int>(), E.act(), B.S, nmax, K.cont.as<int>(), h, 1);
+        }
+        E.st = keep;
+        cudaGraph_t bo = nullptr;
+        e = cudaStreamEndCapture(cs, &bo);
+        if (r != QS3_OK) { rc = r; break; }
+        if (e != cudaSuccess) { fail("body end capture", e); break; }
+        size_t nn = 0;
+        cudaGraphGetNodes(body, nullptr, &nn);
+        count_launch(-(long long)(nn - 2));   // the step's kernels were counted while captured
+        if ((e = cudaGraphInstantiate(&gx, g, 0)) != cudaSuccess) { gx = nullptr; fail("instantiate", e); break; }
+        // x = 1 on the device, then the whole loop
+        k_setx<<<1, 1, 0, E.st>>>(E.xdev.template as<int>(), 1);
+        count_launch();
+        if ((e = cudaGraphLaunch(gx, E.st)) != cudaSuccess) { fail("launch", e); break; }
+        if ((e = cudaStreamSynchronize(E.st)) != cudaSuccess) { fail("run", e); break; }
+        if ((e = cudaMemcpy(&steps, E.xdev.p, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            fail("step count", e);
+            break;
+        }
+        count_launch(1 + (long long)(steps - 1) * (long long)nn);    // the prologue and every iteration
+    } while (false);
+    if (gx) cudaGraphExecDestroy(gx);
+    if (g) cudaGraphDestroy(g);
+    if (cs) {
+        cudaStreamSynchronize(E.st);
+        cudaStreamDestroy(cs);
+    }
+    return rc;
+}
 
 // Lanczos to the lowest eigenpair of each sector; out (fp64, total dim) gets the vectors.
 template <typename VT, typename EN = Engine<VT>>
@@ -1824,76 +2062,85 @@ static int lanczos_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT
     const int S = B.S;
     R.e.assign(S, NAN);
     R.conv.assign(S, 0);
-    std::vector<double> eprev(S, NAN), a, b;
-    std::vector<int> msize(S, 0), fin(S, 0);
-    std::vector<std::vector<double>> coef(S);
     for (int s = 0; s < S; ++s)
         if (!B.dims[s]) R.conv[s] = 1;
     const int every = std::max(1, o.check_every);
-    const auto tl0 = std::chrono::steady_clock::now();
-    int x = 0;
-    for (; x < nmax && E.any_active(); ++x) {
-        QS3_TRY(E.step(x));
-        const int n = x + 1;
-        if (!((n >= o.min_iter && n % every == 0) || n == nmax)) continue;
-        QS3_TRY(E.fetch(a, b));
-        std::vector<int> newly(S, 0);
-        bool any = false;
-        for (int s = 0; s < S; ++s) {
-            if (!E.h_active[s]) continue;
-            const double *as = &a[(size_t)s * E.cap], *bs = &b[(size_t)s * E.cap];
-            int m = n;
-            bool brk = false;
-            for (int k = 0; k < n; ++k)
-                if (bs[k] == 0.0) { m = k + 1; brk = true; break; }
-            const double e = tri_eig_k(m, as, bs, 0);
-            bool ok = brk || (std::isfinite(eprev[s]) && std::fabs(e - eprev[s]) <= o.eps * std::fabs(e));
-            double rres = 0.0;
-            if ((ok || log_on()) && !brk && o.res_tol > 0) {
-                // Ritz residual |H y - e y| = beta_{m-1} |c_{m-1}| (full reorthogonalisation keeps it exact)
-                std::vector<double> c;
-                tri_eigvec(m, as, bs, e, c);
-                rres = std::fabs(bs[m - 1] * c[m - 1]);
-                ok = ok && rres <= o.res_tol * std::max(std::fabs(e), 1.0);
+    LzState K;
+    QS3_TRY(K.init(S, E.cap, st));
+    DevBuf dnnz;
+    QS3_TRY(dnnz.upload(B.nnz_sec.data(), (size_t)S * 8));
+    const uint64_t nz0 = hs.nnz;
+    int cont = 0;
+    auto check = [&](int n) -> int {
+        k_lz_check<<<S, 32, 0, st>>>(n, nullptr, E.alpha.template as<double>(), E.beta.template as<double>(), E.cap,
+                                     E.act(), dnnz.as<uint64_t>(), K.nnz.as<unsigned long long>(),
+                                     K.eprev.as<double>(), K.eval.as<double>(), K.msz.as<int>(), K.conv.as<int>(),
+                                     K.coef.as<double>(), K.ws.as<double>(), o.eps, o.res_tol, o.min_iter, every,
+                                     nmax);
+        QS3_LAUNCHED();
+        return QS3_OK;
+    };
+    auto cond = [&](int n) -> int {
+        k_lz_cond<<<1, 32, 0, st>>>(n, nullptr, E.act(), S, nmax, K.cont.as<int>(), 0, 0);
+        QS3_LAUNCHED();
+        QS3_CUDA(cudaMemcpyAsync(&cont, K.cont.p, 4, cudaMemcpyDeviceToHost, st));
+        QS3_CUDA(cudaStreamSynchronize(st));
+        // the host copy of the active set (the engine's statistics)
+        QS3_CUDA(cudaMemcpy(E.h_active.data(), E.active.p, S * sizeof(int), cudaMemcpyDeviceToHost));
+        return QS3_OK;
+    };
+    if (B.nchunks > 0) {
+        QS3_TRY(E.step(0));
+        QS3_TRY(check(1));
+        QS3_TRY(cond(1));
+        if (cont && E.loop_graph_ok()) {
+            QS3_TRY(lanczos_loop_graph(E, K, B, o, nmax, every, dnnz.as<uint64_t>(), R.steps));
+            hs.calls += R.steps - 1;
+            hs.graph_calls += R.steps - 1;
+        } else {
+            int x = 1;
+            for (; cont && x < nmax; ++x) {
+                QS3_TRY(E.step(x));
+                const int n = x + 1;
+                QS3_TRY(check(n));
+                if ((n >= o.min_iter && n % every == 0) || n >= nmax) QS3_TRY(cond(n));
             }
-            if (log_on())
-                fprintf(stderr, "[qs3] lanczos vt=%zu n=%d s=%d m=%d e=%.17g de=%.3g beta=%.3g rres=%.3g ok=%d t=%.4f\n",
-                        sizeof(VT), n, s, m, e, e - eprev[s], bs[m - 1], rres, (int)ok,
-                        std::chrono::duration<double>(std::chrono::steady_clock::now() - tl0).count());
-            eprev[s] = e;
-            R.e[s] = e;
-            msize[s] = m;
-            if (ok || n == nmax) {
-                newly[s] = 1;
-                any = true;
-                R.conv[s] = ok;
-            }
-        }
-        if (any) {
-            // Ritz vector coefficients of the newly finished sectors; the sectors
-            // leave every launch, so their stored basis stays intact until the
-            // single combination at the end
-            for (int s = 0; s < S; ++s) {
-                if (!newly[s]) continue;
-                tri_eigvec(msize[s], &a[(size_t)s * E.cap], &b[(size_t)s * E.cap], R.e[s], coef[s]);
-                E.h_active[s] = 0;
-                fin[s] = 1;
-            }
-            QS3_TRY(E.push_active());
+            R.steps = x;
         }
     }
-    // psi = sum_x c_x psi_x over the computed vectors (later slots are uninitialised)
+    // results of every sector (the converged ones and those stopped at nmax)
+    std::vector<double> ev(S), coef((size_t)S * E.cap);
+    std::vector<int> msz(S), conv(S);
+    unsigned long long nzd = 0;
+    QS3_CUDA(cudaMemcpyAsync(ev.data(), K.eval.p, S * 8, cudaMemcpyDeviceToHost, st));
+    QS3_CUDA(cudaMemcpyAsync(msz.data(), K.msz.p, S * 4, cudaMemcpyDeviceToHost, st));
+    QS3_CUDA(cudaMemcpyAsync(conv.data(), K.conv.p, S * 4, cudaMemcpyDeviceToHost, st));
+    QS3_CUDA(cudaMemcpyAsync(coef.data(), K.coef.p, coef.size() * 8, cudaMemcpyDeviceToHost, st));
+    QS3_CUDA(cudaMemcpyAsync(&nzd, K.nnz.p, 8, cudaMemcpyDeviceToHost, st));
+    QS3_CUDA(cudaStreamSynchronize(st));
+    QS3_TRY(hs.harvest());
+    hs.nnz = nz0 + nzd;
+    if (log_on())
+        for (int s = 0; s < S; ++s)
+            fprintf(stderr, "[qs3] lanczos vt=%zu s=%d m=%d e=%.17g conv=%d steps=%d\n", sizeof(VT), s, msz[s], ev[s],
+                    conv[s], R.steps);
+    std::vector<int> fin(S, 0);
     int nin = 0;
-    for (int s = 0; s < S; ++s)
-        if (fin[s]) nin = std::max(nin, msize[s]);
+    for (int s = 0; s < S; ++s) {
+        if (!B.dims[s]) continue;
+        R.e[s] = ev[s];
+        R.conv[s] = conv[s];
+        fin[s] = msz[s] > 0;
+        nin = std::max(nin, msz[s]);
+    }
+    // psi = sum_x c_x psi_x over the computed vectors (later slots are uninitialised)
     if (nin > 0) {
         std::vector<double> C((size_t)S * nin, 0.0);
         for (int s = 0; s < S; ++s)
             if (fin[s])
-                for (int k = 0; k < msize[s]; ++k) C[(size_t)s * nin + k] = coef[s][k];
+                for (int k = 0; k < msz[s]; ++k) C[(size_t)s * nin + k] = coef[(size_t)s * E.cap + k];
         QS3_TRY(E.template combine<typename Wide<VT>::T>(out, B.total, nin, 1, C, fin));
     }
-    R.steps = x;
     return QS3_OK;
 }
 
@@ -1907,7 +2154,8 @@ struct TrlResult {
 
 template <typename VT, typename EN = Engine<VT>>
 static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T *start,
-                   typename Wide<VT>::T *out, cudaStream_t st, TrlResult &R, HphiStats &hs) {
+                   typename Wide<VT>::T *out, cudaStream_t st, TrlResult &R, HphiStats &hs, int nconv = 0,
+                   const std::vector<double> *targets = nullptr) {
     using WT = typename Wide<VT>::T;
     const int S = B.S;
     const int NM = std::max(2, o.n_max);
@@ -1925,7 +2173,15 @@ static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T
     for (int s = 0; s < S; ++s)
         if (!B.dims[s]) R.conv[s] = 1;
     std::vector<double> a, b;
-    std::vector<std::vector<double>> ev(S), Cm(S), eprev(S), bK(S);
+    std::vector<std::vector<double>> ev(S), Cm(S), eprev(S), bK(S), rres(S);
+    // nconv > 0 (the binary64 refinement of an fp32 run): the criterion covers
+    // the nconv lowest kept values only, needs their Ritz residuals
+    // beta_{N_M} |c_{N_M, y}| <= res_tol max(|e_y|, 1), and needs them to
+    // reproduce the fp32 run's values (targets, S x nconv) within fp32
+    // accuracy, so a copy of a degenerate level that the single start vector
+    // lacks at first is waited for; 0: the paper's criterion over all N_K
+    // kept values
+    const int ny = nconv > 0 ? std::min(nconv, NK) : NK;
     std::vector<int> msize(S, NM);
     int steps = 0;
     // finish the sectors in `done`: write their NE lowest Ritz vectors
@@ -1964,6 +2220,8 @@ static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T
                 if (i + 1 < m) T[(size_t)i * m + i + 1] = T[(size_t)(i + 1) * m + i] = bs[i];
             }
             jacobi_eig(m, T, ev[s], Cm[s]);
+            rres[s].assign(m, 0.0);
+            for (int y = 0; y < m; ++y) rres[s][y] = std::fabs(bs[m - 1] * Cm[s][(size_t)(m - 1) * m + y]);
             if (m < NM || bs[NM - 1] == 0.0) { done[s] = 1; R.conv[s] = 1; }   // Krylov space exhausted
         }
         QS3_TRY(finish(done));
@@ -1976,8 +2234,17 @@ static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T
             if (!E.h_active[s]) continue;
             if (I > 1) {
                 double dmax = 0.0;
-                for (int y = 0; y < NK; ++y) dmax = std::max(dmax, std::fabs(eprev[s][y] / ev[s][y] - 1.0));
-                if (dmax < o.eps) { done[s] = 1; R.conv[s] = 1; anyc = true; }
+                for (int y = 0; y < ny; ++y) dmax = std::max(dmax, std::fabs(eprev[s][y] / ev[s][y] - 1.0));
+                bool ok = dmax < o.eps;
+                if (ok && nconv > 0 && o.res_tol > 0)
+                    for (int y = 0; y < ny && y < (int)rres[s].size(); ++y)
+                        ok = ok && rres[s][y] <= o.res_tol * std::max(std::fabs(ev[s][y]), 1.0);
+                if (ok && nconv > 0 && targets)
+                    for (int y = 0; y < ny; ++y) {
+                        const double tg = (*targets)[(size_t)s * ny + y];
+                        if (std::isfinite(tg)) ok = ok && std::fabs(ev[s][y] - tg) <= 1e-4 * std::max(std::fabs(tg), 1.0);
+                    }
+                if (ok) { done[s] = 1; R.conv[s] = 1; anyc = true; }
             }
             eprev[s].assign(ev[s].begin(), ev[s].begin() + NK);
         }
@@ -2016,6 +2283,8 @@ static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T
             }
             std::vector<double> w2, Z2;
             jacobi_eig(m, T, w2, Z2);
+            rres[s].assign(m, 0.0);
+            for (int y = 0; y < m; ++y) rres[s][y] = std::fabs(bs[m - 1] * Z2[(size_t)(m - 1) * m + y]);
             if (m < NM) {            // invariant subspace: the Ritz values are exact
                 msize[s] = m;
                 ev[s] = w2;
@@ -2165,10 +2434,18 @@ static int trl_entry(Basis &B, const qs3_solve_opts &o, double *evals, void *eve
             }
             QS3_CUDA(cudaStreamSynchronize(st));
         }
+        // binary64 refinement: the wanted n_eig values to refine_tol, with
+        // their Ritz residuals below refine_tol |E| as well
         TrlResult R2;
         qs3_solve_opts o2 = o;
-        if (o.refine_tol > 0) o2.eps = std::max(o.eps, 0.1 * o.refine_tol);
-        QS3_TRY((trl_run<V64, Engine64<V64>>(B, o2, sum.as<V64>(), out, st, R2, hs)));
+        if (o.refine_tol > 0) {
+            o2.eps = std::max(o.eps, 0.1 * o.refine_tol);
+            o2.res_tol = o.refine_tol;
+        }
+        std::vector<double> tg((size_t)B.S * NE);
+        for (int s = 0; s < B.S; ++s)
+            for (int y = 0; y < NE; ++y) tg[(size_t)s * NE + y] = R.e[(size_t)s * NK + y];
+        QS3_TRY((trl_run<V64, Engine64<V64>>(B, o2, sum.as<V64>(), out, st, R2, hs, NE, &tg)));
         refine = R2.steps;
         iters += R2.steps;
         restarts += R2.restarts;
