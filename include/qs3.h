@@ -68,9 +68,17 @@ typedef enum { QS3_OP_SPLUS = 1, QS3_OP_SMINUS = 2, QS3_OP_SZ = 3 } qs3_sq_op;
 /* Lattice and couplings of Eq. (1): H = sum_b [Jxy_b (s^x s^x + s^y s^y) +
  * Jz_b s^z s^z] - sum_i h_i s^z_i.  Bond b joins sites bi[b] != bj[b]; a
  * repeated pair adds its couplings.  h may be NULL (no field).  L = {0,0,0}
- * means no translation group (U(1) only); otherwise Lx*Ly*Lz must equal
+ * means no translation group (U(1) only).  Otherwise L is the translation
+ * group of the unit cells and n_sub the spins per cell (0 or 1: a Bravais
+ * lattice, one spin per cell; more: the multi-spin cells the paper's Summary
+ * names, e.g. honeycomb or kagome): site r is spin r % n_sub of the cell
+ * r / n_sub, cells numbered x + Lx (y + Ly z), T^t moves every cell by +t
+ * and keeps each spin's place in its cell, and n_sub*Lx*Ly*Lz must equal
  * n_sites.  pos (3*n_sites doubles, in lattice units) gives the site
- * positions used by e^{-i q.r}; NULL means the coordinates (x, y, z).
+ * positions used by e^{-i q.r}; NULL means the cell coordinates (x, y, z).
+ * The S^alpha_q operators, S(q, omega) and the translation-symmetrised
+ * correlations of k-sectors take one spin per cell, and S(q) of a lattice
+ * with several needs pos (INVALID_ARG otherwise).
  * All pointers are host pointers and are copied; the caller keeps them. */
 typedef struct {
     int32_t n_sites, n_bonds;
@@ -79,6 +87,8 @@ typedef struct {
     const double *h;
     int32_t L[3];
     const double *pos;
+    int32_t n_sub;
+    int32_t reserved;
 } qs3_lattice;
 
 typedef struct qs3_basis_s *qs3_basis_t;

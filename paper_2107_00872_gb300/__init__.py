@@ -145,6 +145,7 @@ class Basis:
         L = tuple(getattr(lattice, "L", (0, 0, 0)) or (0, 0, 0))
         lat.L[0], lat.L[1], lat.L[2] = int(L[0]), int(L[1]), int(L[2])
         lat.pos = _ptr(arr(getattr(lattice, "pos", None), np.float64))
+        lat.n_sub = int(getattr(lattice, "n_sub", 1) or 1)
         self.lattice = lattice
         self.n_down = int(n_down)
         if K is None:

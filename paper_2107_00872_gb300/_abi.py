@@ -19,7 +19,7 @@ STATUS = {0: "QS3_OK", -1: "QS3_ERR_INVALID_ARG", -2: "QS3_ERR_OVERFLOW", -3: "Q
 
 class qs3_lattice(ctypes.Structure):
     _fields_ = [("n_sites", I32), ("n_bonds", I32), ("bi", P), ("bj", P), ("jxy", P), ("jz", P), ("h", P),
-                ("L", I32 * 3), ("pos", P)]
+                ("L", I32 * 3), ("pos", P), ("n_sub", I32), ("reserved", I32)]
 
 
 class qs3_solve_opts(ctypes.Structure):

@@ -95,8 +95,17 @@ size_t row_kernel_smem(const Basis &B, int /*extra_nd*/) {
 
 // ------------------------------------------------------ enumeration kernel
 
+// Candidates: the states with a spin at site (cell 0, place s0) and none on
+// places below s0 (s0 = the lowest place of the cell that the state
+// occupies; with one spin per cell s0 = 0): the other N_down - 1 spins are
+// an (N_down - 1)-subset of the M - 1 sites after it in the list of sites
+// with place >= s0 (index q -> place s0 + q % w, cell q / w, w = nsub - s0).
+// Every orbit has such members (move any spin on place s0 to cell 0); a
+// candidate is designated when it has the smallest rank of them, so each
+// orbit is taken once, from its designated member, with |Stab| (the moves
+// that give the candidate back) and the compatibility of those moves with K.
 template <int ND>
-__global__ void __launch_bounds__(NTHREADS) k_enum_reps(LatView L, int Kx, int Ky, int Kz, uint64_t ncand,
+__global__ void __launch_bounds__(NTHREADS) k_enum_reps(LatView L, int Kx, int Ky, int Kz, int s0, uint64_t ncand,
                                                         int emit, unsigned long long *counter,
                                                         uint64_t *out_rank, uint8_t *out_stab) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -107,7 +116,7 @@ __global__ void __launch_bounds__(NTHREADS) k_enum_reps(LatView L, int Kx, int K
     for (int i = threadIdx.x; i < L.N; i += blockDim.x) sxyz[i] = L.xyz[i];
     __syncthreads();
     const int Lx = L.L[0], Ly = L.L[1], Lz = L.L[2];
-    const int N = L.N;
+    const int G = L.ncell, ns = L.nsub, w = ns - s0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < ncand; base += stride) {
         const uint64_t j = base + threadIdx.x;
@@ -116,43 +125,48 @@ __global__ void __launch_bounds__(NTHREADS) k_enum_reps(LatView L, int Kx, int K
         int st = 0;
         if (j < ncand) {
             int c[ND];
-            c[0] = 0;
+            c[0] = s0;
             if (ND >= 2) {
                 constexpr int NM1 = (ND > 1) ? ND - 1 : 1;
                 int cc[NM1];
                 unrank<NM1>(j, sC, L.np1, cc);
 #pragma unroll
-                for (int m = 0; m + 1 < ND; ++m) c[m + 1] = cc[m] + 1;
+                for (int m = 0; m + 1 < ND; ++m) {
+                    const int q = cc[m] + 1;
+                    c[m + 1] = (w == 1) ? s0 + ns * q : s0 + q % w + ns * (q / w);
+                }
             }
             const uint64_t rc = rank_of(c, sC, L.np1);
-            int X[ND], Y[ND], Z[ND];
+            int X[ND], Y[ND], Z[ND], SB[ND];
 #pragma unroll
             for (int m = 0; m < ND; ++m) {
                 uint32_t p = sxyz[c[m]];
                 X[m] = p & 2047u;
                 Y[m] = (p >> 11) & 2047u;
                 Z[m] = p >> 22;
+                SB[m] = ns > 1 ? c[m] % ns : 0;
             }
             bool designated = true, compat = true;
 #pragma unroll
             for (int m = 0; m < ND; ++m) {
-                int s[ND];
+                if (SB[m] != s0) continue;
+                int sl[ND];
 #pragma unroll
                 for (int q = 0; q < ND; ++q) {
                     int xx = X[q] - X[m]; xx += (xx < 0) ? Lx : 0;
                     int yy = Y[q] - Y[m]; yy += (yy < 0) ? Ly : 0;
                     int zz = Z[q] - Z[m]; zz += (zz < 0) ? Lz : 0;
-                    s[q] = xx + Lx * (yy + Ly * zz);
+                    sl[q] = SB[q] + ns * (xx + Lx * (yy + Ly * zz));
                 }
-                sort_net(s);
-                const uint64_t rm = rank_of(s, sC, L.np1);
+                sort_net(sl);
+                const uint64_t rm = rank_of(sl, sC, L.np1);
                 designated &= (rm >= rc);
                 if (rm == rc) {
                     ++st;
-                    // stabiliser element t = pos(c_m): compatible iff k.t is a multiple of 2 pi
-                    long long num = (long long)Kx * X[m] * (N / Lx) + (long long)Ky * Y[m] * (N / Ly) +
-                                    (long long)Kz * Z[m] * (N / Lz);
-                    compat &= (num % N) == 0;
+                    // stabiliser element t = cell(c_m): compatible iff k.t is a multiple of 2 pi
+                    long long num = (long long)Kx * X[m] * (G / Lx) + (long long)Ky * Y[m] * (G / Ly) +
+                                    (long long)Kz * Z[m] * (G / Lz);
+                    compat &= (num % G) == 0;
                 }
             }
             take = designated && compat;
@@ -207,10 +221,10 @@ __global__ void k_pidx(const uint32_t *__restrict__ P, uint64_t d, uint32_t np, 
 template <int ND>
 static int enum_sorted_reps(Basis &B, const int *K, DevBuf &kout, DevBuf &vout, uint64_t &d,
                             std::vector<uint64_t> &hb, int &nsm) {
-    // C(N-1, ND-1) candidates
+    // per lowest occupied place s0 of the cell: C(M - 1, ND - 1) candidates,
+    // M = (cells) (nsub - s0); one spin per cell: C(N - 1, ND - 1)
     hb.resize((size_t)(B.nd + 3) * (B.N + 1));
     QS3_CUDA(cudaMemcpy(hb.data(), B.d_binom.p, hb.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
-    const uint64_t nc = hb[(size_t)(ND - 1) * (B.N + 1) + (B.N - 1)];
     const size_t smem = (size_t)(B.nd + 3) * (B.N + 1) * 8 + (size_t)B.N * 4;
     QS3_CUDA(cudaFuncSetAttribute(k_enum_reps<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
     DevBuf cnt;
@@ -219,11 +233,23 @@ static int enum_sorted_reps(Basis &B, const int *K, DevBuf &kout, DevBuf &vout, 
     int dev = 0;
     QS3_CUDA(cudaGetDevice(&dev));
     QS3_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    uint64_t want = (nc + NTHREADS - 1) / NTHREADS;
-    int grid = (int)std::min<uint64_t>(want ? want : 1, (uint64_t)nsm * 8);
-    k_enum_reps<ND><<<grid, NTHREADS, smem>>>(B.lv, K[0], K[1], K[2], nc, 0, cnt.as<unsigned long long>(),
-                                              nullptr, nullptr);
-    QS3_LAUNCHED();
+    std::vector<uint64_t> nc(B.nsub, 0);
+    for (int s0 = 0; s0 < B.nsub; ++s0) {
+        const uint64_t M = (uint64_t)B.ncell * (B.nsub - s0);
+        nc[s0] = (M >= 1 && M - 1 >= (uint64_t)(ND - 1)) ? hb[(size_t)(ND - 1) * (B.N + 1) + (M - 1)] : 0;
+    }
+    auto run = [&](int emit, uint64_t *kp, uint8_t *vp) -> int {
+        for (int s0 = 0; s0 < B.nsub; ++s0) {
+            if (!nc[s0]) continue;
+            const uint64_t want = (nc[s0] + NTHREADS - 1) / NTHREADS;
+            const int grid = (int)std::min<uint64_t>(want ? want : 1, (uint64_t)nsm * 8);
+            k_enum_reps<ND><<<grid, NTHREADS, smem>>>(B.lv, K[0], K[1], K[2], s0, nc[s0], emit,
+                                                      cnt.as<unsigned long long>(), kp, vp);
+            QS3_LAUNCHED();
+        }
+        return QS3_OK;
+    };
+    QS3_TRY(run(0, nullptr, nullptr));
     d = 0;
     QS3_CUDA(cudaMemcpy(&d, cnt.p, sizeof(d), cudaMemcpyDeviceToHost));
     if (d >= (1ull << 32)) return set_err(QS3_ERR_OVERFLOW, "sector dimension %llu exceeds 2^32", (unsigned long long)d);
@@ -231,9 +257,7 @@ static int enum_sorted_reps(Basis &B, const int *K, DevBuf &kout, DevBuf &vout, 
     QS3_TRY(kin.alloc(d * 8));
     QS3_TRY(vin.alloc(d));
     QS3_CUDA(cudaMemset(cnt.p, 0, sizeof(unsigned long long)));
-    k_enum_reps<ND><<<grid, NTHREADS, smem>>>(B.lv, K[0], K[1], K[2], nc, 1, cnt.as<unsigned long long>(),
-                                              kin.as<uint64_t>(), vin.as<uint8_t>());
-    QS3_LAUNCHED();
+    QS3_TRY(run(1, kin.as<uint64_t>(), vin.as<uint8_t>()));
     QS3_TRY(kout.alloc(d * 8));
     QS3_TRY(vout.alloc(d));
     if (d > 0) {
@@ -315,15 +339,15 @@ __global__ void __launch_bounds__(NTHREADS) k_orbit_fill(LatView L, const uint64
     for (int i = threadIdx.x; i < nC; i += blockDim.x) sC[i] = L.binom[i];
     for (int i = threadIdx.x; i < L.N; i += blockDim.x) sxyz[i] = L.xyz[i];
     __syncthreads();
-    const int Lx = L.L[0], Ly = L.L[1], Lz = L.L[2], N = L.N;
-    const uint64_t total = n * (uint64_t)N;
+    const int Lx = L.L[0], Ly = L.L[1], Lz = L.L[2], G = L.ncell, ns = L.nsub;
+    const uint64_t total = n * (uint64_t)G;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t g = i / (uint64_t)N;
-        const int u = (int)(i - g * (uint64_t)N);
+        const uint64_t g = i / (uint64_t)G;
+        const int u = (int)(i - g * (uint64_t)G);         // cell translation
         int c[ND];
         unrank(reps[g], sC, L.np1, c);
-        const uint32_t pu = sxyz[u];
+        const uint32_t pu = sxyz[u * ns];                  // the coordinates of cell u
         const int ux = pu & 2047u, uy = (pu >> 11) & 2047u, uz = pu >> 22;
         int t[ND];
 #pragma unroll
@@ -333,7 +357,7 @@ __global__ void __launch_bounds__(NTHREADS) k_orbit_fill(LatView L, const uint64
             x -= (x >= Lx) ? Lx : 0;
             y -= (y >= Ly) ? Ly : 0;
             z -= (z >= Lz) ? Lz : 0;
-            t[m] = x + Lx * (y + Ly * z);
+            t[m] = c[m] % ns + ns * (x + Lx * (y + Ly * z));
         }
         sort_net(t);
         orb[rank_of(t, sC, L.np1)] = ((uint32_t)g << 12) | (uint32_t)u;
@@ -365,7 +389,7 @@ static int build_table_nd(Basis &B, size_t max_bytes) {
     QS3_CUDA(cudaMemcpy(hb.data(), B.d_binom.p, hb.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost));
     const uint64_t ns = hb[(size_t)ND * (B.N + 1) + B.N];           // C(N, N_down)
     if (ns >= (1ull << 32)) return set_err(QS3_ERR_OVERFLOW, "C(N, N_down) = %llu states: no table", (unsigned long long)ns);
-    const uint64_t n_est = ns / (uint64_t)B.N + 1;                 // orbits, about C(N, N_down) / N
+    const uint64_t n_est = ns / (uint64_t)B.ncell + 1;             // orbits, about C(N, N_down) / (cells)
     if (ns * 4 + n_est * 4 * (uint64_t)B.S > max_bytes)
         return set_err(QS3_ERR_OOM, "representative table of ~%llu bytes exceeds the limit",
                        (unsigned long long)(ns * 4 + n_est * 4 * (uint64_t)B.S));
@@ -384,7 +408,7 @@ static int build_table_nd(Basis &B, size_t max_bytes) {
     QS3_CUDA(cudaMemset(orb.p, 0xff, ns * 4));
     const size_t smem = (size_t)(B.nd + 3) * (B.N + 1) * 8 + (size_t)B.N * 4;
     QS3_CUDA(cudaFuncSetAttribute(k_orbit_fill<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
-    const uint64_t tot = n * (uint64_t)B.N;
+    const uint64_t tot = n * (uint64_t)B.ncell;
     int grid = (int)std::min<uint64_t>((tot + NTHREADS - 1) / NTHREADS, (uint64_t)nsm * 8);
     k_orbit_fill<ND><<<std::max(grid, 1), NTHREADS, smem>>>(B.lv, reps.as<uint64_t>(), n, orb.as<uint32_t>());
     QS3_LAUNCHED();
@@ -433,16 +457,19 @@ void drop_rep_table(Basis &B) {
 // per-sector phase tables ph[s N + r] = exp(-2 pi i sum_alpha K_alpha r_alpha / L_alpha):
 // the phase e^{ik.t} of the translation t = -(r_x, r_y, r_z) that moves site r
 // to the origin; the angle is reduced exactly in integers
-__global__ void k_phase_tables(int S, int N, int Lx, int Ly, int Lz, const int *__restrict__ K,
+// per sector s and cell translation u (u < G = Lx Ly Lz; rows of N entries,
+// the entries past G repeat the table): e^{-2 pi i K.t_u / L} with the angle
+// reduced exactly in integers
+__global__ void k_phase_tables(int S, int N, int G, int Lx, int Ly, int Lz, const int *__restrict__ K,
                                double2 *__restrict__ ph64, float2 *__restrict__ ph32, float4 *__restrict__ phdf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= S * N) return;
-    const int s = i / N, r = i % N;
+    const int s = i / N, r = (i % N) % G;
     const long long x = r % Lx, y = (r / Lx) % Ly, z = r / (Lx * Ly);
     const long long num =
-        ((long long)K[3 * s] * x * (N / Lx) + (long long)K[3 * s + 1] * y * (N / Ly) + (long long)K[3 * s + 2] * z * (N / Lz)) % N;
+        ((long long)K[3 * s] * x * (G / Lx) + (long long)K[3 * s + 1] * y * (G / Ly) + (long long)K[3 * s + 2] * z * (G / Lz)) % G;
     double sn, cs;
-    sincospi(-2.0 * (double)num / (double)N, &sn, &cs);
+    sincospi(-2.0 * (double)num / (double)G, &sn, &cs);
     ph64[i] = make_double2(cs, sn);
     ph32[i] = make_float2((float)cs, (float)sn);
     const float ch = __double2float_rn(cs), sh = __double2float_rn(sn);
@@ -475,13 +502,15 @@ static int check_translation(const Basis &B) {
         v.first += B.jxy[b];
         v.second += B.jz[b];
     }
-    const int Lx = B.L[0], Ly = B.L[1];
+    const int Lx = B.L[0], Ly = B.L[1], ns = B.nsub;
+    // site r = spin r % ns of cell r / ns; the shift moves the cell by one along axis a
     auto shift = [&](int r, int a) {
-        int x = r % Lx, y = (r / Lx) % Ly, z = r / (Lx * Ly);
+        const int sb = r % ns, q = r / ns;
+        int x = q % Lx, y = (q / Lx) % Ly, z = q / (Lx * Ly);
         if (a == 0) x = (x + 1) % Lx;
         if (a == 1) y = (y + 1) % Ly;
         if (a == 2) z = (z + 1) % B.L[2];
-        return x + Lx * (y + Ly * z);
+        return sb + ns * (x + Lx * (y + Ly * z));
     };
     for (int a = 0; a < 3; ++a) {
         if (B.L[a] == 1) continue;
@@ -494,9 +523,10 @@ static int check_translation(const Basis &B) {
                                kv.first.first, kv.first.second, a);
         }
     }
+    // the field must be the same on every copy of a spin of the unit cell
     if (B.has_h)
         for (int i = 1; i < B.N; ++i)
-            if (B.h[i] != B.h[0]) return set_err(QS3_ERR_SYMMETRY, "site field is not uniform (site %d)", i);
+            if (B.h[i] != B.h[i % ns]) return set_err(QS3_ERR_SYMMETRY, "site field is not translation invariant (site %d)", i);
     return QS3_OK;
 }
 
@@ -527,13 +557,16 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     if (B.has_h) B.h.assign(lat->h, lat->h + N);
     for (int a = 0; a < 3; ++a) B.L[a] = lat->L[a];
     const bool haveL = B.L[0] > 0 || B.L[1] > 0 || B.L[2] > 0;
+    B.nsub = lat->n_sub > 0 ? lat->n_sub : 1;
     if (haveL) {
         for (int a = 0; a < 3; ++a)
             if (B.L[a] < 1 || B.L[a] > (a == 2 ? 1023 : 2047))
                 return set_err(QS3_ERR_INVALID_ARG, "L[%d] = %d outside the coordinate range", a, B.L[a]);
-        if ((long long)B.L[0] * B.L[1] * B.L[2] != N)
-            return set_err(QS3_ERR_INVALID_ARG, "Lx*Ly*Lz = %lld != n_sites %d", (long long)B.L[0] * B.L[1] * B.L[2], N);
+        if ((long long)B.nsub * B.L[0] * B.L[1] * B.L[2] != N)
+            return set_err(QS3_ERR_INVALID_ARG, "n_sub*Lx*Ly*Lz = %lld != n_sites %d",
+                           (long long)B.nsub * B.L[0] * B.L[1] * B.L[2], N);
     } else {
+        if (B.nsub != 1) return set_err(QS3_ERR_INVALID_ARG, "n_sub %d without a translation group", B.nsub);
         if (N > 2047 && K) return set_err(QS3_ERR_INVALID_ARG, "translation group needed");
     }
     B.has_k = K != nullptr;
@@ -550,6 +583,7 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
         B.K.assign(3, 0);
     }
     if (!haveL) { B.L[0] = N; B.L[1] = 1; B.L[2] = 1; }
+    B.ncell = B.L[0] * B.L[1] * B.L[2];
     if (lat->pos) B.pos.assign(lat->pos, lat->pos + 3 * (size_t)N);
 
     // binomial rows 0..nd+2
@@ -623,7 +657,9 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     }
     std::vector<uint32_t> xyz(N);
     for (int r = 0; r < N; ++r) {
-        int x = r % B.L[0], y = (r / B.L[0]) % B.L[1], z = r / (B.L[0] * B.L[1]);
+        // the coordinates of the site's cell
+        const int q = r / B.nsub;
+        int x = q % B.L[0], y = (q / B.L[0]) % B.L[1], z = q / (B.L[0] * B.L[1]);
         // coordinates are only used with a translation group (x, y < 2048, z < 1024)
         xyz[r] = haveL ? ((uint32_t)x | ((uint32_t)y << 11) | ((uint32_t)z << 22)) : 0u;
     }
@@ -654,6 +690,8 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
     L.adj_jz_lo = B.d_adj_jz_lo.as<float>();
     L.c0lo = (float)(c0 - (double)(float)c0);
     L.xyz = B.d_xyz.as<uint32_t>();
+    L.nsub = B.nsub;
+    L.ncell = B.ncell;
     L.adj_pad = B.d_adj_pad.as<int2>();
     L.adj_jz_pad = B.d_adj_jz_pad.as<float>();
     L.pad_w = padw;
@@ -705,7 +743,7 @@ static int basis_create(const qs3_lattice *lat, int nd, int nsec, const int32_t 
         QS3_TRY(B.d_phdf.alloc((size_t)nsec * N * sizeof(float4)));
         QS3_TRY(B.d_secs.upload(B.K.data(), B.K.size() * sizeof(int)));     // momenta for the table kernel
         const int tot = nsec * N;
-        k_phase_tables<<<(tot + 255) / 256, 256>>>(nsec, N, B.L[0], B.L[1], B.L[2], B.d_secs.as<int>(),
+        k_phase_tables<<<(tot + 255) / 256, 256>>>(nsec, N, B.ncell, B.L[0], B.L[1], B.L[2], B.d_secs.as<int>(),
                                                    B.d_ph64.as<double2>(), B.d_ph32.as<float2>(),
                                                    B.d_phdf.as<float4>());
         QS3_LAUNCHED();

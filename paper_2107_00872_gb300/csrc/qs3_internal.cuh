@@ -95,7 +95,9 @@ struct LatView {
     const float *u_lo;
     const float *adj_jz_lo;
     float c0lo;
-    const uint32_t *xyz;          // N: x | y << 11 | z << 22
+    const uint32_t *xyz;          // N: the site's cell coordinates x | y << 11 | z << 22
+    int nsub;                     // spins per unit cell: site r is spin r % nsub of cell r / nsub
+    int ncell;                    // cells, the order of the translation group
     // representative table (k-sectors, optional): for every state a, by its
     // rank0, orb[rank0] = g << 12 | u, where the orbit's representative is the
     // g-th of the sorted list of all representatives and a = T_u (rep): the
@@ -129,6 +131,7 @@ struct SecView {
 struct Basis {
     int N = 0, nd = 0, nb = 0;
     int L[3] = {0, 0, 0};
+    int nsub = 1, ncell = 0;                // spins per cell, cells (the group order)
     bool has_k = false;
     int S = 0;                              // sectors
     std::vector<int> K;                     // 3 S
@@ -316,7 +319,9 @@ __device__ __forceinline__ bool seen_before(const int (&a)[ND], int i, int v) {
 }
 
 // Minimum-rank translate of the site list t (the representative of its
-// orbit, Alg. 7), found without trying every translation.
+// orbit, Alg. 7), found without trying every translation.  Translations move
+// unit cells; a site is spin sb of cell (x, y, z), index sb + nsub (x + Lx
+// (y + Ly z)), so the order of sites follows their cells first.
 //
 // The rank order is the lexicographic order of the descending list of site
 // indices r = x + Lx (y + Ly z), so a representative first minimises its
@@ -337,13 +342,14 @@ template <int ND>
 __device__ __forceinline__ uint64_t canon(const int (&t)[ND], const LatView &L, const uint32_t *__restrict__ sxyz,
                                           const uint64_t *__restrict__ sC, int (&rep)[ND], int &ax, int &by,
                                           int &cz) {
-    int X[ND], Y[ND], Z[ND];
+    int X[ND], Y[ND], Z[ND], SB[ND];
 #pragma unroll
     for (int m = 0; m < ND; ++m) {
         uint32_t p = sxyz[t[m]];
         X[m] = p & 2047u;
         Y[m] = (p >> 11) & 2047u;
         Z[m] = p >> 22;
+        SB[m] = L.nsub > 1 ? t[m] % L.nsub : 0;     // the spin's place in its cell
     }
     const int Lx = L.L[0], Ly = L.L[1], Lz = L.L[2];
     const int kb = L.key_bits;
@@ -452,7 +458,7 @@ __device__ __forceinline__ uint64_t canon(const int (&t)[ND], const LatView &L, 
                 for (int m = 0; m < ND; ++m) {
                     int d = X[m] - xa;
                     d += (d < 0) ? Lx : 0;
-                    s[m] = d + Lx * (yy[m] + Ly * zz[m]);
+                    s[m] = SB[m] + L.nsub * (d + Lx * (yy[m] + Ly * zz[m]));
                 }
                 sort_net(s);
                 uint64_t key;

@@ -564,6 +564,8 @@ static std::vector<double2> site_phases(const Basis &B, const int *Q) {
 }
 
 int smq_launch(Basis &S, int ss, const void *phi, Basis &Dd, int sd, const int *Q, void *psi, cudaStream_t st) {
+    if (S.nsub > 1 || Dd.nsub > 1)
+        return set_err(QS3_ERR_INVALID_ARG, "S^alpha_q takes one spin per unit cell");
     if (S.N != Dd.N || S.L[0] != Dd.L[0] || S.L[1] != Dd.L[1] || S.L[2] != Dd.L[2])
         return set_err(QS3_ERR_INVALID_ARG, "source and target bases are on different lattices");
     if (Dd.nd != S.nd + 1) return set_err(QS3_ERR_INVALID_ARG, "target n_down must be source n_down + 1");
@@ -665,6 +667,9 @@ int sq_launch(int op, Basis &S, int ss, const void *phi, Basis &Dd, int sd, cons
               cudaStream_t st) {
     if (op == QS3_OP_SMINUS) return smq_launch(S, ss, phi, Dd, sd, Q, psi, st);
     if (op != QS3_OP_SPLUS && op != QS3_OP_SZ) return set_err(QS3_ERR_INVALID_ARG, "operator %d", op);
+    if (S.nsub > 1 || Dd.nsub > 1)
+        return set_err(QS3_ERR_INVALID_ARG, "S^alpha_q takes one spin per unit cell");
+
     if (S.N != Dd.N || S.L[0] != Dd.L[0] || S.L[1] != Dd.L[1] || S.L[2] != Dd.L[2])
         return set_err(QS3_ERR_INVALID_ARG, "source and target bases are on different lattices");
     const int want = op == QS3_OP_SPLUS ? S.nd - 1 : S.nd;
@@ -741,6 +746,10 @@ static int dispatch_corr_k(Basis &B, int s, const double2 *phi, bool pm, double2
 static int correlations(Basis &B, int s, const void *gs, int npairs, const int *pairs, double *szsz, double *spsm,
                         double *szl, int nq, const double *q, double *sqz, double *sqp, cudaStream_t st) {
     const int N = B.N, nd = B.nd;
+    if (B.has_k && B.nsub > 1)
+        return set_err(QS3_ERR_INVALID_ARG, "translation-symmetrised correlations take one spin per unit cell");
+    if (B.nsub > 1 && nq > 0 && B.pos.empty())
+        return set_err(QS3_ERR_INVALID_ARG, "S(q) on a lattice with several spins per cell needs the site positions");
     const bool want_pm = (spsm && npairs > 0) || (sqp && nq > 0);
     for (int p = 0; p < npairs; ++p)
         if (pairs[2 * p] < 0 || pairs[2 * p] >= N || pairs[2 * p + 1] < 0 || pairs[2 * p + 1] >= N)
@@ -1020,6 +1029,8 @@ __global__ void k_site_phases(int N, int Lx, int Ly, int Lz, int Qx, int Qy, int
 
 static int smq_noalloc(Basis &S, int ss, const void *phi, Basis &Dd, int sd, const int *Q, void *psi,
                        cudaStream_t st) {
+    if (S.nsub > 1 || Dd.nsub > 1)
+        return set_err(QS3_ERR_INVALID_ARG, "S^alpha_q takes one spin per unit cell");
     if (S.N > NOALLOC_MAX_SITES)
         return set_err(QS3_ERR_INVALID_ARG, "n_sites %d exceeds the %d sites of the no-allocation scratch", S.N,
                        NOALLOC_MAX_SITES);

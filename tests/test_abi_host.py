@@ -116,6 +116,20 @@ def test_symmetry_violations(qs3):
     assert _status(qs3, lambda: qs3.Basis(noL, 2, [(0, 0, 0)])) == SYMMETRY
 
 
+def test_unit_cell_validation(qs3):
+    """Several spins per unit cell: n_sub Lx Ly Lz must equal N, n_sub needs a
+    translation group, and a field must repeat from cell to cell."""
+    kg = qi.kagome(2, 2)
+    bad = qi.LatticeSpec(kg.n_sites, kg.bi, kg.bj, kg.jxy, kg.jz, None, (2, 2, 1), "k", None, 2)
+    assert _status(qs3, lambda: qs3.Basis(bad, 2, [(0, 0, 0)])) == INVALID
+    noL = qi.LatticeSpec(kg.n_sites, kg.bi, kg.bj, kg.jxy, kg.jz, None, (0, 0, 0), "k", None, 3)
+    assert _status(qs3, lambda: qs3.Basis(noL, 2)) == INVALID
+    h = np.tile([0.1, 0.2, 0.3], 4)
+    h[7] = 0.5
+    fld = qi.LatticeSpec(kg.n_sites, kg.bi, kg.bj, kg.jxy, kg.jz, h, (2, 2, 1), "k", None, 3)
+    assert _status(qs3, lambda: qs3.Basis(fld, 2, [(0, 0, 0)])) == SYMMETRY
+
+
 def test_injected_allocation_failure_is_oom(qs3):
     prev = qs3.inject_alloc_failure(0)
     try:
