@@ -173,6 +173,26 @@ int qs3_basis_store_terms(qs3_basis_t b, int32_t mode, uint64_t *bytes);
  * Errors: STATE (real dtype on a k-sector basis, C128DF on a U(1)-only one). */
 int qs3_hphi(qs3_basis_t b, qs3_dtype dtype, const void *phi, void *psi, void *stream);
 
+/* Dot products of the Gram-Schmidt pass of Alg. 10 (the reorthogonalisation
+ * of a new Lanczos vector against the stored ones), per sector:
+ * out[2 (s m + j)], out[2 (s m + j) + 1] = re, im of conj(V_j) . w summed
+ * over the rows of sector s, V_j = V + j ldv elements, j < m.  dtype F64
+ * (real vectors, im = 0) or C128 (interleaved re, im); V and w are device
+ * binary64 vectors of the basis' total dimension, out is host memory of
+ * 2 S m doubles, written when the call returns (synchronous on stream).
+ * mode 0 (the dots of fp64 solves): every operand is rounded once onto a
+ * fixed-point grid set by the largest exponent among the 128 rows of its
+ * warp (rows r with the same r mod 2048 div 32 within a chunk of 2048),
+ * at most 2^-53 of that largest magnitude; the products of those images
+ * are summed exactly in 64-bit integers, each warp's sum rounded to
+ * binary64 once and the warps and chunks summed in binary64.
+ * mode 1 (strict64 solves): binary64 FMA chains per thread, summed in a
+ * fixed order.  Device scratch of m x the vector size is allocated per call.
+ * Errors: INVALID_ARG (NULL, m < 0, ldv < total dimension for m > 1, dtype,
+ * mode), OOM. */
+int qs3_gs_dots(qs3_basis_t b, qs3_dtype dtype, int32_t m, const void *V, uint64_t ldv, const void *w,
+                double *out, int32_t mode, void *stream);
+
 /* x_df[r] = double-float split of the complex128 x[r], r < n: re.hi =
  * fl32(re), re.lo = fl32(re - re.hi), the same for im (device pointers, the
  * layout QS3_C128DF reads). */

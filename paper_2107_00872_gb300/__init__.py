@@ -262,6 +262,25 @@ class Basis:
                               _dev(psi, self.total_dim, "psi"), _stream(stream)), "qs3_hphi")
         return psi
 
+    def gs_dots(self, V, w, exact: bool = True, stream=None) -> np.ndarray:
+        """conj(V_j) . w per sector (the Gram-Schmidt dots of Alg. 10) as a
+        complex (or real) array [n_sectors, m]; V is [m, total_dim] and w
+        [total_dim], both float64 or complex128 on the device.  exact: the
+        fixed-point exact-accumulation dots of fp64 solves, else binary64
+        FMA chains (strict64)."""
+        torch = _torch()
+        if V.dim() != 2 or V.shape[1] != self.total_dim:
+            raise ValueError(f"V must be [m, {self.total_dim}]")
+        if V.dtype != w.dtype or V.dtype not in (torch.float64, torch.complex128):
+            raise TypeError("V and w must both be float64 or complex128")
+        m = int(V.shape[0])
+        out = np.zeros((self.n_sectors, m, 2), np.float64)
+        check(load().qs3_gs_dots(self._h, dtype_code(V), m, _dev(V), self.total_dim, _dev(w, self.total_dim, "w"),
+                                 _ptr(out), 0 if exact else 1, _stream(stream)), "qs3_gs_dots")
+        if V.dtype == torch.complex128:
+            return out[..., 0] + 1j * out[..., 1]
+        return out[..., 0].copy()
+
     def hphi_df(self, phi_df, psi=None, stream=None):
         """psi = H phi for phi in double-float form (float32 tensor of 4 x the
         total dimension: re.hi, re.lo, im.hi, im.lo per element, see

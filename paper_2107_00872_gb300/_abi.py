@@ -54,6 +54,7 @@ SIGNATURES = {
     "qs3_full_diag": ([P, I32, P, P, P], I32),
     "qs3_thermal": ([ctypes.c_int64, P, P, P, I32, P, P, P], I32),
     "qs3_hphi": ([P, I32, P, P, P], I32),
+    "qs3_gs_dots": ([P, I32, I32, P, U64, P, P, I32, P], I32),
     "qs3_split_df": ([P, P, U64, P], I32),
     "qs3_lanczos": ([P, P, P, P, P, P], I32),
     "qs3_trlanczos": ([P, P, P, P, P, P], I32),

@@ -132,6 +132,213 @@ __global__ void __launch_bounds__(NTHREADS, NV == 1 ? 3 : NV == 2 ? 2 : 1)
     }
 }
 
+// ------------------------------------------------ exact fixed-point dots
+// The fp64 pipe of this GPU retires one FMA per ~70 fp32 FMAs, so a complex
+// binary64 dot (4 DFMA per 16 bytes) cannot pass ~2.1 TB/s, a third of HBM.
+// k_dotx forms the same dot products on the integer units, exactly:
+//  - every operand is rounded once (to nearest) onto a fixed-point grid set
+//    by the largest exponent among its warp's rows: for biased exponent em,
+//    v -> P = round(v 2^(1075 - em)), |P| <= 2^53, an error of at most
+//    2^-53 of the warp's largest magnitude (binary64 rounds its largest
+//    element by as much);
+//  - P is split into balanced base-2^26 digits P = P1 2^26 + P0 (|P0| <=
+//    2^25, |P1| <= 2^27 + 1); the digit products P1 W1 (weight 2^52) and
+//    P1 W0 + P0 W1 (weight 2^26) are summed exactly in 64-bit integers
+//    (mad.wide.s32); P0 W0 (at most 2^50, random in sign: a quarter of the
+//    grid error) is left out;
+//  - each warp's two sums per component are rounded to binary64 once, the
+//    warps and chunks are summed in binary64 in a fixed order.
+// Bounds: per thread 8 (real: 4) top-digit products of <= 2^54.1 and 16 (4)
+// middle products of <= 2^52.1, so a warp's sums stay below 2^63.
+constexpr int XT = 512;                 // threads per chunk of k_dotx
+constexpr int XR = BROWS / XT;          // rows per thread
+constexpr int XW = XT / 32;             // warps per chunk
+static_assert(XR * XT == BROWS, "k_dotx covers a chunk");
+
+__device__ __forceinline__ int fx_exp(uint32_t h) { return (int)((h >> 20) & 0x7ffu); }
+
+// the binary64 with high word h and low word l on the grid of em (em >= its
+// biased exponent, em >= 54): balanced digits (p1, p0) of round(v 2^(1075-em)).
+// A zero or subnormal v (exponent field 0) is at least 2^54 grid steps below
+// em and rounds to 0.
+__device__ __forceinline__ void fx_digits(uint32_t h, uint32_t l, int em, int &p1, int &p0) {
+    const uint32_t sh = min((uint32_t)(em - fx_exp(h)), 63u);
+    // 2m, m = 2^52 + the 52 stored significand bits: high word mh2, low l2
+    const uint32_t mh2 = (__funnelshift_l(l, h, 1) & 0x1fffffu) | 0x200000u;
+    const uint32_t l2 = l << 1;
+    // t = floor(2m / 2^sh) = floor(m / 2^(sh-1)): words thi, tlo
+    const uint32_t f = __funnelshift_rc(l2, mh2, sh);                  // (2m) >> min(sh, 32), low word
+    const uint32_t thi = __funnelshift_rc(mh2, 0u, sh);                // its high word (0 for sh >= 32)
+    const uint32_t tlo = f >> (max(sh, 32u) - 32u);                    // the rest of the shift (thi = 0 then)
+    // Q = round(m / 2^sh) = floor((t + 1) / 2); Q1 = floor((Q + 2^25) / 2^26),
+    // Q0 = Q - Q1 2^26 (the low 26 bits of Q, sign-extended)
+    const uint64_t t = ((uint64_t)thi << 32) | tlo;
+    const int q1 = (int)((t + 0x4000001ull) >> 27);
+    const int q0 = ((int)(((tlo + 1u) >> 1) << 6)) >> 6;
+    const int sg = ((int)h >> 31) | 1;
+    p1 = q1 * sg;
+    p0 = q0 * sg;
+}
+
+__device__ __forceinline__ long long mad_w(int a, int b, long long c) { return (long long)a * (long long)b + c; }
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ void words(uint2 h, uint2 l, uint32_t (&hw)[2], uint32_t (&lw)[2]) {
+    hw[0] = h.x; hw[1] = h.y; lw[0] = l.x; lw[1] = l.y;
+}
+__device__ __forceinline__ void words(uint32_t h, uint32_t l, uint32_t (&hw)[2], uint32_t (&lw)[2]) {
+    hw[0] = h; hw[1] = 0u; lw[0] = l; lw[1] = 0u;
+}
+
+// part[c * m + j] = conj(V_{j0+j}) . w over chunk c, exact on the
+// fixed-point images (see above); V the word-planar store, w interleaved
+// binary64.  NV vectors per pass have their loads in flight together; the
+// results of up to 32 vectors meet in shared memory per block.  Graph mode
+// (dx): the range of graph_range.
+template <typename VT, int NV>
+__global__ void __launch_bounds__(XT, 1)
+    k_dotx(const typename PlS<VT>::T *__restrict__ V, uint64_t D, int j0, int m, const VT *__restrict__ w,
+           const SecView *__restrict__ secs, const int *__restrict__ chunk0, int S, const int *__restrict__ active,
+           double2 *__restrict__ part, const int *__restrict__ dx = nullptr, int ring = 0) {
+    using T = typename PlS<VT>::T;
+    constexpr bool CX = IsC<VT>::v;
+    constexpr int NC = CX ? 2 : 1;
+    constexpr int GB = 32;
+    __shared__ double2 red[GB][XW];
+    graph_range(dx, ring, j0, m);
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (ci.n - (int)threadIdx.x + XT - 1) / XT;          // rows of this thread
+    const uint64_t r0 = ci.base + threadIdx.x;
+    // w on its warp's grid: digits (w1, w0) per row and component, and the
+    // negated real-part digits for the imaginary part of conj(a) w
+    int w1[XR][2], w0[XR][2], nw1[XR], nw0[XR];
+    int ew = 54;
+    {
+        uint32_t hw[XR][2], lw[XR][2];
+#pragma unroll
+        for (int k = 0; k < XR; ++k) {
+            const double2 v = k < nk ? ld2(w + r0 + (uint64_t)k * XT) : make_double2(0.0, 0.0);
+            hw[k][0] = (uint32_t)__double2hiint(v.x);
+            lw[k][0] = (uint32_t)__double2loint(v.x);
+            hw[k][1] = (uint32_t)__double2hiint(v.y);
+            lw[k][1] = (uint32_t)__double2loint(v.y);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) ew = max(ew, fx_exp(hw[k][c]));
+        }
+        ew = (int)__reduce_max_sync(0xffffffffu, (unsigned)ew);
+#pragma unroll
+        for (int k = 0; k < XR; ++k) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (c < NC) fx_digits(hw[k][c], lw[k][c], ew, w1[k][c], w0[k][c]);
+                else w1[k][c] = w0[k][c] = 0;
+            }
+            nw1[k] = -w1[k][0];
+            nw0[k] = -w0[k][0];
+        }
+    }
+    for (int jb = 0; jb < m; jb += GB) {
+        const int nj = min(GB, m - jb);
+        for (int jj = 0; jj < nj; jj += NV) {
+            T ah[NV][XR], al[NV][XR];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const int jv = jj + v < nj ? jj + v : nj - 1;      // past the batch: a repeat, discarded
+                const T *slot = V + (uint64_t)(j0 + jb + jv) * 2 * D;
+#pragma unroll
+                for (int k = 0; k < XR; ++k) {
+                    if (k < nk) {
+                        ah[v][k] = slot[r0 + (uint64_t)k * XT];
+                        al[v][k] = slot[D + r0 + (uint64_t)k * XT];
+                    } else {
+                        ah[v][k] = T{};
+                        al[v][k] = T{};
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                uint32_t hw[XR][2], lw[XR][2];
+                int em = 54;
+#pragma unroll
+                for (int k = 0; k < XR; ++k) {
+                    words(ah[v][k], al[v][k], hw[k], lw[k]);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) em = max(em, fx_exp(hw[k][c]));
+                }
+                em = (int)__reduce_max_sync(0xffffffffu, (unsigned)em);
+                long long hr = 0, mr = 0, hi = 0, mi = 0;
+#pragma unroll
+                for (int k = 0; k < XR; ++k) {
+                    int a1r, a0r;
+                    fx_digits(hw[k][0], lw[k][0], em, a1r, a0r);
+                    hr = mad_w(a1r, w1[k][0], hr);
+                    mr = mad_w(a1r, w0[k][0], mr);
+                    mr = mad_w(a0r, w1[k][0], mr);
+                    if (CX) {
+                        int a1i, a0i;
+                        fx_digits(hw[k][1], lw[k][1], em, a1i, a0i);
+                        // conj(a) w = (a.r w.r + a.i w.i) + i (a.r w.i - a.i w.r)
+                        hr = mad_w(a1i, w1[k][1], hr);
+                        mr = mad_w(a1i, w0[k][1], mr);
+                        mr = mad_w(a0i, w1[k][1], mr);
+                        hi = mad_w(a1r, w1[k][1], hi);
+                        hi = mad_w(a1i, nw1[k], hi);
+                        mi = mad_w(a1r, w0[k][1], mi);
+                        mi = mad_w(a0r, w1[k][1], mi);
+                        mi = mad_w(a1i, nw0[k], mi);
+                        mi = mad_w(a0i, nw1[k], mi);
+                    }
+                }
+                hr = warp_sum_ll(hr);
+                mr = warp_sum_ll(mr);
+                if (CX) {
+                    hi = warp_sum_ll(hi);
+                    mi = warp_sum_ll(mi);
+                }
+                if (lane == 0 && jj + v < nj) {
+                    // (h 2^52 + m 2^26) u_a u_w = (h 2^26 + m) 2^(em + ew - 2124)
+                    const int k = em + ew - 2124;
+                    const double re = ldexp(fma((double)hr, 0x1p26, (double)mr), k);
+                    const double im = CX ? ldexp(fma((double)hi, 0x1p26, (double)mi), k) : 0.0;
+                    red[jj + v][warp] = make_double2(re, im);
+                }
+            }
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < nj) {
+            double2 t = red[threadIdx.x][0];
+#pragma unroll
+            for (int q = 1; q < XW; ++q) {
+                t.x += red[threadIdx.x][q].x;
+                t.y += red[threadIdx.x][q].y;
+            }
+            part[(uint64_t)blockIdx.x * m + jb + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename VT>
+static int dotx_launch(int nv, const typename PlS<VT>::T *v, uint64_t D, int j0, int m, const VT *w,
+                       const SecView *secs, const int *c0, int S, const int *act, double2 *pp, int grid,
+                       cudaStream_t st, const int *dx = nullptr, int ring = 0) {
+    if (ring || (!dx && m <= 2)) nv = std::min(nv, 2);
+    if (nv == 1)
+        k_dotx<VT, 1><<<grid, XT, 0, st>>>(v, D, j0, m, w, secs, c0, S, act, pp, dx, ring);
+    else if (nv == 4)
+        k_dotx<VT, 4><<<grid, XT, 0, st>>>(v, D, j0, m, w, secs, c0, S, act, pp, dx, ring);
+    else
+        k_dotx<VT, 2><<<grid, XT, 0, st>>>(v, D, j0, m, w, secs, c0, S, act, pp, dx, ring);
+    QS3_LAUNCHED();
+    return QS3_OK;
+}
+
 // out[s * ldo + j] = sum over the chunks of sector s of part[c * m + j], one
 // warp per coefficient (graph mode: the range of graph_range, written from
 // out + j0)
@@ -471,18 +678,15 @@ struct Engine64 {
         QS3_LAUNCHED();
         return QS3_OK;
     }
-    // k_dot64 with nv stored vectors per pass (1, 2 or 4)
+    // the dot products of w against stored vectors j0 .. j0 + m - 1 into part:
+    // k_dotx with nv stored vectors per pass (1, 2 or 4), or under strict64
+    // k_dot64 (binary64 FMA chains)
     int dot_launch(int nv, int j0, int m, const int *dx = nullptr, int ring = 0) {
         const ST *v = V.as<ST>();
         double2 *pp = part.as<double2>();
         const VT *w = wv();
-        if (ring || (!dx && m <= 2)) nv = std::min(nv, 2);
-        if (nv == 1)
-            k_dot64<VT, 1><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx, ring);
-        else if (nv == 4)
-            k_dot64<VT, 4><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx, ring);
-        else
-            k_dot64<VT, 2><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx, ring);
+        if (!strict) return dotx_launch<VT>(nv, v, D, j0, m, w, secs(), c0(), B.S, act(), pp, grid(), st, dx, ring);
+        k_dot64<VT, 2><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx, ring);
         QS3_LAUNCHED();
         return QS3_OK;
     }

@@ -2500,6 +2500,48 @@ static int check_opts(const qs3_solve_opts *o) {
     return QS3_OK;
 }
 
+// ---------------------------------------------- Gram-Schmidt dot products
+// the dot kernels of the binary64 engine on caller vectors: each V_j copied
+// into a word-planar slot, then k_dotx (mode 0) or k_dot64 (mode 1)
+template <typename VT>
+__global__ void k_to_planar(const VT *__restrict__ x, typename PlS<VT>::T *__restrict__ slot, uint64_t D) {
+    for (uint64_t r = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; r < D; r += (uint64_t)gridDim.x * blockDim.x)
+        pl_st(slot, D, r, ld2(x + r));
+}
+
+template <typename VT>
+static int gs_dots_run(Basis &B, int m, const VT *V, uint64_t ldv, const VT *w, double *out, int mode,
+                       cudaStream_t st) {
+    using T = typename PlS<VT>::T;
+    const uint64_t D = B.total;
+    memset(out, 0, (size_t)B.S * m * 2 * sizeof(double));
+    if (m == 0 || B.nchunks == 0) return QS3_OK;
+    DevBuf pl, part, res;
+    QS3_TRY(pl.alloc((uint64_t)m * D * sizeof(VT)));
+    QS3_TRY(part.alloc((uint64_t)B.nchunks * m * sizeof(double2)));
+    QS3_TRY(res.alloc((uint64_t)B.S * m * sizeof(double2)));
+    const int g = (int)std::min<uint64_t>((D + 255) / 256, 4096);
+    for (int j = 0; j < m; ++j) {
+        k_to_planar<VT><<<g, 256, 0, st>>>(V + (uint64_t)j * ldv, pl.as<T>() + (uint64_t)j * 2 * D, D);
+        QS3_LAUNCHED();
+    }
+    const SecView *secs = B.d_secs.as<SecView>();
+    const int *c0 = B.d_chunk0.as<int>();
+    if (mode == 0) {
+        QS3_TRY(dotx_launch<VT>(2, pl.as<T>(), D, 0, m, w, secs, c0, B.S, nullptr, part.as<double2>(), B.nchunks,
+                                st));
+    } else {
+        k_dot64<VT, 2><<<B.nchunks, NTHREADS, 0, st>>>(pl.as<T>(), D, 0, m, w, secs, c0, B.S, nullptr,
+                                                        part.as<double2>());
+        QS3_LAUNCHED();
+    }
+    k_reduce64<<<dim3((m + 7) / 8, B.S), NTHREADS, 0, st>>>(part.as<double2>(), m, c0, nullptr, res.as<double2>(), m);
+    QS3_LAUNCHED();
+    QS3_CUDA(cudaMemcpyAsync(out, res.p, (size_t)B.S * m * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    QS3_CUDA(cudaStreamSynchronize(st));
+    return QS3_OK;
+}
+
 }  // namespace qs3
 
 using namespace qs3;
@@ -2529,6 +2571,23 @@ extern "C" int qs3_trlanczos(qs3_basis_t b, const qs3_solve_opts *o, double *eva
     cudaStream_t st = (cudaStream_t)stream;
     if (B.has_k) return trl_entry<float2, double2>(B, *o, evals, evecs, info, st);
     return trl_entry<float, double>(B, *o, evals, evecs, info, st);
+}
+
+extern "C" int qs3_gs_dots(qs3_basis_t b, qs3_dtype dtype, int32_t m, const void *V, uint64_t ldv, const void *w,
+                           double *out, int32_t mode, void *stream) {
+    clear_err();
+    if (!b) return set_err(QS3_ERR_INVALID_ARG, "basis is NULL");
+    if (m < 0) return set_err(QS3_ERR_INVALID_ARG, "m %d", m);
+    if (m > 0 && (!V || !w || !out)) return set_err(QS3_ERR_INVALID_ARG, "NULL argument");
+    if (mode != 0 && mode != 1) return set_err(QS3_ERR_INVALID_ARG, "mode %d (need 0 or 1)", mode);
+    Basis &B = b->B;
+    if (m > 1 && ldv < B.total)
+        return set_err(QS3_ERR_INVALID_ARG, "ldv %llu below the total dimension %llu", (unsigned long long)ldv,
+                       (unsigned long long)B.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == QS3_C128) return gs_dots_run<double2>(B, m, (const double2 *)V, ldv, (const double2 *)w, out, mode, st);
+    if (dtype == QS3_F64) return gs_dots_run<double>(B, m, (const double *)V, ldv, (const double *)w, out, mode, st);
+    return set_err(QS3_ERR_INVALID_ARG, "dtype %d (need F64 or C128)", (int)dtype);
 }
 
 // ------------------------------------------- dynamical structure factor

@@ -146,6 +146,7 @@ def test_null_handles(qs3):
     assert lib.qs3_lanczos(None, None, None, None, None, None) == INVALID
     assert lib.qs3_basis_tuning(None, 0, None, None, None) == INVALID
     assert lib.qs3_probe_peaks(None, None) == INVALID
+    assert lib.qs3_gs_dots(None, 3, 1, None, 0, None, None, 0, None) == INVALID
 
 
 def test_thermal_average_definition(qs3):
