@@ -146,10 +146,16 @@ __global__ void __launch_bounds__(NTHREADS, NV == 1 ? 3 : NV == 2 ? 2 : 1)
 //    P1 W0 + P0 W1 (weight 2^26) are summed exactly in 64-bit integers
 //    (mad.wide.s32); P0 W0 (at most 2^50, random in sign: a quarter of the
 //    grid error) is left out;
-//  - each warp's two sums per component are rounded to binary64 once, the
-//    warps and chunks are summed in binary64 in a fixed order.
-// Bounds: per thread 8 (real: 4) top-digit products of <= 2^54.1 and 16 (4)
-// middle products of <= 2^52.1, so a warp's sums stay below 2^63.
+//  - each thread folds its middle sum into its top sum (rounded to nearest
+//    at weight 2^52), the warp adds its 32 threads' sums exactly
+//    (redux.sync on 26-bit limbs) and writes them with its grid exponent;
+//  - k_reducex aligns the warp sums of every chunk of a sector to the
+//    coarsest grid among them (rounded to nearest), adds them exactly in
+//    128-bit integers and rounds the sector's dot to binary64 once.
+// Neither kernel issues an fp64 instruction on the normal path.
+// Bounds: a thread's folded sum (8 top-digit products of <= 2^54.1 and 16
+// middle ones of <= 2^52.1 for complex data) stays below 2^57.2, a warp's
+// below 2^62.2.
 constexpr int XT = 512;                 // threads per chunk of k_dotx
 constexpr int XR = BROWS / XT;          // rows per thread
 constexpr int XW = XT / 32;             // warps per chunk
@@ -180,12 +186,67 @@ __device__ __forceinline__ void fx_digits(uint32_t h, uint32_t l, int em, int &p
     p0 = q0 * sg;
 }
 
-__device__ __forceinline__ long long mad_w(int a, int b, long long c) { return (long long)a * (long long)b + c; }
-__device__ __forceinline__ long long warp_sum_ll(long long v) {
+// a b + c with the 64-bit product of two 32-bit integers (one mad.wide.s32)
+__device__ __forceinline__ long long mad_w(int a, int b, long long c) {
+    long long d;
+    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+// the sum over the warp of t, |t| < 2^58: three limbs of at most 26 bits,
+// whose 32-lane sums fit in int32, each summed by one redux.sync
+__device__ __forceinline__ long long warp_sum_ll(long long t) {
+    const int l0 = (int)(t & 0x3ffffffll);
+    const int l1 = (int)((t >> 26) & 0x3ffffffll);
+    const int l2 = (int)(t >> 52);
+    const long long s0 = __reduce_add_sync(0xffffffffu, l0);
+    const long long s1 = __reduce_add_sync(0xffffffffu, l1);
+    const long long s2 = __reduce_add_sync(0xffffffffu, l2);
+    return s0 + s1 * (1ll << 26) + s2 * (1ll << 52);
+}
+// the sum over the warp of a 128-bit value (exact, all lanes)
+__device__ __forceinline__ __int128 warp_sum_i128(__int128 v) {
 #pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)((unsigned __int128)v >> 64);
+        const unsigned long long olo = __shfl_xor_sync(0xffffffffu, lo, o), ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        v += (__int128)(((unsigned __int128)ohi << 64) | olo);
+    }
     return v;
 }
+// a 2^k rounded to the nearest binary64 (ties to even) in integer operations
+// (the fp64 pipe issues one warp instruction per ~70 ALU ones, even for a
+// single active lane); only a result below the normal range takes fp64 ops
+__device__ __forceinline__ double i128_ldexp(__int128 a, int k) {
+    if (a == 0) return 0.0;
+    const unsigned long long sgn = a < 0 ? 0x8000000000000000ull : 0ull;
+    const unsigned __int128 u = a < 0 ? (unsigned __int128)(-a) : (unsigned __int128)a;
+    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+    const int n = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);     // bit length
+    unsigned long long mant;
+    int e = n - 1 + k;                                                               // exponent of the top bit
+    if (n <= 53) {
+        mant = lo << (53 - n);
+    } else {
+        const int sh = n - 53;
+        mant = (unsigned long long)(u >> sh);
+        const unsigned __int128 rem = u & (((unsigned __int128)1 << sh) - 1);
+        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1ull))) {
+            ++mant;
+            if (mant == (1ull << 53)) {
+                mant >>= 1;
+                ++e;
+            }
+        }
+    }
+    if (e > 1023) return __longlong_as_double((long long)(sgn | 0x7ff0000000000000ull));
+    if (e < -1022) {
+        const double r = ldexp((double)mant, e - 52);
+        return sgn ? -r : r;
+    }
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) | (mant & 0xfffffffffffffull)));
+}
+
 __device__ __forceinline__ void words(uint2 h, uint2 l, uint32_t (&hw)[2], uint32_t (&lw)[2]) {
     hw[0] = h.x; hw[1] = h.y; lw[0] = l.x; lw[1] = l.y;
 }
@@ -193,31 +254,106 @@ __device__ __forceinline__ void words(uint32_t h, uint32_t l, uint32_t (&hw)[2],
     hw[0] = h; hw[1] = 0u; lw[0] = l; lw[1] = 0u;
 }
 
-// part[c * m + j] = conj(V_{j0+j}) . w over chunk c, exact on the
-// fixed-point images (see above); V the word-planar store, w interleaved
-// binary64.  NV vectors per pass have their loads in flight together; the
-// results of up to 32 vectors meet in shared memory per block.  Graph mode
-// (dx): the range of graph_range.
+// The digit store.  Every stored vector also exists as its fixed-point
+// image: per row the balanced digits (P1, P0) of each component (int4 for
+// complex rows: re.P1, re.P0, im.P1, im.P0; int2 for real rows), and per
+// chunk and warp group (the 128 rows base + 32 q + lane + 512 k of a chunk)
+// the grid exponent em.  It is derived from the binary64 store by the kernels
+// that write it (k_scale64, k_digitize) and read only by the dot products.
+template <typename VT> struct DigT { using T = int2; };
+template <> struct DigT<double2> { using T = int4; };
+
+__device__ __forceinline__ void dig_st(int4 *p, const int (&d1)[2], const int (&d0)[2]) {
+    *p = make_int4(d1[0], d0[0], d1[1], d0[1]);
+}
+__device__ __forceinline__ void dig_st(int2 *p, const int (&d1)[2], const int (&d0)[2]) { *p = make_int2(d1[0], d0[0]); }
+__device__ __forceinline__ void dig_ld(const int4 *p, int (&d1)[2], int (&d0)[2]) {
+    const int4 v = *p;
+    d1[0] = v.x; d0[0] = v.y; d1[1] = v.z; d0[1] = v.w;
+}
+__device__ __forceinline__ void dig_ld(const int2 *p, int (&d1)[2], int (&d0)[2]) {
+    const int2 v = *p;
+    d1[0] = v.x; d0[0] = v.y; d1[1] = 0; d0[1] = 0;
+}
+
+// the XR binary64 values (hi, lo words per component) of one thread of a
+// warp group on the group's grid: the warp's largest biased exponent em
+// (at least 54) and the digits of every value
+template <int NC>
+__device__ __forceinline__ int fx_group(const uint32_t (&hw)[XR][2], const uint32_t (&lw)[XR][2], int (&d1)[XR][2],
+                                        int (&d0)[XR][2]) {
+    int em = 54;
+#pragma unroll
+    for (int k = 0; k < XR; ++k)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) em = max(em, fx_exp(hw[k][c]));
+    em = (int)__reduce_max_sync(0xffffffffu, (unsigned)em);
+#pragma unroll
+    for (int k = 0; k < XR; ++k)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (c < NC) fx_digits(hw[k][c], lw[k][c], em, d1[k][c], d0[k][c]);
+            else d1[k][c] = d0[k][c] = 0;
+        }
+    return em;
+}
+
+// digit store slots j0 .. j0 + gridDim.y - 1 from the binary64 store (one
+// block of XT threads per chunk)
+template <typename VT>
+__global__ void __launch_bounds__(XT)
+    k_digitize(const typename PlS<VT>::T *__restrict__ V, uint64_t D, int j0, typename DigT<VT>::T *__restrict__ dg,
+               int *__restrict__ ge, int nchunks, const SecView *__restrict__ secs, const int *__restrict__ chunk0,
+               int S) {
+    using T = typename PlS<VT>::T;
+    constexpr int NC = IsC<VT>::v ? 2 : 1;
+    const int j = j0 + blockIdx.y;
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T *slot = V + (uint64_t)j * 2 * D;
+    uint32_t hw[XR][2], lw[XR][2];
+#pragma unroll
+    for (int k = 0; k < XR; ++k) {
+        const int r = threadIdx.x + k * XT;
+        const T h = r < ci.n ? slot[ci.base + r] : T{};
+        const T l = r < ci.n ? slot[D + ci.base + r] : T{};
+        words(h, l, hw[k], lw[k]);
+    }
+    int d1[XR][2], d0[XR][2];
+    const int em = fx_group<NC>(hw, lw, d1, d0);
+    typename DigT<VT>::T *out = dg + (uint64_t)j * D + ci.base;
+#pragma unroll
+    for (int k = 0; k < XR; ++k) {
+        const int r = threadIdx.x + k * XT;
+        if (r < ci.n) dig_st(out + r, d1[k], d0[k]);
+    }
+    if (lane == 0) ge[((uint64_t)j * nchunks + blockIdx.x) * XW + warp] = em;
+}
+
+// The exact dot products conj(V_{j0+j}) . w over chunk c, as warp partials:
+// part[((c m + j) XW + q) 3 + {0, 1, 2}] = the re and im sums of warp q (in
+// units of 2^(k - 2098)) and k = em + ew, the sum of its two grid exponents.
+// The stored vectors are read from the digit store (dg, ge), w (interleaved
+// binary64) is put on its warps' grids here.  NV vectors per pass have their
+// loads in flight together.  Graph mode (dx): the range of graph_range.
 template <typename VT, int NV>
 __global__ void __launch_bounds__(XT, 1)
-    k_dotx(const typename PlS<VT>::T *__restrict__ V, uint64_t D, int j0, int m, const VT *__restrict__ w,
-           const SecView *__restrict__ secs, const int *__restrict__ chunk0, int S, const int *__restrict__ active,
-           double2 *__restrict__ part, const int *__restrict__ dx = nullptr, int ring = 0) {
-    using T = typename PlS<VT>::T;
+    k_dotx(const typename DigT<VT>::T *__restrict__ dg, const int *__restrict__ ge, int nchunks, uint64_t D, int j0,
+           int m, const VT *__restrict__ w, const SecView *__restrict__ secs, const int *__restrict__ chunk0, int S,
+           const int *__restrict__ active, long long *__restrict__ part, const int *__restrict__ dx = nullptr,
+           int ring = 0) {
+    using G = typename DigT<VT>::T;
     constexpr bool CX = IsC<VT>::v;
     constexpr int NC = CX ? 2 : 1;
-    constexpr int GB = 32;
-    __shared__ double2 red[GB][XW];
     graph_range(dx, ring, j0, m);
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
     if (active && !active[ci.s]) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = (ci.n - (int)threadIdx.x + XT - 1) / XT;          // rows of this thread
     const uint64_t r0 = ci.base + threadIdx.x;
-    // w on its warp's grid: digits (w1, w0) per row and component, and the
-    // negated real-part digits for the imaginary part of conj(a) w
-    int w1[XR][2], w0[XR][2], nw1[XR], nw0[XR];
-    int ew = 54;
+    // w on its warp's grid: digits (w1, w0) per row and component
+    int w1[XR][2], w0[XR][2];
+    int ew;
     {
         uint32_t hw[XR][2], lw[XR][2];
 #pragma unroll
@@ -227,114 +363,140 @@ __global__ void __launch_bounds__(XT, 1)
             lw[k][0] = (uint32_t)__double2loint(v.x);
             hw[k][1] = (uint32_t)__double2hiint(v.y);
             lw[k][1] = (uint32_t)__double2loint(v.y);
-#pragma unroll
-            for (int c = 0; c < NC; ++c) ew = max(ew, fx_exp(hw[k][c]));
         }
-        ew = (int)__reduce_max_sync(0xffffffffu, (unsigned)ew);
-#pragma unroll
-        for (int k = 0; k < XR; ++k) {
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                if (c < NC) fx_digits(hw[k][c], lw[k][c], ew, w1[k][c], w0[k][c]);
-                else w1[k][c] = w0[k][c] = 0;
-            }
-            nw1[k] = -w1[k][0];
-            nw0[k] = -w0[k][0];
-        }
+        ew = fx_group<NC>(hw, lw, w1, w0);
     }
-    for (int jb = 0; jb < m; jb += GB) {
-        const int nj = min(GB, m - jb);
-        for (int jj = 0; jj < nj; jj += NV) {
-            T ah[NV][XR], al[NV][XR];
+    // NV stored vectors per stage, two stages: the loads of the next stage
+    // are in flight while the current one is multiplied
+    struct Stage {
+        int a1[NV][XR][2], a0[NV][XR][2], em[NV];
+    };
+    auto load = [&](Stage &b, int jj) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const int jv = jj + v < nj ? jj + v : nj - 1;      // past the batch: a repeat, discarded
-                const T *slot = V + (uint64_t)(j0 + jb + jv) * 2 * D;
+        for (int v = 0; v < NV; ++v) {
+            const int jv = j0 + (jj + v < m ? jj + v : m - 1);      // past the end: a repeat, discarded
+            const G *slot = dg + (uint64_t)jv * D;
+            b.em[v] = ge[((uint64_t)jv * nchunks + blockIdx.x) * XW + warp];
 #pragma unroll
-                for (int k = 0; k < XR; ++k) {
-                    if (k < nk) {
-                        ah[v][k] = slot[r0 + (uint64_t)k * XT];
-                        al[v][k] = slot[D + r0 + (uint64_t)k * XT];
-                    } else {
-                        ah[v][k] = T{};
-                        al[v][k] = T{};
-                    }
+            for (int k = 0; k < XR; ++k) {
+                if (k < nk) {
+                    dig_ld(slot + r0 + (uint64_t)k * XT, b.a1[v][k], b.a0[v][k]);
+                } else {
+                    b.a1[v][k][0] = b.a0[v][k][0] = b.a1[v][k][1] = b.a0[v][k][1] = 0;
                 }
             }
+        }
+    };
+    auto consume = [&](const Stage &b, int jj) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                uint32_t hw[XR][2], lw[XR][2];
-                int em = 54;
+        for (int v = 0; v < NV; ++v) {
+            // conj(a) w = (a.r w.r + a.i w.i) + i (a.r w.i - a.i w.r): the
+            // subtracted terms go to their own sums (hn, mn)
+            long long hr = 0, mr = 0, hi = 0, mi = 0, hn = 0, mn = 0;
 #pragma unroll
-                for (int k = 0; k < XR; ++k) {
-                    words(ah[v][k], al[v][k], hw[k], lw[k]);
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) em = max(em, fx_exp(hw[k][c]));
-                }
-                em = (int)__reduce_max_sync(0xffffffffu, (unsigned)em);
-                long long hr = 0, mr = 0, hi = 0, mi = 0;
-#pragma unroll
-                for (int k = 0; k < XR; ++k) {
-                    int a1r, a0r;
-                    fx_digits(hw[k][0], lw[k][0], em, a1r, a0r);
-                    hr = mad_w(a1r, w1[k][0], hr);
-                    mr = mad_w(a1r, w0[k][0], mr);
-                    mr = mad_w(a0r, w1[k][0], mr);
-                    if (CX) {
-                        int a1i, a0i;
-                        fx_digits(hw[k][1], lw[k][1], em, a1i, a0i);
-                        // conj(a) w = (a.r w.r + a.i w.i) + i (a.r w.i - a.i w.r)
-                        hr = mad_w(a1i, w1[k][1], hr);
-                        mr = mad_w(a1i, w0[k][1], mr);
-                        mr = mad_w(a0i, w1[k][1], mr);
-                        hi = mad_w(a1r, w1[k][1], hi);
-                        hi = mad_w(a1i, nw1[k], hi);
-                        mi = mad_w(a1r, w0[k][1], mi);
-                        mi = mad_w(a0r, w1[k][1], mi);
-                        mi = mad_w(a1i, nw0[k], mi);
-                        mi = mad_w(a0i, nw1[k], mi);
-                    }
-                }
-                hr = warp_sum_ll(hr);
-                mr = warp_sum_ll(mr);
+            for (int k = 0; k < XR; ++k) {
+                const int a1r = b.a1[v][k][0], a0r = b.a0[v][k][0];
+                hr = mad_w(a1r, w1[k][0], hr);
+                mr = mad_w(a1r, w0[k][0], mr);
+                mr = mad_w(a0r, w1[k][0], mr);
                 if (CX) {
-                    hi = warp_sum_ll(hi);
-                    mi = warp_sum_ll(mi);
-                }
-                if (lane == 0 && jj + v < nj) {
-                    // (h 2^52 + m 2^26) u_a u_w = (h 2^26 + m) 2^(em + ew - 2124)
-                    const int k = em + ew - 2124;
-                    const double re = ldexp(fma((double)hr, 0x1p26, (double)mr), k);
-                    const double im = CX ? ldexp(fma((double)hi, 0x1p26, (double)mi), k) : 0.0;
-                    red[jj + v][warp] = make_double2(re, im);
+                    const int a1i = b.a1[v][k][1], a0i = b.a0[v][k][1];
+                    hr = mad_w(a1i, w1[k][1], hr);
+                    mr = mad_w(a1i, w0[k][1], mr);
+                    mr = mad_w(a0i, w1[k][1], mr);
+                    hi = mad_w(a1r, w1[k][1], hi);
+                    hn = mad_w(a1i, w1[k][0], hn);
+                    mi = mad_w(a1r, w0[k][1], mi);
+                    mi = mad_w(a0r, w1[k][1], mi);
+                    mn = mad_w(a1i, w0[k][0], mn);
+                    mn = mad_w(a0i, w1[k][0], mn);
                 }
             }
-        }
-        __syncthreads();
-        if ((int)threadIdx.x < nj) {
-            double2 t = red[threadIdx.x][0];
-#pragma unroll
-            for (int q = 1; q < XW; ++q) {
-                t.x += red[threadIdx.x][q].x;
-                t.y += red[threadIdx.x][q].y;
+            hi -= hn;
+            mi -= mn;
+            // h 2^52 + m 2^26 = (h + m / 2^26) 2^52, rounded at weight 2^52
+            const long long sr = warp_sum_ll(hr + ((mr + (1ll << 25)) >> 26));
+            const long long si = CX ? warp_sum_ll(hi + ((mi + (1ll << 25)) >> 26)) : 0ll;
+            if (lane == 0 && jj + v < m) {
+                long long *o = part + (((uint64_t)blockIdx.x * m + jj + v) * XW + warp) * 3;
+                o[0] = sr;
+                o[1] = si;
+                o[2] = b.em[v] + ew;
             }
-            part[(uint64_t)blockIdx.x * m + jb + threadIdx.x] = t;
         }
-        __syncthreads();
+    };
+    Stage s0, s1;
+    if (m > 0) load(s0, 0);
+#pragma unroll 1
+    for (int jj = 0; jj < m; jj += 2 * NV) {
+        if (jj + NV < m) load(s1, jj + NV);
+        consume(s0, jj);
+        if (jj + NV >= m) break;
+        if (jj + 2 * NV < m) load(s0, jj + 2 * NV);
+        consume(s1, jj + NV);
+    }
+}
+
+// out[s * ldo + j] = the sector's dot product j from the k_dotx partials of
+// all its chunks and warps: aligned to the coarsest grid among them (rounded
+// to nearest), summed exactly in 128 bits, rounded to binary64 once.  One
+// warp per coefficient (graph mode: the range of graph_range, written from
+// out + j0).  A warp partial s at exponent sum k is worth s 2^(k - 2098).
+__global__ void k_reducex(const long long *__restrict__ part, int m, const int *__restrict__ chunk0,
+                          const int *__restrict__ active, double2 *__restrict__ out, int ldo,
+                          const int *__restrict__ dx, int ring, int cx) {
+    const int s = blockIdx.y;
+    if (dx) {
+        int j0 = 0;
+        graph_range(dx, ring, j0, m);
+        out += j0;
+    }
+    if (active && !active[s]) return;
+    const int wpb = blockDim.x >> 5, lane = threadIdx.x & 31;
+    const int p0 = chunk0[s] * XW, p1 = chunk0[s + 1] * XW;        // (chunk, warp) partials of the sector
+    for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < m; j += gridDim.x * wpb) {
+        int K = -1;
+        for (int p = p0 + lane; p < p1; p += 32) {
+            const long long *q = part + (((uint64_t)(p / XW) * m + j) * XW + p % XW) * 3;
+            K = max(K, (int)q[2]);
+        }
+        K = __reduce_max_sync(0xffffffffu, K);
+        __int128 ar = 0, ai = 0;
+        for (int p = p0 + lane; p < p1; p += 32) {
+            const long long *q = part + (((uint64_t)(p / XW) * m + j) * XW + p % XW) * 3;
+            const int d = K - (int)q[2];
+            if (d > 100) continue;                                 // below 2^-38 of one unit of K
+            __int128 vr = q[0], vi = q[1];
+            if (d > 0) {
+                const __int128 h = (__int128)1 << (d - 1);
+                vr = (vr + h) >> d;
+                vi = (vi + h) >> d;
+            }
+            ar += vr;
+            ai += vi;
+        }
+        ar = warp_sum_i128(ar);
+        if (cx) ai = warp_sum_i128(ai);
+        if (lane == 0)
+            out[(uint64_t)s * ldo + j] = make_double2(i128_ldexp(ar, K - 2098), cx ? i128_ldexp(ai, K - 2098) : 0.0);
     }
 }
 
 template <typename VT>
-static int dotx_launch(int nv, const typename PlS<VT>::T *v, uint64_t D, int j0, int m, const VT *w,
-                       const SecView *secs, const int *c0, int S, const int *act, double2 *pp, int grid,
+static int dotx_launch(int nv, const typename DigT<VT>::T *dg, const int *ge, int nchunks, uint64_t D, int j0, int m,
+                       const VT *w, const SecView *secs, const int *c0, int S, const int *act, long long *pp,
                        cudaStream_t st, const int *dx = nullptr, int ring = 0) {
-    if (ring || (!dx && m <= 2)) nv = std::min(nv, 2);
-    if (nv == 1)
-        k_dotx<VT, 1><<<grid, XT, 0, st>>>(v, D, j0, m, w, secs, c0, S, act, pp, dx, ring);
-    else if (nv == 4)
-        k_dotx<VT, 4><<<grid, XT, 0, st>>>(v, D, j0, m, w, secs, c0, S, act, pp, dx, ring);
-    else
-        k_dotx<VT, 2><<<grid, XT, 0, st>>>(v, D, j0, m, w, secs, c0, S, act, pp, dx, ring);
+    // complex rows stage at most 2 vectors (4 would spill registers)
+    if (ring || (!dx && m <= 2) || IsC<VT>::v) nv = std::min(nv, 2);
+    const int g = std::max(nchunks, 1);
+    if (nv == 1) {
+        k_dotx<VT, 1><<<g, XT, 0, st>>>(dg, ge, nchunks, D, j0, m, w, secs, c0, S, act, pp, dx, ring);
+    } else if (nv == 2) {
+        k_dotx<VT, 2><<<g, XT, 0, st>>>(dg, ge, nchunks, D, j0, m, w, secs, c0, S, act, pp, dx, ring);
+    } else {
+        if constexpr (!IsC<VT>::v)
+            k_dotx<VT, 4><<<g, XT, 0, st>>>(dg, ge, nchunks, D, j0, m, w, secs, c0, S, act, pp, dx, ring);
+    }
     QS3_LAUNCHED();
     return QS3_OK;
 }
@@ -491,28 +653,50 @@ __global__ void __launch_bounds__(NTHREADS)
 }
 
 // psi_{x+1} = w * inv[s]: into the store's slot (graph mode: slot *dx + 1 of
-// the store at out) and into hin, the interleaved input of the next H Phi.
-// w may alias hin (the start vector is normalised in place).
+// the store at out), its digit-store image (dg, ge) and hin, the interleaved
+// input of the next H Phi.  w may alias hin (the start vector is normalised
+// in place).  One block of XT threads per chunk.
 template <typename VT>
-__global__ void __launch_bounds__(NTHREADS)
-    k_scale64(const VT *w, typename PlS<VT>::T *__restrict__ out, VT *hin, const double *__restrict__ inv,
+__global__ void __launch_bounds__(XT)
+    k_scale64(const VT *w, typename PlS<VT>::T *__restrict__ out, typename DigT<VT>::T *__restrict__ dg,
+              int *__restrict__ ge, int nchunks, VT *hin, const double *__restrict__ inv,
               const SecView *__restrict__ secs, const int *__restrict__ chunk0, int S, const int *__restrict__ active,
               const int *__restrict__ dx, uint64_t D) {
-    if (dx) out += (uint64_t)(*dx + 1) * 2 * D;
+    constexpr int NC = IsC<VT>::v ? 2 : 1;
+    if (dx) {
+        out += (uint64_t)(*dx + 1) * 2 * D;
+        dg += (uint64_t)(*dx + 1) * D;
+        ge += (uint64_t)(*dx + 1) * nchunks * XW;
+    }
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
     if (active && !active[ci.s]) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double f = inv[ci.s];
+    uint32_t hw[XR][2], lw[XR][2];
 #pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int r = threadIdx.x + k * NTHREADS;
+    for (int k = 0; k < XR; ++k) {
+        const int r = threadIdx.x + k * XT;
+        double2 v = make_double2(0.0, 0.0);
         if (r < ci.n) {
-            double2 v = ld2(w + ci.base + r);
+            v = ld2(w + ci.base + r);
             v.x *= f;
             v.y *= f;
             pl_st(out, D, ci.base + r, v);
             st2(hin + ci.base + r, v);
         }
+        hw[k][0] = (uint32_t)__double2hiint(v.x);
+        lw[k][0] = (uint32_t)__double2loint(v.x);
+        hw[k][1] = (uint32_t)__double2hiint(v.y);
+        lw[k][1] = (uint32_t)__double2loint(v.y);
     }
+    int d1[XR][2], d0[XR][2];
+    const int em = fx_group<NC>(hw, lw, d1, d0);
+#pragma unroll
+    for (int k = 0; k < XR; ++k) {
+        const int r = threadIdx.x + k * XT;
+        if (r < ci.n) dig_st(dg + ci.base + r, d1[k], d0[k]);
+    }
+    if (lane == 0) ge[(uint64_t)blockIdx.x * XW + warp] = em;
 }
 
 // out_y[r] = sum_x V_x[r] C[s][x][y] (binary64 FMAs), y < nout <= MAXOUT, for
@@ -603,7 +787,7 @@ struct Engine64 {
     HphiStats *stats;
     int cap = 0, nscr = 0;
     uint64_t D = 0;
-    DevBuf V, wbuf, hinb, part, h1, h2, alpha, beta, nrm, nrm1, inv, active;
+    DevBuf V, DG, GE, wbuf, hinb, part, partx, h1, h2, alpha, beta, nrm, nrm1, inv, active;
     std::vector<int> h_active;
     double brk = 1e-12;
     int strict = 0;                        // 1: every update on binary64 FMAs
@@ -632,6 +816,9 @@ struct Engine64 {
     qs3_dtype dtype() const { return IsC<VT>::v ? QS3_C128 : QS3_F64; }
     // slot j of the store (2 D words-per-element units)
     ST *svec(int j) { return V.as<ST>() + (uint64_t)j * 2 * D; }
+    // the digit store: slot j's digits and its grid exponents
+    typename DigT<VT>::T *dg(int j = 0) { return DG.as<typename DigT<VT>::T>() + (uint64_t)j * D; }
+    int *ge(int j = 0) { return GE.as<int>() + (uint64_t)j * std::max(B.nchunks, 1) * XW; }
     size_t slot_bytes() const { return (size_t)D * sizeof(VT); }
     VT *hin(int) { return hinb.as<VT>(); }
     VT *wv() { return wbuf.as<VT>(); }
@@ -645,9 +832,12 @@ struct Engine64 {
         nscr = nscratch;
         D = B.total;
         QS3_TRY(V.alloc((uint64_t)(cap + nscr) * D * sizeof(VT)));
+        QS3_TRY(DG.alloc((uint64_t)(cap + nscr) * D * sizeof(VT)));
+        QS3_TRY(GE.alloc((uint64_t)(cap + nscr) * std::max(B.nchunks, 1) * XW * sizeof(int)));
         QS3_TRY(wbuf.alloc(std::max<uint64_t>(D, 1) * sizeof(VT)));
         QS3_TRY(hinb.alloc(std::max<uint64_t>(D, 1) * sizeof(VT)));
         QS3_TRY(part.alloc((uint64_t)std::max(B.nchunks, 1) * cap * sizeof(double2)));
+        QS3_TRY(partx.alloc((uint64_t)std::max(B.nchunks, 1) * cap * XW * 3 * sizeof(long long)));
         QS3_TRY(h1.alloc((uint64_t)B.S * cap * sizeof(double2)));
         QS3_TRY(h2.alloc((uint64_t)B.S * cap * sizeof(double2)));
         QS3_TRY(alpha.alloc((uint64_t)B.S * cap * sizeof(double)));
@@ -678,15 +868,25 @@ struct Engine64 {
         QS3_LAUNCHED();
         return QS3_OK;
     }
-    // the dot products of w against stored vectors j0 .. j0 + m - 1 into part:
-    // k_dotx with nv stored vectors per pass (1, 2 or 4), or under strict64
-    // k_dot64 (binary64 FMA chains)
+    // the dot products of w against stored vectors j0 .. j0 + m - 1 as chunk
+    // partials: k_dotx with nv stored vectors per pass (1, 2 or 4), or under
+    // strict64 k_dot64 (binary64 FMA chains); dot_reduce sums them per sector
     int dot_launch(int nv, int j0, int m, const int *dx = nullptr, int ring = 0) {
         const ST *v = V.as<ST>();
-        double2 *pp = part.as<double2>();
         const VT *w = wv();
-        if (!strict) return dotx_launch<VT>(nv, v, D, j0, m, w, secs(), c0(), B.S, act(), pp, grid(), st, dx, ring);
-        k_dot64<VT, 2><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), pp, dx, ring);
+        if (!strict)
+            return dotx_launch<VT>(nv, dg(), ge(), B.nchunks, D, j0, m, w, secs(), c0(), B.S, act(),
+                                   partx.as<long long>(), st, dx, ring);
+        k_dot64<VT, 2><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), part.as<double2>(), dx,
+                                                     ring);
+        QS3_LAUNCHED();
+        return QS3_OK;
+    }
+    int dot_reduce(int m, double2 *out, int ldo, const int *dx = nullptr, int ring = 0, int mgrid = 0) {
+        if (strict) return reduce(m, out, ldo, dx, ring, mgrid);
+        const int mg = mgrid > 0 ? mgrid : m;
+        k_reducex<<<dim3((mg + 7) / 8, B.S), NTHREADS, 0, st>>>(partx.as<long long>(), m, c0(), act(), out, ldo, dx,
+                                                                ring, IsC<VT>::v ? 1 : 0);
         QS3_LAUNCHED();
         return QS3_OK;
     }
@@ -694,7 +894,7 @@ struct Engine64 {
     int mdot(int j0, int m, double2 *out, int ldo) {
         if (B.nchunks == 0) return QS3_OK;
         QS3_TRY(dot_launch(B.tune_nv64 > 0 ? B.tune_nv64 : 2, j0, m));
-        return reduce(m, out, ldo);
+        return dot_reduce(m, out, ldo);
     }
     // the staging depth of k_dot64: time 1, 2 and 4 vectors per pass on
     // min(cap, 48) zeroed slots and keep the fastest for this basis
@@ -705,6 +905,8 @@ struct Engine64 {
         if (cst != cudaStreamCaptureStatusNone) return QS3_OK;
         const int m = std::min(cap, 48);
         QS3_CUDA(cudaMemsetAsync(V.p, 0, (size_t)m * slot_bytes(), st));
+        QS3_CUDA(cudaMemsetAsync(DG.p, 0, (size_t)m * slot_bytes(), st));
+        QS3_CUDA(cudaMemsetAsync(GE.p, 0, (size_t)m * B.nchunks * XW * sizeof(int), st));
         QS3_CUDA(cudaMemsetAsync(wbuf.p, 0, wbuf.n, st));
         cudaEvent_t e0, e1;
         QS3_CUDA(cudaEventCreate(&e0));
@@ -745,8 +947,8 @@ struct Engine64 {
     // psi_j = w * inv (per sector) into slot j and hin
     int scale_store(const VT *w, int j) {
         if (B.nchunks == 0) return QS3_OK;
-        k_scale64<VT><<<grid(), NTHREADS, 0, st>>>(w, svec(j), hin(0), inv.as<double>(), secs(), c0(), B.S, act(),
-                                                   nullptr, D);
+        k_scale64<VT><<<grid(), XT, 0, st>>>(w, svec(j), dg(j), ge(j), B.nchunks, hin(0), inv.as<double>(), secs(),
+                                             c0(), B.S, act(), nullptr, D);
         QS3_LAUNCHED();
         return QS3_OK;
     }
@@ -801,13 +1003,13 @@ struct Engine64 {
         double2 *hh1 = h1.as<double2>(), *n1 = nrm1.as<double2>();
         QS3_TRY(hphi_launch(B, dtype(), hin(0), w, st, act()));
         QS3_TRY(dot_launch(2, 0, 2, dx, 1));
-        QS3_TRY(reduce(2, hh1, cap, dx, 1, 2));
+        QS3_TRY(dot_reduce(2, hh1, cap, dx, 1, 2));
         k_upd64<VT><<<grid(), NTHREADS, 2 * (sizeof(double2) + sizeof(float2)), st>>>(
             w, V.as<ST>(), D, 0, 2, hh1, cap, secs(), c0(), B.S, act(), nullptr, strict, part.as<double2>(), dx, 1);
         QS3_LAUNCHED();
         QS3_TRY(reduce(1, n1, 1));
         QS3_TRY(dot_launch(B.tune_nv64 > 0 ? B.tune_nv64 : 2, 0, cap, dx, 0));
-        QS3_TRY(reduce(cap, h2.as<double2>(), cap, dx, 0, cap));
+        QS3_TRY(dot_reduce(cap, h2.as<double2>(), cap, dx, 0, cap));
         k_upd64<VT><<<grid(), NTHREADS, (size_t)cap * (sizeof(double2) + sizeof(float2)), st>>>(
             w, V.as<ST>(), D, 0, cap, h2.as<double2>(), cap, secs(), c0(), B.S, act(), n1, strict,
             part.as<double2>(), dx, 0);
@@ -817,8 +1019,8 @@ struct Engine64 {
                                                          alpha.as<double>(), beta.as<double>(), inv.as<double>(), brk,
                                                          dx);
         QS3_LAUNCHED();
-        k_scale64<VT><<<grid(), NTHREADS, 0, st>>>(w, V.as<ST>(), hin(0), inv.as<double>(), secs(), c0(), B.S, act(),
-                                                   dx, D);
+        k_scale64<VT><<<grid(), XT, 0, st>>>(w, V.as<ST>(), dg(), ge(), B.nchunks, hin(0), inv.as<double>(), secs(),
+                                             c0(), B.S, act(), dx, D);
         QS3_LAUNCHED();
         k_advance<<<1, 1, 0, st>>>(xdev.as<int>());
         QS3_LAUNCHED();
@@ -920,13 +1122,21 @@ struct Engine64 {
         static_assert(std::is_same<OT, WT>::value, "results are binary64 vectors");
         return combine_to<false>(out, ldo, nin, nout, C, mask);
     }
+    // the digit store of slots j0 .. j0 + n - 1 from the binary64 store
+    int digitize(int j0, int n) {
+        if (B.nchunks == 0 || n <= 0) return QS3_OK;
+        k_digitize<VT><<<dim3(B.nchunks, n), XT, 0, st>>>(V.as<ST>(), D, j0, DG.as<typename DigT<VT>::T>(),
+                                                           GE.as<int>(), B.nchunks, secs(), c0(), B.S);
+        QS3_LAUNCHED();
+        return QS3_OK;
+    }
     // thick restart (Alg. 10 lines 14-19): psi_y = Psi C[:, y] for y < NK
     // (through the scratch slots), psi_NK = psi_NM; hin already holds psi_NM
     int thick_restart(int NM, int NK, const std::vector<double> &C) {
         QS3_TRY(combine_to<true>(svec(cap), 0, NM, NK, C, h_active));
         QS3_CUDA(cudaMemcpyAsync(svec(0), svec(cap), (size_t)NK * slot_bytes(), cudaMemcpyDeviceToDevice, st));
         QS3_CUDA(cudaMemcpyAsync(svec(NK), svec(NM), slot_bytes(), cudaMemcpyDeviceToDevice, st));
-        return QS3_OK;
+        return digitize(0, NK + 1);
     }
 };
 

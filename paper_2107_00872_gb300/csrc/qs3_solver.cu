@@ -2516,9 +2516,9 @@ static int gs_dots_run(Basis &B, int m, const VT *V, uint64_t ldv, const VT *w, 
     const uint64_t D = B.total;
     memset(out, 0, (size_t)B.S * m * 2 * sizeof(double));
     if (m == 0 || B.nchunks == 0) return QS3_OK;
-    DevBuf pl, part, res;
+    DevBuf pl, dgt, get, part, res;
     QS3_TRY(pl.alloc((uint64_t)m * D * sizeof(VT)));
-    QS3_TRY(part.alloc((uint64_t)B.nchunks * m * sizeof(double2)));
+    QS3_TRY(part.alloc((uint64_t)B.nchunks * m * (mode == 0 ? XW * 3 * sizeof(long long) : sizeof(double2))));
     QS3_TRY(res.alloc((uint64_t)B.S * m * sizeof(double2)));
     const int g = (int)std::min<uint64_t>((D + 255) / 256, 4096);
     for (int j = 0; j < m; ++j) {
@@ -2528,15 +2528,25 @@ static int gs_dots_run(Basis &B, int m, const VT *V, uint64_t ldv, const VT *w, 
     const SecView *secs = B.d_secs.as<SecView>();
     const int *c0 = B.d_chunk0.as<int>();
     if (mode == 0) {
-        QS3_TRY(dotx_launch<VT>(2, pl.as<T>(), D, 0, m, w, secs, c0, B.S, nullptr, part.as<double2>(), B.nchunks,
-                                st));
+        using G = typename DigT<VT>::T;
+        QS3_TRY(dgt.alloc((uint64_t)m * D * sizeof(VT)));
+        QS3_TRY(get.alloc((uint64_t)m * B.nchunks * XW * sizeof(int)));
+        k_digitize<VT><<<dim3(B.nchunks, m), XT, 0, st>>>(pl.as<T>(), D, 0, dgt.as<G>(), get.as<int>(), B.nchunks,
+                                                           secs, c0, B.S);
+        QS3_LAUNCHED();
+        QS3_TRY(dotx_launch<VT>(2, dgt.as<G>(), get.as<int>(), B.nchunks, D, 0, m, w, secs, c0, B.S, nullptr,
+                                part.as<long long>(), st));
+        k_reducex<<<dim3((m + 7) / 8, B.S), NTHREADS, 0, st>>>(part.as<long long>(), m, c0, nullptr,
+                                                               res.as<double2>(), m, nullptr, 0, IsC<VT>::v ? 1 : 0);
+        QS3_LAUNCHED();
     } else {
         k_dot64<VT, 2><<<B.nchunks, NTHREADS, 0, st>>>(pl.as<T>(), D, 0, m, w, secs, c0, B.S, nullptr,
                                                         part.as<double2>());
         QS3_LAUNCHED();
+        k_reduce64<<<dim3((m + 7) / 8, B.S), NTHREADS, 0, st>>>(part.as<double2>(), m, c0, nullptr,
+                                                                res.as<double2>(), m);
+        QS3_LAUNCHED();
     }
-    k_reduce64<<<dim3((m + 7) / 8, B.S), NTHREADS, 0, st>>>(part.as<double2>(), m, c0, nullptr, res.as<double2>(), m);
-    QS3_LAUNCHED();
     QS3_CUDA(cudaMemcpyAsync(out, res.p, (size_t)B.S * m * sizeof(double2), cudaMemcpyDeviceToHost, st));
     QS3_CUDA(cudaStreamSynchronize(st));
     return QS3_OK;
@@ -2674,6 +2684,8 @@ static size_t solve_mem_estimate(const Basis &B, const qs3_solve_opts &o) {
     size_t m = cap * B.total * ev + 2 * B.total * ev64 + (size_t)std::max(B.nchunks, 1) * cap * 16;
     if (o.precision == QS3_F32) m += cap * B.total * ev64;   // the binary64 refinement
     m += 3 * B.total * ev64;                                 // w, H's input copy (and the double-float ring)
+    if (o.precision != QS3_C128DF)       // the digit store and the exact-dot warp partials
+        m += cap * B.total * ev64 + (size_t)std::max(B.nchunks, 1) * cap * XW * (24 + 4);
     if (B.has_k && o.precision == QS3_C128DF && !o.hphi_ieee) m += 2 * B.total * 16;   // double-float w and input
     return m;
 }
