@@ -3,31 +3,34 @@
 //
 // Alg. 10 in the paper's arithmetic, complex double (k-sectors) or double
 // (U(1)-only bases): every Lanczos vector, every product H psi_x and every
-// Gram-Schmidt operand is an IEEE binary64 value, and every operation on
-// them is a binary64 fused multiply-add (the fp64 pipe).
+// Gram-Schmidt operand is an IEEE binary64 value.
 //
 // Layout.  The Krylov basis is kept as binary64 values split into their high
 // and low 32-bit words, stored in two planes per vector (word-planar): slot j
 // holds D high words (complex: (re.hi, im.hi) pairs) and then D low words.
-// A value is reassembled bit for bit from its two words; the planes only let
-// a pass that needs no more than the high words read half the bytes.  The
-// product H psi_x reads an interleaved copy of psi_x (hin) written together
-// with slot x.
+// A value is reassembled bit for bit from its two words.  Beside it a digit
+// store holds each vector's fixed-point image (below).  The product H psi_x
+// reads an interleaved copy of psi_x (hin) written together with slot x.
 //
 // One step (Alg. 10 lines 5-11, full reorthogonalisation):
 //   w = H psi_x;  three-term part: c_j = psi_j^H w for j = x-1, x (alpha_x
 //   among them), w -= sum_j c_j psi_j;  one classical Gram-Schmidt pass:
 //   g_j = psi_j^H w for j = 0..x, w -= sum_j g_j psi_j;  beta_x = |w|;
 //   psi_{x+1} = w / beta_x.
-// Dot products and updates are binary64 FMA chains per thread, reduced in a
-// fixed order (deterministic).  The one exception is the Gram-Schmidt
-// update whose coefficients are all tiny: when sum_j |g_j| <= 2^-36 |w|
-// (the normal case: w is already orthogonal to the basis to O(eps)), the
-// correction u = sum_j g_j psi_j is summed in fp32 from the high words
-// (20-bit significands, relative error < 2^-19 per term), so |error of u| <=
-// 2^-19 * 2^-36 |w| = 2^-55 |w|, below half an ulp of binary64 applied to
-// |w|; w - u is then formed in binary64.  The solve option strict64 keeps
-// that update on binary64 FMAs as well.
+// Updates are binary64 FMA chains per thread.  Two exceptions, both bounded
+// below binary64's own rounding:
+//  - the dot products are exact sums on fixed-point images of the operands
+//    (k_dotx, below; the stored vectors' images are kept in a digit store);
+//  - the Gram-Schmidt update whose coefficients are all tiny: when
+//    sum_j |g_j| <= 2^-40 |w| (the normal case: w is already orthogonal to
+//    the basis to O(eps)), the correction u = sum_j g_j psi_j is summed in
+//    fp32 from the top digits of the digit store (each value known to 2^-21
+//    of its warp group's largest magnitude, so |delta psi_j| <= 2^-17.5 in
+//    norm), and the fp32 sums of m <= 2^8 terms add relative 2^-16:
+//    |error of u| <= (2^-17.5 + 2^-16) 2^-40 |w| < 2^-55.5 |w|, below half an
+//    ulp of binary64 applied to |w| (for m > 2^8 the limit 2^-40 shrinks by
+//    2^8 / m); w - u is then formed in binary64.
+// The solve option strict64 keeps the dots and that update on binary64 FMAs.
 #pragma once
 
 namespace qs3 {
@@ -50,20 +53,6 @@ __device__ __forceinline__ void pl_st(uint32_t *slot, uint64_t D, uint64_t r, do
     slot[r] = (unsigned)__double2hiint(v.x);
     slot[D + r] = (unsigned)__double2loint(v.x);
 }
-// the high word of a binary64 as binary32: sign, exponent rebiased from 1023
-// to 127, the 20 significand bits it holds (truncated); magnitudes outside
-// the binary32 normal range give 0 (Lanczos vectors have norm 1, so only
-// values below 2^-126 do, and they are dropped with an error below 2^-126)
-__device__ __forceinline__ float hi_f(uint32_t h) {
-    const uint32_t e = (h >> 20) & 0x7ffu;
-    const uint32_t f = (((h & 0x7fffffffu) << 3) - (896u << 23)) | (h & 0x80000000u);
-    return (e - 897u < 254u) ? __uint_as_float(f) : 0.f;
-}
-__device__ __forceinline__ float2 pl_ld_hi(const uint2 *slot, uint64_t r) {
-    const uint2 h = slot[r];
-    return make_float2(hi_f(h.x), hi_f(h.y));
-}
-__device__ __forceinline__ float2 pl_ld_hi(const uint32_t *slot, uint64_t r) { return make_float2(hi_f(slot[r]), 0.f); }
 
 // part[c * m + j] = conj(V_{j0+j}) . w over chunk c (binary64 FMAs); V the
 // word-planar store (slots of 2D words-per-element units), w interleaved.
@@ -255,26 +244,35 @@ __device__ __forceinline__ void words(uint32_t h, uint32_t l, uint32_t (&hw)[2],
 }
 
 // The digit store.  Every stored vector also exists as its fixed-point
-// image: per row the balanced digits (P1, P0) of each component (int4 for
-// complex rows: re.P1, re.P0, im.P1, im.P0; int2 for real rows), and per
-// chunk and warp group (the 128 rows base + 32 q + lane + 512 k of a chunk)
-// the grid exponent em.  It is derived from the binary64 store by the kernels
-// that write it (k_scale64, k_digitize) and read only by the dot products.
-template <typename VT> struct DigT { using T = int2; };
-template <> struct DigT<double2> { using T = int4; };
+// image: per row the balanced digits (P1, P0) of each component, in two
+// planes per slot (D P1 words: (re, im) pairs for complex rows, then D P0
+// words), and per chunk and warp group (the 128 rows base + 32 q + lane +
+// 512 k of a chunk) the grid exponent em.  It is derived from the binary64
+// store by the kernels that write it (k_scale64, k_digitize) and read by the
+// dot products (both planes) and the fp32 Gram-Schmidt correction (P1 only).
+template <typename VT> struct DigT { using T = int; };
+template <> struct DigT<double2> { using T = int2; };
 
-__device__ __forceinline__ void dig_st(int4 *p, const int (&d1)[2], const int (&d0)[2]) {
-    *p = make_int4(d1[0], d0[0], d1[1], d0[1]);
+__device__ __forceinline__ void dig_st(int2 *slot, uint64_t D, uint64_t r, const int (&d1)[2], const int (&d0)[2]) {
+    slot[r] = make_int2(d1[0], d1[1]);
+    slot[D + r] = make_int2(d0[0], d0[1]);
 }
-__device__ __forceinline__ void dig_st(int2 *p, const int (&d1)[2], const int (&d0)[2]) { *p = make_int2(d1[0], d0[0]); }
-__device__ __forceinline__ void dig_ld(const int4 *p, int (&d1)[2], int (&d0)[2]) {
-    const int4 v = *p;
-    d1[0] = v.x; d0[0] = v.y; d1[1] = v.z; d0[1] = v.w;
+__device__ __forceinline__ void dig_st(int *slot, uint64_t D, uint64_t r, const int (&d1)[2], const int (&d0)[2]) {
+    slot[r] = d1[0];
+    slot[D + r] = d0[0];
 }
-__device__ __forceinline__ void dig_ld(const int2 *p, int (&d1)[2], int (&d0)[2]) {
-    const int2 v = *p;
-    d1[0] = v.x; d0[0] = v.y; d1[1] = 0; d0[1] = 0;
+__device__ __forceinline__ void dig_ld(const int2 *slot, uint64_t D, uint64_t r, int (&d1)[2], int (&d0)[2]) {
+    const int2 h = slot[r], l = slot[D + r];
+    d1[0] = h.x; d1[1] = h.y; d0[0] = l.x; d0[1] = l.y;
 }
+__device__ __forceinline__ void dig_ld(const int *slot, uint64_t D, uint64_t r, int (&d1)[2], int (&d0)[2]) {
+    d1[0] = slot[r]; d1[1] = 0; d0[0] = slot[D + r]; d0[1] = 0;
+}
+// the top digit P1 (|P1| <= 2^27) as the float P1 / 32 rounded down to an
+// integer (|.| <= 2^22, exact: 1.5 2^23 + x has unit spacing)
+__device__ __forceinline__ float p1_f(int p1) { return __int_as_float(0x4B400000 + (p1 >> 5)) - 12582912.0f; }
+__device__ __forceinline__ float2 p1_f2(int2 p) { return make_float2(p1_f(p.x), p1_f(p.y)); }
+__device__ __forceinline__ float2 p1_f2(int p) { return make_float2(p1_f(p), 0.f); }
 
 // the XR binary64 values (hi, lo words per component) of one thread of a
 // warp group on the group's grid: the warp's largest biased exponent em
@@ -321,11 +319,11 @@ __global__ void __launch_bounds__(XT)
     }
     int d1[XR][2], d0[XR][2];
     const int em = fx_group<NC>(hw, lw, d1, d0);
-    typename DigT<VT>::T *out = dg + (uint64_t)j * D + ci.base;
+    typename DigT<VT>::T *out = dg + (uint64_t)j * 2 * D;
 #pragma unroll
     for (int k = 0; k < XR; ++k) {
         const int r = threadIdx.x + k * XT;
-        if (r < ci.n) dig_st(out + r, d1[k], d0[k]);
+        if (r < ci.n) dig_st(out, D, ci.base + r, d1[k], d0[k]);
     }
     if (lane == 0) ge[((uint64_t)j * nchunks + blockIdx.x) * XW + warp] = em;
 }
@@ -375,12 +373,12 @@ __global__ void __launch_bounds__(XT, 1)
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const int jv = j0 + (jj + v < m ? jj + v : m - 1);      // past the end: a repeat, discarded
-            const G *slot = dg + (uint64_t)jv * D;
+            const G *slot = dg + (uint64_t)jv * 2 * D;
             b.em[v] = ge[((uint64_t)jv * nchunks + blockIdx.x) * XW + warp];
 #pragma unroll
             for (int k = 0; k < XR; ++k) {
                 if (k < nk) {
-                    dig_ld(slot + r0 + (uint64_t)k * XT, b.a1[v][k], b.a0[v][k]);
+                    dig_ld(slot, D, r0 + (uint64_t)k * XT, b.a1[v][k], b.a0[v][k]);
                 } else {
                     b.a1[v][k][0] = b.a0[v][k][0] = b.a1[v][k][1] = b.a0[v][k][1] = 0;
                 }
@@ -529,13 +527,18 @@ __global__ void k_reduce64(const double2 *__restrict__ part, int m, const int *_
 
 // w -= sum_j V_{j0+j} coef[s][j] (binary64 FMAs from w), and part[c] = |w|^2
 // over chunk c.  With wn2 (|w|^2 before the update) and strict == 0, a sector
-// whose coefficients satisfy (sum_j |re c_j| + |im c_j|)^2 <= 2^-72 |w|^2
-// forms the correction in fp32 from the high words instead (see the file
-// head for the bound).  Graph mode (dx): the range of graph_range, and for
-// the three-term pass (ring) the coefficients from coef + j0.
+// whose coefficients satisfy (sum_j |re c_j| + |im c_j|)^2 <= 2^-80 |w|^2
+// (times (256 / m)^2 for m > 256)
+// forms the correction in fp32 from the top digits of the digit store
+// instead (see the file head for the bound).  One block of XT threads per
+// chunk; the fp32 pass reads UV vectors' top digits per stage, two stages in
+// flight.  Graph mode (dx): the range of graph_range, and for the three-term
+// pass (ring) the coefficients from coef + j0.
+constexpr int UV = 4;
 template <typename VT>
-__global__ void __launch_bounds__(NTHREADS)
-    k_upd64(VT *__restrict__ w, const typename PlS<VT>::T *__restrict__ V, uint64_t D, int j0, int m,
+__global__ void __launch_bounds__(XT)
+    k_upd64(VT *__restrict__ w, const typename PlS<VT>::T *__restrict__ V, const typename DigT<VT>::T *__restrict__ dg,
+            const int *__restrict__ ge, int nchunks, uint64_t D, int j0, int m,
             const double2 *__restrict__ coef, int ldc, const SecView *__restrict__ secs,
             const int *__restrict__ chunk0, int S, const int *__restrict__ active, const double2 *__restrict__ wn2,
             int strict, double2 *__restrict__ part, const int *__restrict__ dx = nullptr, int ring = 0) {
@@ -547,58 +550,99 @@ __global__ void __launch_bounds__(NTHREADS)
     }
     extern __shared__ double2 scd[];              // m coefficients, then m fp32 copies
     float2 *scf = (float2 *)(scd + m);
-    __shared__ double red[NTHREADS / 32];
+    __shared__ double red[XW];
     __shared__ int lite_s;
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
     if (active && !active[ci.s]) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double cs = 0.0;
-    for (int j = threadIdx.x; j < m; j += NTHREADS) {
+    for (int j = threadIdx.x; j < m; j += XT) {
         const double2 c = coef[(uint64_t)ci.s * ldc + j];
         scd[j] = c;
         scf[j] = make_float2((float)c.x, (float)c.y);
         cs += fabs(c.x) + fabs(c.y);
     }
+    if (m > 32) {
 #pragma unroll
-    for (int o = 16; o; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
-    if (lane == 0) red[warp] = cs;
+        for (int o = 16; o; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        if (lane == 0) red[warp] = cs;
+    } else if (warp == 0) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+        if (lane == 0) red[0] = cs;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int q = 0; q < NTHREADS / 32; ++q) t += red[q];
-        lite_s = (!strict && wn2 && t * t <= 0x1p-72 * wn2[ci.s].x) ? 1 : 0;
+        const int nw = m > 32 ? XW : 1;
+        for (int q = 0; q < nw; ++q) t += red[q];
+        const double lim = m > 256 ? 0x1p-80 * (256.0 / m) * (256.0 / m) : 0x1p-80;
+        lite_s = (!strict && wn2 && t * t <= lim * wn2[ci.s].x) ? 1 : 0;
     }
     __syncthreads();
     const bool lite = lite_s != 0;
-    const int nk = (ci.n - (int)threadIdx.x + NTHREADS - 1) / NTHREADS;
+    const int nk = (ci.n - (int)threadIdx.x + XT - 1) / XT;
     const uint64_t r0 = ci.base + threadIdx.x;
     double nrm = 0.0;
     if (lite) {
-        float2 u[RPT];
+        // stored vector j, row: psi ~ (P1 / 32) 2^(em - 1044) (floor of P1 / 32,
+        // an error below 2^-21 of the warp group's largest magnitude)
+        using G = typename DigT<VT>::T;
+        struct Stage {
+            G h[UV][XR];
+            int em[UV];
+        };
+        float2 u[XR];
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) u[k] = make_float2(0.f, 0.f);
-#pragma unroll 2
-        for (int j = 0; j < m; ++j) {
-            const float2 c = scf[j];
-            const T *slot = V + (uint64_t)(j0 + j) * 2 * D;
+        for (int k = 0; k < XR; ++k) u[k] = make_float2(0.f, 0.f);
+        auto load = [&](Stage &b, int jb) {
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                if (k < nk) {
-                    const float2 a = pl_ld_hi(slot, r0 + (uint64_t)k * NTHREADS);
-                    // u += a c: re += a.r c.r - a.i c.i ; im += a.r c.i + a.i c.r
-                    u[k].x = fmaf(a.x, c.x, u[k].x);
-                    if (CX) {
-                        u[k].x = fmaf(-a.y, c.y, u[k].x);
-                        u[k].y = fmaf(a.x, c.y, u[k].y);
-                        u[k].y = fmaf(a.y, c.x, u[k].y);
+            for (int v = 0; v < UV; ++v) {
+                const int j = j0 + min(jb + v, m - 1);
+                const G *slot = dg + (uint64_t)j * 2 * D;
+                b.em[v] = ge[((uint64_t)j * nchunks + blockIdx.x) * XW + warp];
+#pragma unroll
+                for (int k = 0; k < XR; ++k) b.h[v][k] = k < nk ? slot[r0 + (uint64_t)k * XT] : G{};
+            }
+        };
+        auto consume = [&](const Stage &b, int jb) {
+#pragma unroll
+            for (int v = 0; v < UV; ++v) {
+                if (jb + v < m) {
+                    // the coefficient times the group's scale 2^(em - 1044) (0 below
+                    // the fp32 range: those values are under 2^-104)
+                    const int ex = b.em[v] - 1044 + 127;
+                    const float sc = (ex >= 1 && ex <= 254) ? __int_as_float(ex << 23) : 0.f;
+                    const float2 c0 = scf[jb + v];
+                    const float2 c = make_float2(c0.x * sc, c0.y * sc);
+#pragma unroll
+                    for (int k = 0; k < XR; ++k) {
+                        // u += a c: re += a.r c.r - a.i c.i ; im += a.r c.i + a.i c.r
+                        const float2 a = p1_f2(b.h[v][k]);
+                        u[k].x = fmaf(a.x, c.x, u[k].x);
+                        if (CX) {
+                            u[k].x = fmaf(-a.y, c.y, u[k].x);
+                            u[k].y = fmaf(a.x, c.y, u[k].y);
+                            u[k].y = fmaf(a.y, c.x, u[k].y);
+                        }
                     }
                 }
             }
+        };
+        Stage s0, s1;
+        if (m > 0) load(s0, 0);
+#pragma unroll 1
+        for (int jb = 0; jb < m; jb += 2 * UV) {
+            if (jb + UV < m) load(s1, jb + UV);
+            consume(s0, jb);
+            if (jb + UV >= m) break;
+            if (jb + 2 * UV < m) load(s0, jb + 2 * UV);
+            consume(s1, jb + UV);
         }
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
+        for (int k = 0; k < XR; ++k) {
             if (k < nk) {
-                const uint64_t r = r0 + (uint64_t)k * NTHREADS;
+                const uint64_t r = r0 + (uint64_t)k * XT;
                 double2 v = ld2(w + r);
                 v.x -= (double)u[k].x;
                 if (CX) v.y -= (double)u[k].y;
@@ -608,17 +652,17 @@ __global__ void __launch_bounds__(NTHREADS)
             }
         }
     } else {
-        double2 acc[RPT];
+        double2 acc[XR];
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) acc[k] = k < nk ? ld2(w + r0 + (uint64_t)k * NTHREADS) : make_double2(0.0, 0.0);
+        for (int k = 0; k < XR; ++k) acc[k] = k < nk ? ld2(w + r0 + (uint64_t)k * XT) : make_double2(0.0, 0.0);
 #pragma unroll 2
         for (int j = 0; j < m; ++j) {
             const double2 c = scd[j];
             const T *slot = V + (uint64_t)(j0 + j) * 2 * D;
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
+            for (int k = 0; k < XR; ++k) {
                 if (k < nk) {
-                    const double2 a = pl_ld(slot, D, r0 + (uint64_t)k * NTHREADS);
+                    const double2 a = pl_ld(slot, D, r0 + (uint64_t)k * XT);
                     // w -= a c: re -= a.r c.r - a.i c.i ; im -= a.r c.i + a.i c.r
                     acc[k].x = fma(-a.x, c.x, acc[k].x);
                     if (CX) {
@@ -630,9 +674,9 @@ __global__ void __launch_bounds__(NTHREADS)
             }
         }
 #pragma unroll
-        for (int k = 0; k < RPT; ++k) {
+        for (int k = 0; k < XR; ++k) {
             if (k < nk) {
-                st2(w + r0 + (uint64_t)k * NTHREADS, acc[k]);
+                st2(w + r0 + (uint64_t)k * XT, acc[k]);
                 nrm = fma(acc[k].x, acc[k].x, nrm);
                 if (CX) nrm = fma(acc[k].y, acc[k].y, nrm);
             }
@@ -646,7 +690,7 @@ __global__ void __launch_bounds__(NTHREADS)
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
-            for (int q = 0; q < NTHREADS / 32; ++q) t += red[q];
+            for (int q = 0; q < XW; ++q) t += red[q];
             part[blockIdx.x] = make_double2(t, 0.0);
         }
     }
@@ -665,7 +709,7 @@ __global__ void __launch_bounds__(XT)
     constexpr int NC = IsC<VT>::v ? 2 : 1;
     if (dx) {
         out += (uint64_t)(*dx + 1) * 2 * D;
-        dg += (uint64_t)(*dx + 1) * D;
+        dg += (uint64_t)(*dx + 1) * 2 * D;
         ge += (uint64_t)(*dx + 1) * nchunks * XW;
     }
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
@@ -694,7 +738,7 @@ __global__ void __launch_bounds__(XT)
 #pragma unroll
     for (int k = 0; k < XR; ++k) {
         const int r = threadIdx.x + k * XT;
-        if (r < ci.n) dig_st(dg + ci.base + r, d1[k], d0[k]);
+        if (r < ci.n) dig_st(dg, D, ci.base + r, d1[k], d0[k]);
     }
     if (lane == 0) ge[(uint64_t)blockIdx.x * XW + warp] = em;
 }
@@ -817,7 +861,7 @@ struct Engine64 {
     // slot j of the store (2 D words-per-element units)
     ST *svec(int j) { return V.as<ST>() + (uint64_t)j * 2 * D; }
     // the digit store: slot j's digits and its grid exponents
-    typename DigT<VT>::T *dg(int j = 0) { return DG.as<typename DigT<VT>::T>() + (uint64_t)j * D; }
+    typename DigT<VT>::T *dg(int j = 0) { return DG.as<typename DigT<VT>::T>() + (uint64_t)j * 2 * D; }
     int *ge(int j = 0) { return GE.as<int>() + (uint64_t)j * std::max(B.nchunks, 1) * XW; }
     size_t slot_bytes() const { return (size_t)D * sizeof(VT); }
     VT *hin(int) { return hinb.as<VT>(); }
@@ -939,8 +983,9 @@ struct Engine64 {
     // wn2: |w|^2 before it (enables the fp32 correction of tiny coefficients)
     int mupdate(int j0, int m, const double2 *cf, int ldc, double2 *nrm_out, const double2 *wn2 = nullptr) {
         if (B.nchunks == 0) return QS3_OK;
-        k_upd64<VT><<<grid(), NTHREADS, (size_t)m * (sizeof(double2) + sizeof(float2)), st>>>(
-            wv(), V.as<ST>(), D, j0, m, cf, ldc, secs(), c0(), B.S, act(), wn2, strict, part.as<double2>());
+        k_upd64<VT><<<grid(), XT, (size_t)m * (sizeof(double2) + sizeof(float2)), st>>>(
+            wv(), V.as<ST>(), dg(), ge(), B.nchunks, D, j0, m, cf, ldc, secs(), c0(), B.S, act(), wn2, strict,
+            part.as<double2>());
         QS3_LAUNCHED();
         return reduce(1, nrm_out, 1);
     }
@@ -1004,15 +1049,16 @@ struct Engine64 {
         QS3_TRY(hphi_launch(B, dtype(), hin(0), w, st, act()));
         QS3_TRY(dot_launch(2, 0, 2, dx, 1));
         QS3_TRY(dot_reduce(2, hh1, cap, dx, 1, 2));
-        k_upd64<VT><<<grid(), NTHREADS, 2 * (sizeof(double2) + sizeof(float2)), st>>>(
-            w, V.as<ST>(), D, 0, 2, hh1, cap, secs(), c0(), B.S, act(), nullptr, strict, part.as<double2>(), dx, 1);
+        k_upd64<VT><<<grid(), XT, 2 * (sizeof(double2) + sizeof(float2)), st>>>(
+            w, V.as<ST>(), dg(), ge(), B.nchunks, D, 0, 2, hh1, cap, secs(), c0(), B.S, act(), nullptr, strict,
+            part.as<double2>(), dx, 1);
         QS3_LAUNCHED();
         QS3_TRY(reduce(1, n1, 1));
         QS3_TRY(dot_launch(B.tune_nv64 > 0 ? B.tune_nv64 : 2, 0, cap, dx, 0));
         QS3_TRY(dot_reduce(cap, h2.as<double2>(), cap, dx, 0, cap));
-        k_upd64<VT><<<grid(), NTHREADS, (size_t)cap * (sizeof(double2) + sizeof(float2)), st>>>(
-            w, V.as<ST>(), D, 0, cap, h2.as<double2>(), cap, secs(), c0(), B.S, act(), n1, strict,
-            part.as<double2>(), dx, 0);
+        k_upd64<VT><<<grid(), XT, (size_t)cap * (sizeof(double2) + sizeof(float2)), st>>>(
+            w, V.as<ST>(), dg(), ge(), B.nchunks, D, 0, cap, h2.as<double2>(), cap, secs(), c0(), B.S, act(), n1,
+            strict, part.as<double2>(), dx, 0);
         QS3_LAUNCHED();
         QS3_TRY(reduce(1, nrm.as<double2>(), 1));
         k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, 0, cap, hh1, nrm.as<double2>(), act(),

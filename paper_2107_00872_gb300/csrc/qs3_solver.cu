@@ -1742,20 +1742,25 @@ static int residuals(Basis &B, const WT *v, const std::vector<double> &e, cudaSt
 // [2^-500, 2^500], which keeps every ratio exact.  A vanishing p_i takes the
 // sign opposite to p_{i-1} (one change, as for a zero pivot of T - x I = L D L^T
 // counted negative).
-__device__ int sturm_count_dev(int n, const double *__restrict__ a, const double *__restrict__ b, double x) {
+__device__ int sturm_count_dev(int n, const double *__restrict__ a, const double *__restrict__ bb, double x) {
+    // bb[i] = b_{i-1}^2 (bb[0] unused).  Signs, zeros and the rescaling test
+    // read the bit pattern in integer instructions, so the only fp64 work on
+    // the dependent chain is the fma of each step.
     int cnt = 0, sp = 1;
     double pm = 0.0, p = 1.0;
     for (int i = 0; i < n; ++i) {
-        const double bb = i ? b[i - 1] * b[i - 1] : 0.0;
-        const double pn = fma(a[i] - x, p, -bb * pm);
-        const int sn = pn > 0.0 ? 1 : (pn < 0.0 ? -1 : -sp);
+        const double t = i ? bb[i] * pm : 0.0;
+        const double pn = fma(a[i] - x, p, -t);
+        const long long bits = __double_as_longlong(pn);
+        const bool zero = (bits << 1) == 0;
+        const int sn = zero ? -sp : (bits < 0 ? -1 : 1);
         cnt += sn != sp;
         sp = sn;
         pm = p;
         p = pn;
-        const double ap = fabs(p);
-        if (ap > 0x1p500 || (ap < 0x1p-500 && ap != 0.0)) {
-            const double f = ap > 1.0 ? 0x1p-500 : 0x1p500;
+        const int e = (int)((bits >> 52) & 0x7ff);
+        if (e > 1523 || (e < 523 && !zero)) {        // |p| >= 2^501 or 0 < |p| < 2^-500
+            const double f = e > 1523 ? 0x1p-500 : 0x1p500;
             p *= f;
             pm *= f;
         }
@@ -1769,7 +1774,8 @@ __device__ int sturm_count_dev(int n, const double *__restrict__ a, const double
 // shrinking in fp64 (all lanes return the same value).  The bracket starts
 // around e_prev when given (the lowest Ritz value of a shorter Krylov space,
 // which the new one does not exceed) and falls back to the Gershgorin bounds.
-__device__ double tri_lowest_warp(int n, const double *__restrict__ a, const double *__restrict__ b, double e_prev) {
+__device__ double tri_lowest_warp(int n, const double *__restrict__ a, const double *__restrict__ b,
+                                  const double *__restrict__ bb, double e_prev) {
     const int lane = threadIdx.x & 31;
     double lo = 1e300, hi = -1e300;
     for (int i = lane; i < n; i += 32) {
@@ -1789,7 +1795,7 @@ __device__ double tri_lowest_warp(int n, const double *__restrict__ a, const dou
         // lane 0 tests e_prev + margin (must hold an eigenvalue below it),
         // lane 1 e_prev - 1e-6 w (must hold none)
         const double t = lane == 0 ? e_prev + 1e-12 * w : e_prev - 1e-6 * w;
-        const int c = lane < 2 ? sturm_count_dev(n, a, b, t) : 0;
+        const int c = lane < 2 ? sturm_count_dev(n, a, bb, t) : 0;
         const int c0 = __shfl_sync(0xffffffffu, c, 0), c1 = __shfl_sync(0xffffffffu, c, 1);
         const double t0 = __shfl_sync(0xffffffffu, t, 0), t1 = __shfl_sync(0xffffffffu, t, 1);
         if (c0 > 0 && t0 < hi) hi = t0;
@@ -1798,7 +1804,7 @@ __device__ double tri_lowest_warp(int n, const double *__restrict__ a, const dou
     for (int it = 0; it < 64; ++it) {
         const double h = (hi - lo) / 32.0;
         const double xl = lo + h * (double)(lane + 1);
-        const int cnt = (lane < 31 && xl > lo && xl < hi) ? sturm_count_dev(n, a, b, xl) : 0;
+        const int cnt = (lane < 31 && xl > lo && xl < hi) ? sturm_count_dev(n, a, bb, xl) : 0;
         const unsigned mk = __ballot_sync(0xffffffffu, lane < 31 && cnt > 0);
         const int j = mk ? __ffs(mk) - 1 : 31;
         const double nlo = j == 0 ? lo : fmax(lo, lo + h * (double)j);
@@ -1811,17 +1817,23 @@ __device__ double tri_lowest_warp(int n, const double *__restrict__ a, const dou
 }
 
 // eigenvector of the tridiagonal for eigenvalue e by inverse iteration
-// (Gaussian elimination with partial pivoting on T - e I, three sweeps; one
-// thread), largest component positive; ws holds 5 n doubles of workspace
+// (Gaussian elimination with partial pivoting on T - e I; one thread),
+// largest component positive; ws holds 5 n doubles of workspace.  From the
+// start vector in v (start) and `sweeps` sweeps, else from all ones and
+// three sweeps.
 __device__ void tri_vec_dev(int n, const double *__restrict__ a, const double *__restrict__ b, double e,
-                            double *__restrict__ v, double *__restrict__ ws) {
-    for (int i = 0; i < n; ++i) v[i] = 1.0;
-    if (n == 1) return;
+                            double *__restrict__ v, double *__restrict__ ws, bool start = false, int sweeps = 3) {
+    if (!start)
+        for (int i = 0; i < n; ++i) v[i] = 1.0;
+    if (n == 1) {
+        v[0] = 1.0;
+        return;
+    }
     double *d = ws, *du = ws + n, *du2 = ws + 2 * n, *dl = ws + 3 * n, *x = ws + 4 * n;
     double scale = 0.0;
     for (int i = 0; i < n; ++i) scale = fmax(scale, fabs(a[i]) + (i < n - 1 ? fabs(b[i]) : 0.0));
     const double pert = fmax(scale, 1e-300) * 1e-14;
-    for (int it = 0; it < 3; ++it) {
+    for (int it = 0; it < sweeps; ++it) {
         for (int i = 0; i < n; ++i) {
             d[i] = a[i] - e - pert;
             du[i] = i < n - 1 ? b[i] : 0.0;
@@ -1870,6 +1882,48 @@ __device__ void tri_vec_dev(int n, const double *__restrict__ a, const double *_
     if (v[im] < 0.0) for (int i = 0; i < n; ++i) v[i] = -v[i];
 }
 
+// |y_n| of the normalised eigenvector y of the tridiagonal for eigenvalue e,
+// for the Ritz residual beta |y_n|: y solved from the bottom up with y_n = 1,
+// y_{k-1} = -((a_k - e) y_k + b_k y_{k+1}) / b_{k-1} (rb = 1 / b), then
+// normalised.  The lowest Ritz vector of a converging Lanczos run decays
+// towards the bottom, so the recurrence follows its growing direction and
+// keeps |y_n| to about a percent down to 1e-20 (measured against dense
+// eigenvectors), while the forward recurrences lose it below ~1e-8.  Growth
+// past 2^500 means |y_n| < 2^-500: returned as 0.  One thread.
+__device__ double tri_last_dev(int n, const double *__restrict__ a, const double *__restrict__ b,
+                               const double *__restrict__ rb, double e) {
+    double yk = 1.0, yk1 = 0.0, nrm = 1.0;
+    for (int k = n - 1; k >= 1; --k) {
+        const double t = k + 1 < n ? b[k] * yk1 : 0.0;
+        const double y = -fma(a[k] - e, yk, t) * rb[k - 1];
+        nrm = fma(y, y, nrm);
+        yk1 = yk;
+        yk = y;
+        if (((__double_as_longlong(y) >> 52) & 0x7ff) > 1523) return 0.0;
+    }
+    return 1.0 / sqrt(nrm);
+}
+
+// the bottom-up solution of tri_last_dev stored in v and normalised (its
+// entries below 2^-500 of the largest flushed to 0): the start vector of one
+// inverse-iteration sweep for the Ritz coefficients, which it leaves as
+// accurate as three sweeps from all ones (measured against dense
+// eigenvectors).  One thread.
+__device__ void tri_bottom_up_dev(int n, const double *__restrict__ a, const double *__restrict__ b,
+                                  const double *__restrict__ rb, double e, double *__restrict__ v) {
+    v[n - 1] = 1.0;
+    for (int k = n - 1; k >= 1; --k) {
+        const double t = k + 1 < n ? b[k] * v[k + 1] : 0.0;
+        v[k - 1] = -fma(a[k] - e, v[k], t) * rb[k - 1];
+        if (((__double_as_longlong(v[k - 1]) >> 52) & 0x7ff) > 1523)
+            for (int i = k - 1; i < n; ++i) v[i] *= 0x1p-500;
+    }
+    double nrm = 0.0;
+    for (int i = 0; i < n; ++i) nrm = fma(v[i], v[i], nrm);
+    const double f = 1.0 / sqrt(nrm);
+    for (int i = 0; i < n; ++i) v[i] *= f;
+}
+
 // per-sector state of the convergence checks (device)
 struct LzState {
     DevBuf eprev, eval, msz, conv, coef, ws, cont, nnz;
@@ -1879,7 +1933,7 @@ struct LzState {
         QS3_TRY(msz.alloc((size_t)S * 4));
         QS3_TRY(conv.alloc((size_t)S * 4));
         QS3_TRY(coef.alloc((size_t)S * cap * 8));
-        QS3_TRY(ws.alloc((size_t)S * 5 * cap * 8));
+        QS3_TRY(ws.alloc((size_t)S * 7 * cap * 8));
         QS3_TRY(cont.alloc(4));
         QS3_TRY(nnz.alloc(8));
         // eprev = NaN (no previous Ritz value); everything else 0
@@ -1899,6 +1953,14 @@ struct LzState {
 // exact).  Converged: |e - e_prev| <= eps |e| and the Ritz residual
 // beta_{m-1} |c_{m-1}| <= res_tol max(|e|, 1).  A converged sector (or any at
 // n = nmax) stores its Ritz coefficients and leaves the active set.
+// With lz_smem(cap) bytes of dynamic shared memory the sector's alpha, beta,
+// the inverse-iteration workspace, the eigenvector, 1 / beta and beta^2 live
+// in shared memory (the dependent stores and loads then stay on the SM; the
+// vector is copied to coef at the end); else ws (7 cap per sector) holds the
+// workspaces and the rest is read and written in global memory.
+__host__ __device__ constexpr size_t lz_smem_need(int cap) { return (size_t)10 * cap * sizeof(double); }
+static size_t lz_smem(int cap) { return lz_smem_need(cap) <= 48 * 1024 ? lz_smem_need(cap) : 0; }
+
 __global__ void __launch_bounds__(32) k_lz_check(int n_arg, const int *__restrict__ dx, const double *__restrict__ alpha,
                                                  const double *__restrict__ beta, int cap, int *__restrict__ active,
                                                  const uint64_t *__restrict__ nnz_sec,
@@ -1907,12 +1969,34 @@ __global__ void __launch_bounds__(32) k_lz_check(int n_arg, const int *__restric
                                                  int *__restrict__ conv, double *__restrict__ coef,
                                                  double *__restrict__ ws, double eps, double res_tol, int min_iter,
                                                  int every, int nmax) {
+    extern __shared__ double lzs[];
     const int s = blockIdx.x, lane = threadIdx.x;
     const int n = dx ? *dx : n_arg;
     if (!active[s]) return;
     if (lane == 0) atomicAdd(nnz_acc, (unsigned long long)nnz_sec[s]);
     if (!((n >= min_iter && n % every == 0) || n >= nmax)) return;
+    unsigned dyn;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
     const double *a = alpha + (size_t)s * cap, *b = beta + (size_t)s * cap;
+    double *wsp = ws + (size_t)s * 7 * cap;          // inverse-iteration workspace (5 cap), 1 / b, b^2
+    double *rb = wsp + 5 * cap, *bb = wsp + 6 * cap;
+    double *const vg = coef + (size_t)s * cap;
+    double *v = vg;
+    const bool sm = dyn >= lz_smem_need(cap);
+    if (sm) {
+        double *sa = lzs, *sb = lzs + cap;
+        for (int i = lane; i < n; i += 32) {
+            sa[i] = a[i];
+            sb[i] = b[i];
+        }
+        __syncwarp();
+        a = sa;
+        b = sb;
+        wsp = lzs + 2 * cap;
+        v = lzs + 7 * cap;
+        rb = lzs + 8 * cap;
+        bb = lzs + 9 * cap;
+    }
     // the first vanishing beta ends the Krylov sequence
     int m = n;
     for (int k0 = 0; k0 < n; k0 += 32) {
@@ -1920,25 +2004,45 @@ __global__ void __launch_bounds__(32) k_lz_check(int n_arg, const int *__restric
         if (z) { m = k0 + __ffs(z); break; }
     }
     const bool brk = m < n || b[m - 1] == 0.0;
-    const double e = tri_lowest_warp(m, a, b, eprev[s]);
+    for (int i = 1 + lane; i < m; i += 32) bb[i] = b[i - 1] * b[i - 1];
+    __syncwarp();
+    const double ep = eprev[s];
+    const double e = tri_lowest_warp(m, a, b, bb, ep);
+    bool ok = brk || (isfinite(ep) && fabs(e - ep) <= eps * fabs(e));
+    // the Ritz residual beta_{m-1} |y_m| once the value is stable
+    const bool need_res = ok && !brk && res_tol > 0.0;
+    if (ok) {
+        for (int i = lane; i < m - 1; i += 32) rb[i] = 1.0 / b[i];
+        __syncwarp();
+    }
+    if (need_res) {
+        double ym = 0.0;
+        if (lane == 0) ym = tri_last_dev(m, a, b, rb, e);
+        ym = __shfl_sync(0xffffffffu, ym, 0);
+        ok = fabs(b[m - 1]) * ym <= res_tol * fmax(fabs(e), 1.0);
+    }
+    const bool done = ok || n >= nmax;
     if (lane == 0) {
-        const double ep = eprev[s];
-        bool ok = brk || (isfinite(ep) && fabs(e - ep) <= eps * fabs(e));
-        double *v = coef + (size_t)s * cap;
-        bool have_v = false;
-        if (ok && !brk && res_tol > 0.0) {
-            tri_vec_dev(m, a, b, e, v, ws + (size_t)s * 5 * cap);
-            have_v = true;
-            ok = fabs(b[m - 1] * v[m - 1]) <= res_tol * fmax(fabs(e), 1.0);
-        }
         eprev[s] = e;
         eval[s] = e;
         msz[s] = m;
-        if (ok || n >= nmax) {
-            if (!have_v) tri_vec_dev(m, a, b, e, v, ws + (size_t)s * 5 * cap);
+        if (done) {
+            // the Ritz coefficients of a sector that leaves the active set:
+            // converged, one inverse-iteration sweep from the bottom-up
+            // solution; stopped at n_max, three sweeps from all ones
+            if (ok) {
+                tri_bottom_up_dev(m, a, b, rb, e, v);
+                tri_vec_dev(m, a, b, e, v, wsp, true, 1);
+            } else {
+                tri_vec_dev(m, a, b, e, v, wsp);
+            }
             conv[s] = ok ? 1 : 0;
             active[s] = 0;
         }
+    }
+    if (sm && done) {
+        __syncwarp();
+        for (int i = lane; i < m; i += 32) vg[i] = v[i];
     }
 }
 
@@ -2012,7 +2116,7 @@ static int lanczos_loop_graph(EN &E, LzState &K, Basis &B, const qs3_solve_opts 
         E.st = cs;
         int r = E.step_body_dev();
         if (r == QS3_OK) {
-            k_lz_check<<<B.S, 32, 0, cs>>>(0, E.xdev.template as<int>(), E.alpha.template as<double>(),
+            k_lz_check<<<B.S, 32, lz_smem(E.cap), cs>>>(0, E.xdev.template as<int>(), E.alpha.template as<double>(),
                                            E.beta.template as<double>(), E.cap, E.act(), nnz_sec,
                                            K.nnz.as<unsigned long long>(), K.eprev.as<double>(), K.eval.as<double>(),
                                            K.msz.as<int>(), K.conv.as<int>(), K.coef.as<double>(), K.ws.as<double>(),
@@ -2072,7 +2176,7 @@ static int lanczos_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT
     const uint64_t nz0 = hs.nnz;
     int cont = 0;
     auto check = [&](int n) -> int {
-        k_lz_check<<<S, 32, 0, st>>>(n, nullptr, E.alpha.template as<double>(), E.beta.template as<double>(), E.cap,
+        k_lz_check<<<S, 32, lz_smem(E.cap), st>>>(n, nullptr, E.alpha.template as<double>(), E.beta.template as<double>(), E.cap,
                                      E.act(), dnnz.as<uint64_t>(), K.nnz.as<unsigned long long>(),
                                      K.eprev.as<double>(), K.eval.as<double>(), K.msz.as<int>(), K.conv.as<int>(),
                                      K.coef.as<double>(), K.ws.as<double>(), o.eps, o.res_tol, o.min_iter, every,
