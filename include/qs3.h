@@ -207,9 +207,10 @@ typedef struct {
     int32_t min_iter;     /* minitr: Lanczos steps before the first check */
     int32_t check_every;  /* itrint: steps between convergence checks */
     double eps;           /* lnc_ene_conv: relative Ritz-value change for convergence */
-    int32_t precision;    /* QS3_F64: IEEE binary64 throughout (complex double on k-sector bases): Lanczos
-                             vectors stored as binary64, H Phi, dot products and updates on binary64
-                             FMAs (see strict64);
+    int32_t precision;    /* QS3_F64: IEEE binary64 (complex double on k-sector bases): Lanczos vectors
+                             stored as binary64, H Phi and updates on binary64 FMAs, dot products
+                             summed exactly on 53-bit fixed-point images of the operands (see
+                             qs3_gs_dots and strict64);
                              QS3_F32: fp32 vectors and H Phi with fp32 row sums, fp64 alpha/beta and
                              dot products (double-float sums of exact fp32 products), then a QS3_F64
                              refinement from the fp32 Ritz vectors;
@@ -225,10 +226,12 @@ typedef struct {
     int32_t hphi_ieee;    /* precision QS3_C128DF on k-sector bases: 0 applies H to the double-float copy
                              of each Lanczos vector in double-float arithmetic; 1 uses the IEEE
                              complex128 H Phi.  Residuals are always IEEE binary64. */
-    int32_t strict64;     /* QS3_F64 engine: 0 lets the Gram-Schmidt update whose coefficients are all
-                             below 2^-36 |w| in sum form its correction in fp32 from the stored values'
-                             high words (error below 2^-55 |w|, less than binary64 rounding of w);
-                             1 keeps every update on binary64 FMAs */
+    int32_t strict64;     /* QS3_F64 engine: 0 computes the dot products exactly on fixed-point
+                             images (qs3_gs_dots mode 0) and lets the Gram-Schmidt update whose m
+                             coefficients are below 2^-40 |w| in sum (times 256 / m for m > 256)
+                             form its correction in fp32 from the images' top digits (error below
+                             2^-55.5 |w|, less than binary64 rounding of w); 1 keeps the dot
+                             products and every update on binary64 FMAs */
 } qs3_solve_opts;
 
 typedef struct {
@@ -246,8 +249,10 @@ typedef struct {
     uint64_t gs_dot_bytes;    /* their algorithmic bytes: stored basis vectors and w read, active sectors */
     int32_t gs_dot_calls;     /* those launches */
     int32_t reserved;
-    uint64_t gs_dot_fma;      /* binary64 engine: fused multiply-adds of those launches (4 per complex
-                                 element and stored vector, 1 per real one); 0 for the other engines */
+    uint64_t gs_dot_fma;      /* binary64 engine: the real multiply-adds those launches stand for (4 per
+                                 complex element and stored vector, 1 per real one; binary64 FMAs
+                                 under strict64, integer digit products otherwise); 0 for the other
+                                 engines */
 } qs3_solve_info;
 
 /* Conventional Lanczos with full reorthogonalisation (Alg. 10 lines 2-12)
