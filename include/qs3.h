@@ -59,8 +59,15 @@ enum {
  * double-float form, four floats (re.hi, re.lo, im.hi, im.lo) with re =
  * re.hi + re.lo (qs3_split_df makes it from complex128); psi is complex128;
  * the product runs in double-float arithmetic (error-free fp32 products and
- * two-sums, about 48 significant bits), k-sector bases only. */
-typedef enum { QS3_F32 = 0, QS3_F64 = 1, QS3_C64 = 2, QS3_C128 = 3, QS3_C128DF = 4 } qs3_dtype;
+ * two-sums, about 48 significant bits), k-sector bases only.
+ * QS3_C128X: phi and psi complex128; the product of the binary64 engine on
+ * the integer units (k-sector bases with the representative table and one
+ * hop amplitude on every bond): each hop's phase x phi formed exactly on
+ * fixed-point images (phi rounded to 2^-53 of the largest magnitude among
+ * its 128-row warp group, the phases to 2^-53), summed exactly per row in
+ * 128-bit integers and rounded to binary64 once; terms whose target
+ * stabiliser differs from the row's, and the diagonal, in binary64. */
+typedef enum { QS3_F32 = 0, QS3_F64 = 1, QS3_C64 = 2, QS3_C128 = 3, QS3_C128DF = 4, QS3_C128X = 5 } qs3_dtype;
 
 /* S^alpha_q operators, numbered as the paper's input parameter spsmsz. */
 typedef enum { QS3_OP_SPLUS = 1, QS3_OP_SMINUS = 2, QS3_OP_SZ = 3 } qs3_sq_op;
@@ -170,7 +177,9 @@ int qs3_basis_store_terms(qs3_basis_t b, int32_t mode, uint64_t *bytes);
  * sectors, within a few 2^-48 relative of the exact product per term.
  * phi and psi are device vectors of the basis' total dimension and must not
  * alias.  F32/C64 use fp32 matrix elements and fp32 row accumulation.
- * Errors: STATE (real dtype on a k-sector basis, C128DF on a U(1)-only one). */
+ * C128X allocates device scratch of twice the vector size per call.
+ * Errors: STATE (real dtype on a k-sector basis, C128DF on a U(1)-only one,
+ * C128X without the representative table or with bond-dependent J^xy). */
 int qs3_hphi(qs3_basis_t b, qs3_dtype dtype, const void *phi, void *psi, void *stream);
 
 /* Dot products of the Gram-Schmidt pass of Alg. 10 (the reorthogonalisation

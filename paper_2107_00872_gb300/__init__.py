@@ -10,7 +10,7 @@ import ctypes
 import numpy as np
 
 from . import _abi
-from ._abi import QS3_C64, QS3_C128, QS3_C128DF, QS3_F32, QS3_F64, QS3Error, check, load
+from ._abi import QS3_C64, QS3_C128, QS3_C128DF, QS3_C128X, QS3_F32, QS3_F64, QS3Error, check, load
 
 __all__ = ["Basis", "QS3Error", "load", "hphi", "dtype_code", "SolveOpts", "split_df", "probe_peaks",
            "inject_alloc_failure"]
@@ -254,11 +254,18 @@ class Basis:
 
     # ---------------------------------------------------------- operations
 
-    def hphi(self, phi, psi=None, stream=None):
-        """psi = H phi on the device (psi allocated like phi when omitted)."""
+    def hphi(self, phi, psi=None, stream=None, integer: bool = False):
+        """psi = H phi on the device (psi allocated like phi when omitted).
+        integer: complex128 only, the binary64 engine's product on the integer
+        units (QS3_C128X)."""
         if psi is None:
             psi = _torch().empty_like(phi)
-        check(load().qs3_hphi(self._h, dtype_code(phi), _dev(phi, self.total_dim, "phi"),
+        dt = dtype_code(phi)
+        if integer:
+            if dt != QS3_C128:
+                raise TypeError("the integer product takes complex128 vectors")
+            dt = QS3_C128X
+        check(load().qs3_hphi(self._h, dt, _dev(phi, self.total_dim, "phi"),
                               _dev(psi, self.total_dim, "psi"), _stream(stream)), "qs3_hphi")
         return psi
 

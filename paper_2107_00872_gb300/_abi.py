@@ -11,7 +11,7 @@ I32 = ctypes.c_int32
 U64 = ctypes.c_uint64
 F64 = ctypes.c_double
 
-QS3_F32, QS3_F64, QS3_C64, QS3_C128, QS3_C128DF = 0, 1, 2, 3, 4
+QS3_F32, QS3_F64, QS3_C64, QS3_C128, QS3_C128DF, QS3_C128X = 0, 1, 2, 3, 4, 5
 STATUS = {0: "QS3_OK", -1: "QS3_ERR_INVALID_ARG", -2: "QS3_ERR_OVERFLOW", -3: "QS3_ERR_SYMMETRY",
           -4: "QS3_ERR_OOM", -5: "QS3_ERR_CUDA", -6: "QS3_ERR_NOT_CONVERGED", -7: "QS3_ERR_TIMEOUT",
           -8: "QS3_ERR_STATE"}

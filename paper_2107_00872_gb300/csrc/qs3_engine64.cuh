@@ -33,6 +33,8 @@
 // The solve option strict64 keeps the dots and that update on binary64 FMAs.
 #pragma once
 
+#include "qs3_fixed.cuh"
+
 namespace qs3 {
 
 template <typename VT> struct PlS { using T = uint32_t; };     // real: one word per plane
@@ -145,42 +147,6 @@ __global__ void __launch_bounds__(NTHREADS, NV == 1 ? 3 : NV == 2 ? 2 : 1)
 // Bounds: a thread's folded sum (8 top-digit products of <= 2^54.1 and 16
 // middle ones of <= 2^52.1 for complex data) stays below 2^57.2, a warp's
 // below 2^62.2.
-constexpr int XT = 512;                 // threads per chunk of k_dotx
-constexpr int XR = BROWS / XT;          // rows per thread
-constexpr int XW = XT / 32;             // warps per chunk
-static_assert(XR * XT == BROWS, "k_dotx covers a chunk");
-
-__device__ __forceinline__ int fx_exp(uint32_t h) { return (int)((h >> 20) & 0x7ffu); }
-
-// the binary64 with high word h and low word l on the grid of em (em >= its
-// biased exponent, em >= 54): balanced digits (p1, p0) of round(v 2^(1075-em)).
-// A zero or subnormal v (exponent field 0) is at least 2^54 grid steps below
-// em and rounds to 0.
-__device__ __forceinline__ void fx_digits(uint32_t h, uint32_t l, int em, int &p1, int &p0) {
-    const uint32_t sh = min((uint32_t)(em - fx_exp(h)), 63u);
-    // 2m, m = 2^52 + the 52 stored significand bits: high word mh2, low l2
-    const uint32_t mh2 = (__funnelshift_l(l, h, 1) & 0x1fffffu) | 0x200000u;
-    const uint32_t l2 = l << 1;
-    // t = floor(2m / 2^sh) = floor(m / 2^(sh-1)): words thi, tlo
-    const uint32_t f = __funnelshift_rc(l2, mh2, sh);                  // (2m) >> min(sh, 32), low word
-    const uint32_t thi = __funnelshift_rc(mh2, 0u, sh);                // its high word (0 for sh >= 32)
-    const uint32_t tlo = f >> (max(sh, 32u) - 32u);                    // the rest of the shift (thi = 0 then)
-    // Q = round(m / 2^sh) = floor((t + 1) / 2); Q1 = floor((Q + 2^25) / 2^26),
-    // Q0 = Q - Q1 2^26 (the low 26 bits of Q, sign-extended)
-    const uint64_t t = ((uint64_t)thi << 32) | tlo;
-    const int q1 = (int)((t + 0x4000001ull) >> 27);
-    const int q0 = ((int)(((tlo + 1u) >> 1) << 6)) >> 6;
-    const int sg = ((int)h >> 31) | 1;
-    p1 = q1 * sg;
-    p0 = q0 * sg;
-}
-
-// a b + c with the 64-bit product of two 32-bit integers (one mad.wide.s32)
-__device__ __forceinline__ long long mad_w(int a, int b, long long c) {
-    long long d;
-    asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
-    return d;
-}
 // the sum over the warp of t, |t| < 2^58: three limbs of at most 26 bits,
 // whose 32-lane sums fit in int32, each summed by one redux.sync
 __device__ __forceinline__ long long warp_sum_ll(long long t) {
@@ -202,40 +168,6 @@ __device__ __forceinline__ __int128 warp_sum_i128(__int128 v) {
     }
     return v;
 }
-// a 2^k rounded to the nearest binary64 (ties to even) in integer operations
-// (the fp64 pipe issues one warp instruction per ~70 ALU ones, even for a
-// single active lane); only a result below the normal range takes fp64 ops
-__device__ __forceinline__ double i128_ldexp(__int128 a, int k) {
-    if (a == 0) return 0.0;
-    const unsigned long long sgn = a < 0 ? 0x8000000000000000ull : 0ull;
-    const unsigned __int128 u = a < 0 ? (unsigned __int128)(-a) : (unsigned __int128)a;
-    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
-    const int n = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);     // bit length
-    unsigned long long mant;
-    int e = n - 1 + k;                                                               // exponent of the top bit
-    if (n <= 53) {
-        mant = lo << (53 - n);
-    } else {
-        const int sh = n - 53;
-        mant = (unsigned long long)(u >> sh);
-        const unsigned __int128 rem = u & (((unsigned __int128)1 << sh) - 1);
-        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-        if (rem > half || (rem == half && (mant & 1ull))) {
-            ++mant;
-            if (mant == (1ull << 53)) {
-                mant >>= 1;
-                ++e;
-            }
-        }
-    }
-    if (e > 1023) return __longlong_as_double((long long)(sgn | 0x7ff0000000000000ull));
-    if (e < -1022) {
-        const double r = ldexp((double)mant, e - 52);
-        return sgn ? -r : r;
-    }
-    return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) | (mant & 0xfffffffffffffull)));
-}
-
 __device__ __forceinline__ void words(uint2 h, uint2 l, uint32_t (&hw)[2], uint32_t (&lw)[2]) {
     hw[0] = h.x; hw[1] = h.y; lw[0] = l.x; lw[1] = l.y;
 }
@@ -831,7 +763,7 @@ struct Engine64 {
     HphiStats *stats;
     int cap = 0, nscr = 0;
     uint64_t D = 0;
-    DevBuf V, DG, GE, wbuf, hinb, part, partx, h1, h2, alpha, beta, nrm, nrm1, inv, active;
+    DevBuf V, DG, GE, wbuf, hinb, part, partx, h1, h2, alpha, beta, nrm, nrm1, inv, active, erefb;
     std::vector<int> h_active;
     double brk = 1e-12;
     int strict = 0;                        // 1: every update on binary64 FMAs
@@ -878,6 +810,10 @@ struct Engine64 {
         QS3_TRY(V.alloc((uint64_t)(cap + nscr) * D * sizeof(VT)));
         QS3_TRY(DG.alloc((uint64_t)(cap + nscr) * D * sizeof(VT)));
         QS3_TRY(GE.alloc((uint64_t)(cap + nscr) * std::max(B.nchunks, 1) * XW * sizeof(int)));
+        // the integer H Phi's bound on the group exponents of psi_x: a normalised
+        // vector has none above 1023 (|psi_i| <= 1)
+        const int eref = 1023 + 8;
+        QS3_TRY(erefb.upload(&eref, sizeof(int)));
         QS3_TRY(wbuf.alloc(std::max<uint64_t>(D, 1) * sizeof(VT)));
         QS3_TRY(hinb.alloc(std::max<uint64_t>(D, 1) * sizeof(VT)));
         QS3_TRY(part.alloc((uint64_t)std::max(B.nchunks, 1) * cap * sizeof(double2)));
@@ -1024,6 +960,15 @@ struct Engine64 {
         for (int s = 0; s < B.S; ++s)
             if (h_active[s]) stats->nnz += B.nnz_sec[s];
     }
+    // w = H psi_x: on the integer units from the digit image of slot x (slot
+    // *dx in graph mode) when the basis allows it and strict64 is off, else
+    // the binary64 FMA kernels
+    int hphi_apply(int x, const int *dx) {
+        if (!strict && IsC<VT>::v && hphi_x_ok(B))
+            return dx ? hphi_x_launch(B, hin(0), DG.p, GE.as<int>(), erefb.as<int>(), dx, wv(), st, act())
+                      : hphi_x_launch(B, hin(0), dg(x), ge(x), erefb.as<int>(), nullptr, wv(), st, act());
+        return hphi_launch(B, dtype(), hin(x), wv(), st, act());
+    }
     // the Gram-Schmidt dot pass against psi_0 .. psi_x, timed with events
     int gs_dots(int x) {
         std::pair<cudaEvent_t, cudaEvent_t> ev;
@@ -1046,7 +991,7 @@ struct Engine64 {
         const int *dx = xdev.as<int>();
         VT *w = wv();
         double2 *hh1 = h1.as<double2>(), *n1 = nrm1.as<double2>();
-        QS3_TRY(hphi_launch(B, dtype(), hin(0), w, st, act()));
+        QS3_TRY(hphi_apply(0, dx));
         QS3_TRY(dot_launch(2, 0, 2, dx, 1));
         QS3_TRY(dot_reduce(2, hh1, cap, dx, 1, 2));
         k_upd64<VT><<<grid(), XT, 2 * (sizeof(double2) + sizeof(float2)), st>>>(
@@ -1120,7 +1065,7 @@ struct Engine64 {
         std::pair<cudaEvent_t, cudaEvent_t> ev;
         QS3_TRY(stats->pair(ev));
         QS3_CUDA(cudaEventRecord(ev.first, st));
-        QS3_TRY(hphi_launch(B, dtype(), hin(x), w, st, act()));
+        QS3_TRY(hphi_apply(x, nullptr));
         QS3_CUDA(cudaEventRecord(ev.second, st));
         stats->pend.push_back(ev);
         count_hphi();

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <atomic>
 
+#include "qs3_fixed.cuh"
 #include "qs3_hphi_common.cuh"
 
 namespace qs3 {
@@ -236,6 +237,156 @@ __global__ void __launch_bounds__(NTHREADS, (KS && TB && sizeof(VT) == 16) ? 4 :
         if (KS && uni) madd_r(acc, juni, acch);
         madd_r(acc, e + (R)0.5 * dd, x0);
         store(psi + sv.off + row, acc);
+    }
+}
+
+// H Phi of the binary64 engine on the integer units: k-sectors with the
+// representative table and one hop amplitude J/2 on every bond.  phi comes
+// twice: as binary64 (the diagonal term) and as its digit-store image (dg:
+// the top-digit plane then the low-digit plane, D int2 (re, im) each; ge:
+// the grid exponent of every chunk's warp groups).  Each hop's product
+// phase x phi is formed exactly on the images (the phases on the grid 2^-52,
+// staged per sector as digits) with mad.wide.s32, folded at weight 2^52
+// (rounded to nearest) and added to a 128-bit row sum on the grid
+// 2^(eref - 1139): 64 bits below the coarsest grid of phi (eref >= every
+// group exponent; a normalised vector has eref <= 1023 + 8), so a term
+// loses nothing above 2^-108 of it.  Terms whose target stabiliser differs
+// from the row's (norm ratio != 1, rare) are summed in binary64 as in
+// k_hphi.  The row sum is rounded to binary64 once, then psi = J/2 sum +
+// diag phi in binary64.  Graph mode (dx): dg and ge are the store's, slot *dx.
+__device__ __forceinline__ void add_shifted(__int128 &acc, long long t, int sh) {
+    if (sh >= 0) {
+        acc += (__int128)t << min(sh, 70);
+    } else if (sh > -63) {
+        acc += (t + (1ll << (-sh - 1))) >> (-sh);
+    }
+}
+
+template <int ND>
+__global__ void __launch_bounds__(NTHREADS, 3) k_hphi_x(LatView L, const SecView *__restrict__ secs,
+                                                       const int *__restrict__ tile0, int S, int ntiles,
+                                                       const double2 *__restrict__ phi, const int2 *__restrict__ dg,
+                                                       const int *__restrict__ ge, const int *__restrict__ chunk0,
+                                                       int nchunks, uint64_t D, const int *__restrict__ eref_p,
+                                                       const int *__restrict__ dx, double2 *__restrict__ psi,
+                                                       const int *__restrict__ active) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemLayout sm = carve(L, smem);
+    stage_tables(L, sm.sC, sm.sxyz);
+    double *snorm = (double *)sm.snorm;
+    if (threadIdx.x < 9) {
+        snorm[threadIdx.x] = sqrt((double)threadIdx.x);
+        snorm[9 + threadIdx.x] = threadIdx.x ? 1.0 / sqrt((double)threadIdx.x) : 0.0;
+    }
+    if (dx) {
+        dg += (uint64_t)(*dx) * 2 * D;
+        ge += (uint64_t)(*dx) * nchunks * XW;
+    }
+    const int eref = *eref_p;
+    const double juni = L.jh_uniform;
+    __syncthreads();
+    int4 *pd = (int4 *)sm.sph;          // the current sector's phases: (re.P1, re.P0, im.P1, im.P0) on 2^-52
+    int cur = -1, c0s = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int s = (S == 1) ? 0 : sector_of_tile(tile0, S, t);
+        if (active && !active[s]) continue;
+        const SecView sv = secs[s];
+        if (s != cur) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < L.N; i += blockDim.x) {
+                const double2 p = sv.ph64[i];
+                int a1, a0, b1, b0;
+                fx_digits((uint32_t)__double2hiint(p.x), (uint32_t)__double2loint(p.x), 1023, a1, a0);
+                fx_digits((uint32_t)__double2hiint(p.y), (uint32_t)__double2loint(p.y), 1023, b1, b0);
+                pd[i] = make_int4(a1, a0, b1, b0);
+            }
+            c0s = chunk0[s];
+            __syncthreads();
+            cur = s;
+        }
+        const uint64_t row = (uint64_t)(t - sv.tile0) * TILE + threadIdx.x;
+        if (row >= sv.dim) continue;
+        const uint64_t rank = __ldg(sv.sigma + row);
+        int c[ND];
+        unrank(rank, sm.sC, L.np1, c);
+        const double2 x0 = phi[sv.off + row];
+        const int st_row = sv.stab[row];
+        const double rs = snorm[9 + st_row];
+        double e = L.c0, dd = 0.0;
+        __int128 ar = 0, ai = 0;
+        double2 acc64 = make_double2(0.0, 0.0);
+#pragma unroll 1
+        for (int m = 0; m < ND; ++m) {
+            const int i = pick(c, m);
+            e += diag_u<double>(L, i);
+            const int e0 = __ldg(L.adj_ptr + i), e1 = __ldg(L.adj_ptr + i + 1);
+            // a hop to c_{m-1} < j < c_{m+1} keeps its place in the sorted list
+            const int lo = m > 0 ? pick(c, m > 0 ? m - 1 : 0) : -1;
+            const int hi = m < ND - 1 ? pick(c, m < ND - 1 ? m + 1 : m) : L.np1;
+            const uint64_t base = rank - sm.sC[(m + 1) * L.np1 + i];
+            for (int q = e0; q < e1; ++q) {
+                const int j = __ldg(L.adj_nbr + q);
+                const bool inpl = j > lo && j < hi;
+                if (!inpl) {
+                    bool occ = false;
+#pragma unroll
+                    for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
+                    if (occ) {
+                        dd += diag_jz<double>(L, q);
+                        continue;
+                    }
+                }
+                uint64_t r2;
+                if (inpl) {
+                    r2 = base + sm.sC[(m + 1) * L.np1 + j];
+                } else {
+                    int tt[ND];
+#pragma unroll
+                    for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
+                    sort_net(tt);
+                    r2 = rank_of(tt, sm.sC, L.np1);
+                }
+                const uint32_t ee = __ldg(L.orb + r2);
+                if ((ee >> 12) >= L.n_orb) continue;     // never for a complete table
+                const int32_t row2 = __ldg(sv.t2 + (ee >> 12));
+                if (row2 < 0) continue;
+                const uint32_t idx = (uint32_t)row2;
+                const int u = (int)(ee & 4095u);
+                const int st = __ldg(sv.stab + idx);
+                if (st == st_row) {
+                    const uint64_t gi = sv.off + idx;
+                    const int2 f1 = dg[gi], f0 = dg[D + gi];
+                    const int em = __ldg(ge + (uint64_t)(c0s + (int)(idx >> 11)) * XW + dg_group((int)(idx & 2047u)));
+                    const int4 p = pd[u];
+                    // (pr + i pi)(fr + i fi) = (pr fr - pi fi) + i (pr fi + pi fr)
+                    const long long hr = mad_w(p.x, f1.x, 0), hn = mad_w(p.z, f1.y, 0);
+                    const long long mr = mad_w(p.x, f0.x, mad_w(p.y, f1.x, 0));
+                    const long long mn = mad_w(p.z, f0.y, mad_w(p.w, f1.y, 0));
+                    const long long hi2 = mad_w(p.x, f1.y, mad_w(p.z, f1.x, 0));
+                    const long long mi = mad_w(p.x, f0.y, mad_w(p.y, f1.y, mad_w(p.z, f0.x, mad_w(p.w, f1.x, 0))));
+                    // units 2^(em - 1075) after the fold; the row sum's units 2^(eref - 1139)
+                    const long long tr = (hr - hn) + ((mr - mn + (1ll << 25)) >> 26);
+                    const long long ti = hi2 + ((mi + (1ll << 25)) >> 26);
+                    const int sh = em - eref + 64;
+                    add_shifted(ar, tr, sh);
+                    add_shifted(ai, ti, sh);
+                } else {
+                    double2 p = sv.ph64[u];
+                    const double f = snorm[st] * rs;
+                    p.x *= f;
+                    p.y *= f;
+                    acc_add(acc64, p, phi[sv.off + idx]);
+                }
+            }
+        }
+        double2 acch;
+        acch.x = i128_ldexp(ar, eref - 1139) + acc64.x;
+        acch.y = i128_ldexp(ai, eref - 1139) + acc64.y;
+        const double ed = e + 0.5 * dd;
+        double2 out;
+        out.x = fma(ed, x0.x, juni * acch.x);
+        out.y = fma(ed, x0.y, juni * acch.y);
+        psi[sv.off + row] = out;
     }
 }
 
@@ -471,10 +622,63 @@ static int hphi_vt(Basis &B, const void *phi, void *psi, cudaStream_t st, const 
     }
 }
 
+template <int ND>
+static int hphix_nd(Basis &B, const double2 *phi, const int2 *dg, const int *ge, const int *eref, const int *dx,
+                    double2 *psi, cudaStream_t st, const int *active) {
+    static std::atomic<unsigned long long> cache{0};
+    int grid = 1, occ = 1;
+    QS3_TRY(launch_rows(k_hphi_x<ND>, B, B.smem_bytes, cache, &grid, &occ));
+    if (B.ntiles == 0) return QS3_OK;
+    auto launch = [&](int g) {
+        k_hphi_x<ND><<<g, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S,
+                                                         B.ntiles, phi, dg, ge, B.d_chunk0.as<int>(), B.nchunks,
+                                                         B.total, eref, dx, psi, active);
+    };
+    int &bps = B.tune_hphix;
+    if (bps == 0) {
+        cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+        QS3_CUDA(cudaStreamIsCapturing(st, &cst));
+        if (cst == cudaStreamCaptureStatusNone && !dx) {
+            int b = occ;
+            QS3_TRY(tune_blocks(B, occ, st, b, launch));
+            bps = b;
+        }
+    }
+    if (bps > 0) grid = std::max(1, std::min(B.ntiles, std::min(bps, occ) * num_sms()));
+    launch(grid);
+    QS3_LAUNCHED();
+    return QS3_OK;
+}
+
+bool hphi_x_ok(const Basis &B) {
+    return B.has_k && B.lv.orb && B.lv.jh_uniform != 0.0 && B.nd > 0 && !B.stored_terms && B.total > 0;
+}
+
+int hphi_x_launch(Basis &B, const void *phi, const void *dg, const int *ge, const int *eref, const int *dx, void *psi,
+                  cudaStream_t st, const int *active) {
+    if (!hphi_x_ok(B)) return set_err(QS3_ERR_STATE, "the integer H Phi needs a k-sector basis with the "
+                                                     "representative table and one hop amplitude");
+    const double2 *p = (const double2 *)phi;
+    const int2 *g = (const int2 *)dg;
+    double2 *o = (double2 *)psi;
+    switch (B.nd) {
+        case 1: return hphix_nd<1>(B, p, g, ge, eref, dx, o, st, active);
+        case 2: return hphix_nd<2>(B, p, g, ge, eref, dx, o, st, active);
+        case 3: return hphix_nd<3>(B, p, g, ge, eref, dx, o, st, active);
+        case 4: return hphix_nd<4>(B, p, g, ge, eref, dx, o, st, active);
+        case 5: return hphix_nd<5>(B, p, g, ge, eref, dx, o, st, active);
+        case 6: return hphix_nd<6>(B, p, g, ge, eref, dx, o, st, active);
+        case 7: return hphix_nd<7>(B, p, g, ge, eref, dx, o, st, active);
+        case 8: return hphix_nd<8>(B, p, g, ge, eref, dx, o, st, active);
+        default: return set_err(QS3_ERR_INVALID_ARG, "n_down %d", B.nd);
+    }
+}
+
 int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t st, const int *active) {
     if (!phi || !psi) return set_err(QS3_ERR_INVALID_ARG, "NULL vector");
     if (phi == psi) return set_err(QS3_ERR_INVALID_ARG, "phi and psi alias");
     if (dt == QS3_C128DF) return hphi_df_launch(B, phi, nullptr, 0, psi, st, active);
+    if (dt == QS3_C128X) return hphi_x_binary64(B, phi, psi, st);
     if (B.has_k && (dt == QS3_F32 || dt == QS3_F64))
         return set_err(QS3_ERR_STATE, "k-sector bases need complex vectors (C64/C128)");
     if (B.total == 0) return QS3_OK;

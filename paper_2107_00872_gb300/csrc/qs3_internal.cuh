@@ -165,6 +165,7 @@ struct Basis {
     // SM per vector dtype (the persistent grid, i.e. rows in flight per SM),
     // and basis vectors per pass of the double-float dot products
     int tune_hphi[5] = {0, 0, 0, 0, 0};     // indexed by qs3_dtype
+    int tune_hphix = 0;                     // the same for the binary64 engine's integer H Phi
     int tune_nv = 0;
     int tune_nv64 = 0;                      // the same for the binary64 dot products (IEEE engine)
     bool narrow_ranks = false;              // U(1) with C(N, N_down) < 2^32: 32-bit rank kernels apply
@@ -522,6 +523,15 @@ int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t
 int hphi_df_launch(Basis &B, const void *phi, const int *dx, uint64_t ld, void *psi, cudaStream_t st,
                    const int *active = nullptr, bool out_df = false);
 int count_nnz(Basis &B, uint64_t *nnz);
+// the binary64 engine's H Phi on the integer units (qs3_hphi.cu, k_hphi_x): phi as
+// binary64 and as its digit-store image (dg, ge: slot *dx of the store when dx is
+// given), eref (device) an upper bound of its group exponents
+bool hphi_x_ok(const Basis &B);
+int hphi_x_launch(Basis &B, const void *phi, const void *dg, const int *ge, const int *eref, const int *dx, void *psi,
+                  cudaStream_t st, const int *active = nullptr);
+// qs3_hphi with QS3_C128X: phi's digit image in scratch, then hphi_x_launch
+// (qs3_solver.cu, where the digit kernels live); synchronous on st
+int hphi_x_binary64(Basis &B, const void *phi, void *psi, cudaStream_t st);
 // representative table: build (QS3_OK, or an error when it cannot be built) / release
 int build_rep_table(Basis &B, size_t max_bytes);
 // stored-term H Phi of k-sector bases: build (QS3_OK or an error) / release / apply
