@@ -235,7 +235,7 @@ def run_ours(args, rank, world):
     # algorithmic bytes of one full launch: diagonal read, one gather per term,
     # psi write, sigma row rank, one sigma probe per term
     B_alg = frac_work * (D * s_phi + (nnz_h - D) * s_phi + D * s_phi + D * 8 + (nnz_h - D) * 8)
-    hphi = {"kernel": "k_hphi<complex128, representative table>", "full_launch_ms": round(1e3 * t_launch / frac_work, 4),
+    hphi = {"kernel": "k_hphi_x (complex128, products on the integer units, representative table)", "full_launch_ms": round(1e3 * t_launch / frac_work, 4),
             "avg_launch_ms": round(1e3 * t_launch, 4), "launch_gnnz_s": round(per_launch_nnz / t_launch / 1e9, 2),
             "alg_gbs": round(B_alg / t_launch / 1e9, 1), "hbm_frac_alg": round(B_alg / t_launch / 1e9 / hbm_peak, 4),
             "share_of_step": round(hphi_s / t_local, 3)}

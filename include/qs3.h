@@ -217,9 +217,10 @@ typedef struct {
     int32_t check_every;  /* itrint: steps between convergence checks */
     double eps;           /* lnc_ene_conv: relative Ritz-value change for convergence */
     int32_t precision;    /* QS3_F64: IEEE binary64 (complex double on k-sector bases): Lanczos vectors
-                             stored as binary64, H Phi and updates on binary64 FMAs, dot products
-                             summed exactly on 53-bit fixed-point images of the operands (see
-                             qs3_gs_dots and strict64);
+                             stored as binary64, updates on binary64 FMAs, dot products and (k-sector
+                             bases with the representative table and one hop amplitude) the H Phi
+                             products summed exactly on 53-bit fixed-point images of the operands
+                             (see qs3_gs_dots, QS3_C128X and strict64);
                              QS3_F32: fp32 vectors and H Phi with fp32 row sums, fp64 alpha/beta and
                              dot products (double-float sums of exact fp32 products), then a QS3_F64
                              refinement from the fp32 Ritz vectors;
@@ -235,12 +236,13 @@ typedef struct {
     int32_t hphi_ieee;    /* precision QS3_C128DF on k-sector bases: 0 applies H to the double-float copy
                              of each Lanczos vector in double-float arithmetic; 1 uses the IEEE
                              complex128 H Phi.  Residuals are always IEEE binary64. */
-    int32_t strict64;     /* QS3_F64 engine: 0 computes the dot products exactly on fixed-point
-                             images (qs3_gs_dots mode 0) and lets the Gram-Schmidt update whose m
+    int32_t strict64;     /* QS3_F64 engine: 0 computes the dot products (qs3_gs_dots mode 0) and the
+                             H Phi products (QS3_C128X) exactly on fixed-point images and lets the
+                             Gram-Schmidt update whose m
                              coefficients are below 2^-40 |w| in sum (times 256 / m for m > 256)
                              form its correction in fp32 from the images' top digits (error below
-                             2^-55.5 |w|, less than binary64 rounding of w); 1 keeps the dot
-                             products and every update on binary64 FMAs */
+                             2^-55.5 |w|, less than binary64 rounding of w); 1 keeps H Phi, the
+                             dot products and every update on binary64 FMAs */
 } qs3_solve_opts;
 
 typedef struct {
