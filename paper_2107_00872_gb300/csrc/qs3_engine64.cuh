@@ -367,14 +367,80 @@ __global__ void __launch_bounds__(XT, 1)
     }
 }
 
-// out[s * ldo + j] = the sector's dot product j from the k_dotx partials of
-// all its chunks and warps: aligned to the coarsest grid among them (rounded
-// to nearest), summed exactly in 128 bits, rounded to binary64 once.  One
-// warp per coefficient (graph mode: the range of graph_range, written from
-// out + j0).  A warp partial s at exponent sum k is worth s 2^(k - 2098).
-__global__ void k_reducex(const long long *__restrict__ part, int m, const int *__restrict__ chunk0,
-                          const int *__restrict__ active, double2 *__restrict__ out, int ldo,
-                          const int *__restrict__ dx, int ring, int cx) {
+// The sector sums of the k_dotx partials, exactly, in two levels so that a
+// sector of many chunks is reduced by many warps: k_reducex1 takes slices of
+// RSL (chunk, warp) partials of one sector, aligns them to the coarsest grid
+// in the slice (rounded to nearest) and sums them in 128 bits; k_reducex2
+// aligns the slice sums of a sector the same way, sums them and rounds to
+// binary64 once.  A warp partial s at exponent sum k is worth s 2^(k - 2098).
+constexpr int RSL = 4096;
+
+// first slice of every sector (S + 1 entries)
+static inline std::vector<int> reduce_slices(const Basis &B) {
+    std::vector<int> s0(B.S + 1, 0);
+    for (int s = 0; s < B.S; ++s) {
+        const int parts = (B.chunk0[s + 1] - B.chunk0[s]) * XW;
+        s0[s + 1] = s0[s] + (parts + RSL - 1) / RSL;
+    }
+    return s0;
+}
+
+__device__ __forceinline__ __int128 align_round(__int128 v, int d) {
+    if (d <= 0) return v;
+    if (d > 120) return 0;
+    return (v + ((__int128)1 << (d - 1))) >> d;
+}
+
+// out1[(sl m + j) 5 + {0..4}] = re (lo, hi words), im (lo, hi), K of slice sl
+// and coefficient j; one warp per coefficient (graph mode: graph_range)
+__global__ void k_reducex1(const long long *__restrict__ part, int m, const int *__restrict__ chunk0,
+                           const int *__restrict__ slice0, int S, const int *__restrict__ active,
+                           long long *__restrict__ out1, const int *__restrict__ dx, int ring) {
+    if (dx) {
+        int j0 = 0;
+        graph_range(dx, ring, j0, m);
+    }
+    const int sl = blockIdx.x;
+    int lo = 0, hi = S - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (slice0[mid] <= sl) lo = mid; else hi = mid - 1;
+    }
+    const int s = lo;
+    if (active && !active[s]) return;
+    const int j = blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= m) return;
+    const int p0 = chunk0[s] * XW + (sl - slice0[s]) * RSL, p1 = min(p0 + RSL, chunk0[s + 1] * XW);
+    int K = -1;
+    for (int p = p0 + lane; p < p1; p += 32) {
+        const long long *q = part + (((uint64_t)(p / XW) * m + j) * XW + p % XW) * 3;
+        K = max(K, (int)q[2]);
+    }
+    K = __reduce_max_sync(0xffffffffu, K);
+    __int128 ar = 0, ai = 0;
+    for (int p = p0 + lane; p < p1; p += 32) {
+        const long long *q = part + (((uint64_t)(p / XW) * m + j) * XW + p % XW) * 3;
+        const int d = K - (int)q[2];
+        ar += align_round(q[0], d);
+        ai += align_round(q[1], d);
+    }
+    ar = warp_sum_i128(ar);
+    ai = warp_sum_i128(ai);
+    if (lane == 0) {
+        long long *o = out1 + ((uint64_t)sl * m + j) * 5;
+        o[0] = (long long)(unsigned long long)ar;
+        o[1] = (long long)(ar >> 64);
+        o[2] = (long long)(unsigned long long)ai;
+        o[3] = (long long)(ai >> 64);
+        o[4] = K;
+    }
+}
+
+// out[s * ldo + j] from the slice sums of sector s (graph mode: the range of
+// graph_range, written from out + j0); one warp per coefficient
+__global__ void k_reducex2(const long long *__restrict__ out1, int m, const int *__restrict__ slice0,
+                           const int *__restrict__ active, double2 *__restrict__ out, int ldo,
+                           const int *__restrict__ dx, int ring, int cx) {
     const int s = blockIdx.y;
     if (dx) {
         int j0 = 0;
@@ -383,33 +449,41 @@ __global__ void k_reducex(const long long *__restrict__ part, int m, const int *
     }
     if (active && !active[s]) return;
     const int wpb = blockDim.x >> 5, lane = threadIdx.x & 31;
-    const int p0 = chunk0[s] * XW, p1 = chunk0[s + 1] * XW;        // (chunk, warp) partials of the sector
     for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < m; j += gridDim.x * wpb) {
         int K = -1;
-        for (int p = p0 + lane; p < p1; p += 32) {
-            const long long *q = part + (((uint64_t)(p / XW) * m + j) * XW + p % XW) * 3;
-            K = max(K, (int)q[2]);
-        }
+        for (int sl = slice0[s] + lane; sl < slice0[s + 1]; sl += 32)
+            K = max(K, (int)out1[((uint64_t)sl * m + j) * 5 + 4]);
         K = __reduce_max_sync(0xffffffffu, K);
         __int128 ar = 0, ai = 0;
-        for (int p = p0 + lane; p < p1; p += 32) {
-            const long long *q = part + (((uint64_t)(p / XW) * m + j) * XW + p % XW) * 3;
-            const int d = K - (int)q[2];
-            if (d > 100) continue;                                 // below 2^-38 of one unit of K
-            __int128 vr = q[0], vi = q[1];
-            if (d > 0) {
-                const __int128 h = (__int128)1 << (d - 1);
-                vr = (vr + h) >> d;
-                vi = (vi + h) >> d;
-            }
-            ar += vr;
-            ai += vi;
+        for (int sl = slice0[s] + lane; sl < slice0[s + 1]; sl += 32) {
+            const long long *q = out1 + ((uint64_t)sl * m + j) * 5;
+            const int d = K - (int)q[4];
+            const __int128 vr = (__int128)(((unsigned __int128)(unsigned long long)q[1] << 64) |
+                                           (unsigned long long)q[0]);
+            const __int128 vi = (__int128)(((unsigned __int128)(unsigned long long)q[3] << 64) |
+                                           (unsigned long long)q[2]);
+            ar += align_round(vr, d);
+            ai += align_round(vi, d);
         }
         ar = warp_sum_i128(ar);
         if (cx) ai = warp_sum_i128(ai);
         if (lane == 0)
             out[(uint64_t)s * ldo + j] = make_double2(i128_ldexp(ar, K - 2098), cx ? i128_ldexp(ai, K - 2098) : 0.0);
     }
+}
+
+// both levels: the per-sector dot products of the last k_dotx launch
+static int reducex_launch(const long long *part, long long *out1, int m, int mgrid, const int *chunk0,
+                          const int *slice0, int nslices, int S, const int *active, double2 *out, int ldo,
+                          cudaStream_t st, const int *dx = nullptr, int ring = 0, int cx = 1) {
+    if (nslices > 0) {
+        k_reducex1<<<dim3(nslices, (mgrid + 7) / 8), NTHREADS, 0, st>>>(part, m, chunk0, slice0, S, active, out1,
+                                                                         dx, ring);
+        QS3_LAUNCHED();
+    }
+    k_reducex2<<<dim3((mgrid + 7) / 8, S), NTHREADS, 0, st>>>(out1, m, slice0, active, out, ldo, dx, ring, cx);
+    QS3_LAUNCHED();
+    return QS3_OK;
 }
 
 template <typename VT>
@@ -763,7 +837,8 @@ struct Engine64 {
     HphiStats *stats;
     int cap = 0, nscr = 0;
     uint64_t D = 0;
-    DevBuf V, DG, GE, wbuf, hinb, part, partx, h1, h2, alpha, beta, nrm, nrm1, inv, active, erefb;
+    DevBuf V, DG, GE, wbuf, hinb, part, partx, partr, slices, h1, h2, alpha, beta, nrm, nrm1, inv, active, erefb;
+    int nslices = 0;
     std::vector<int> h_active;
     double brk = 1e-12;
     int strict = 0;                        // 1: every update on binary64 FMAs
@@ -818,6 +893,12 @@ struct Engine64 {
         QS3_TRY(hinb.alloc(std::max<uint64_t>(D, 1) * sizeof(VT)));
         QS3_TRY(part.alloc((uint64_t)std::max(B.nchunks, 1) * cap * sizeof(double2)));
         QS3_TRY(partx.alloc((uint64_t)std::max(B.nchunks, 1) * cap * XW * 3 * sizeof(long long)));
+        {
+            const std::vector<int> s0 = reduce_slices(B);
+            nslices = s0[B.S];
+            QS3_TRY(slices.upload(s0.data(), s0.size() * sizeof(int)));
+            QS3_TRY(partr.alloc((uint64_t)std::max(nslices, 1) * cap * 5 * sizeof(long long)));
+        }
         QS3_TRY(h1.alloc((uint64_t)B.S * cap * sizeof(double2)));
         QS3_TRY(h2.alloc((uint64_t)B.S * cap * sizeof(double2)));
         QS3_TRY(alpha.alloc((uint64_t)B.S * cap * sizeof(double)));
@@ -864,11 +945,8 @@ struct Engine64 {
     }
     int dot_reduce(int m, double2 *out, int ldo, const int *dx = nullptr, int ring = 0, int mgrid = 0) {
         if (strict) return reduce(m, out, ldo, dx, ring, mgrid);
-        const int mg = mgrid > 0 ? mgrid : m;
-        k_reducex<<<dim3((mg + 7) / 8, B.S), NTHREADS, 0, st>>>(partx.as<long long>(), m, c0(), act(), out, ldo, dx,
-                                                                ring, IsC<VT>::v ? 1 : 0);
-        QS3_LAUNCHED();
-        return QS3_OK;
+        return reducex_launch(partx.as<long long>(), partr.as<long long>(), m, mgrid > 0 ? mgrid : m, c0(),
+                              slices.as<int>(), nslices, B.S, act(), out, ldo, st, dx, ring, IsC<VT>::v ? 1 : 0);
     }
     // dot products of w against stored vectors j0 .. j0 + m - 1 into out (S x ldo)
     int mdot(int j0, int m, double2 *out, int ldo) {

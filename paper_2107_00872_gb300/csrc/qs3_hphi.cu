@@ -263,7 +263,7 @@ __device__ __forceinline__ void add_shifted(__int128 &acc, long long t, int sh) 
 }
 
 template <int ND>
-__global__ void __launch_bounds__(NTHREADS, 3) k_hphi_x(LatView L, const SecView *__restrict__ secs,
+__global__ void __launch_bounds__(NTHREADS, 4) k_hphi_x(LatView L, const SecView *__restrict__ secs,
                                                        const int *__restrict__ tile0, int S, int ntiles,
                                                        const double2 *__restrict__ phi, const int2 *__restrict__ dg,
                                                        const int *__restrict__ ge, const int *__restrict__ chunk0,

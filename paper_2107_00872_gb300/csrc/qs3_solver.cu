@@ -2620,7 +2620,7 @@ static int gs_dots_run(Basis &B, int m, const VT *V, uint64_t ldv, const VT *w, 
     const uint64_t D = B.total;
     memset(out, 0, (size_t)B.S * m * 2 * sizeof(double));
     if (m == 0 || B.nchunks == 0) return QS3_OK;
-    DevBuf pl, dgt, get, part, res;
+    DevBuf pl, dgt, get, part, res, dsl, pr;
     QS3_TRY(pl.alloc((uint64_t)m * D * sizeof(VT)));
     QS3_TRY(part.alloc((uint64_t)B.nchunks * m * (mode == 0 ? XW * 3 * sizeof(long long) : sizeof(double2))));
     QS3_TRY(res.alloc((uint64_t)B.S * m * sizeof(double2)));
@@ -2640,9 +2640,11 @@ static int gs_dots_run(Basis &B, int m, const VT *V, uint64_t ldv, const VT *w, 
         QS3_LAUNCHED();
         QS3_TRY(dotx_launch<VT>(2, dgt.as<G>(), get.as<int>(), B.nchunks, D, 0, m, w, secs, c0, B.S, nullptr,
                                 part.as<long long>(), st));
-        k_reducex<<<dim3((m + 7) / 8, B.S), NTHREADS, 0, st>>>(part.as<long long>(), m, c0, nullptr,
-                                                               res.as<double2>(), m, nullptr, 0, IsC<VT>::v ? 1 : 0);
-        QS3_LAUNCHED();
+        const std::vector<int> s0 = reduce_slices(B);
+        QS3_TRY(dsl.upload(s0.data(), s0.size() * sizeof(int)));
+        QS3_TRY(pr.alloc((uint64_t)std::max(s0[B.S], 1) * m * 5 * sizeof(long long)));
+        QS3_TRY(reducex_launch(part.as<long long>(), pr.as<long long>(), m, m, c0, dsl.as<int>(), s0[B.S], B.S,
+                               nullptr, res.as<double2>(), m, st, nullptr, 0, IsC<VT>::v ? 1 : 0));
     } else {
         k_dot64<VT, 2><<<B.nchunks, NTHREADS, 0, st>>>(pl.as<T>(), D, 0, m, w, secs, c0, B.S, nullptr,
                                                         part.as<double2>());

@@ -142,3 +142,19 @@ def test_gs_dots_empty_and_invalid():
                            0, None) == -1
     assert lib.qs3_gs_dots(b.handle, qs3.QS3_C128, 1, p, b.total_dim, p, buf.ctypes.data_as(ctypes.c_void_p),
                            2, None) == -1
+
+
+def test_gs_dots_many_slices():
+    """A sector of 1,184,040 rows (578 chunks, 9,248 warp partials): the
+    partials are reduced in slices of 4,096, then the slices; the result is
+    still the exact dot within the grid bound."""
+    torch = torch_cuda()
+    b = lib_basis(qi.chain(28, Jz=0.5), 7)
+    assert b.total_dim == 1184040
+    rng = np.random.default_rng(3)
+    w = rng.standard_normal(b.total_dim)
+    V = np.stack([rng.standard_normal(b.total_dim) * 2.0 ** rng.uniform(-30, 0, b.total_dim), w / np.linalg.norm(w)])
+    got = b.gs_dots(to_dev(V, torch.float64), to_dev(w, torch.float64), exact=True)
+    for j in range(2):
+        ex = _exact_dot(V[j], w)
+        assert abs(got[0, j] - ex) <= _bound(V[j], w), (j, got[0, j], ex)

@@ -71,15 +71,22 @@ def test_stored_full_size_square10_nd4():
 
 
 def test_stored_terms_in_lanczos():
+    """Stored terms give the binary64 FMA product bit for bit, so a strict64
+    solve (FMA products throughout) is identical with and without them; the
+    default solve (integer products on the matrix-free path) agrees within
+    rounding."""
     torch_cuda()
     import paper_2107_00872_gb300 as qs3
     b = lib_basis(qi.square(6), 3, [(0, 0, 0), (1, 2, 0), (3, 3, 0)])
-    o = qs3.SolveOpts(n_max=120, eps=1e-14, res_tol=1e-12)
+    o = qs3.SolveOpts(n_max=120, eps=1e-14, res_tol=1e-12, strict64=True)
+    od = qs3.SolveOpts(n_max=120, eps=1e-14, res_tol=1e-12)
     e0, _, i0 = b.lanczos(o, vectors=False)
+    ed, _, _ = b.lanczos(od, vectors=False)
     b.store_terms(1)
     e1, _, i1 = b.lanczos(o, vectors=False)
     np.testing.assert_array_equal(e0, e1)
     assert i0["iterations"] == i1["iterations"]
+    assert float(np.max(np.abs(ed - e0))) <= 1e-13 * float(np.max(np.abs(e0)))
 
 
 def test_stored_terms_errors():
