@@ -64,9 +64,10 @@ enum {
  * the integer units (k-sector bases with the representative table and one
  * hop amplitude on every bond): each hop's phase x phi formed exactly on
  * fixed-point images (phi rounded to 2^-53 of the largest magnitude among
- * its 128-row warp group, the phases to 2^-53), summed exactly per row in
- * 128-bit integers and rounded to binary64 once; terms whose target
- * stabiliser differs from the row's, and the diagonal, in binary64. */
+ * its 128-row warp group, the phases to 2^-53), summed per row in a 64-bit
+ * integer on the grid of the row's largest term (each term rounded once to
+ * it) and rounded to binary64 once; terms whose target stabiliser differs
+ * from the row's, and the diagonal, in binary64. */
 typedef enum { QS3_F32 = 0, QS3_F64 = 1, QS3_C64 = 2, QS3_C128 = 3, QS3_C128DF = 4, QS3_C128X = 5 } qs3_dtype;
 
 /* S^alpha_q operators, numbered as the paper's input parameter spsmsz. */

@@ -26,6 +26,7 @@
 #include <utility>
 
 #include "qs3_internal.cuh"
+#include "qs3_fixed.cuh"
 
 namespace qs3 {
 
@@ -383,6 +384,18 @@ __global__ void k_orbit_rows(const SecView *__restrict__ secs, int S, const uint
     }
 }
 
+// the per-site phases of every sector as fixed-point digits on the grid
+// 2^-52 (re.P1, re.P0, im.P1, im.P0), for the integer H Phi
+__global__ void k_phase_digits(const double2 *__restrict__ ph64, uint64_t n, int4 *__restrict__ out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const double2 p = ph64[i];
+        int a1, a0, b1, b0;
+        fx_digits((uint32_t)__double2hiint(p.x), (uint32_t)__double2loint(p.x), 1023, a1, a0);
+        fx_digits((uint32_t)__double2hiint(p.y), (uint32_t)__double2loint(p.y), 1023, b1, b0);
+        out[i] = make_int4(a1, a0, b1, b0);
+    }
+}
+
 template <int ND>
 static int build_table_nd(Basis &B, size_t max_bytes) {
     std::vector<uint64_t> hb((size_t)(B.nd + 3) * (B.N + 1));
@@ -417,8 +430,18 @@ static int build_table_nd(Basis &B, size_t max_bytes) {
     k_orbit_rows<<<std::max(grid2, 1), 256>>>(B.d_secs.as<SecView>(), B.S, reps.as<uint64_t>(), n, t2.as<int32_t>());
     QS3_LAUNCHED();
     QS3_CUDA(cudaDeviceSynchronize());
+    DevBuf phd;
+    const uint64_t nph = (uint64_t)B.S * B.N;
+    QS3_TRY(phd.alloc(nph * sizeof(int4)));
+    k_phase_digits<<<(int)std::min<uint64_t>((nph + 255) / 256, 4096), 256>>>(B.d_ph64.as<double2>(), nph,
+                                                                              phd.as<int4>());
+    QS3_LAUNCHED();
+    QS3_CUDA(cudaDeviceSynchronize());
     B.d_orb = std::move(orb);
     B.d_t2 = std::move(t2);
+    B.d_oreps = std::move(reps);
+    B.d_ostab = std::move(stab);
+    B.d_phdig = std::move(phd);
     B.n_orb = n;
     B.lv.orb = B.d_orb.as<uint32_t>();
     B.lv.n_orb = (uint32_t)n;
@@ -450,6 +473,9 @@ void drop_rep_table(Basis &B) {
     for (auto &v : B.secs) v.t2 = nullptr;
     B.d_orb.release();
     B.d_t2.release();
+    B.d_oreps.release();
+    B.d_ostab.release();
+    B.d_phdig.release();
     B.n_orb = 0;
     if (!B.secs.empty()) B.d_secs.upload(B.secs.data(), B.secs.size() * sizeof(SecView));
 }

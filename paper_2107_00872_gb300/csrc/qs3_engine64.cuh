@@ -837,7 +837,7 @@ struct Engine64 {
     HphiStats *stats;
     int cap = 0, nscr = 0;
     uint64_t D = 0;
-    DevBuf V, DG, GE, wbuf, hinb, part, partx, partr, slices, h1, h2, alpha, beta, nrm, nrm1, inv, active, erefb;
+    DevBuf V, DG, GE, wbuf, hinb, part, partx, partr, slices, h1, h2, alpha, beta, nrm, nrm1, inv, active;
     int nslices = 0;
     std::vector<int> h_active;
     double brk = 1e-12;
@@ -885,10 +885,6 @@ struct Engine64 {
         QS3_TRY(V.alloc((uint64_t)(cap + nscr) * D * sizeof(VT)));
         QS3_TRY(DG.alloc((uint64_t)(cap + nscr) * D * sizeof(VT)));
         QS3_TRY(GE.alloc((uint64_t)(cap + nscr) * std::max(B.nchunks, 1) * XW * sizeof(int)));
-        // the integer H Phi's bound on the group exponents of psi_x: a normalised
-        // vector has none above 1023 (|psi_i| <= 1)
-        const int eref = 1023 + 8;
-        QS3_TRY(erefb.upload(&eref, sizeof(int)));
         QS3_TRY(wbuf.alloc(std::max<uint64_t>(D, 1) * sizeof(VT)));
         QS3_TRY(hinb.alloc(std::max<uint64_t>(D, 1) * sizeof(VT)));
         QS3_TRY(part.alloc((uint64_t)std::max(B.nchunks, 1) * cap * sizeof(double2)));
@@ -1043,8 +1039,8 @@ struct Engine64 {
     // the binary64 FMA kernels
     int hphi_apply(int x, const int *dx) {
         if (!strict && IsC<VT>::v && hphi_x_ok(B))
-            return dx ? hphi_x_launch(B, hin(0), DG.p, GE.as<int>(), erefb.as<int>(), dx, wv(), st, act())
-                      : hphi_x_launch(B, hin(0), dg(x), ge(x), erefb.as<int>(), nullptr, wv(), st, act());
+            return dx ? hphi_x_launch(B, hin(0), DG.p, GE.as<int>(), dx, wv(), st, act())
+                      : hphi_x_launch(B, hin(0), dg(x), ge(x), nullptr, wv(), st, act());
         return hphi_launch(B, dtype(), hin(x), wv(), st, act());
     }
     // the Gram-Schmidt dot pass against psi_0 .. psi_x, timed with events

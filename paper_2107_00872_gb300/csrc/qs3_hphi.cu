@@ -247,19 +247,49 @@ __global__ void __launch_bounds__(NTHREADS, (KS && TB && sizeof(VT) == 16) ? 4 :
 // the grid exponent of every chunk's warp groups).  Each hop's product
 // phase x phi is formed exactly on the images (the phases on the grid 2^-52,
 // staged per sector as digits) with mad.wide.s32, folded at weight 2^52
-// (rounded to nearest) and added to a 128-bit row sum on the grid
-// 2^(eref - 1139): 64 bits below the coarsest grid of phi (eref >= every
-// group exponent; a normalised vector has eref <= 1023 + 8), so a term
-// loses nothing above 2^-108 of it.  Terms whose target stabiliser differs
-// from the row's (norm ratio != 1, rare) are summed in binary64 as in
-// k_hphi.  The row sum is rounded to binary64 once, then psi = J/2 sum +
-// diag phi in binary64.  Graph mode (dx): dg and ge are the store's, slot *dx.
-__device__ __forceinline__ void add_shifted(__int128 &acc, long long t, int sh) {
-    if (sh >= 0) {
-        acc += (__int128)t << min(sh, 70);
-    } else if (sh > -63) {
-        acc += (t + (1ll << (-sh - 1))) >> (-sh);
+// (rounded to nearest) and added to the row sum (RowAcc); terms whose target
+// stabiliser differs from the row's (norm ratio != 1, rare) are summed in
+// binary64 as in k_hphi.  The row sum is rounded to binary64 once, then
+// psi = J/2 sum + diag phi in binary64.  Graph mode (dx): dg and ge are the
+// store's, slot *dx.
+// the row sum of the integer H Phi: (re, im) 2^(r - 1075), r the group
+// exponent of the largest term so far; a term T 2^(em - 1075) (|T| <= 2^54)
+// is rounded to nearest onto that grid, and a term of a coarser group first
+// moves the sum to its grid.  With at most 48 terms |sum| < 2^60, and the
+// error is at most (terms + moves) / 2 units of the final grid, i.e. about
+// 2^-54 of the largest term each (binary64 accumulation: 2^-53 of each
+// partial sum).
+struct RowAcc {
+    long long re = 0, im = 0;
+    int r = -100000;
+};
+__device__ __forceinline__ long long rshift_round(long long x, int d) {
+    if (d <= 0) return x;
+    if (d > 62) return 0;
+    return (x + (1ll << (d - 1))) >> d;
+}
+__device__ __forceinline__ void row_add(RowAcc &a, long long tr, long long ti, int em) {
+    if (em > a.r) {
+        const int d = min(em - a.r, 63);
+        a.re = rshift_round(a.re, d);
+        a.im = rshift_round(a.im, d);
+        a.r = em;
     }
+    const int d = a.r - em;
+    a.re += rshift_round(tr, d);
+    a.im += rshift_round(ti, d);
+}
+// the term phase x phi on the digits: (pr + i pi)(fr + i fi), folded at
+// weight 2^52 (rounded to nearest): units 2^(em - 1075) for phi on the grid
+// of em and the phase on 2^-52
+__device__ __forceinline__ void term_x(int4 p, int2 f1, int2 f0, long long &tr, long long &ti) {
+    const long long hr = mad_w(p.x, f1.x, 0), hn = mad_w(p.z, f1.y, 0);
+    const long long mr = mad_w(p.x, f0.x, mad_w(p.y, f1.x, 0));
+    const long long mn = mad_w(p.z, f0.y, mad_w(p.w, f1.y, 0));
+    const long long hi = mad_w(p.x, f1.y, mad_w(p.z, f1.x, 0));
+    const long long mi = mad_w(p.x, f0.y, mad_w(p.y, f1.y, mad_w(p.z, f0.x, mad_w(p.w, f1.x, 0))));
+    tr = (hr - hn) + ((mr - mn + (1ll << 25)) >> 26);
+    ti = hi + ((mi + (1ll << 25)) >> 26);
 }
 
 template <int ND>
@@ -267,7 +297,7 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_hphi_x(LatView L, const SecView
                                                        const int *__restrict__ tile0, int S, int ntiles,
                                                        const double2 *__restrict__ phi, const int2 *__restrict__ dg,
                                                        const int *__restrict__ ge, const int *__restrict__ chunk0,
-                                                       int nchunks, uint64_t D, const int *__restrict__ eref_p,
+                                                       int nchunks, uint64_t D,
                                                        const int *__restrict__ dx, double2 *__restrict__ psi,
                                                        const int *__restrict__ active) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -282,7 +312,6 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_hphi_x(LatView L, const SecView
         dg += (uint64_t)(*dx) * 2 * D;
         ge += (uint64_t)(*dx) * nchunks * XW;
     }
-    const int eref = *eref_p;
     const double juni = L.jh_uniform;
     __syncthreads();
     int4 *pd = (int4 *)sm.sph;          // the current sector's phases: (re.P1, re.P0, im.P1, im.P0) on 2^-52
@@ -313,7 +342,7 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_hphi_x(LatView L, const SecView
         const int st_row = sv.stab[row];
         const double rs = snorm[9 + st_row];
         double e = L.c0, dd = 0.0;
-        __int128 ar = 0, ai = 0;
+        RowAcc acc;
         double2 acc64 = make_double2(0.0, 0.0);
 #pragma unroll 1
         for (int m = 0; m < ND; ++m) {
@@ -357,19 +386,9 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_hphi_x(LatView L, const SecView
                     const uint64_t gi = sv.off + idx;
                     const int2 f1 = dg[gi], f0 = dg[D + gi];
                     const int em = __ldg(ge + (uint64_t)(c0s + (int)(idx >> 11)) * XW + dg_group((int)(idx & 2047u)));
-                    const int4 p = pd[u];
-                    // (pr + i pi)(fr + i fi) = (pr fr - pi fi) + i (pr fi + pi fr)
-                    const long long hr = mad_w(p.x, f1.x, 0), hn = mad_w(p.z, f1.y, 0);
-                    const long long mr = mad_w(p.x, f0.x, mad_w(p.y, f1.x, 0));
-                    const long long mn = mad_w(p.z, f0.y, mad_w(p.w, f1.y, 0));
-                    const long long hi2 = mad_w(p.x, f1.y, mad_w(p.z, f1.x, 0));
-                    const long long mi = mad_w(p.x, f0.y, mad_w(p.y, f1.y, mad_w(p.z, f0.x, mad_w(p.w, f1.x, 0))));
-                    // units 2^(em - 1075) after the fold; the row sum's units 2^(eref - 1139)
-                    const long long tr = (hr - hn) + ((mr - mn + (1ll << 25)) >> 26);
-                    const long long ti = hi2 + ((mi + (1ll << 25)) >> 26);
-                    const int sh = em - eref + 64;
-                    add_shifted(ar, tr, sh);
-                    add_shifted(ai, ti, sh);
+                    long long tr, ti;
+                    term_x(pd[u], f1, f0, tr, ti);
+                    row_add(acc, tr, ti, em);
                 } else {
                     double2 p = sv.ph64[u];
                     const double f = snorm[st] * rs;
@@ -380,13 +399,170 @@ __global__ void __launch_bounds__(NTHREADS, 4) k_hphi_x(LatView L, const SecView
             }
         }
         double2 acch;
-        acch.x = i128_ldexp(ar, eref - 1139) + acc64.x;
-        acch.y = i128_ldexp(ai, eref - 1139) + acc64.y;
+        acch.x = i128_ldexp(acc.re, acc.r - 1075) + acc64.x;
+        acch.y = i128_ldexp(acc.im, acc.r - 1075) + acc64.y;
         const double ed = e + 0.5 * dd;
         double2 out;
         out.x = fma(ed, x0.x, juni * acch.x);
         out.y = fma(ed, x0.y, juni * acch.y);
         psi[sv.off + row] = out;
+    }
+}
+
+// The same product batched over sectors (all momenta of one basis share the
+// orbits and their hops; only the phases and the rows differ): one thread per
+// (orbit g, group of OSG sectors) unranks g's representative once, lists its
+// hop targets (orbit, translation, |Stab|) and its diagonal once, then forms
+// g's row in each sector of the group from them: per term one row lookup,
+// the digits of the target and its group exponent, the exact product with
+// the sector's phase digits and the row sum, as in k_hphi_x (whose output it
+// reproduces bit for bit: the terms come in the same order).  The hop lists
+// live in shared memory, maxh entries per thread.
+constexpr int OSG = 8;
+
+template <int ND>
+__global__ void __launch_bounds__(NTHREADS) k_hphi_o(LatView L, const SecView *__restrict__ secs, int S,
+                                                   const uint64_t *__restrict__ oreps,
+                                                   const uint8_t *__restrict__ ostab, uint32_t n_orb, int ngrp,
+                                                   const int4 *__restrict__ phdig, const double2 *__restrict__ phi,
+                                                   const int2 *__restrict__ dg, const int *__restrict__ ge,
+                                                   const int *__restrict__ chunk0, int nchunks, uint64_t D,
+                                                   const int *__restrict__ dx,
+                                                   double2 *__restrict__ psi, const int *__restrict__ active,
+                                                   int maxh) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint64_t *sC = (uint64_t *)smem;
+    double *snorm = (double *)(sC + (L.nd + 3) * L.np1);
+    uint32_t *hl = (uint32_t *)(snorm + 18);                     // hop targets g2 << 12 | u
+    uint8_t *hs = (uint8_t *)(hl + (size_t)maxh * blockDim.x);     // their |Stab|
+    for (int i = threadIdx.x; i < (L.nd + 3) * L.np1; i += blockDim.x) sC[i] = L.binom[i];
+    if (threadIdx.x < 9) {
+        snorm[threadIdx.x] = sqrt((double)threadIdx.x);
+        snorm[9 + threadIdx.x] = threadIdx.x ? 1.0 / sqrt((double)threadIdx.x) : 0.0;
+    }
+    if (dx) {
+        dg += (uint64_t)(*dx) * 2 * D;
+        ge += (uint64_t)(*dx) * nchunks * XW;
+    }
+    __syncthreads();
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (uint64_t)n_orb * ngrp) return;
+    const uint32_t g = (uint32_t)(tid % n_orb);
+    const int grp = (int)(tid / n_orb);
+    const int s_lo = grp * OSG, s_hi = min(S, s_lo + OSG);
+    bool any = false;
+    for (int s = s_lo; s < s_hi; ++s) any |= (!active || active[s]) && __ldg(secs[s].t2 + g) >= 0;
+    if (!any) return;
+    uint32_t *my = hl + threadIdx.x;                             // entry h at my[h * blockDim.x]
+    uint8_t *mys = hs + threadIdx.x;
+    const uint64_t rank = __ldg(oreps + g);
+    int c[ND];
+    unrank(rank, sC, L.np1, c);
+    const int st_row = __ldg(ostab + g);
+    const double rs = snorm[9 + st_row];
+    double e = L.c0, dd = 0.0;
+    int nh = 0;
+#pragma unroll 1
+    for (int m = 0; m < ND; ++m) {
+        const int i = pick(c, m);
+        e += diag_u<double>(L, i);
+        const int e0 = __ldg(L.adj_ptr + i), e1 = __ldg(L.adj_ptr + i + 1);
+        const int lo = m > 0 ? pick(c, m > 0 ? m - 1 : 0) : -1;
+        const int hi = m < ND - 1 ? pick(c, m < ND - 1 ? m + 1 : m) : L.np1;
+        const uint64_t base = rank - sC[(m + 1) * L.np1 + i];
+        for (int q = e0; q < e1; ++q) {
+            const int j = __ldg(L.adj_nbr + q);
+            const bool inpl = j > lo && j < hi;
+            if (!inpl) {
+                bool occ = false;
+#pragma unroll
+                for (int k = 0; k < ND; ++k) occ |= (c[k] == j);
+                if (occ) {
+                    dd += diag_jz<double>(L, q);
+                    continue;
+                }
+            }
+            uint64_t r2;
+            if (inpl) {
+                r2 = base + sC[(m + 1) * L.np1 + j];
+            } else {
+                int tt[ND];
+#pragma unroll
+                for (int k = 0; k < ND; ++k) tt[k] = (k == m) ? j : c[k];
+                sort_net(tt);
+                r2 = rank_of(tt, sC, L.np1);
+            }
+            const uint32_t ee = __ldg(L.orb + r2);
+            if ((ee >> 12) >= n_orb) continue;                   // never for a complete table
+            my[(size_t)nh * blockDim.x] = ee;
+            mys[(size_t)nh * blockDim.x] = __ldg(ostab + (ee >> 12));
+            ++nh;
+        }
+    }
+    const double ed = e + 0.5 * dd;
+    const double juni = L.jh_uniform;
+    for (int s = s_lo; s < s_hi; ++s) {
+        if (active && !active[s]) continue;
+        const int32_t *t2 = secs[s].t2;
+        const int32_t row = __ldg(t2 + g);
+        if (row < 0) continue;
+        const uint64_t off = secs[s].off;
+        const int c0s = __ldg(chunk0 + s);
+        const int4 *pds = phdig + (size_t)s * L.N;
+        RowAcc acc;
+        double2 acc64 = make_double2(0.0, 0.0);
+        // four terms at a time: their row lookups, then their digit gathers,
+        // are in flight together; the terms are added in list order
+        for (int h0 = 0; h0 < nh; h0 += 4) {
+            uint32_t ee[4];
+            int32_t r2[4];
+            int stb[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const bool in = h0 + b < nh;
+                ee[b] = in ? my[(size_t)(h0 + b) * blockDim.x] : 0u;
+                stb[b] = in ? mys[(size_t)(h0 + b) * blockDim.x] : 0;
+                r2[b] = in ? __ldg(t2 + (ee[b] >> 12)) : -1;
+            }
+            int2 f1[4], f0[4];
+            int em[4];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                if (r2[b] >= 0 && stb[b] == st_row) {
+                    const uint64_t gi = off + (uint32_t)r2[b];
+                    f1[b] = dg[gi];
+                    f0[b] = dg[D + gi];
+                    em[b] = __ldg(ge + (uint64_t)(c0s + (r2[b] >> 11)) * XW + dg_group(r2[b] & 2047));
+                } else {
+                    f1[b] = f0[b] = make_int2(0, 0);
+                    em[b] = 0;
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                if (r2[b] < 0) continue;
+                const int u = (int)(ee[b] & 4095u);
+                if (stb[b] == st_row) {
+                    long long tr, ti;
+                    term_x(__ldg(pds + u), f1[b], f0[b], tr, ti);
+                    row_add(acc, tr, ti, em[b]);
+                } else {
+                    double2 p = secs[s].ph64[u];
+                    const double f = snorm[stb[b]] * rs;
+                    p.x *= f;
+                    p.y *= f;
+                    acc_add(acc64, p, phi[off + (uint32_t)r2[b]]);
+                }
+            }
+        }
+        double2 acch;
+        acch.x = i128_ldexp(acc.re, acc.r - 1075) + acc64.x;
+        acch.y = i128_ldexp(acc.im, acc.r - 1075) + acc64.y;
+        const double2 x0 = phi[off + (uint32_t)row];
+        double2 out;
+        out.x = fma(ed, x0.x, juni * acch.x);
+        out.y = fma(ed, x0.y, juni * acch.y);
+        psi[off + (uint32_t)row] = out;
     }
 }
 
@@ -623,7 +799,7 @@ static int hphi_vt(Basis &B, const void *phi, void *psi, cudaStream_t st, const 
 }
 
 template <int ND>
-static int hphix_nd(Basis &B, const double2 *phi, const int2 *dg, const int *ge, const int *eref, const int *dx,
+static int hphix_nd(Basis &B, const double2 *phi, const int2 *dg, const int *ge, const int *dx,
                     double2 *psi, cudaStream_t st, const int *active) {
     static std::atomic<unsigned long long> cache{0};
     int grid = 1, occ = 1;
@@ -632,7 +808,7 @@ static int hphix_nd(Basis &B, const double2 *phi, const int2 *dg, const int *ge,
     auto launch = [&](int g) {
         k_hphi_x<ND><<<g, NTHREADS, B.smem_bytes, st>>>(B.lv, B.d_secs.as<SecView>(), B.d_tile0.as<int>(), B.S,
                                                          B.ntiles, phi, dg, ge, B.d_chunk0.as<int>(), B.nchunks,
-                                                         B.total, eref, dx, psi, active);
+                                                         B.total, dx, psi, active);
     };
     int &bps = B.tune_hphix;
     if (bps == 0) {
@@ -650,26 +826,63 @@ static int hphix_nd(Basis &B, const double2 *phi, const int2 *dg, const int *ge,
     return QS3_OK;
 }
 
+template <int ND>
+static int hphio_nd(Basis &B, const double2 *phi, const int2 *dg, const int *ge, const int *dx,
+                    double2 *psi, cudaStream_t st, const int *active) {
+    const int maxh = std::max(1, B.nd * B.max_degree);
+    const size_t smem = (size_t)(B.nd + 3) * (B.N + 1) * 8 + 18 * 8 + (size_t)maxh * NTHREADS * 5;
+    if (smem > (size_t)MAX_DYN_SMEM) return set_err(QS3_ERR_OVERFLOW, "hop lists of %d entries per row", maxh);
+    static std::atomic<int> attr{0};
+    if (attr.load(std::memory_order_acquire) == 0) {
+        QS3_CUDA(cudaFuncSetAttribute(k_hphi_o<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_DYN_SMEM));
+        attr.store(1, std::memory_order_release);
+    }
+    const int ngrp = (B.S + OSG - 1) / OSG;
+    const uint64_t nthr = B.n_orb * (uint64_t)ngrp;
+    if (nthr == 0) return QS3_OK;
+    const int grid = (int)((nthr + NTHREADS - 1) / NTHREADS);
+    k_hphi_o<ND><<<grid, NTHREADS, smem, st>>>(B.lv, B.d_secs.as<SecView>(), B.S, B.d_oreps.as<uint64_t>(),
+                                                B.d_ostab.as<uint8_t>(), (uint32_t)B.n_orb, ngrp,
+                                                B.d_phdig.as<int4>(), phi, dg, ge, B.d_chunk0.as<int>(), B.nchunks,
+                                                B.total, dx, psi, active, maxh);
+    QS3_LAUNCHED();
+    return QS3_OK;
+}
+
 bool hphi_x_ok(const Basis &B) {
     return B.has_k && B.lv.orb && B.lv.jh_uniform != 0.0 && B.nd > 0 && !B.stored_terms && B.total > 0;
 }
 
-int hphi_x_launch(Basis &B, const void *phi, const void *dg, const int *ge, const int *eref, const int *dx, void *psi,
-                  cudaStream_t st, const int *active) {
+int hphi_x_launch(Basis &B, const void *phi, const void *dg, const int *ge, const int *dx, void *psi, cudaStream_t st,
+                  const int *active) {
     if (!hphi_x_ok(B)) return set_err(QS3_ERR_STATE, "the integer H Phi needs a k-sector basis with the "
                                                      "representative table and one hop amplitude");
     const double2 *p = (const double2 *)phi;
     const int2 *g = (const int2 *)dg;
     double2 *o = (double2 *)psi;
+    // several sectors share the orbits: the orbit-batched kernel
+    if (B.S >= 2 && B.d_oreps.p) {
+        switch (B.nd) {
+            case 1: return hphio_nd<1>(B, p, g, ge, dx, o, st, active);
+            case 2: return hphio_nd<2>(B, p, g, ge, dx, o, st, active);
+            case 3: return hphio_nd<3>(B, p, g, ge, dx, o, st, active);
+            case 4: return hphio_nd<4>(B, p, g, ge, dx, o, st, active);
+            case 5: return hphio_nd<5>(B, p, g, ge, dx, o, st, active);
+            case 6: return hphio_nd<6>(B, p, g, ge, dx, o, st, active);
+            case 7: return hphio_nd<7>(B, p, g, ge, dx, o, st, active);
+            case 8: return hphio_nd<8>(B, p, g, ge, dx, o, st, active);
+            default: return set_err(QS3_ERR_INVALID_ARG, "n_down %d", B.nd);
+        }
+    }
     switch (B.nd) {
-        case 1: return hphix_nd<1>(B, p, g, ge, eref, dx, o, st, active);
-        case 2: return hphix_nd<2>(B, p, g, ge, eref, dx, o, st, active);
-        case 3: return hphix_nd<3>(B, p, g, ge, eref, dx, o, st, active);
-        case 4: return hphix_nd<4>(B, p, g, ge, eref, dx, o, st, active);
-        case 5: return hphix_nd<5>(B, p, g, ge, eref, dx, o, st, active);
-        case 6: return hphix_nd<6>(B, p, g, ge, eref, dx, o, st, active);
-        case 7: return hphix_nd<7>(B, p, g, ge, eref, dx, o, st, active);
-        case 8: return hphix_nd<8>(B, p, g, ge, eref, dx, o, st, active);
+        case 1: return hphix_nd<1>(B, p, g, ge, dx, o, st, active);
+        case 2: return hphix_nd<2>(B, p, g, ge, dx, o, st, active);
+        case 3: return hphix_nd<3>(B, p, g, ge, dx, o, st, active);
+        case 4: return hphix_nd<4>(B, p, g, ge, dx, o, st, active);
+        case 5: return hphix_nd<5>(B, p, g, ge, dx, o, st, active);
+        case 6: return hphix_nd<6>(B, p, g, ge, dx, o, st, active);
+        case 7: return hphix_nd<7>(B, p, g, ge, dx, o, st, active);
+        case 8: return hphix_nd<8>(B, p, g, ge, dx, o, st, active);
         default: return set_err(QS3_ERR_INVALID_ARG, "n_down %d", B.nd);
     }
 }

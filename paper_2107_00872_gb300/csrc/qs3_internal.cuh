@@ -161,6 +161,8 @@ struct Basis {
     size_t smem_bytes = 0;                  // dynamic shared memory of the row kernels
     DevBuf d_orb, d_t2;                     // representative table (LatView::orb, SecView::t2)
     uint64_t n_orb = 0;                     // orbits (all representatives) when the table exists
+    DevBuf d_oreps, d_ostab;                // with the table: each orbit's representative (rank0) and |Stab|
+    DevBuf d_phdig;                         // with the table: S x N phases as digits on 2^-52 (int4)
     // autotuned launch choices, 0 = not yet tuned: resident H Phi blocks per
     // SM per vector dtype (the persistent grid, i.e. rows in flight per SM),
     // and basis vectors per pass of the double-float dot products
@@ -523,12 +525,12 @@ int hphi_launch(Basis &B, qs3_dtype dt, const void *phi, void *psi, cudaStream_t
 int hphi_df_launch(Basis &B, const void *phi, const int *dx, uint64_t ld, void *psi, cudaStream_t st,
                    const int *active = nullptr, bool out_df = false);
 int count_nnz(Basis &B, uint64_t *nnz);
-// the binary64 engine's H Phi on the integer units (qs3_hphi.cu, k_hphi_x): phi as
-// binary64 and as its digit-store image (dg, ge: slot *dx of the store when dx is
-// given), eref (device) an upper bound of its group exponents
+// the binary64 engine's H Phi on the integer units (qs3_hphi.cu, k_hphi_x and the
+// orbit-batched k_hphi_o): phi as binary64 and as its digit-store image (dg, ge:
+// slot *dx of the store when dx is given)
 bool hphi_x_ok(const Basis &B);
-int hphi_x_launch(Basis &B, const void *phi, const void *dg, const int *ge, const int *eref, const int *dx, void *psi,
-                  cudaStream_t st, const int *active = nullptr);
+int hphi_x_launch(Basis &B, const void *phi, const void *dg, const int *ge, const int *dx, void *psi, cudaStream_t st,
+                  const int *active = nullptr);
 // qs3_hphi with QS3_C128X: phi's digit image in scratch, then hphi_x_launch
 // (qs3_solver.cu, where the digit kernels live); synchronous on st
 int hphi_x_binary64(Basis &B, const void *phi, void *psi, cudaStream_t st);

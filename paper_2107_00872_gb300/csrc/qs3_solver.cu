@@ -2692,26 +2692,16 @@ extern "C" int qs3_trlanczos(qs3_basis_t b, const qs3_solve_opts *o, double *eva
 namespace qs3 {
 
 // qs3_hphi with QS3_C128X: phi's digit image (the layout of the engine's
-// digit store, one slot) in scratch, its largest group exponent as the
-// integer H Phi's grid bound, then the product
-__global__ void k_max_int(const int *__restrict__ v, uint64_t n, int *__restrict__ out) {
-    int m = 0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        m = max(m, v[i]);
-    m = (int)__reduce_max_sync(0xffffffffu, (unsigned)m);
-    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
-}
-
+// digit store, one slot) in scratch, then the product
 int hphi_x_binary64(Basis &B, const void *phi, void *psi, cudaStream_t st) {
     if (!hphi_x_ok(B))
         return set_err(QS3_ERR_STATE, "QS3_C128X needs a k-sector basis with the representative table and one hop "
                                       "amplitude");
     const uint64_t D = B.total;
-    DevBuf pl, dgt, get, er;
+    DevBuf pl, dgt, get;
     QS3_TRY(pl.alloc(D * sizeof(double2)));
     QS3_TRY(dgt.alloc(D * sizeof(double2)));
     QS3_TRY(get.alloc((uint64_t)B.nchunks * XW * sizeof(int)));
-    QS3_TRY(er.alloc(sizeof(int)));
     const int g = (int)std::min<uint64_t>((D + 255) / 256, 4096);
     k_to_planar<double2><<<g, 256, 0, st>>>((const double2 *)phi, pl.as<uint2>(), D);
     QS3_LAUNCHED();
@@ -2719,11 +2709,7 @@ int hphi_x_binary64(Basis &B, const void *phi, void *psi, cudaStream_t st) {
                                                            B.nchunks, B.d_secs.as<SecView>(), B.d_chunk0.as<int>(),
                                                            B.S);
     QS3_LAUNCHED();
-    QS3_CUDA(cudaMemsetAsync(er.p, 0, sizeof(int), st));
-    const uint64_t ng = (uint64_t)B.nchunks * XW;
-    k_max_int<<<(int)std::min<uint64_t>((ng + 255) / 256, 1024), 256, 0, st>>>(get.as<int>(), ng, er.as<int>());
-    QS3_LAUNCHED();
-    QS3_TRY(hphi_x_launch(B, phi, dgt.p, get.as<int>(), er.as<int>(), nullptr, psi, st, nullptr));
+    QS3_TRY(hphi_x_launch(B, phi, dgt.p, get.as<int>(), nullptr, psi, st, nullptr));
     QS3_CUDA(cudaStreamSynchronize(st));     // the scratch is released on return
     return QS3_OK;
 }

@@ -125,3 +125,23 @@ def test_integer_hphi_limits():
     assert info["status"] == "QS3_OK"
     w = np.linalg.eigvalsh(orc.dense_k(orc.mk_list(olat(aniso), 2, (1, 0, 0))))
     assert abs(e[0, 0] - w[0]) <= 1e-12 * max(1.0, abs(w[0]))
+
+
+@pytest.mark.parametrize("name,dims,nd", [("square6_nd3", (6, 6, 1), 3), ("chain12_nd4", (12, 1, 1), 4),
+                                          ("cube3_nd3", (3, 3, 3), 3)])
+def test_orbit_batched_equals_per_sector(name, dims, nd):
+    """A basis of several momenta runs the orbit-batched kernel (each orbit's
+    hops listed once for a group of sectors); one-sector bases run the
+    per-row kernel.  The integer row sums are exact and the binary64 terms
+    come in the same order, so the outputs agree bit for bit."""
+    torch = torch_cuda()
+    spec = qi.hypercubic(dims, J=1.0, Jz=0.6)
+    K = qi.all_k(dims)
+    b = lib_basis(spec, nd, K)
+    phi_h = _vector(3, b.total_dim, "binades")
+    multi = b.hphi(to_dev(phi_h, torch.complex128), integer=True).cpu().numpy()
+    for s, k in enumerate(K):
+        lo, hi = b.offsets[s], b.offsets[s + 1]
+        one = lib_basis(spec, nd, [k])
+        got = one.hphi(to_dev(phi_h[lo:hi], torch.complex128), integer=True).cpu().numpy()
+        np.testing.assert_array_equal(got.view(np.uint64), multi[lo:hi].view(np.uint64))
