@@ -148,13 +148,15 @@ int qs3_basis_rep_table(qs3_basis_t b, int32_t mode, int32_t *active);
  *     dtype, and keeps the fastest;
  *   - the dot products of the Gram-Schmidt pass with 1, 2 or 4 basis vectors
  *     per pass (loads in flight together): dot_vectors for the double-float
- *     engine and the fp32 phase, dot_vectors64 for the binary64 engine.
+ *     engine and the fp32 phase, dot_vectors64 for the binary64 engine, which
+ *     also has 8: the stored vectors' digits copied by bulk asynchronous
+ *     copies (TMA) into a six-stage ring in shared memory (k_dotb).
  * set = 0: write the current choices (0 = not tuned yet) to
  *          hphi_blocks_per_sm[5] (indexed by qs3_dtype), *dot_vectors and
  *          *dot_vectors64;
  * set = 1: impose them (0 = tune again at the next use; blocks per SM above
- *          the occupancy limit are clamped; vectors per pass in {0, 1, 2, 4};
- *          INVALID_ARG otherwise).
+ *          the occupancy limit are clamped; vectors per pass in {0, 1, 2, 4},
+ *          and 8 for dot_vectors64; INVALID_ARG otherwise).
  * Any pointer may be NULL.  Results do not depend on the choices. */
 int qs3_basis_tuning(qs3_basis_t b, int32_t set, int32_t *hphi_blocks_per_sm, int32_t *dot_vectors,
                      int32_t *dot_vectors64);
@@ -193,13 +195,20 @@ int qs3_hphi(qs3_basis_t b, qs3_dtype dtype, const void *phi, void *psi, void *s
  * mode 0 (the dots of fp64 solves): every operand is rounded once onto a
  * fixed-point grid set by the largest exponent among the 128 rows of its
  * warp (rows r with the same r mod 2048 div 32 within a chunk of 2048),
- * at most 2^-53 of that largest magnitude; the products of those images
- * are summed exactly in 64-bit integers, each warp's sum rounded to
- * binary64 once and the warps and chunks summed in binary64.
+ * at most 2^-53 of that largest magnitude, and split into two balanced
+ * digits (weights 2^26 and 1); the top x top and the cross digit products
+ * are summed exactly in 64-bit integers, the low x low ones dropped, each
+ * thread's cross sum rounded to the nearest multiple of 2^26; the warps'
+ * sums are aligned to the coarsest grid of the sector (rounded to nearest)
+ * and added exactly in 128-bit integers, and each sector's dot is rounded
+ * to binary64 once.  The pass is the one the basis' dot_vectors64 choice
+ * selects (qs3_basis_tuning; 2 when untuned): the results are the same bits
+ * for every choice.
  * mode 1 (strict64 solves): binary64 FMA chains per thread, summed in a
  * fixed order.  Device scratch of m x the vector size is allocated per call.
  * Errors: INVALID_ARG (NULL, m < 0, ldv < total dimension for m > 1, dtype,
- * mode), OOM. */
+ * mode), OOM, TIMEOUT (a bounded wait of the copy ring ran out; the context
+ * stays usable). */
 int qs3_gs_dots(qs3_basis_t b, qs3_dtype dtype, int32_t m, const void *V, uint64_t ldv, const void *w,
                 double *out, int32_t mode, void *stream);
 
@@ -425,6 +434,15 @@ int qs3_probe_peaks(qs3_peaks *out, void *stream);
  * injection off.  Process-wide (all threads).  Returns the previous setting
  * (-1 = off).  Calls that fail this way release what they allocated. */
 int64_t qs3_inject_alloc_failure(int64_t after);
+
+/* Wait-timeout injection for tests of the bounded device waits (no
+ * counterpart in the paper).  n > 0: the next n launches of the copy-ring
+ * dot pass (k_dotb) run with their copy warp issuing no copies, so every
+ * consumer warp's wait on its first stage runs out after one second and the
+ * call that launched it returns QS3_ERR_TIMEOUT (the context stays usable;
+ * no fault, trap or endless wait is involved).  n <= 0 switches it off.
+ * Process-wide.  Returns the previous count. */
+int32_t qs3_inject_wait_timeout(int32_t n);
 
 /* Text of a status code, and of the last failure on the calling thread. */
 const char *qs3_strerror(int status);

@@ -13,7 +13,7 @@ from . import _abi
 from ._abi import QS3_C64, QS3_C128, QS3_C128DF, QS3_C128X, QS3_F32, QS3_F64, QS3Error, check, load
 
 __all__ = ["Basis", "QS3Error", "load", "hphi", "dtype_code", "SolveOpts", "split_df", "probe_peaks",
-           "inject_alloc_failure"]
+           "inject_alloc_failure", "inject_wait_timeout"]
 
 
 def _torch():
@@ -110,6 +110,13 @@ def inject_alloc_failure(after: int) -> int:
     library succeed and fail every later one with QS3_ERR_OOM (after < 0:
     off).  Returns the previous setting."""
     return int(load().qs3_inject_alloc_failure(int(after)))
+
+
+def inject_wait_timeout(n: int) -> int:
+    """qs3_inject_wait_timeout: the next n copy-ring dot passes launch with
+    no copies issued, so their bounded waits run out (QS3_ERR_TIMEOUT);
+    n <= 0 switches it off.  Returns the previous count."""
+    return int(load().qs3_inject_wait_timeout(int(n)))
 
 
 def _info_dict(info: _abi.qs3_solve_info) -> dict:

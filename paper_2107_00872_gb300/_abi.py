@@ -67,6 +67,7 @@ SIGNATURES = {
     "qs3_dsf_op": ([I32, I32, P, I32, P, F64, P, I32, P, I32, F64, F64, I32, P, P, P, P, P, P], I32),
     "qs3_probe_peaks": ([P, P], I32),
     "qs3_inject_alloc_failure": ([ctypes.c_int64], ctypes.c_int64),
+    "qs3_inject_wait_timeout": ([I32], I32),
     "qs3_strerror": ([I32], ctypes.c_char_p),
     "qs3_last_error": ([], ctypes.c_char_p),
     "qs3_version": ([], ctypes.c_char_p),

@@ -57,6 +57,12 @@ void DevBuf::release() {
 // allocation fault injection (qs3_inject_alloc_failure): the number of
 // allocations still allowed to succeed, or -1 when off
 static std::atomic<long long> g_alloc_budget{-1};
+static std::atomic<int> g_wait_starve{0};
+int take_wait_injection() {
+    for (int n = g_wait_starve.load(); n > 0;)
+        if (g_wait_starve.compare_exchange_weak(n, n - 1)) return 1;
+    return 0;
+}
 
 int DevBuf::alloc(size_t bytes) {
     release();
@@ -898,12 +904,13 @@ int qs3_basis_tuning(qs3_basis_t b, int32_t set, int32_t *hphi_blocks_per_sm, in
     if (!b) return set_err(QS3_ERR_INVALID_ARG, "basis is NULL");
     Basis &B = b->B;
     auto nv_ok = [](const int32_t *v) { return !v || *v == 0 || *v == 1 || *v == 2 || *v == 4; };
+    auto nv64_ok = [&](const int32_t *v) { return nv_ok(v) || *v == 8; };
     if (set) {
         if (hphi_blocks_per_sm)
             for (int i = 0; i < 5; ++i)
                 if (hphi_blocks_per_sm[i] < 0) return set_err(QS3_ERR_INVALID_ARG, "blocks per SM %d", hphi_blocks_per_sm[i]);
         if (!nv_ok(dot_vectors)) return set_err(QS3_ERR_INVALID_ARG, "dot vectors per pass %d", *dot_vectors);
-        if (!nv_ok(dot_vectors64)) return set_err(QS3_ERR_INVALID_ARG, "dot vectors per pass %d", *dot_vectors64);
+        if (!nv64_ok(dot_vectors64)) return set_err(QS3_ERR_INVALID_ARG, "dot vectors per pass %d", *dot_vectors64);
         if (hphi_blocks_per_sm)
             for (int i = 0; i < 5; ++i) B.tune_hphi[i] = hphi_blocks_per_sm[i];
         if (dot_vectors) B.tune_nv = *dot_vectors;
@@ -920,6 +927,8 @@ int qs3_basis_tuning(qs3_basis_t b, int32_t set, int32_t *hphi_blocks_per_sm, in
 int64_t qs3_inject_alloc_failure(int64_t after) {
     return (int64_t)qs3::g_alloc_budget.exchange(after < 0 ? -1 : (long long)after);
 }
+
+int32_t qs3_inject_wait_timeout(int32_t n) { return qs3::g_wait_starve.exchange(n > 0 ? n : 0); }
 
 const char *qs3_last_error(void) { return qs3::last_err(); }
 

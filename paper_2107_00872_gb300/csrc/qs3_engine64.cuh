@@ -228,6 +228,65 @@ __device__ __forceinline__ int fx_group(const uint32_t (&hw)[XR][2], const uint3
     return em;
 }
 
+// w's digits as the dot products use them: per row the top and low digits
+// (w1, w0) of each component and, for complex rows, those of w.r + w.i (e)
+// and w.i - w.r (f), each the sum of the components' digits
+struct WDig {
+    int w1[XR][2], w0[XR][2], e1[XR], e0[XR], f1[XR], f0[XR];
+    __device__ __forceinline__ void pairs() {
+#pragma unroll
+        for (int k = 0; k < XR; ++k) {
+            e1[k] = w1[k][0] + w1[k][1];
+            e0[k] = w0[k][0] + w0[k][1];
+            f1[k] = w1[k][1] - w1[k][0];
+            f0[k] = w0[k][1] - w0[k][0];
+        }
+    }
+};
+
+// One thread's share of conj(a) . w over its XR rows: the sum of the top
+// digit products (weight 2^52) plus the sum of the middle ones (weight 2^26)
+// rounded to nearest at 2^52; the low x low products are dropped.  Complex
+// rows take three products per digit pair instead of four, from
+//   re = w.r s + a.i (w.r + w.i),  im = w.r s + a.r (w.i - w.r),  s = a.r - a.i:
+// the digits of s, w.r + w.i and w.i - w.r are sums of the operands' digits,
+// so the top, middle and dropped sums are the same integers as those of
+// (a.r w.r + a.i w.i) + i (a.r w.i - a.i w.r) taken product by product.
+// Bounds: digits of s, e, f below 2^28 (top) and 2^26 (low), so every
+// product and every partial sum here stays far inside 64 bits.
+template <bool CX>
+__device__ __forceinline__ void fx_thread_dot(const int (&a1)[XR][2], const int (&a0)[XR][2], const WDig &d,
+                                              long long &tr, long long &ti) {
+    if constexpr (CX) {
+        long long hk = 0, mk = 0, h3 = 0, m3 = 0, h2 = 0, m2 = 0;
+#pragma unroll
+        for (int k = 0; k < XR; ++k) {
+            const int s1 = a1[k][0] - a1[k][1], s0 = a0[k][0] - a0[k][1];
+            hk = mad_w(d.w1[k][0], s1, hk);
+            mk = mad_w(d.w1[k][0], s0, mk);
+            mk = mad_w(d.w0[k][0], s1, mk);
+            h3 = mad_w(a1[k][1], d.e1[k], h3);
+            m3 = mad_w(a1[k][1], d.e0[k], m3);
+            m3 = mad_w(a0[k][1], d.e1[k], m3);
+            h2 = mad_w(a1[k][0], d.f1[k], h2);
+            m2 = mad_w(a1[k][0], d.f0[k], m2);
+            m2 = mad_w(a0[k][0], d.f1[k], m2);
+        }
+        tr = (hk + h3) + ((mk + m3 + (1ll << 25)) >> 26);
+        ti = (hk + h2) + ((mk + m2 + (1ll << 25)) >> 26);
+    } else {
+        long long h = 0, m1 = 0, m0 = 0;
+#pragma unroll
+        for (int k = 0; k < XR; ++k) {
+            h = mad_w(a1[k][0], d.w1[k][0], h);
+            m1 = mad_w(a1[k][0], d.w0[k][0], m1);
+            m0 = mad_w(a0[k][0], d.w1[k][0], m0);
+        }
+        tr = h + ((m1 + m0 + (1ll << 25)) >> 26);
+        ti = 0;
+    }
+}
+
 // digit store slots j0 .. j0 + gridDim.y - 1 from the binary64 store (one
 // block of XT threads per chunk)
 template <typename VT>
@@ -281,8 +340,8 @@ __global__ void __launch_bounds__(XT, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = (ci.n - (int)threadIdx.x + XT - 1) / XT;          // rows of this thread
     const uint64_t r0 = ci.base + threadIdx.x;
-    // w on its warp's grid: digits (w1, w0) per row and component
-    int w1[XR][2], w0[XR][2];
+    // w on its warp's grid: digits per row and component
+    WDig wd;
     int ew;
     {
         uint32_t hw[XR][2], lw[XR][2];
@@ -294,7 +353,8 @@ __global__ void __launch_bounds__(XT, 1)
             hw[k][1] = (uint32_t)__double2hiint(v.y);
             lw[k][1] = (uint32_t)__double2loint(v.y);
         }
-        ew = fx_group<NC>(hw, lw, w1, w0);
+        ew = fx_group<NC>(hw, lw, wd.w1, wd.w0);
+        wd.pairs();
     }
     // NV stored vectors per stage, two stages: the loads of the next stage
     // are in flight while the current one is multiplied
@@ -320,33 +380,10 @@ __global__ void __launch_bounds__(XT, 1)
     auto consume = [&](const Stage &b, int jj) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            // conj(a) w = (a.r w.r + a.i w.i) + i (a.r w.i - a.i w.r): the
-            // subtracted terms go to their own sums (hn, mn)
-            long long hr = 0, mr = 0, hi = 0, mi = 0, hn = 0, mn = 0;
-#pragma unroll
-            for (int k = 0; k < XR; ++k) {
-                const int a1r = b.a1[v][k][0], a0r = b.a0[v][k][0];
-                hr = mad_w(a1r, w1[k][0], hr);
-                mr = mad_w(a1r, w0[k][0], mr);
-                mr = mad_w(a0r, w1[k][0], mr);
-                if (CX) {
-                    const int a1i = b.a1[v][k][1], a0i = b.a0[v][k][1];
-                    hr = mad_w(a1i, w1[k][1], hr);
-                    mr = mad_w(a1i, w0[k][1], mr);
-                    mr = mad_w(a0i, w1[k][1], mr);
-                    hi = mad_w(a1r, w1[k][1], hi);
-                    hn = mad_w(a1i, w1[k][0], hn);
-                    mi = mad_w(a1r, w0[k][1], mi);
-                    mi = mad_w(a0r, w1[k][1], mi);
-                    mn = mad_w(a1i, w0[k][0], mn);
-                    mn = mad_w(a0i, w1[k][0], mn);
-                }
-            }
-            hi -= hn;
-            mi -= mn;
-            // h 2^52 + m 2^26 = (h + m / 2^26) 2^52, rounded at weight 2^52
-            const long long sr = warp_sum_ll(hr + ((mr + (1ll << 25)) >> 26));
-            const long long si = CX ? warp_sum_ll(hi + ((mi + (1ll << 25)) >> 26)) : 0ll;
+            long long tr, ti;
+            fx_thread_dot<CX>(b.a1[v], b.a0[v], wd, tr, ti);
+            const long long sr = warp_sum_ll(tr);
+            const long long si = CX ? warp_sum_ll(ti) : 0ll;
             if (lane == 0 && jj + v < m) {
                 long long *o = part + (((uint64_t)blockIdx.x * m + jj + v) * XW + warp) * 3;
                 o[0] = sr;
@@ -364,6 +401,220 @@ __global__ void __launch_bounds__(XT, 1)
         if (jj + NV >= m) break;
         if (jj + 2 * NV < m) load(s0, jj + 2 * NV);
         consume(s1, jj + NV);
+    }
+}
+
+// The same dot products with the stored vectors' digits brought in by TMA
+// bulk copies (k_dotb).  A producer warp (warp XW, one elected lane) copies,
+// per stored vector, the chunk's slices of both digit planes and its XW group
+// exponents into stage jj % NS of a ring in shared memory (complete_tx on the
+// stage's "full" mbarrier); each of the XW consumer warps multiplies the
+// stage and arrives on its "empty" mbarrier, which the producer waits for
+// before refilling the stage.  A slice starts at the 16-byte boundary at or
+// below the chunk's first element (off elements earlier, off computed per
+// plane) and its size is rounded up to 16 bytes: the store must have 16
+// readable bytes past its end.  Every wait is bounded by the global timer
+// (MB_NS nanoseconds): a wait that runs out sets *err, the warp leaves its
+// loop, and the producer waits (bounded) for the copies it has in flight
+// before it exits, so that no copy lands in a finished block's memory.
+// starve != 0 (the test injection of a lost copy): the producer issues no
+// copies, so the consumers' first waits run out.
+constexpr unsigned long long MB_NS = 1000000000ull;     // 1 s
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, unsigned n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, unsigned parity) {
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// wait for the completion of the phase with the given parity, at most MB_NS
+// nanoseconds; false when the wait ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity) {
+    if (mbar_try(b, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try(b, parity))
+        if (gtimer() - t0 > MB_NS) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+// one ring stage: two digit slices (a chunk plus up to 16 bytes before it,
+// rounded up to 16 bytes), then the chunk's XW group exponents
+template <typename VT> constexpr unsigned dotb_slice() {
+    return (unsigned)((BROWS * sizeof(typename DigT<VT>::T) + 16 + 15) / 16 * 16);
+}
+template <typename VT> constexpr unsigned dotb_stage() { return 2 * dotb_slice<VT>() + XW * 4; }
+template <typename VT, int NS> constexpr unsigned dotb_smem() { return NS * dotb_stage<VT>(); }
+
+template <typename VT, int NS>
+__global__ void __launch_bounds__(XT + 32, 1)
+    k_dotb(const typename DigT<VT>::T *__restrict__ dg, const int *__restrict__ ge, int nchunks, uint64_t D, int j0,
+           int m, const VT *__restrict__ w, const SecView *__restrict__ secs, const int *__restrict__ chunk0, int S,
+           const int *__restrict__ active, long long *__restrict__ part, int *__restrict__ err, int starve,
+           const int *__restrict__ dx = nullptr, int ring = 0) {
+    using G = typename DigT<VT>::T;
+    constexpr bool CX = IsC<VT>::v;
+    constexpr int NC = CX ? 2 : 1;
+    constexpr unsigned SL = dotb_slice<VT>(), SB = dotb_stage<VT>();
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t full[NS], empty[NS];
+    graph_range(dx, ring, j0, m);
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int t = 0; t < NS; ++t) {
+            mbar_init(&full[t], 1);
+            mbar_init(&empty[t], XW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // the chunk's first element in plane pl of stored vector jj, and its byte
+    // offset above the 16-byte boundary: that of vector 0 plus jj times the
+    // slot size (2 D elements) modulo 16
+    auto plane = [&](int jj, int pl) { return dg + ((uint64_t)(j0 + jj) * 2 + pl) * D + ci.base; };
+    auto offb = [&](const G *p) { return (unsigned)((uintptr_t)p & 15u); };
+    const unsigned ob1 = offb(plane(0, 0)), ob0 = offb(plane(0, 1));
+    const unsigned osl = (unsigned)(2 * D * sizeof(G)) & 15u;
+    auto offj = [&](unsigned ob, int jj) { return (ob + (unsigned)jj * osl) & 15u; };
+    if (warp == XW) {
+        // producer
+        if (lane == 0) {
+            const unsigned nb = (unsigned)ci.n * (unsigned)sizeof(G);
+            int issued = 0;
+            bool ok = true;
+            for (; issued < m && !starve; ++issued) {
+                const int t = issued % NS;
+                if (issued >= NS && !mbar_wait(&empty[t], (unsigned)(issued / NS - 1) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char *sp = dsm + (size_t)t * SB;
+                const G *p1 = plane(issued, 0), *p0 = plane(issued, 1);
+                const unsigned o1 = offb(p1), o0 = offb(p0);
+                const unsigned b1 = (o1 + nb + 15u) & ~15u, b0 = (o0 + nb + 15u) & ~15u;
+                mbar_expect_tx(&full[t], b1 + b0 + XW * 4);
+                bulk_g2s(sp, (const unsigned char *)p1 - o1, b1, &full[t]);
+                bulk_g2s(sp + SL, (const unsigned char *)p0 - o0, b0, &full[t]);
+                bulk_g2s(sp + 2 * SL, ge + ((uint64_t)(j0 + issued) * nchunks + blockIdx.x) * XW, XW * 4, &full[t]);
+            }
+            if (!ok) atomicExch(err, 1);
+            // the copies in flight land before the block ends
+            for (int jj = issued - NS > 0 ? issued - NS : 0; jj < issued; ++jj)
+                mbar_wait(&full[jj % NS], (unsigned)(jj / NS) & 1u);
+        }
+        return;
+    }
+    const int nk = (ci.n - (int)threadIdx.x + XT - 1) / XT;          // rows of this thread
+    const uint64_t r0 = ci.base + threadIdx.x;
+    // w on its warp's grid
+    WDig wd;
+    int ew;
+    {
+        uint32_t hw[XR][2], lw[XR][2];
+#pragma unroll
+        for (int k = 0; k < XR; ++k) {
+            const double2 v = k < nk ? ld2(w + r0 + (uint64_t)k * XT) : make_double2(0.0, 0.0);
+            hw[k][0] = (uint32_t)__double2hiint(v.x);
+            lw[k][0] = (uint32_t)__double2loint(v.x);
+            hw[k][1] = (uint32_t)__double2hiint(v.y);
+            lw[k][1] = (uint32_t)__double2loint(v.y);
+        }
+        ew = fx_group<NC>(hw, lw, wd.w1, wd.w0);
+        wd.pairs();
+    }
+    // the thread's folded sums of one stored vector (fx_thread_dot)
+    auto tsum = [&](const unsigned char *sp, int jj, long long &tr, long long &ti) {
+        const G *p1 = (const G *)(sp + offj(ob1, jj));
+        const G *p0 = (const G *)(sp + SL + offj(ob0, jj));
+        int a1[XR][2], a0[XR][2];
+#pragma unroll
+        for (int k = 0; k < XR; ++k) {
+            a1[k][0] = a1[k][1] = a0[k][0] = a0[k][1] = 0;
+            if (k < nk) {
+                const G q1 = p1[threadIdx.x + k * XT], q0 = p0[threadIdx.x + k * XT];
+                if constexpr (CX) {
+                    a1[k][0] = q1.x; a1[k][1] = q1.y; a0[k][0] = q0.x; a0[k][1] = q0.y;
+                } else {
+                    a1[k][0] = q1; a0[k][0] = q0;
+                }
+            }
+        }
+        fx_thread_dot<CX>(a1, a0, wd, tr, ti);
+    };
+    // two stored vectors per pass (their chains interleave); lane 0 waits
+    // for the stages, then every lane observes the completed phases itself
+#pragma unroll 1
+    for (int jj = 0; jj < m; jj += 2) {
+        const bool two = jj + 1 < m;
+        const int t0 = jj % NS, t1 = (jj + 1) % NS;
+        const unsigned q0 = (unsigned)(jj / NS) & 1u, q1 = (unsigned)((jj + 1) / NS) & 1u;
+        bool ok = true;
+        if (lane == 0) {
+            ok = mbar_wait(&full[t0], q0);
+            if (ok && two) ok = mbar_wait(&full[t1], q1);
+        }
+        if (!__shfl_sync(0xffffffffu, (int)ok, 0)) {
+            // a wait ran out: record it and leave zero partials for the
+            // vectors not multiplied, so that what follows stays finite
+            if (lane == 0) {
+                atomicExch(err, 1);
+                for (int j = jj; j < m; ++j) {
+                    long long *o = part + (((uint64_t)blockIdx.x * m + j) * XW + warp) * 3;
+                    o[0] = 0;
+                    o[1] = 0;
+                    o[2] = ew + 54;
+                }
+            }
+            break;
+        }
+        mbar_try(&full[t0], q0);
+        if (two) mbar_try(&full[t1], q1);
+        const unsigned char *s0 = dsm + (size_t)t0 * SB, *s1 = dsm + (size_t)t1 * SB;
+        long long tr0, ti0, tr1 = 0, ti1 = 0;
+        const int em0 = ((const int *)(s0 + 2 * SL))[warp];
+        const int em1 = two ? ((const int *)(s1 + 2 * SL))[warp] : 0;
+        tsum(s0, jj, tr0, ti0);
+        if (two) tsum(s1, jj + 1, tr1, ti1);
+        // both stages are read: release them to the producer
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(&empty[t0]);
+            if (two) mbar_arrive(&empty[t1]);
+        }
+        const long long sr0 = warp_sum_ll(tr0), sr1 = warp_sum_ll(tr1);
+        const long long si0 = CX ? warp_sum_ll(ti0) : 0ll, si1 = CX ? warp_sum_ll(ti1) : 0ll;
+        if (lane == 0) {
+            long long *o = part + (((uint64_t)blockIdx.x * m + jj) * XW + warp) * 3;
+            o[0] = sr0;
+            o[1] = si0;
+            o[2] = em0 + ew;
+            if (two) {
+                o += XW * 3;
+                o[0] = sr1;
+                o[1] = si1;
+                o[2] = em1 + ew;
+            }
+        }
     }
 }
 
@@ -486,12 +737,40 @@ static int reducex_launch(const long long *part, long long *out1, int m, int mgr
     return QS3_OK;
 }
 
+// the wait-timeout injection (qs3_inject_wait_timeout): 1 while launches to
+// starve remain, counting them down
+int take_wait_injection();
+
+// k_dotb's ring: one resident block per SM and six stages of complex rows
+// (197 KB of shared memory), twelve of real rows (half the bytes each)
+template <typename VT> constexpr int dotb_ns() { return IsC<VT>::v ? 6 : 12; }
+// the shared-memory size of k_dotb (once per process, before any launch or
+// capture)
+template <typename VT> static int dotb_prepare() {
+    static const cudaError_t e = cudaFuncSetAttribute(k_dotb<VT, dotb_ns<VT>()>,
+                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)dotb_smem<VT, dotb_ns<VT>()>());
+    QS3_CUDA(e);
+    return QS3_OK;
+}
+
+// The dot pass: nv = 1, 2 or 4 stored vectors per pass of k_dotx (register
+// staging), or nv = 8 the copy-engine ring of k_dotb (dg must then have 16
+// readable bytes past its last slot, err a device int; dotb_prepare done).
+// Passes over at most two vectors (the three-term part) run k_dotx.
 template <typename VT>
 static int dotx_launch(int nv, const typename DigT<VT>::T *dg, const int *ge, int nchunks, uint64_t D, int j0, int m,
                        const VT *w, const SecView *secs, const int *c0, int S, const int *act, long long *pp,
-                       cudaStream_t st, const int *dx = nullptr, int ring = 0) {
+                       cudaStream_t st, const int *dx = nullptr, int ring = 0, int *err = nullptr) {
+    const bool small = ring || (!dx && m <= 2);
+    if (nv >= 8 && !small && err) {
+        k_dotb<VT, dotb_ns<VT>()><<<std::max(nchunks, 1), XT + 32, dotb_smem<VT, dotb_ns<VT>()>(), st>>>(
+            dg, ge, nchunks, D, j0, m, w, secs, c0, S, act, pp, err, take_wait_injection(), dx, ring);
+        QS3_LAUNCHED();
+        return QS3_OK;
+    }
     // complex rows stage at most 2 vectors (4 would spill registers)
-    if (ring || (!dx && m <= 2) || IsC<VT>::v) nv = std::min(nv, 2);
+    if (nv >= 8 || small || IsC<VT>::v) nv = std::min(nv, 2);
     const int g = std::max(nchunks, 1);
     if (nv == 1) {
         k_dotx<VT, 1><<<g, XT, 0, st>>>(dg, ge, nchunks, D, j0, m, w, secs, c0, S, act, pp, dx, ring);
@@ -837,7 +1116,7 @@ struct Engine64 {
     HphiStats *stats;
     int cap = 0, nscr = 0;
     uint64_t D = 0;
-    DevBuf V, DG, GE, wbuf, hinb, part, partx, partr, slices, h1, h2, alpha, beta, nrm, nrm1, inv, active;
+    DevBuf V, DG, GE, wbuf, hinb, part, partx, partr, slices, h1, h2, alpha, beta, nrm, nrm1, inv, active, derr;
     int nslices = 0;
     std::vector<int> h_active;
     double brk = 1e-12;
@@ -883,7 +1162,7 @@ struct Engine64 {
         nscr = nscratch;
         D = B.total;
         QS3_TRY(V.alloc((uint64_t)(cap + nscr) * D * sizeof(VT)));
-        QS3_TRY(DG.alloc((uint64_t)(cap + nscr) * D * sizeof(VT)));
+        QS3_TRY(DG.alloc((uint64_t)(cap + nscr) * D * sizeof(VT) + 16));     // k_dotb reads up to 16 bytes past
         QS3_TRY(GE.alloc((uint64_t)(cap + nscr) * std::max(B.nchunks, 1) * XW * sizeof(int)));
         QS3_TRY(wbuf.alloc(std::max<uint64_t>(D, 1) * sizeof(VT)));
         QS3_TRY(hinb.alloc(std::max<uint64_t>(D, 1) * sizeof(VT)));
@@ -903,12 +1182,24 @@ struct Engine64 {
         QS3_TRY(nrm1.alloc((uint64_t)B.S * sizeof(double2)));
         QS3_TRY(inv.alloc((uint64_t)B.S * sizeof(double)));
         QS3_TRY(active.alloc((uint64_t)B.S * sizeof(int)));
+        QS3_TRY(derr.alloc(sizeof(int)));
+        QS3_CUDA(cudaMemsetAsync(derr.p, 0, sizeof(int), st));
+        QS3_TRY(dotb_prepare<VT>());
         QS3_CUDA(cudaMemsetAsync(alpha.p, 0, alpha.n, st));
         QS3_CUDA(cudaMemsetAsync(beta.p, 0, beta.n, st));
         h_active.assign(B.S, 0);
         for (int s = 0; s < B.S; ++s) h_active[s] = B.dims[s] > 0;
         QS3_TRY(push_active());
         return tune_dots();
+    }
+    // QS3_ERR_TIMEOUT if a bounded device wait of the dot pass ran out
+    // (synchronises the stream)
+    int check_err() {
+        int e = 0;
+        QS3_CUDA(cudaMemcpyAsync(&e, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        QS3_CUDA(cudaStreamSynchronize(st));
+        if (e) return set_err(QS3_ERR_TIMEOUT, "a wait of the dot pass (k_dotb) ran out");
+        return QS3_OK;
     }
     int push_active() {
         QS3_CUDA(cudaMemcpyAsync(active.p, h_active.data(), B.S * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -933,7 +1224,7 @@ struct Engine64 {
         const VT *w = wv();
         if (!strict)
             return dotx_launch<VT>(nv, dg(), ge(), B.nchunks, D, j0, m, w, secs(), c0(), B.S, act(),
-                                   partx.as<long long>(), st, dx, ring);
+                                   partx.as<long long>(), st, dx, ring, derr.as<int>());
         k_dot64<VT, 2><<<grid(), NTHREADS, 0, st>>>(v, D, j0, m, w, secs(), c0(), B.S, act(), part.as<double2>(), dx,
                                                      ring);
         QS3_LAUNCHED();
@@ -950,8 +1241,9 @@ struct Engine64 {
         QS3_TRY(dot_launch(B.tune_nv64 > 0 ? B.tune_nv64 : 2, j0, m));
         return dot_reduce(m, out, ldo);
     }
-    // the staging depth of k_dot64: time 1, 2 and 4 vectors per pass on
-    // min(cap, 48) zeroed slots and keep the fastest for this basis
+    // the dot pass: time k_dotx with 1, 2 and 4 vectors per pass and the
+    // k_dotb ring (8) on min(cap, 48) zeroed slots and keep the fastest
+    // for this basis
     int tune_dots() {
         if (B.tune_nv64 != 0 || B.nchunks == 0) return QS3_OK;
         cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
@@ -967,7 +1259,7 @@ struct Engine64 {
         QS3_CUDA(cudaEventCreate(&e1));
         float best = 1e30f;
         int bnv = 2, rc = QS3_OK;
-        for (int nv : {1, 2, 4}) {
+        for (int nv : {1, 2, 4, 8}) {
             float tmin = 1e30f;
             for (int rep = 0; rep < 4 && rc == QS3_OK; ++rep) {
                 if (cudaEventRecord(e0, st) != cudaSuccess) { rc = QS3_ERR_CUDA; break; }

@@ -1254,6 +1254,7 @@ struct Engine {
         QS3_TRY(push_active());
         return tune_dots();
     }
+    int check_err() { return QS3_OK; }     // no bounded device waits here
     int push_active() {
         QS3_CUDA(cudaMemcpyAsync(active.p, h_active.data(), B.S * sizeof(int), cudaMemcpyHostToDevice, st));
         return QS3_OK;
@@ -2222,6 +2223,7 @@ static int lanczos_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT
     QS3_CUDA(cudaMemcpyAsync(coef.data(), K.coef.p, coef.size() * 8, cudaMemcpyDeviceToHost, st));
     QS3_CUDA(cudaMemcpyAsync(&nzd, K.nnz.p, 8, cudaMemcpyDeviceToHost, st));
     QS3_CUDA(cudaStreamSynchronize(st));
+    QS3_TRY(E.check_err());
     QS3_TRY(hs.harvest());
     hs.nnz = nz0 + nzd;
     if (log_on())
@@ -2411,7 +2413,7 @@ static int trl_run(Basis &B, const qs3_solve_opts &o, const typename Wide<VT>::T
         QS3_TRY(finish(rest));
     }
     R.steps = steps;
-    return QS3_OK;
+    return E.check_err();
 }
 
 // ------------------------------------------------------------- entry points
@@ -2620,7 +2622,7 @@ static int gs_dots_run(Basis &B, int m, const VT *V, uint64_t ldv, const VT *w, 
     const uint64_t D = B.total;
     memset(out, 0, (size_t)B.S * m * 2 * sizeof(double));
     if (m == 0 || B.nchunks == 0) return QS3_OK;
-    DevBuf pl, dgt, get, part, res, dsl, pr;
+    DevBuf pl, dgt, get, part, res, dsl, pr, derr;
     QS3_TRY(pl.alloc((uint64_t)m * D * sizeof(VT)));
     QS3_TRY(part.alloc((uint64_t)B.nchunks * m * (mode == 0 ? XW * 3 * sizeof(long long) : sizeof(double2))));
     QS3_TRY(res.alloc((uint64_t)B.S * m * sizeof(double2)));
@@ -2633,13 +2635,16 @@ static int gs_dots_run(Basis &B, int m, const VT *V, uint64_t ldv, const VT *w, 
     const int *c0 = B.d_chunk0.as<int>();
     if (mode == 0) {
         using G = typename DigT<VT>::T;
-        QS3_TRY(dgt.alloc((uint64_t)m * D * sizeof(VT)));
+        QS3_TRY(dgt.alloc((uint64_t)m * D * sizeof(VT) + 16));      // k_dotb reads up to 16 bytes past
         QS3_TRY(get.alloc((uint64_t)m * B.nchunks * XW * sizeof(int)));
+        QS3_TRY(derr.alloc(sizeof(int)));
+        QS3_CUDA(cudaMemsetAsync(derr.p, 0, sizeof(int), st));
+        QS3_TRY(dotb_prepare<VT>());
         k_digitize<VT><<<dim3(B.nchunks, m), XT, 0, st>>>(pl.as<T>(), D, 0, dgt.as<G>(), get.as<int>(), B.nchunks,
                                                            secs, c0, B.S);
         QS3_LAUNCHED();
-        QS3_TRY(dotx_launch<VT>(2, dgt.as<G>(), get.as<int>(), B.nchunks, D, 0, m, w, secs, c0, B.S, nullptr,
-                                part.as<long long>(), st));
+        QS3_TRY(dotx_launch<VT>(B.tune_nv64 > 0 ? B.tune_nv64 : 2, dgt.as<G>(), get.as<int>(), B.nchunks, D, 0, m,
+                                w, secs, c0, B.S, nullptr, part.as<long long>(), st, nullptr, 0, derr.as<int>()));
         const std::vector<int> s0 = reduce_slices(B);
         QS3_TRY(dsl.upload(s0.data(), s0.size() * sizeof(int)));
         QS3_TRY(pr.alloc((uint64_t)std::max(s0[B.S], 1) * m * 5 * sizeof(long long)));
@@ -2654,7 +2659,10 @@ static int gs_dots_run(Basis &B, int m, const VT *V, uint64_t ldv, const VT *w, 
         QS3_LAUNCHED();
     }
     QS3_CUDA(cudaMemcpyAsync(out, res.p, (size_t)B.S * m * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    int e = 0;
+    if (derr.p) QS3_CUDA(cudaMemcpyAsync(&e, derr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     QS3_CUDA(cudaStreamSynchronize(st));
+    if (e) return set_err(QS3_ERR_TIMEOUT, "a wait of the dot pass (k_dotb) ran out");
     return QS3_OK;
 }
 
@@ -2765,6 +2773,7 @@ int dsf_run(int op, Basis &S, int ss, const void *gs, double e0, Basis &Dd, int 
     }
     QS3_TRY(E.push_active());
     for (int x = 0; x < n_iter && E.any_active(); ++x) QS3_TRY(E.step(x));
+    QS3_TRY(E.check_err());
     std::vector<double> a, b;
     QS3_TRY(E.fetch(a, b));
     std::vector<int> msz(nq, 0);

@@ -158,3 +158,40 @@ def test_gs_dots_many_slices():
     for j in range(2):
         ex = _exact_dot(V[j], w)
         assert abs(got[0, j] - ex) <= _bound(V[j], w), (j, got[0, j], ex)
+
+
+@pytest.mark.parametrize("name,spec,nd,Ks", [
+    ("square8_k", qi.square(8), 4, [(0, 0, 0), (1, 2, 0), (4, 4, 0)]),
+    ("square6_k_odd", qi.square(6), 3, [(0, 0, 0), (1, 0, 0), (2, 1, 0)]),
+    ("chain21_u1_odd", qi.chain(21, Jz=0.5), 5, None),
+])
+def test_gs_dots_copy_ring_identical(name, spec, nd, Ks):
+    """The dot pass with the stored vectors' digits brought in by bulk copies
+    into a ring in shared memory (k_dotb: dot_vectors64 = 8) sums the
+    same integer products as the register-staged pass (k_dotx): the results
+    agree bit for bit, and stay within the grid bound of the exact dots.
+    Odd dimensions put the digit planes and sector starts off the 16-byte
+    boundary, so the copies start below the chunk."""
+    torch = torch_cuda()
+    b = lib_basis(spec, nd, Ks)
+    cx = Ks is not None
+    esz = 8 if cx else 4                      # bytes of one element of a digit plane
+    if name.endswith("_odd"):
+        assert (b.total_dim * esz) % 16 != 0
+        assert Ks is None or any((o * esz) % 16 for o in b.offsets)
+    V, w = _vectors(b.total_dim, cx, seed=11)
+    dt = torch.complex128 if cx else torch.float64
+    Vd, wd = to_dev(V, dt), to_dev(w, dt)
+    got = {}
+    for nv in (2, 8):
+        b.tuning(dot_vectors64=nv)
+        got[nv] = b.gs_dots(Vd, wd, exact=True)
+        assert b.tuning()["dot_vectors64"] == nv
+    np.testing.assert_array_equal(got[8], got[2])
+    for s in range(b.n_sectors):
+        lo, hi = b.offsets[s], b.offsets[s + 1]
+        for j in range(V.shape[0]):
+            ex = _exact_dot(V[j, lo:hi], w[lo:hi])
+            bd = _bound(V[j, lo:hi], w[lo:hi])
+            assert abs(np.real(got[8][s, j]) - np.real(ex)) <= bd, (name, s, j)
+            assert abs(np.imag(got[8][s, j]) - np.imag(ex)) <= bd, (name, s, j)

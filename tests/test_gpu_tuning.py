@@ -43,9 +43,11 @@ def test_dot_staging_choices_identical(prec, key):
     b = _basis()
     o = qs3.SolveOpts(n_max=60, eps=1e-12, res_tol=1e-10, use_graphs=False, precision=prec)
     e_auto, _, _ = b.lanczos(o, vectors=False)
-    assert b.tuning()[key] in (1, 2, 4)
+    # the binary64 engine also has the copy-engine ring of k_dotb (8)
+    choices = (1, 2, 4, 8) if key == "dot_vectors64" else (1, 2, 4)
+    assert b.tuning()[key] in choices
     res = []
-    for nv in (1, 2, 4):
+    for nv in choices:
         b.tuning(**{key: nv})
         e, _, info = b.lanczos(o, vectors=False)
         res.append((e, info["iterations"]))
@@ -63,5 +65,9 @@ def test_tuning_rejects_bad_values():
         b.tuning(dot_vectors=3)
     with pytest.raises(qs3.QS3Error):
         b.tuning(dot_vectors64=5)
+    with pytest.raises(qs3.QS3Error):
+        b.tuning(dot_vectors64=16)
+    with pytest.raises(qs3.QS3Error):
+        b.tuning(dot_vectors=8)
     with pytest.raises(qs3.QS3Error):
         b.tuning(hphi_blocks_per_sm=[-1, 0, 0, 0])
