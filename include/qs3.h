@@ -150,7 +150,8 @@ int qs3_basis_rep_table(qs3_basis_t b, int32_t mode, int32_t *active);
  *     per pass (loads in flight together): dot_vectors for the double-float
  *     engine and the fp32 phase, dot_vectors64 for the binary64 engine, which
  *     also has 8: the stored vectors' digits copied by bulk asynchronous
- *     copies (TMA) into a six-stage ring in shared memory (k_dotb).
+ *     copies (TMA) into rings in shared memory, for the dot pass (k_dotb)
+ *     and for the Gram-Schmidt update (k_updb).
  * set = 0: write the current choices (0 = not tuned yet) to
  *          hphi_blocks_per_sm[5] (indexed by qs3_dtype), *dot_vectors and
  *          *dot_vectors64;

@@ -981,6 +981,351 @@ __global__ void __launch_bounds__(XT)
     }
 }
 
+// |x| with its significand truncated to 24 bits, as a float (0 below the
+// normal fp32 range and above 2^54, where the square would leave the fp32
+// range): never above |x|
+__device__ __forceinline__ float f_trunc_abs(double x) {
+    const int hi = __double2hiint(x);
+    const int e = ((hi >> 20) & 0x7ff) - 896;               // the float's biased exponent
+    if (e <= 0 || e > 181) return 0.f;
+    return __int_as_float((e << 23) | ((hi & 0xfffff) << 3) | ((unsigned)__double2loint(x) >> 29));
+}
+
+// The three-term part of a step (Alg. 10): w -= sum_j psi_{j0+j} coef[s][j]
+// for m <= 2 stored vectors, in binary64 FMAs in the order of k_upd64, and
+// part[c] = a lower estimate of |w|^2 over chunk c (values truncated to 24
+// bits, squared and summed in fp32, the sum lowered by 2^-18 of itself): it
+// only feeds the test of the fp32 Gram-Schmidt correction, which a low |w|
+// makes stricter.  Two blocks per SM, so that one block's FMAs (the fp64
+// pipe is the bound) overlap another's loads.  Graph mode (dx): the range of
+// graph_range and, for the three-term pass (ring), coefficients from coef + j0.
+template <typename VT>
+__global__ void __launch_bounds__(XT, 2)
+    k_upd3(VT *__restrict__ w, const typename PlS<VT>::T *__restrict__ V, uint64_t D, int j0, int m,
+           const double2 *__restrict__ coef, int ldc, const SecView *__restrict__ secs,
+           const int *__restrict__ chunk0, int S, const int *__restrict__ active, double2 *__restrict__ part,
+           const int *__restrict__ dx = nullptr, int ring = 0) {
+    using T = typename PlS<VT>::T;
+    constexpr bool CX = IsC<VT>::v;
+    if (dx) {
+        graph_range(dx, ring, j0, m);
+        if (ring) coef += j0;
+    }
+    __shared__ float red[XW];
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = (ci.n - (int)threadIdx.x + XT - 1) / XT;
+    const uint64_t r0 = ci.base + threadIdx.x;
+    double2 acc[XR];
+#pragma unroll
+    for (int k = 0; k < XR; ++k) acc[k] = k < nk ? ld2(w + r0 + (uint64_t)k * XT) : make_double2(0.0, 0.0);
+    double2 a[2][XR];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const T *slot = V + (uint64_t)(j0 + j) * 2 * D;
+#pragma unroll
+        for (int k = 0; k < XR; ++k)
+            a[j][k] = (j < m && k < nk) ? pl_ld(slot, D, r0 + (uint64_t)k * XT) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        if (j < m) {
+            const double2 c = coef[(uint64_t)ci.s * ldc + j];
+#pragma unroll
+            for (int k = 0; k < XR; ++k) {
+                if (k < nk) {
+                    acc[k].x = fma(-a[j][k].x, c.x, acc[k].x);
+                    if (CX) {
+                        acc[k].x = fma(a[j][k].y, c.y, acc[k].x);
+                        acc[k].y = fma(-a[j][k].x, c.y, acc[k].y);
+                        acc[k].y = fma(-a[j][k].y, c.x, acc[k].y);
+                    }
+                }
+            }
+        }
+    }
+    float nf = 0.f;
+#pragma unroll
+    for (int k = 0; k < XR; ++k) {
+        if (k < nk) {
+            st2(w + r0 + (uint64_t)k * XT, acc[k]);
+            const float fx = f_trunc_abs(acc[k].x);
+            nf = fmaf(fx, fx, nf);
+            if (CX) {
+                const float fy = f_trunc_abs(acc[k].y);
+                nf = fmaf(fy, fy, nf);
+            }
+        }
+    }
+    if (part) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) nf += __shfl_xor_sync(0xffffffffu, nf, o);
+        if (lane == 0) red[warp] = nf;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < XW; ++q) t += (double)red[q];
+            part[blockIdx.x] = make_double2(t * (1.0 - 0x1p-18), 0.0);
+        }
+    }
+}
+
+// The Gram-Schmidt update with the stored vectors' top digits brought in by
+// TMA bulk copies (k_updb): the arithmetic of k_upd64 (the same lite test,
+// the fp32 correction from the P1 digits summed in the same order, w - u in
+// binary64; the binary64 FMA path when the test fails), with a copy warp
+// (warp XW) filling a ring of ns stages, each the chunk's slice of the P1
+// plane of one stored vector (from the 16-byte boundary at or below the
+// chunk, rounded up to 16 bytes) and its XW group exponents.  Dynamic shared
+// memory: the ring, then the m coefficients and their fp32 copies.  Waits
+// are bounded as in k_dotb (a wait that runs out sets *err; the block still
+// writes w and its norm, both finite).  starve != 0: the copy warp issues
+// nothing (the test injection).  Graph mode (dx): the range of graph_range.
+constexpr int UB_NSMAX = 24;
+constexpr int UPDB_SMEM = 110 * 1024;          // dynamic shared memory per block (two blocks per SM)
+template <typename VT> constexpr unsigned updb_stage() { return dotb_slice<VT>() + XW * 4; }
+
+__device__ __forceinline__ void bar_consumers() { asm volatile("bar.sync 1, %0;" ::"r"(XT) : "memory"); }
+
+template <typename VT>
+__global__ void __launch_bounds__(XT + 32, 2)
+    k_updb(VT *__restrict__ w, const typename PlS<VT>::T *__restrict__ V, const typename DigT<VT>::T *__restrict__ dg,
+           const int *__restrict__ ge, int nchunks, uint64_t D, int j0, int m, int ns,
+           const double2 *__restrict__ coef, int ldc, const SecView *__restrict__ secs,
+           const int *__restrict__ chunk0, int S, const int *__restrict__ active, const double2 *__restrict__ wn2,
+           double2 *__restrict__ part, int *__restrict__ err, int starve, const int *__restrict__ dx = nullptr) {
+    using G = typename DigT<VT>::T;
+    using T = typename PlS<VT>::T;
+    constexpr bool CX = IsC<VT>::v;
+    constexpr unsigned SL = dotb_slice<VT>(), SB = updb_stage<VT>();
+    extern __shared__ __align__(128) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t full[UB_NSMAX], empty[UB_NSMAX];
+    __shared__ double red[XW];
+    __shared__ int lite_s;
+    graph_range(dx, 0, j0, m);
+    double2 *scd = (double2 *)(dsm + (size_t)ns * SB);
+    float2 *scf = (float2 *)(scd + m);
+    const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
+    if (active && !active[ci.s]) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int t = 0; t < ns; ++t) {
+            mbar_init(&full[t], 1);
+            mbar_init(&empty[t], XW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // the copy warp fills the first stages at once (most passes take the fp32
+    // correction) and the consumers fetch their rows of w, both while the
+    // coefficients are read and the test below is taken
+    auto plane1 = [&](int jj) { return dg + (uint64_t)(j0 + jj) * 2 * D + ci.base; };
+    const unsigned nb = (unsigned)ci.n * (unsigned)sizeof(G);
+    int issued = 0;
+    auto issue = [&](int t) {
+        unsigned char *sp = dsm + (size_t)t * SB;
+        const G *p1 = plane1(issued);
+        const unsigned o1 = (unsigned)((uintptr_t)p1 & 15u);
+        const unsigned b1 = (o1 + nb + 15u) & ~15u;
+        mbar_expect_tx(&full[t], b1 + XW * 4);
+        bulk_g2s(sp, (const unsigned char *)p1 - o1, b1, &full[t]);
+        bulk_g2s(sp + SL, ge + ((uint64_t)(j0 + issued) * nchunks + blockIdx.x) * XW, XW * 4, &full[t]);
+        ++issued;
+    };
+    if (warp == XW && lane == 0 && wn2 && !starve)
+        while (issued < m && issued < ns) issue(issued);
+    const int nk = (ci.n - (int)threadIdx.x + XT - 1) / XT;
+    const uint64_t r0 = ci.base + threadIdx.x;
+    double2 wr[XR];
+    // the coefficients, their fp32 copies and the lite test (as k_upd64)
+    if (warp < XW) {
+#pragma unroll
+        for (int k = 0; k < XR; ++k) wr[k] = k < nk ? ld2(w + r0 + (uint64_t)k * XT) : make_double2(0.0, 0.0);
+        double cs = 0.0;
+        for (int j = threadIdx.x; j < m; j += XT) {
+            const double2 c = coef[(uint64_t)ci.s * ldc + j];
+            scd[j] = c;
+            scf[j] = make_float2((float)c.x, (float)c.y);
+            cs += fabs(c.x) + fabs(c.y);
+        }
+        if (m > 32) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+            if (lane == 0) red[warp] = cs;
+        } else if (warp == 0) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+            if (lane == 0) red[0] = cs;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        const int nw = m > 32 ? XW : 1;
+        for (int q = 0; q < nw; ++q) t += red[q];
+        const double lim = m > 256 ? 0x1p-80 * (256.0 / m) * (256.0 / m) : 0x1p-80;
+        lite_s = (wn2 && t * t <= lim * wn2[ci.s].x) ? 1 : 0;
+    }
+    __syncthreads();
+    const bool lite = lite_s != 0;
+    if (warp == XW) {
+        // the copy warp: the rest of the ring for the fp32 correction; the
+        // binary64 path reads no digits (the stages in flight land first)
+        if (lane == 0) {
+            bool ok = true;
+            int t = issued % ns;
+            unsigned q = (unsigned)(issued / ns - 1) & 1u;     // parity of the empty phase to wait for
+            for (; lite && issued < m && !starve;) {
+                if (!mbar_wait(&empty[t], q)) {
+                    ok = false;
+                    break;
+                }
+                issue(t);
+                if (++t == ns) {
+                    t = 0;
+                    q ^= 1u;
+                }
+            }
+            if (!ok) atomicExch(err, 1);
+            for (int jj = issued - ns > 0 ? issued - ns : 0; jj < issued; ++jj)
+                mbar_wait(&full[jj % ns], (unsigned)(jj / ns) & 1u);
+        }
+        return;
+    }
+    double nrm = 0.0;
+    if (lite) {
+        // stored vector j, row: psi ~ (P1 / 32) 2^(em - 1044), as in k_upd64
+        const unsigned ob1 = (unsigned)((uintptr_t)plane1(0) & 15u);
+        const unsigned osl = (unsigned)(2 * D * sizeof(G)) & 15u;
+        float2 u[XR];
+#pragma unroll
+        for (int k = 0; k < XR; ++k) u[k] = make_float2(0.f, 0.f);
+        // two stored vectors per pass; the stage index t and the phase parity
+        // q advance with the pass (no division by the runtime ring depth)
+        auto corr = [&](const G (&h)[XR], int em, int jj) {
+            const int ex = em - 1044 + 127;
+            const float sc = (ex >= 1 && ex <= 254) ? __int_as_float(ex << 23) : 0.f;
+            const float2 c0 = scf[jj];
+            const float2 c = make_float2(c0.x * sc, c0.y * sc);
+#pragma unroll
+            for (int k = 0; k < XR; ++k) {
+                const float2 a = p1_f2(h[k]);
+                u[k].x = fmaf(a.x, c.x, u[k].x);
+                if (CX) {
+                    u[k].x = fmaf(-a.y, c.y, u[k].x);
+                    u[k].y = fmaf(a.x, c.y, u[k].y);
+                    u[k].y = fmaf(a.y, c.x, u[k].y);
+                }
+            }
+        };
+        int t = 0;
+        unsigned q = 0;
+#pragma unroll 1
+        for (int jj = 0; jj < m; jj += 2) {
+            const bool two = jj + 1 < m;
+            const int t1 = t + 1 == ns ? 0 : t + 1;
+            const unsigned q1 = t + 1 == ns ? q ^ 1u : q;
+            bool ok = true;
+            if (lane == 0) {
+                ok = mbar_wait(&full[t], q);
+                if (ok && two) ok = mbar_wait(&full[t1], q1);
+            }
+            if (!__shfl_sync(0xffffffffu, (int)ok, 0)) {
+                if (lane == 0) atomicExch(err, 1);
+                break;
+            }
+            mbar_try(&full[t], q);
+            if (two) mbar_try(&full[t1], q1);
+            const unsigned char *s0 = dsm + (size_t)t * SB, *s1 = dsm + (size_t)t1 * SB;
+            const G *pa = (const G *)(s0 + ((ob1 + (unsigned)jj * osl) & 15u));
+            const G *pb = (const G *)(s1 + ((ob1 + (unsigned)(jj + 1) * osl) & 15u));
+            G h0[XR], h1[XR];
+#pragma unroll
+            for (int k = 0; k < XR; ++k) {
+                h0[k] = k < nk ? pa[threadIdx.x + k * XT] : G{};
+                h1[k] = (two && k < nk) ? pb[threadIdx.x + k * XT] : G{};
+            }
+            const int em0 = ((const int *)(s0 + SL))[warp];
+            const int em1 = two ? ((const int *)(s1 + SL))[warp] : 0;
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&empty[t]);
+                if (two) mbar_arrive(&empty[t1]);
+            }
+            corr(h0, em0, jj);
+            if (two) corr(h1, em1, jj + 1);
+            t = t1 + 1 == ns ? 0 : t1 + 1;
+            q = t1 + 1 == ns ? q1 ^ 1u : q1;
+        }
+#pragma unroll
+        for (int k = 0; k < XR; ++k) {
+            if (k < nk) {
+                const uint64_t r = r0 + (uint64_t)k * XT;
+                double2 v = wr[k];
+                v.x -= (double)u[k].x;
+                if (CX) v.y -= (double)u[k].y;
+                st2(w + r, v);
+                nrm = fma(v.x, v.x, nrm);
+                if (CX) nrm = fma(v.y, v.y, nrm);
+            }
+        }
+    } else {
+        double2 acc[XR];
+#pragma unroll
+        for (int k = 0; k < XR; ++k) acc[k] = wr[k];
+#pragma unroll 2
+        for (int j = 0; j < m; ++j) {
+            const double2 c = scd[j];
+            const T *slot = V + (uint64_t)(j0 + j) * 2 * D;
+#pragma unroll
+            for (int k = 0; k < XR; ++k) {
+                if (k < nk) {
+                    const double2 a = pl_ld(slot, D, r0 + (uint64_t)k * XT);
+                    acc[k].x = fma(-a.x, c.x, acc[k].x);
+                    if (CX) {
+                        acc[k].x = fma(a.y, c.y, acc[k].x);
+                        acc[k].y = fma(-a.x, c.y, acc[k].y);
+                        acc[k].y = fma(-a.y, c.x, acc[k].y);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < XR; ++k) {
+            if (k < nk) {
+                st2(w + r0 + (uint64_t)k * XT, acc[k]);
+                nrm = fma(acc[k].x, acc[k].x, nrm);
+                if (CX) nrm = fma(acc[k].y, acc[k].y, nrm);
+            }
+        }
+    }
+    if (part) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+        bar_consumers();                          // red is reused
+        if (lane == 0) red[warp] = nrm;
+        bar_consumers();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < XW; ++q) t += red[q];
+            part[blockIdx.x] = make_double2(t, 0.0);
+        }
+    }
+}
+
+// the ring depth of k_updb for up to mmax coefficients (0: k_upd64 instead)
+template <typename VT> static int updb_ns(int mmax) {
+    const long long ns = ((long long)UPDB_SMEM - (long long)mmax * 24) / (long long)updb_stage<VT>();
+    return ns >= 2 ? (int)std::min<long long>(ns, UB_NSMAX) : 0;
+}
+template <typename VT> static int updb_prepare() {
+    static const cudaError_t e =
+        cudaFuncSetAttribute(k_updb<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, UPDB_SMEM);
+    QS3_CUDA(e);
+    return QS3_OK;
+}
+
 // psi_{x+1} = w * inv[s]: into the store's slot (graph mode: slot *dx + 1 of
 // the store at out), its digit-store image (dg, ge) and hin, the interleaved
 // input of the next H Phi.  w may alias hin (the start vector is normalised
@@ -1185,6 +1530,7 @@ struct Engine64 {
         QS3_TRY(derr.alloc(sizeof(int)));
         QS3_CUDA(cudaMemsetAsync(derr.p, 0, sizeof(int), st));
         QS3_TRY(dotb_prepare<VT>());
+        QS3_TRY(updb_prepare<VT>());
         QS3_CUDA(cudaMemsetAsync(alpha.p, 0, alpha.n, st));
         QS3_CUDA(cudaMemsetAsync(beta.p, 0, beta.n, st));
         h_active.assign(B.S, 0);
@@ -1281,10 +1627,32 @@ struct Engine64 {
         B.tune_nv64 = bnv;
         return QS3_OK;
     }
+    // the Gram-Schmidt update runs k_updb (the copy ring) with the copy-ring
+    // dot pass (dot_vectors64 = 8), when the fp32 correction is possible
+    // (wn2 given, strict64 off), the pass is longer than the three-term one
+    // and the ring fits beside mmax coefficients
+    bool updb_ok(const double2 *wn2, int m, int mmax) const {
+        return B.tune_nv64 == 8 && !strict && wn2 && m > 2 && updb_ns<VT>(mmax) > 0;
+    }
     // w -= sum_j psi_{j0+j} cf[s][j]; nrm_out: per-sector |w|^2 after it;
     // wn2: |w|^2 before it (enables the fp32 correction of tiny coefficients)
     int mupdate(int j0, int m, const double2 *cf, int ldc, double2 *nrm_out, const double2 *wn2 = nullptr) {
         if (B.nchunks == 0) return QS3_OK;
+        if (!wn2 && m <= 2) {
+            // the three-term part: its |w|^2 only feeds the test of the next pass
+            k_upd3<VT><<<grid(), XT, 0, st>>>(wv(), V.as<ST>(), D, j0, m, cf, ldc, secs(), c0(), B.S, act(),
+                                              part.as<double2>());
+            QS3_LAUNCHED();
+            return reduce(1, nrm_out, 1);
+        }
+        if (updb_ok(wn2, m, m)) {
+            const int ns = updb_ns<VT>(m);
+            k_updb<VT><<<grid(), XT + 32, (size_t)ns * updb_stage<VT>() + (size_t)m * 24, st>>>(
+                wv(), V.as<ST>(), dg(), ge(), B.nchunks, D, j0, m, ns, cf, ldc, secs(), c0(), B.S, act(), wn2,
+                part.as<double2>(), derr.as<int>(), take_wait_injection());
+            QS3_LAUNCHED();
+            return reduce(1, nrm_out, 1);
+        }
         k_upd64<VT><<<grid(), XT, (size_t)m * (sizeof(double2) + sizeof(float2)), st>>>(
             wv(), V.as<ST>(), dg(), ge(), B.nchunks, D, j0, m, cf, ldc, secs(), c0(), B.S, act(), wn2, strict,
             part.as<double2>());
@@ -1360,16 +1728,22 @@ struct Engine64 {
         QS3_TRY(hphi_apply(0, dx));
         QS3_TRY(dot_launch(2, 0, 2, dx, 1));
         QS3_TRY(dot_reduce(2, hh1, cap, dx, 1, 2));
-        k_upd64<VT><<<grid(), XT, 2 * (sizeof(double2) + sizeof(float2)), st>>>(
-            w, V.as<ST>(), dg(), ge(), B.nchunks, D, 0, 2, hh1, cap, secs(), c0(), B.S, act(), nullptr, strict,
-            part.as<double2>(), dx, 1);
+        k_upd3<VT><<<grid(), XT, 0, st>>>(w, V.as<ST>(), D, 0, 2, hh1, cap, secs(), c0(), B.S, act(),
+                                          part.as<double2>(), dx, 1);
         QS3_LAUNCHED();
         QS3_TRY(reduce(1, n1, 1));
         QS3_TRY(dot_launch(B.tune_nv64 > 0 ? B.tune_nv64 : 2, 0, cap, dx, 0));
         QS3_TRY(dot_reduce(cap, h2.as<double2>(), cap, dx, 0, cap));
-        k_upd64<VT><<<grid(), XT, (size_t)cap * (sizeof(double2) + sizeof(float2)), st>>>(
-            w, V.as<ST>(), dg(), ge(), B.nchunks, D, 0, cap, h2.as<double2>(), cap, secs(), c0(), B.S, act(), n1,
-            strict, part.as<double2>(), dx, 0);
+        if (updb_ok(n1, cap, cap)) {
+            const int ns = updb_ns<VT>(cap);
+            k_updb<VT><<<grid(), XT + 32, (size_t)ns * updb_stage<VT>() + (size_t)cap * 24, st>>>(
+                w, V.as<ST>(), dg(), ge(), B.nchunks, D, 0, cap, ns, h2.as<double2>(), cap, secs(), c0(), B.S, act(),
+                n1, part.as<double2>(), derr.as<int>(), take_wait_injection(), dx);
+        } else {
+            k_upd64<VT><<<grid(), XT, (size_t)cap * (sizeof(double2) + sizeof(float2)), st>>>(
+                w, V.as<ST>(), dg(), ge(), B.nchunks, D, 0, cap, h2.as<double2>(), cap, secs(), c0(), B.S, act(), n1,
+                strict, part.as<double2>(), dx, 0);
+        }
         QS3_LAUNCHED();
         QS3_TRY(reduce(1, nrm.as<double2>(), 1));
         k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, 0, cap, hh1, nrm.as<double2>(), act(),
