@@ -64,10 +64,11 @@ def load_peaks():
 # bytes (dram__bytes_read.sum + dram__bytes_write.sum) over the launch's
 # algorithmic bytes; the ratio scales to the launches of a run (None: not
 # captured since the kernel last changed).
-GS_PROFILE = {"kernel": "k_dotx<complex> (exact fixed-point Gram-Schmidt dot products)",
-              # (578.4 MB read + 8.9 MB written) / 577.0 MB algorithmic, 20 sectors, 45 stored vectors
-              "dram_over_alg": 1.0179,
-              "profile": "profiles/k_dotx_square10x10_nd4_20k.md"}
+GS_PROFILE = {"kernel": "k_dotb<complex> (exact fixed-point Gram-Schmidt dot products, digits through a "
+                        "shared-memory ring filled by bulk copies)",
+              # (540.7 MB read + 8.6 MB written) / 539.4 MB algorithmic, 20 sectors, 42 stored vectors
+              "dram_over_alg": 1.0184,
+              "profile": "profiles/k_dotb_square10x10_nd4_20k.md"}
 
 WORKLOADS = {
     # name: (lattice factory, n_down, momenta)
@@ -175,6 +176,8 @@ def run_ours(args, rank, world):
     spec = mk()
     Ks = sector_subset(ks(), args.sectors)
     basis = qs3.Basis(spec, nd, Ks)
+    if args.dot_vectors64:
+        basis.tuning(dot_vectors64=args.dot_vectors64)
     nnz_h = basis.nnz()
     stream = torch.cuda.current_stream()
     # the pipes' measured throughput: the fp64 FMA rate is the roof of the
@@ -235,7 +238,7 @@ def run_ours(args, rank, world):
     # algorithmic bytes of one full launch: diagonal read, one gather per term,
     # psi write, sigma row rank, one sigma probe per term
     B_alg = frac_work * (D * s_phi + (nnz_h - D) * s_phi + D * s_phi + D * 8 + (nnz_h - D) * 8)
-    hphi = {"kernel": "k_hphi_x (complex128, products on the integer units, representative table)", "full_launch_ms": round(1e3 * t_launch / frac_work, 4),
+    hphi = {"kernel": "k_hphi_o (complex128, products on the integer units, orbit-batched over the sectors)", "full_launch_ms": round(1e3 * t_launch / frac_work, 4),
             "avg_launch_ms": round(1e3 * t_launch, 4), "launch_gnnz_s": round(per_launch_nnz / t_launch / 1e9, 2),
             "alg_gbs": round(B_alg / t_launch / 1e9, 1), "hbm_frac_alg": round(B_alg / t_launch / 1e9 / hbm_peak, 4),
             "share_of_step": round(hphi_s / t_local, 3)}
@@ -795,6 +798,8 @@ def main():
     ap.add_argument("--dtype", default="c128", choices=["c128", "c128df", "c64", "f64", "f32"], help="--mode hphi only")
     ap.add_argument("--workload", default="square10x10_nd4_all_k", choices=sorted(WORKLOADS))
     ap.add_argument("--n-max", dest="n_max", type=int, default=250)
+    ap.add_argument("--dot-vectors64", dest="dot_vectors64", type=int, default=0,
+                    help="impose the binary64 dot pass (1, 2, 4: k_dotx vectors per pass; 8: the copy rings); 0 tunes")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e / fp32 / cpu_baseline legs")
     ap.add_argument("--sectors", type=int, default=0,
                     help="solve only the first N momentum sectors (a small case for profiling; 0 = all)")

@@ -451,6 +451,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity) {
         if (gtimer() - t0 > MB_NS) return false;
     return true;
 }
+// orders this thread's view of earlier generic-proxy accesses to shared
+// memory (the consumers' reads of a stage, observed through its empty
+// barrier) before the bulk copies it issues next (async proxy)
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                  ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
@@ -504,9 +508,12 @@ __global__ void __launch_bounds__(XT + 32, 1)
             bool ok = true;
             for (; issued < m && !starve; ++issued) {
                 const int t = issued % NS;
-                if (issued >= NS && !mbar_wait(&empty[t], (unsigned)(issued / NS - 1) & 1u)) {
-                    ok = false;
-                    break;
+                if (issued >= NS) {
+                    if (!mbar_wait(&empty[t], (unsigned)(issued / NS - 1) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_proxy_async();
                 }
                 unsigned char *sp = dsm + (size_t)t * SB;
                 const G *p1 = plane(issued, 0), *p0 = plane(issued, 1);
@@ -635,6 +642,12 @@ static inline std::vector<int> reduce_slices(const Basis &B) {
     }
     return s0;
 }
+// every sector has exactly one slice (the first level then finishes)
+static inline bool one_slice(const std::vector<int> &s0) {
+    for (size_t s = 0; s + 1 < s0.size(); ++s)
+        if (s0[s + 1] - s0[s] != 1) return false;
+    return s0.size() > 1;
+}
 
 __device__ __forceinline__ __int128 align_round(__int128 v, int d) {
     if (d <= 0) return v;
@@ -646,10 +659,12 @@ __device__ __forceinline__ __int128 align_round(__int128 v, int d) {
 // and coefficient j; one warp per coefficient (graph mode: graph_range)
 __global__ void k_reducex1(const long long *__restrict__ part, int m, const int *__restrict__ chunk0,
                            const int *__restrict__ slice0, int S, const int *__restrict__ active,
-                           long long *__restrict__ out1, const int *__restrict__ dx, int ring) {
+                           long long *__restrict__ out1, const int *__restrict__ dx, int ring,
+                           double2 *__restrict__ out = nullptr, int ldo = 0, int cx = 1) {
     if (dx) {
         int j0 = 0;
         graph_range(dx, ring, j0, m);
+        if (out) out += j0;               // the one-level form only
     }
     const int sl = blockIdx.x;
     int lo = 0, hi = S - 1;
@@ -677,6 +692,12 @@ __global__ void k_reducex1(const long long *__restrict__ part, int m, const int 
     }
     ar = warp_sum_i128(ar);
     ai = warp_sum_i128(ai);
+    if (out) {
+        // one slice per sector: the slice sum is the sector's dot
+        if (lane == 0)
+            out[(uint64_t)s * ldo + j] = make_double2(i128_ldexp(ar, K - 2098), cx ? i128_ldexp(ai, K - 2098) : 0.0);
+        return;
+    }
     if (lane == 0) {
         long long *o = out1 + ((uint64_t)sl * m + j) * 5;
         o[0] = (long long)(unsigned long long)ar;
@@ -724,9 +745,17 @@ __global__ void k_reducex2(const long long *__restrict__ out1, int m, const int 
 }
 
 // both levels: the per-sector dot products of the last k_dotx launch
+// (nslices == S with one slice per sector, as reduce_slices reports: the
+// first level writes them)
 static int reducex_launch(const long long *part, long long *out1, int m, int mgrid, const int *chunk0,
                           const int *slice0, int nslices, int S, const int *active, double2 *out, int ldo,
-                          cudaStream_t st, const int *dx = nullptr, int ring = 0, int cx = 1) {
+                          cudaStream_t st, const int *dx = nullptr, int ring = 0, int cx = 1, bool one = false) {
+    if (one && nslices == S && S > 0) {
+        k_reducex1<<<dim3(nslices, (mgrid + 7) / 8), NTHREADS, 0, st>>>(part, m, chunk0, slice0, S, active, out1,
+                                                                         dx, ring, out, ldo, cx);
+        QS3_LAUNCHED();
+        return QS3_OK;
+    }
     if (nslices > 0) {
         k_reducex1<<<dim3(nslices, (mgrid + 7) / 8), NTHREADS, 0, st>>>(part, m, chunk0, slice0, S, active, out1,
                                                                          dx, ring);
@@ -991,64 +1020,54 @@ __device__ __forceinline__ float f_trunc_abs(double x) {
     return __int_as_float((e << 23) | ((hi & 0xfffff) << 3) | ((unsigned)__double2loint(x) >> 29));
 }
 
-// The three-term part of a step (Alg. 10): w -= sum_j psi_{j0+j} coef[s][j]
-// for m <= 2 stored vectors, in binary64 FMAs in the order of k_upd64, and
-// part[c] = a lower estimate of |w|^2 over chunk c (values truncated to 24
-// bits, squared and summed in fp32, the sum lowered by 2^-18 of itself): it
-// only feeds the test of the fp32 Gram-Schmidt correction, which a low |w|
-// makes stricter.  Two blocks per SM, so that one block's FMAs (the fp64
-// pipe is the bound) overlap another's loads.  Graph mode (dx): the range of
-// graph_range and, for the three-term pass (ring), coefficients from coef + j0.
+// The three-term part of step x (Alg. 10): w -= beta_{x-1} psi_{x-1} +
+// alpha_x psi_x with the recurrence's real scalars -- alpha_x the real part
+// of the dot psi_x^H w in h[s][x], beta_{x-1} from the previous step (none
+// for x = 0); what remains of w along psi_x and psi_{x-1} (the imaginary
+// part of the dot, rounding) goes to the Gram-Schmidt pass -- in binary64
+// FMAs (psi_{x-1} first), and part[c] = a lower estimate of |w|^2 over chunk
+// c (values truncated to 24 bits, squared and summed in fp32, the sum lowered
+// by 2^-18 of itself): it only feeds the test of the fp32 Gram-Schmidt
+// correction, which a low |w| makes stricter.  Two blocks per SM, so that one
+// block's FMAs (the fp64 pipe is the bound) overlap another's loads.  Graph
+// mode (dx): x = *dx.
 template <typename VT>
 __global__ void __launch_bounds__(XT, 2)
-    k_upd3(VT *__restrict__ w, const typename PlS<VT>::T *__restrict__ V, uint64_t D, int j0, int m,
-           const double2 *__restrict__ coef, int ldc, const SecView *__restrict__ secs,
+    k_upd3(VT *__restrict__ w, const typename PlS<VT>::T *__restrict__ V, uint64_t D, int x,
+           const double2 *__restrict__ h, const double *__restrict__ beta, int cap, const SecView *__restrict__ secs,
            const int *__restrict__ chunk0, int S, const int *__restrict__ active, double2 *__restrict__ part,
-           const int *__restrict__ dx = nullptr, int ring = 0) {
+           const int *__restrict__ dx = nullptr) {
     using T = typename PlS<VT>::T;
     constexpr bool CX = IsC<VT>::v;
-    if (dx) {
-        graph_range(dx, ring, j0, m);
-        if (ring) coef += j0;
-    }
+    if (dx) x = *dx;
     __shared__ float red[XW];
     const ChunkInfo ci = chunk_info(secs, chunk0, S, blockIdx.x);
     if (active && !active[ci.s]) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = (ci.n - (int)threadIdx.x + XT - 1) / XT;
     const uint64_t r0 = ci.base + threadIdx.x;
-    double2 acc[XR];
+    double2 acc[XR], p[XR], q[XR];
+    const T *sp = V + (uint64_t)(x > 0 ? x - 1 : 0) * 2 * D, *sq = V + (uint64_t)x * 2 * D;
 #pragma unroll
-    for (int k = 0; k < XR; ++k) acc[k] = k < nk ? ld2(w + r0 + (uint64_t)k * XT) : make_double2(0.0, 0.0);
-    double2 a[2][XR];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const T *slot = V + (uint64_t)(j0 + j) * 2 * D;
-#pragma unroll
-        for (int k = 0; k < XR; ++k)
-            a[j][k] = (j < m && k < nk) ? pl_ld(slot, D, r0 + (uint64_t)k * XT) : make_double2(0.0, 0.0);
+    for (int k = 0; k < XR; ++k) {
+        const bool in = k < nk;
+        const uint64_t r = r0 + (uint64_t)k * XT;
+        acc[k] = in ? ld2(w + r) : make_double2(0.0, 0.0);
+        p[k] = (in && x > 0) ? pl_ld(sp, D, r) : make_double2(0.0, 0.0);
+        q[k] = in ? pl_ld(sq, D, r) : make_double2(0.0, 0.0);
     }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        if (j < m) {
-            const double2 c = coef[(uint64_t)ci.s * ldc + j];
-#pragma unroll
-            for (int k = 0; k < XR; ++k) {
-                if (k < nk) {
-                    acc[k].x = fma(-a[j][k].x, c.x, acc[k].x);
-                    if (CX) {
-                        acc[k].x = fma(a[j][k].y, c.y, acc[k].x);
-                        acc[k].y = fma(-a[j][k].x, c.y, acc[k].y);
-                        acc[k].y = fma(-a[j][k].y, c.x, acc[k].y);
-                    }
-                }
-            }
-        }
-    }
+    const double a = h[(uint64_t)ci.s * cap + x].x;
+    const double b = x > 0 ? beta[(uint64_t)ci.s * cap + x - 1] : 0.0;
     float nf = 0.f;
 #pragma unroll
     for (int k = 0; k < XR; ++k) {
         if (k < nk) {
+            if (x > 0) {
+                acc[k].x = fma(-p[k].x, b, acc[k].x);
+                if (CX) acc[k].y = fma(-p[k].y, b, acc[k].y);
+            }
+            acc[k].x = fma(-q[k].x, a, acc[k].x);
+            if (CX) acc[k].y = fma(-q[k].y, a, acc[k].y);
             st2(w + r0 + (uint64_t)k * XT, acc[k]);
             const float fx = f_trunc_abs(acc[k].x);
             nf = fmaf(fx, fx, nf);
@@ -1065,7 +1084,7 @@ __global__ void __launch_bounds__(XT, 2)
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
-            for (int q = 0; q < XW; ++q) t += (double)red[q];
+            for (int qq = 0; qq < XW; ++qq) t += (double)red[qq];
             part[blockIdx.x] = make_double2(t * (1.0 - 0x1p-18), 0.0);
         }
     }
@@ -1181,6 +1200,7 @@ __global__ void __launch_bounds__(XT + 32, 2)
                     ok = false;
                     break;
                 }
+                fence_proxy_async();
                 issue(t);
                 if (++t == ns) {
                     t = 0;
@@ -1463,6 +1483,7 @@ struct Engine64 {
     uint64_t D = 0;
     DevBuf V, DG, GE, wbuf, hinb, part, partx, partr, slices, h1, h2, alpha, beta, nrm, nrm1, inv, active, derr;
     int nslices = 0;
+    bool slice1 = false;                   // one reduction slice per sector
     std::vector<int> h_active;
     double brk = 1e-12;
     int strict = 0;                        // 1: every update on binary64 FMAs
@@ -1516,6 +1537,7 @@ struct Engine64 {
         {
             const std::vector<int> s0 = reduce_slices(B);
             nslices = s0[B.S];
+            slice1 = one_slice(s0);
             QS3_TRY(slices.upload(s0.data(), s0.size() * sizeof(int)));
             QS3_TRY(partr.alloc((uint64_t)std::max(nslices, 1) * cap * 5 * sizeof(long long)));
         }
@@ -1579,7 +1601,8 @@ struct Engine64 {
     int dot_reduce(int m, double2 *out, int ldo, const int *dx = nullptr, int ring = 0, int mgrid = 0) {
         if (strict) return reduce(m, out, ldo, dx, ring, mgrid);
         return reducex_launch(partx.as<long long>(), partr.as<long long>(), m, mgrid > 0 ? mgrid : m, c0(),
-                              slices.as<int>(), nslices, B.S, act(), out, ldo, st, dx, ring, IsC<VT>::v ? 1 : 0);
+                              slices.as<int>(), nslices, B.S, act(), out, ldo, st, dx, ring, IsC<VT>::v ? 1 : 0,
+                              slice1);
     }
     // dot products of w against stored vectors j0 .. j0 + m - 1 into out (S x ldo)
     int mdot(int j0, int m, double2 *out, int ldo) {
@@ -1638,13 +1661,6 @@ struct Engine64 {
     // wn2: |w|^2 before it (enables the fp32 correction of tiny coefficients)
     int mupdate(int j0, int m, const double2 *cf, int ldc, double2 *nrm_out, const double2 *wn2 = nullptr) {
         if (B.nchunks == 0) return QS3_OK;
-        if (!wn2 && m <= 2) {
-            // the three-term part: its |w|^2 only feeds the test of the next pass
-            k_upd3<VT><<<grid(), XT, 0, st>>>(wv(), V.as<ST>(), D, j0, m, cf, ldc, secs(), c0(), B.S, act(),
-                                              part.as<double2>());
-            QS3_LAUNCHED();
-            return reduce(1, nrm_out, 1);
-        }
         if (updb_ok(wn2, m, m)) {
             const int ns = updb_ns<VT>(m);
             k_updb<VT><<<grid(), XT + 32, (size_t)ns * updb_stage<VT>() + (size_t)m * 24, st>>>(
@@ -1726,10 +1742,10 @@ struct Engine64 {
         VT *w = wv();
         double2 *hh1 = h1.as<double2>(), *n1 = nrm1.as<double2>();
         QS3_TRY(hphi_apply(0, dx));
-        QS3_TRY(dot_launch(2, 0, 2, dx, 1));
-        QS3_TRY(dot_reduce(2, hh1, cap, dx, 1, 2));
-        k_upd3<VT><<<grid(), XT, 0, st>>>(w, V.as<ST>(), D, 0, 2, hh1, cap, secs(), c0(), B.S, act(),
-                                          part.as<double2>(), dx, 1);
+        QS3_TRY(dot_launch(2, 0, 1, dx, 2));
+        QS3_TRY(dot_reduce(1, hh1, cap, dx, 2, 1));
+        k_upd3<VT><<<grid(), XT, 0, st>>>(w, V.as<ST>(), D, 0, hh1, beta.as<double>(), cap, secs(), c0(), B.S,
+                                          act(), part.as<double2>(), dx);
         QS3_LAUNCHED();
         QS3_TRY(reduce(1, n1, 1));
         QS3_TRY(dot_launch(B.tune_nv64 > 0 ? B.tune_nv64 : 2, 0, cap, dx, 0));
@@ -1809,10 +1825,19 @@ struct Engine64 {
         QS3_CUDA(cudaEventRecord(ev.second, st));
         stats->pend.push_back(ev);
         count_hphi();
-        const int j0 = full2 ? 0 : std::max(0, x - 1);
         double2 *n1 = nrm1.as<double2>();
-        QS3_TRY(mdot(j0, x + 1 - j0, h1.as<double2>() + j0, cap));
-        QS3_TRY(mupdate(j0, x + 1 - j0, h1.as<double2>() + j0, cap, n1));
+        if (full2) {
+            // after a thick restart: a full first pass with complex coefficients
+            QS3_TRY(mdot(0, x + 1, h1.as<double2>(), cap));
+            QS3_TRY(mupdate(0, x + 1, h1.as<double2>(), cap, n1));
+        } else {
+            // alpha_x = Re psi_x^H w, then w -= beta_{x-1} psi_{x-1} + alpha_x psi_x
+            QS3_TRY(mdot(x, 1, h1.as<double2>() + x, cap));
+            k_upd3<VT><<<grid(), XT, 0, st>>>(w, V.as<ST>(), D, x, h1.as<double2>(), beta.as<double>(), cap, secs(),
+                                              c0(), B.S, act(), part.as<double2>());
+            QS3_LAUNCHED();
+            QS3_TRY(reduce(1, n1, 1));
+        }
         QS3_TRY(gs_dots(x));
         QS3_TRY(mupdate(0, x + 1, h2.as<double2>(), cap, nrm.as<double2>(), n1));
         k_step_scalars<<<(B.S + 127) / 128, 128, 0, st>>>(B.S, x, cap, h1.as<double2>(), nrm.as<double2>(), act(),

@@ -518,9 +518,12 @@ __device__ __forceinline__ float4 ld_w(const float *p) { return make_float4(*p, 
 __device__ __forceinline__ float4 ld_w(const float2 *p) { const float2 v = *p; return make_float4(v.x, 0.f, v.y, 0.f); }
 // graph mode (dx): the three-term pass takes vectors x - 1, x (m = 2, x >= 1),
 // the full pass vectors 0 .. x
+// the stored vectors a kernel of the captured step reads, from x = *dx:
+// ring 0: psi_0 .. psi_x; ring 1: psi_{x-1}, psi_x; ring 2: psi_x alone
 __device__ __forceinline__ void graph_range(const int *dx, int ring, int &j0, int &m) {
     if (!dx) return;
-    if (ring) { j0 = *dx - 1; m = 2; }
+    if (ring == 2) { j0 = *dx; m = 1; }
+    else if (ring) { j0 = *dx - 1; m = 2; }
     else { j0 = 0; m = *dx + 1; }
 }
 
@@ -2649,7 +2652,7 @@ static int gs_dots_run(Basis &B, int m, const VT *V, uint64_t ldv, const VT *w, 
         QS3_TRY(dsl.upload(s0.data(), s0.size() * sizeof(int)));
         QS3_TRY(pr.alloc((uint64_t)std::max(s0[B.S], 1) * m * 5 * sizeof(long long)));
         QS3_TRY(reducex_launch(part.as<long long>(), pr.as<long long>(), m, m, c0, dsl.as<int>(), s0[B.S], B.S,
-                               nullptr, res.as<double2>(), m, st, nullptr, 0, IsC<VT>::v ? 1 : 0));
+                               nullptr, res.as<double2>(), m, st, nullptr, 0, IsC<VT>::v ? 1 : 0, one_slice(s0)));
     } else {
         k_dot64<VT, 2><<<B.nchunks, NTHREADS, 0, st>>>(pl.as<T>(), D, 0, m, w, secs, c0, B.S, nullptr,
                                                         part.as<double2>());

@@ -71,3 +71,20 @@ def test_tuning_rejects_bad_values():
         b.tuning(dot_vectors=8)
     with pytest.raises(qs3.QS3Error):
         b.tuning(hphi_blocks_per_sm=[-1, 0, 0, 0])
+
+
+def test_ring_solves_repeat_bit_identical():
+    """Solves on the copy rings (dot_vectors64 = 8: k_dotb and k_updb) repeat
+    bit for bit -- no ring stage is refilled before every warp has read it --
+    and equal the solves on the register-staged passes."""
+    torch_cuda()
+    import paper_2107_00872_gb300 as qs3
+    b = _basis()
+    o = qs3.SolveOpts(n_max=150, min_iter=20, check_every=5, eps=1e-14, res_tol=1e-12, use_graphs=False,
+                      precision="f64")
+    b.tuning(dot_vectors64=8)
+    runs = [b.lanczos(o, vectors=False)[0] for _ in range(3)]
+    b.tuning(dot_vectors64=2)
+    runs.append(b.lanczos(o, vectors=False)[0])
+    for e in runs[1:]:
+        np.testing.assert_array_equal(e, runs[0])
