@@ -13,10 +13,10 @@ throughput over the whole step: structural non-zeros applied by all H Phi
 launches of the step divided by the step time (Gnnz/s).
 
 Also reported:
-- roofline of the step's largest kernel (the binary64 Gram-Schmidt dot
-  products, bound by the fp64 FMA pipe) from CUDA events recorded inside the
-  library on the solve's stream, against the fp64 FMA rate measured in the
-  same run (qs3_probe_peaks), with its HBM fraction beside it;
+- roofline of the step's largest kernel (the Gram-Schmidt dot pass, exact
+  integer dots on the digit images, HBM-bound) from CUDA events recorded
+  inside the library on the solve's stream, against the measured HBM copy
+  bandwidth, with H Phi's figures beside it;
 - e2e: the same step through the C ABI from host buffers (basis built from
   host lattice arrays, eigenvectors copied back to host) per step;
 - variants of the same solve: strict64 (every Gram-Schmidt update on binary64
@@ -275,12 +275,15 @@ def run_ours(args, rank, world):
         "config": {"workload": args.workload + (f"_first{args.sectors}k" if args.sectors > 0 else ""),
                    "lattice": spec.name, "n_sites": spec.n_sites, "n_down": nd,
                    "sectors": basis.n_sectors, "total_dim": D, "nnz_per_hphi": nnz_h,
-                   "solver": "Lanczos with full reorthogonalisation every step on the binary64 engine: Lanczos "
-                             "vectors stored as IEEE binary64, H Phi and updates on binary64 FMAs; dot products "
-                             "summed exactly in 64-bit integers on 53-bit fixed-point images of the operands "
-                             "(each operand rounded once, by at most 2^-53 of the largest magnitude among its "
-                             "warp's 128 rows); the Gram-Schmidt update with coefficients below 2^-36 |w| in sum "
-                             "forms its correction in fp32 from the stored high words (error below 2^-55 |w|)",
+                   "solver": "Lanczos (Alg. 10) with full reorthogonalisation every step on the binary64 engine: "
+                             "Lanczos vectors stored as IEEE binary64 beside a fixed-point digit image; H Phi "
+                             "with each term formed exactly on the integer units and each row rounded once; "
+                             "alpha_x = Re psi_x^H w and the three-term update w -= beta psi_{x-1} + alpha psi_x "
+                             "in binary64 FMAs; dot products summed exactly in 64-bit integers on 53-bit "
+                             "fixed-point images of the operands (each rounded once, by at most 2^-53 of the "
+                             "largest magnitude among its warp's 128 rows); the Gram-Schmidt update with "
+                             "coefficients below 2^-40 |w| in sum forms its correction in fp32 from the top "
+                             "digits (error below 2^-55 |w|)",
                    "l2": "working set > L2 (Krylov basis of ~100 vectors x 63 MB)",
                    "parallelism": f"replicas x{world} (independent sectors per GPU)"},
         "roofline": roof,
