@@ -798,8 +798,10 @@ static int dotx_launch(int nv, const typename DigT<VT>::T *dg, const int *ge, in
         QS3_LAUNCHED();
         return QS3_OK;
     }
-    // complex rows stage at most 2 vectors (4 would spill registers)
+    // complex rows stage at most 2 vectors (4 would spill registers); a
+    // one-vector pass (alpha_x's dot) stages one
     if (nv >= 8 || small || IsC<VT>::v) nv = std::min(nv, 2);
+    if (ring == 2 || (!dx && m == 1)) nv = 1;
     const int g = std::max(nchunks, 1);
     if (nv == 1) {
         k_dotx<VT, 1><<<g, XT, 0, st>>>(dg, ge, nchunks, D, j0, m, w, secs, c0, S, act, pp, dx, ring);
@@ -1008,6 +1010,17 @@ __global__ void __launch_bounds__(XT)
             part[blockIdx.x] = make_double2(t, 0.0);
         }
     }
+}
+
+// a float as a double, exactly, in integer instructions (the conversion
+// instruction runs on the fp64 pipe): a normal float moves its exponent and
+// significand into place; zero, subnormals, inf and NaN take the conversion
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
 }
 
 // |x| with its significand truncated to 24 bits, as a float (0 below the
@@ -1283,8 +1296,8 @@ __global__ void __launch_bounds__(XT + 32, 2)
             if (k < nk) {
                 const uint64_t r = r0 + (uint64_t)k * XT;
                 double2 v = wr[k];
-                v.x -= (double)u[k].x;
-                if (CX) v.y -= (double)u[k].y;
+                v.x -= f2d_exact(u[k].x);
+                if (CX) v.y -= f2d_exact(u[k].y);
                 st2(w + r, v);
                 nrm = fma(v.x, v.x, nrm);
                 if (CX) nrm = fma(v.y, v.y, nrm);

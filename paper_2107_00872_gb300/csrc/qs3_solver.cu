@@ -1796,14 +1796,28 @@ __device__ double tri_lowest_warp(int n, const double *__restrict__ a, const dou
     lo -= 1e-3 * w;
     hi += 1e-3 * w;
     if (isfinite(e_prev) && e_prev > lo && e_prev < hi) {
-        // lane 0 tests e_prev + margin (must hold an eigenvalue below it),
-        // lane 1 e_prev - 1e-6 w (must hold none)
-        const double t = lane == 0 ? e_prev + 1e-12 * w : e_prev - 1e-6 * w;
-        const int c = lane < 2 ? sturm_count_dev(n, a, bb, t) : 0;
-        const int c0 = __shfl_sync(0xffffffffu, c, 0), c1 = __shfl_sync(0xffffffffu, c, 1);
-        const double t0 = __shfl_sync(0xffffffffu, t, 0), t1 = __shfl_sync(0xffffffffu, t, 1);
+        // lane 0 tests e_prev + margin (an eigenvalue lies below it), lanes
+        // 1..31 a ladder below e_prev at distances 1e-6 w 4^-(lane-1): the
+        // Ritz value moved down by a small, shrinking amount since e_prev,
+        // so the last ladder point without an eigenvalue below it and the
+        // first with one bracket it to within a factor of four of that move
+        const double t = lane == 0 ? e_prev + 1e-12 * w : e_prev - ldexp(1e-6 * w, -2 * (lane - 1));
+        const int c = sturm_count_dev(n, a, bb, t);
+        const unsigned some = __ballot_sync(0xffffffffu, lane > 0 && c > 0);   // counts rise with t
+        const unsigned none = __ballot_sync(0xffffffffu, lane > 0 && c == 0);
+        const int c0 = __shfl_sync(0xffffffffu, c, 0);
+        const double t0 = __shfl_sync(0xffffffffu, t, 0);
         if (c0 > 0 && t0 < hi) hi = t0;
-        if (c1 == 0 && t1 > lo) lo = t1;
+        if (none) {
+            const int jl = 31 - __clz(none);                                    // the highest point with none
+            const double tl = __shfl_sync(0xffffffffu, t, jl);
+            if (tl > lo && tl < hi) lo = tl;
+        }
+        const unsigned above = some & ~((2u << (31 - __clz(none | 1u))) - 1u);
+        if (above) {
+            const double th = __shfl_sync(0xffffffffu, t, __ffs(above) - 1);   // the lowest point above it with one
+            if (th < hi && th > lo) hi = th;
+        }
     }
     for (int it = 0; it < 64; ++it) {
         const double h = (hi - lo) / 32.0;
