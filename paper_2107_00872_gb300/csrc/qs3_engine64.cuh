@@ -13,10 +13,15 @@
 // reads an interleaved copy of psi_x (hin) written together with slot x.
 //
 // One step (Alg. 10 lines 5-11, full reorthogonalisation):
-//   w = H psi_x;  three-term part: c_j = psi_j^H w for j = x-1, x (alpha_x
-//   among them), w -= sum_j c_j psi_j;  one classical Gram-Schmidt pass:
-//   g_j = psi_j^H w for j = 0..x, w -= sum_j g_j psi_j;  beta_x = |w|;
-//   psi_{x+1} = w / beta_x.
+//   w = H psi_x;  alpha_x = Re psi_x^H w;  w -= beta_{x-1} psi_{x-1} +
+//   alpha_x psi_x (the recurrence, real scalars);  one classical
+//   Gram-Schmidt pass: g_j = psi_j^H w for j = 0..x, w -= sum_j g_j psi_j
+//   (it also removes what the recurrence left along psi_x, psi_{x-1});
+//   beta_x = |w|;  psi_{x+1} = w / beta_x.  The first step after a thick
+//   restart runs a full first pass with complex coefficients instead of the
+//   recurrence.  The Gram-Schmidt kernels read the digit store either with
+//   register staging (k_dotx, k_upd64) or through shared-memory rings filled
+//   by bulk asynchronous copies (k_dotb, k_updb), as the autotuner chooses.
 // Updates are binary64 FMA chains per thread.  Two exceptions, both bounded
 // below binary64's own rounding:
 //  - the dot products are exact sums on fixed-point images of the operands
