@@ -278,18 +278,23 @@ typedef struct {
 } qs3_solve_info;
 
 /* Conventional Lanczos with full reorthogonalisation (Alg. 10 lines 2-12)
- * to the lowest eigenpair of every sector, batched over the sectors.
+ * to the lowest eigenpair of every sector, batched over the sectors.  The
+ * QS3_F64 engine takes the recurrence as printed (alpha_x = Re psi_x^H v,
+ * v - alpha_x psi_x - beta_{x-1} psi_{x-1}) and then one classical
+ * Gram-Schmidt pass against every stored vector.
  * evals: host, n_sectors doubles.  evecs: device fp64 vector (F64 for a
  * U(1)-only basis, C128 otherwise) of the total dimension, or NULL.
  * Returns NOT_CONVERGED when n_max steps did not meet eps (results are the
- * last Ritz values). */
+ * last Ritz values), TIMEOUT when a bounded wait of a copy ring ran out (see
+ * qs3_inject_wait_timeout; the context stays usable). */
 int qs3_lanczos(qs3_basis_t b, const qs3_solve_opts *o, double *evals, void *evecs, qs3_solve_info *info,
                 void *stream);
 
 /* Thick-restart Lanczos (Alg. 10) for the n_eig lowest eigenpairs of every
  * sector, batched.  evals: host, n_sectors * n_eig (sector-major).  evecs:
  * device, n_eig fp64 vectors of the total dimension one after another, or
- * NULL. */
+ * NULL.  The first step after a restart removes the arrowhead couplings by
+ * a full first pass; errors as qs3_lanczos. */
 int qs3_trlanczos(qs3_basis_t b, const qs3_solve_opts *o, double *evals, void *evecs, qs3_solve_info *info,
                   void *stream);
 
