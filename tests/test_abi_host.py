@@ -139,6 +139,14 @@ def test_injected_allocation_failure_is_oom(qs3):
         assert qs3.inject_alloc_failure(prev) == 0
 
 
+def test_wait_timeout_injection_counter(qs3):
+    """The host side of the wait-timeout injection: a count of ring launches
+    to starve, set, read back and cleared (n <= 0 switches it off)."""
+    assert qs3.inject_wait_timeout(3) == 0
+    assert qs3.inject_wait_timeout(-5) == 3
+    assert qs3.inject_wait_timeout(0) == 0
+
+
 def test_null_handles(qs3):
     lib = qs3.load()
     assert lib.qs3_basis_create(None, 2, 1, None, None) == INVALID
